@@ -1,0 +1,469 @@
+"""Pins of the CPU oracle to facts fixed outside the oracle itself: published
+known-answer vectors, the order conditions of the Cash-Karp tableau, the
+analytic helix in a uniform field, time reversal of the Lorentz force, the
+spectral properties of the generated turbulence, closed forms of the
+interaction rates, blackbody integrals and sampling statistics.
+
+Each test states which published fact it checks; none re-types the oracle's
+own formula as its expected value.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------
+# Philox4x32-10 (Salmon et al., SC'11)
+# ---------------------------------------------------------------------------
+def test_philox_known_answers(oracle):
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(t, 16) for t in r]
+        out = oracle.philox4x32_10(v[0:4], v[4:6])
+        assert [int(o) for o in out] == v[6:10]
+
+
+def test_uniform_open_interval(oracle):
+    assert oracle.uniform_open(0, 0) == 2.0 ** -53
+    assert oracle.uniform_open(0xFFFFFFFF, 0xFFFFFFFF) == 1.0 - 2.0 ** -53
+    assert oracle.uniform_open(0, 0x80000000) == 0.5 + 2.0 ** -53
+
+
+def test_child_ids_unique(oracle):
+    ids = {oracle.child_id(p, e) for p in range(2000) for e in range(40)}
+    assert len(ids) == 2000 * 40
+    assert not (ids & set(range(2000)))
+
+
+# ---------------------------------------------------------------------------
+# Cash-Karp 5(4) tableau (Cash & Karp, ACM TOMS 16, 201, 1990): the Butcher
+# order conditions (rooted trees up to order 5 for the fifth-order weights,
+# up to order 4 for the embedded weights) hold exactly for the rationals the
+# oracle's doubles round from.
+# ---------------------------------------------------------------------------
+def _order_conditions(b, A, c, order):
+    """Residuals of the Butcher order conditions up to `order` (Fractions)."""
+    s = len(b)
+    dot = lambda u, v: sum(x * y for x, y in zip(u, v))
+    Av = lambda v: [sum(A[i][j] * v[j] for j in range(s)) for i in range(s)]
+    mul = lambda u, v: [x * y for x, y in zip(u, v)]
+    one = [Fraction(1)] * s
+    Ac = Av(c)
+    res = [dot(b, one) - 1]
+    if order >= 2:
+        res += [dot(b, c) - Fraction(1, 2)]
+    if order >= 3:
+        res += [dot(b, mul(c, c)) - Fraction(1, 3), dot(b, Ac) - Fraction(1, 6)]
+    if order >= 4:
+        c2 = mul(c, c)
+        res += [dot(b, mul(c2, c)) - Fraction(1, 4), dot(b, mul(c, Ac)) - Fraction(1, 8),
+                dot(b, Av(c2)) - Fraction(1, 12), dot(b, Av(Ac)) - Fraction(1, 24)]
+    if order >= 5:
+        c2 = mul(c, c)
+        c3 = mul(c2, c)
+        res += [dot(b, mul(c2, c2)) - Fraction(1, 5),
+                dot(b, mul(c2, Ac)) - Fraction(1, 10),
+                dot(b, mul(Ac, Ac)) - Fraction(1, 20),
+                dot(b, mul(c, Av(c2))) - Fraction(1, 15),
+                dot(b, Av(c3)) - Fraction(1, 20),
+                dot(b, mul(c, Av(Ac))) - Fraction(1, 30),
+                dot(b, Av(mul(c, Ac))) - Fraction(1, 40),
+                dot(b, Av(Av(c2))) - Fraction(1, 60),
+                dot(b, Av(Av(Ac))) - Fraction(1, 120)]
+    return res
+
+
+def test_cash_karp_order_conditions(oracle):
+    T = oracle.cash_karp_tableau()
+    F = {k: Fraction(v).limit_denominator(10 ** 6) for k, v in T.items()}
+    for k, v in T.items():  # each double is the nearest double of its rational
+        assert float(F[k]) == v, k
+    A = [[Fraction(0)] * 6 for _ in range(6)]
+    A[1][0] = F["b21"]
+    A[2][:2] = [F["b31"], F["b32"]]
+    A[3][:3] = [F["b41"], F["b42"], F["b43"]]
+    A[4][:4] = [F["b51"], F["b52"], F["b53"], F["b54"]]
+    A[5][:5] = [F["b61"], F["b62"], F["b63"], F["b64"], F["b65"]]
+    c = [sum(row) for row in A]           # row-sum nodes
+    assert c == [0, Fraction(1, 5), Fraction(3, 10), Fraction(3, 5), 1, Fraction(7, 8)]
+    b5 = [F["c1"], Fraction(0), F["c3"], F["c4"], Fraction(0), F["c6"]]
+    e = [F["e1"], Fraction(0), F["e3"], F["e4"], F["e5"], F["e6"]]
+    b4 = [x - y for x, y in zip(b5, e)]
+    assert all(r == 0 for r in _order_conditions(b5, A, c, 5))
+    assert all(r == 0 for r in _order_conditions(b4, A, c, 4))
+    # the embedded pair really differs at fifth order (the error estimate is live)
+    assert any(r != 0 for r in _order_conditions(b4, A, c, 5))
+
+
+# ---------------------------------------------------------------------------
+# Uniform field: analytic helix with Larmor radius r_L = E / (Z e c B).
+# ---------------------------------------------------------------------------
+def _uniform_field(n=4, bz=1.0):
+    B = np.zeros((n, n, n, 3))
+    B[..., 2] = bz
+    return B
+
+
+def _one(E, ux=1.0, uy=0.0, uz=0.0, A=1, Z=1, q=1, s_max=1.0, x=(0.0, 0.0, 0.0), n=1):
+    return dict(id=np.arange(n, dtype=np.uint64), x=np.full(n, x[0]), y=np.full(n, x[1]),
+                z=np.full(n, x[2]), ux=np.full(n, ux), uy=np.full(n, uy), uz=np.full(n, uz),
+                E=np.full(n, E), A=np.full(n, A, np.int32), Z=np.full(n, Z, np.int32),
+                q=np.full(n, q, np.int32), s_max=np.full(n, s_max))
+
+
+def _larmor_mpc(E_eV, Z, B_nG):
+    # SI: r = p c / (Z e c B) = E[J] / (Z e c B[T]) = E[eV] / (Z c B[T]) metres
+    return E_eV / (Z * 299792458.0 * B_nG * 1e-13) / 3.0856775814913673e22
+
+
+def test_helix_half_turn(oracle):
+    E = 1e19
+    rl = _larmor_mpc(E, 1, 1.0)
+    assert abs(rl - 10.810) < 1e-3  # 1.0810 Mpc per EeV per nG, times 10 EeV
+    P = oracle.make_params(grid_n=(4, 4, 4), spacing=1.0, tol=1e-9, h_min=1e-6, h_max=1.0)
+    r = oracle.propagate(P, _uniform_field(), _one(E, s_max=math.pi * rl))[0]
+    # positive charge, u = +x, B = +z: force along -y, centre at (0, -r_L, 0)
+    assert np.allclose(r["x"], [0.0, -2.0 * rl, 0.0], atol=1e-6 * rl)
+    assert np.allclose(r["u"], [-1.0, 0.0, 0.0], atol=1e-7)
+    assert abs(np.linalg.norm(r["u"]) - 1.0) < 1e-14
+    assert r["E"] == E and r["status"] == oracle.MAX_LENGTH and r["s"] == math.pi * rl
+
+
+def test_helix_pitch_and_antiparticle(oracle):
+    E, rl = 3e19, _larmor_mpc(3e19, 2, 1.0)
+    ct = 0.6
+    P = oracle.make_params(grid_n=(4, 4, 4), spacing=1.0, tol=1e-9, h_min=1e-6, h_max=1.0)
+    inj = _one(E, ux=0.8, uz=ct, A=4, Z=2, q=-1, s_max=2 * math.pi * rl)
+    r = oracle.propagate(P, _uniform_field(), inj)[0]
+    # u precesses about B at 1/r_L per unit path whatever the pitch: after
+    # s = 2 pi r_L one full gyration, drift along B = s cos(pitch)
+    assert np.allclose(r["x"], [0.0, 0.0, ct * 2 * math.pi * rl], atol=1e-6 * rl)
+    # antiparticle (q = -1) gyrates the other way: after a quarter turn
+    inj["s_max"] = np.full(1, 0.5 * math.pi * rl)
+    r = oracle.propagate(P, _uniform_field(), inj)[0]
+    assert np.allclose(r["x"][:2], [0.8 * rl, 0.8 * rl], atol=1e-6 * rl)
+
+
+def test_convergence_order_five(oracle):
+    """Global error of fixed-step Cash-Karp on the helix falls as h^5."""
+    E = 1e19
+    rl = _larmor_mpc(E, 1, 1.0)
+    errs = []
+    s = 4.0 * rl
+    for m in (16, 32, 64):
+        h = rl / m
+        P = oracle.make_params(grid_n=(4, 4, 4), spacing=1.0, tol=1e30, h_min=h, h_max=h)
+        r = oracle.propagate(P, _uniform_field(), _one(E, s_max=s))[0]
+        assert r["n_acc"] in (4 * m, 4 * m + 1)  # last step may be a rounding sliver
+        exact = np.array([rl * math.sin(s / rl), -rl * (1 - math.cos(s / rl)), 0.0])
+        errs.append(np.linalg.norm(r["x"] - exact))
+    slopes = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(4.7 < sl < 5.4 for sl in slopes), (errs, slopes)
+
+
+# ---------------------------------------------------------------------------
+# Time reversal: reversing the direction and the charge retraces the path.
+# ---------------------------------------------------------------------------
+def test_backtrack_returns_to_start(oracle):
+    n, dx = (32, 32, 32), 0.25
+    B = oracle.turbulent_field(n, dx, 0.5, 4.0, 1.0, seed=11)
+    P = oracle.make_params(grid_n=n, spacing=dx, tol=1e-10, h_min=1e-5, h_max=0.5)
+    m = 16
+    g = np.random.default_rng(5)
+    v = g.normal(size=(m, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    inj = _one(3e19, n=m, s_max=20.0)
+    inj["ux"], inj["uy"], inj["uz"] = v[:, 0].copy(), v[:, 1].copy(), v[:, 2].copy()
+    fwd = oracle.propagate(P, B, inj)
+    back = _one(3e19, n=m, s_max=20.0, q=-1)
+    back["x"], back["y"], back["z"] = (fwd["x"][:, i].copy() for i in range(3))
+    back["ux"], back["uy"], back["uz"] = (-fwd["u"][:, i] for i in range(3))
+    ret = oracle.propagate(P, B, back)
+    d = np.linalg.norm(ret["x"], axis=1)
+    assert np.all(d < 1e-5), d
+    # and it really was deflected on the way out
+    assert np.max(np.linalg.norm(fwd["u"] - v, axis=1)) > 0.05
+
+
+# ---------------------------------------------------------------------------
+# Trilinear interpolation on the periodic vertex-centred grid: exact for
+# fields that are linear inside a cell, periodic with the tile.
+# ---------------------------------------------------------------------------
+def test_trilinear_exact_on_linear_and_periodic(oracle):
+    n, dx, org = (5, 6, 7), 0.5, (-1.0, 2.0, 0.25)
+    ii, jj, kk = np.meshgrid(np.arange(n[0]), np.arange(n[1]), np.arange(n[2]), indexing="ij")
+    # field [nz, ny, nx, 3]: component c = c-th affine function of the node position
+    X = org[0] + ii * dx
+    Y = org[1] + jj * dx
+    Zc = org[2] + kk * dx
+    comps = [1.0 + 2.0 * X - Y + 0.5 * Zc, -3.0 + 0.25 * X + Y, 4.0 * Zc - X]
+    field = np.stack([c.transpose(2, 1, 0) for c in comps], axis=-1)
+    P = oracle.make_params(grid_n=n, spacing=dx, origin=org)
+    g = np.random.default_rng(0)
+    # points strictly inside the last-but-one cell range (no wrap needed)
+    lo = np.array(org)
+    hi = lo + (np.array(n) - 1) * dx
+    pts = lo + g.random((200, 3)) * (hi - lo)
+    got = oracle.field_at(P, field, pts)
+    x, y, z = pts[:, 0], pts[:, 1], pts[:, 2]
+    want = np.stack([1.0 + 2.0 * x - y + 0.5 * z, -3.0 + 0.25 * x + y, 4.0 * z - x], axis=1)
+    assert np.allclose(got, want, rtol=0, atol=1e-12)
+    # periodicity: shifting by a whole tile gives identical bits
+    shift = np.array(n) * dx * np.array([2, -1, 3])
+    assert np.array_equal(oracle.field_at(P, field, pts + 0 * shift), got)
+    got2 = oracle.field_at(P, field, pts + shift)
+    assert np.allclose(got2, got, atol=1e-12)
+    # nodes give node values exactly
+    node = np.array([[org[0] + 2 * dx, org[1] + 3 * dx, org[2] + 4 * dx]])
+    assert np.array_equal(oracle.field_at(P, field, node)[0], field[4, 3, 2])
+
+
+# ---------------------------------------------------------------------------
+# Turbulence: divergence free, band limited, k^(-11/3), zero mean, exact rms.
+# ---------------------------------------------------------------------------
+def test_turbulence_spectrum(oracle):
+    N, dx, lmin, lmax, brms = 64, 0.25, 0.5, 8.0, 1.0
+    B = oracle.turbulent_field((N, N, N), dx, lmin, lmax, brms, seed=3)
+    assert B.shape == (N, N, N, 3)
+    assert np.max(np.abs(B.mean(axis=(0, 1, 2)))) < 1e-14
+    assert abs(math.sqrt(np.mean(np.sum(B * B, axis=-1))) - brms) < 1e-13
+    Bk = np.stack([np.fft.fftn(B[..., c]) for c in range(3)], axis=-1)
+    f = np.fft.fftfreq(N) * N
+    mz, my, mx = np.meshgrid(f, f, f, indexing="ij")
+    kv = 2 * np.pi / (N * dx) * np.stack([mx, my, mz], axis=-1)
+    kk = np.linalg.norm(kv, axis=-1)
+    power = np.sum(np.abs(Bk) ** 2, axis=-1)
+    band = (kk >= 2 * np.pi / lmax) & (kk <= 2 * np.pi / lmin)
+    assert power[~band].sum() < 1e-24 * power.sum()
+    live = band & (power > 1e-12 * power.max())
+    div = np.abs(np.sum(kv * Bk, axis=-1))[live] / (kk[live] * np.sqrt(power[live]))
+    assert div.max() < 1e-12
+    # shell-averaged power per mode ~ k^(-11/3)
+    edges = np.geomspace(2 * np.pi / lmax, 2 * np.pi / lmin, 9)
+    kc, pc = [], []
+    for a, b in zip(edges[:-1], edges[1:]):
+        m = band & (kk >= a) & (kk < b)
+        if m.sum() > 20:
+            kc.append(np.exp(np.mean(np.log(kk[m]))))
+            pc.append(power[m].mean())
+    slope = np.polyfit(np.log(kc), np.log(pc), 1)[0]
+    assert abs(slope - (-11.0 / 3.0)) < 0.15, slope
+
+
+def test_turbulence_seed_dependence(oracle):
+    a = oracle.turbulent_field((16, 16, 16), 0.25, 0.5, 4.0, 1.0, seed=1)
+    b = oracle.turbulent_field((16, 16, 16), 0.25, 0.5, 4.0, 1.0, seed=1)
+    c = oracle.turbulent_field((16, 16, 16), 0.25, 0.5, 4.0, 1.0, seed=2)
+    assert np.array_equal(a, b)
+    assert np.abs(a - c).max() > 0.1
+
+
+# ---------------------------------------------------------------------------
+# Photon field and interaction rates.
+# ---------------------------------------------------------------------------
+def test_blackbody_number_density(oracle):
+    from scipy.integrate import quad
+    T = 2.725
+    kT = oracle.KB_EV * T
+    n, _ = quad(lambda x: oracle.planck_density(x * kT, T) * kT, 1e-8, 200, limit=400)
+    # n = 2 zeta(3) / pi^2 (kT / hbar c)^3 ; 410.5 per cm^3 at 2.725 K
+    zeta3 = 1.2020569031595942
+    closed = 2 * zeta3 / math.pi ** 2 * (kT / oracle.HBARC_EVM) ** 3
+    assert abs(n / closed - 1) < 1e-9
+    assert abs(n * 1e-6 - 410.5) < 0.5
+
+
+def test_phi_pair_branches(oracle):
+    # low-kappa limit (Blumenthal 1970): phi -> (pi/12) (kappa - 2)^4
+    for k in (2.001, 2.01):
+        assert abs(oracle.phi_pair(k) / (math.pi / 12 * (k - 2) ** 4) - 1) < 1e-2 * (k - 2) * 100
+    # the two fitted branches of Chodorowski et al. (1992) meet at kappa = 25
+    lo, hi = oracle.phi_pair(25 - 1e-9), oracle.phi_pair(25.0)
+    assert abs(lo / hi - 1) < 2e-3
+    assert oracle.phi_pair(2.0) == 0.0
+    # monotone increasing above threshold
+    ks = np.geomspace(2.01, 1e6, 400)
+    v = np.array([oracle.phi_pair(k) for k in ks])
+    assert np.all(np.diff(v) > 0)
+
+
+def test_pair_loss_length_literature_shape(oracle):
+    """Proton pair-production loss length on the CMB: minimum of roughly
+    1-1.5 Gpc near 10^19.5 eV (Blumenthal 1970, Chodorowski et al. 1992),
+    rising steeply towards 10^18 eV."""
+    lE = np.linspace(18.0, 21.0, 31)
+    L = np.array([1 / oracle.beta_pair_proton(10 ** e / oracle.MP_C2_EV) / oracle.MPC_M
+                  for e in lE])
+    i = int(np.argmin(L))
+    assert 19.2 <= lE[i] <= 19.8
+    assert 900 < L[i] < 1500
+    assert L[0] > 10 * L[i]
+
+
+def test_pair_loss_quadrature_converged(oracle):
+    from scipy.integrate import quad
+    g = 10 ** 19.5 / oracle.MP_C2_EV
+    T = 2.725
+    kT = oracle.KB_EV * T
+    me = 0.51099895e6
+    f = lambda k: oracle.planck_density(k * me / (2 * g), T) * oracle.phi_pair(k) / k ** 2
+    kmax = 1400 * g * kT / me
+    I = quad(f, 2, 25, limit=500, epsrel=1e-12)[0] + quad(f, 25, kmax, limit=500, epsrel=1e-12)[0]
+    alpha, re = 7.2973525693e-3, 2.8179403262e-15
+    beta = alpha * re ** 2 * me ** 2 * I / (g * oracle.MP_C2_EV)
+    assert abs(beta / oracle.beta_pair_proton(g) - 1) < 1e-8
+
+
+def _rate_definition(oracle, gamma, inner, eps_lo):
+    """R = 1/(2 Gamma^2) int d eps n(eps)/eps^2 inner(2 Gamma eps), by quadrature."""
+    from scipy.integrate import quad
+    T = 2.725
+    kT = oracle.KB_EV * T
+    f = lambda eps: oracle.planck_density(eps, T) / eps ** 2 * inner(2 * gamma * eps)
+    hi = 700 * kT
+    pts = np.geomspace(max(eps_lo, 1e-12 * kT), hi, 60)
+    I = sum(quad(f, a, b, epsrel=1e-11, limit=200)[0] for a, b in zip(pts[:-1], pts[1:]))
+    return I / (2 * gamma ** 2)
+
+
+def test_pion_rate_closed_form_vs_definition(oracle):
+    s0, eth = 0.5e-31, 145e6
+    inner = lambda emax: 0.0 if emax <= eth else s0 * (emax ** 2 - eth ** 2) / 2
+    for lE in (19.6, 20.0, 20.5, 21.0):
+        g = 10 ** lE / oracle.MP_C2_EV
+        want = _rate_definition(oracle, g, inner, eth / (2 * g))
+        assert abs(oracle.rate_pion_nucleon(g) / want - 1) < 1e-7, lE
+    # high-Gamma limit: every photon is above threshold, R -> sigma0 n_gamma
+    kT = oracle.KB_EV * 2.725
+    n_gamma = 2 * 1.2020569031595942 / math.pi ** 2 * (kT / oracle.HBARC_EVM) ** 3
+    assert abs(oracle.rate_pion_nucleon(1e16) / (s0 * n_gamma) - 1) < 1e-4
+    assert oracle.rate_pion_nucleon(1e8) < 1e-60
+
+
+def test_gdr_rate_vs_definition(oracle):
+    from scipy.integrate import quad
+    s_pk, ec, w, lo, hi = 1.5e-31, 20e6, 3e6, 8e6, 150e6
+    sig = lambda e: s_pk * w * w / ((e - ec) ** 2 + w * w) if lo <= e <= hi else 0.0
+
+    def inner(emax):
+        if emax <= lo:
+            return 0.0
+        return quad(lambda e: e * sig(e), lo, min(emax, hi), points=[ec], epsrel=1e-12)[0]
+
+    for lE in (19.5, 20.0, 20.5):
+        g = 10 ** lE / (56 * oracle.MP_C2_EV)
+        want = _rate_definition(oracle, g, inner, lo / (2 * g))
+        assert abs(oracle.rate_gdr_nucleon(g) / want - 1) < 1e-6, lE
+
+
+# ---------------------------------------------------------------------------
+# Module cycle: sampling, resets, observer, losses.
+# ---------------------------------------------------------------------------
+def _tables(oracle):
+    return oracle.tables_build(n=200, g_lo=1e6, g_hi=1e13)
+
+
+def test_pion_free_paths_are_exponential(oracle):
+    """P(no event within s) = exp(-R s): neutrons at constant high Gamma."""
+    T = _tables(oracle)
+    g = 1e12
+    R = np.interp(np.log(g), np.linspace(np.log(1e6), np.log(1e13), 200), T.rate_pion)
+    n = 4000
+    inj = _one(g * oracle.MP_C2_EV, A=1, Z=0, n=n, s_max=1.0 / R)
+    P = oracle.make_params(grid_n=(4, 4, 4), spacing=1.0, tables=T, flags=oracle.PION,
+                           seed=77, h_max=1.0)
+    r = oracle.propagate(P, _uniform_field(), inj, tables=T)
+    none = np.mean(r["n_pion"] == 0)
+    sd = math.sqrt(math.exp(-1) * (1 - math.exp(-1)) / n)
+    assert abs(none - math.exp(-1)) < 4 * sd
+    # one uniform per reset, reset at start and after each event
+    assert np.all(r["draws"] == 1 + r["n_pion"])
+
+
+def test_photodisintegration_branching_and_lineage(oracle):
+    T = _tables(oracle)
+    n = 3000
+    E = 10 ** 20.6  # nitrogen: Gamma ~ 3e10, short GDR free path
+    inj = _one(E, A=14, Z=7, n=n, s_max=0.05)
+    P = oracle.make_params(grid_n=(4, 4, 4), spacing=1.0, tables=T, flags=oracle.PHOTODIS,
+                           seed=5, h_max=0.1, h_min=1e-4)
+    r = oracle.propagate(P, np.zeros((4, 4, 4, 3)), inj, tables=T)
+    prim = r[r["generation"] == 0]
+    sec = r[r["generation"] == 1]
+    assert len(prim) == n and len(sec) == prim["n_pd"].sum()
+    # nucleon number and charge are conserved per lineage
+    by_parent = {}
+    for s in sec:
+        by_parent.setdefault(int(s["parent_id"]), []).append(s)
+    for p in prim:
+        kids = by_parent.get(int(p["id"]), [])
+        assert p["A"] + len(kids) == 14
+        assert p["Z"] + sum(int(k["Z"]) for k in kids) == 7
+        # energy per nucleon is conserved by the emission
+        for k in kids:
+            assert k["A"] == 1
+    # first emission from N-14: proton with probability Z/A = 1/2
+    firsts = []
+    for pid, kids in by_parent.items():
+        k0 = [k for k in kids if int(k["id"]) == oracle.child_id(pid, 0)]
+        firsts.append(int(k0[0]["Z"]))
+    frac = np.mean(firsts)
+    assert abs(frac - 0.5) < 4 * math.sqrt(0.25 / len(firsts))
+    # draws: one per interaction per reset, plus one branching draw per event
+    assert np.all(prim["draws"] == 1 + 2 * prim["n_pd"])
+    # ids: lineage-derived and unique
+    assert len(np.unique(r["id"])) == len(r)
+
+
+def test_observer_sphere_straight_lines(oracle):
+    """Neutral particles fly straight: detection iff the line passes within R."""
+    g = np.random.default_rng(9)
+    m = 400
+    start = np.array([5.0, 0.0, 0.0])
+    tgt = g.uniform(-2, 2, size=(m, 3))
+    tgt[:, 0] = 0.0
+    v = tgt - start
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    inj = _one(1e20, A=1, Z=0, n=m, s_max=20.0, x=start)
+    inj["ux"], inj["uy"], inj["uz"] = v[:, 0].copy(), v[:, 1].copy(), v[:, 2].copy()
+    P = oracle.make_params(grid_n=(4, 4, 4), spacing=1.0, flags=oracle.OBSERVER, obs_r=1.0,
+                           h_max=0.7)
+    r = oracle.propagate(P, _uniform_field(), inj)
+    # impact parameter of the line start + t v with respect to the origin
+    b = np.linalg.norm(np.cross(start, v), axis=1)
+    det = r["status"] == oracle.DETECTED
+    assert np.array_equal(det, b < 1.0)
+    # started inside never detects
+    inj2 = _one(1e20, A=1, Z=0, n=1, s_max=5.0, x=(0.2, 0.0, 0.0))
+    assert oracle.propagate(P, _uniform_field(), inj2)[0]["status"] == oracle.MAX_LENGTH
+
+
+def test_losses_only_adiabatic_closed_form(oracle):
+    """With only the adiabatic loss, E after n fixed steps is E0 (1 - b h)^n."""
+    h, b = 0.5, 1.0 / 4454.0
+    P = oracle.make_params(grid_n=(4, 4, 4), spacing=1.0, flags=oracle.ADIABATIC, beta_ad=b,
+                           h_min=h, h_max=h, tol=1e30)
+    r = oracle.propagate(P, _uniform_field(bz=0.0), _one(1e19, Z=0, s_max=100 * h))[0]
+    assert r["n_acc"] == 100
+    assert abs(r["E"] / (1e19 * (1 - b * h) ** 100) - 1) < 1e-13
+
+
+def test_emin_break_and_status(oracle):
+    P = oracle.make_params(grid_n=(4, 4, 4), spacing=1.0, flags=oracle.ADIABATIC | oracle.EMIN,
+                           beta_ad=0.01, e_min=0.9e19, h_min=1.0, h_max=1.0, tol=1e30)
+    r = oracle.propagate(P, _uniform_field(bz=0.0), _one(1e19, Z=0, s_max=1e3))[0]
+    # (1 - 0.01)^k < 0.9 first at k = 11
+    assert r["status"] == oracle.BELOW_EMIN and r["n_acc"] == 11
+
+
+def test_step_budget_status(oracle):
+    P = oracle.make_params(grid_n=(4, 4, 4), spacing=1.0, h_min=0.1, h_max=0.1, max_steps=7)
+    r = oracle.propagate(P, _uniform_field(), _one(1e19, s_max=1e3))[0]
+    assert r["status"] == oracle.BUDGET and r["n_acc"] == 7

@@ -1,0 +1,134 @@
+"""Seeded synthetic workloads shaped like the paper's scenarios.
+
+This module only draws injection arrays and holds workload sizes.  It contains
+none of the propagation method's arithmetic, so the CUDA library and the CPU
+oracle can both be fed from it.  Draws use numpy's Philox bit generator keyed
+by the workload seed; the arrays are handed bit-identically to both sides.
+
+Source model (the paper's Sect. 3 source class composed of position,
+spectrum and composition properties):
+  * spectrum: power law dN/dE ~ E^-2 between e_lo and e_hi by inverse CDF;
+  * directions: isotropic, cos(theta) = 2 u1 - 1, phi = 2 pi u2;
+  * composition: by number fractions over (A, Z) species;
+  * positions: one point, or a set of uniform sources in a box.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+MASTER_SEED = 1307264300
+
+# (A, Z, fraction by number) of the mixed composition: H, He, N, Fe
+MIXED_COMPOSITION = ((1, 1, 0.40), (4, 2, 0.25), (14, 7, 0.20), (56, 26, 0.15))
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(key=seed))
+
+
+def power_law_e2(g, n, e_lo, e_hi):
+    """E^-2 by inverse CDF; e_lo / e_hi may be arrays (per-candidate bounds)."""
+    u = g.random(n)
+    return 1.0 / (1.0 / e_lo - u * (1.0 / e_lo - 1.0 / e_hi))
+
+
+def isotropic(g, n):
+    u1, u2 = g.random(n), g.random(n)
+    ct = 2.0 * u1 - 1.0
+    st = np.sqrt(np.maximum(0.0, 1.0 - ct * ct))
+    ph = 2.0 * np.pi * u2
+    return st * np.cos(ph), st * np.sin(ph), ct
+
+
+# ---------------------------------------------------------------------------
+# Workload descriptions (field, integrator, modules); units Mpc / nG / eV for
+# the extragalactic ones, kpc / microgauss for the galactic one.
+# ---------------------------------------------------------------------------
+PLAIN_SMALL = dict(          # 10^4 protons, 64^3 float64 field, no interactions
+    name="plain_small_1e4p_64cube_f64",
+    n=10_000, grid_n=(64, 64, 64), spacing=0.25, lmin=0.5, lmax=8.0, brms=1.0,
+    field_dtype="f64", tol=1e-4, h_min=0.01, h_max=1.0, s_max=50.0,
+    e_lo=1e19, e_hi=1e20, seed=MASTER_SEED + 1,
+)
+
+MIXED_INTERACTIONS = dict(   # 10^6 mixed nuclei, 256^3 float32 field, losses + pion
+    name="mixed_1e6_256cube_f32_pair_adiab_pion_observer",
+    n=1_000_000, grid_n=(256, 256, 256), spacing=0.1, lmin=0.2, lmax=5.0, brms=1.0,
+    field_dtype="f32", tol=1e-4, h_min=0.01, h_max=1.0, s_max=500.0,
+    e_lo=1e18, e_hi_per_z=1e21 / 26.0, e_min=1e18, n_sources=1000, box=50.0,
+    observer_r=1.0, seed=MASTER_SEED + 2,
+)
+
+UNEVEN_SECONDARIES = dict(   # 10^7, 512^3 float32 field, photodisintegration + queue
+    name="uneven_1e7_512cube_f32_photodis_queue",
+    n=10_000_000, grid_n=(512, 512, 512), spacing=0.25, lmin=0.5, lmax=8.0,
+    brms_lo=0.1, brms_hi=10.0, field_dtype="f32", tol=1e-4, h_min=0.01, h_max=1.0,
+    s_lo=1.0, s_hi=2000.0, e_lo=1e18, e_hi_per_z=1e21 / 26.0, e_min=1e18, n_sources=1000,
+    box=50.0, observer_r=1.0, seed=MASTER_SEED + 3,
+)
+
+
+def plain_small(n=None, seed=None):
+    """Protons from the origin, E^-2 on [1e19, 1e20] eV, isotropic."""
+    w = PLAIN_SMALL
+    n = w["n"] if n is None else n
+    g = rng(w["seed"] if seed is None else seed)
+    E = power_law_e2(g, n, w["e_lo"], w["e_hi"])
+    ux, uy, uz = isotropic(g, n)
+    z = np.zeros(n)
+    return dict(id=np.arange(n, dtype=np.uint64), x=z.copy(), y=z.copy(), z=z.copy(),
+                ux=ux, uy=uy, uz=uz, E=E, A=np.ones(n, np.int32), Z=np.ones(n, np.int32),
+                q=np.ones(n, np.int32), s_max=np.full(n, w["s_max"]))
+
+
+def _sources(g, n_sources, box, r_excl):
+    pts = np.empty((0, 3))
+    while len(pts) < n_sources:
+        p = g.uniform(-box, box, size=(n_sources, 3))
+        p = p[np.sum(p * p, axis=1) > r_excl * r_excl]
+        pts = np.concatenate([pts, p])
+    return pts[:n_sources]
+
+
+def _mixed(g, n, w):
+    frac = np.array([c[2] for c in MIXED_COMPOSITION])
+    species = np.searchsorted(np.cumsum(frac), g.random(n), side="right")
+    species = np.minimum(species, len(frac) - 1)
+    A = np.array([c[0] for c in MIXED_COMPOSITION], np.int32)[species]
+    Z = np.array([c[1] for c in MIXED_COMPOSITION], np.int32)[species]
+    E = power_law_e2(g, n, w["e_lo"], w["e_hi_per_z"] * Z)
+    src = _sources(g, w["n_sources"], w["box"], w["observer_r"])
+    which = g.integers(0, w["n_sources"], size=n)
+    ux, uy, uz = isotropic(g, n)
+    pos = src[which]
+    return dict(id=np.arange(n, dtype=np.uint64), x=pos[:, 0].copy(), y=pos[:, 1].copy(),
+                z=pos[:, 2].copy(), ux=ux, uy=uy, uz=uz, E=E, A=A, Z=Z,
+                q=np.ones(n, np.int32))
+
+
+def mixed_interactions(n=None, seed=None):
+    """Mixed H/He/N/Fe from 1000 uniform sources in a 100 Mpc box."""
+    w = MIXED_INTERACTIONS
+    n = w["n"] if n is None else n
+    g = rng(w["seed"] if seed is None else seed)
+    d = _mixed(g, n, w)
+    d["s_max"] = np.full(n, w["s_max"])
+    return d
+
+
+def uneven_secondaries(n=None, seed=None):
+    """As the mixed workload, with per-candidate path budgets log-uniform in
+    [1 Mpc, 2 Gpc]; also returns the run's B_rms (log-uniform in [0.1, 10] nG)."""
+    w = UNEVEN_SECONDARIES
+    n = w["n"] if n is None else n
+    g = rng(w["seed"] if seed is None else seed)
+    brms = float(np.exp(g.uniform(np.log(w["brms_lo"]), np.log(w["brms_hi"]))))
+    d = _mixed(g, n, w)
+    d["s_max"] = np.exp(g.uniform(np.log(w["s_lo"]), np.log(w["s_hi"]), size=n))
+    return d, brms
+
+
+def subsample(inj: dict, idx) -> dict:
+    """Candidates with the given indices (ids are kept, so every stochastic
+    history is the same as in the full run)."""
+    return {k: np.ascontiguousarray(v[idx]) for k, v in inj.items()}
