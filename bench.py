@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Throughput of the candidate propagator: accepted Cash-Karp candidate-steps/s.
+
+One bench step = one full pass of the hot path over one batch: inject the
+batch of candidates into the pool, run the module list (Cash-Karp Lorentz
+steps with trilinear gathers, pair / adiabatic losses, Philox-sampled pion
+production, E_min / length / observer breaks) until every candidate is
+inactive.  Workload: 10^6 mixed H/He/N/Fe candidates from 1000 sources in a
+100 Mpc box, rigidity-scaled E^-2 spectrum, 256^3 float32 Kolmogorov grid
+(100 kpc spacing, B_rms 1 nG, lmax 5 Mpc), observer sphere R = 1 Mpc, E_min
+10^18 eV, 500 Mpc path budget.  Field and tables are built on the GPU before
+the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank propagates its own batch (weak scaling, candidate ids
+offset by rank; no data-path collective).  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "Cash-Karp candidate-steps/s on 1 GB300, mixed-precision vs FP64 at equal error"
+UNIT = "candidate-steps/s"
+H0_OVER_C = 67.3e3 / 299792458.0          # 1/Mpc (H0 = 67.3 km/s/Mpc)
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
+    ap.add_argument("--n", type=int, default=None, help="candidates per rank (default 10^6)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def setup_dist(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return rank, world, local, dist
+
+
+def workload_inputs(n, rank):
+    w = workloads.MIXED_INTERACTIONS
+    inj = workloads.mixed_interactions(n=n, seed=w["seed"] + 7919 * rank)
+    inj["id"] = inj["id"] + np.uint64(rank * n)
+    return w, inj
+
+
+def modules_for(crp, precision, tables):
+    w = workloads.MIXED_INTERACTIONS
+    return crp.modules(precision=precision,
+                       flags=crp.PAIR | crp.ADIABATIC | crp.PION | crp.EMIN | crp.OBSERVER,
+                       tol=w["tol"], h_min=w["h_min"], h_max=w["h_max"], beta_ad=H0_OVER_C,
+                       e_min=w["e_min"], tables=tables, observer_radius=w["observer_r"])
+
+
+def flops_per_trial_mixed():
+    """Algorithmic binary32 flops of one mixed-precision Cash-Karp trial, by
+    count of the arithmetic the method needs:
+      field gather (x6): 3 fma + 3 floor + 3 sub for the in-cell coordinates,
+                         21 lerps x 3 flops                         = 75
+      Lorentz force (x6): cross product 9 + scale 3                  = 12
+      stage directions u_2..u_6: sum_j (2j - 1) x 3 components       = 105
+      stage offsets o_2..o_6:    sum_j 2(j - 1) x 3 components       = 90
+      fifth-order offset 8 x 3, direction 9 x 3, error 10 x 3        = 81
+    """
+    return 6 * (75 + 12) + 105 + 90 + 81
+
+
+def run_ours(args):
+    import torch
+    from paper_1307_2643_gb300 import crp
+    from paper_1307_2643_gb300.build import build
+
+    rank, world, local, dist = setup_dist(args)
+    torch.cuda.set_device(local)
+    build()
+    crp.use_torch_allocator(local)
+    n = args.n or workloads.MIXED_INTERACTIONS["n"]
+    w, inj = workload_inputs(n, rank)
+    inj = crp.host_injection(inj)
+    ctx = crp.crp_context_create(local, w["seed"], int(n * 1.02) + 1024)
+    gd = crp.grid_desc(w["grid_n"], w["spacing"], dtype=crp.F32, source=crp.GRID_TURBULENT,
+                       lmin=w["lmin"], lmax=w["lmax"], brms=w["brms"], seed=w["seed"])
+    grid = crp.crp_grid_create(ctx, gd)
+    tables = crp.crp_tables_build(ctx, crp.tables_desc(n=1000))
+    prec = crp.MIXED if args.precision == "mixed" else crp.FP64
+    mods = modules_for(crp, prec, tables)
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    dev = {k: torch.from_numpy(v).cuda() for k, v in inj.items()}
+    arr_dev = crp.candidate_arrays(dev, on_device=True)
+    pinned = {k: torch.from_numpy(v).pin_memory() for k, v in inj.items()}
+    arr_host = crp.candidate_arrays(pinned, on_device=False)
+
+    def one_step(arrays):
+        crp.crp_candidates_clear(ctx)
+        crp.crp_candidates_inject(ctx, arrays, n, 0, sh)
+        _, st = crp.crp_propagate(ctx, grid, mods, sh)
+        return st
+
+    for _ in range(args.warmup):
+        one_step(arr_dev)
+
+    # ---- device-resident timed region -------------------------------------
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = [one_step(arr_dev) for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    acc = sum(s.accepted_steps for s in stats)
+    rej = sum(s.rejected_trials for s in stats)
+    kern_ms = sum(s.kernel_ms for s in stats)
+    launches = sum(s.launches for s in stats)
+    if dist:
+        t = torch.tensor([elapsed], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t[0])
+        a = torch.tensor([acc], dtype=torch.float64)
+        dist.all_reduce(a)
+        acc_all = float(a[0])
+    else:
+        acc_all = float(acc)
+    value = acc_all / elapsed
+
+    # ---- end to end through the public API with host buffers ---------------
+    e2e = None
+    if not args.no_e2e:
+        rec_cap = int(n * 1.02) + 1024
+        out = np.zeros(rec_cap, dtype=crp.RECORD_DTYPE)
+        out_t = torch.from_numpy(out.view(np.uint8)).pin_memory()
+        out_p = out_t.numpy().view(crp.RECORD_DTYPE)
+        h2d = sum(v.nbytes for v in inj.values())
+        d2h = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        acc_e = 0
+        for _ in range(args.steps):
+            st = one_step(arr_host)
+            acc_e += st.accepted_steps
+            nrec = crp.C.c_size_t()
+            crp._check(crp.lib().crp_collect(ctx, crp.COLLECT_FINISHED, out_p.ctypes.data, rec_cap,
+                                             crp.C.byref(nrec), 0, sh))
+            d2h += nrec.value * crp.RECORD_DTYPE.itemsize
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        e2e = {"value": acc_e / te * world, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h // args.steps)}
+
+    # ---- FP64 leg on the same workload (one step) --------------------------
+    fp64 = None
+    if not args.no_fp64 and prec == crp.MIXED:
+        m64 = modules_for(crp, crp.FP64, tables)
+        crp.crp_candidates_clear(ctx)
+        crp.crp_candidates_inject(ctx, arr_dev, n, 0, sh)
+        torch.cuda.synchronize()
+        f0 = time.perf_counter()
+        _, st64 = crp.crp_propagate(ctx, grid, m64, sh)
+        torch.cuda.synchronize()
+        ft = time.perf_counter() - f0
+        fp64 = {"value": st64.accepted_steps / ft, "unit": UNIT,
+                "kernel_ms": st64.kernel_ms, "accepted_steps": st64.accepted_steps,
+                "rejected_trials": st64.rejected_trials,
+                "mixed_over_fp64": value / world / (st64.accepted_steps / ft)}
+
+    # ---- roofline of the propagate kernel ----------------------------------
+    peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
+    sm_mhz = clk.get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 1440.0
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
+    trials = acc + rej
+    flops = trials * flops_per_trial_mixed() if prec == crp.MIXED else None
+    kern_s = kern_ms / 1e3
+    if prec == crp.MIXED:
+        peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12   # FP32 FMA lanes x 2 flops x clock
+        achieved = flops / kern_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz "
+                               "(median SM clock sampled during the timed region)",
+                "flops_per_trial": flops_per_trial_mixed()}
+    else:
+        roof = None
+
+    # ---- CPU baseline: the oracle on a bounded sample ----------------------
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        cpu = cpu_baseline(inj, grid_host=crp.crp_grid_copy_out(grid, w["grid_n"]),
+                           seconds=args.cpu_seconds)
+
+    crp.crp_tables_destroy(tables)
+    crp.crp_grid_destroy(grid)
+    crp.crp_context_destroy(ctx)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec == crp.MIXED else "f64",
+            "data": "synthetic (seeded injection, GPU-generated turbulent field)",
+            "config": {"workload": w["name"], "candidates_per_gpu": n, "grid": "256^3 f32",
+                       "precision": args.precision, "l2": "inputs larger than L2 (268 MB grid, "
+                       "245 MB candidate pool)", "parallelism": f"candidate shards x{world}"},
+            "accepted_steps": acc, "rejected_trials": rej,
+            "rejected_trials_per_s": rej / elapsed,
+            "kernel_ms_per_step": kern_ms / args.steps,
+            "gpu_launches": int(args.steps * 2 + launches * 2),
+            "e2e": e2e, "fp64": fp64, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+        }
+        print(json.dumps(line))
+
+
+def cpu_baseline(inj, grid_host, seconds=15.0):
+    """The oracle, as it stands, on a bounded id-subsample of the workload,
+    timed on this host's cores (histories are the same ids' histories)."""
+    import oracle
+    w = workloads.MIXED_INTERACTIONS
+    oracle.build()
+    T = oracle.tables_build(n=1000)
+    P = oracle.make_params(grid_n=w["grid_n"], spacing=w["spacing"], tol=w["tol"],
+                           h_min=w["h_min"], h_max=w["h_max"],
+                           flags=oracle.PAIR | oracle.ADIABATIC | oracle.PION | oracle.EMIN |
+                           oracle.OBSERVER, e_min=w["e_min"], beta_ad=H0_OVER_C,
+                           seed=w["seed"], tables=T, obs_r=w["observer_r"])
+    cores = len(os.sched_getaffinity(0))
+    rng = np.random.default_rng(1)
+    order = rng.permutation(len(inj["E"]))
+    steps, done, t_used, chunk = 0, 0, 0.0, 64
+    while t_used < seconds and done < len(order):
+        idx = np.sort(order[done:done + chunk])
+        sub = workloads.subsample(inj, idx)
+        t0 = time.perf_counter()
+        r = oracle.propagate(P, grid_host, sub, tables=T, nthreads=cores)
+        t_used += time.perf_counter() - t0
+        steps += int(r["n_acc"].sum())
+        done += len(idx)
+        chunk = min(4096, chunk * 2)
+    return {"value": steps / t_used, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} candidates drawn by id from the same 10^6-candidate batch, "
+                      f"{steps} accepted steps in {t_used:.1f} s"}
+
+
+def run_reference(args):
+    """The oracle (FP64 C++ on the host cores) on bounded samples of the same
+    workload; rank 0 only."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    w = workloads.MIXED_INTERACTIONS
+    n = args.n or w["n"]
+    _, inj = workload_inputs(n, 0)
+    field = oracle.turbulent_field(w["grid_n"], w["spacing"], w["lmin"], w["lmax"], w["brms"],
+                                   seed=w["seed"]).astype(np.float32).astype(np.float64)
+    T = oracle.tables_build(n=1000)
+    P = oracle.make_params(grid_n=w["grid_n"], spacing=w["spacing"], tol=w["tol"],
+                           h_min=w["h_min"], h_max=w["h_max"],
+                           flags=oracle.PAIR | oracle.ADIABATIC | oracle.PION | oracle.EMIN |
+                           oracle.OBSERVER, e_min=w["e_min"], beta_ad=H0_OVER_C,
+                           seed=w["seed"], tables=T, obs_r=w["observer_r"])
+    cores = len(os.sched_getaffinity(0))
+    per_step = max(16, min(n, 256))
+    rng = np.random.default_rng(2)
+
+    def step(i):
+        idx = np.sort(rng.choice(n, per_step, replace=False))
+        return int(oracle.propagate(P, field, workloads.subsample(inj, idx), tables=T,
+                                    nthreads=cores)["n_acc"].sum())
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    acc = sum(step(i) for i in range(args.steps))
+    dt = time.perf_counter() - t0
+    v = acc / dt
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w["name"], "grid": "256^3 (float32 values)"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} random candidates of the batch per step"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -1,0 +1,296 @@
+/*
+ * crp.h -- C ABI of the GB300 candidate propagator.
+ *
+ * The library advances many independent cosmic-ray candidates (protons and
+ * nuclei) through a gridded magnetic field, following the module / candidate
+ * / IsActive statement of the propagation problem in CRPropa 3.0
+ * (Alves Batista et al., ICRC 2013, arXiv:1307.2643, Sect. 3 and Fig. 1):
+ *   - a candidate holds all of its propagation state, so candidates are
+ *     processed concurrently (Sect. 3, "Cosmic Ray Candidate and Modules");
+ *   - per step the module list runs in order: integration (deflection in the
+ *     field; updates position, direction and trajectory length), interaction
+ *     modules (continuous losses; stochastic interactions that decide
+ *     independently and reset all interaction states after any interaction),
+ *     boundary and observer modules; IsActive is checked after each cycle;
+ *   - interactions append secondary candidates (Sect. 3).
+ *
+ * Conventions for every call:
+ *   - Every call returns a crp_status; 0 is success, negative values are
+ *     errors.  crp_last_error() returns a message for the calling thread's
+ *     last failure.  No call aborts, traps or waits without a bound.
+ *   - Pointers marked "host" are CPU memory, "device" are CUDA device memory
+ *     of the context's device.  The library never keeps a caller's pointer
+ *     after a call returns; caller buffers stay owned by the caller.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls that return data to the host synchronise that stream.
+ *   - All device memory the library uses is owned by the context (or by the
+ *     grid / tables / lens object) and released by the matching destroy
+ *     call.  It is taken from crp_set_allocator's functions when set, else
+ *     from cudaMalloc / cudaFree.
+ *   - Results are a pure function of (seed, injected arrays, grid, tables,
+ *     modules): they do not depend on the launch configuration.
+ */
+#ifndef CRP_H_
+#define CRP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t crp_status;
+#define CRP_OK 0
+#define CRP_E_INVALID (-1)     /* bad argument; nothing was changed        */
+#define CRP_E_OOM (-2)         /* device allocation failed                 */
+#define CRP_E_CUDA (-3)        /* a CUDA runtime / cuFFT call failed       */
+#define CRP_E_QUEUE_FULL (-4)  /* secondaries did not fit the capacity     */
+#define CRP_E_TIMEOUT (-5)     /* step budget or deadline reached; resumable */
+#define CRP_E_BOUNDS (-6)      /* a kernel index check failed (error word) */
+#define CRP_E_STATE (-7)       /* call not valid in the context's state    */
+
+typedef struct crp_context crp_context;
+typedef struct crp_grid crp_grid;
+typedef struct crp_tables crp_tables;
+
+/* Message describing the calling thread's last failed call ("" if none). */
+const char* crp_last_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t crp_version(void);
+
+/* ------------------------------------------------------------------------
+ * Device memory.  Optional allocator used by every later allocation of the
+ * process (for instance a framework's caching allocator).  alloc returns a
+ * device pointer of at least `bytes` bytes aligned to 256 bytes, or NULL.
+ * Pass NULL functions to return to cudaMalloc / cudaFree.  Objects must be
+ * destroyed with the allocator that created them still installed.
+ * ---------------------------------------------------------------------- */
+typedef void* (*crp_alloc_fn)(size_t bytes, void* user);
+typedef void (*crp_free_fn)(void* ptr, void* user);
+crp_status crp_set_allocator(crp_alloc_fn alloc, crp_free_fn release, void* user);
+
+/* ------------------------------------------------------------------------
+ * Context: one device, one random seed, one candidate pool of fixed
+ * capacity (primaries plus all secondaries they may spawn).  The pool is
+ * the set of candidates of the paper's Sect. 3; each candidate's record is
+ * self-contained.  Device memory is taken on the first inject.
+ * ---------------------------------------------------------------------- */
+crp_status crp_context_create(int32_t device, uint64_t seed, size_t capacity, crp_context** out);
+crp_status crp_context_destroy(crp_context* ctx);
+/* Number of candidates in the pool (primaries + secondaries so far). */
+crp_status crp_context_size(const crp_context* ctx, size_t* n_out);
+
+/* ------------------------------------------------------------------------
+ * Field grid (Sect. 4, "Magnetic field techniques": precomputed fields on
+ * grids for fast lookup).  Vertex-centred and periodic: node (i, j, k) sits
+ * at origin + (i, j, k) * spacing and index i wraps modulo n[0]; the field
+ * between nodes is the trilinear interpolation, along x, then y, then z.
+ * Units are the caller's: lengths in `length unit`, field in `field unit`
+ * (crp_modules names both).
+ * ---------------------------------------------------------------------- */
+#define CRP_F32 0
+#define CRP_F64 1
+
+#define CRP_GRID_FROM_HOST 0    /* copy `data` from host memory            */
+#define CRP_GRID_FROM_DEVICE 1  /* copy `data` from device memory          */
+#define CRP_GRID_TURBULENT 2    /* generate a Kolmogorov turbulent field    */
+
+typedef struct {
+  int64_t n[3];          /* nodes along x, y, z (each >= 2)                  */
+  double spacing;        /* node spacing (length unit), > 0                  */
+  double origin[3];      /* position of node (0, 0, 0)                       */
+  int32_t dtype;         /* storage / interpolation type: CRP_F32 | CRP_F64 */
+  int32_t source;        /* CRP_GRID_*                                       */
+  /* FROM_HOST / FROM_DEVICE: field values, layout [n2][n1][n0][3]
+   * (x fastest, components Bx, By, Bz adjacent), element type data_dtype.  */
+  const void* data;
+  int32_t data_dtype;
+  int32_t reserved;
+  /* TURBULENT: Gaussian Fourier modes with 2pi/lmax <= |k| <= 2pi/lmin,
+   * projected perpendicular to k (divergence free), power |B(k)|^2 ~ |k|^index
+   * (index = -11/3 for Kolmogorov), inverse FFT, real part, mean removed,
+   * scaled so that <|B|^2> = brms^2.  Modes on a Nyquist plane stay empty.
+   * Random numbers: Philox4x32-10, key = seed, counter = (component, 1,
+   * mode index lo, mode index hi), Box-Muller on two uniforms per component.  */
+  double lmin, lmax, brms, spectral_index;
+  uint64_t seed;
+} crp_grid_desc;
+
+crp_status crp_grid_create(crp_context* ctx, const crp_grid_desc* desc, crp_grid** out);
+crp_status crp_grid_destroy(crp_grid* grid);
+/* Copy the stored field to host memory as float64, layout [n2][n1][n0][3]. */
+crp_status crp_grid_copy_out(const crp_grid* grid, double* host_out);
+
+/* ------------------------------------------------------------------------
+ * Interaction tables (Sect. 2 interactions; the paper gives no formulas).
+ * n nodes uniform in ln(Gamma) over [gamma_lo, gamma_hi], values in
+ * 1 / length unit, linear interpolation in ln(Gamma), clamped at both ends:
+ *   beta_pair[i]: (1/E) dE/dx of a proton by pair production on a blackbody
+ *     of temperature T_cmb, from Blumenthal, Phys. Rev. D 1, 1596 (1970)
+ *     with the phi(kappa) fit of Chodorowski, Zdziarski & Sikora, ApJ 400,
+ *     181 (1992); a nucleus (A, Z) loses (Z^2 / A) beta_pair(Gamma).
+ *   rate_pion[i]: photo-pion rate of one nucleon for a step cross section
+ *     pion_sigma above the rest-frame photon energy pion_eth; a nucleus has
+ *     A times that rate.
+ *   rate_gdr[i]: photodisintegration rate per nucleon for a Lorentzian giant
+ *     dipole resonance (peak gdr_peak per nucleon at gdr_center, full width
+ *     gdr_fwhm, cut to [gdr_lo, gdr_hi]); a nucleus with A >= 2 has A times it.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  int64_t n;                 /* >= 2 */
+  double gamma_lo, gamma_hi; /* Lorentz-factor range, 0 < lo < hi */
+  double length_unit_m;      /* metres per length unit */
+  double T_cmb;              /* blackbody temperature [K] */
+  double pion_sigma_mb, pion_eth_eV;
+  double gdr_peak_mb, gdr_center_eV, gdr_fwhm_eV, gdr_lo_eV, gdr_hi_eV;
+} crp_tables_desc;
+
+/* Compute the tables on the device (quadrature kernels). */
+crp_status crp_tables_build(crp_context* ctx, const crp_tables_desc* desc, crp_tables** out);
+/* Use tables supplied by the caller (host arrays of desc->n doubles each). */
+crp_status crp_tables_from_host(crp_context* ctx, const crp_tables_desc* desc,
+                                const double* beta_pair, const double* rate_pion,
+                                const double* rate_gdr, crp_tables** out);
+crp_status crp_tables_copy_out(const crp_tables* t, double* beta_pair, double* rate_pion,
+                               double* rate_gdr);
+crp_status crp_tables_destroy(crp_tables* t);
+
+/* ------------------------------------------------------------------------
+ * Candidates (Sect. 3, source model: position, spectrum, composition).
+ * Structure of arrays, n entries each, host or device memory (on_device).
+ * Appended to the pool; ids are id[i], or first_id + i when id is NULL.
+ * Directions must be unit vectors.  A >= 1, 0 <= Z <= A.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  const uint64_t* id;                        /* optional */
+  const double *x, *y, *z;                   /* position (length unit)   */
+  const double *ux, *uy, *uz;                /* unit direction           */
+  const double* E;                           /* energy [eV], > 0         */
+  const int32_t *A, *Z;                      /* mass and charge numbers  */
+  const int32_t* q;                          /* optional charge sign +1/-1 (antiparticles -1) */
+  const double* s_max;                       /* optional trajectory budget (default +inf) */
+  int32_t on_device;                         /* 1: device pointers, 0: host */
+  int32_t reserved;
+} crp_candidate_arrays;
+
+crp_status crp_candidates_inject(crp_context* ctx, const crp_candidate_arrays* a, size_t n,
+                                 uint64_t first_id, void* stream);
+/* Empty the pool (keeps its memory). */
+crp_status crp_candidates_clear(crp_context* ctx);
+
+/* ------------------------------------------------------------------------
+ * Module list and propagation.
+ * ---------------------------------------------------------------------- */
+#define CRP_FP64 0   /* every step in float64                                    */
+#define CRP_MIXED 1  /* field, Lorentz force, RK stages float32; positions,
+                        trajectory length, energy, free paths and the
+                        step-error norm float64                                 */
+
+/* module flags */
+#define CRP_PAIR (1u << 0)       /* pair production on the CMB (continuous)   */
+#define CRP_ADIABATIC (1u << 1)  /* adiabatic loss beta_ad (continuous)       */
+#define CRP_PION (1u << 2)       /* photo-pion production (stochastic)        */
+#define CRP_PHOTODIS (1u << 3)   /* photodisintegration (stochastic, secondaries) */
+#define CRP_EMIN (1u << 4)       /* break below e_min                         */
+#define CRP_OBSERVER (1u << 5)   /* observer sphere: detect on entry          */
+#define CRP_BORDER (1u << 6)     /* border sphere: stop on reaching it        */
+#define CRP_GALACTIC (1u << 7)   /* add the analytic galactic disk+halo field */
+
+typedef struct {
+  int32_t precision;         /* CRP_FP64 | CRP_MIXED */
+  uint32_t flags;            /* CRP_PAIR | ... */
+  double tol;                /* Cash-Karp tolerance on the direction error */
+  double h_min, h_max;       /* step bounds (length unit) */
+  double field_unit_T;       /* tesla per field unit (1e-13 for nG) */
+  double length_unit_m;      /* metres per length unit (Mpc: 3.0856775814913673e22) */
+  double beta_ad;            /* adiabatic loss rate (1 / length unit) */
+  double e_min;              /* [eV] */
+  const crp_tables* tables;  /* required by PAIR / PION / PHOTODIS */
+  double observer_center[3], observer_radius;
+  double border_center[3], border_radius;
+  /* analytic galactic field (CRP_GALACTIC), in field / length units:
+   * disk  B = disk_b exp(-|z|/disk_hz) (sin p r_hat + cos p phi_hat) for
+   *       disk_rmin <= r <= disk_rmax, p = disk_pitch_rad;
+   * halo  B_phi = halo_b sign(z) exp(-(|z| - halo_z0)^2 / (2 halo_sigma^2)),
+   * cylindrical coordinates about gal_center. */
+  double disk_b, disk_pitch_rad, disk_hz, disk_rmin, disk_rmax;
+  double halo_b, halo_z0, halo_sigma;
+  double gal_center[3];
+  uint64_t max_steps;        /* per-candidate accepted-step budget; 0 = 1e8.  A
+                                candidate reaching it stops with CRP_BUDGET. */
+  uint64_t step_budget;      /* accepted steps in this call before TIMEOUT (0 = none) */
+  double deadline_ms;        /* wall-clock limit of this call (0 = none) */
+  int32_t block_size;        /* threads per block, multiple of 32 up to 256 (0 = default) */
+  int32_t blocks_per_sm;     /* resident blocks per SM (0 = autotuned) */
+} crp_modules;
+
+typedef struct {
+  uint64_t accepted_steps;   /* module cycles completed */
+  uint64_t rejected_trials;  /* Cash-Karp trials rejected by the controller */
+  uint64_t rhs_evals;        /* field gathers + Lorentz evaluations */
+  uint64_t n_pion, n_pd;     /* interactions */
+  uint64_t n_secondaries;    /* secondaries appended to the pool */
+  uint64_t n_dropped;        /* secondaries below e_min, not propagated */
+  uint64_t n_overflow;       /* secondaries lost to a full pool */
+  uint64_t n_active;         /* candidates still active after the call */
+  uint64_t n_detected;       /* candidates detected by the observer (pool total) */
+  double kernel_ms;          /* device time of the propagate launches */
+  uint32_t launches;         /* kernel launches issued by the call */
+  uint32_t error_word;       /* kernel error bits (0 = none) */
+} crp_stats;
+
+/* Run the module list on every active candidate in the pool (and on every
+ * secondary they spawn) until none is active.  Returns CRP_E_TIMEOUT if the
+ * step budget or deadline ran out first (state stays resumable: call again),
+ * CRP_E_QUEUE_FULL if secondaries were lost to the pool capacity.  stats_out
+ * may be NULL.  Synchronises `stream`. */
+crp_status crp_propagate(crp_context* ctx, const crp_grid* grid, const crp_modules* m,
+                         void* stream, crp_stats* stats_out);
+
+/* ------------------------------------------------------------------------
+ * Output (Sect. 3, output modules: store candidates on detection or at the
+ * end).  One record per candidate.
+ * ---------------------------------------------------------------------- */
+#define CRP_ACTIVE 0
+#define CRP_BELOW_EMIN 1
+#define CRP_MAX_LENGTH 2
+#define CRP_DETECTED 3
+#define CRP_AT_BORDER 4
+#define CRP_BUDGET 5
+
+typedef struct {
+  uint64_t id, parent_id;    /* parent_id 0 for primaries */
+  double x[3], u[3];         /* final position, direction */
+  double E, s;               /* final energy [eV], trajectory length */
+  double x0[3], u0[3];       /* at injection / creation */
+  double E0, s_max;
+  uint64_t n_acc, n_rej;     /* accepted steps, rejected trials */
+  int32_t A, Z, A0, Z0, q;
+  int32_t status;            /* CRP_ACTIVE ... CRP_BUDGET */
+  uint32_t n_pion, n_pd, draws, generation, n_dropped, lens_pixel;
+} crp_record;                /* 208 bytes */
+
+#define CRP_COLLECT_ALL 0
+#define CRP_COLLECT_FINISHED 1
+#define CRP_COLLECT_DETECTED 2
+#define CRP_COLLECT_ACTIVE 3
+#define CRP_COLLECT_AT_BORDER 4
+
+/* Copy the records selected by `what`, in pool order, into `out` (host or
+ * device memory per out_on_device; capacity records).  *n_out receives the
+ * number selected; CRP_E_INVALID if capacity is too small (nothing copied). */
+crp_status crp_collect(crp_context* ctx, int32_t what, crp_record* out, size_t capacity,
+                       size_t* n_out, int32_t out_on_device, void* stream);
+
+/* Histogram over the selected records: nbins log-uniform bins of E over
+ * [e_lo, e_hi) (under/overflow dropped).  out: host uint64 array of nbins. */
+crp_status crp_histogram_energy(crp_context* ctx, int32_t what, double e_lo, double e_hi,
+                                int32_t nbins, uint64_t* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CRP_H_ */

@@ -126,6 +126,7 @@ def lib():
                 [p, i64, C.POINTER(i64), C.c_int]
             L.orc_propagate.restype = C.c_int
             L.orc_field_at.argtypes = [C.POINTER(Params), p, i64, p, p]
+            L.orc_table_axis.argtypes = [i64, d, d, C.POINTER(d), C.POINTER(d)]
             _lib = L
     return _lib
 
@@ -209,13 +210,11 @@ class Tables:
         self.n, self.g_lo, self.g_hi = n, g_lo, g_hi
         self.beta_pair, self.rate_pion, self.rate_gdr = beta_pair, rate_pion, rate_gdr
 
-    @property
-    def lg0(self):
-        return float(np.log(self.g_lo))
-
-    @property
-    def inv_dlg(self):
-        return float((self.n - 1) / (np.log(self.g_hi) - np.log(self.g_lo)))
+    def axis(self):
+        """(ln Gamma of node 0, nodes per unit ln Gamma), evaluated in C."""
+        lg0, inv = C.c_double(), C.c_double()
+        lib().orc_table_axis(self.n, self.g_lo, self.g_hi, C.byref(lg0), C.byref(inv))
+        return lg0.value, inv.value
 
 
 def tables_build(n=1000, g_lo=1e6, g_hi=1e13, length_unit_m=MPC_M, T=2.725,
@@ -269,7 +268,7 @@ def make_params(*, grid_n, spacing, origin=(0.0, 0.0, 0.0), tol=1e-4, h_min=0.01
     P.flags = flags
     P.seed = seed
     if tables is not None:
-        P.tab_lg0, P.tab_inv_dlg, P.tab_n = tables.lg0, tables.inv_dlg, tables.n
+        (P.tab_lg0, P.tab_inv_dlg), P.tab_n = tables.axis(), tables.n
     else:
         P.tab_n = 2
     P.obs_c[:] = obs_c

@@ -933,6 +933,12 @@ int orc_propagate(const orc_params* P, const double* grid, const double* t_beta,
 
 extern "C" {
 
+// Table axis: ln(Gamma) of node 0 and nodes per unit ln(Gamma).
+void orc_table_axis(int64_t n, double g_lo, double g_hi, double* lg0, double* inv_dlg) {
+  *lg0 = std::log(g_lo);
+  *inv_dlg = (double)(n - 1) / (std::log(g_hi) - std::log(g_lo));
+}
+
 // Field at a list of points (grid interpolation, plus the analytic galactic
 // field when its flag is set); used by the interpolation pins.
 void orc_field_at(const orc_params* P, const double* grid, int64_t n, const double* pts,

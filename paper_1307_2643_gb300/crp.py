@@ -1,0 +1,372 @@
+"""ctypes binding of the C ABI declared in ``include/crp.h``.
+
+Argument marshalling only: every step of the propagation runs in the CUDA
+library ``_build/libcrp.so``.  There is no CPU fallback; importing a function
+here without the built library raises.  The names follow the C functions
+(``crp_context_create`` ...); non-zero statuses raise :class:`CrpError` with
+the library's message.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libcrp.so")
+
+# status codes
+OK, E_INVALID, E_OOM, E_CUDA, E_QUEUE_FULL, E_TIMEOUT, E_BOUNDS, E_STATE = 0, -1, -2, -3, -4, -5, -6, -7
+F32, F64 = 0, 1
+GRID_FROM_HOST, GRID_FROM_DEVICE, GRID_TURBULENT = 0, 1, 2
+FP64, MIXED = 0, 1
+PAIR, ADIABATIC, PION, PHOTODIS, EMIN, OBSERVER, BORDER, GALACTIC = (1 << i for i in range(8))
+ACTIVE, BELOW_EMIN, MAX_LENGTH, DETECTED, AT_BORDER, BUDGET = range(6)
+COLLECT_ALL, COLLECT_FINISHED, COLLECT_DETECTED, COLLECT_ACTIVE, COLLECT_AT_BORDER = range(5)
+
+MPC_M = 3.0856775814913673e22
+KPC_M = 3.0856775814913673e19
+NANOGAUSS_T = 1e-13
+MICROGAUSS_T = 1e-10
+
+
+class CrpError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"crp status {status}: {msg}")
+        self.status = status
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("n", C.c_int64 * 3), ("spacing", C.c_double), ("origin", C.c_double * 3),
+                ("dtype", C.c_int32), ("source", C.c_int32), ("data", C.c_void_p),
+                ("data_dtype", C.c_int32), ("reserved", C.c_int32),
+                ("lmin", C.c_double), ("lmax", C.c_double), ("brms", C.c_double),
+                ("spectral_index", C.c_double), ("seed", C.c_uint64)]
+
+
+class TablesDesc(C.Structure):
+    _fields_ = [("n", C.c_int64), ("gamma_lo", C.c_double), ("gamma_hi", C.c_double),
+                ("length_unit_m", C.c_double), ("T_cmb", C.c_double),
+                ("pion_sigma_mb", C.c_double), ("pion_eth_eV", C.c_double),
+                ("gdr_peak_mb", C.c_double), ("gdr_center_eV", C.c_double),
+                ("gdr_fwhm_eV", C.c_double), ("gdr_lo_eV", C.c_double), ("gdr_hi_eV", C.c_double)]
+
+
+class CandidateArrays(C.Structure):
+    _fields_ = [("id", C.c_void_p), ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p),
+                ("ux", C.c_void_p), ("uy", C.c_void_p), ("uz", C.c_void_p), ("E", C.c_void_p),
+                ("A", C.c_void_p), ("Z", C.c_void_p), ("q", C.c_void_p), ("s_max", C.c_void_p),
+                ("on_device", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Modules(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("flags", C.c_uint32), ("tol", C.c_double),
+                ("h_min", C.c_double), ("h_max", C.c_double), ("field_unit_T", C.c_double),
+                ("length_unit_m", C.c_double), ("beta_ad", C.c_double), ("e_min", C.c_double),
+                ("tables", C.c_void_p),
+                ("observer_center", C.c_double * 3), ("observer_radius", C.c_double),
+                ("border_center", C.c_double * 3), ("border_radius", C.c_double),
+                ("disk_b", C.c_double), ("disk_pitch_rad", C.c_double), ("disk_hz", C.c_double),
+                ("disk_rmin", C.c_double), ("disk_rmax", C.c_double),
+                ("halo_b", C.c_double), ("halo_z0", C.c_double), ("halo_sigma", C.c_double),
+                ("gal_center", C.c_double * 3),
+                ("max_steps", C.c_uint64), ("step_budget", C.c_uint64),
+                ("deadline_ms", C.c_double), ("block_size", C.c_int32),
+                ("blocks_per_sm", C.c_int32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("accepted_steps", C.c_uint64), ("rejected_trials", C.c_uint64),
+                ("rhs_evals", C.c_uint64), ("n_pion", C.c_uint64), ("n_pd", C.c_uint64),
+                ("n_secondaries", C.c_uint64), ("n_dropped", C.c_uint64),
+                ("n_overflow", C.c_uint64), ("n_active", C.c_uint64),
+                ("n_detected", C.c_uint64), ("kernel_ms", C.c_double),
+                ("launches", C.c_uint32), ("error_word", C.c_uint32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+RECORD_DTYPE = np.dtype([
+    ("id", "<u8"), ("parent_id", "<u8"),
+    ("x", "<f8", 3), ("u", "<f8", 3),
+    ("E", "<f8"), ("s", "<f8"),
+    ("x0", "<f8", 3), ("u0", "<f8", 3),
+    ("E0", "<f8"), ("s_max", "<f8"),
+    ("n_acc", "<u8"), ("n_rej", "<u8"),
+    ("A", "<i4"), ("Z", "<i4"), ("A0", "<i4"), ("Z0", "<i4"), ("q", "<i4"),
+    ("status", "<i4"),
+    ("n_pion", "<u4"), ("n_pd", "<u4"), ("draws", "<u4"), ("generation", "<u4"),
+    ("n_dropped", "<u4"), ("lens_pixel", "<u4"),
+])
+assert RECORD_DTYPE.itemsize == 208
+
+# exported symbols (every function declared in include/crp.h)
+SYMBOLS = (
+    "crp_last_error", "crp_version", "crp_set_allocator",
+    "crp_context_create", "crp_context_destroy", "crp_context_size",
+    "crp_grid_create", "crp_grid_destroy", "crp_grid_copy_out",
+    "crp_tables_build", "crp_tables_from_host", "crp_tables_copy_out", "crp_tables_destroy",
+    "crp_candidates_inject", "crp_candidates_clear",
+    "crp_propagate", "crp_collect", "crp_histogram_energy",
+)
+
+_lock = threading.Lock()
+_lib = None
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+def lib():
+    """Load libcrp.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libcrp.so is not built ({LIB_PATH}); run "
+                                   "paper_1307_2643_gb300.build.build()")
+            L = C.CDLL(LIB_PATH)
+            p, st, sz, u64, i32 = C.c_void_p, C.c_int32, C.c_size_t, C.c_uint64, C.c_int32
+            L.crp_last_error.restype = C.c_char_p
+            L.crp_version.restype = i32
+            L.crp_set_allocator.argtypes = [ALLOC_FN, FREE_FN, p]
+            L.crp_context_create.argtypes = [i32, u64, sz, C.POINTER(p)]
+            L.crp_context_destroy.argtypes = [p]
+            L.crp_context_size.argtypes = [p, C.POINTER(sz)]
+            L.crp_grid_create.argtypes = [p, C.POINTER(GridDesc), C.POINTER(p)]
+            L.crp_grid_destroy.argtypes = [p]
+            L.crp_grid_copy_out.argtypes = [p, p]
+            L.crp_tables_build.argtypes = [p, C.POINTER(TablesDesc), C.POINTER(p)]
+            L.crp_tables_from_host.argtypes = [p, C.POINTER(TablesDesc), p, p, p, C.POINTER(p)]
+            L.crp_tables_copy_out.argtypes = [p, p, p, p]
+            L.crp_tables_destroy.argtypes = [p]
+            L.crp_candidates_inject.argtypes = [p, C.POINTER(CandidateArrays), sz, u64, p]
+            L.crp_candidates_clear.argtypes = [p]
+            L.crp_propagate.argtypes = [p, p, C.POINTER(Modules), p, C.POINTER(Stats)]
+            L.crp_collect.argtypes = [p, i32, p, sz, C.POINTER(sz), i32, p]
+            L.crp_histogram_energy.argtypes = [p, i32, C.c_double, C.c_double, i32, p, p]
+            for name in SYMBOLS:
+                if name not in ("crp_last_error", "crp_version"):
+                    getattr(L, name).restype = st
+            _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != OK:
+        raise CrpError(status, lib().crp_last_error().decode(errors="replace"))
+    return status
+
+
+def _addr(a):
+    """Data pointer of a numpy array or torch tensor (None stays None)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+# ---------------------------------------------------------------------------
+# allocator: route the library's device allocations through torch's caching
+# allocator (PyTorch supplies device memory and streams).
+# ---------------------------------------------------------------------------
+_alloc_keep = []
+
+
+def use_torch_allocator(device=0):
+    import torch
+
+    @ALLOC_FN
+    def _alloc(nbytes, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device)
+        except Exception:  # out of memory -> NULL, the library reports CRP_E_OOM
+            return None
+
+    @FREE_FN
+    def _free(ptr, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    _alloc_keep[:] = [_alloc, _free]
+    _check(lib().crp_set_allocator(_alloc, _free, None))
+
+
+def use_cuda_allocator():
+    _check(lib().crp_set_allocator(ALLOC_FN(0), FREE_FN(0), None))
+    _alloc_keep.clear()
+
+
+# ---------------------------------------------------------------------------
+# functions with the C names
+# ---------------------------------------------------------------------------
+def crp_version():
+    return lib().crp_version()
+
+
+def crp_context_create(device=0, seed=0, capacity=1 << 20):
+    h = C.c_void_p()
+    _check(lib().crp_context_create(device, seed, capacity, C.byref(h)))
+    return h
+
+
+def crp_context_destroy(ctx):
+    _check(lib().crp_context_destroy(ctx))
+
+
+def crp_context_size(ctx):
+    n = C.c_size_t()
+    _check(lib().crp_context_size(ctx, C.byref(n)))
+    return n.value
+
+
+def crp_grid_create(ctx, desc: GridDesc):
+    h = C.c_void_p()
+    _check(lib().crp_grid_create(ctx, C.byref(desc), C.byref(h)))
+    return h
+
+
+def crp_grid_destroy(grid):
+    _check(lib().crp_grid_destroy(grid))
+
+
+def crp_grid_copy_out(grid, n):
+    out = np.empty((n[2], n[1], n[0], 3), dtype=np.float64)
+    _check(lib().crp_grid_copy_out(grid, out.ctypes.data))
+    return out
+
+
+def crp_tables_build(ctx, desc: TablesDesc):
+    h = C.c_void_p()
+    _check(lib().crp_tables_build(ctx, C.byref(desc), C.byref(h)))
+    return h
+
+
+def crp_tables_from_host(ctx, desc: TablesDesc, beta, pion, gdr):
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (beta, pion, gdr)]
+    h = C.c_void_p()
+    _check(lib().crp_tables_from_host(ctx, C.byref(desc), *(a.ctypes.data for a in arrs),
+                                      C.byref(h)))
+    return h
+
+
+def crp_tables_copy_out(tables, n):
+    out = [np.empty(n) for _ in range(3)]
+    _check(lib().crp_tables_copy_out(tables, *(a.ctypes.data for a in out)))
+    return out
+
+
+def crp_tables_destroy(tables):
+    _check(lib().crp_tables_destroy(tables))
+
+
+def crp_candidates_inject(ctx, arrays: CandidateArrays, n, first_id=0, stream=None):
+    _check(lib().crp_candidates_inject(ctx, C.byref(arrays), n, first_id, stream))
+
+
+def crp_candidates_clear(ctx):
+    _check(lib().crp_candidates_clear(ctx))
+
+
+def crp_propagate(ctx, grid, modules: Modules, stream=None, raise_on_error=True):
+    """Returns (status, Stats).  TIMEOUT / QUEUE_FULL raise unless
+    raise_on_error is False."""
+    s = Stats()
+    status = lib().crp_propagate(ctx, grid, C.byref(modules), stream, C.byref(s))
+    if raise_on_error:
+        _check(status)
+    return status, s
+
+
+def crp_collect(ctx, what=COLLECT_ALL, out=None, stream=None):
+    """Records selected by `what` as a numpy structured array (host), or into
+    a caller-supplied device buffer (torch uint8 tensor of capacity*200 bytes)
+    whose record count is returned."""
+    n = C.c_size_t()
+    if out is None:
+        _check(lib().crp_collect(ctx, what, None, 0, C.byref(n), 0, stream))
+        rec = np.zeros(n.value, dtype=RECORD_DTYPE)
+        if n.value:
+            _check(lib().crp_collect(ctx, what, rec.ctypes.data, n.value, C.byref(n), 0, stream))
+        return rec
+    on_dev = 1 if getattr(out, "is_cuda", False) else 0
+    cap = out.numel() * out.element_size() // RECORD_DTYPE.itemsize if on_dev else len(out)
+    _check(lib().crp_collect(ctx, what, _addr(out), cap, C.byref(n), on_dev, stream))
+    return n.value
+
+
+def crp_histogram_energy(ctx, what, e_lo, e_hi, nbins, stream=None):
+    out = np.zeros(nbins, dtype=np.uint64)
+    _check(lib().crp_histogram_energy(ctx, what, e_lo, e_hi, nbins, out.ctypes.data, stream))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# small conveniences (still marshalling only)
+# ---------------------------------------------------------------------------
+def candidate_arrays(inj: dict, on_device=False):
+    """CandidateArrays pointing at the arrays of `inj` (numpy on the host, or
+    torch tensors on the device).  Keep `inj` alive during the call."""
+    a = CandidateArrays()
+    for k in ("id", "x", "y", "z", "ux", "uy", "uz", "E", "A", "Z", "q", "s_max"):
+        setattr(a, k, _addr(inj.get(k)))
+    a.on_device = 1 if on_device else 0
+    return a
+
+
+def host_injection(inj: dict) -> dict:
+    """Contiguous host arrays of the dtypes the ABI expects."""
+    out = {}
+    for k, v in inj.items():
+        dt = {"id": np.uint64, "A": np.int32, "Z": np.int32, "q": np.int32}.get(k, np.float64)
+        out[k] = np.ascontiguousarray(v, dtype=dt)
+    return out
+
+
+def grid_desc(n, spacing, origin=(0.0, 0.0, 0.0), dtype=F64, source=GRID_FROM_HOST, data=None,
+              data_dtype=F64, lmin=0.0, lmax=0.0, brms=0.0, spectral_index=-11.0 / 3.0, seed=0):
+    d = GridDesc()
+    d.n[:] = n
+    d.spacing = spacing
+    d.origin[:] = origin
+    d.dtype, d.source = dtype, source
+    d.data = _addr(data)
+    d.data_dtype = data_dtype
+    d.lmin, d.lmax, d.brms, d.spectral_index, d.seed = lmin, lmax, brms, spectral_index, seed
+    return d
+
+
+def tables_desc(n=1000, gamma_lo=1e6, gamma_hi=1e13, length_unit_m=MPC_M, T_cmb=2.725,
+                pion_sigma_mb=0.5, pion_eth_eV=145e6, gdr_peak_mb=1.5, gdr_center_eV=20e6,
+                gdr_fwhm_eV=6e6, gdr_lo_eV=8e6, gdr_hi_eV=150e6):
+    d = TablesDesc()
+    d.n, d.gamma_lo, d.gamma_hi, d.length_unit_m, d.T_cmb = n, gamma_lo, gamma_hi, length_unit_m, T_cmb
+    d.pion_sigma_mb, d.pion_eth_eV = pion_sigma_mb, pion_eth_eV
+    d.gdr_peak_mb, d.gdr_center_eV, d.gdr_fwhm_eV = gdr_peak_mb, gdr_center_eV, gdr_fwhm_eV
+    d.gdr_lo_eV, d.gdr_hi_eV = gdr_lo_eV, gdr_hi_eV
+    return d
+
+
+def modules(precision=FP64, flags=0, tol=1e-4, h_min=0.01, h_max=1.0, field_unit_T=NANOGAUSS_T,
+            length_unit_m=MPC_M, beta_ad=0.0, e_min=0.0, tables=None, observer_center=(0, 0, 0),
+            observer_radius=0.0, border_center=(0, 0, 0), border_radius=0.0, galactic=None,
+            max_steps=10_000_000, step_budget=0, deadline_ms=0.0, block_size=0, blocks_per_sm=0):
+    m = Modules()
+    m.precision, m.flags, m.tol, m.h_min, m.h_max = precision, flags, tol, h_min, h_max
+    m.field_unit_T, m.length_unit_m, m.beta_ad, m.e_min = field_unit_T, length_unit_m, beta_ad, e_min
+    m.tables = tables.value if isinstance(tables, C.c_void_p) else tables
+    m.observer_center[:] = observer_center
+    m.observer_radius = observer_radius
+    m.border_center[:] = border_center
+    m.border_radius = border_radius
+    if galactic:
+        for k, v in galactic.items():
+            if k == "center":
+                m.gal_center[:] = v
+            else:
+                setattr(m, k, v)
+    m.max_steps, m.step_budget, m.deadline_ms = max_steps, step_budget, deadline_ms
+    m.block_size, m.blocks_per_sm = block_size, blocks_per_sm
+    return m

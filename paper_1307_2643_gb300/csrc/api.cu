@@ -1,0 +1,960 @@
+// api.cu -- the C ABI: contexts, grids, tables, candidate pool, propagate
+// driver and output collection.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <new>
+
+#include "crp_internal.cuh"
+#include "field_internal.h"
+
+// ===========================================================================
+// errors and memory
+// ===========================================================================
+namespace crp {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+crp_status fail_cuda(cudaError_t e, const char* what) {
+  set_error("%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+  cudaGetLastError();  // clear a non-sticky error
+  return CRP_E_CUDA;
+}
+
+static std::mutex g_alloc_mu;
+static crp_alloc_fn g_alloc = nullptr;
+static crp_free_fn g_free = nullptr;
+static void* g_alloc_user = nullptr;
+
+void* dev_alloc(size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  crp_alloc_fn a;
+  void* u;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    a = g_alloc;
+    u = g_alloc_user;
+  }
+  if (a) return a(bytes, u);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void dev_free(void* p) {
+  if (!p) return;
+  crp_free_fn f;
+  void* u;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    f = g_free;
+    u = g_alloc_user;
+  }
+  if (f)
+    f(p, u);
+  else
+    cudaFree(p);
+}
+
+}  // namespace crp
+
+using namespace crp;
+
+struct crp_context {
+  int device;
+  uint64_t seed;
+  size_t capacity;
+  size_t size;            // candidates in the pool
+  void* pool;             // one allocation holding every SoA array
+  DevState st;
+  DevCounters* dc;        // device counters
+  DevCounters* hc;        // pinned host mirror
+  int sm_count;
+  cudaEvent_t ev0, ev1;
+};
+
+struct crp_grid {
+  crp_context* ctx;
+  crp_grid_desc desc;
+  void* nodes;
+  int64_t N;
+};
+
+struct crp_tables {
+  crp_context* ctx;
+  crp_tables_desc desc;
+  double* data;  // beta | pion | gdr, n each
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+// Lay out the SoA arrays of `cap` candidates inside one allocation.
+size_t layout_pool(char* base, size_t cap, DevState* st) {
+  size_t off = 0;
+  auto take = [&](auto** ptr, size_t elem) {
+    using T = typename std::remove_pointer<typename std::remove_pointer<decltype(ptr)>::type>::type;
+    if (base) *ptr = reinterpret_cast<T*>(base + off);
+    off += align_up(elem * cap);
+  };
+  DevState s;
+  memset(&s, 0, sizeof(s));
+  take(&s.id, 8); take(&s.parent, 8);
+  take(&s.x, 8); take(&s.y, 8); take(&s.z, 8);
+  take(&s.ux, 8); take(&s.uy, 8); take(&s.uz, 8);
+  take(&s.E, 8); take(&s.s, 8); take(&s.s_max, 8); take(&s.h, 8);
+  take(&s.d_pion, 8); take(&s.d_pd, 8);
+  take(&s.x0, 8); take(&s.y0, 8); take(&s.z0, 8);
+  take(&s.ux0, 8); take(&s.uy0, 8); take(&s.uz0, 8); take(&s.E0, 8);
+  take(&s.n_acc, 8); take(&s.n_rej, 8);
+  take(&s.A, 4); take(&s.Z, 4); take(&s.q, 4); take(&s.A0, 4); take(&s.Z0, 4); take(&s.status, 4);
+  take(&s.draws, 4); take(&s.events, 4); take(&s.generation, 4); take(&s.n_pion, 4);
+  take(&s.n_pd, 4); take(&s.n_dropped, 4); take(&s.flags, 4); take(&s.lens_pixel, 4);
+  if (st) *st = s;
+  return off;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+crp_status ensure_pool(crp_context* c) {
+  if (c->pool) return CRP_OK;
+  const size_t bytes = layout_pool(nullptr, c->capacity, nullptr);
+  c->pool = dev_alloc(bytes);
+  if (!c->pool) {
+    set_error("candidate pool: cannot allocate %zu bytes for capacity %zu", bytes, c->capacity);
+    return CRP_E_OOM;
+  }
+  layout_pool(static_cast<char*>(c->pool), c->capacity, &c->st);
+  c->dc = static_cast<DevCounters*>(dev_alloc(sizeof(DevCounters)));
+  if (!c->dc) {
+    dev_free(c->pool);
+    c->pool = nullptr;
+    set_error("candidate pool: cannot allocate counters");
+    return CRP_E_OOM;
+  }
+  return CRP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// inject kernels
+// ---------------------------------------------------------------------------
+__global__ void k_inject_init(DevState st, uint64_t base, uint64_t n, uint64_t first_id,
+                              int has_id, int has_q, int has_smax, unsigned* bad) {
+  for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < n;
+       j += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t i = base + j;
+    if (!has_id) st.id[i] = first_id + j;
+    if (!has_q) st.q[i] = 1;
+    if (!has_smax) st.s_max[i] = (double)INFINITY;
+    const double ux = st.ux[i], uy = st.uy[i], uz = st.uz[i];
+    const double un = ux * ux + uy * uy + uz * uz;
+    const int A = st.A[i], Z = st.Z[i], q = st.q[i];
+    const double E = st.E[i];
+    const bool ok = A >= 1 && Z >= 0 && Z <= A && (q == 1 || q == -1) && E > 0.0 &&
+                    E < (double)INFINITY && fabs(un - 1.0) < 1e-6 && st.s_max[i] >= 0.0;
+    if (!ok) atomicAdd(bad, 1u);
+    st.parent[i] = 0;
+    st.x0[i] = st.x[i];
+    st.y0[i] = st.y[i];
+    st.z0[i] = st.z[i];
+    st.ux0[i] = ux;
+    st.uy0[i] = uy;
+    st.uz0[i] = uz;
+    st.E0[i] = E;
+    st.A0[i] = A;
+    st.Z0[i] = Z;
+    st.s[i] = 0.0;
+    st.h[i] = (double)INFINITY;  // first trial step: h_max
+    st.d_pion[i] = 0.0;
+    st.d_pd[i] = 0.0;
+    st.status[i] = CRP_ACTIVE;
+    st.draws[i] = 0;
+    st.events[i] = 0;
+    st.generation[i] = 0;
+    st.n_pion[i] = 0;
+    st.n_pd[i] = 0;
+    st.n_dropped[i] = 0;
+    st.flags[i] = 0;
+    st.lens_pixel[i] = 0xffffffffu;
+    st.n_acc[i] = 0;
+    st.n_rej[i] = 0;
+  }
+}
+
+__global__ void k_set_u64(unsigned long long* p, unsigned long long v) { *p = v; }
+
+__global__ void k_count_active(const int32_t* status, uint64_t n, unsigned long long* out) {
+  unsigned long long cnt = 0;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    cnt += status[i] == CRP_ACTIVE;
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(out, cnt);
+}
+
+// ---------------------------------------------------------------------------
+// collect kernels: selection -> per-block counts -> scan -> ordered scatter
+// ---------------------------------------------------------------------------
+constexpr int kCollectBlock = 1024;
+
+__device__ __forceinline__ bool selected(int what, int status) {
+  switch (what) {
+    case CRP_COLLECT_ALL: return true;
+    case CRP_COLLECT_FINISHED: return status != CRP_ACTIVE;
+    case CRP_COLLECT_DETECTED: return status == CRP_DETECTED;
+    case CRP_COLLECT_ACTIVE: return status == CRP_ACTIVE;
+    case CRP_COLLECT_AT_BORDER: return status == CRP_AT_BORDER;
+  }
+  return false;
+}
+
+__global__ void k_collect_count(const int32_t* status, uint64_t n, int what, unsigned* counts) {
+  __shared__ unsigned sh;
+  if (threadIdx.x == 0) sh = 0;
+  __syncthreads();
+  const uint64_t i = blockIdx.x * (uint64_t)kCollectBlock + threadIdx.x;
+  const bool sel = i < n && selected(what, status[i]);
+  const unsigned b = __ballot_sync(0xffffffffu, sel);
+  if ((threadIdx.x & 31) == 0 && b) atomicAdd(&sh, __popc(b));
+  __syncthreads();
+  if (threadIdx.x == 0) counts[blockIdx.x] = sh;
+}
+
+// exclusive scan of nb counts in a single block (fixed order)
+__global__ void k_collect_scan(const unsigned* counts, int nb, unsigned long long* offsets) {
+  __shared__ unsigned long long part[1024];
+  const int t = threadIdx.x;
+  const int per = (nb + blockDim.x - 1) / blockDim.x;
+  const int lo = t * per, hi = min(nb, lo + per);
+  unsigned long long s = 0;
+  for (int i = lo; i < hi; ++i) s += counts[i];
+  part[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    unsigned long long run = 0;
+    for (int i = 0; i < (int)blockDim.x; ++i) {
+      const unsigned long long v = part[i];
+      part[i] = run;
+      run += v;
+    }
+    offsets[nb] = run;
+  }
+  __syncthreads();
+  unsigned long long run = part[t];
+  for (int i = lo; i < hi; ++i) {
+    offsets[i] = run;
+    run += counts[i];
+  }
+}
+
+__global__ void k_collect_scatter(DevState st, uint64_t n, int what,
+                                  const unsigned long long* offsets, crp_record* out) {
+  __shared__ unsigned warp_base[kCollectBlock / 32];
+  const uint64_t i = blockIdx.x * (uint64_t)kCollectBlock + threadIdx.x;
+  const bool sel = i < n && selected(what, st.status[i]);
+  const unsigned b = __ballot_sync(0xffffffffu, sel);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) warp_base[warp] = __popc(b);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned run = 0;
+    for (int w = 0; w < kCollectBlock / 32; ++w) {
+      const unsigned v = warp_base[w];
+      warp_base[w] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  if (!sel) return;
+  const uint64_t o = offsets[blockIdx.x] + warp_base[warp] + __popc(b & ((1u << lane) - 1u));
+  crp_record r;
+  r.id = st.id[i];
+  r.parent_id = st.parent[i];
+  r.x[0] = st.x[i]; r.x[1] = st.y[i]; r.x[2] = st.z[i];
+  r.u[0] = st.ux[i]; r.u[1] = st.uy[i]; r.u[2] = st.uz[i];
+  r.E = st.E[i];
+  r.s = st.s[i];
+  r.x0[0] = st.x0[i]; r.x0[1] = st.y0[i]; r.x0[2] = st.z0[i];
+  r.u0[0] = st.ux0[i]; r.u0[1] = st.uy0[i]; r.u0[2] = st.uz0[i];
+  r.E0 = st.E0[i];
+  r.s_max = st.s_max[i];
+  r.n_acc = st.n_acc[i];
+  r.n_rej = st.n_rej[i];
+  r.A = st.A[i]; r.Z = st.Z[i]; r.A0 = st.A0[i]; r.Z0 = st.Z0[i]; r.q = st.q[i];
+  r.status = st.status[i];
+  r.n_pion = st.n_pion[i];
+  r.n_pd = st.n_pd[i];
+  r.draws = st.draws[i];
+  r.generation = st.generation[i];
+  r.n_dropped = st.n_dropped[i];
+  r.lens_pixel = st.lens_pixel[i];
+  out[o] = r;
+}
+
+__global__ void k_hist_energy(const int32_t* status, const double* E, uint64_t n, int what,
+                              double l0, double inv_dl, int nb, unsigned long long* bins) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    if (!selected(what, status[i])) continue;
+    const double t = (log(E[i]) - l0) * inv_dl;
+    if (!(t >= 0.0) || t >= (double)nb) continue;
+    atomicAdd(bins + (int)t, 1ull);
+  }
+}
+
+int blocks_for(uint64_t n, int block) {
+  const uint64_t b = (n + block - 1) / block;
+  return (int)(b < 1 ? 1 : (b > 65536 ? 65536 : b));
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* crp_last_error(void) { return g_err; }
+
+int32_t crp_version(void) { return 100; }
+
+crp_status crp_set_allocator(crp_alloc_fn alloc, crp_free_fn release, void* user) {
+  if ((alloc == nullptr) != (release == nullptr)) {
+    set_error("crp_set_allocator: alloc and release must both be set or both be NULL");
+    return CRP_E_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc = alloc;
+  g_free = release;
+  g_alloc_user = user;
+  return CRP_OK;
+}
+
+crp_status crp_context_create(int32_t device, uint64_t seed, size_t capacity, crp_context** out) {
+  if (!out || capacity == 0) {
+    set_error("crp_context_create: out must be non-NULL and capacity > 0");
+    return CRP_E_INVALID;
+  }
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return fail_cuda(e, "crp_context_create: cudaGetDeviceCount");
+  if (device < 0 || device >= ndev) {
+    set_error("crp_context_create: device %d not present (%d devices)", device, ndev);
+    return CRP_E_INVALID;
+  }
+  DeviceGuard g(device);
+  crp_context* c = new (std::nothrow) crp_context;
+  if (!c) {
+    set_error("crp_context_create: host allocation failed");
+    return CRP_E_OOM;
+  }
+  memset(c, 0, sizeof(*c));
+  c->device = device;
+  c->seed = seed;
+  c->capacity = capacity;
+  cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  e = cudaMallocHost(&c->hc, sizeof(DevCounters));
+  if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+  if (e != cudaSuccess) {
+    delete c;
+    return fail_cuda(e, "crp_context_create");
+  }
+  *out = c;
+  return CRP_OK;
+}
+
+crp_status crp_context_destroy(crp_context* c) {
+  if (!c) return CRP_OK;
+  DeviceGuard g(c->device);
+  cudaDeviceSynchronize();
+  dev_free(c->pool);
+  dev_free(c->dc);
+  if (c->hc) cudaFreeHost(c->hc);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  delete c;
+  return CRP_OK;
+}
+
+crp_status crp_context_size(const crp_context* c, size_t* n_out) {
+  if (!c || !n_out) {
+    set_error("crp_context_size: NULL argument");
+    return CRP_E_INVALID;
+  }
+  *n_out = c->size;
+  return CRP_OK;
+}
+
+// ---------------------------------------------------------------------------
+crp_status crp_grid_create(crp_context* c, const crp_grid_desc* d, crp_grid** out) {
+  if (!c || !d || !out) {
+    set_error("crp_grid_create: NULL argument");
+    return CRP_E_INVALID;
+  }
+  *out = nullptr;
+  if (d->n[0] < 2 || d->n[1] < 2 || d->n[2] < 2 || !(d->spacing > 0.0) ||
+      (d->dtype != CRP_F32 && d->dtype != CRP_F64)) {
+    set_error("crp_grid_create: need n >= 2 per axis, spacing > 0, dtype F32|F64");
+    return CRP_E_INVALID;
+  }
+  if (d->n[0] > (1 << 20) || d->n[1] > (1 << 20) || d->n[2] > (1 << 20)) {
+    set_error("crp_grid_create: at most 2^20 nodes per axis");
+    return CRP_E_INVALID;
+  }
+  const int64_t N = d->n[0] * d->n[1] * d->n[2];
+  if (d->source == CRP_GRID_TURBULENT) {
+    if (!(d->lmin > 0.0) || !(d->lmax >= d->lmin) || !(d->brms >= 0.0)) {
+      set_error("crp_grid_create: turbulence needs 0 < lmin <= lmax and brms >= 0");
+      return CRP_E_INVALID;
+    }
+  } else if (d->source == CRP_GRID_FROM_HOST || d->source == CRP_GRID_FROM_DEVICE) {
+    if (!d->data || (d->data_dtype != CRP_F32 && d->data_dtype != CRP_F64)) {
+      set_error("crp_grid_create: data pointer and data_dtype F32|F64 required");
+      return CRP_E_INVALID;
+    }
+  } else {
+    set_error("crp_grid_create: unknown source %d", d->source);
+    return CRP_E_INVALID;
+  }
+  DeviceGuard g(c->device);
+  crp_grid* gr = new (std::nothrow) crp_grid;
+  if (!gr) {
+    set_error("crp_grid_create: host allocation failed");
+    return CRP_E_OOM;
+  }
+  gr->ctx = c;
+  gr->desc = *d;
+  gr->desc.data = nullptr;
+  gr->N = N;
+  gr->nodes = dev_alloc((size_t)N * node_bytes(d->dtype));
+  if (!gr->nodes) {
+    delete gr;
+    set_error("crp_grid_create: cannot allocate %zu bytes", (size_t)N * node_bytes(d->dtype));
+    return CRP_E_OOM;
+  }
+  crp_status st = CRP_OK;
+  cudaStream_t s = 0;
+  if (d->source == CRP_GRID_TURBULENT) {
+    st = grid_turbulence(d, gr->nodes, s);
+  } else {
+    const size_t esz = d->data_dtype == CRP_F32 ? 4 : 8;
+    const size_t bytes = (size_t)N * 3 * esz;
+    const void* src = d->data;
+    void* staging = nullptr;
+    if (d->source == CRP_GRID_FROM_HOST) {
+      staging = dev_alloc(bytes);
+      if (!staging) {
+        st = CRP_E_OOM;
+        set_error("crp_grid_create: cannot allocate staging buffer");
+      } else {
+        cudaError_t e = cudaMemcpy(staging, d->data, bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) st = fail_cuda(e, "crp_grid_create: copy from host");
+        src = staging;
+      }
+    }
+    if (st == CRP_OK) st = grid_pack(src, d->data_dtype, N, d->dtype, gr->nodes, s);
+    if (st == CRP_OK) {
+      cudaError_t e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) st = fail_cuda(e, "crp_grid_create");
+    }
+    dev_free(staging);
+  }
+  if (st != CRP_OK) {
+    dev_free(gr->nodes);
+    delete gr;
+    return st;
+  }
+  *out = gr;
+  return CRP_OK;
+}
+
+crp_status crp_grid_destroy(crp_grid* g) {
+  if (!g) return CRP_OK;
+  DeviceGuard dg(g->ctx->device);
+  cudaDeviceSynchronize();
+  dev_free(g->nodes);
+  delete g;
+  return CRP_OK;
+}
+
+crp_status crp_grid_copy_out(const crp_grid* g, double* host_out) {
+  if (!g || !host_out) {
+    set_error("crp_grid_copy_out: NULL argument");
+    return CRP_E_INVALID;
+  }
+  DeviceGuard dg(g->ctx->device);
+  const size_t bytes = (size_t)g->N * 3 * sizeof(double);
+  double* tmp = static_cast<double*>(dev_alloc(bytes));
+  if (!tmp) {
+    set_error("crp_grid_copy_out: cannot allocate %zu bytes", bytes);
+    return CRP_E_OOM;
+  }
+  crp_status st = grid_unpack(g->nodes, g->desc.dtype, g->N, tmp, 0);
+  if (st == CRP_OK) {
+    cudaError_t e = cudaMemcpy(host_out, tmp, bytes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) st = fail_cuda(e, "crp_grid_copy_out");
+  }
+  dev_free(tmp);
+  return st;
+}
+
+// ---------------------------------------------------------------------------
+static crp_status tables_check(const crp_tables_desc* d) {
+  if (!d || d->n < 2 || d->n > (1 << 24) || !(d->gamma_lo > 0.0) || !(d->gamma_hi > d->gamma_lo) ||
+      !(d->length_unit_m > 0.0)) {
+    set_error("tables: need n >= 2, 0 < gamma_lo < gamma_hi, length_unit_m > 0");
+    return CRP_E_INVALID;
+  }
+  return CRP_OK;
+}
+
+static crp_tables* tables_alloc(crp_context* c, const crp_tables_desc* d) {
+  crp_tables* t = new (std::nothrow) crp_tables;
+  if (!t) return nullptr;
+  t->ctx = c;
+  t->desc = *d;
+  t->data = static_cast<double*>(dev_alloc(3 * (size_t)d->n * sizeof(double)));
+  if (!t->data) {
+    delete t;
+    return nullptr;
+  }
+  return t;
+}
+
+crp_status crp_tables_build(crp_context* c, const crp_tables_desc* d, crp_tables** out) {
+  if (!c || !out) {
+    set_error("crp_tables_build: NULL argument");
+    return CRP_E_INVALID;
+  }
+  if (tables_check(d) != CRP_OK) return CRP_E_INVALID;
+  if (!(d->T_cmb > 0.0) || !(d->gdr_fwhm_eV > 0.0) || !(d->gdr_hi_eV > d->gdr_lo_eV)) {
+    set_error("crp_tables_build: need T_cmb > 0, gdr_fwhm > 0, gdr_lo < gdr_hi");
+    return CRP_E_INVALID;
+  }
+  DeviceGuard g(c->device);
+  crp_tables* t = tables_alloc(c, d);
+  if (!t) {
+    set_error("crp_tables_build: allocation failed");
+    return CRP_E_OOM;
+  }
+  crp_status st = tables_compute(d, t->data, t->data + d->n, t->data + 2 * d->n, 0);
+  if (st != CRP_OK) {
+    dev_free(t->data);
+    delete t;
+    return st;
+  }
+  *out = t;
+  return CRP_OK;
+}
+
+crp_status crp_tables_from_host(crp_context* c, const crp_tables_desc* d, const double* beta,
+                                const double* pion, const double* gdr, crp_tables** out) {
+  if (!c || !out || !beta || !pion || !gdr) {
+    set_error("crp_tables_from_host: NULL argument");
+    return CRP_E_INVALID;
+  }
+  if (tables_check(d) != CRP_OK) return CRP_E_INVALID;
+  DeviceGuard g(c->device);
+  crp_tables* t = tables_alloc(c, d);
+  if (!t) {
+    set_error("crp_tables_from_host: allocation failed");
+    return CRP_E_OOM;
+  }
+  const size_t b = (size_t)d->n * sizeof(double);
+  cudaError_t e = cudaMemcpy(t->data, beta, b, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(t->data + d->n, pion, b, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(t->data + 2 * d->n, gdr, b, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    dev_free(t->data);
+    delete t;
+    return fail_cuda(e, "crp_tables_from_host");
+  }
+  *out = t;
+  return CRP_OK;
+}
+
+crp_status crp_tables_copy_out(const crp_tables* t, double* beta, double* pion, double* gdr) {
+  if (!t || !beta || !pion || !gdr) {
+    set_error("crp_tables_copy_out: NULL argument");
+    return CRP_E_INVALID;
+  }
+  DeviceGuard g(t->ctx->device);
+  const size_t b = (size_t)t->desc.n * sizeof(double);
+  cudaError_t e = cudaMemcpy(beta, t->data, b, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(pion, t->data + t->desc.n, b, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(gdr, t->data + 2 * t->desc.n, b, cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? CRP_OK : fail_cuda(e, "crp_tables_copy_out");
+}
+
+crp_status crp_tables_destroy(crp_tables* t) {
+  if (!t) return CRP_OK;
+  DeviceGuard g(t->ctx->device);
+  cudaDeviceSynchronize();
+  dev_free(t->data);
+  delete t;
+  return CRP_OK;
+}
+
+// ---------------------------------------------------------------------------
+crp_status crp_candidates_inject(crp_context* c, const crp_candidate_arrays* a, size_t n,
+                                 uint64_t first_id, void* stream) {
+  if (!c || !a) {
+    set_error("crp_candidates_inject: NULL argument");
+    return CRP_E_INVALID;
+  }
+  if (n == 0) return CRP_OK;
+  if (!a->x || !a->y || !a->z || !a->ux || !a->uy || !a->uz || !a->E || !a->A || !a->Z) {
+    set_error("crp_candidates_inject: x, y, z, ux, uy, uz, E, A, Z are required");
+    return CRP_E_INVALID;
+  }
+  if (n > c->capacity - c->size) {
+    set_error("crp_candidates_inject: %zu candidates do not fit (pool %zu of %zu used)", n,
+              c->size, c->capacity);
+    return CRP_E_QUEUE_FULL;
+  }
+  DeviceGuard g(c->device);
+  crp_status st = ensure_pool(c);
+  if (st != CRP_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const cudaMemcpyKind kind = a->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const size_t base = c->size;
+  cudaError_t e = cudaSuccess;
+  auto cp = [&](void* dst, const void* src, size_t elem) {
+    if (e == cudaSuccess && src) e = cudaMemcpyAsync(dst, src, n * elem, kind, s);
+  };
+  cp(c->st.x + base, a->x, 8);
+  cp(c->st.y + base, a->y, 8);
+  cp(c->st.z + base, a->z, 8);
+  cp(c->st.ux + base, a->ux, 8);
+  cp(c->st.uy + base, a->uy, 8);
+  cp(c->st.uz + base, a->uz, 8);
+  cp(c->st.E + base, a->E, 8);
+  cp(c->st.A + base, a->A, 4);
+  cp(c->st.Z + base, a->Z, 4);
+  cp(c->st.q + base, a->q, 4);
+  cp(c->st.s_max + base, a->s_max, 8);
+  cp(c->st.id + base, a->id, 8);
+  if (e != cudaSuccess) return fail_cuda(e, "crp_candidates_inject: copy");
+  e = cudaMemsetAsync(&c->dc->error_word, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return fail_cuda(e, "crp_candidates_inject: memset");
+  k_inject_init<<<blocks_for(n, 256), 256, 0, s>>>(c->st, base, n, first_id, a->id != nullptr,
+                                                     a->q != nullptr, a->s_max != nullptr,
+                                                     &c->dc->error_word);
+  e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&c->hc->error_word, &c->dc->error_word, sizeof(unsigned),
+                        cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail_cuda(e, "crp_candidates_inject");
+  if (c->hc->error_word) {
+    set_error("crp_candidates_inject: %u invalid candidates (need A >= 1, 0 <= Z <= A, q = +-1, "
+              "finite E > 0, |u| = 1, s_max >= 0); nothing injected",
+              c->hc->error_word);
+    return CRP_E_INVALID;
+  }
+  c->size += n;
+  return CRP_OK;
+}
+
+crp_status crp_candidates_clear(crp_context* c) {
+  if (!c) {
+    set_error("crp_candidates_clear: NULL argument");
+    return CRP_E_INVALID;
+  }
+  c->size = 0;
+  return CRP_OK;
+}
+
+// ---------------------------------------------------------------------------
+static void fill_field_view(const crp_grid* g, FieldView& f) {
+  f.data = g->nodes;
+  for (int d = 0; d < 3; ++d) {
+    f.n[d] = g->desc.n[d];
+    f.mask[d] = (g->desc.n[d] & (g->desc.n[d] - 1)) == 0 ? g->desc.n[d] - 1 : -1;
+    f.origin[d] = g->desc.origin[d];
+  }
+  f.spacing = g->desc.spacing;
+  f.inv_spacing = 1.0 / g->desc.spacing;
+  f.inv_spacing_f = (float)f.inv_spacing;
+  f.dtype = g->desc.dtype;
+}
+
+crp_status crp_propagate(crp_context* c, const crp_grid* g, const crp_modules* m, void* stream,
+                         crp_stats* stats_out) {
+  if (!c || !g || !m) {
+    set_error("crp_propagate: NULL argument");
+    return CRP_E_INVALID;
+  }
+  if (g->ctx->device != c->device) {
+    set_error("crp_propagate: grid belongs to another device");
+    return CRP_E_INVALID;
+  }
+  if (m->precision != CRP_FP64 && m->precision != CRP_MIXED) {
+    set_error("crp_propagate: precision must be CRP_FP64 or CRP_MIXED");
+    return CRP_E_INVALID;
+  }
+  if (!(m->tol > 0.0) || !(m->h_min > 0.0) || !(m->h_max >= m->h_min) ||
+      !(m->field_unit_T > 0.0) || !(m->length_unit_m > 0.0)) {
+    set_error("crp_propagate: need tol > 0, 0 < h_min <= h_max, positive units");
+    return CRP_E_INVALID;
+  }
+  const uint32_t need_tab = CRP_PAIR | CRP_PION | CRP_PHOTODIS;
+  if ((m->flags & need_tab) && !m->tables) {
+    set_error("crp_propagate: PAIR / PION / PHOTODIS need tables");
+    return CRP_E_INVALID;
+  }
+  if (m->block_size < 0 || m->block_size > 256 || (m->block_size % 32) != 0 ||
+      m->blocks_per_sm < 0) {
+    set_error("crp_propagate: block_size must be a multiple of 32 up to 256");
+    return CRP_E_INVALID;
+  }
+  if (stats_out) memset(stats_out, 0, sizeof(*stats_out));
+  if (c->size == 0) return CRP_OK;
+  DeviceGuard dg(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+  KParams kp;
+  memset(&kp, 0, sizeof(kp));
+  fill_field_view(g, kp.f);
+  kp.tol = m->tol;
+  kp.tol2 = m->tol * m->tol;
+  kp.h_min = m->h_min;
+  kp.h_max = m->h_max;
+  kp.curv_k = 299792458.0 * m->field_unit_T * m->length_unit_m;
+  kp.beta_ad = m->beta_ad;
+  kp.e_min = m->e_min;
+  kp.flags = m->flags;
+  kp.seed = c->seed;
+  if (m->tables) {
+    const crp_tables* t = m->tables;
+    kp.t_beta = t->data;
+    kp.t_pion = t->data + t->desc.n;
+    kp.t_gdr = t->data + 2 * t->desc.n;
+    kp.tab_lg0 = log(t->desc.gamma_lo);
+    kp.tab_inv_dlg = (double)(t->desc.n - 1) / (log(t->desc.gamma_hi) - log(t->desc.gamma_lo));
+    kp.tab_n = t->desc.n;
+  } else {
+    kp.tab_n = 2;
+  }
+  for (int d = 0; d < 3; ++d) {
+    kp.obs_c[d] = m->observer_center[d];
+    kp.border_c[d] = m->border_center[d];
+    kp.gal_c[d] = m->gal_center[d];
+  }
+  kp.obs_r = m->observer_radius;
+  kp.border_r = m->border_radius;
+  kp.disk_b = m->disk_b;
+  kp.sin_pitch = sin(m->disk_pitch_rad);
+  kp.cos_pitch = cos(m->disk_pitch_rad);
+  kp.disk_hz = m->disk_hz;
+  kp.disk_rmin = m->disk_rmin;
+  kp.disk_rmax = m->disk_rmax;
+  kp.halo_b = m->halo_b;
+  kp.halo_z0 = m->halo_z0;
+  kp.halo_sigma = m->halo_sigma;
+  kp.max_steps = m->max_steps ? m->max_steps : 100000000ull;  // bound every candidate
+  kp.step_budget = m->step_budget;
+  kp.deadline_ns = m->deadline_ms > 0.0 ? (uint64_t)(m->deadline_ms * 1e6) : 0;
+  kp.capacity = c->capacity;
+
+  const int block = m->block_size ? m->block_size : 128;
+  int bps = m->blocks_per_sm;
+  if (!bps) {
+    cudaError_t e = m->precision == CRP_FP64
+                        ? occupancy_propagate_fp64(kp.f.dtype, block, &bps)
+                        : occupancy_propagate_mixed(kp.f.dtype, block, &bps);
+    if (e != cudaSuccess) return fail_cuda(e, "crp_propagate: occupancy query");
+    if (bps < 1) bps = 1;
+  }
+
+  cudaError_t e = cudaMemsetAsync(c->dc, 0, sizeof(DevCounters), s);
+  if (e == cudaSuccess) {
+    k_set_u64<<<1, 1, 0, s>>>(&c->dc->tail, (unsigned long long)c->size);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return fail_cuda(e, "crp_propagate: counters");
+
+  crp_status st = CRP_OK;
+  uint64_t lo = 0, hi = c->size;
+  uint32_t launches = 0;
+  float total_ms = 0.f;
+  while (lo < hi) {
+    kp.lo = lo;
+    kp.hi = hi;
+    const uint64_t work = hi - lo;
+    uint64_t gsz = (uint64_t)c->sm_count * (uint64_t)bps;
+    const uint64_t need = (work + block - 1) / block;
+    if (need < gsz) gsz = need;
+    k_set_u64<<<1, 1, 0, s>>>(&c->dc->head, (unsigned long long)lo);
+    cudaEventRecord(c->ev0, s);
+    e = m->precision == CRP_FP64 ? launch_propagate_fp64(kp, c->st, c->dc, (int)gsz, block, s)
+                                 : launch_propagate_mixed(kp, c->st, c->dc, (int)gsz, block, s);
+    if (e != cudaSuccess) return fail_cuda(e, "crp_propagate: launch");
+    cudaEventRecord(c->ev1, s);
+    launches += 1;
+    e = cudaMemcpyAsync(c->hc, c->dc, sizeof(DevCounters), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_cuda(e, "crp_propagate: kernel");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    total_ms += ms;
+    if (c->hc->stop) {
+      st = CRP_E_TIMEOUT;
+      set_error("crp_propagate: step budget or deadline reached; candidates stay resumable");
+      break;
+    }
+    uint64_t tail = c->hc->tail < c->capacity ? c->hc->tail : c->capacity;
+    lo = hi;
+    hi = tail;
+  }
+  uint64_t tail = c->hc->tail < c->capacity ? c->hc->tail : c->capacity;
+  c->size = tail;
+  if (st == CRP_OK && c->hc->overflow) {
+    st = CRP_E_QUEUE_FULL;
+    set_error("crp_propagate: %llu secondaries did not fit the pool capacity %zu",
+              (unsigned long long)c->hc->overflow, c->capacity);
+  }
+  if (stats_out) {
+    stats_out->accepted_steps = c->hc->acc;
+    stats_out->rejected_trials = c->hc->rej;
+    stats_out->rhs_evals = c->hc->rhs;
+    stats_out->n_pion = c->hc->pion;
+    stats_out->n_pd = c->hc->pd;
+    stats_out->n_secondaries = c->hc->secondaries;
+    stats_out->n_dropped = c->hc->dropped;
+    stats_out->n_overflow = c->hc->overflow;
+    stats_out->n_detected = c->hc->detected;
+    stats_out->kernel_ms = total_ms;
+    stats_out->launches = launches;
+    stats_out->error_word = c->hc->error_word;
+    // candidates still active (non-zero only after a timeout)
+    if (st == CRP_E_TIMEOUT) {
+      unsigned long long* cnt = &c->dc->head;
+      cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s);
+      k_count_active<<<blocks_for(c->size, 256), 256, 0, s>>>(c->st.status, c->size, cnt);
+      cudaMemcpyAsync(&c->hc->head, cnt, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+      cudaStreamSynchronize(s);
+      stats_out->n_active = c->hc->head;
+    }
+  }
+  return st;
+}
+
+// ---------------------------------------------------------------------------
+crp_status crp_collect(crp_context* c, int32_t what, crp_record* out, size_t capacity,
+                       size_t* n_out, int32_t out_on_device, void* stream) {
+  if (!c || !n_out || (capacity && !out) || what < CRP_COLLECT_ALL || what > CRP_COLLECT_AT_BORDER) {
+    set_error("crp_collect: bad argument");
+    return CRP_E_INVALID;
+  }
+  *n_out = 0;
+  if (c->size == 0) return CRP_OK;
+  DeviceGuard dg(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const uint64_t n = c->size;
+  const int nb = (int)((n + kCollectBlock - 1) / kCollectBlock);
+  unsigned* counts = static_cast<unsigned*>(dev_alloc(sizeof(unsigned) * nb));
+  unsigned long long* offs =
+      static_cast<unsigned long long*>(dev_alloc(sizeof(unsigned long long) * (nb + 1)));
+  crp_status st = CRP_OK;
+  crp_record* tmp = nullptr;
+  do {
+    if (!counts || !offs) {
+      st = CRP_E_OOM;
+      set_error("crp_collect: allocation failed");
+      break;
+    }
+    k_collect_count<<<nb, kCollectBlock, 0, s>>>(c->st.status, n, what, counts);
+    k_collect_scan<<<1, 1024, 0, s>>>(counts, nb, offs);
+    unsigned long long total = 0;
+    cudaError_t e = cudaMemcpyAsync(&total, offs + nb, sizeof(total), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { st = fail_cuda(e, "crp_collect: count"); break; }
+    *n_out = (size_t)total;
+    if (total == 0) break;
+    if (total > capacity) {
+      st = CRP_E_INVALID;
+      set_error("crp_collect: %llu records selected, capacity %zu", total, capacity);
+      break;
+    }
+    crp_record* dst = out;
+    if (!out_on_device) {
+      tmp = static_cast<crp_record*>(dev_alloc(sizeof(crp_record) * total));
+      if (!tmp) { st = CRP_E_OOM; set_error("crp_collect: staging allocation failed"); break; }
+      dst = tmp;
+    }
+    k_collect_scatter<<<nb, kCollectBlock, 0, s>>>(c->st, n, what, offs, dst);
+    e = cudaGetLastError();
+    if (e == cudaSuccess && !out_on_device)
+      e = cudaMemcpyAsync(out, tmp, sizeof(crp_record) * total, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { st = fail_cuda(e, "crp_collect"); break; }
+  } while (0);
+  dev_free(tmp);
+  dev_free(counts);
+  dev_free(offs);
+  return st;
+}
+
+crp_status crp_histogram_energy(crp_context* c, int32_t what, double e_lo, double e_hi,
+                                int32_t nbins, uint64_t* out, void* stream) {
+  if (!c || !out || nbins < 1 || !(e_lo > 0.0) || !(e_hi > e_lo) || what < CRP_COLLECT_ALL ||
+      what > CRP_COLLECT_AT_BORDER) {
+    set_error("crp_histogram_energy: bad argument");
+    return CRP_E_INVALID;
+  }
+  memset(out, 0, sizeof(uint64_t) * nbins);
+  if (c->size == 0) return CRP_OK;
+  DeviceGuard dg(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned long long* bins = static_cast<unsigned long long*>(dev_alloc(8 * (size_t)nbins));
+  if (!bins) {
+    set_error("crp_histogram_energy: allocation failed");
+    return CRP_E_OOM;
+  }
+  const double l0 = log(e_lo), inv = (double)nbins / (log(e_hi) - l0);
+  cudaError_t e = cudaMemsetAsync(bins, 0, 8 * (size_t)nbins, s);
+  if (e == cudaSuccess) {
+    k_hist_energy<<<blocks_for(c->size, 256), 256, 0, s>>>(c->st.status, c->st.E, c->size, what,
+                                                           l0, inv, nbins, bins);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, bins, 8 * (size_t)nbins, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  dev_free(bins);
+  return e == cudaSuccess ? CRP_OK : fail_cuda(e, "crp_histogram_energy");
+}
+
+}  // extern "C"
+
+static_assert(sizeof(crp_record) == 208, "crp_record layout");
+static_assert(sizeof(crp_stats) == 96, "crp_stats layout");

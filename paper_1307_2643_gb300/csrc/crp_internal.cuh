@@ -1,0 +1,100 @@
+// crp_internal.cuh -- device-side data layout shared by the library's kernels.
+//
+// Candidate pool: structure of arrays in HBM, one slot per candidate
+// (primaries first, secondaries appended).  Each array is 256-byte aligned so
+// a warp touching 32 consecutive slots issues full 32-byte sectors.  A
+// candidate's whole propagation state lives in its slot (CRPropa 3.0,
+// Sect. 3: all propagation state is stored in the candidate), which is what
+// lets any warp pick any candidate up, stop it and resume it later.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/crp.h"
+
+namespace crp {
+
+// Binary64 grid node: (Bx, By, Bz, 0), 32-byte aligned for two 16-byte loads.
+struct __align__(32) DNode {
+  double x, y, z, w;
+};
+
+// ---- error reporting (api.cu) -------------------------------------------
+void set_error(const char* fmt, ...);
+crp_status fail_cuda(cudaError_t e, const char* what);
+void* dev_alloc(size_t bytes);
+void dev_free(void* p);
+
+// ---- kernel error-word bits ---------------------------------------------
+enum : uint32_t {
+  ERR_QUEUE_FULL = 1u << 0,
+  ERR_BAD_CANDIDATE = 1u << 1,
+  ERR_TRIAL_LIMIT = 1u << 2,
+};
+
+// per-candidate flag bits
+enum : uint32_t {
+  CF_STATES_DRAWN = 1u << 0,
+};
+
+struct DevState {
+  uint64_t *id, *parent;
+  double *x, *y, *z, *ux, *uy, *uz;
+  double *E, *s, *s_max, *h, *d_pion, *d_pd;
+  double *x0, *y0, *z0, *ux0, *uy0, *uz0, *E0;
+  uint64_t *n_acc, *n_rej;
+  int32_t *A, *Z, *q, *A0, *Z0, *status;
+  uint32_t *draws, *events, *generation, *n_pion, *n_pd, *n_dropped, *flags, *lens_pixel;
+};
+
+// Device-resident counters of one propagate call.
+struct DevCounters {
+  unsigned long long head;         // next pool index to hand out
+  unsigned long long tail;         // pool size (secondaries appended atomically)
+  unsigned long long acc, rej, rhs, pion, pd, secondaries, dropped, overflow, detected;
+  unsigned int error_word;
+  unsigned int stop;               // set when the step budget or deadline ran out
+  unsigned long long t_start;      // globaltimer at first warp start
+};
+
+struct FieldView {
+  const void* data;                // float4 (F32) or DNode (F64) per node
+  int64_t n[3];
+  int64_t mask[3];                 // n-1 when n is a power of two, else -1
+  double origin[3];
+  double spacing, inv_spacing;
+  float inv_spacing_f;
+  int dtype;
+};
+
+struct KParams {
+  FieldView f;
+  double tol, tol2, h_min, h_max, curv_k, beta_ad, e_min;
+  uint32_t flags;
+  uint64_t seed;
+  const double* t_beta;
+  const double* t_pion;
+  const double* t_gdr;
+  double tab_lg0, tab_inv_dlg;
+  int64_t tab_n;
+  double obs_c[3], obs_r;
+  double border_c[3], border_r;
+  double disk_b, sin_pitch, cos_pitch, disk_hz, disk_rmin, disk_rmax;
+  double halo_b, halo_z0, halo_sigma;
+  double gal_c[3];
+  uint64_t max_steps;
+  uint64_t step_budget;
+  uint64_t deadline_ns;
+  uint64_t lo, hi, capacity;
+};
+
+// Launch one propagate generation over pool slots [kp.lo, kp.hi).
+cudaError_t launch_propagate_fp64(const KParams& kp, const DevState& st, DevCounters* dc,
+                                  int grid, int block, cudaStream_t s);
+cudaError_t launch_propagate_mixed(const KParams& kp, const DevState& st, DevCounters* dc,
+                                   int grid, int block, cudaStream_t s);
+cudaError_t occupancy_propagate_fp64(int dtype, int block, int* blocks_per_sm);
+cudaError_t occupancy_propagate_mixed(int dtype, int block, int* blocks_per_sm);
+
+}  // namespace crp

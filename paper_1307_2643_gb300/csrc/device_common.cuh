@@ -1,0 +1,81 @@
+// device_common.cuh -- device primitives: counter-based random numbers,
+// lineage ids and the Cash-Karp tableau.
+#pragma once
+
+#include <stdint.h>
+
+namespace crp {
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+// easy as 1, 2, 3", SC'11): per round, two 32x32 -> 64-bit products of
+// counter words 0 and 2 with 0xD2511F53 / 0xCD9E8D57; the new counter is
+// (hi(c2 m1) ^ c1 ^ k0, lo(c2 m1), hi(c0 m0) ^ c3 ^ k1, lo(c0 m0)); the key
+// advances by the Weyl increments 0x9E3779B9 / 0xBB67AE85 between rounds.
+struct Philox4 {
+  uint32_t v0, v1, v2, v3;
+};
+
+__device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                 uint32_t c3, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi_a = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo_a = 0xD2511F53u * c0;
+    const uint32_t hi_b = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t lo_b = 0xCD9E8D57u * c2;
+    const uint32_t n0 = hi_b ^ c1 ^ k0;
+    const uint32_t n2 = hi_a ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo_b;
+    c2 = n2;
+    c3 = lo_a;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return Philox4{c0, c1, c2, c3};
+}
+
+// Open-interval uniform from two words: (top 52 bits of hi:lo + 1/2) * 2^-52.
+__device__ __forceinline__ double u01_open(uint32_t lo, uint32_t hi) {
+  const unsigned long long v = ((unsigned long long)hi << 32) | lo;
+  return ((double)(v >> 12) + 0.5) * 2.220446049250313080847263336181640625e-16;
+}
+
+// Stream tags of the counter (draw, tag, id_lo, id_hi).
+constexpr uint32_t TAG_FIELD = 1;
+constexpr uint32_t TAG_INTERACTION = 2;
+
+__device__ __forceinline__ Philox4 draw4(uint64_t seed, uint32_t tag, uint64_t id,
+                                         uint32_t draw) {
+  return philox4x32_10(draw, tag, (uint32_t)id, (uint32_t)(id >> 32), (uint32_t)seed,
+                       (uint32_t)(seed >> 32));
+}
+
+// SplitMix64 finaliser (Steele, Lea, Flood, OOPSLA 2014) over a Weyl step:
+// id of the secondary of a parent's event number `ev`.
+__device__ __forceinline__ uint64_t lineage_id(uint64_t parent, uint32_t ev) {
+  uint64_t z = parent + 0x9E3779B97F4A7C15ull * ((uint64_t)ev + 1ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Cash-Karp 5(4) (Cash & Karp, ACM TOMS 16, 201, 1990): stage coefficients,
+// fifth-order weights and (fifth - embedded fourth) weights, each the
+// nearest double of its rational.
+namespace ck {
+constexpr double a21 = 1.0 / 5.0;
+constexpr double a31 = 3.0 / 40.0, a32 = 9.0 / 40.0;
+constexpr double a41 = 3.0 / 10.0, a42 = -9.0 / 10.0, a43 = 6.0 / 5.0;
+constexpr double a51 = -11.0 / 54.0, a52 = 5.0 / 2.0, a53 = -70.0 / 27.0, a54 = 35.0 / 27.0;
+constexpr double a61 = 1631.0 / 55296.0, a62 = 175.0 / 512.0, a63 = 575.0 / 13824.0,
+                 a64 = 44275.0 / 110592.0, a65 = 253.0 / 4096.0;
+constexpr double w1 = 37.0 / 378.0, w3 = 250.0 / 621.0, w4 = 125.0 / 594.0, w6 = 512.0 / 1771.0;
+constexpr double d1 = -277.0 / 64512.0, d3 = 6925.0 / 370944.0, d4 = -6925.0 / 202752.0,
+                 d5 = -277.0 / 14336.0, d6 = 277.0 / 7084.0;
+}  // namespace ck
+
+// Proton rest energy [eV] (CODATA 2018).
+constexpr double MP_C2_EV = 938.27208816e6;
+
+}  // namespace crp

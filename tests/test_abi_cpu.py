@@ -1,0 +1,85 @@
+"""CPU-side checks of the C ABI: the library builds, loads without a GPU,
+exports every function include/crp.h declares, and the ctypes structures have
+the C layout.  No compute call is made."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "crp.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\**\s+\**(crp_[a-z_0-9]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def crp():
+    from paper_1307_2643_gb300.build import build
+    build()
+    from paper_1307_2643_gb300 import crp as mod
+    mod.lib()
+    return mod
+
+
+def test_every_declared_symbol_is_exported(crp):
+    names = declared_functions()
+    assert len(names) >= 15
+    L = ctypes.CDLL(crp.LIB_PATH)
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    assert sorted(crp.SYMBOLS) == names
+
+
+def test_version_and_error_string(crp):
+    assert crp.lib().crp_version() == 100
+    assert isinstance(crp.lib().crp_last_error(), bytes)
+
+
+def test_struct_layouts_match_c(crp, tmp_path):
+    prog = tmp_path / "sizes.c"
+    prog.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "crp.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu\\n\","
+        "sizeof(crp_grid_desc), sizeof(crp_tables_desc), sizeof(crp_candidate_arrays),"
+        "sizeof(crp_modules), sizeof(crp_stats), sizeof(crp_record),"
+        "offsetof(crp_modules, tables), offsetof(crp_record, status));return 0;}\n")
+    exe = tmp_path / "sizes"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)],
+                   check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    want = [ctypes.sizeof(crp.GridDesc), ctypes.sizeof(crp.TablesDesc),
+            ctypes.sizeof(crp.CandidateArrays), ctypes.sizeof(crp.Modules),
+            ctypes.sizeof(crp.Stats), crp.RECORD_DTYPE.itemsize,
+            crp.Modules.tables.offset, crp.RECORD_DTYPE.fields["status"][1]]
+    assert got == want
+
+
+def test_no_oracle_in_product_package():
+    """The product package neither imports nor reads the oracle."""
+    pkg = os.path.join(ROOT, "paper_1307_2643_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "crp_oracle" not in text and "liborc" not in text, f
+
+
+def test_context_create_without_gpu_fails_cleanly(crp):
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    with pytest.raises(crp.CrpError):
+        crp.crp_context_create(0, 1, 16)
+    assert len(crp.lib().crp_last_error()) > 0

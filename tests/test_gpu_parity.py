@@ -1,0 +1,333 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle on
+the same seeded inputs.
+
+Bars (from the method's required tolerances):
+  * integer / index results (statuses, interaction counts, draw counters,
+    species, lineage ids, generations) bit-exact;
+  * FP64 path: positions, directions, energies, lengths within rel 1e-9;
+  * mixed path: within rel 1e-5 on quasi-ballistic candidates, and by
+    distribution (KS p > 0.01) where the trajectories are chaotic.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+import workloads  # noqa: E402
+from gpu_util import assert_chains_equal, oracle_params, rel_err, run_gpu  # noqa: E402
+from paper_1307_2643_gb300 import crp  # noqa: E402
+
+H0_OVER_C = 67.3e3 / 299792458.0  # 1/Mpc
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1307_2643_gb300.build import build
+    build()
+    oracle.build()
+
+
+@pytest.fixture(scope="module")
+def field64():
+    n, dx = (64, 64, 64), 0.25
+    return n, dx, oracle.turbulent_field(n, dx, 0.5, 8.0, 1.0, seed=21)
+
+
+@pytest.fixture(scope="module")
+def tables():
+    return oracle.tables_build(n=1000)
+
+
+def _plain(n_cand, seed=31, s_max=50.0):
+    inj = workloads.plain_small(n=n_cand, seed=seed)
+    inj["s_max"] = np.full(n_cand, s_max)
+    return inj
+
+
+# ---------------------------------------------------------------------------
+# setup kernels
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [(64, 64, 64), (24, 20, 18)])
+def test_turbulence_generator_matches_oracle(n):
+    dx, lmin, lmax, brms, seed = 0.25, 0.5, 5.0, 1.7, 4242
+    ref = oracle.turbulent_field(n, dx, lmin, lmax, brms, seed=seed)
+    ctx = crp.crp_context_create(0, 1, 16)
+    try:
+        d = crp.grid_desc(n, dx, dtype=crp.F64, source=crp.GRID_TURBULENT, lmin=lmin, lmax=lmax,
+                          brms=brms, seed=seed)
+        g = crp.crp_grid_create(ctx, d)
+        got = crp.crp_grid_copy_out(g, n)
+        crp.crp_grid_destroy(g)
+    finally:
+        crp.crp_context_destroy(ctx)
+    assert got.shape == ref.shape
+    assert np.max(np.abs(got - ref)) < 1e-10 * brms
+
+
+def test_turbulence_f32_storage_is_rounded_f64():
+    n, dx = (32, 32, 32), 0.25
+    ctx = crp.crp_context_create(0, 1, 16)
+    try:
+        out = []
+        for dt in (crp.F64, crp.F32):
+            d = crp.grid_desc(n, dx, dtype=dt, source=crp.GRID_TURBULENT, lmin=0.5, lmax=8.0,
+                              brms=1.0, seed=3)
+            g = crp.crp_grid_create(ctx, d)
+            out.append(crp.crp_grid_copy_out(g, n))
+            crp.crp_grid_destroy(g)
+    finally:
+        crp.crp_context_destroy(ctx)
+    assert np.array_equal(out[0].astype(np.float32).astype(np.float64), out[1])
+
+
+def test_tables_match_oracle(tables):
+    ctx = crp.crp_context_create(0, 1, 16)
+    try:
+        t = crp.crp_tables_build(ctx, crp.tables_desc(n=1000))
+        beta, pion, gdr = crp.crp_tables_copy_out(t, 1000)
+        crp.crp_tables_destroy(t)
+    finally:
+        crp.crp_context_destroy(ctx)
+    for got, ref in ((beta, tables.beta_pair), (pion, tables.rate_pion), (gdr, tables.rate_gdr)):
+        live = ref > 1e-200 * ref.max()
+        assert np.all((got == 0) == (ref == 0)) or np.all(np.abs(got[~live]) < 1e-150 * ref.max())
+        assert np.max(rel_err(got[live], ref[live], floor=0.0)) < 1e-8
+
+
+# ---------------------------------------------------------------------------
+# FP64 path: bit-level agreement expected (same operation order, no FMA)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype", [crp.F64, crp.F32])
+def test_fp64_plain_parity(field64, dtype):
+    n, dx, B = field64
+    Bin = B if dtype == crp.F64 else B.astype(np.float32).astype(np.float64)
+    inj = _plain(3001)
+    kw = dict(tol=1e-4, h_min=0.01, h_max=1.0)
+    gpu, st, status = run_gpu(Bin, n, dx, inj, precision=crp.FP64, dtype=dtype, **kw)
+    ref = oracle.propagate(oracle_params(n, dx, **kw), Bin, inj)
+    assert status == crp.OK
+    assert_chains_equal(gpu, ref)
+    assert np.array_equal(gpu["n_acc"], ref["n_acc"]) and np.array_equal(gpu["n_rej"], ref["n_rej"])
+    for f in ("x", "u", "E", "s"):
+        assert np.max(rel_err(gpu[f], ref[f])) < 1e-9, f
+    assert st["accepted_steps"] == int(ref["n_acc"].sum())
+    assert st["rejected_trials"] == int(ref["n_rej"].sum())
+    assert np.all(gpu["status"] == crp.MAX_LENGTH)
+
+
+def _interaction_inputs(n_mixed=1200, n_hot=240, seed=77):
+    w = workloads.MIXED_INTERACTIONS
+    inj = workloads.mixed_interactions(n=n_mixed, seed=seed)
+    g = np.random.default_rng(seed)
+    A = np.where(g.random(n_hot) < 0.5, 56, 14).astype(np.int32)
+    Z = np.where(A == 56, 26, 7).astype(np.int32)
+    v = g.normal(size=(n_hot, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    hot = dict(id=np.arange(n_mixed, n_mixed + n_hot, dtype=np.uint64),
+               x=g.uniform(-20, 20, n_hot), y=g.uniform(-20, 20, n_hot), z=g.uniform(-20, 20, n_hot),
+               ux=v[:, 0].copy(), uy=v[:, 1].copy(), uz=v[:, 2].copy(),
+               E=10 ** g.uniform(19.8, 21.0, n_hot), A=A, Z=Z, q=np.ones(n_hot, np.int32))
+    out = {k: np.concatenate([inj[k], hot[k]]) for k in hot}
+    out["s_max"] = np.full(len(out["E"]), 40.0)
+    return out
+
+
+INTERACTION_FLAGS = (crp.PAIR | crp.ADIABATIC | crp.PION | crp.PHOTODIS | crp.EMIN |
+                     crp.OBSERVER)
+
+
+def _interaction_kw():
+    return dict(tol=1e-4, h_min=0.01, h_max=1.0, beta_ad=H0_OVER_C, e_min=1e18)
+
+
+@pytest.fixture(scope="module")
+def field_f32_small():
+    n, dx = (64, 64, 64), 0.1
+    B = oracle.turbulent_field(n, dx, 0.2, 5.0, 1.0, seed=22)
+    return n, dx, B.astype(np.float32).astype(np.float64)
+
+
+@pytest.fixture(scope="module")
+def interaction_ref(field_f32_small, tables):
+    n, dx, B = field_f32_small
+    inj = _interaction_inputs()
+    P = oracle_params(n, dx, tables=tables, flags=INTERACTION_FLAGS, obs_r=1.0, **_interaction_kw())
+    return inj, oracle.propagate(P, B, inj, tables=tables)
+
+
+def test_fp64_interactions_parity(field_f32_small, tables, interaction_ref):
+    n, dx, B = field_f32_small
+    inj, ref = interaction_ref
+    gpu, st, status = run_gpu(B, n, dx, inj, precision=crp.FP64, dtype=crp.F32, tables=tables,
+                              flags=INTERACTION_FLAGS, observer_radius=1.0, **_interaction_kw())
+    assert status == crp.OK
+    # the workload exercises every module
+    assert ref["n_pion"].sum() > 50 and ref["n_pd"].sum() > 50
+    assert (ref["generation"] > 0).sum() > 20
+    assert set(np.unique(ref["status"])) >= {crp.BELOW_EMIN, crp.MAX_LENGTH}
+    assert_chains_equal(gpu, ref)
+    for f in ("x", "u", "E", "s", "x0", "u0", "E0"):
+        assert np.max(rel_err(gpu[f], ref[f])) < 1e-9, f
+    assert st["n_pion"] == int(ref["n_pion"].sum())
+    assert st["n_pd"] == int(ref["n_pd"].sum())
+    assert st["n_secondaries"] == int((ref["generation"] > 0).sum())
+
+
+def test_launch_configuration_does_not_change_results(field_f32_small, tables):
+    n, dx, B = field_f32_small
+    inj = _interaction_inputs(n_mixed=300, n_hot=100, seed=5)
+    kw = dict(precision=crp.FP64, dtype=crp.F32, tables=tables, flags=INTERACTION_FLAGS,
+              observer_radius=1.0, **_interaction_kw())
+    a, _, _ = run_gpu(B, n, dx, inj, block_size=32, blocks_per_sm=1, **kw)
+    b, _, _ = run_gpu(B, n, dx, inj, block_size=256, **kw)
+    c, _, _ = run_gpu(B, n, dx, inj, block_size=64, blocks_per_sm=3, **kw)
+    assert a.tobytes() == b.tobytes() == c.tobytes()
+
+
+def test_timeout_and_resume_is_bit_identical(field_f32_small, tables):
+    n, dx, B = field_f32_small
+    inj = crp.host_injection(_interaction_inputs(n_mixed=400, n_hot=80, seed=9))
+    m = len(inj["E"])
+    full, _, _ = run_gpu(B, n, dx, inj, precision=crp.FP64, dtype=crp.F32, tables=tables,
+                         flags=INTERACTION_FLAGS, observer_radius=1.0, **_interaction_kw())
+    ctx = crp.crp_context_create(0, 1234, 4 * m)
+    try:
+        g = crp.crp_grid_create(ctx, crp.grid_desc(n, dx, dtype=crp.F32, data=B))
+        th = crp.crp_tables_from_host(ctx, crp.tables_desc(n=tables.n), tables.beta_pair,
+                                      tables.rate_pion, tables.rate_gdr)
+        crp.crp_candidates_inject(ctx, crp.candidate_arrays(inj), m)
+        M = crp.modules(precision=crp.FP64, tables=th, flags=INTERACTION_FLAGS,
+                        observer_radius=1.0, step_budget=20000, **_interaction_kw())
+        calls = 0
+        while True:
+            status, st = crp.crp_propagate(ctx, g, M, raise_on_error=False)
+            calls += 1
+            assert status in (crp.OK, crp.E_TIMEOUT)
+            if status == crp.OK:
+                break
+            assert st.n_active > 0
+            assert calls < 10000
+        resumed = np.sort(crp.crp_collect(ctx, crp.COLLECT_ALL), order="id")
+        crp.crp_tables_destroy(th)
+        crp.crp_grid_destroy(g)
+    finally:
+        crp.crp_context_destroy(ctx)
+    assert calls > 3
+    assert resumed.tobytes() == full.tobytes()
+
+
+def test_queue_overflow_reports_and_finishes(field_f32_small, tables):
+    n, dx, B = field_f32_small
+    inj = _interaction_inputs(n_mixed=0, n_hot=200, seed=13)
+    m = len(inj["E"])
+    gpu, st, status = run_gpu(B, n, dx, inj, precision=crp.FP64, dtype=crp.F32, tables=tables,
+                              capacity=m + 5, flags=INTERACTION_FLAGS, observer_radius=1.0,
+                              **_interaction_kw())
+    assert status == crp.E_QUEUE_FULL
+    assert st["n_overflow"] > 0 and st["error_word"] & 1
+    assert len(gpu) == m + 5
+    assert np.all(gpu["status"] != crp.ACTIVE)
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+def test_edge_cases(field64):
+    n, dx, B = field64
+    kw = dict(tol=1e-4, h_min=0.01, h_max=1.0, flags=crp.EMIN | crp.OBSERVER, e_min=2e19,
+              observer_radius=1.0)
+    inj = _plain(7)
+    inj["s_max"][0] = 0.0                      # zero budget: one zero-length step
+    inj["E"][1] = 1e19                         # below e_min at injection
+    inj["x"][2], inj["y"][2], inj["z"][2] = 0.3, 0.0, 0.0  # starts inside the observer
+    inj["x"][3] = 5.0                          # heads for the observer
+    inj["ux"][3], inj["uy"][3], inj["uz"][3] = -1.0, 0.0, 0.0
+    inj["E"][3] = 1e21
+    gpu, _, status = run_gpu(B, n, dx, inj, precision=crp.FP64, **kw)
+    okw = dict(kw)
+    flags = okw.pop("flags")
+    okw.pop("observer_radius")
+    ref = oracle.propagate(oracle_params(n, dx, flags=oracle.EMIN | oracle.OBSERVER, obs_r=1.0,
+                                         **okw), B, inj)
+    assert status == crp.OK
+    assert_chains_equal(gpu, ref)
+    assert gpu["status"][0] == crp.MAX_LENGTH and gpu["n_acc"][0] == 1 and gpu["s"][0] == 0.0
+    assert gpu["status"][1] == crp.BELOW_EMIN and gpu["n_acc"][1] == 1
+    assert gpu["status"][2] != crp.DETECTED
+    assert gpu["status"][3] == crp.DETECTED
+    assert np.max(rel_err(gpu["x"], ref["x"])) < 1e-9
+
+
+def test_empty_and_invalid_inputs(field64):
+    n, dx, B = field64
+    ctx = crp.crp_context_create(0, 1, 8)
+    try:
+        g = crp.crp_grid_create(ctx, crp.grid_desc(n, dx, dtype=crp.F64, data=B))
+        status, st = crp.crp_propagate(ctx, g, crp.modules())   # empty pool
+        assert status == crp.OK and st.accepted_steps == 0
+        assert len(crp.crp_collect(ctx)) == 0
+        bad = crp.host_injection(_plain(3))
+        bad["A"][1] = 0
+        with pytest.raises(crp.CrpError) as e:
+            crp.crp_candidates_inject(ctx, crp.candidate_arrays(bad), 3)
+        assert e.value.status == crp.E_INVALID
+        assert crp.crp_context_size(ctx) == 0
+        with pytest.raises(crp.CrpError) as e:
+            crp.crp_candidates_inject(ctx, crp.candidate_arrays(crp.host_injection(_plain(9))), 9)
+        assert e.value.status == crp.E_QUEUE_FULL
+        with pytest.raises(crp.CrpError):
+            crp.crp_propagate(ctx, g, crp.modules(h_min=0.0))
+        crp.crp_grid_destroy(g)
+    finally:
+        crp.crp_context_destroy(ctx)
+
+
+# ---------------------------------------------------------------------------
+# mixed precision
+# ---------------------------------------------------------------------------
+def test_mixed_parity_quasi_ballistic(field64):
+    """1e19-1e20 eV protons over 50 Mpc in 1 nG: rel 1e-5 per candidate."""
+    n, dx, B = field64
+    B32 = B.astype(np.float32).astype(np.float64)
+    inj = _plain(3001)
+    kw = dict(tol=1e-4, h_min=0.01, h_max=1.0)
+    gpu, st, status = run_gpu(B32, n, dx, inj, precision=crp.MIXED, dtype=crp.F32, **kw)
+    ref = oracle.propagate(oracle_params(n, dx, **kw), B32, inj)
+    assert status == crp.OK
+    assert_chains_equal(gpu, ref)
+    ex = rel_err(gpu["x"], ref["x"]).max(axis=1)
+    eu = np.abs(gpu["u"] - ref["u"]).max(axis=1)
+    assert np.max(ex) < 1e-5, np.max(ex)
+    assert np.max(eu) < 1e-5, np.max(eu)
+    assert np.array_equal(gpu["E"], ref["E"]) and np.array_equal(gpu["s"], ref["s"])
+    # the mixed path takes essentially the same steps
+    assert abs(int(gpu["n_acc"].sum()) - int(ref["n_acc"].sum())) < 1e-3 * ref["n_acc"].sum()
+
+
+def test_mixed_interactions_statistics(field_f32_small, tables, interaction_ref):
+    """Chaotic low-rigidity nuclei: per-candidate paths diverge, the physics
+    must not: energies and species agree by distribution, interaction counts
+    and energies of quasi-ballistic candidates per candidate."""
+    from scipy.stats import ks_2samp
+    n, dx, B = field_f32_small
+    inj, ref = interaction_ref
+    gpu, _, status = run_gpu(B, n, dx, inj, precision=crp.MIXED, dtype=crp.F32, tables=tables,
+                             flags=INTERACTION_FLAGS, observer_radius=1.0, **_interaction_kw())
+    assert status == crp.OK
+    assert abs(len(gpu) - len(ref)) <= 0.02 * len(ref)
+    for f in ("E",):
+        p = ks_2samp(np.log(gpu[f]), np.log(ref[f])).pvalue
+        assert p > 0.01, (f, p)
+    prim_g = gpu[gpu["generation"] == 0]
+    prim_r = ref[ref["generation"] == 0]
+    assert np.array_equal(prim_g["id"], prim_r["id"])
+    # energy losses and interactions do not depend on position: per candidate
+    # they agree wherever the stopping condition did
+    same = prim_g["status"] == prim_r["status"]
+    assert same.mean() > 0.95
+    e = rel_err(prim_g["E"][same], prim_r["E"][same], floor=0.0)
+    assert np.median(e) < 1e-5
+    assert np.mean(prim_g["n_pion"][same] == prim_r["n_pion"][same]) > 0.95
