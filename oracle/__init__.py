@@ -108,7 +108,7 @@ def lib():
             L.orc_uniform_open.restype = d
             L.orc_child_id.argtypes = [u64, u32]
             L.orc_child_id.restype = u64
-            for name in ("orc_phi_pair",):
+            for name in ("orc_phi_pair", "orc_series_log"):
                 getattr(L, name).argtypes = [d]
                 getattr(L, name).restype = d
             L.orc_planck_density.argtypes = [d, d]
@@ -170,6 +170,10 @@ def uniform_open(lo: int, hi: int) -> float:
 
 def child_id(parent: int, event_index: int) -> int:
     return lib().orc_child_id(parent, event_index)
+
+
+def series_log(x: float) -> float:
+    return lib().orc_series_log(x)
 
 
 def phi_pair(k: float) -> float:

@@ -117,6 +117,50 @@ uint64_t child_id(uint64_t parent_id, uint32_t event_index) {
 }
 
 // ---------------------------------------------------------------------------
+// Natural logarithm by the classical atanh series (reading: both the oracle
+// and the GPU library evaluate the logarithms that steer the propagation --
+// interaction free paths -ln(u) and the ln(Gamma) of table lookups -- with
+// this one formula, so that those values agree bit for bit; a library log
+// may differ by an ulp, and the adaptive step controller turns an ulp into a
+// different step sequence).
+//   x = 2^k m with m in [sqrt(1/2), sqrt(2)],  s = (m - 1)/(m + 1),
+//   ln m = 2 atanh(s) = 2 s (1 + s^2/3 + s^4/5 + ... + s^26/27),
+//   ln x = k ln 2 + ln m.
+// Valid for positive normal finite x; |s| <= 0.172, so the truncated tail is
+// below 1e-21 and the result is within a few ulp of ln x.
+// ---------------------------------------------------------------------------
+double series_log(double x) {
+  uint64_t b;
+  std::memcpy(&b, &x, sizeof(b));
+  int k = (int)((b >> 52) & 0x7ff) - 1023;
+  uint64_t mb = (b & 0x000FFFFFFFFFFFFFULL) | 0x3FF0000000000000ULL;
+  double m;
+  std::memcpy(&m, &mb, sizeof(m));
+  if (m > 1.4142135623730951) {
+    m = m * 0.5;
+    k = k + 1;
+  }
+  const double s = (m - 1.0) / (m + 1.0);
+  const double z = s * s;
+  double poly = 1.0 / 27.0;
+  poly = poly * z + 1.0 / 25.0;
+  poly = poly * z + 1.0 / 23.0;
+  poly = poly * z + 1.0 / 21.0;
+  poly = poly * z + 1.0 / 19.0;
+  poly = poly * z + 1.0 / 17.0;
+  poly = poly * z + 1.0 / 15.0;
+  poly = poly * z + 1.0 / 13.0;
+  poly = poly * z + 1.0 / 11.0;
+  poly = poly * z + 1.0 / 9.0;
+  poly = poly * z + 1.0 / 7.0;
+  poly = poly * z + 1.0 / 5.0;
+  poly = poly * z + 1.0 / 3.0;
+  poly = poly * z + 1.0;
+  const double ln_m = 2.0 * s * poly;
+  return (double)k * 0.69314718055994530942 + ln_m;
+}
+
+// ---------------------------------------------------------------------------
 // Photon field: Planck spectrum of the CMB.
 // n(eps) = eps^2 / (pi^2 (hbar c)^3 (exp(eps/kT) - 1))   [1 / (m^3 eV)]
 // ---------------------------------------------------------------------------
@@ -418,6 +462,7 @@ void orc_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out) 
 double orc_uniform_open(uint32_t lo, uint32_t hi) { return uniform_open(lo, hi); }
 uint64_t orc_child_id(uint64_t parent, uint32_t ev) { return child_id(parent, ev); }
 double orc_phi_pair(double k) { return phi_pair(k); }
+double orc_series_log(double x) { return series_log(x); }
 double orc_planck_density(double eps, double kT) { return planck_density(eps, kT); }
 double orc_beta_pair_proton(double gamma, double T) { return beta_pair_proton(gamma, kKB * T); }
 double orc_rate_pion_nucleon(double gamma, double T, double sigma0_mb, double eps_th_eV) {
@@ -663,16 +708,16 @@ double draw_uniform(const Ctx& C, Cand& c) {
 // module-list order [pion production, photodisintegration].
 void reset_states(const Ctx& C, Cand& c) {
   const orc_params& P = *C.P;
-  double lng = std::log(gamma_of(c));
+  double lng = series_log(gamma_of(c));
   if (P.flags & ORC_PION) {
     double u = draw_uniform(C, c);
     double R = (double)c.A * table_lookup(C, C.t_pion, lng);
-    c.d_pion = R > 0.0 ? -std::log(u) / R : INFINITY;
+    c.d_pion = R > 0.0 ? -series_log(u) / R : INFINITY;
   }
   if (P.flags & ORC_PHOTODIS) {
     double u = draw_uniform(C, c);
     double R = c.A >= 2 ? (double)c.A * table_lookup(C, C.t_gdr, lng) : 0.0;
-    c.d_pd = R > 0.0 ? -std::log(u) / R : INFINITY;
+    c.d_pd = R > 0.0 ? -series_log(u) / R : INFINITY;
   }
   c.states_drawn = true;
 }
@@ -793,7 +838,7 @@ void propagate_one(const Ctx& C, Cand& c, std::vector<Cand>& out_secondaries) {
     if (P.flags & (ORC_PAIR | ORC_ADIABATIC)) {
       double beta = 0.0;
       if (P.flags & ORC_PAIR) {
-        double bp = table_lookup(C, C.t_beta, std::log(gamma_of(c)));
+        double bp = table_lookup(C, C.t_beta, series_log(gamma_of(c)));
         beta = bp * (double)(c.Z * c.Z) / (double)c.A;
       }
       if (P.flags & ORC_ADIABATIC) beta = beta + P.beta_ad;
