@@ -222,8 +222,13 @@ typedef struct {
                                 candidate reaching it stops with CRP_BUDGET. */
   uint64_t step_budget;      /* accepted steps in this call before TIMEOUT (0 = none) */
   double deadline_ms;        /* wall-clock limit of this call (0 = none) */
-  int32_t block_size;        /* threads per block, multiple of 32 up to 256 (0 = default) */
-  int32_t blocks_per_sm;     /* resident blocks per SM (0 = autotuned) */
+  int32_t block_size;        /* threads per block, multiple of 32, at most 128 (FP64)
+                                or 256 (MIXED); 0 = that maximum */
+  int32_t blocks_per_sm;     /* resident blocks per SM (0 = occupancy maximum) */
+  uint32_t slice;            /* accepted steps a lane runs on one candidate before
+                                requeueing it for the next round (0 = 512); bounds
+                                the load imbalance between lanes of a warp */
+  uint32_t reserved;
 } crp_modules;
 
 typedef struct {
@@ -280,7 +285,8 @@ typedef struct {
 
 /* Copy the records selected by `what`, in pool order, into `out` (host or
  * device memory per out_on_device; capacity records).  *n_out receives the
- * number selected; CRP_E_INVALID if capacity is too small (nothing copied). */
+ * number selected; CRP_E_INVALID if capacity is too small (nothing copied).
+ * out = NULL with capacity 0 only counts (size query). */
 crp_status crp_collect(crp_context* ctx, int32_t what, crp_record* out, size_t capacity,
                        size_t* n_out, int32_t out_on_device, void* stream);
 

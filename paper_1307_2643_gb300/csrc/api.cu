@@ -82,6 +82,7 @@ struct crp_context {
   DevState st;
   DevCounters* dc;        // device counters
   DevCounters* hc;        // pinned host mirror
+  uint32_t* queue[2];     // work queues of the propagate rounds (capacity each)
   int sm_count;
   cudaEvent_t ev0, ev1;
 };
@@ -96,7 +97,8 @@ struct crp_grid {
 struct crp_tables {
   crp_context* ctx;
   crp_tables_desc desc;
-  double* data;  // beta | pion | gdr, n each
+  double* data;   // beta | pion | gdr, n each
+  float* data_f;  // binary32 copy of the three tables
 };
 
 namespace {
@@ -153,10 +155,17 @@ crp_status ensure_pool(crp_context* c) {
   }
   layout_pool(static_cast<char*>(c->pool), c->capacity, &c->st);
   c->dc = static_cast<DevCounters*>(dev_alloc(sizeof(DevCounters)));
-  if (!c->dc) {
+  c->queue[0] = static_cast<uint32_t*>(dev_alloc(c->capacity * sizeof(uint32_t)));
+  c->queue[1] = static_cast<uint32_t*>(dev_alloc(c->capacity * sizeof(uint32_t)));
+  if (!c->dc || !c->queue[0] || !c->queue[1]) {
     dev_free(c->pool);
+    dev_free(c->dc);
+    dev_free(c->queue[0]);
+    dev_free(c->queue[1]);
     c->pool = nullptr;
-    set_error("candidate pool: cannot allocate counters");
+    c->dc = nullptr;
+    c->queue[0] = c->queue[1] = nullptr;
+    set_error("candidate pool: cannot allocate counters / work queues");
     return CRP_E_OOM;
   }
   return CRP_OK;
@@ -209,6 +218,36 @@ __global__ void k_inject_init(DevState st, uint64_t base, uint64_t n, uint64_t f
 }
 
 __global__ void k_set_u64(unsigned long long* p, unsigned long long v) { *p = v; }
+
+__global__ void k_to_float(const double* in, float* out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+// Work queue of the first round: every active candidate of the pool.  The
+// loop bound is warp-uniform so every lane takes part in each ballot.
+__global__ void k_build_queue(const int32_t* status, uint64_t n, uint32_t* queue,
+                              unsigned long long* count) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  for (uint64_t base_i = blockIdx.x * (uint64_t)blockDim.x; base_i < n; base_i += stride) {
+    const uint64_t i = base_i + threadIdx.x;
+    const bool act = i < n && status[i] == CRP_ACTIVE;
+    const unsigned m = __ballot_sync(0xffffffffu, act);
+    if (!m) continue;
+    const int leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (act) queue[base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)i;
+  }
+}
+
+__global__ void k_round_reset(DevCounters* dc) {
+  dc->head = 0;
+  dc->q_out = 0;
+}
 
 __global__ void k_count_active(const int32_t* status, uint64_t n, unsigned long long* out) {
   unsigned long long cnt = 0;
@@ -398,6 +437,8 @@ crp_status crp_context_destroy(crp_context* c) {
   cudaDeviceSynchronize();
   dev_free(c->pool);
   dev_free(c->dc);
+  dev_free(c->queue[0]);
+  dev_free(c->queue[1]);
   if (c->hc) cudaFreeHost(c->hc);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
@@ -543,7 +584,10 @@ static crp_tables* tables_alloc(crp_context* c, const crp_tables_desc* d) {
   t->ctx = c;
   t->desc = *d;
   t->data = static_cast<double*>(dev_alloc(3 * (size_t)d->n * sizeof(double)));
-  if (!t->data) {
+  t->data_f = static_cast<float*>(dev_alloc(3 * (size_t)d->n * sizeof(float)));
+  if (!t->data || !t->data_f) {
+    dev_free(t->data);
+    dev_free(t->data_f);
     delete t;
     return nullptr;
   }
@@ -567,8 +611,14 @@ crp_status crp_tables_build(crp_context* c, const crp_tables_desc* d, crp_tables
     return CRP_E_OOM;
   }
   crp_status st = tables_compute(d, t->data, t->data + d->n, t->data + 2 * d->n, 0);
+  if (st == CRP_OK) {
+    k_to_float<<<blocks_for(3 * d->n, 256), 256>>>(t->data, t->data_f, 3 * d->n);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) st = fail_cuda(e, "crp_tables_build: float copy");
+  }
   if (st != CRP_OK) {
     dev_free(t->data);
+    dev_free(t->data_f);
     delete t;
     return st;
   }
@@ -593,8 +643,13 @@ crp_status crp_tables_from_host(crp_context* c, const crp_tables_desc* d, const 
   cudaError_t e = cudaMemcpy(t->data, beta, b, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(t->data + d->n, pion, b, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(t->data + 2 * d->n, gdr, b, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_to_float<<<blocks_for(3 * d->n, 256), 256>>>(t->data, t->data_f, 3 * d->n);
+    e = cudaDeviceSynchronize();
+  }
   if (e != cudaSuccess) {
     dev_free(t->data);
+    dev_free(t->data_f);
     delete t;
     return fail_cuda(e, "crp_tables_from_host");
   }
@@ -620,6 +675,7 @@ crp_status crp_tables_destroy(crp_tables* t) {
   DeviceGuard g(t->ctx->device);
   cudaDeviceSynchronize();
   dev_free(t->data);
+  dev_free(t->data_f);
   delete t;
   return CRP_OK;
 }
@@ -732,9 +788,10 @@ crp_status crp_propagate(crp_context* c, const crp_grid* g, const crp_modules* m
     set_error("crp_propagate: PAIR / PION / PHOTODIS need tables");
     return CRP_E_INVALID;
   }
-  if (m->block_size < 0 || m->block_size > 256 || (m->block_size % 32) != 0 ||
+  const int max_block = m->precision == CRP_FP64 ? 128 : 256;
+  if (m->block_size < 0 || m->block_size > max_block || (m->block_size % 32) != 0 ||
       m->blocks_per_sm < 0) {
-    set_error("crp_propagate: block_size must be a multiple of 32 up to 256");
+    set_error("crp_propagate: block_size must be a multiple of 32 up to %d", max_block);
     return CRP_E_INVALID;
   }
   if (stats_out) memset(stats_out, 0, sizeof(*stats_out));
@@ -762,9 +819,27 @@ crp_status crp_propagate(crp_context* c, const crp_grid* g, const crp_modules* m
     kp.tab_lg0 = log(t->desc.gamma_lo);
     kp.tab_inv_dlg = (double)(t->desc.n - 1) / (log(t->desc.gamma_hi) - log(t->desc.gamma_lo));
     kp.tab_n = t->desc.n;
+    kp.t_beta_f = t->data_f;
   } else {
     kp.tab_n = 2;
   }
+  kp.tol2_f = (float)kp.tol2;
+  kp.inv_tol2_f = (float)(1.0 / kp.tol2);
+  kp.h_min_f = (float)kp.h_min;
+  kp.h_max_f = (float)kp.h_max;
+  kp.curv_k_f = (float)kp.curv_k;
+  kp.beta_ad_f = (float)kp.beta_ad;
+  kp.tab_lg0_f = (float)kp.tab_lg0;
+  kp.tab_inv_dlg_f = (float)kp.tab_inv_dlg;
+  kp.gdisk_b = (float)m->disk_b;
+  kp.gsin = (float)kp.sin_pitch;
+  kp.gcos = (float)kp.cos_pitch;
+  kp.ginv_hz = m->disk_hz > 0.0 ? (float)(1.0 / m->disk_hz) : 0.f;
+  kp.grmin = (float)m->disk_rmin;
+  kp.grmax = (float)m->disk_rmax;
+  kp.ghalo_b = (float)m->halo_b;
+  kp.ghalo_z0 = (float)m->halo_z0;
+  kp.ghalo_inv2s2 = m->halo_sigma > 0.0 ? (float)(1.0 / (2.0 * m->halo_sigma * m->halo_sigma)) : 0.f;
   for (int d = 0; d < 3; ++d) {
     kp.obs_c[d] = m->observer_center[d];
     kp.border_c[d] = m->border_center[d];
@@ -786,7 +861,7 @@ crp_status crp_propagate(crp_context* c, const crp_grid* g, const crp_modules* m
   kp.deadline_ns = m->deadline_ms > 0.0 ? (uint64_t)(m->deadline_ms * 1e6) : 0;
   kp.capacity = c->capacity;
 
-  const int block = m->block_size ? m->block_size : 128;
+  const int block = m->block_size ? m->block_size : (m->precision == CRP_FP64 ? 128 : 256);
   int bps = m->blocks_per_sm;
   if (!bps) {
     cudaError_t e = m->precision == CRP_FP64
@@ -796,25 +871,37 @@ crp_status crp_propagate(crp_context* c, const crp_grid* g, const crp_modules* m
     if (bps < 1) bps = 1;
   }
 
+  if (c->size > 0xffffffffull) {
+    set_error("crp_propagate: pool indices must fit 32 bits");
+    return CRP_E_INVALID;
+  }
+  // round 0 work queue: the active candidates of the pool
   cudaError_t e = cudaMemsetAsync(c->dc, 0, sizeof(DevCounters), s);
   if (e == cudaSuccess) {
     k_set_u64<<<1, 1, 0, s>>>(&c->dc->tail, (unsigned long long)c->size);
+    k_build_queue<<<blocks_for(c->size, 256), 256, 0, s>>>(c->st.status, c->size, c->queue[0],
+                                                           &c->dc->q_out);
     e = cudaGetLastError();
   }
-  if (e != cudaSuccess) return fail_cuda(e, "crp_propagate: counters");
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->hc, c->dc, sizeof(DevCounters), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail_cuda(e, "crp_propagate: work queue");
+  uint64_t n_in = c->hc->q_out;
+  int qi = 0;
+  kp.slice = m->slice ? m->slice : 512u;
 
   crp_status st = CRP_OK;
-  uint64_t lo = 0, hi = c->size;
   uint32_t launches = 0;
   float total_ms = 0.f;
-  while (lo < hi) {
-    kp.lo = lo;
-    kp.hi = hi;
-    const uint64_t work = hi - lo;
+  while (n_in > 0) {
+    kp.queue_in = c->queue[qi];
+    kp.queue_out = c->queue[qi ^ 1];
+    kp.n_in = n_in;
     uint64_t gsz = (uint64_t)c->sm_count * (uint64_t)bps;
-    const uint64_t need = (work + block - 1) / block;
+    const uint64_t need = (n_in + block - 1) / block;
     if (need < gsz) gsz = need;
-    k_set_u64<<<1, 1, 0, s>>>(&c->dc->head, (unsigned long long)lo);
+    k_round_reset<<<1, 1, 0, s>>>(c->dc);
     cudaEventRecord(c->ev0, s);
     e = m->precision == CRP_FP64 ? launch_propagate_fp64(kp, c->st, c->dc, (int)gsz, block, s)
                                  : launch_propagate_mixed(kp, c->st, c->dc, (int)gsz, block, s);
@@ -832,9 +919,8 @@ crp_status crp_propagate(crp_context* c, const crp_grid* g, const crp_modules* m
       set_error("crp_propagate: step budget or deadline reached; candidates stay resumable");
       break;
     }
-    uint64_t tail = c->hc->tail < c->capacity ? c->hc->tail : c->capacity;
-    lo = hi;
-    hi = tail;
+    n_in = c->hc->q_out < c->capacity ? c->hc->q_out : c->capacity;
+    qi ^= 1;
   }
   uint64_t tail = c->hc->tail < c->capacity ? c->hc->tail : c->capacity;
   c->size = tail;
@@ -900,7 +986,7 @@ crp_status crp_collect(crp_context* c, int32_t what, crp_record* out, size_t cap
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { st = fail_cuda(e, "crp_collect: count"); break; }
     *n_out = (size_t)total;
-    if (total == 0) break;
+    if (total == 0 || (!out && capacity == 0)) break;  // size query
     if (total > capacity) {
       st = CRP_E_INVALID;
       set_error("crp_collect: %llu records selected, capacity %zu", total, capacity);

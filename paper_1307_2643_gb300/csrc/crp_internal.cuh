@@ -50,12 +50,12 @@ struct DevState {
 
 // Device-resident counters of one propagate call.
 struct DevCounters {
-  unsigned long long head;         // next pool index to hand out
+  unsigned long long head;         // next entry of the input work queue to hand out
   unsigned long long tail;         // pool size (secondaries appended atomically)
+  unsigned long long q_out;        // entries written to the output work queue
   unsigned long long acc, rej, rhs, pion, pd, secondaries, dropped, overflow, detected;
   unsigned int error_word;
   unsigned int stop;               // set when the step budget or deadline ran out
-  unsigned long long t_start;      // globaltimer at first warp start
 };
 
 struct FieldView {
@@ -71,6 +71,10 @@ struct FieldView {
 struct KParams {
   FieldView f;
   double tol, tol2, h_min, h_max, curv_k, beta_ad, e_min;
+  // binary32 copies for the mixed policy (converted once on the host)
+  float tol2_f, inv_tol2_f, h_min_f, h_max_f, curv_k_f, beta_ad_f, tab_lg0_f, tab_inv_dlg_f;
+  const float* t_beta_f;
+  float gdisk_b, gsin, gcos, ginv_hz, grmin, grmax, ghalo_b, ghalo_z0, ghalo_inv2s2;
   uint32_t flags;
   uint64_t seed;
   const double* t_beta;
@@ -86,15 +90,23 @@ struct KParams {
   uint64_t max_steps;
   uint64_t step_budget;
   uint64_t deadline_ns;
-  uint64_t lo, hi, capacity;
+  uint64_t capacity;
+  // work queues of one round: pool indices of active candidates
+  const uint32_t* queue_in;
+  uint64_t n_in;
+  uint32_t* queue_out;
+  uint32_t slice;                  // accepted steps per candidate per round
 };
 
-// Launch one propagate generation over pool slots [kp.lo, kp.hi).
+// Launch one propagate round over the candidates listed in kp.queue_in.
 cudaError_t launch_propagate_fp64(const KParams& kp, const DevState& st, DevCounters* dc,
                                   int grid, int block, cudaStream_t s);
 cudaError_t launch_propagate_mixed(const KParams& kp, const DevState& st, DevCounters* dc,
                                    int grid, int block, cudaStream_t s);
 cudaError_t occupancy_propagate_fp64(int dtype, int block, int* blocks_per_sm);
 cudaError_t occupancy_propagate_mixed(int dtype, int block, int* blocks_per_sm);
+// Dynamic shared memory of one propagate block (per-thread stage storage).
+size_t propagate_smem_fp64(int block);
+size_t propagate_smem_mixed(int block);
 
 }  // namespace crp

@@ -75,6 +75,41 @@ constexpr double d1 = -277.0 / 64512.0, d3 = 6925.0 / 370944.0, d4 = -6925.0 / 2
                  d5 = -277.0 / 14336.0, d6 = 277.0 / 7084.0;
 }  // namespace ck
 
+// Natural logarithm for the quantities that steer the propagation (free
+// paths -ln(u), ln(Gamma) of table lookups): x = 2^k m with m in
+// [sqrt(1/2), sqrt(2)], s = (m-1)/(m+1), ln m = 2 atanh(s) summed as the
+// series 2 s (1 + s^2/3 + ... + s^26/27) by Horner, ln x = k ln2 + ln m.
+// Positive normal finite x only.  Written out operation by operation so that
+// a translation unit built without multiply-add contraction reproduces the
+// same bits as any other IEEE binary64 evaluation of the same sequence.
+__device__ __forceinline__ double series_log(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  int k = (int)((b >> 52) & 0x7ffull) - 1023;
+  double m = __longlong_as_double((long long)((b & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull));
+  if (m > 1.4142135623730951) {
+    m = m * 0.5;
+    k = k + 1;
+  }
+  const double s = (m - 1.0) / (m + 1.0);
+  const double z = s * s;
+  double poly = 1.0 / 27.0;
+  poly = poly * z + 1.0 / 25.0;
+  poly = poly * z + 1.0 / 23.0;
+  poly = poly * z + 1.0 / 21.0;
+  poly = poly * z + 1.0 / 19.0;
+  poly = poly * z + 1.0 / 17.0;
+  poly = poly * z + 1.0 / 15.0;
+  poly = poly * z + 1.0 / 13.0;
+  poly = poly * z + 1.0 / 11.0;
+  poly = poly * z + 1.0 / 9.0;
+  poly = poly * z + 1.0 / 7.0;
+  poly = poly * z + 1.0 / 5.0;
+  poly = poly * z + 1.0 / 3.0;
+  poly = poly * z + 1.0;
+  const double ln_m = 2.0 * s * poly;
+  return (double)k * 0.69314718055994530942 + ln_m;
+}
+
 // Proton rest energy [eV] (CODATA 2018).
 constexpr double MP_C2_EV = 938.27208816e6;
 

@@ -1,19 +1,25 @@
 // propagate.cuh -- the persistent propagate kernel.
 //
-// One thread owns one candidate at a time and runs the module list of
-// CRPropa 3.0 (Sect. 3, Fig. 1) on it, one full cycle per loop iteration:
+// One lane owns one candidate at a time and runs the module list of
+// CRPropa 3.0 (Sect. 3, Fig. 1) on it:
 //   integration   Cash-Karp 5(4) trial steps of the Lorentz equation with
 //                 trilinear field interpolation until the step controller
-//                 accepts (Sect. 3: "deflects the particle ... updates the
-//                 position, direction and trajectory length");
+//                 accepts (the integration module deflects the particle and
+//                 updates position, direction and trajectory length);
 //   interactions  continuous pair-production and adiabatic losses; pion
 //                 production and photodisintegration, each deciding
 //                 independently, with all interaction states reset after any
 //                 interaction and secondaries appended to the pool;
 //   boundary / observer modules, then the IsActive check.
-// Warps are persistent: when a lane's candidate stops, the warp hands the
-// free lanes new pool slots with one atomic (ballot + popc), so candidates
-// of very different path lengths share warps without idling them.
+// Scheduling (GB300 design, not from the paper): a warp advances one
+// Cash-Karp trial per loop iteration for all its lanes, so the expensive
+// stage loop runs converged; a lane keeps a candidate for at most `slice`
+// accepted steps, then requeues it for the next round and takes the next
+// queue entry (one atomic per warp: ballot + popc).  Candidates whose path
+// lengths differ by orders of magnitude therefore share warps without
+// idling them, and the imbalance at the end of a round is bounded by one
+// slice.  Stage directions and forces live in shared memory (one column per
+// thread), so the stage loop is not unrolled and the code stays small.
 //
 // Two precision policies:
 //   FP64   every operation in binary64, in the same order as the reference
@@ -129,15 +135,14 @@ __device__ __forceinline__ float3 galactic_f32(const KParams& p, float rx, float
   const float cr = rx * ir, sr = ry * ir;
   const float az = fabsf(z);
   float b_r = 0.f, b_phi = 0.f;
-  if (r >= (float)p.disk_rmin && r <= (float)p.disk_rmax) {
-    const float bd = (float)p.disk_b * __expf(-az / (float)p.disk_hz);
-    b_r = bd * (float)p.sin_pitch;
-    b_phi = bd * (float)p.cos_pitch;
+  if (r >= p.grmin && r <= p.grmax) {
+    const float bd = p.gdisk_b * __expf(-az * p.ginv_hz);
+    b_r = bd * p.gsin;
+    b_phi = bd * p.gcos;
   }
   if (z != 0.f) {
-    const float dz = az - (float)p.halo_z0;
-    const float s = (float)p.halo_sigma;
-    const float bh = (float)p.halo_b * __expf(-dz * dz / (2.f * s * s));
+    const float dz = az - p.ghalo_z0;
+    const float bh = p.ghalo_b * __expf(-dz * dz * p.ghalo_inv2s2);
     b_phi += z > 0.f ? bh : -bh;
   }
   return make_float3(b_r * cr - b_phi * sr, b_r * sr + b_phi * cr, 0.f);
@@ -224,14 +229,14 @@ __device__ __forceinline__ double table_fp64(const KParams& p, const double* tab
   return a + f * (b - a);
 }
 
-__device__ __forceinline__ float table_f32(const KParams& p, const double* tab, float lng) {
-  float t = (lng - (float)p.tab_lg0) * (float)p.tab_inv_dlg;
+__device__ __forceinline__ float table_f32(const KParams& p, const float* tab, float lng) {
+  float t = (lng - p.tab_lg0_f) * p.tab_inv_dlg_f;
   const float tmax = (float)(p.tab_n - 1);
   t = fminf(fmaxf(t, 0.f), tmax);
   int i = (int)t;
   if (i > (int)p.tab_n - 2) i = (int)p.tab_n - 2;
   const float f = t - (float)i;
-  const float a = (float)__ldg(tab + i), b = (float)__ldg(tab + i + 1);
+  const float a = __ldg(tab + i), b = __ldg(tab + i + 1);
   return fmaf(f, b - a, a);
 }
 
@@ -246,17 +251,7 @@ struct LaneCore {
   int A, Z, q, status;
   uint32_t draws, events, n_pion, n_pd, n_dropped, flags;
   uint64_t n_acc, n_rej;
-};
-
-struct LaneFP64 : LaneCore {
-  double u[3];
-};
-
-struct LaneMixed : LaneCore {
-  float u[3];
-  int cell[3];   // grid cell of the current position
-  float frac[3]; // fractional position inside that cell (grid units)
-  float gal[3];  // position relative to the galactic centre (binary32)
+  int rejections;  // rejected trials of the current step
 };
 
 struct LaneCounters {
@@ -288,6 +283,7 @@ __device__ __forceinline__ void load_core(const DevState& st, uint64_t i, LaneCo
   c.flags = st.flags[i];
   c.n_acc = st.n_acc[i];
   c.n_rej = st.n_rej[i];
+  c.rejections = 0;
 }
 
 __device__ __forceinline__ void store_core(const DevState& st, const LaneCore& c) {
@@ -313,6 +309,18 @@ __device__ __forceinline__ void store_core(const DevState& st, const LaneCore& c
   st.n_rej[i] = c.n_rej;
 }
 
+// Per-thread stage storage in shared memory: slot k of this thread lives at
+// base[k * stride], so a warp touching one slot hits 32 consecutive words.
+// Slots 0..17: stage directions U[j][c]; 18..35: stage forces K[j][c].
+template <class T>
+struct StageStore {
+  T* base;
+  int stride;
+  __device__ __forceinline__ T& u(int j, int c) { return base[(j * 3 + c) * stride]; }
+  __device__ __forceinline__ T& k(int j, int c) { return base[(18 + j * 3 + c) * stride]; }
+};
+constexpr int kStageSlots = 36;
+
 // ---------------------------------------------------------------------------
 // Stochastic interactions (binary64 on both policies): draws, resets, events.
 // ---------------------------------------------------------------------------
@@ -325,27 +333,27 @@ __device__ __forceinline__ double draw_u(const KParams& p, LaneCore& c) {
 // Remaining free path d = -ln(u) / R(E) per interaction, in module order
 // [pion production, photodisintegration], at the current energy.
 __device__ __forceinline__ void reset_states(const KParams& p, LaneCore& c) {
-  const double lng = log(c.E / ((double)c.A * MP_C2_EV));
+  const double lng = series_log(c.E / ((double)c.A * MP_C2_EV));
   if (p.flags & CRP_PION) {
     const double u = draw_u(p, c);
     const double R = (double)c.A * table_fp64(p, p.t_pion, lng);
-    c.d_pion = R > 0.0 ? -log(u) / R : (double)INFINITY;
+    c.d_pion = R > 0.0 ? -series_log(u) / R : (double)INFINITY;
   }
   if (p.flags & CRP_PHOTODIS) {
     const double u = draw_u(p, c);
     const double R = c.A >= 2 ? (double)c.A * table_fp64(p, p.t_gdr, lng) : 0.0;
-    c.d_pd = R > 0.0 ? -log(u) / R : (double)INFINITY;
+    c.d_pd = R > 0.0 ? -series_log(u) / R : (double)INFINITY;
   }
   c.flags |= CF_STATES_DRAWN;
 }
 
 // Single-nucleon emission: proton with probability Z/A (kept away from
 // Z' = 0 or N' = 0 daughters with A' >= 2); the nucleon carries E/A, the
-// daughter E (A-1)/A; the nucleon is appended to the pool when E/A >= e_min.
-template <class Lane>
+// daughter E (A-1)/A; the nucleon is appended to the pool, and to the next
+// round's work queue, when E/A >= e_min.
 __device__ __forceinline__ void photodisintegrate(const KParams& p, const DevState& st,
-                                               DevCounters* dc, Lane& c, LaneCounters& lc,
-                                               const double u_dir[3]) {
+                                               DevCounters* dc, LaneCore& c, LaneCounters& lc,
+                                               double ux, double uy, double uz) {
   const double u = draw_u(p, c);
   bool proton = u < (double)c.Z / (double)c.A;
   const int Ad = c.A - 1;
@@ -362,15 +370,15 @@ __device__ __forceinline__ void photodisintegrate(const KParams& p, const DevSta
       st.x[slot] = c.x[0];
       st.y[slot] = c.x[1];
       st.z[slot] = c.x[2];
-      st.ux[slot] = u_dir[0];
-      st.uy[slot] = u_dir[1];
-      st.uz[slot] = u_dir[2];
+      st.ux[slot] = ux;
+      st.uy[slot] = uy;
+      st.uz[slot] = uz;
       st.x0[slot] = c.x[0];
       st.y0[slot] = c.x[1];
       st.z0[slot] = c.x[2];
-      st.ux0[slot] = u_dir[0];
-      st.uy0[slot] = u_dir[1];
-      st.uz0[slot] = u_dir[2];
+      st.ux0[slot] = ux;
+      st.uy0[slot] = uy;
+      st.uz0[slot] = uz;
       st.E[slot] = En;
       st.E0[slot] = En;
       st.s[slot] = c.s;
@@ -394,6 +402,9 @@ __device__ __forceinline__ void photodisintegrate(const KParams& p, const DevSta
       st.lens_pixel[slot] = 0xffffffffu;
       st.n_acc[slot] = 0;
       st.n_rej[slot] = 0;
+      // the nucleon joins the next round (its slot is fully written first)
+      const unsigned long long qo = atomicAdd(&dc->q_out, 1ull);
+      if (qo < p.capacity) p.queue_out[qo] = (uint32_t)slot;
       lc.sec += 1;
     } else {
       atomicAdd(&dc->overflow, 1ull);
@@ -436,80 +447,54 @@ __device__ __forceinline__ bool segment_enters(const double a[3], const double b
   return m2 <= R2;
 }
 
-// Interaction modules + break conditions after an accepted step of length h.
-// `x_old` is the position before the step; `u_dir` the direction after it.
-template <class Lane, bool MIXED>
-__device__ __forceinline__ void modules_after_step(const KParams& p, const DevState& st,
-                                                   DevCounters* dc, Lane& c, LaneCounters& lc,
-                                                   double h, const double x_old[3],
-                                                   const double u_dir[3]) {
-  const bool pion_on = (p.flags & CRP_PION) != 0;
-  const bool pd_on = (p.flags & CRP_PHOTODIS) != 0;
-  // continuous losses
-  if (p.flags & (CRP_PAIR | CRP_ADIABATIC)) {
-    if (MIXED) {
-      float beta = 0.f;
-      if (p.flags & CRP_PAIR) {
-        const float g = (float)c.E / ((float)c.A * (float)MP_C2_EV);
-        const float bp = table_f32(p, p.t_beta, __logf(g));
-        beta = bp * (float)(c.Z * c.Z) / (float)c.A;
-      }
-      if (p.flags & CRP_ADIABATIC) beta += (float)p.beta_ad;
-      c.E = c.E * (1.0 - (double)(beta * (float)h));
-    } else {
-      double beta = 0.0;
-      if (p.flags & CRP_PAIR) {
-        const double bp = table_fp64(p, p.t_beta, log(c.E / ((double)c.A * MP_C2_EV)));
-        beta = bp * (double)(c.Z * c.Z) / (double)c.A;
-      }
-      if (p.flags & CRP_ADIABATIC) beta = beta + p.beta_ad;
-      c.E = c.E * (1.0 - beta * h);
-    }
-  }
-  // stochastic interactions
-  if (pion_on || pd_on) {
-    if (pion_on) c.d_pion = c.d_pion - h;
-    if (pd_on) c.d_pd = c.d_pd - h;
-    if (pion_on && c.d_pion <= 0.0) {
-      c.E = c.E - 0.2 * c.E / (double)c.A;
-      c.n_pion += 1;
-      c.events += 1;
-      lc.pion += 1;
-      reset_states(p, c);
-    } else if (pd_on && c.d_pd <= 0.0) {
-      photodisintegrate(p, st, dc, c, lc, u_dir);
-    }
-  }
-  // break conditions
-  if ((p.flags & CRP_EMIN) && c.E < p.e_min) {
-    c.status = CRP_BELOW_EMIN;
-  } else if (c.s >= c.s_max) {
-    c.status = CRP_MAX_LENGTH;
-  } else if ((p.flags & CRP_OBSERVER) && segment_enters(x_old, c.x, p.obs_c, p.obs_r)) {
-    c.status = CRP_DETECTED;
-    lc.detected += 1;
-  } else if (p.flags & CRP_BORDER) {
-    const double dx = c.x[0] - p.border_c[0], dy = c.x[1] - p.border_c[1],
-                 dz = c.x[2] - p.border_c[2];
-    if (dx * dx + dy * dy + dz * dz >= p.border_r * p.border_r) c.status = CRP_AT_BORDER;
-  }
-  if (c.status == CRP_ACTIVE && p.max_steps && c.n_acc >= p.max_steps) c.status = CRP_BUDGET;
+// Pion event (one nucleon loses the inelasticity 0.2 of its energy), then
+// reset of all interaction states.
+__device__ __forceinline__ void pion_event(const KParams& p, LaneCore& c, LaneCounters& lc) {
+  c.E = c.E - 0.2 * c.E / (double)c.A;
+  c.n_pion += 1;
+  c.events += 1;
+  lc.pion += 1;
+  reset_states(p, c);
 }
 
+// Cash-Karp tableau in constant memory (uniform across a warp whose lanes
+// all run the same stage), for the stage loop.
+__constant__ double c_a64[6][6] = {
+    {0, 0, 0, 0, 0, 0},
+    {ck::a21, 0, 0, 0, 0, 0},
+    {ck::a31, ck::a32, 0, 0, 0, 0},
+    {ck::a41, ck::a42, ck::a43, 0, 0, 0},
+    {ck::a51, ck::a52, ck::a53, ck::a54, 0, 0},
+    {ck::a61, ck::a62, ck::a63, ck::a64, ck::a65, 0}};
+__constant__ float c_a32[6][6] = {
+    {0, 0, 0, 0, 0, 0},
+    {(float)ck::a21, 0, 0, 0, 0, 0},
+    {(float)ck::a31, (float)ck::a32, 0, 0, 0, 0},
+    {(float)ck::a41, (float)ck::a42, (float)ck::a43, 0, 0, 0},
+    {(float)ck::a51, (float)ck::a52, (float)ck::a53, (float)ck::a54, 0, 0},
+    {(float)ck::a61, (float)ck::a62, (float)ck::a63, (float)ck::a64, (float)ck::a65, 0}};
+
 // ---------------------------------------------------------------------------
-// FP64 policy: one module cycle.
+// FP64 policy.  begin_step / trial / finish_step split the module cycle so
+// that a warp advances one Cash-Karp trial per iteration; the arithmetic and
+// its order are those of the reference formulation.
 // ---------------------------------------------------------------------------
 struct PolicyFP64 {
-  using Lane = LaneFP64;
-  static constexpr bool kMixed = false;
+  using Real = double;
+  struct Lane : LaneCore {
+    double u[3];
+    double cap_s, kappa, eps;
+    double y5[6];
+  };
 
-  __device__ __forceinline__ static void load(const DevState& st, uint64_t i, Lane& c) {
+  __device__ __forceinline__ static void load(const KParams&, const DevState& st, uint64_t i,
+                                              Lane& c) {
     load_core(st, i, c);
     c.u[0] = st.ux[i];
     c.u[1] = st.uy[i];
     c.u[2] = st.uz[i];
   }
-  __device__ __forceinline__ static void store(const DevState& st, const Lane& c) {
+  __device__ __forceinline__ static void store(const DevState& st, Lane& c) {
     store_core(st, c);
     st.ux[c.slot] = c.u[0];
     st.uy[c.slot] = c.u[1];
@@ -517,74 +502,105 @@ struct PolicyFP64 {
   }
 
   template <class NodeT>
-  __device__ __forceinline__ static void cycle(const KParams& p, const DevState& st,
-                                               DevCounters* dc, Lane& c, LaneCounters& lc) {
-    using namespace ck;
+  __device__ __forceinline__ static void force(const KParams& p, const double x[3],
+                                               const double u[3], double kappa, double k[3]) {
+    double B[3];
+    field_fp64<NodeT>(p, x, B);
+    const double cx = u[1] * B[2] - u[2] * B[1];
+    const double cy = u[2] * B[0] - u[0] * B[2];
+    const double cz = u[0] * B[1] - u[1] * B[0];
+    k[0] = kappa * cx;
+    k[1] = kappa * cy;
+    k[2] = kappa * cz;
+  }
+
+  template <class NodeT>
+  __device__ __forceinline__ static void begin_step(const KParams& p, Lane& c,
+                                                    StageStore<double>& S, LaneCounters& lc) {
     const bool pion_on = (p.flags & CRP_PION) != 0;
     const bool pd_on = (p.flags & CRP_PHOTODIS) != 0;
     if ((pion_on || pd_on) && !(c.flags & CF_STATES_DRAWN)) reset_states(p, c);
     double h = c.h;
     if (h > p.h_max) h = p.h_max;
-    const double cap_s = c.s_max - c.s;
-    if (cap_s < h) h = cap_s;
+    c.cap_s = c.s_max - c.s;
+    if (c.cap_s < h) h = c.cap_s;
     if (pion_on && c.d_pion < h) h = c.d_pion;
     if (pd_on && c.d_pd < h) h = c.d_pd;
-    const double kappa = (double)(c.q * c.Z) * p.curv_k / c.E;
-    const double y[6] = {c.x[0], c.x[1], c.x[2], c.u[0], c.u[1], c.u[2]};
-    double k1[6], k2[6], k3[6], k4[6], k5[6], k6[6], yt[6], y5[6];
-    rhs_fp64<NodeT>(p, y, kappa, k1);
-    lc.rhs += 1;
-    double eps;
-    int rejections = 0;
-    for (;;) {
-#pragma unroll
-      for (int i = 0; i < 6; ++i) yt[i] = y[i] + h * (a21 * k1[i]);
-      rhs_fp64<NodeT>(p, yt, kappa, k2);
-#pragma unroll
-      for (int i = 0; i < 6; ++i) yt[i] = y[i] + h * (a31 * k1[i] + a32 * k2[i]);
-      rhs_fp64<NodeT>(p, yt, kappa, k3);
-#pragma unroll
-      for (int i = 0; i < 6; ++i) yt[i] = y[i] + h * (a41 * k1[i] + a42 * k2[i] + a43 * k3[i]);
-      rhs_fp64<NodeT>(p, yt, kappa, k4);
-#pragma unroll
-      for (int i = 0; i < 6; ++i)
-        yt[i] = y[i] + h * (a51 * k1[i] + a52 * k2[i] + a53 * k3[i] + a54 * k4[i]);
-      rhs_fp64<NodeT>(p, yt, kappa, k5);
-#pragma unroll
-      for (int i = 0; i < 6; ++i)
-        yt[i] = y[i] + h * (a61 * k1[i] + a62 * k2[i] + a63 * k3[i] + a64 * k4[i] + a65 * k5[i]);
-      rhs_fp64<NodeT>(p, yt, kappa, k6);
-      lc.rhs += 5;
-#pragma unroll
-      for (int i = 0; i < 6; ++i)
-        y5[i] = y[i] + h * (w1 * k1[i] + w3 * k3[i] + w4 * k4[i] + w6 * k6[i]);
-      double err[3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-        err[i] = h * (d1 * k1[3 + i] + d3 * k3[3 + i] + d4 * k4[3 + i] + d5 * k5[3 + i] +
-                      d6 * k6[3 + i]);
-      eps = sqrt(err[0] * err[0] + err[1] * err[1] + err[2] * err[2]) / p.tol;
-      if (eps <= 1.0 || h <= p.h_min || rejections >= 64) break;
-      double fac = 0.95 / sqrt(sqrt(eps));
-      if (fac < 0.1) fac = 0.1;
-      double hn = h * fac;
-      if (hn < p.h_min) hn = p.h_min;
-      h = hn;
-      rejections += 1;
-      c.n_rej += 1;
-      lc.rej += 1;
+    c.h = h;  // trial step of this step
+    c.kappa = (double)(c.q * c.Z) * p.curv_k / c.E;
+    double k[3];
+    force<NodeT>(p, c.x, c.u, c.kappa, k);
+    for (int i = 0; i < 3; ++i) {
+      S.u(0, i) = c.u[i];
+      S.k(0, i) = k[i];
     }
+    c.rejections = 0;
+    lc.rhs += 1;
+  }
+
+  // One Cash-Karp trial with step c.h.  Returns true when accepted.
+  template <class NodeT>
+  __device__ __forceinline__ static bool trial(const KParams& p, Lane& c, StageStore<double>& S,
+                                               LaneCounters& lc) {
+    using namespace ck;
+    const double h = c.h;
+#pragma unroll 1
+    for (int j = 1; j < 6; ++j) {
+      double xs[3], us[3];
+      for (int i = 0; i < 3; ++i) {
+        double sx = c_a64[j][0] * S.u(0, i);
+        double su = c_a64[j][0] * S.k(0, i);
+        for (int m = 1; m < j; ++m) {
+          sx = sx + c_a64[j][m] * S.u(m, i);
+          su = su + c_a64[j][m] * S.k(m, i);
+        }
+        xs[i] = c.x[i] + h * sx;
+        us[i] = c.u[i] + h * su;
+      }
+      double k[3];
+      force<NodeT>(p, xs, us, c.kappa, k);
+      for (int i = 0; i < 3; ++i) {
+        S.u(j, i) = us[i];
+        S.k(j, i) = k[i];
+      }
+    }
+    lc.rhs += 5;
+    double err[3];
+    for (int i = 0; i < 3; ++i) {
+      c.y5[i] = c.x[i] + h * (w1 * S.u(0, i) + w3 * S.u(2, i) + w4 * S.u(3, i) + w6 * S.u(5, i));
+      c.y5[3 + i] =
+          c.u[i] + h * (w1 * S.k(0, i) + w3 * S.k(2, i) + w4 * S.k(3, i) + w6 * S.k(5, i));
+      err[i] = h * (d1 * S.k(0, i) + d3 * S.k(2, i) + d4 * S.k(3, i) + d5 * S.k(4, i) +
+                    d6 * S.k(5, i));
+    }
+    c.eps = sqrt(err[0] * err[0] + err[1] * err[1] + err[2] * err[2]) / p.tol;
+    if (c.eps <= 1.0 || h <= p.h_min || c.rejections >= 64) return true;
+    double fac = 0.95 / sqrt(sqrt(c.eps));
+    if (fac < 0.1) fac = 0.1;
+    double hn = h * fac;
+    if (hn < p.h_min) hn = p.h_min;
+    c.h = hn;
+    c.rejections += 1;
+    c.n_rej += 1;
+    lc.rej += 1;
+    return false;
+  }
+
+  __device__ __forceinline__ static void finish_step(const KParams& p, const DevState& st,
+                                                     DevCounters* dc, Lane& c,
+                                                     LaneCounters& lc) {
+    const double h = c.h;
     const double x_old[3] = {c.x[0], c.x[1], c.x[2]};
-    c.x[0] = y5[0];
-    c.x[1] = y5[1];
-    c.x[2] = y5[2];
-    const double un = sqrt(y5[3] * y5[3] + y5[4] * y5[4] + y5[5] * y5[5]);
+    c.x[0] = c.y5[0];
+    c.x[1] = c.y5[1];
+    c.x[2] = c.y5[2];
+    const double un = sqrt(c.y5[3] * c.y5[3] + c.y5[4] * c.y5[4] + c.y5[5] * c.y5[5]);
     const double inv = 1.0 / un;
-    c.u[0] = y5[3] * inv;
-    c.u[1] = y5[4] * inv;
-    c.u[2] = y5[5] * inv;
-    c.s = (h == cap_s) ? c.s_max : c.s + h;
-    double grow = eps == 0.0 ? 5.0 : 0.95 / sqrt(sqrt(eps));
+    c.u[0] = c.y5[3] * inv;
+    c.u[1] = c.y5[4] * inv;
+    c.u[2] = c.y5[5] * inv;
+    c.s = (h == c.cap_s) ? c.s_max : c.s + h;
+    double grow = c.eps == 0.0 ? 5.0 : 0.95 / sqrt(sqrt(c.eps));
     if (grow > 5.0) grow = 5.0;
     double h_next = h * grow;
     if (h_next < p.h_min) h_next = p.h_min;
@@ -593,19 +609,71 @@ struct PolicyFP64 {
     c.n_acc += 1;
     lc.acc += 1;
     lc.pending_acc += 1;
-    modules_after_step<Lane, false>(p, st, dc, c, lc, h, x_old, c.u);
+    // continuous losses
+    if (p.flags & (CRP_PAIR | CRP_ADIABATIC)) {
+      double beta = 0.0;
+      if (p.flags & CRP_PAIR) {
+        const double bp = table_fp64(p, p.t_beta, series_log(c.E / ((double)c.A * MP_C2_EV)));
+        beta = bp * (double)(c.Z * c.Z) / (double)c.A;
+      }
+      if (p.flags & CRP_ADIABATIC) beta = beta + p.beta_ad;
+      c.E = c.E * (1.0 - beta * h);
+    }
+    // stochastic interactions
+    const bool pion_on = (p.flags & CRP_PION) != 0;
+    const bool pd_on = (p.flags & CRP_PHOTODIS) != 0;
+    if (pion_on || pd_on) {
+      if (pion_on) c.d_pion = c.d_pion - h;
+      if (pd_on) c.d_pd = c.d_pd - h;
+      if (pion_on && c.d_pion <= 0.0) {
+        pion_event(p, c, lc);
+      } else if (pd_on && c.d_pd <= 0.0) {
+        photodisintegrate(p, st, dc, c, lc, c.u[0], c.u[1], c.u[2]);
+      }
+    }
+    // break conditions
+    if ((p.flags & CRP_EMIN) && c.E < p.e_min) {
+      c.status = CRP_BELOW_EMIN;
+    } else if (c.s >= c.s_max) {
+      c.status = CRP_MAX_LENGTH;
+    } else if ((p.flags & CRP_OBSERVER) && segment_enters(x_old, c.x, p.obs_c, p.obs_r)) {
+      c.status = CRP_DETECTED;
+      lc.detected += 1;
+    } else if (p.flags & CRP_BORDER) {
+      const double dx = c.x[0] - p.border_c[0], dy = c.x[1] - p.border_c[1],
+                   dz = c.x[2] - p.border_c[2];
+      if (dx * dx + dy * dy + dz * dz >= p.border_r * p.border_r) c.status = CRP_AT_BORDER;
+    }
+    if (c.status == CRP_ACTIVE && c.n_acc >= p.max_steps) c.status = CRP_BUDGET;
   }
+
+  // Mid-step suspension: keep the current trial step (a resumed step
+  // restarts from it with the same caps and the same first stage).
+  __device__ __forceinline__ static void suspend(Lane&) {}
 };
 
 // ---------------------------------------------------------------------------
-// Mixed policy: binary32 field / force / stages relative to the current cell.
+// Mixed policy: binary32 field, force and stages relative to the current
+// grid cell; binary64 position, trajectory length, energy, free paths and
+// error norm.
 // ---------------------------------------------------------------------------
-struct PolicyMixed {
-  using Lane = LaneMixed;
-  static constexpr bool kMixed = true;
+enum : int { CAP_NONE = 0, CAP_S = 1, CAP_PION = 2, CAP_PD = 3 };
 
-  // Cell index and in-cell fraction of the binary64 position; also the
-  // binary32 offset from the galactic centre.
+struct PolicyMixed {
+  using Real = float;
+  struct Lane : LaneCore {
+    float u[3];
+    int cell[3];    // grid cell of the current position
+    float frac[3];  // in-cell fraction (grid units)
+    float gal[3];   // position relative to the galactic centre
+    float hf;      // trial step of the current step
+    float hn;      // proposed next step, in [h_min, h_max]
+    float E_f;     // binary32 copy of the energy
+    float kap, d_obs, d_bord, err2, dx[3], u5[3];
+    int cap, since_rebase;
+  };
+
+  // Cell and fraction from the binary64 position (exact rebase).
   __device__ __forceinline__ static void rebase(const KParams& p, Lane& c) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -618,24 +686,46 @@ struct PolicyMixed {
 #pragma unroll
       for (int d = 0; d < 3; ++d) c.gal[d] = (float)(c.x[d] - p.gal_c[d]);
     }
+    c.since_rebase = 0;
   }
 
-  __device__ __forceinline__ static void load(const DevState& st, uint64_t i, Lane& c,
-                                              const KParams& p) {
+  // Conservative distances to the observer and border spheres (binary64
+  // once; then lowered by each step's length, so the exact binary64 test
+  // runs only when a sphere can be reached in the coming step).
+  __device__ __forceinline__ static void bounds(const KParams& p, Lane& c) {
+    if (p.flags & CRP_OBSERVER) {
+      const double a = c.x[0] - p.obs_c[0], b = c.x[1] - p.obs_c[1], d = c.x[2] - p.obs_c[2];
+      const double r = sqrt(a * a + b * b + d * d);
+      c.d_obs = (float)((r - p.obs_r) * (1.0 - 1e-6));
+    }
+    if (p.flags & CRP_BORDER) {
+      const double a = c.x[0] - p.border_c[0], b = c.x[1] - p.border_c[1],
+                   d = c.x[2] - p.border_c[2];
+      const double r = sqrt(a * a + b * b + d * d);
+      c.d_bord = (float)((p.border_r - r) * (1.0 - 1e-6));
+    }
+  }
+
+  __device__ __forceinline__ static void load(const KParams& p, const DevState& st, uint64_t i,
+                                              Lane& c) {
     load_core(st, i, c);
     c.u[0] = (float)st.ux[i];
     c.u[1] = (float)st.uy[i];
     c.u[2] = (float)st.uz[i];
+    c.hn = fminf(fmaxf((float)c.h, p.h_min_f), p.h_max_f);
+    c.E_f = (float)c.E;
     rebase(p, c);
+    bounds(p, c);
   }
-  __device__ __forceinline__ static void store(const DevState& st, const Lane& c) {
+  __device__ __forceinline__ static void store(const DevState& st, Lane& c) {
+    c.h = (double)c.hn;
     store_core(st, c);
     st.ux[c.slot] = (double)c.u[0];
     st.uy[c.slot] = (double)c.u[1];
     st.uz[c.slot] = (double)c.u[2];
   }
 
-  // Field at the current position plus offset o (length unit).
+  // Field at the current position plus offset (ox, oy, oz) (length unit).
   template <class NodeT>
   __device__ __forceinline__ static float3 field(const KParams& p, const Lane& c, float ox,
                                                  float oy, float oz) {
@@ -682,169 +772,238 @@ struct PolicyMixed {
     return B;
   }
 
-  __device__ __forceinline__ static float3 force(float kap, float ux, float uy, float uz,
-                                                 float3 B) {
-    return make_float3(kap * (uy * B.z - uz * B.y), kap * (uz * B.x - ux * B.z),
-                       kap * (ux * B.y - uy * B.x));
-  }
-
   template <class NodeT>
-  __device__ __forceinline__ static void cycle(const KParams& p, const DevState& st,
-                                               DevCounters* dc, Lane& c, LaneCounters& lc) {
+  __device__ __forceinline__ static void begin_step(const KParams& p, Lane& c,
+                                                    StageStore<float>& S, LaneCounters& lc) {
     const bool pion_on = (p.flags & CRP_PION) != 0;
     const bool pd_on = (p.flags & CRP_PHOTODIS) != 0;
     if ((pion_on || pd_on) && !(c.flags & CF_STATES_DRAWN)) reset_states(p, c);
-    double h = c.h;
-    if (h > p.h_max) h = p.h_max;
-    const double cap_s = c.s_max - c.s;
-    if (cap_s < h) h = cap_s;
-    if (pion_on && c.d_pion < h) h = c.d_pion;
-    if (pd_on && c.d_pd < h) h = c.d_pd;
-    const float kap = (float)(c.q * c.Z) * (float)p.curv_k / (float)c.E;
-    constexpr float A21 = (float)ck::a21, A31 = (float)ck::a31, A32 = (float)ck::a32;
-    constexpr float A41 = (float)ck::a41, A42 = (float)ck::a42, A43 = (float)ck::a43;
-    constexpr float A51 = (float)ck::a51, A52 = (float)ck::a52, A53 = (float)ck::a53,
-                    A54 = (float)ck::a54;
-    constexpr float A61 = (float)ck::a61, A62 = (float)ck::a62, A63 = (float)ck::a63,
-                    A64 = (float)ck::a64, A65 = (float)ck::a65;
+    c.cap = CAP_NONE;
+    double h = (double)c.hn;
+    const double rem = c.s_max - c.s;
+    if (rem < h) {
+      h = rem;
+      c.cap = CAP_S;
+    }
+    if (pion_on && c.d_pion < h) {
+      h = c.d_pion;
+      c.cap = CAP_PION;
+    }
+    if (pd_on && c.d_pd < h) {
+      h = c.d_pd;
+      c.cap = CAP_PD;
+    }
+    c.hf = c.cap == CAP_NONE ? c.hn : (float)h;
+    c.kap = (float)(c.q * c.Z) * p.curv_k_f / c.E_f;
+    const float3 B = field<NodeT>(p, c, 0.f, 0.f, 0.f);
+    S.u(0, 0) = c.u[0];
+    S.u(0, 1) = c.u[1];
+    S.u(0, 2) = c.u[2];
+    S.k(0, 0) = c.kap * (c.u[1] * B.z - c.u[2] * B.y);
+    S.k(0, 1) = c.kap * (c.u[2] * B.x - c.u[0] * B.z);
+    S.k(0, 2) = c.kap * (c.u[0] * B.y - c.u[1] * B.x);
+    c.rejections = 0;
+    lc.rhs += 1;
+  }
+
+  template <class NodeT>
+  __device__ __forceinline__ static bool trial(const KParams& p, Lane& c, StageStore<float>& S,
+                                               LaneCounters& lc) {
+    const float h = c.hf;
+#pragma unroll 1
+    for (int j = 1; j < 6; ++j) {
+      float ox = 0.f, oy = 0.f, oz = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
+      for (int m = 0; m < j; ++m) {
+        const float a = c_a32[j][m];
+        ox = fmaf(a, S.u(m, 0), ox);
+        oy = fmaf(a, S.u(m, 1), oy);
+        oz = fmaf(a, S.u(m, 2), oz);
+        sx = fmaf(a, S.k(m, 0), sx);
+        sy = fmaf(a, S.k(m, 1), sy);
+        sz = fmaf(a, S.k(m, 2), sz);
+      }
+      const float ux = fmaf(h, sx, c.u[0]), uy = fmaf(h, sy, c.u[1]), uz = fmaf(h, sz, c.u[2]);
+      const float3 B = field<NodeT>(p, c, h * ox, h * oy, h * oz);
+      S.u(j, 0) = ux;
+      S.u(j, 1) = uy;
+      S.u(j, 2) = uz;
+      S.k(j, 0) = c.kap * (uy * B.z - uz * B.y);
+      S.k(j, 1) = c.kap * (uz * B.x - ux * B.z);
+      S.k(j, 2) = c.kap * (ux * B.y - uy * B.x);
+    }
+    lc.rhs += 5;
     constexpr float W1 = (float)ck::w1, W3 = (float)ck::w3, W4 = (float)ck::w4,
                     W6 = (float)ck::w6;
     constexpr float D1 = (float)ck::d1, D3 = (float)ck::d3, D4 = (float)ck::d4,
                     D5 = (float)ck::d5, D6 = (float)ck::d6;
-    const float u1x = c.u[0], u1y = c.u[1], u1z = c.u[2];
-    const float3 k1 = force(kap, u1x, u1y, u1z, field<NodeT>(p, c, 0.f, 0.f, 0.f));
-    lc.rhs += 1;
-    float dxx, dxy, dxz, u5x, u5y, u5z;
-    double err2;
-    float e32 = 0.f;
-    int rejections = 0;
-    for (;;) {
-      const float hf = (float)h;
-      // stage 2
-      const float u2x = fmaf(hf, A21 * k1.x, u1x), u2y = fmaf(hf, A21 * k1.y, u1y),
-                  u2z = fmaf(hf, A21 * k1.z, u1z);
-      const float3 k2 =
-          force(kap, u2x, u2y, u2z, field<NodeT>(p, c, hf * A21 * u1x, hf * A21 * u1y, hf * A21 * u1z));
-      // stage 3
-      const float u3x = fmaf(hf, A31 * k1.x + A32 * k2.x, u1x),
-                  u3y = fmaf(hf, A31 * k1.y + A32 * k2.y, u1y),
-                  u3z = fmaf(hf, A31 * k1.z + A32 * k2.z, u1z);
-      const float3 k3 = force(kap, u3x, u3y, u3z,
-                              field<NodeT>(p, c, hf * (A31 * u1x + A32 * u2x),
-                                           hf * (A31 * u1y + A32 * u2y),
-                                           hf * (A31 * u1z + A32 * u2z)));
-      // stage 4
-      const float u4x = fmaf(hf, A41 * k1.x + A42 * k2.x + A43 * k3.x, u1x),
-                  u4y = fmaf(hf, A41 * k1.y + A42 * k2.y + A43 * k3.y, u1y),
-                  u4z = fmaf(hf, A41 * k1.z + A42 * k2.z + A43 * k3.z, u1z);
-      const float3 k4 = force(kap, u4x, u4y, u4z,
-                              field<NodeT>(p, c, hf * (A41 * u1x + A42 * u2x + A43 * u3x),
-                                           hf * (A41 * u1y + A42 * u2y + A43 * u3y),
-                                           hf * (A41 * u1z + A42 * u2z + A43 * u3z)));
-      // stage 5
-      const float u5sx = fmaf(hf, A51 * k1.x + A52 * k2.x + A53 * k3.x + A54 * k4.x, u1x),
-                  u5sy = fmaf(hf, A51 * k1.y + A52 * k2.y + A53 * k3.y + A54 * k4.y, u1y),
-                  u5sz = fmaf(hf, A51 * k1.z + A52 * k2.z + A53 * k3.z + A54 * k4.z, u1z);
-      const float3 k5 = force(
-          kap, u5sx, u5sy, u5sz,
-          field<NodeT>(p, c, hf * (A51 * u1x + A52 * u2x + A53 * u3x + A54 * u4x),
-                       hf * (A51 * u1y + A52 * u2y + A53 * u3y + A54 * u4y),
-                       hf * (A51 * u1z + A52 * u2z + A53 * u3z + A54 * u4z)));
-      // stage 6
-      const float u6x = fmaf(hf, A61 * k1.x + A62 * k2.x + A63 * k3.x + A64 * k4.x + A65 * k5.x, u1x),
-                  u6y = fmaf(hf, A61 * k1.y + A62 * k2.y + A63 * k3.y + A64 * k4.y + A65 * k5.y, u1y),
-                  u6z = fmaf(hf, A61 * k1.z + A62 * k2.z + A63 * k3.z + A64 * k4.z + A65 * k5.z, u1z);
-      const float3 k6 = force(
-          kap, u6x, u6y, u6z,
-          field<NodeT>(p, c, hf * (A61 * u1x + A62 * u2x + A63 * u3x + A64 * u4x + A65 * u5sx),
-                       hf * (A61 * u1y + A62 * u2y + A63 * u3y + A64 * u4y + A65 * u5sy),
-                       hf * (A61 * u1z + A62 * u2z + A63 * u3z + A64 * u4z + A65 * u5sz)));
-      lc.rhs += 5;
-      dxx = hf * (W1 * u1x + W3 * u3x + W4 * u4x + W6 * u6x);
-      dxy = hf * (W1 * u1y + W3 * u3y + W4 * u4y + W6 * u6y);
-      dxz = hf * (W1 * u1z + W3 * u3z + W4 * u4z + W6 * u6z);
-      u5x = fmaf(hf, W1 * k1.x + W3 * k3.x + W4 * k4.x + W6 * k6.x, u1x);
-      u5y = fmaf(hf, W1 * k1.y + W3 * k3.y + W4 * k4.y + W6 * k6.y, u1y);
-      u5z = fmaf(hf, W1 * k1.z + W3 * k3.z + W4 * k4.z + W6 * k6.z, u1z);
-      const float ex = hf * (D1 * k1.x + D3 * k3.x + D4 * k4.x + D5 * k5.x + D6 * k6.x);
-      const float ey = hf * (D1 * k1.y + D3 * k3.y + D4 * k4.y + D5 * k5.y + D6 * k6.y);
-      const float ez = hf * (D1 * k1.z + D3 * k3.z + D4 * k4.z + D5 * k5.z + D6 * k6.z);
-      // error norm in binary64
-      const double dex = ex, dey = ey, dez = ez;
-      err2 = dex * dex + dey * dey + dez * dez;
-      if (err2 <= p.tol2 || h <= p.h_min || rejections >= 64) break;
-      e32 = (float)(err2 / p.tol2);
-      float fac = 0.95f * rsqrtf(sqrtf(sqrtf(e32)));  // 0.95 eps^(-1/4)
-      fac = fmaxf(fac, 0.1f);
-      double hn = h * (double)fac;
-      if (hn < p.h_min) hn = p.h_min;
-      h = hn;
-      rejections += 1;
-      c.n_rej += 1;
-      lc.rej += 1;
+    float e[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      c.dx[i] = h * (W1 * S.u(0, i) + W3 * S.u(2, i) + W4 * S.u(3, i) + W6 * S.u(5, i));
+      c.u5[i] = fmaf(h, W1 * S.k(0, i) + W3 * S.k(2, i) + W4 * S.k(3, i) + W6 * S.k(5, i), c.u[i]);
+      e[i] = h * (D1 * S.k(0, i) + D3 * S.k(2, i) + D4 * S.k(3, i) + D5 * S.k(4, i) +
+                  D6 * S.k(5, i));
     }
+    // Error norm: the binary32 sum of squares is within a few ulp of the
+    // binary64 one, so it decides acceptance exactly as binary64 does except
+    // in a +-1e-5 band around the tolerance, where the binary64 norm decides.
+    const float e2 = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
+    c.err2 = e2;
+    bool accept;
+    if (e2 < 0.99999f * p.tol2_f) {
+      accept = true;
+    } else if (e2 > 1.00001f * p.tol2_f) {
+      accept = false;
+    } else {
+      const double d0 = e[0], d1 = e[1], d2 = e[2];
+      accept = d0 * d0 + d1 * d1 + d2 * d2 <= p.tol2;
+    }
+    if (accept || h <= p.h_min_f || c.rejections >= 64) return true;
+    float fac = 0.95f * rsqrtf(sqrtf(sqrtf(e2 * p.inv_tol2_f)));  // 0.95 eps^(-1/4)
+    fac = fmaxf(fac, 0.1f);
+    c.hf = fmaxf(h * fac, p.h_min_f);
+    c.cap = CAP_NONE;
+    c.rejections += 1;
+    c.n_rej += 1;
+    lc.rej += 1;
+    return false;
+  }
+
+  __device__ __forceinline__ static void finish_step(const KParams& p, const DevState& st,
+                                                     DevCounters* dc, Lane& c,
+                                                     LaneCounters& lc) {
+    const float hf = c.hf;
+    const double h = (double)hf;
     const double x_old[3] = {c.x[0], c.x[1], c.x[2]};
-    c.x[0] = c.x[0] + (double)dxx;
-    c.x[1] = c.x[1] + (double)dxy;
-    c.x[2] = c.x[2] + (double)dxz;
-    const float inv = rsqrtf(u5x * u5x + u5y * u5y + u5z * u5z);
-    c.u[0] = u5x * inv;
-    c.u[1] = u5y * inv;
-    c.u[2] = u5z * inv;
-    c.s = (h == cap_s) ? c.s_max : c.s + h;
+    c.x[0] = c.x[0] + (double)c.dx[0];
+    c.x[1] = c.x[1] + (double)c.dx[1];
+    c.x[2] = c.x[2] + (double)c.dx[2];
+    const float inv = rsqrtf(c.u5[0] * c.u5[0] + c.u5[1] * c.u5[1] + c.u5[2] * c.u5[2]);
+    c.u[0] = c.u5[0] * inv;
+    c.u[1] = c.u5[1] * inv;
+    c.u[2] = c.u5[2] * inv;
+    c.s = c.cap == CAP_S ? c.s_max : c.s + h;
     float grow = 5.f;
-    if (err2 > 0.0) {
-      e32 = (float)(err2 / p.tol2);
-      grow = fminf(5.f, 0.95f * rsqrtf(sqrtf(sqrtf(e32))));
-    }
-    double h_next = h * (double)grow;
-    if (h_next < p.h_min) h_next = p.h_min;
-    if (h_next > p.h_max) h_next = p.h_max;
-    c.h = h_next;
+    if (c.err2 > 0.f) grow = fminf(5.f, 0.95f * rsqrtf(sqrtf(sqrtf(c.err2 * p.inv_tol2_f))));
+    c.hn = fminf(fmaxf(hf * grow, p.h_min_f), p.h_max_f);
     c.n_acc += 1;
     lc.acc += 1;
     lc.pending_acc += 1;
-    rebase(p, c);
-    const double u_dir[3] = {(double)c.u[0], (double)c.u[1], (double)c.u[2]};
-    modules_after_step<Lane, true>(p, st, dc, c, lc, h, x_old, u_dir);
+    // field-lookup coordinate: advance in binary32, exact rebase every 32 steps
+    if (++c.since_rebase >= 32) {
+      rebase(p, c);
+    } else {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const float r = fmaf(c.dx[d], p.f.inv_spacing_f, c.frac[d]);
+        const float fl = floorf(r);
+        c.frac[d] = r - fl;
+        c.cell[d] = wrap_int(c.cell[d] + (int)fl, (int)p.f.n[d], (int)p.f.mask[d]);
+      }
+      if (p.flags & CRP_GALACTIC) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) c.gal[d] += c.dx[d];
+      }
+    }
+    // continuous losses
+    if (p.flags & (CRP_PAIR | CRP_ADIABATIC)) {
+      float beta = 0.f;
+      if (p.flags & CRP_PAIR) {
+        const float g = c.E_f / ((float)c.A * (float)MP_C2_EV);
+        const float bp = table_f32(p, p.t_beta_f, __logf(g));
+        beta = bp * (float)(c.Z * c.Z) / (float)c.A;
+      }
+      if (p.flags & CRP_ADIABATIC) beta += p.beta_ad_f;
+      c.E = c.E * (1.0 - (double)(beta * hf));
+    }
+    // stochastic interactions
+    const bool pion_on = (p.flags & CRP_PION) != 0;
+    const bool pd_on = (p.flags & CRP_PHOTODIS) != 0;
+    if (pion_on || pd_on) {
+      if (pion_on) c.d_pion = c.cap == CAP_PION ? 0.0 : c.d_pion - h;
+      if (pd_on) c.d_pd = c.cap == CAP_PD ? 0.0 : c.d_pd - h;
+      if (pion_on && c.d_pion <= 0.0) {
+        pion_event(p, c, lc);
+      } else if (pd_on && c.d_pd <= 0.0) {
+        photodisintegrate(p, st, dc, c, lc, (double)c.u[0], (double)c.u[1], (double)c.u[2]);
+      }
+    }
+    c.E_f = (float)c.E;
+    // break conditions
+    const float reach = 1.01f * hf;
+    if ((p.flags & CRP_EMIN) && c.E < p.e_min) {
+      c.status = CRP_BELOW_EMIN;
+    } else if (c.s >= c.s_max) {
+      c.status = CRP_MAX_LENGTH;
+    } else {
+      if (p.flags & CRP_OBSERVER) {
+        c.d_obs -= reach;
+        if (c.d_obs <= 0.f) {
+          if (segment_enters(x_old, c.x, p.obs_c, p.obs_r)) {
+            c.status = CRP_DETECTED;
+            lc.detected += 1;
+          } else {
+            bounds(p, c);
+          }
+        }
+      }
+      if (c.status == CRP_ACTIVE && (p.flags & CRP_BORDER)) {
+        c.d_bord -= reach;
+        if (c.d_bord <= 0.f) {
+          const double dx = c.x[0] - p.border_c[0], dy = c.x[1] - p.border_c[1],
+                       dz = c.x[2] - p.border_c[2];
+          if (dx * dx + dy * dy + dz * dz >= p.border_r * p.border_r)
+            c.status = CRP_AT_BORDER;
+          else
+            bounds(p, c);
+        }
+      }
+    }
+    if (c.status == CRP_ACTIVE && c.n_acc >= p.max_steps) c.status = CRP_BUDGET;
   }
+
+  __device__ __forceinline__ static void suspend(Lane& c) { c.hn = c.hf; }
 };
 
 // ---------------------------------------------------------------------------
-// Persistent driver.
+// Persistent driver: lanes take candidates from the round's work queue, run
+// at most `slice` accepted steps on each (one Cash-Karp trial per loop
+// iteration for the whole warp), then requeue still-active candidates for
+// the next round and take the next one.
 // ---------------------------------------------------------------------------
-template <class Policy>
-__device__ __forceinline__ void policy_load(const DevState& st, uint64_t i,
-                                            typename Policy::Lane& c, const KParams& p);
-template <>
-__device__ __forceinline__ void policy_load<PolicyFP64>(const DevState& st, uint64_t i,
-                                                        LaneFP64& c, const KParams&) {
-  PolicyFP64::load(st, i, c);
-}
-template <>
-__device__ __forceinline__ void policy_load<PolicyMixed>(const DevState& st, uint64_t i,
-                                                         LaneMixed& c, const KParams& p) {
-  PolicyMixed::load(st, i, c, p);
-}
-
 __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
   return v;
 }
 
+template <class Policy>
+struct Bounds;
+template <>
+struct Bounds<PolicyFP64> {
+  static constexpr int kThreads = 128, kMinBlocks = 2;
+};
+template <>
+struct Bounds<PolicyMixed> {
+  static constexpr int kThreads = 256, kMinBlocks = 2;
+};
+
 template <class Policy, class NodeT>
-__global__ void __launch_bounds__(256) propagate_kernel(const KParams p, const DevState st,
-                                                        DevCounters* dc) {
+__global__ void __launch_bounds__(Bounds<Policy>::kThreads, Bounds<Policy>::kMinBlocks)
+    propagate_kernel(const KParams p, const DevState st, DevCounters* dc) {
+  using Real = typename Policy::Real;
   using Lane = typename Policy::Lane;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  StageStore<Real> S{reinterpret_cast<Real*>(smem_raw) + threadIdx.x, (int)blockDim.x};
   const int lane = threadIdx.x & 31;
   const unsigned long long t0 = globaltimer_ns();
   Lane c;
   LaneCounters lc = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-  bool has = false, exhausted = false;
+  bool has = false, exhausted = false, in_step = false;
+  uint32_t slice_steps = 0;
   int iter = 0;
   for (;;) {
-    // hand free lanes the next pool slots (one atomic per warp)
+    // hand free lanes the next queue entries (one atomic per warp)
     const bool need = !has && !exhausted;
     const unsigned m = __ballot_sync(FULL_MASK, need);
     if (m) {
@@ -854,10 +1013,13 @@ __global__ void __launch_bounds__(256) propagate_kernel(const KParams p, const D
       base = __shfl_sync(FULL_MASK, base, leader);
       if (need) {
         const unsigned long long mine = base + __popc(m & ((1u << lane) - 1u));
-        if (mine < p.hi) {
-          if (st.status[mine] == CRP_ACTIVE) {
-            policy_load<Policy>(st, mine, c, p);
+        if (mine < p.n_in) {
+          const uint32_t slot = p.queue_in[mine];
+          if (st.status[slot] == CRP_ACTIVE) {
+            Policy::load(p, st, slot, c);
             has = true;
+            in_step = false;
+            slice_steps = 0;
           }
         } else {
           exhausted = true;
@@ -866,13 +1028,26 @@ __global__ void __launch_bounds__(256) propagate_kernel(const KParams p, const D
     }
     if (__ballot_sync(FULL_MASK, has || !exhausted) == 0) break;
     if (has) {
-      Policy::template cycle<NodeT>(p, st, dc, c, lc);
-      if (c.status != CRP_ACTIVE) {
-        Policy::store(st, c);
-        has = false;
+      if (!in_step) {
+        Policy::template begin_step<NodeT>(p, c, S, lc);
+        in_step = true;
+      }
+      if (Policy::template trial<NodeT>(p, c, S, lc)) {
+        Policy::finish_step(p, st, dc, c, lc);
+        in_step = false;
+        slice_steps += 1;
+        if (c.status != CRP_ACTIVE) {
+          Policy::store(st, c);
+          has = false;
+        } else if (slice_steps >= p.slice) {
+          Policy::store(st, c);
+          const unsigned long long qo = atomicAdd(&dc->q_out, 1ull);
+          if (qo < p.capacity) p.queue_out[qo] = (uint32_t)c.slot;
+          has = false;
+        }
       }
     }
-    if ((++iter & 31) == 0 && (p.step_budget || p.deadline_ns)) {
+    if ((++iter & 63) == 0 && (p.step_budget || p.deadline_ns)) {
       const unsigned pend = __reduce_add_sync(FULL_MASK, lc.pending_acc);
       lc.pending_acc = 0;
       unsigned stop = 0;
@@ -884,13 +1059,17 @@ __global__ void __launch_bounds__(256) propagate_kernel(const KParams p, const D
       }
       stop = __shfl_sync(FULL_MASK, stop, 0);
       if (stop) {
-        if (has) Policy::store(st, c);  // still active: resumable
+        if (has) {
+          if (in_step) Policy::suspend(c);
+          Policy::store(st, c);  // still active: resumable
+        }
         break;
       }
     }
   }
   // fold lane counters into the call's totals
-  const uint64_t acc_rem = warp_sum_u64((p.step_budget || p.deadline_ns) ? lc.pending_acc : lc.acc);
+  const bool budgeted = p.step_budget || p.deadline_ns;
+  const uint64_t acc_rem = warp_sum_u64(budgeted ? lc.pending_acc : lc.acc);
   const uint64_t rej = warp_sum_u64(lc.rej), rhs = warp_sum_u64(lc.rhs);
   const uint64_t pion = warp_sum_u64(lc.pion), pd = warp_sum_u64(lc.pd);
   const uint64_t sec = warp_sum_u64(lc.sec), dropped = warp_sum_u64(lc.dropped);
@@ -898,7 +1077,7 @@ __global__ void __launch_bounds__(256) propagate_kernel(const KParams p, const D
   if (lane == 0) {
     if (acc_rem) atomicAdd(&dc->acc, (unsigned long long)acc_rem);
     if (rej) atomicAdd(&dc->rej, (unsigned long long)rej);
-    atomicAdd(&dc->rhs, (unsigned long long)rhs);
+    if (rhs) atomicAdd(&dc->rhs, (unsigned long long)rhs);
     if (pion) atomicAdd(&dc->pion, (unsigned long long)pion);
     if (pd) atomicAdd(&dc->pd, (unsigned long long)pd);
     if (sec) atomicAdd(&dc->secondaries, (unsigned long long)sec);
@@ -908,22 +1087,37 @@ __global__ void __launch_bounds__(256) propagate_kernel(const KParams p, const D
 }
 
 template <class Policy>
+size_t smem_bytes(int block) {
+  return (size_t)kStageSlots * (size_t)block * sizeof(typename Policy::Real);
+}
+
+template <class Policy>
 cudaError_t launch_policy(const KParams& kp, const DevState& st, DevCounters* dc, int grid,
                           int block, cudaStream_t s) {
-  if (kp.f.dtype == CRP_F32)
-    propagate_kernel<Policy, float4><<<grid, block, 0, s>>>(kp, st, dc);
-  else
-    propagate_kernel<Policy, DNode><<<grid, block, 0, s>>>(kp, st, dc);
+  const size_t sm = smem_bytes<Policy>(block);
+  if (kp.f.dtype == CRP_F32) {
+    auto k = propagate_kernel<Policy, float4>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k<<<grid, block, sm, s>>>(kp, st, dc);
+  } else {
+    auto k = propagate_kernel<Policy, DNode>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k<<<grid, block, sm, s>>>(kp, st, dc);
+  }
   return cudaGetLastError();
 }
 
 template <class Policy>
 cudaError_t occupancy_policy(int dtype, int block, int* bps) {
-  if (dtype == CRP_F32)
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, propagate_kernel<Policy, float4>,
-                                                         block, 0);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, propagate_kernel<Policy, DNode>,
-                                                       block, 0);
+  const size_t sm = smem_bytes<Policy>(block);
+  if (dtype == CRP_F32) {
+    auto k = propagate_kernel<Policy, float4>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k, block, sm);
+  }
+  auto k = propagate_kernel<Policy, DNode>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k, block, sm);
 }
 
 }  // namespace crp

@@ -13,4 +13,6 @@ cudaError_t occupancy_propagate_fp64(int dtype, int block, int* bps) {
   return occupancy_policy<PolicyFP64>(dtype, block, bps);
 }
 
+size_t propagate_smem_fp64(int block) { return smem_bytes<PolicyFP64>(block); }
+
 }  // namespace crp

@@ -14,4 +14,6 @@ cudaError_t occupancy_propagate_mixed(int dtype, int block, int* bps) {
   return occupancy_policy<PolicyMixed>(dtype, block, bps);
 }
 
+size_t propagate_smem_mixed(int block) { return smem_bytes<PolicyMixed>(block); }
+
 }  // namespace crp

@@ -12,7 +12,7 @@ def run_gpu(field, n, spacing, inj, *, precision=crp.FP64, dtype=crp.F64, origin
     """Propagate `inj` on the GPU; returns (records sorted by id, stats dict, status)."""
     inj = crp.host_injection(inj)
     m = len(inj["E"])
-    cap = capacity or max(64, 4 * m)
+    cap = capacity or max(64, 64 * m)
     ctx = crp.crp_context_create(0, seed, cap)
     try:
         if grid_source is not None:
