@@ -862,11 +862,14 @@ crp_status crp_propagate(crp_context* c, const crp_grid* g, const crp_modules* m
   kp.capacity = c->capacity;
 
   const int block = m->block_size ? m->block_size : (m->precision == CRP_FP64 ? 128 : 256);
+  // mixed kernels come in two register budgets: 2 or 3 resident blocks of 256
+  const int variant = (m->blocks_per_sm >= 3 || (m->block_size && m->block_size <= 128)) ? 3 : 2;
   int bps = m->blocks_per_sm;
   if (!bps) {
     cudaError_t e = m->precision == CRP_FP64
                         ? occupancy_propagate_fp64(kp.f.dtype, block, &bps)
-                        : occupancy_propagate_mixed(kp.f.dtype, block, &bps);
+                        : occupancy_propagate_mixed(kp.f.dtype, (m->flags & CRP_GALACTIC) != 0,
+                                                variant, block, &bps);
     if (e != cudaSuccess) return fail_cuda(e, "crp_propagate: occupancy query");
     if (bps < 1) bps = 1;
   }
@@ -904,7 +907,8 @@ crp_status crp_propagate(crp_context* c, const crp_grid* g, const crp_modules* m
     k_round_reset<<<1, 1, 0, s>>>(c->dc);
     cudaEventRecord(c->ev0, s);
     e = m->precision == CRP_FP64 ? launch_propagate_fp64(kp, c->st, c->dc, (int)gsz, block, s)
-                                 : launch_propagate_mixed(kp, c->st, c->dc, (int)gsz, block, s);
+                                 : launch_propagate_mixed(kp, c->st, c->dc, (int)gsz, block,
+                                                          variant, s);
     if (e != cudaSuccess) return fail_cuda(e, "crp_propagate: launch");
     cudaEventRecord(c->ev1, s);
     launches += 1;

@@ -102,9 +102,10 @@ struct KParams {
 cudaError_t launch_propagate_fp64(const KParams& kp, const DevState& st, DevCounters* dc,
                                   int grid, int block, cudaStream_t s);
 cudaError_t launch_propagate_mixed(const KParams& kp, const DevState& st, DevCounters* dc,
-                                   int grid, int block, cudaStream_t s);
+                                   int grid, int block, int variant, cudaStream_t s);
 cudaError_t occupancy_propagate_fp64(int dtype, int block, int* blocks_per_sm);
-cudaError_t occupancy_propagate_mixed(int dtype, int block, int* blocks_per_sm);
+cudaError_t occupancy_propagate_mixed(int dtype, int galactic, int variant, int block,
+                                      int* blocks_per_sm);
 // Dynamic shared memory of one propagate block (per-thread stage storage).
 size_t propagate_smem_fp64(int block);
 size_t propagate_smem_mixed(int block);

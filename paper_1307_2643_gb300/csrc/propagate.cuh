@@ -32,6 +32,8 @@
 
 #include <math.h>
 
+#include <type_traits>
+
 #include "crp_internal.cuh"
 #include "device_common.cuh"
 
@@ -241,90 +243,23 @@ __device__ __forceinline__ float table_f32(const KParams& p, const float* tab, f
 }
 
 // ---------------------------------------------------------------------------
-// Per-lane candidate state and per-lane counters.
+// Candidate state as the rare paths (interaction draws, pion production,
+// photodisintegration) see it.  These run on the candidate's slot in global
+// memory, out of line, so the hot lane state below stays in registers.
 // ---------------------------------------------------------------------------
-struct LaneCore {
-  uint64_t id;
-  uint64_t slot;
+struct EvCore {
+  uint64_t id, slot;
   double x[3];
-  double E, s, s_max, h, d_pion, d_pd;
-  int A, Z, q, status;
+  double E, s, s_max, d_pion, d_pd;
+  int A, Z, q;
   uint32_t draws, events, n_pion, n_pd, n_dropped, flags;
-  uint64_t n_acc, n_rej;
-  int rejections;  // rejected trials of the current step
 };
 
-struct LaneCounters {
-  uint64_t acc, rej, rhs, pion, pd, sec, dropped, detected;
-  uint32_t pending_acc;
+struct EvCounts {
+  uint32_t pion, pd, sec, dropped;
 };
 
-__device__ __forceinline__ void load_core(const DevState& st, uint64_t i, LaneCore& c) {
-  c.slot = i;
-  c.id = st.id[i];
-  c.x[0] = st.x[i];
-  c.x[1] = st.y[i];
-  c.x[2] = st.z[i];
-  c.E = st.E[i];
-  c.s = st.s[i];
-  c.s_max = st.s_max[i];
-  c.h = st.h[i];
-  c.d_pion = st.d_pion[i];
-  c.d_pd = st.d_pd[i];
-  c.A = st.A[i];
-  c.Z = st.Z[i];
-  c.q = st.q[i];
-  c.status = st.status[i];
-  c.draws = st.draws[i];
-  c.events = st.events[i];
-  c.n_pion = st.n_pion[i];
-  c.n_pd = st.n_pd[i];
-  c.n_dropped = st.n_dropped[i];
-  c.flags = st.flags[i];
-  c.n_acc = st.n_acc[i];
-  c.n_rej = st.n_rej[i];
-  c.rejections = 0;
-}
-
-__device__ __forceinline__ void store_core(const DevState& st, const LaneCore& c) {
-  const uint64_t i = c.slot;
-  st.x[i] = c.x[0];
-  st.y[i] = c.x[1];
-  st.z[i] = c.x[2];
-  st.E[i] = c.E;
-  st.s[i] = c.s;
-  st.h[i] = c.h;
-  st.d_pion[i] = c.d_pion;
-  st.d_pd[i] = c.d_pd;
-  st.A[i] = c.A;
-  st.Z[i] = c.Z;
-  st.status[i] = c.status;
-  st.draws[i] = c.draws;
-  st.events[i] = c.events;
-  st.n_pion[i] = c.n_pion;
-  st.n_pd[i] = c.n_pd;
-  st.n_dropped[i] = c.n_dropped;
-  st.flags[i] = c.flags;
-  st.n_acc[i] = c.n_acc;
-  st.n_rej[i] = c.n_rej;
-}
-
-// Per-thread stage storage in shared memory: slot k of this thread lives at
-// base[k * stride], so a warp touching one slot hits 32 consecutive words.
-// Slots 0..17: stage directions U[j][c]; 18..35: stage forces K[j][c].
-template <class T>
-struct StageStore {
-  T* base;
-  int stride;
-  __device__ __forceinline__ T& u(int j, int c) { return base[(j * 3 + c) * stride]; }
-  __device__ __forceinline__ T& k(int j, int c) { return base[(18 + j * 3 + c) * stride]; }
-};
-constexpr int kStageSlots = 36;
-
-// ---------------------------------------------------------------------------
-// Stochastic interactions (binary64 on both policies): draws, resets, events.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ double draw_u(const KParams& p, LaneCore& c) {
+__device__ __forceinline__ double draw_u(const KParams& p, EvCore& c) {
   const Philox4 w = draw4(p.seed, TAG_INTERACTION, c.id, c.draws);
   c.draws += 1;
   return u01_open(w.v0, w.v1);
@@ -332,7 +267,7 @@ __device__ __forceinline__ double draw_u(const KParams& p, LaneCore& c) {
 
 // Remaining free path d = -ln(u) / R(E) per interaction, in module order
 // [pion production, photodisintegration], at the current energy.
-__device__ __forceinline__ void reset_states(const KParams& p, LaneCore& c) {
+__device__ __forceinline__ void reset_states(const KParams& p, EvCore& c) {
   const double lng = series_log(c.E / ((double)c.A * MP_C2_EV));
   if (p.flags & CRP_PION) {
     const double u = draw_u(p, c);
@@ -347,13 +282,22 @@ __device__ __forceinline__ void reset_states(const KParams& p, LaneCore& c) {
   c.flags |= CF_STATES_DRAWN;
 }
 
+// Pion event: one nucleon loses the inelasticity 0.2 of its energy.
+__device__ __forceinline__ void pion_event(const KParams& p, EvCore& c, EvCounts& n) {
+  c.E = c.E - 0.2 * c.E / (double)c.A;
+  c.n_pion += 1;
+  c.events += 1;
+  n.pion += 1;
+  reset_states(p, c);
+}
+
 // Single-nucleon emission: proton with probability Z/A (kept away from
 // Z' = 0 or N' = 0 daughters with A' >= 2); the nucleon carries E/A, the
 // daughter E (A-1)/A; the nucleon is appended to the pool, and to the next
 // round's work queue, when E/A >= e_min.
 __device__ __forceinline__ void photodisintegrate(const KParams& p, const DevState& st,
-                                               DevCounters* dc, LaneCore& c, LaneCounters& lc,
-                                               double ux, double uy, double uz) {
+                                                  DevCounters* dc, EvCore& c, EvCounts& n,
+                                                  double ux, double uy, double uz) {
   const double u = draw_u(p, c);
   bool proton = u < (double)c.Z / (double)c.A;
   const int Ad = c.A - 1;
@@ -364,8 +308,7 @@ __device__ __forceinline__ void photodisintegrate(const KParams& p, const DevSta
   if (!(p.flags & CRP_EMIN) || En >= p.e_min) {
     const unsigned long long slot = atomicAdd(&dc->tail, 1ull);
     if (slot < p.capacity) {
-      const uint64_t cid = lineage_id(c.id, c.events);
-      st.id[slot] = cid;
+      st.id[slot] = lineage_id(c.id, c.events);
       st.parent[slot] = c.id;
       st.x[slot] = c.x[0];
       st.y[slot] = c.x[1];
@@ -405,22 +348,72 @@ __device__ __forceinline__ void photodisintegrate(const KParams& p, const DevSta
       // the nucleon joins the next round (its slot is fully written first)
       const unsigned long long qo = atomicAdd(&dc->q_out, 1ull);
       if (qo < p.capacity) p.queue_out[qo] = (uint32_t)slot;
-      lc.sec += 1;
+      n.sec += 1;
     } else {
       atomicAdd(&dc->overflow, 1ull);
       atomicOr(&dc->error_word, ERR_QUEUE_FULL);
     }
   } else {
     c.n_dropped += 1;
-    lc.dropped += 1;
+    n.dropped += 1;
   }
   c.A = Ad;
   c.Z = c.Z - (proton ? 1 : 0);
   c.E = Ed;
   c.n_pd += 1;
   c.events += 1;
-  lc.pd += 1;
+  n.pd += 1;
   reset_states(p, c);
+}
+
+enum : int { EV_NONE = 0, EV_PION = 1, EV_PD = 2, EV_DRAW = 3 };
+
+// Run one rare path on the slot: first free-path draw (EV_DRAW), a pion
+// event or a photodisintegration event.
+static __device__ __noinline__ void slot_event(const KParams& p, const DevState& st, DevCounters* dc,
+                                        uint64_t i, int kind) {
+  EvCore c;
+  c.slot = i;
+  c.id = st.id[i];
+  c.x[0] = st.x[i];
+  c.x[1] = st.y[i];
+  c.x[2] = st.z[i];
+  c.E = st.E[i];
+  c.s = st.s[i];
+  c.s_max = st.s_max[i];
+  c.d_pion = st.d_pion[i];
+  c.d_pd = st.d_pd[i];
+  c.A = st.A[i];
+  c.Z = st.Z[i];
+  c.q = st.q[i];
+  c.draws = st.draws[i];
+  c.events = st.events[i];
+  c.n_pion = st.n_pion[i];
+  c.n_pd = st.n_pd[i];
+  c.n_dropped = st.n_dropped[i];
+  c.flags = st.flags[i];
+  EvCounts n = {0, 0, 0, 0};
+  if (kind == EV_PION)
+    pion_event(p, c, n);
+  else if (kind == EV_PD)
+    photodisintegrate(p, st, dc, c, n, st.ux[i], st.uy[i], st.uz[i]);
+  else
+    reset_states(p, c);
+  st.E[i] = c.E;
+  st.A[i] = c.A;
+  st.Z[i] = c.Z;
+  st.d_pion[i] = c.d_pion;
+  st.d_pd[i] = c.d_pd;
+  st.draws[i] = c.draws;
+  st.events[i] = c.events;
+  st.n_pion[i] = c.n_pion;
+  st.n_pd[i] = c.n_pd;
+  st.n_dropped[i] = c.n_dropped;
+  st.flags[i] = c.flags;
+  if (n.pion) atomicAdd(&dc->pion, (unsigned long long)n.pion);
+  if (n.pd) atomicAdd(&dc->pd, (unsigned long long)n.pd);
+  if (n.sec) atomicAdd(&dc->secondaries, (unsigned long long)n.sec);
+  if (n.dropped) atomicAdd(&dc->dropped, (unsigned long long)n.dropped);
 }
 
 // Does the segment a -> b enter the sphere (centre cen, radius R) from outside?
@@ -447,26 +440,112 @@ __device__ __forceinline__ bool segment_enters(const double a[3], const double b
   return m2 <= R2;
 }
 
-// Pion event (one nucleon loses the inelasticity 0.2 of its energy), then
-// reset of all interaction states.
-__device__ __forceinline__ void pion_event(const KParams& p, LaneCore& c, LaneCounters& lc) {
-  c.E = c.E - 0.2 * c.E / (double)c.A;
-  c.n_pion += 1;
-  c.events += 1;
-  lc.pion += 1;
-  reset_states(p, c);
+// ---------------------------------------------------------------------------
+// Hot per-lane state.
+// ---------------------------------------------------------------------------
+struct LaneCore {
+  uint32_t slot;
+  int A, Z, q, status;
+  double x[3];
+  double E, s, s_max, h, d_pion, d_pd;
+  uint32_t dacc, drej;  // accepted steps / rejected trials since the last store
+  uint32_t budget;      // accepted steps left before CRP_BUDGET
+  int rejections;       // rejected trials of the current step
+  bool crossed;         // this step's segment entered the observer sphere
+};
+
+struct LaneCounters {
+  uint32_t acc, rej, detected, pending_acc;
+};
+
+__device__ __forceinline__ void load_core(const KParams& p, const DevState& st, uint32_t i,
+                                          LaneCore& c) {
+  c.slot = i;
+  c.x[0] = st.x[i];
+  c.x[1] = st.y[i];
+  c.x[2] = st.z[i];
+  c.E = st.E[i];
+  c.s = st.s[i];
+  c.s_max = st.s_max[i];
+  c.h = st.h[i];
+  c.d_pion = st.d_pion[i];
+  c.d_pd = st.d_pd[i];
+  c.A = st.A[i];
+  c.Z = st.Z[i];
+  c.q = st.q[i];
+  c.status = st.status[i];
+  const uint64_t done = st.n_acc[i];
+  const uint64_t left = done >= p.max_steps ? 0 : p.max_steps - done;
+  c.budget = left > 0xffffffffull ? 0xffffffffu : (uint32_t)left;
+  c.dacc = 0;
+  c.drej = 0;
+  c.rejections = 0;
+  c.crossed = false;
 }
+
+__device__ __forceinline__ void store_core(const DevState& st, LaneCore& c) {
+  const uint32_t i = c.slot;
+  st.x[i] = c.x[0];
+  st.y[i] = c.x[1];
+  st.z[i] = c.x[2];
+  st.E[i] = c.E;
+  st.s[i] = c.s;
+  st.h[i] = c.h;
+  st.d_pion[i] = c.d_pion;
+  st.d_pd[i] = c.d_pd;
+  st.status[i] = c.status;
+  st.n_acc[i] += c.dacc;
+  st.n_rej[i] += c.drej;
+  c.dacc = 0;
+  c.drej = 0;
+}
+
+// Fields a rare path may change.
+__device__ __forceinline__ void reload_event_fields(const DevState& st, LaneCore& c) {
+  const uint32_t i = c.slot;
+  c.E = st.E[i];
+  c.A = st.A[i];
+  c.Z = st.Z[i];
+  c.d_pion = st.d_pion[i];
+  c.d_pd = st.d_pd[i];
+}
+
+// One accepted step done: step budget bookkeeping.
+__device__ __forceinline__ void count_step(LaneCore& c, LaneCounters& lc) {
+  c.dacc += 1;
+  if (c.budget) c.budget -= 1;
+  lc.acc += 1;
+  lc.pending_acc += 1;
+}
+
+__device__ __forceinline__ void count_reject(LaneCore& c, LaneCounters& lc) {
+  c.rejections += 1;
+  c.drej += 1;
+  lc.rej += 1;
+}
+
+// Per-thread stage storage in shared memory: slot k of this thread lives at
+// base[k * stride], so a warp touching one slot hits 32 consecutive words.
+// Slots 0..17: stage directions U[j][c]; 18..35: stage forces K[j][c].
+template <class T>
+struct StageStore {
+  T* base;
+  int stride;
+  __device__ __forceinline__ T& u(int j, int c) { return base[(j * 3 + c) * stride]; }
+  __device__ __forceinline__ T& k(int j, int c) { return base[(18 + j * 3 + c) * stride]; }
+};
+constexpr int kStageSlots = 36;
 
 // Cash-Karp tableau in constant memory (uniform across a warp whose lanes
 // all run the same stage), for the stage loop.
-__constant__ double c_a64[6][6] = {
+static __constant__ double c_a64[6][6] = {
     {0, 0, 0, 0, 0, 0},
     {ck::a21, 0, 0, 0, 0, 0},
     {ck::a31, ck::a32, 0, 0, 0, 0},
     {ck::a41, ck::a42, ck::a43, 0, 0, 0},
     {ck::a51, ck::a52, ck::a53, ck::a54, 0, 0},
     {ck::a61, ck::a62, ck::a63, ck::a64, ck::a65, 0}};
-__constant__ float c_a32[6][6] = {
+static __constant__ float c_a32[6][6] = {
     {0, 0, 0, 0, 0, 0},
     {(float)ck::a21, 0, 0, 0, 0, 0},
     {(float)ck::a31, (float)ck::a32, 0, 0, 0, 0},
@@ -475,9 +554,9 @@ __constant__ float c_a32[6][6] = {
     {(float)ck::a61, (float)ck::a62, (float)ck::a63, (float)ck::a64, (float)ck::a65, 0}};
 
 // ---------------------------------------------------------------------------
-// FP64 policy.  begin_step / trial / finish_step split the module cycle so
-// that a warp advances one Cash-Karp trial per iteration; the arithmetic and
-// its order are those of the reference formulation.
+// FP64 policy.  begin_step / trial / finish_step / breaks split the module
+// cycle so that a warp advances one Cash-Karp trial per iteration; the
+// arithmetic and its order are those of the reference formulation.
 // ---------------------------------------------------------------------------
 struct PolicyFP64 {
   using Real = double;
@@ -487,9 +566,9 @@ struct PolicyFP64 {
     double y5[6];
   };
 
-  __device__ __forceinline__ static void load(const KParams&, const DevState& st, uint64_t i,
+  __device__ __forceinline__ static void load(const KParams& p, const DevState& st, uint32_t i,
                                               Lane& c) {
-    load_core(st, i, c);
+    load_core(p, st, i, c);
     c.u[0] = st.ux[i];
     c.u[1] = st.uy[i];
     c.u[2] = st.uz[i];
@@ -516,16 +595,13 @@ struct PolicyFP64 {
 
   template <class NodeT>
   __device__ __forceinline__ static void begin_step(const KParams& p, Lane& c,
-                                                    StageStore<double>& S, LaneCounters& lc) {
-    const bool pion_on = (p.flags & CRP_PION) != 0;
-    const bool pd_on = (p.flags & CRP_PHOTODIS) != 0;
-    if ((pion_on || pd_on) && !(c.flags & CF_STATES_DRAWN)) reset_states(p, c);
+                                                    StageStore<double>& S) {
     double h = c.h;
     if (h > p.h_max) h = p.h_max;
     c.cap_s = c.s_max - c.s;
     if (c.cap_s < h) h = c.cap_s;
-    if (pion_on && c.d_pion < h) h = c.d_pion;
-    if (pd_on && c.d_pd < h) h = c.d_pd;
+    if ((p.flags & CRP_PION) && c.d_pion < h) h = c.d_pion;
+    if ((p.flags & CRP_PHOTODIS) && c.d_pd < h) h = c.d_pd;
     c.h = h;  // trial step of this step
     c.kappa = (double)(c.q * c.Z) * p.curv_k / c.E;
     double k[3];
@@ -535,7 +611,6 @@ struct PolicyFP64 {
       S.k(0, i) = k[i];
     }
     c.rejections = 0;
-    lc.rhs += 1;
   }
 
   // One Cash-Karp trial with step c.h.  Returns true when accepted.
@@ -564,7 +639,6 @@ struct PolicyFP64 {
         S.k(j, i) = k[i];
       }
     }
-    lc.rhs += 5;
     double err[3];
     for (int i = 0; i < 3; ++i) {
       c.y5[i] = c.x[i] + h * (w1 * S.u(0, i) + w3 * S.u(2, i) + w4 * S.u(3, i) + w6 * S.u(5, i));
@@ -580,15 +654,14 @@ struct PolicyFP64 {
     double hn = h * fac;
     if (hn < p.h_min) hn = p.h_min;
     c.h = hn;
-    c.rejections += 1;
-    c.n_rej += 1;
-    lc.rej += 1;
+    count_reject(c, lc);
     return false;
   }
 
-  __device__ __forceinline__ static void finish_step(const KParams& p, const DevState& st,
-                                                     DevCounters* dc, Lane& c,
-                                                     LaneCounters& lc) {
+  // Accepted step: state update, continuous losses, free-path bookkeeping.
+  // Returns the stochastic interaction that fires (EV_NONE if none).
+  __device__ __forceinline__ static int finish_step(const KParams& p, Lane& c,
+                                                    LaneCounters& lc) {
     const double h = c.h;
     const double x_old[3] = {c.x[0], c.x[1], c.x[2]};
     c.x[0] = c.y5[0];
@@ -606,9 +679,8 @@ struct PolicyFP64 {
     if (h_next < p.h_min) h_next = p.h_min;
     if (h_next > p.h_max) h_next = p.h_max;
     c.h = h_next;
-    c.n_acc += 1;
-    lc.acc += 1;
-    lc.pending_acc += 1;
+    count_step(c, lc);
+    c.crossed = (p.flags & CRP_OBSERVER) && segment_enters(x_old, c.x, p.obs_c, p.obs_r);
     // continuous losses
     if (p.flags & (CRP_PAIR | CRP_ADIABATIC)) {
       double beta = 0.0;
@@ -619,24 +691,24 @@ struct PolicyFP64 {
       if (p.flags & CRP_ADIABATIC) beta = beta + p.beta_ad;
       c.E = c.E * (1.0 - beta * h);
     }
-    // stochastic interactions
+    // stochastic interactions: the first in module order whose free path ran out
     const bool pion_on = (p.flags & CRP_PION) != 0;
     const bool pd_on = (p.flags & CRP_PHOTODIS) != 0;
-    if (pion_on || pd_on) {
-      if (pion_on) c.d_pion = c.d_pion - h;
-      if (pd_on) c.d_pd = c.d_pd - h;
-      if (pion_on && c.d_pion <= 0.0) {
-        pion_event(p, c, lc);
-      } else if (pd_on && c.d_pd <= 0.0) {
-        photodisintegrate(p, st, dc, c, lc, c.u[0], c.u[1], c.u[2]);
-      }
-    }
-    // break conditions
+    if (pion_on) c.d_pion = c.d_pion - h;
+    if (pd_on) c.d_pd = c.d_pd - h;
+    if (pion_on && c.d_pion <= 0.0) return EV_PION;
+    if (pd_on && c.d_pd <= 0.0) return EV_PD;
+    return EV_NONE;
+  }
+
+  // Break conditions in module order: minimum energy, trajectory length,
+  // observer, border; then the per-candidate step budget.
+  __device__ __forceinline__ static void breaks(const KParams& p, Lane& c, LaneCounters& lc) {
     if ((p.flags & CRP_EMIN) && c.E < p.e_min) {
       c.status = CRP_BELOW_EMIN;
     } else if (c.s >= c.s_max) {
       c.status = CRP_MAX_LENGTH;
-    } else if ((p.flags & CRP_OBSERVER) && segment_enters(x_old, c.x, p.obs_c, p.obs_r)) {
+    } else if (c.crossed) {
       c.status = CRP_DETECTED;
       lc.detected += 1;
     } else if (p.flags & CRP_BORDER) {
@@ -644,31 +716,40 @@ struct PolicyFP64 {
                    dz = c.x[2] - p.border_c[2];
       if (dx * dx + dy * dy + dz * dz >= p.border_r * p.border_r) c.status = CRP_AT_BORDER;
     }
-    if (c.status == CRP_ACTIVE && c.n_acc >= p.max_steps) c.status = CRP_BUDGET;
+    if (c.status == CRP_ACTIVE && c.budget == 0) c.status = CRP_BUDGET;
   }
 
-  // Mid-step suspension: keep the current trial step (a resumed step
-  // restarts from it with the same caps and the same first stage).
+  __device__ __forceinline__ static void after_event(const DevState& st, Lane& c) {
+    reload_event_fields(st, c);
+  }
+
+  // Mid-step suspension: c.h already holds the current trial step, and a
+  // resumed step restarts from it with the same caps and the same first stage.
   __device__ __forceinline__ static void suspend(Lane&) {}
 };
 
 // ---------------------------------------------------------------------------
 // Mixed policy: binary32 field, force and stages relative to the current
 // grid cell; binary64 position, trajectory length, energy, free paths and
-// error norm.
+// error norm (decided in binary64 near the tolerance).  GAL adds the
+// analytic galactic field.
 // ---------------------------------------------------------------------------
 enum : int { CAP_NONE = 0, CAP_S = 1, CAP_PION = 2, CAP_PD = 3 };
 
-struct PolicyMixed {
+template <bool GAL>
+struct PolicyMixedT {
   using Real = float;
-  struct Lane : LaneCore {
+  struct LaneGal {
+    float gal[3];  // position relative to the galactic centre
+  };
+  struct LaneNoGal {};
+  struct Lane : LaneCore, std::conditional<GAL, LaneGal, LaneNoGal>::type {
     float u[3];
     int cell[3];    // grid cell of the current position
     float frac[3];  // in-cell fraction (grid units)
-    float gal[3];   // position relative to the galactic centre
-    float hf;      // trial step of the current step
-    float hn;      // proposed next step, in [h_min, h_max]
-    float E_f;     // binary32 copy of the energy
+    float hf;       // trial step of the current step
+    float hn;       // proposed next step, in [h_min, h_max]
+    float E_f;      // binary32 copy of the energy
     float kap, d_obs, d_bord, err2, dx[3], u5[3];
     int cap, since_rebase;
   };
@@ -682,7 +763,7 @@ struct PolicyMixed {
       c.frac[d] = (float)(r - fl);
       c.cell[d] = (int)wrap_fl(fl, p.f.n[d], p.f.mask[d]);
     }
-    if (p.flags & CRP_GALACTIC) {
+    if constexpr (GAL) {
 #pragma unroll
       for (int d = 0; d < 3; ++d) c.gal[d] = (float)(c.x[d] - p.gal_c[d]);
     }
@@ -706,9 +787,9 @@ struct PolicyMixed {
     }
   }
 
-  __device__ __forceinline__ static void load(const KParams& p, const DevState& st, uint64_t i,
+  __device__ __forceinline__ static void load(const KParams& p, const DevState& st, uint32_t i,
                                               Lane& c) {
-    load_core(st, i, c);
+    load_core(p, st, i, c);
     c.u[0] = (float)st.ux[i];
     c.u[1] = (float)st.uy[i];
     c.u[2] = (float)st.uz[i];
@@ -763,7 +844,7 @@ struct PolicyMixed {
                lerp(lerp(v4.y, v5.y, tx), lerp(v6.y, v7.y, tx), ty), tz);
     B.z = lerp(lerp(lerp(v0.z, v1.z, tx), lerp(v2.z, v3.z, tx), ty),
                lerp(lerp(v4.z, v5.z, tx), lerp(v6.z, v7.z, tx), ty), tz);
-    if (p.flags & CRP_GALACTIC) {
+    if constexpr (GAL) {
       const float3 G = galactic_f32(p, c.gal[0] + ox, c.gal[1] + oy, c.gal[2] + oz);
       B.x += G.x;
       B.y += G.y;
@@ -774,10 +855,7 @@ struct PolicyMixed {
 
   template <class NodeT>
   __device__ __forceinline__ static void begin_step(const KParams& p, Lane& c,
-                                                    StageStore<float>& S, LaneCounters& lc) {
-    const bool pion_on = (p.flags & CRP_PION) != 0;
-    const bool pd_on = (p.flags & CRP_PHOTODIS) != 0;
-    if ((pion_on || pd_on) && !(c.flags & CF_STATES_DRAWN)) reset_states(p, c);
+                                                    StageStore<float>& S) {
     c.cap = CAP_NONE;
     double h = (double)c.hn;
     const double rem = c.s_max - c.s;
@@ -785,11 +863,11 @@ struct PolicyMixed {
       h = rem;
       c.cap = CAP_S;
     }
-    if (pion_on && c.d_pion < h) {
+    if ((p.flags & CRP_PION) && c.d_pion < h) {
       h = c.d_pion;
       c.cap = CAP_PION;
     }
-    if (pd_on && c.d_pd < h) {
+    if ((p.flags & CRP_PHOTODIS) && c.d_pd < h) {
       h = c.d_pd;
       c.cap = CAP_PD;
     }
@@ -803,7 +881,6 @@ struct PolicyMixed {
     S.k(0, 1) = c.kap * (c.u[2] * B.x - c.u[0] * B.z);
     S.k(0, 2) = c.kap * (c.u[0] * B.y - c.u[1] * B.x);
     c.rejections = 0;
-    lc.rhs += 1;
   }
 
   template <class NodeT>
@@ -831,7 +908,6 @@ struct PolicyMixed {
       S.k(j, 1) = c.kap * (uz * B.x - ux * B.z);
       S.k(j, 2) = c.kap * (ux * B.y - uy * B.x);
     }
-    lc.rhs += 5;
     constexpr float W1 = (float)ck::w1, W3 = (float)ck::w3, W4 = (float)ck::w4,
                     W6 = (float)ck::w6;
     constexpr float D1 = (float)ck::d1, D3 = (float)ck::d3, D4 = (float)ck::d4,
@@ -863,15 +939,12 @@ struct PolicyMixed {
     fac = fmaxf(fac, 0.1f);
     c.hf = fmaxf(h * fac, p.h_min_f);
     c.cap = CAP_NONE;
-    c.rejections += 1;
-    c.n_rej += 1;
-    lc.rej += 1;
+    count_reject(c, lc);
     return false;
   }
 
-  __device__ __forceinline__ static void finish_step(const KParams& p, const DevState& st,
-                                                     DevCounters* dc, Lane& c,
-                                                     LaneCounters& lc) {
+  __device__ __forceinline__ static int finish_step(const KParams& p, Lane& c,
+                                                    LaneCounters& lc) {
     const float hf = c.hf;
     const double h = (double)hf;
     const double x_old[3] = {c.x[0], c.x[1], c.x[2]};
@@ -886,9 +959,7 @@ struct PolicyMixed {
     float grow = 5.f;
     if (c.err2 > 0.f) grow = fminf(5.f, 0.95f * rsqrtf(sqrtf(sqrtf(c.err2 * p.inv_tol2_f))));
     c.hn = fminf(fmaxf(hf * grow, p.h_min_f), p.h_max_f);
-    c.n_acc += 1;
-    lc.acc += 1;
-    lc.pending_acc += 1;
+    count_step(c, lc);
     // field-lookup coordinate: advance in binary32, exact rebase every 32 steps
     if (++c.since_rebase >= 32) {
       rebase(p, c);
@@ -900,9 +971,18 @@ struct PolicyMixed {
         c.frac[d] = r - fl;
         c.cell[d] = wrap_int(c.cell[d] + (int)fl, (int)p.f.n[d], (int)p.f.mask[d]);
       }
-      if (p.flags & CRP_GALACTIC) {
+      if constexpr (GAL) {
 #pragma unroll
         for (int d = 0; d < 3; ++d) c.gal[d] += c.dx[d];
+      }
+    }
+    // observer: exact binary64 segment test only when the sphere is in reach
+    c.crossed = false;
+    if (p.flags & CRP_OBSERVER) {
+      c.d_obs -= 1.01f * hf;
+      if (c.d_obs <= 0.f) {
+        c.crossed = segment_enters(x_old, c.x, p.obs_c, p.obs_r);
+        if (!c.crossed) bounds(p, c);
       }
     }
     // continuous losses
@@ -915,55 +995,50 @@ struct PolicyMixed {
       }
       if (p.flags & CRP_ADIABATIC) beta += p.beta_ad_f;
       c.E = c.E * (1.0 - (double)(beta * hf));
+      c.E_f = (float)c.E;
     }
     // stochastic interactions
     const bool pion_on = (p.flags & CRP_PION) != 0;
     const bool pd_on = (p.flags & CRP_PHOTODIS) != 0;
-    if (pion_on || pd_on) {
-      if (pion_on) c.d_pion = c.cap == CAP_PION ? 0.0 : c.d_pion - h;
-      if (pd_on) c.d_pd = c.cap == CAP_PD ? 0.0 : c.d_pd - h;
-      if (pion_on && c.d_pion <= 0.0) {
-        pion_event(p, c, lc);
-      } else if (pd_on && c.d_pd <= 0.0) {
-        photodisintegrate(p, st, dc, c, lc, (double)c.u[0], (double)c.u[1], (double)c.u[2]);
-      }
-    }
-    c.E_f = (float)c.E;
-    // break conditions
-    const float reach = 1.01f * hf;
+    if (pion_on) c.d_pion = c.cap == CAP_PION ? 0.0 : c.d_pion - h;
+    if (pd_on) c.d_pd = c.cap == CAP_PD ? 0.0 : c.d_pd - h;
+    if (pion_on && c.d_pion <= 0.0) return EV_PION;
+    if (pd_on && c.d_pd <= 0.0) return EV_PD;
+    return EV_NONE;
+  }
+
+  __device__ __forceinline__ static void breaks(const KParams& p, Lane& c, LaneCounters& lc) {
     if ((p.flags & CRP_EMIN) && c.E < p.e_min) {
       c.status = CRP_BELOW_EMIN;
     } else if (c.s >= c.s_max) {
       c.status = CRP_MAX_LENGTH;
-    } else {
-      if (p.flags & CRP_OBSERVER) {
-        c.d_obs -= reach;
-        if (c.d_obs <= 0.f) {
-          if (segment_enters(x_old, c.x, p.obs_c, p.obs_r)) {
-            c.status = CRP_DETECTED;
-            lc.detected += 1;
-          } else {
-            bounds(p, c);
-          }
-        }
-      }
-      if (c.status == CRP_ACTIVE && (p.flags & CRP_BORDER)) {
-        c.d_bord -= reach;
-        if (c.d_bord <= 0.f) {
-          const double dx = c.x[0] - p.border_c[0], dy = c.x[1] - p.border_c[1],
-                       dz = c.x[2] - p.border_c[2];
-          if (dx * dx + dy * dy + dz * dz >= p.border_r * p.border_r)
-            c.status = CRP_AT_BORDER;
-          else
-            bounds(p, c);
-        }
+    } else if (c.crossed) {
+      c.status = CRP_DETECTED;
+      lc.detected += 1;
+    } else if (p.flags & CRP_BORDER) {
+      c.d_bord -= 1.01f * c.hf;
+      if (c.d_bord <= 0.f) {
+        const double dx = c.x[0] - p.border_c[0], dy = c.x[1] - p.border_c[1],
+                     dz = c.x[2] - p.border_c[2];
+        if (dx * dx + dy * dy + dz * dz >= p.border_r * p.border_r)
+          c.status = CRP_AT_BORDER;
+        else
+          bounds(p, c);
       }
     }
-    if (c.status == CRP_ACTIVE && c.n_acc >= p.max_steps) c.status = CRP_BUDGET;
+    if (c.status == CRP_ACTIVE && c.budget == 0) c.status = CRP_BUDGET;
+  }
+
+  __device__ __forceinline__ static void after_event(const DevState& st, Lane& c) {
+    reload_event_fields(st, c);
+    c.E_f = (float)c.E;
   }
 
   __device__ __forceinline__ static void suspend(Lane& c) { c.hn = c.hf; }
 };
+
+using PolicyMixed = PolicyMixedT<false>;
+using PolicyMixedGal = PolicyMixedT<true>;
 
 // ---------------------------------------------------------------------------
 // Persistent driver: lanes take candidates from the round's work queue, run
@@ -971,25 +1046,19 @@ struct PolicyMixed {
 // iteration for the whole warp), then requeue still-active candidates for
 // the next round and take the next one.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
-  return v;
-}
-
+// Threads per block of each policy; MINB, the resident blocks per SM the
+// register allocation is sized for, is a launch variant the tuner chooses.
 template <class Policy>
-struct Bounds;
+struct Bounds {
+  static constexpr int kThreads = 256;
+};
 template <>
 struct Bounds<PolicyFP64> {
-  static constexpr int kThreads = 128, kMinBlocks = 2;
-};
-template <>
-struct Bounds<PolicyMixed> {
-  static constexpr int kThreads = 256, kMinBlocks = 2;
+  static constexpr int kThreads = 128;
 };
 
-template <class Policy, class NodeT>
-__global__ void __launch_bounds__(Bounds<Policy>::kThreads, Bounds<Policy>::kMinBlocks)
+template <class Policy, class NodeT, int MINB>
+__global__ void __launch_bounds__(Bounds<Policy>::kThreads, MINB)
     propagate_kernel(const KParams p, const DevState st, DevCounters* dc) {
   using Real = typename Policy::Real;
   using Lane = typename Policy::Lane;
@@ -998,7 +1067,7 @@ __global__ void __launch_bounds__(Bounds<Policy>::kThreads, Bounds<Policy>::kMin
   const int lane = threadIdx.x & 31;
   const unsigned long long t0 = globaltimer_ns();
   Lane c;
-  LaneCounters lc = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  LaneCounters lc = {0, 0, 0, 0};
   bool has = false, exhausted = false, in_step = false;
   uint32_t slice_steps = 0;
   int iter = 0;
@@ -1016,6 +1085,8 @@ __global__ void __launch_bounds__(Bounds<Policy>::kThreads, Bounds<Policy>::kMin
         if (mine < p.n_in) {
           const uint32_t slot = p.queue_in[mine];
           if (st.status[slot] == CRP_ACTIVE) {
+            if ((p.flags & (CRP_PION | CRP_PHOTODIS)) && !(st.flags[slot] & CF_STATES_DRAWN))
+              slot_event(p, st, dc, slot, EV_DRAW);  // first free paths of this candidate
             Policy::load(p, st, slot, c);
             has = true;
             in_step = false;
@@ -1029,11 +1100,17 @@ __global__ void __launch_bounds__(Bounds<Policy>::kThreads, Bounds<Policy>::kMin
     if (__ballot_sync(FULL_MASK, has || !exhausted) == 0) break;
     if (has) {
       if (!in_step) {
-        Policy::template begin_step<NodeT>(p, c, S, lc);
+        Policy::template begin_step<NodeT>(p, c, S);
         in_step = true;
       }
       if (Policy::template trial<NodeT>(p, c, S, lc)) {
-        Policy::finish_step(p, st, dc, c, lc);
+        const int ev = Policy::finish_step(p, c, lc);
+        if (ev != EV_NONE) {
+          Policy::store(st, c);
+          slot_event(p, st, dc, c.slot, ev);
+          Policy::after_event(st, c);
+        }
+        Policy::breaks(p, c, lc);
         in_step = false;
         slice_steps += 1;
         if (c.status != CRP_ACTIVE) {
@@ -1042,7 +1119,7 @@ __global__ void __launch_bounds__(Bounds<Policy>::kThreads, Bounds<Policy>::kMin
         } else if (slice_steps >= p.slice) {
           Policy::store(st, c);
           const unsigned long long qo = atomicAdd(&dc->q_out, 1ull);
-          if (qo < p.capacity) p.queue_out[qo] = (uint32_t)c.slot;
+          if (qo < p.capacity) p.queue_out[qo] = c.slot;
           has = false;
         }
       }
@@ -1067,21 +1144,18 @@ __global__ void __launch_bounds__(Bounds<Policy>::kThreads, Bounds<Policy>::kMin
       }
     }
   }
-  // fold lane counters into the call's totals
+  // fold lane counters into the call's totals; every completed step evaluated
+  // the force once at its start and five times per trial
   const bool budgeted = p.step_budget || p.deadline_ns;
-  const uint64_t acc_rem = warp_sum_u64(budgeted ? lc.pending_acc : lc.acc);
-  const uint64_t rej = warp_sum_u64(lc.rej), rhs = warp_sum_u64(lc.rhs);
-  const uint64_t pion = warp_sum_u64(lc.pion), pd = warp_sum_u64(lc.pd);
-  const uint64_t sec = warp_sum_u64(lc.sec), dropped = warp_sum_u64(lc.dropped);
-  const uint64_t det = warp_sum_u64(lc.detected);
+  const unsigned acc_rem = __reduce_add_sync(FULL_MASK, budgeted ? lc.pending_acc : lc.acc);
+  const unsigned acc = __reduce_add_sync(FULL_MASK, lc.acc);
+  const unsigned rej = __reduce_add_sync(FULL_MASK, lc.rej);
+  const unsigned det = __reduce_add_sync(FULL_MASK, lc.detected);
   if (lane == 0) {
     if (acc_rem) atomicAdd(&dc->acc, (unsigned long long)acc_rem);
     if (rej) atomicAdd(&dc->rej, (unsigned long long)rej);
-    if (rhs) atomicAdd(&dc->rhs, (unsigned long long)rhs);
-    if (pion) atomicAdd(&dc->pion, (unsigned long long)pion);
-    if (pd) atomicAdd(&dc->pd, (unsigned long long)pd);
-    if (sec) atomicAdd(&dc->secondaries, (unsigned long long)sec);
-    if (dropped) atomicAdd(&dc->dropped, (unsigned long long)dropped);
+    const unsigned long long rhs = 6ull * acc + 5ull * rej;
+    if (rhs) atomicAdd(&dc->rhs, rhs);
     if (det) atomicAdd(&dc->detected, (unsigned long long)det);
   }
 }
@@ -1091,31 +1165,31 @@ size_t smem_bytes(int block) {
   return (size_t)kStageSlots * (size_t)block * sizeof(typename Policy::Real);
 }
 
-template <class Policy>
+template <class Policy, int MINB>
 cudaError_t launch_policy(const KParams& kp, const DevState& st, DevCounters* dc, int grid,
                           int block, cudaStream_t s) {
   const size_t sm = smem_bytes<Policy>(block);
   if (kp.f.dtype == CRP_F32) {
-    auto k = propagate_kernel<Policy, float4>;
+    auto k = propagate_kernel<Policy, float4, MINB>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k<<<grid, block, sm, s>>>(kp, st, dc);
   } else {
-    auto k = propagate_kernel<Policy, DNode>;
+    auto k = propagate_kernel<Policy, DNode, MINB>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k<<<grid, block, sm, s>>>(kp, st, dc);
   }
   return cudaGetLastError();
 }
 
-template <class Policy>
+template <class Policy, int MINB>
 cudaError_t occupancy_policy(int dtype, int block, int* bps) {
   const size_t sm = smem_bytes<Policy>(block);
   if (dtype == CRP_F32) {
-    auto k = propagate_kernel<Policy, float4>;
+    auto k = propagate_kernel<Policy, float4, MINB>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k, block, sm);
   }
-  auto k = propagate_kernel<Policy, DNode>;
+  auto k = propagate_kernel<Policy, DNode, MINB>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k, block, sm);
 }
