@@ -228,7 +228,8 @@ typedef struct {
   uint32_t slice;            /* accepted steps a lane runs on one candidate before
                                 requeueing it for the next round (0 = 512); bounds
                                 the load imbalance between lanes of a warp */
-  uint32_t reserved;
+  int32_t spatial_sort;      /* 0: sort each round's work queue by grid brick so
+                                neighbouring lanes gather nearby cells; -1: off */
 } crp_modules;
 
 typedef struct {

@@ -74,7 +74,7 @@ class Modules(C.Structure):
                 ("gal_center", C.c_double * 3),
                 ("max_steps", C.c_uint64), ("step_budget", C.c_uint64),
                 ("deadline_ms", C.c_double), ("block_size", C.c_int32),
-                ("blocks_per_sm", C.c_int32), ("slice", C.c_uint32), ("reserved", C.c_uint32)]
+                ("blocks_per_sm", C.c_int32), ("slice", C.c_uint32), ("spatial_sort", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -353,7 +353,7 @@ def modules(precision=FP64, flags=0, tol=1e-4, h_min=0.01, h_max=1.0, field_unit
             length_unit_m=MPC_M, beta_ad=0.0, e_min=0.0, tables=None, observer_center=(0, 0, 0),
             observer_radius=0.0, border_center=(0, 0, 0), border_radius=0.0, galactic=None,
             max_steps=10_000_000, step_budget=0, deadline_ms=0.0, block_size=0, blocks_per_sm=0,
-            slice=0):
+            slice=0, spatial_sort=0):
     m = Modules()
     m.precision, m.flags, m.tol, m.h_min, m.h_max = precision, flags, tol, h_min, h_max
     m.field_unit_T, m.length_unit_m, m.beta_ad, m.e_min = field_unit_T, length_unit_m, beta_ad, e_min
@@ -370,4 +370,5 @@ def modules(precision=FP64, flags=0, tol=1e-4, h_min=0.01, h_max=1.0, field_unit
                 setattr(m, k, v)
     m.max_steps, m.step_budget, m.deadline_ms = max_steps, step_budget, deadline_ms
     m.block_size, m.blocks_per_sm, m.slice = block_size, blocks_per_sm, slice
+    m.spatial_sort = spatial_sort
     return m

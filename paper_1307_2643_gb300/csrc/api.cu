@@ -7,8 +7,11 @@
 
 #include <mutex>
 #include <new>
+#include <type_traits>
+#include <utility>
 
 #include "crp_internal.cuh"
+#include "device_common.cuh"
 #include "field_internal.h"
 
 // ===========================================================================
@@ -83,6 +86,8 @@ struct crp_context {
   DevCounters* dc;        // device counters
   DevCounters* hc;        // pinned host mirror
   uint32_t* queue[2];     // work queues of the propagate rounds (capacity each)
+  uint32_t* keys;         // spatial keys of the entries a round writes (capacity)
+  uint32_t* bins;         // counting-sort histogram (kSortBins + 1)
   int sm_count;
   cudaEvent_t ev0, ev1;
 };
@@ -157,14 +162,19 @@ crp_status ensure_pool(crp_context* c) {
   c->dc = static_cast<DevCounters*>(dev_alloc(sizeof(DevCounters)));
   c->queue[0] = static_cast<uint32_t*>(dev_alloc(c->capacity * sizeof(uint32_t)));
   c->queue[1] = static_cast<uint32_t*>(dev_alloc(c->capacity * sizeof(uint32_t)));
-  if (!c->dc || !c->queue[0] || !c->queue[1]) {
+  c->keys = static_cast<uint32_t*>(dev_alloc(c->capacity * sizeof(uint32_t)));
+  c->bins = static_cast<uint32_t*>(dev_alloc((kSortBins + 1) * sizeof(uint32_t)));
+  if (!c->dc || !c->queue[0] || !c->queue[1] || !c->keys || !c->bins) {
     dev_free(c->pool);
     dev_free(c->dc);
     dev_free(c->queue[0]);
     dev_free(c->queue[1]);
+    dev_free(c->keys);
+    dev_free(c->bins);
     c->pool = nullptr;
     c->dc = nullptr;
     c->queue[0] = c->queue[1] = nullptr;
+    c->keys = c->bins = nullptr;
     set_error("candidate pool: cannot allocate counters / work queues");
     return CRP_E_OOM;
   }
@@ -225,23 +235,77 @@ __global__ void k_to_float(const double* in, float* out, int64_t n) {
     out[i] = (float)in[i];
 }
 
-// Work queue of the first round: every active candidate of the pool.  The
-// loop bound is warp-uniform so every lane takes part in each ballot.
-__global__ void k_build_queue(const int32_t* status, uint64_t n, uint32_t* queue,
-                              unsigned long long* count) {
+// Work queue of the first round: every active candidate of the pool, with
+// its spatial key.  The loop bound is warp-uniform so every lane takes part
+// in each ballot.
+__global__ void k_build_queue(DevState st, uint64_t n, FieldView f, int3 shift, uint32_t* queue,
+                              uint32_t* keys, unsigned long long* count) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const int lane = threadIdx.x & 31;
+  const int sh[3] = {shift.x, shift.y, shift.z};
   for (uint64_t base_i = blockIdx.x * (uint64_t)blockDim.x; base_i < n; base_i += stride) {
     const uint64_t i = base_i + threadIdx.x;
-    const bool act = i < n && status[i] == CRP_ACTIVE;
+    const bool act = i < n && st.status[i] == CRP_ACTIVE;
     const unsigned m = __ballot_sync(0xffffffffu, act);
     if (!m) continue;
     const int leader = __ffs(m) - 1;
     unsigned long long base = 0;
     if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(m));
     base = __shfl_sync(0xffffffffu, base, leader);
-    if (act) queue[base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)i;
+    if (act) {
+      const uint64_t o = base + __popc(m & ((1u << lane) - 1u));
+      queue[o] = (uint32_t)i;
+      const double r[3] = {st.x[i], st.y[i], st.z[i]};
+      int cell[3];
+      for (int d = 0; d < 3; ++d) {
+        const double fl = floor((r[d] - f.origin[d]) * f.inv_spacing);
+        int64_t c = (int64_t)fl % f.n[d];
+        if (c < 0) c += f.n[d];
+        cell[d] = (int)c;
+      }
+      keys[o] = brick_key(cell[0], cell[1], cell[2], sh);
+    }
   }
+}
+
+// Counting sort of a work queue by spatial key: lanes that run adjacent
+// queue entries then gather from nearby grid cells.
+__global__ void k_sort_hist(const uint32_t* keys, uint64_t n, uint32_t* bins) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    atomicAdd(bins + keys[i], 1u);
+}
+
+__global__ void k_sort_scan(uint32_t* bins) {  // exclusive scan, one block of 1024
+  __shared__ uint32_t part[1024];
+  constexpr int per = kSortBins / 1024;
+  const int t = threadIdx.x;
+  uint32_t s = 0;
+  for (int i = 0; i < per; ++i) s += bins[t * per + i];
+  part[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    uint32_t run = 0;
+    for (int i = 0; i < 1024; ++i) {
+      const uint32_t v = part[i];
+      part[i] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  uint32_t run = part[t];
+  for (int i = 0; i < per; ++i) {
+    const uint32_t v = bins[t * per + i];
+    bins[t * per + i] = run;
+    run += v;
+  }
+}
+
+__global__ void k_sort_scatter(const uint32_t* keys, const uint32_t* in, uint64_t n,
+                               uint32_t* bins, uint32_t* out) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    out[atomicAdd(bins + keys[i], 1u)] = in[i];
 }
 
 __global__ void k_round_reset(DevCounters* dc) {
@@ -439,6 +503,8 @@ crp_status crp_context_destroy(crp_context* c) {
   dev_free(c->dc);
   dev_free(c->queue[0]);
   dev_free(c->queue[1]);
+  dev_free(c->keys);
+  dev_free(c->bins);
   if (c->hc) cudaFreeHost(c->hc);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
@@ -878,12 +944,34 @@ crp_status crp_propagate(crp_context* c, const crp_grid* g, const crp_modules* m
     set_error("crp_propagate: pool indices must fit 32 bits");
     return CRP_E_INVALID;
   }
-  // round 0 work queue: the active candidates of the pool
+  for (int d = 0; d < 3; ++d) {
+    int bits = 0;
+    while ((1ll << bits) < kp.f.n[d]) ++bits;
+    kp.key_shift[d] = bits > 5 ? bits - 5 : 0;
+  }
+  const bool sort_on = m->spatial_sort >= 0;
+  const int3 shift3 = make_int3(kp.key_shift[0], kp.key_shift[1], kp.key_shift[2]);
+  // Work queue of round r is the list round r-1 wrote (requeued candidates
+  // and new secondaries), sorted by spatial brick; round 0 lists the pool.
+  uint32_t* q_in = c->queue[0];
+  uint32_t* q_out = c->queue[1];
+  auto sort_into_qin = [&](uint64_t n) -> cudaError_t {
+    if (!sort_on || n < 8192) {
+      std::swap(q_in, q_out);
+      return cudaSuccess;
+    }
+    cudaError_t err = cudaMemsetAsync(c->bins, 0, (kSortBins + 1) * sizeof(uint32_t), s);
+    if (err != cudaSuccess) return err;
+    k_sort_hist<<<blocks_for(n, 256), 256, 0, s>>>(c->keys, n, c->bins);
+    k_sort_scan<<<1, 1024, 0, s>>>(c->bins);
+    k_sort_scatter<<<blocks_for(n, 256), 256, 0, s>>>(c->keys, q_out, n, c->bins, q_in);
+    return cudaGetLastError();
+  };
   cudaError_t e = cudaMemsetAsync(c->dc, 0, sizeof(DevCounters), s);
   if (e == cudaSuccess) {
     k_set_u64<<<1, 1, 0, s>>>(&c->dc->tail, (unsigned long long)c->size);
-    k_build_queue<<<blocks_for(c->size, 256), 256, 0, s>>>(c->st.status, c->size, c->queue[0],
-                                                           &c->dc->q_out);
+    k_build_queue<<<blocks_for(c->size, 256), 256, 0, s>>>(c->st, c->size, kp.f, shift3, q_out,
+                                                           c->keys, &c->dc->q_out);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess)
@@ -891,15 +979,17 @@ crp_status crp_propagate(crp_context* c, const crp_grid* g, const crp_modules* m
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fail_cuda(e, "crp_propagate: work queue");
   uint64_t n_in = c->hc->q_out;
-  int qi = 0;
+  e = sort_into_qin(n_in);
+  if (e != cudaSuccess) return fail_cuda(e, "crp_propagate: queue sort");
   kp.slice = m->slice ? m->slice : 512u;
 
   crp_status st = CRP_OK;
   uint32_t launches = 0;
   float total_ms = 0.f;
   while (n_in > 0) {
-    kp.queue_in = c->queue[qi];
-    kp.queue_out = c->queue[qi ^ 1];
+    kp.queue_in = q_in;
+    kp.queue_out = q_out;
+    kp.keys_out = c->keys;
     kp.n_in = n_in;
     uint64_t gsz = (uint64_t)c->sm_count * (uint64_t)bps;
     const uint64_t need = (n_in + block - 1) / block;
@@ -924,7 +1014,8 @@ crp_status crp_propagate(crp_context* c, const crp_grid* g, const crp_modules* m
       break;
     }
     n_in = c->hc->q_out < c->capacity ? c->hc->q_out : c->capacity;
-    qi ^= 1;
+    e = sort_into_qin(n_in);
+    if (e != cudaSuccess) return fail_cuda(e, "crp_propagate: queue sort");
   }
   uint64_t tail = c->hc->tail < c->capacity ? c->hc->tail : c->capacity;
   c->size = tail;

@@ -95,6 +95,8 @@ struct KParams {
   const uint32_t* queue_in;
   uint64_t n_in;
   uint32_t* queue_out;
+  uint32_t* keys_out;              // spatial brick key of each queue_out entry
+  int key_shift[3];                // cell -> brick shift per axis (32 bricks per axis)
   uint32_t slice;                  // accepted steps per candidate per round
 };
 

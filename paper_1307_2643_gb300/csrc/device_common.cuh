@@ -110,6 +110,20 @@ __device__ __forceinline__ double series_log(double x) {
   return (double)k * 0.69314718055994530942 + ln_m;
 }
 
+// Spatial key of a grid cell for the work-queue sort: the cell's brick
+// (cell >> shift, 32 bricks per axis) in Morton order, 15 bits.
+__device__ __forceinline__ uint32_t brick_key(int cx, int cy, int cz, const int shift[3]) {
+  const uint32_t bx = (uint32_t)(cx >> shift[0]) & 31u, by = (uint32_t)(cy >> shift[1]) & 31u,
+                 bz = (uint32_t)(cz >> shift[2]) & 31u;
+  uint32_t key = 0;
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+    key |= (((bx >> i) & 1u) << (3 * i)) | (((by >> i) & 1u) << (3 * i + 1)) |
+           (((bz >> i) & 1u) << (3 * i + 2));
+  return key;
+}
+constexpr int kSortBins = 1 << 15;
+
 // Proton rest energy [eV] (CODATA 2018).
 constexpr double MP_C2_EV = 938.27208816e6;
 

@@ -102,6 +102,16 @@ __device__ __forceinline__ int wrap_int(int i, int n, int mask) {
 
 __device__ __forceinline__ double lerp_d(double a, double b, double t) { return a + t * (b - a); }
 
+__device__ __forceinline__ uint32_t key_of_position(const KParams& p, double x, double y,
+                                                    double z) {
+  const double r[3] = {x, y, z};
+  int c[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    c[d] = (int)wrap_fl(floor((r[d] - p.f.origin[d]) * p.f.inv_spacing), p.f.n[d], p.f.mask[d]);
+  return brick_key(c[0], c[1], c[2], p.key_shift);
+}
+
 // ---------------------------------------------------------------------------
 // Analytic galactic field (disk log-spiral + toroidal halo), binary64.
 // ---------------------------------------------------------------------------
@@ -347,7 +357,10 @@ __device__ __forceinline__ void photodisintegrate(const KParams& p, const DevSta
       st.n_rej[slot] = 0;
       // the nucleon joins the next round (its slot is fully written first)
       const unsigned long long qo = atomicAdd(&dc->q_out, 1ull);
-      if (qo < p.capacity) p.queue_out[qo] = (uint32_t)slot;
+      if (qo < p.capacity) {
+        p.queue_out[qo] = (uint32_t)slot;
+        p.keys_out[qo] = key_of_position(p, c.x[0], c.x[1], c.x[2]);
+      }
       n.sec += 1;
     } else {
       atomicAdd(&dc->overflow, 1ull);
@@ -560,6 +573,7 @@ static __constant__ float c_a32[6][6] = {
 // ---------------------------------------------------------------------------
 struct PolicyFP64 {
   using Real = double;
+  static constexpr bool kSharedStages = true;
   struct Lane : LaneCore {
     double u[3];
     double cap_s, kappa, eps;
@@ -723,6 +737,10 @@ struct PolicyFP64 {
     reload_event_fields(st, c);
   }
 
+  __device__ __forceinline__ static uint32_t key(const KParams& p, const Lane& c) {
+    return key_of_position(p, c.x[0], c.x[1], c.x[2]);
+  }
+
   // Mid-step suspension: c.h already holds the current trial step, and a
   // resumed step restarts from it with the same caps and the same first stage.
   __device__ __forceinline__ static void suspend(Lane&) {}
@@ -739,6 +757,7 @@ enum : int { CAP_NONE = 0, CAP_S = 1, CAP_PION = 2, CAP_PD = 3 };
 template <bool GAL>
 struct PolicyMixedT {
   using Real = float;
+  static constexpr bool kSharedStages = false;
   struct LaneGal {
     float gal[3];  // position relative to the galactic centre
   };
@@ -751,6 +770,7 @@ struct PolicyMixedT {
     float hn;       // proposed next step, in [h_min, h_max]
     float E_f;      // binary32 copy of the energy
     float kap, d_obs, d_bord, err2, dx[3], u5[3];
+    float3 k1;      // force at the start of the step
     int cap, since_rebase;
   };
 
@@ -853,9 +873,15 @@ struct PolicyMixedT {
     return B;
   }
 
+  __device__ __forceinline__ static float3 force(float kap, float ux, float uy, float uz,
+                                                 float3 B) {
+    return make_float3(kap * (uy * B.z - uz * B.y), kap * (uz * B.x - ux * B.z),
+                       kap * (ux * B.y - uy * B.x));
+  }
+
   template <class NodeT>
   __device__ __forceinline__ static void begin_step(const KParams& p, Lane& c,
-                                                    StageStore<float>& S) {
+                                                    StageStore<float>&) {
     c.cap = CAP_NONE;
     double h = (double)c.hn;
     const double rem = c.s_max - c.s;
@@ -873,53 +899,60 @@ struct PolicyMixedT {
     }
     c.hf = c.cap == CAP_NONE ? c.hn : (float)h;
     c.kap = (float)(c.q * c.Z) * p.curv_k_f / c.E_f;
-    const float3 B = field<NodeT>(p, c, 0.f, 0.f, 0.f);
-    S.u(0, 0) = c.u[0];
-    S.u(0, 1) = c.u[1];
-    S.u(0, 2) = c.u[2];
-    S.k(0, 0) = c.kap * (c.u[1] * B.z - c.u[2] * B.y);
-    S.k(0, 1) = c.kap * (c.u[2] * B.x - c.u[0] * B.z);
-    S.k(0, 2) = c.kap * (c.u[0] * B.y - c.u[1] * B.x);
+    c.k1 = force(c.kap, c.u[0], c.u[1], c.u[2], field<NodeT>(p, c, 0.f, 0.f, 0.f));
     c.rejections = 0;
   }
 
+  // One Cash-Karp trial; the stage vectors stay in registers (stages
+  // unrolled), the first stage's force is reused across rejections.
   template <class NodeT>
-  __device__ __forceinline__ static bool trial(const KParams& p, Lane& c, StageStore<float>& S,
+  __device__ __forceinline__ static bool trial(const KParams& p, Lane& c, StageStore<float>&,
                                                LaneCounters& lc) {
-    const float h = c.hf;
-#pragma unroll 1
-    for (int j = 1; j < 6; ++j) {
-      float ox = 0.f, oy = 0.f, oz = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
-      for (int m = 0; m < j; ++m) {
-        const float a = c_a32[j][m];
-        ox = fmaf(a, S.u(m, 0), ox);
-        oy = fmaf(a, S.u(m, 1), oy);
-        oz = fmaf(a, S.u(m, 2), oz);
-        sx = fmaf(a, S.k(m, 0), sx);
-        sy = fmaf(a, S.k(m, 1), sy);
-        sz = fmaf(a, S.k(m, 2), sz);
-      }
-      const float ux = fmaf(h, sx, c.u[0]), uy = fmaf(h, sy, c.u[1]), uz = fmaf(h, sz, c.u[2]);
-      const float3 B = field<NodeT>(p, c, h * ox, h * oy, h * oz);
-      S.u(j, 0) = ux;
-      S.u(j, 1) = uy;
-      S.u(j, 2) = uz;
-      S.k(j, 0) = c.kap * (uy * B.z - uz * B.y);
-      S.k(j, 1) = c.kap * (uz * B.x - ux * B.z);
-      S.k(j, 2) = c.kap * (ux * B.y - uy * B.x);
-    }
+    constexpr float A21 = (float)ck::a21, A31 = (float)ck::a31, A32 = (float)ck::a32;
+    constexpr float A41 = (float)ck::a41, A42 = (float)ck::a42, A43 = (float)ck::a43;
+    constexpr float A51 = (float)ck::a51, A52 = (float)ck::a52, A53 = (float)ck::a53,
+                    A54 = (float)ck::a54;
+    constexpr float A61 = (float)ck::a61, A62 = (float)ck::a62, A63 = (float)ck::a63,
+                    A64 = (float)ck::a64, A65 = (float)ck::a65;
     constexpr float W1 = (float)ck::w1, W3 = (float)ck::w3, W4 = (float)ck::w4,
                     W6 = (float)ck::w6;
     constexpr float D1 = (float)ck::d1, D3 = (float)ck::d3, D4 = (float)ck::d4,
                     D5 = (float)ck::d5, D6 = (float)ck::d6;
-    float e[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      c.dx[i] = h * (W1 * S.u(0, i) + W3 * S.u(2, i) + W4 * S.u(3, i) + W6 * S.u(5, i));
-      c.u5[i] = fmaf(h, W1 * S.k(0, i) + W3 * S.k(2, i) + W4 * S.k(3, i) + W6 * S.k(5, i), c.u[i]);
-      e[i] = h * (D1 * S.k(0, i) + D3 * S.k(2, i) + D4 * S.k(3, i) + D5 * S.k(4, i) +
-                  D6 * S.k(5, i));
-    }
+    const float h = c.hf, kap = c.kap;
+    const float3 u1 = make_float3(c.u[0], c.u[1], c.u[2]);
+    const float3 k1 = c.k1;
+    auto comb = [](float a, float3 x, float b, float3 y) {
+      return make_float3(fmaf(a, x.x, b * y.x), fmaf(a, x.y, b * y.y), fmaf(a, x.z, b * y.z));
+    };
+    auto madd = [](float a, float3 x, float3 y) {
+      return make_float3(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z));
+    };
+    auto stage = [&](float3 osum, float3 ksum, float3& u_out) {
+      u_out = madd(h, ksum, u1);
+      return force(kap, u_out.x, u_out.y, u_out.z,
+                   field<NodeT>(p, c, h * osum.x, h * osum.y, h * osum.z));
+    };
+    float3 u2, u3, u4, u5, u6;
+    const float3 k2 = stage(make_float3(A21 * u1.x, A21 * u1.y, A21 * u1.z),
+                            make_float3(A21 * k1.x, A21 * k1.y, A21 * k1.z), u2);
+    const float3 k3 = stage(comb(A31, u1, A32, u2), comb(A31, k1, A32, k2), u3);
+    const float3 k4 = stage(madd(A43, u3, comb(A41, u1, A42, u2)),
+                            madd(A43, k3, comb(A41, k1, A42, k2)), u4);
+    const float3 k5 = stage(madd(A54, u4, madd(A53, u3, comb(A51, u1, A52, u2))),
+                            madd(A54, k4, madd(A53, k3, comb(A51, k1, A52, k2))), u5);
+    const float3 k6 =
+        stage(madd(A65, u5, madd(A64, u4, madd(A63, u3, comb(A61, u1, A62, u2)))),
+              madd(A65, k5, madd(A64, k4, madd(A63, k3, comb(A61, k1, A62, k2)))), u6);
+    const float3 dsum = madd(W6, u6, madd(W4, u4, comb(W1, u1, W3, u3)));
+    const float3 usum = madd(W6, k6, madd(W4, k4, comb(W1, k1, W3, k3)));
+    const float3 esum = madd(D6, k6, madd(D5, k5, madd(D4, k4, comb(D1, k1, D3, k3))));
+    c.dx[0] = h * dsum.x;
+    c.dx[1] = h * dsum.y;
+    c.dx[2] = h * dsum.z;
+    c.u5[0] = fmaf(h, usum.x, u1.x);
+    c.u5[1] = fmaf(h, usum.y, u1.y);
+    c.u5[2] = fmaf(h, usum.z, u1.z);
+    const float e[3] = {h * esum.x, h * esum.y, h * esum.z};
     // Error norm: the binary32 sum of squares is within a few ulp of the
     // binary64 one, so it decides acceptance exactly as binary64 does except
     // in a +-1e-5 band around the tolerance, where the binary64 norm decides.
@@ -1035,6 +1068,10 @@ struct PolicyMixedT {
   }
 
   __device__ __forceinline__ static void suspend(Lane& c) { c.hn = c.hf; }
+
+  __device__ __forceinline__ static uint32_t key(const KParams& p, const Lane& c) {
+    return brick_key(c.cell[0], c.cell[1], c.cell[2], p.key_shift);
+  }
 };
 
 using PolicyMixed = PolicyMixedT<false>;
@@ -1119,7 +1156,10 @@ __global__ void __launch_bounds__(Bounds<Policy>::kThreads, MINB)
         } else if (slice_steps >= p.slice) {
           Policy::store(st, c);
           const unsigned long long qo = atomicAdd(&dc->q_out, 1ull);
-          if (qo < p.capacity) p.queue_out[qo] = c.slot;
+          if (qo < p.capacity) {
+            p.queue_out[qo] = c.slot;
+            p.keys_out[qo] = Policy::key(p, c);
+          }
           has = false;
         }
       }
@@ -1162,20 +1202,25 @@ __global__ void __launch_bounds__(Bounds<Policy>::kThreads, MINB)
 
 template <class Policy>
 size_t smem_bytes(int block) {
-  return (size_t)kStageSlots * (size_t)block * sizeof(typename Policy::Real);
+  return Policy::kSharedStages ? (size_t)kStageSlots * (size_t)block * sizeof(typename Policy::Real)
+                               : 0;
 }
 
 template <class Policy, int MINB>
 cudaError_t launch_policy(const KParams& kp, const DevState& st, DevCounters* dc, int grid,
                           int block, cudaStream_t s) {
   const size_t sm = smem_bytes<Policy>(block);
+  // without shared stage storage, give the whole unified L1 to the gathers
+  const int carveout = sm ? -1 : 0;
   if (kp.f.dtype == CRP_F32) {
     auto k = propagate_kernel<Policy, float4, MINB>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, carveout);
     k<<<grid, block, sm, s>>>(kp, st, dc);
   } else {
     auto k = propagate_kernel<Policy, DNode, MINB>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, carveout);
     k<<<grid, block, sm, s>>>(kp, st, dc);
   }
   return cudaGetLastError();
