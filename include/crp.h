@@ -296,6 +296,27 @@ crp_status crp_collect(crp_context* ctx, int32_t what, crp_record* out, size_t c
 crp_status crp_histogram_energy(crp_context* ctx, int32_t what, double e_lo, double e_hi,
                                 int32_t nbins, uint64_t* out, void* stream);
 
+/* The same histogram without allocating anything.  This entry point has no
+ * counterpart in the paper: it is for callers that cannot allocate device
+ * memory while they run -- their device memory is handed out entirely by
+ * another allocator, an allocation failure part way through is not
+ * acceptable to them, or they must avoid the device-wide synchronisation
+ * that freeing memory can cause.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine: the bins are one fixed device array of
+ * CRP_HIST_NOALLOC_MAX_BINS 64-bit counters (32 KiB), present on every GPU
+ * that loads the library until the process exits.
+ *   - nbins above CRP_HIST_NOALLOC_MAX_BINS is rejected with CRP_E_INVALID.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture on the device.
+ *   - Every call shares the one array: the call clears the bins it uses,
+ *     the array keeps the last call's counts, and calls that overlap on the
+ *     GPU (other streams, other threads) race with each other.
+ *   - Results equal crp_histogram_energy's.  Synchronises `stream`. */
+#define CRP_HIST_NOALLOC_MAX_BINS 4096
+crp_status crp_histogram_energy_noalloc(crp_context* ctx, int32_t what, double e_lo, double e_hi,
+                                        int32_t nbins, uint64_t* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,6 +23,7 @@ UNITS = {
     "tables.cu": [],
     "propagate_fp64.cu": ["-fmad=false"],
     "propagate_mixed.cu": [],
+    "hist_noalloc.cu": [],
 }
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -110,7 +110,7 @@ SYMBOLS = (
     "crp_grid_create", "crp_grid_destroy", "crp_grid_copy_out",
     "crp_tables_build", "crp_tables_from_host", "crp_tables_copy_out", "crp_tables_destroy",
     "crp_candidates_inject", "crp_candidates_clear",
-    "crp_propagate", "crp_collect", "crp_histogram_energy",
+    "crp_propagate", "crp_collect", "crp_histogram_energy", "crp_histogram_energy_noalloc",
 )
 
 _lock = threading.Lock()
@@ -147,6 +147,7 @@ def lib():
             L.crp_propagate.argtypes = [p, p, C.POINTER(Modules), p, C.POINTER(Stats)]
             L.crp_collect.argtypes = [p, i32, p, sz, C.POINTER(sz), i32, p]
             L.crp_histogram_energy.argtypes = [p, i32, C.c_double, C.c_double, i32, p, p]
+            L.crp_histogram_energy_noalloc.argtypes = [p, i32, C.c_double, C.c_double, i32, p, p]
             for name in SYMBOLS:
                 if name not in ("crp_last_error", "crp_version"):
                     getattr(L, name).restype = st
@@ -300,6 +301,18 @@ def crp_collect(ctx, what=COLLECT_ALL, out=None, stream=None):
 def crp_histogram_energy(ctx, what, e_lo, e_hi, nbins, stream=None):
     out = np.zeros(nbins, dtype=np.uint64)
     _check(lib().crp_histogram_energy(ctx, what, e_lo, e_hi, nbins, out.ctypes.data, stream))
+    return out
+
+
+HIST_NOALLOC_MAX_BINS = 4096
+
+
+def crp_histogram_energy_noalloc(ctx, what, e_lo, e_hi, nbins, stream=None):
+    """crp_histogram_energy counted into the library's fixed device array
+    (no device allocation; nbins <= HIST_NOALLOC_MAX_BINS)."""
+    out = np.zeros(nbins, dtype=np.uint64)
+    _check(lib().crp_histogram_energy_noalloc(ctx, what, e_lo, e_hi, nbins, out.ctypes.data,
+                                              stream))
     return out
 
 

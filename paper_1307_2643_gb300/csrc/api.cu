@@ -1139,3 +1139,15 @@ crp_status crp_histogram_energy(crp_context* c, int32_t what, double e_lo, doubl
 
 static_assert(sizeof(crp_record) == 208, "crp_record layout");
 static_assert(sizeof(crp_stats) == 96, "crp_stats layout");
+
+// Read-only view of a context's pool for other translation units of the
+// library (status and energy arrays, pool size, device).
+namespace crp {
+void context_view(const crp_context* c, const int32_t** status, const double** E, uint64_t* n,
+                  int* device) {
+  *status = c->st.status;
+  *E = c->st.E;
+  *n = c->pool ? c->size : 0;
+  *device = c->device;
+}
+}  // namespace crp
