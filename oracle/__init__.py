@@ -108,7 +108,7 @@ def lib():
             L.orc_uniform_open.restype = d
             L.orc_child_id.argtypes = [u64, u32]
             L.orc_child_id.restype = u64
-            for name in ("orc_phi_pair", "orc_series_log"):
+            for name in ("orc_phi_pair", "orc_series_log", "orc_series_exp"):
                 getattr(L, name).argtypes = [d]
                 getattr(L, name).restype = d
             L.orc_planck_density.argtypes = [d, d]
@@ -126,6 +126,12 @@ def lib():
                 [p, i64, C.POINTER(i64), C.c_int]
             L.orc_propagate.restype = C.c_int
             L.orc_field_at.argtypes = [C.POINTER(Params), p, i64, p, p]
+            L.orc_ang2pix.argtypes = [i64, d, d]
+            L.orc_ang2pix.restype = i64
+            L.orc_pix2ang.argtypes = [i64, i64, C.POINTER(d), C.POINTER(d)]
+            L.orc_ang2pix_vec.argtypes = [i64, i64, p, p]
+            L.orc_uniform_pairs.argtypes = [u64, u32, u32, i64, p, p]
+            L.orc_series_log_vec.argtypes = [i64, p, p]
             L.orc_table_axis.argtypes = [i64, d, d, C.POINTER(d), C.POINTER(d)]
             _lib = L
     return _lib
@@ -168,12 +174,51 @@ def uniform_open(lo: int, hi: int) -> float:
     return lib().orc_uniform_open(lo, hi)
 
 
+def uniform_pairs(seed: int, tag: int, draw: int, ids) -> np.ndarray:
+    """[n, 2] open uniforms of Philox draw `draw` / `tag` for each id."""
+    ids = np.ascontiguousarray(ids, dtype=np.uint64)
+    out = np.zeros((len(ids), 2))
+    lib().orc_uniform_pairs(seed, tag, draw, len(ids), _ptr(ids), _ptr(out))
+    return out
+
+
 def child_id(parent: int, event_index: int) -> int:
     return lib().orc_child_id(parent, event_index)
 
 
 def series_log(x: float) -> float:
     return lib().orc_series_log(x)
+
+
+def series_log_vec(x) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros_like(x)
+    lib().orc_series_log_vec(len(x), _ptr(x), _ptr(out))
+    return out
+
+
+def series_exp(x: float) -> float:
+    return lib().orc_series_exp(x)
+
+
+def ang2pix(nside: int, z: float, phi: float) -> int:
+    """HEALPix RING pixel of the direction (z = cos theta, phi)."""
+    return lib().orc_ang2pix(nside, z, phi)
+
+
+def pix2ang(nside: int, pix: int):
+    """(z, phi) of the centre of HEALPix RING pixel `pix`."""
+    z, phi = C.c_double(), C.c_double()
+    lib().orc_pix2ang(nside, pix, C.byref(z), C.byref(phi))
+    return z.value, phi.value
+
+
+def ang2pix_vec(nside: int, u) -> np.ndarray:
+    """HEALPix RING pixels of unit vectors u [n, 3]."""
+    u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros(len(u), dtype=np.int64)
+    lib().orc_ang2pix_vec(nside, len(u), _ptr(u), _ptr(out))
+    return out
 
 
 def phi_pair(k: float) -> float:

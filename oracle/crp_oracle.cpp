@@ -160,6 +160,105 @@ double series_log(double x) {
   return (double)k * 0.69314718055994530942 + ln_m;
 }
 
+// Exponential for the analytic galactic field, written out so that an
+// independent binary64 implementation reproduces it bit for bit (reading:
+// as for the logarithm, a library exp may differ by an ulp).  Range
+// reduction x = k ln2 + r with k = nearest integer of x/ln2, ln2 split in a
+// 32-bit high part (k * high is exact) and a low part (Cody & Waite),
+// |r| <= ln2/2; e^r by its
+// Taylor series to r^13/13! (Horner; tail below 1e-17); 2^k applied by
+// building the exponent field.  Valid for -700 <= x <= 700.
+double series_exp(double x) {
+  if (x < -700.0) return 0.0;
+  const double ln2_hi = 2977044472.0 / 4294967296.0;  // ln 2 to 32 bits (exact)
+  const double ln2_lo = -4.2009150726810847e-11;       // ln 2 - ln2_hi
+  double kd = std::floor(x * 1.4426950408889634074 + 0.5);
+  double r = (x - kd * ln2_hi) - kd * ln2_lo;
+  double poly = 1.0 / 6227020800.0;                 // 1/13!
+  poly = poly * r + 1.0 / 479001600.0;              // 1/12!
+  poly = poly * r + 1.0 / 39916800.0;
+  poly = poly * r + 1.0 / 3628800.0;
+  poly = poly * r + 1.0 / 362880.0;
+  poly = poly * r + 1.0 / 40320.0;
+  poly = poly * r + 1.0 / 5040.0;
+  poly = poly * r + 1.0 / 720.0;
+  poly = poly * r + 1.0 / 120.0;
+  poly = poly * r + 1.0 / 24.0;
+  poly = poly * r + 1.0 / 6.0;
+  poly = poly * r + 1.0 / 2.0;
+  poly = poly * r + 1.0;
+  poly = poly * r + 1.0;
+  int k = (int)kd;
+  uint64_t bits = (uint64_t)(k + 1023) << 52;
+  double scale;
+  std::memcpy(&scale, &bits, sizeof(scale));
+  return poly * scale;
+}
+
+// ---------------------------------------------------------------------------
+// HEALPix RING scheme (K. M. Gorski et al., "HEALPix: a framework for high
+// resolution discretization and fast analysis of data distributed on the
+// sphere", ApJ 622, 759 (2005)): 12 nside^2 equal-area pixels; rings of
+// constant z = cos(theta); polar caps |z| > 2/3 and the equatorial belt.
+// Pixel index of a unit direction, and the centre of a pixel.
+// ---------------------------------------------------------------------------
+int64_t healpix_ang2pix_ring(int64_t nside, double z, double phi) {
+  const double pi = kPi;
+  const double twopi = 2.0 * kPi;
+  phi = std::fmod(phi, twopi);
+  if (phi < 0.0) phi += twopi;
+  const double tt = phi / (0.5 * pi);               // in [0, 4)
+  const double za = std::fabs(z);
+  const int64_t ncap = 2 * nside * (nside - 1);
+  const int64_t npix = 12 * nside * nside;
+  if (za <= 2.0 / 3.0) {                           // equatorial belt
+    const double t1 = (double)nside * (0.5 + tt);
+    const double t2 = (double)nside * z * 0.75;
+    const int64_t jp = (int64_t)std::floor(t1 - t2);  // ascending edge line
+    const int64_t jm = (int64_t)std::floor(t1 + t2);  // descending edge line
+    const int64_t ir = nside + 1 + jp - jm;            // ring index from z = 2/3, 1..2nside+1
+    const int64_t kshift = 1 - (ir & 1);
+    int64_t ip = (jp + jm - nside + kshift + 1) / 2;
+    ip = ((ip % (4 * nside)) + 4 * nside) % (4 * nside);
+    return ncap + (ir - 1) * 4 * nside + ip;
+  }
+  const double tp = tt - std::floor(tt);
+  const double tmp = (double)nside * std::sqrt(3.0 * (1.0 - za));
+  const int64_t jp = (int64_t)std::floor(tp * tmp);
+  const int64_t jm = (int64_t)std::floor((1.0 - tp) * tmp);
+  const int64_t ir = jp + jm + 1;                  // ring index from the pole
+  int64_t ip = (int64_t)std::floor(tt * (double)ir);
+  ip = ((ip % (4 * ir)) + 4 * ir) % (4 * ir);
+  if (z > 0.0) return 2 * ir * (ir - 1) + ip;
+  return npix - 2 * ir * (ir + 1) + ip;
+}
+
+void healpix_pix2ang_ring(int64_t nside, int64_t pix, double* z, double* phi) {
+  const double pi = kPi;
+  const int64_t ncap = 2 * nside * (nside - 1);
+  const int64_t npix = 12 * nside * nside;
+  const double fact2 = 4.0 / (double)npix;
+  if (pix < ncap) {                                 // north polar cap
+    const int64_t iring = (int64_t)((1.0 + std::sqrt(1.0 + 2.0 * (double)pix)) * 0.5);
+    const int64_t iphi = pix + 1 - 2 * iring * (iring - 1);
+    *z = 1.0 - (double)(iring * iring) * fact2;
+    *phi = ((double)iphi - 0.5) * pi / (2.0 * (double)iring);
+  } else if (pix < npix - ncap) {                   // equatorial belt
+    const int64_t ip = pix - ncap;
+    const int64_t iring = ip / (4 * nside) + nside; // counted from the north pole
+    const int64_t iphi = ip % (4 * nside) + 1;
+    const double fodd = ((iring + nside) & 1) ? 1.0 : 0.5;
+    *z = (double)(2 * nside - iring) * 2.0 / (3.0 * (double)nside);
+    *phi = ((double)iphi - fodd) * pi / (2.0 * (double)nside);
+  } else {                                          // south polar cap
+    const int64_t ip = npix - pix;
+    const int64_t iring = (int64_t)((1.0 + std::sqrt(2.0 * (double)ip - 1.0)) * 0.5);
+    const int64_t iphi = 4 * iring + 1 - (ip - 2 * iring * (iring - 1));
+    *z = -1.0 + (double)(iring * iring) * fact2;
+    *phi = ((double)iphi - 0.5) * pi / (2.0 * (double)iring);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Photon field: Planck spectrum of the CMB.
 // n(eps) = eps^2 / (pi^2 (hbar c)^3 (exp(eps/kT) - 1))   [1 / (m^3 eV)]
@@ -460,9 +559,33 @@ void orc_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out) 
   for (int i = 0; i < 4; ++i) out[i] = r.w[i];
 }
 double orc_uniform_open(uint32_t lo, uint32_t hi) { return uniform_open(lo, hi); }
+// Two uniforms (words 0,1 and 2,3) of draw `draw` with `tag` for each id.
+void orc_uniform_pairs(uint64_t seed, uint32_t tag, uint32_t draw, int64_t n, const uint64_t* ids,
+                       double* out) {
+  for (int64_t i = 0; i < n; ++i) {
+    Words4 w = draw_words(seed, tag, ids[i], draw);
+    out[2 * i] = uniform_open(w.w[0], w.w[1]);
+    out[2 * i + 1] = uniform_open(w.w[2], w.w[3]);
+  }
+}
 uint64_t orc_child_id(uint64_t parent, uint32_t ev) { return child_id(parent, ev); }
 double orc_phi_pair(double k) { return phi_pair(k); }
 double orc_series_log(double x) { return series_log(x); }
+void orc_series_log_vec(int64_t n, const double* x, double* out) {
+  for (int64_t i = 0; i < n; ++i) out[i] = series_log(x[i]);
+}
+double orc_series_exp(double x) { return series_exp(x); }
+int64_t orc_ang2pix(int64_t nside, double z, double phi) { return healpix_ang2pix_ring(nside, z, phi); }
+void orc_pix2ang(int64_t nside, int64_t pix, double* z, double* phi) {
+  healpix_pix2ang_ring(nside, pix, z, phi);
+}
+// Vectorised forms for the lens oracle.
+void orc_ang2pix_vec(int64_t nside, int64_t n, const double* u, int64_t* out) {
+  for (int64_t i = 0; i < n; ++i) {
+    const double x = u[3 * i], y = u[3 * i + 1], z = u[3 * i + 2];
+    out[i] = healpix_ang2pix_ring(nside, z, std::atan2(y, x));
+  }
+}
 double orc_planck_density(double eps, double kT) { return planck_density(eps, kT); }
 double orc_beta_pair_proton(double gamma, double T) { return beta_pair_proton(gamma, kKB * T); }
 double orc_rate_pion_nucleon(double gamma, double T, double sigma0_mb, double eps_th_eV) {
@@ -642,13 +765,13 @@ void galactic_field(const orc_params& P, const double x[3], double B[3]) {
   double az = std::fabs(z);
   double b_r = 0.0, b_phi = 0.0;
   if (r >= P.gal_disk_rmin && r <= P.gal_disk_rmax) {
-    double bd = P.gal_disk_b * std::exp(-az / P.gal_disk_hz);
+    double bd = P.gal_disk_b * series_exp(-az / P.gal_disk_hz);
     b_r += bd * std::sin(P.gal_disk_pitch_rad);
     b_phi += bd * std::cos(P.gal_disk_pitch_rad);
   }
   if (z != 0.0) {
     double dz = az - P.gal_halo_z0;
-    double bh = P.gal_halo_b * std::exp(-dz * dz / (2.0 * P.gal_halo_sigma * P.gal_halo_sigma));
+    double bh = P.gal_halo_b * series_exp(-dz * dz / (2.0 * P.gal_halo_sigma * P.gal_halo_sigma));
     b_phi += z > 0.0 ? bh : -bh;
   }
   B[0] = b_r * cr - b_phi * sr;

@@ -480,3 +480,85 @@ def test_series_log_against_library(oracle):
         got, want = oracle.series_log(float(x)), math.log(float(x))
         assert abs(got - want) <= 4 * np.spacing(abs(want)) + 1e-300, (x, got, want)
     assert oracle.series_log(1.0) == 0.0
+
+
+def test_series_exp_against_library(oracle):
+    g = np.random.default_rng(4)
+    xs = np.concatenate([g.uniform(-700, 0, 20000), g.uniform(-5, 5, 20000), [0.0, -1e-300, 1.0]])
+    for x in xs:
+        got, want = oracle.series_exp(float(x)), math.exp(float(x))
+        assert abs(got - want) <= 4 * np.spacing(want), (x, got, want)
+    assert oracle.series_exp(0.0) == 1.0
+    assert oracle.series_exp(-800.0) == 0.0
+
+
+# ---------------------------------------------------------------------------
+# HEALPix RING (Gorski et al., ApJ 622, 759, 2005)
+# ---------------------------------------------------------------------------
+def test_healpix_round_trip_and_ring_structure(oracle):
+    for nside in (1, 2, 4, 16, 64):
+        npix = 12 * nside * nside
+        zs = np.empty(npix)
+        for p in range(npix):
+            z, phi = oracle.pix2ang(nside, p)
+            assert oracle.ang2pix(nside, z, phi) == p
+            zs[p] = z
+        # rings of constant z: 4 nside - 1 rings; pixel z decreasing with index
+        rings = np.unique(np.round(zs, 12))
+        assert len(rings) == 4 * nside - 1
+        assert np.all(np.diff(zs) <= 1e-12)
+    # nside = 1: 4 pixels per ring at z = 2/3, 0, -2/3
+    z = [oracle.pix2ang(1, p)[0] for p in range(12)]
+    assert np.allclose(z, [2 / 3] * 4 + [0.0] * 4 + [-2 / 3] * 4)
+
+
+def test_healpix_equal_area(oracle):
+    """Uniform directions fill the 12 nside^2 pixels equally (equal-area
+    property): chi-square of the counts is consistent with uniform."""
+    from scipy.stats import chisquare
+    nside = 16
+    g = np.random.default_rng(8)
+    v = g.normal(size=(600000, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    pix = oracle.ang2pix_vec(nside, v)
+    counts = np.bincount(pix, minlength=12 * nside * nside)
+    assert chisquare(counts).pvalue > 1e-3
+    # a direction maps to the pixel whose centre is nearest (within a pixel size)
+    sub = v[:5000]
+    for u, p in zip(sub, pix[:5000]):
+        z, phi = oracle.pix2ang(nside, int(p))
+        c = np.array([np.sqrt(1 - z * z) * np.cos(phi), np.sqrt(1 - z * z) * np.sin(phi), z])
+        assert np.degrees(np.arccos(np.clip(c @ u, -1, 1))) < 2.0 * 58.6 / nside
+
+
+def test_lens_zero_field_is_identity(oracle):
+    """In a zero field back-tracked antiparticles fly straight: every sample
+    leaves through its own arrival pixel, so the lens is the identity on
+    pixels and a candidate is always observed in its own pixel or shadowed."""
+    import oracle.lens as L
+    import workloads as W
+    nside, nb = 4, 2
+    dirs, E, bins = W.lens_samples(nb, 192 * 3, 1e18, 1e20, 1)
+    P = oracle.make_params(grid_n=(4, 4, 4), spacing=10.0, origin=(-20, -20, -20), tol=1e-4,
+                           h_min=0.001, h_max=0.05, field_unit_T=oracle.MICROGAUSS_T,
+                           length_unit_m=oracle.KPC_M, flags=oracle.BORDER, border_r=20.0)
+    n = len(E)
+    r = oracle.propagate(P, np.zeros((4, 4, 4, 3)), dict(
+        id=np.arange(n, dtype=np.uint64), x=np.full(n, -8.5), y=np.zeros(n), z=np.zeros(n),
+        ux=dirs[:, 0].copy(), uy=dirs[:, 1].copy(), uz=dirs[:, 2].copy(), E=E,
+        A=np.ones(n, np.int32), Z=np.ones(n, np.int32), q=-np.ones(n, np.int32)))
+    assert np.all(r["status"] == oracle.AT_BORDER)
+    lens = L.build(nside, nb, bins, dirs, r)
+    npix = 12 * nside * nside
+    for c in range(nb * npix):
+        col = lens["entries"][lens["col_start"][c]:lens["col_start"][c + 1]]
+        assert np.all(col == c % npix)
+    g = np.random.default_rng(0)
+    u = g.normal(size=(2000, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    Ev = 10 ** g.uniform(18, 20, 2000)
+    out = L.apply(lens, nside, 1e18, 1e20, nb, 9, np.arange(2000, dtype=np.uint64), u, Ev,
+                  np.ones(2000, np.int32))
+    seen = out < npix
+    assert seen.mean() > 0.3
+    assert np.array_equal(out[seen], oracle.ang2pix_vec(nside, -u)[seen])

@@ -132,3 +132,40 @@ def subsample(inj: dict, idx) -> dict:
     """Candidates with the given indices (ids are kept, so every stochastic
     history is the same as in the full run)."""
     return {k: np.ascontiguousarray(v[idx]) for k, v in inj.items()}
+
+
+GALACTIC_LENS = dict(       # back-tracking through a synthetic galactic field (kpc, microgauss)
+    name="galactic_backtrack_256cube_f32_disk_halo_random",
+    grid_n=(256, 256, 256), box=40.0, brms=3.0, lmax=2.0, field_dtype="f32",
+    disk=dict(disk_b=2.0, disk_pitch_rad=11.5 * np.pi / 180.0, disk_hz=1.0, disk_rmin=3.0,
+              disk_rmax=20.0, halo_b=1.0, halo_z0=1.5, halo_sigma=1.0, center=(0.0, 0.0, 0.0)),
+    earth=(-8.5, 0.0, 0.0), border_r=20.0, tol=1e-4, h_min=0.001, h_max=0.05,
+    r_lo=1e18, r_hi=1e20, n_bins=100, nside=64, seed=MASTER_SEED + 4,
+)
+
+
+def galactic_grid_geometry(n=256, box=40.0):
+    """Node spacing, lmin (= 2 spacings) and origin of a periodic random-field
+    grid of n^3 nodes filling a cube of side `box` centred on the Galactic centre."""
+    spacing = box / n
+    return spacing, 2.0 * spacing, (-0.5 * box, -0.5 * box, -0.5 * box)
+
+
+def lens_samples(n_bins, per_bin, r_lo, r_hi, seed):
+    """Isotropic arrival directions, per_bin per rigidity bin; each sample at
+    its bin's geometric-centre rigidity (energy of a proton, eV)."""
+    g = rng(seed)
+    n = n_bins * per_bin
+    ux, uy, uz = isotropic(g, n)
+    edges = np.exp(np.linspace(np.log(r_lo), np.log(r_hi), n_bins + 1))
+    centres = np.sqrt(edges[:-1] * edges[1:])
+    bins = np.repeat(np.arange(n_bins, dtype=np.int32), per_bin)
+    return np.stack([ux, uy, uz], axis=1), centres[bins], bins
+
+
+def backtrack_directions(n, r_lo, r_hi, seed):
+    """Isotropic arrival directions with rigidities log-uniform in [r_lo, r_hi]."""
+    g = rng(seed)
+    ux, uy, uz = isotropic(g, n)
+    R = np.exp(g.uniform(np.log(r_lo), np.log(r_hi), n))
+    return np.stack([ux, uy, uz], axis=1), R
