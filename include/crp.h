@@ -53,6 +53,7 @@ typedef int32_t crp_status;
 typedef struct crp_context crp_context;
 typedef struct crp_grid crp_grid;
 typedef struct crp_tables crp_tables;
+typedef struct crp_lens crp_lens;
 
 /* Message describing the calling thread's last failed call ("" if none). */
 const char* crp_last_error(void);
@@ -290,6 +291,59 @@ typedef struct {
  * out = NULL with capacity 0 only counts (size query). */
 crp_status crp_collect(crp_context* ctx, int32_t what, crp_record* out, size_t capacity,
                        size_t* n_out, int32_t out_on_device, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Galactic lens (Sect. 4, "Galactic propagation": transformation matrices,
+ * one per energy bin, map the directions of cosmic rays at the border of
+ * the Galaxy to the directions observed at Earth; built by tracking through
+ * a galactic field model).
+ *
+ * Build: antiparticles (charge sign -1, A = Z = 1) leave `earth` along the
+ * sample arrival directions dirs[k] with energy E[k] (eV; rigidity E/e) and
+ * are propagated with `m` (which must include CRP_BORDER) through `galaxy`
+ * in a private pool (the context's own candidates are not touched).  A
+ * sample that reaches the border adds its Earth pixel i (HEALPix RING pixel
+ * of dirs[k]) to column j (pixel of its direction at the border) of bin
+ * bin[k].  Columns keep their samples' Earth pixels sorted ascending.
+ * Apply: for each selected candidate with Z > 0, rigidity R = E/Z picks bin
+ * b = floor((ln R - ln r_lo) * n_bins / (ln r_hi - ln r_lo)) clamped to the
+ * first / last bin, and the arrival direction -u picks column j.  With the
+ * uniforms (u1, u2) of Philox draw 0, tag 3 of the candidate's id it is
+ * observed if u1 * max_b < count_j (max_b: largest column count of the
+ * bin), at Earth pixel entries[min(floor(u2 count_j), count_j - 1)];
+ * otherwise lens_pixel = CRP_LENS_NOT_OBSERVED.  Neutral candidates get
+ * CRP_LENS_NOT_APPLIED.  The result is in crp_record.lens_pixel.
+ * ---------------------------------------------------------------------- */
+#define CRP_LENS_NOT_APPLIED 0xFFFFFFFFu
+#define CRP_LENS_NOT_OBSERVED 0xFFFFFFFEu
+
+typedef struct {
+  int32_t nside;             /* HEALPix resolution (RING), 1..8192 */
+  int32_t n_bins;            /* rigidity bins, log-uniform edges over [r_lo, r_hi] */
+  double r_lo, r_hi;         /* rigidity range [V] */
+  double earth[3];           /* observer position (length unit of m) */
+  const double* dirs;        /* host [n_samples][3] unit arrival directions */
+  const double* E;           /* host [n_samples] energies [eV] */
+  const int32_t* bin;        /* host [n_samples] rigidity bin of each sample */
+  int64_t n_samples;
+} crp_lens_desc;
+
+crp_status crp_lens_build(crp_context* ctx, const crp_grid* galaxy, const crp_modules* m,
+                          const crp_lens_desc* d, crp_lens** out, crp_stats* stats_out);
+crp_status crp_lens_apply(crp_context* ctx, const crp_lens* lens, int32_t what, void* stream);
+/* Copy the lens to host memory: col_start (n_bins * 12 nside^2 + 1 entries,
+ * columns ordered by bin then border pixel), entries (*n_entries), max_count
+ * (n_bins).  Any of the three arrays may be NULL. */
+crp_status crp_lens_copy_out(const crp_lens* lens, uint32_t* col_start, uint32_t* entries,
+                             uint32_t* max_count, int64_t* n_entries);
+crp_status crp_lens_destroy(crp_lens* lens);
+
+/* HEALPix RING arrival map of the selected records: source 0 counts the
+ * arrival direction -u at the candidate (extragalactic sky), source 1 the
+ * lens_pixel (sky at Earth; shadowed / not applied are skipped).  out: host
+ * uint64 array of 12 nside^2 bins. */
+crp_status crp_histogram_healpix(crp_context* ctx, int32_t what, int32_t nside, int32_t source,
+                                 uint64_t* out, void* stream);
 
 /* Histogram over the selected records: nbins log-uniform bins of E over
  * [e_lo, e_hi) (under/overflow dropped).  out: host uint64 array of nbins. */

@@ -24,9 +24,11 @@ UNITS = {
     "propagate_fp64.cu": ["-fmad=false"],
     "propagate_mixed.cu": [],
     "hist_noalloc.cu": [],
+    "lens.cu": [],
 }
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+          "-Xcompiler", "-ffp-contract=off",
           "-I", os.path.join(ROOT, "include")]
 
 

@@ -77,6 +77,12 @@ class Modules(C.Structure):
                 ("blocks_per_sm", C.c_int32), ("slice", C.c_uint32), ("spatial_sort", C.c_int32)]
 
 
+class LensDesc(C.Structure):
+    _fields_ = [("nside", C.c_int32), ("n_bins", C.c_int32), ("r_lo", C.c_double),
+                ("r_hi", C.c_double), ("earth", C.c_double * 3), ("dirs", C.c_void_p),
+                ("E", C.c_void_p), ("bin", C.c_void_p), ("n_samples", C.c_int64)]
+
+
 class Stats(C.Structure):
     _fields_ = [("accepted_steps", C.c_uint64), ("rejected_trials", C.c_uint64),
                 ("rhs_evals", C.c_uint64), ("n_pion", C.c_uint64), ("n_pd", C.c_uint64),
@@ -111,6 +117,8 @@ SYMBOLS = (
     "crp_tables_build", "crp_tables_from_host", "crp_tables_copy_out", "crp_tables_destroy",
     "crp_candidates_inject", "crp_candidates_clear",
     "crp_propagate", "crp_collect", "crp_histogram_energy", "crp_histogram_energy_noalloc",
+    "crp_lens_build", "crp_lens_apply", "crp_lens_copy_out", "crp_lens_destroy",
+    "crp_histogram_healpix",
 )
 
 _lock = threading.Lock()
@@ -148,6 +156,12 @@ def lib():
             L.crp_collect.argtypes = [p, i32, p, sz, C.POINTER(sz), i32, p]
             L.crp_histogram_energy.argtypes = [p, i32, C.c_double, C.c_double, i32, p, p]
             L.crp_histogram_energy_noalloc.argtypes = [p, i32, C.c_double, C.c_double, i32, p, p]
+            L.crp_lens_build.argtypes = [p, p, C.POINTER(Modules), C.POINTER(LensDesc), C.POINTER(p),
+                                         C.POINTER(Stats)]
+            L.crp_lens_apply.argtypes = [p, p, i32, p]
+            L.crp_lens_copy_out.argtypes = [p, p, p, p, C.POINTER(C.c_int64)]
+            L.crp_lens_destroy.argtypes = [p]
+            L.crp_histogram_healpix.argtypes = [p, i32, i32, i32, p, p]
             for name in SYMBOLS:
                 if name not in ("crp_last_error", "crp_version"):
                     getattr(L, name).restype = st
@@ -301,6 +315,50 @@ def crp_collect(ctx, what=COLLECT_ALL, out=None, stream=None):
 def crp_histogram_energy(ctx, what, e_lo, e_hi, nbins, stream=None):
     out = np.zeros(nbins, dtype=np.uint64)
     _check(lib().crp_histogram_energy(ctx, what, e_lo, e_hi, nbins, out.ctypes.data, stream))
+    return out
+
+
+LENS_NOT_APPLIED = 0xFFFFFFFF
+LENS_NOT_OBSERVED = 0xFFFFFFFE
+
+
+def crp_lens_build(ctx, galaxy, modules: Modules, nside, n_bins, r_lo, r_hi, earth, dirs, E, bins):
+    """Build a lens by back-tracking; returns (handle, Stats of the back-tracking)."""
+    dirs = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    bins = np.ascontiguousarray(bins, dtype=np.int32)
+    d = LensDesc()
+    d.nside, d.n_bins, d.r_lo, d.r_hi = nside, n_bins, r_lo, r_hi
+    d.earth[:] = earth
+    d.dirs, d.E, d.bin, d.n_samples = dirs.ctypes.data, E.ctypes.data, bins.ctypes.data, len(E)
+    h = C.c_void_p()
+    s = Stats()
+    _check(lib().crp_lens_build(ctx, galaxy, C.byref(modules), C.byref(d), C.byref(h), C.byref(s)))
+    return h, s
+
+
+def crp_lens_apply(ctx, lens, what=COLLECT_ALL, stream=None):
+    _check(lib().crp_lens_apply(ctx, lens, what, stream))
+
+
+def crp_lens_copy_out(lens, n_cols, n_bins):
+    n = C.c_int64()
+    _check(lib().crp_lens_copy_out(lens, None, None, None, C.byref(n)))
+    col = np.zeros(n_cols + 1, np.uint32)
+    ent = np.zeros(max(n.value, 1), np.uint32)
+    mx = np.zeros(n_bins, np.uint32)
+    _check(lib().crp_lens_copy_out(lens, col.ctypes.data, ent.ctypes.data, mx.ctypes.data,
+                                   C.byref(n)))
+    return dict(col_start=col, entries=ent[: n.value], max_count=mx)
+
+
+def crp_lens_destroy(lens):
+    _check(lib().crp_lens_destroy(lens))
+
+
+def crp_histogram_healpix(ctx, what, nside, source, stream=None):
+    out = np.zeros(12 * nside * nside, dtype=np.uint64)
+    _check(lib().crp_histogram_healpix(ctx, what, nside, source, out.ctypes.data, stream))
     return out
 
 

@@ -1140,9 +1140,16 @@ crp_status crp_histogram_energy(crp_context* c, int32_t what, double e_lo, doubl
 static_assert(sizeof(crp_record) == 208, "crp_record layout");
 static_assert(sizeof(crp_stats) == 96, "crp_stats layout");
 
+namespace crp {
+void context_pool(const crp_context* c, DevState* st, uint64_t* n, int* device, uint64_t* seed) {
+  *st = c->st;
+  *n = c->pool ? c->size : 0;
+  *device = c->device;
+  *seed = c->seed;
+}
+
 // Read-only view of a context's pool for other translation units of the
 // library (status and energy arrays, pool size, device).
-namespace crp {
 void context_view(const crp_context* c, const int32_t** status, const double** E, uint64_t* n,
                   int* device) {
   *status = c->st.status;

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <stdint.h>
+#include <string.h>
 
 namespace crp {
 
@@ -82,10 +83,30 @@ constexpr double d1 = -277.0 / 64512.0, d3 = 6925.0 / 370944.0, d4 = -6925.0 / 2
 // Positive normal finite x only.  Written out operation by operation so that
 // a translation unit built without multiply-add contraction reproduces the
 // same bits as any other IEEE binary64 evaluation of the same sequence.
-__device__ __forceinline__ double series_log(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+__host__ __device__ __forceinline__ unsigned long long dbits(double x) {
+#ifdef __CUDA_ARCH__
+  return (unsigned long long)__double_as_longlong(x);
+#else
+  unsigned long long b;
+  memcpy(&b, &x, sizeof(b));
+  return b;
+#endif
+}
+
+__host__ __device__ __forceinline__ double dfrombits(unsigned long long b) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)b);
+#else
+  double x;
+  memcpy(&x, &b, sizeof(x));
+  return x;
+#endif
+}
+
+__host__ __device__ __forceinline__ double series_log(double x) {
+  const unsigned long long b = dbits(x);
   int k = (int)((b >> 52) & 0x7ffull) - 1023;
-  double m = __longlong_as_double((long long)((b & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull));
+  double m = dfrombits((b & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull);
   if (m > 1.4142135623730951) {
     m = m * 0.5;
     k = k + 1;
@@ -108,6 +129,69 @@ __device__ __forceinline__ double series_log(double x) {
   poly = poly * z + 1.0;
   const double ln_m = 2.0 * s * poly;
   return (double)k * 0.69314718055994530942 + ln_m;
+}
+
+// Exponential for the binary64 analytic galactic field, operation by
+// operation: x = k ln2 + r (k nearest integer, ln2 split Cody-Waite style
+// into a 32-bit high part and a low part), e^r by its Taylor series to
+// r^13/13! (Horner), 2^k built in the exponent field.  -700 <= x <= 700.
+__device__ __forceinline__ double series_exp(double x) {
+  if (x < -700.0) return 0.0;
+  const double ln2_hi = 2977044472.0 / 4294967296.0;
+  const double ln2_lo = -4.2009150726810847e-11;
+  const double kd = floor(x * 1.4426950408889634074 + 0.5);
+  const double r = (x - kd * ln2_hi) - kd * ln2_lo;
+  double poly = 1.0 / 6227020800.0;
+  poly = poly * r + 1.0 / 479001600.0;
+  poly = poly * r + 1.0 / 39916800.0;
+  poly = poly * r + 1.0 / 3628800.0;
+  poly = poly * r + 1.0 / 362880.0;
+  poly = poly * r + 1.0 / 40320.0;
+  poly = poly * r + 1.0 / 5040.0;
+  poly = poly * r + 1.0 / 720.0;
+  poly = poly * r + 1.0 / 120.0;
+  poly = poly * r + 1.0 / 24.0;
+  poly = poly * r + 1.0 / 6.0;
+  poly = poly * r + 1.0 / 2.0;
+  poly = poly * r + 1.0;
+  poly = poly * r + 1.0;
+  const int k = (int)kd;
+  const double scale = __longlong_as_double((long long)((unsigned long long)(k + 1023) << 52));
+  return poly * scale;
+}
+
+// HEALPix RING pixel of a direction (Gorski et al., ApJ 622, 759, 2005):
+// 12 nside^2 equal-area pixels; polar caps |z| > 2/3 and the equatorial
+// belt, pixels numbered ring by ring from the north pole.
+__device__ __forceinline__ int64_t healpix_ring_pixel(int64_t nside, double ux, double uy,
+                                                      double uz) {
+  const double halfpi = 1.57079632679489661923;
+  double phi = atan2(uy, ux);
+  if (phi < 0.0) phi += 2.0 * 3.14159265358979323846;
+  const double tt = phi / halfpi;  // [0, 4)
+  const double za = fabs(uz);
+  const int64_t ncap = 2 * nside * (nside - 1);
+  const int64_t npix = 12 * nside * nside;
+  if (za <= 2.0 / 3.0) {
+    const double t1 = (double)nside * (0.5 + tt);
+    const double t2 = (double)nside * uz * 0.75;
+    const int64_t jp = (int64_t)floor(t1 - t2);
+    const int64_t jm = (int64_t)floor(t1 + t2);
+    const int64_t ir = nside + 1 + jp - jm;
+    const int64_t kshift = 1 - (ir & 1);
+    int64_t ip = (jp + jm - nside + kshift + 1) / 2;
+    ip = ((ip % (4 * nside)) + 4 * nside) % (4 * nside);
+    return ncap + (ir - 1) * 4 * nside + ip;
+  }
+  const double tp = tt - floor(tt);
+  const double tmp = (double)nside * sqrt(3.0 * (1.0 - za));
+  const int64_t jp = (int64_t)floor(tp * tmp);
+  const int64_t jm = (int64_t)floor((1.0 - tp) * tmp);
+  const int64_t ir = jp + jm + 1;
+  int64_t ip = (int64_t)floor(tt * (double)ir);
+  ip = ((ip % (4 * ir)) + 4 * ir) % (4 * ir);
+  if (uz > 0.0) return 2 * ir * (ir - 1) + ip;
+  return npix - 2 * ir * (ir + 1) + ip;
 }
 
 // Spatial key of a grid cell for the work-queue sort: the cell's brick

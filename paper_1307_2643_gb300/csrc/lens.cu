@@ -1,0 +1,474 @@
+// lens.cu -- galactic lens: build by back-tracking, apply, arrival maps.
+//
+// CRPropa 3.0 (Sect. 4, "Galactic propagation") maps the directions of
+// cosmic rays at the border of the Galaxy to the directions observed at
+// Earth with a set of transformation matrices, one per energy bin, built by
+// tracking through a galactic field model.  Here, per rigidity bin b and
+// HEALPix RING border pixel j, the lens keeps the multiset of Earth pixels i
+// of the back-tracked samples that left the Galaxy through j (a column of
+// the count matrix N_b[i, j]), sorted ascending, plus the largest column
+// count of each bin.  Apply: observed with probability count_j / max_b
+// (M_b = N_b / max_j sum_i N_b[i, j]; the rest is shadowed), then a
+// uniformly chosen sample of the column gives the Earth pixel.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "crp_internal.cuh"
+#include "device_common.cuh"
+
+namespace crp {
+void context_view(const crp_context* c, const int32_t** status, const double** E, uint64_t* n,
+                  int* device);
+void context_pool(const crp_context* c, DevState* st, uint64_t* n, int* device, uint64_t* seed);
+}  // namespace crp
+
+using namespace crp;
+
+struct crp_lens {
+  int device;
+  int32_t nside, n_bins;
+  double r_lo, r_hi;
+  int64_t npix, n_cols, n_entries;
+  uint32_t* col_start;  // n_cols + 1
+  uint32_t* entries;    // n_entries Earth pixels
+  uint32_t* max_count;  // n_bins
+};
+
+namespace {
+
+constexpr uint32_t kNotApplied = 0xFFFFFFFFu;
+constexpr uint32_t kNotObserved = 0xFFFFFFFEu;
+constexpr uint32_t kNoKey = 0xFFFFFFFFu;
+constexpr int kScanBlock = 1024;
+
+int blocks(uint64_t n, int b) {
+  const uint64_t g = (n + b - 1) / b;
+  return (int)(g < 1 ? 1 : (g > 65536 ? 65536 : g));
+}
+
+// Per back-tracked sample: column key b * npix + j (border pixel of the
+// antiparticle's direction) for samples that reached the border, and the
+// Earth pixel i of its launch direction.
+__global__ void k_lens_keys(DevState st, uint64_t n, const int32_t* bin, int64_t nside,
+                            int64_t npix, uint32_t* key, uint32_t* earth, uint32_t* counts) {
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < n;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    earth[k] = (uint32_t)healpix_ring_pixel(nside, st.ux0[k], st.uy0[k], st.uz0[k]);
+    if (st.status[k] != CRP_AT_BORDER) {
+      key[k] = kNoKey;
+      continue;
+    }
+    const int64_t j = healpix_ring_pixel(nside, st.ux[k], st.uy[k], st.uz[k]);
+    const uint32_t c = (uint32_t)((int64_t)bin[k] * npix + j);
+    key[k] = c;
+    atomicAdd(counts + c, 1u);
+  }
+}
+
+// Exclusive scan of n uint32 in place: block scans, scan of block sums,
+// add-back.  out[n] receives the total.
+__global__ void k_scan_blocks(uint32_t* v, uint64_t n, uint32_t* block_sums) {
+  __shared__ uint32_t sh[kScanBlock];
+  const uint64_t i = blockIdx.x * (uint64_t)kScanBlock + threadIdx.x;
+  const uint32_t x = i < n ? v[i] : 0u;
+  sh[threadIdx.x] = x;
+  __syncthreads();
+  for (int off = 1; off < kScanBlock; off <<= 1) {
+    const uint32_t t = threadIdx.x >= (unsigned)off ? sh[threadIdx.x - off] : 0u;
+    __syncthreads();
+    sh[threadIdx.x] += t;
+    __syncthreads();
+  }
+  if (i < n) v[i] = sh[threadIdx.x] - x;  // exclusive
+  if (threadIdx.x == kScanBlock - 1) block_sums[blockIdx.x] = sh[threadIdx.x];
+}
+
+__global__ void k_scan_sums(uint32_t* sums, int nb, uint32_t* total) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  uint32_t run = 0;
+  for (int b = 0; b < nb; ++b) {
+    const uint32_t v = sums[b];
+    sums[b] = run;
+    run += v;
+  }
+  *total = run;
+}
+
+__global__ void k_scan_add(uint32_t* v, uint64_t n, const uint32_t* sums) {
+  const uint64_t i = blockIdx.x * (uint64_t)kScanBlock + threadIdx.x;
+  if (i < n) v[i] += sums[blockIdx.x];
+}
+
+__global__ void k_lens_scatter(const uint32_t* key, const uint32_t* earth, uint64_t n,
+                               uint32_t* fill, uint32_t* entries) {
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < n;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    if (key[k] == kNoKey) continue;
+    entries[atomicAdd(fill + key[k], 1u)] = earth[k];
+  }
+}
+
+// Canonical order inside each column (ascending Earth pixel), so the lens
+// does not depend on the order the samples were scattered in.
+__global__ void k_lens_sort_columns(const uint32_t* col_start, int64_t n_cols, uint32_t* entries) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n_cols;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t a = col_start[c], b = col_start[c + 1];
+    for (uint32_t i = a + 1; i < b; ++i) {
+      const uint32_t v = entries[i];
+      uint32_t j = i;
+      while (j > a && entries[j - 1] > v) {
+        entries[j] = entries[j - 1];
+        --j;
+      }
+      entries[j] = v;
+    }
+  }
+}
+
+__global__ void k_lens_max(const uint32_t* col_start, int64_t npix, int n_bins, uint32_t* mx) {
+  __shared__ uint32_t sh[256];
+  const int b = blockIdx.x;
+  if (b >= n_bins) return;
+  uint32_t m = 0;
+  for (int64_t j = threadIdx.x; j < npix; j += blockDim.x) {
+    const int64_t c = (int64_t)b * npix + j;
+    const uint32_t cnt = col_start[c + 1] - col_start[c];
+    m = cnt > m ? cnt : m;
+  }
+  sh[threadIdx.x] = m;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < (unsigned)s) sh[threadIdx.x] = max(sh[threadIdx.x], sh[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) mx[b] = sh[0];
+}
+
+__device__ __forceinline__ bool pick(int what, int status) {
+  switch (what) {
+    case CRP_COLLECT_ALL: return true;
+    case CRP_COLLECT_FINISHED: return status != CRP_ACTIVE;
+    case CRP_COLLECT_DETECTED: return status == CRP_DETECTED;
+    case CRP_COLLECT_ACTIVE: return status == CRP_ACTIVE;
+    case CRP_COLLECT_AT_BORDER: return status == CRP_AT_BORDER;
+  }
+  return false;
+}
+
+__global__ void k_lens_apply(DevState st, uint64_t n, int what, uint64_t seed, int64_t nside,
+                             int64_t npix, int n_bins, double lg_lo, double inv_dlg,
+                             const uint32_t* col_start, const uint32_t* entries,
+                             const uint32_t* max_count) {
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < n;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    if (!pick(what, st.status[k])) continue;
+    const int Z = st.Z[k];
+    if (Z <= 0) {
+      st.lens_pixel[k] = kNotApplied;
+      continue;
+    }
+    const double R = st.E[k] / (double)Z;
+    const double t = (series_log(R) - lg_lo) * inv_dlg;
+    double bf = floor(t);
+    if (!(bf >= 0.0)) bf = 0.0;
+    if (bf > (double)(n_bins - 1)) bf = (double)(n_bins - 1);
+    const int64_t b = (int64_t)bf;
+    const int64_t j = healpix_ring_pixel(nside, -st.ux[k], -st.uy[k], -st.uz[k]);
+    const int64_t col = b * npix + j;
+    const uint32_t start = col_start[col];
+    const int64_t count = (int64_t)(col_start[col + 1] - start);
+    const double mx = (double)max_count[b];
+    const Philox4 w = draw4(seed, 3u, st.id[k], 0u);
+    const double u1 = u01_open(w.v0, w.v1), u2 = u01_open(w.v2, w.v3);
+    uint32_t out = kNotObserved;
+    if (count > 0 && u1 * mx < (double)count) {
+      int64_t pk = (int64_t)(u2 * (double)count);
+      if (pk > count - 1) pk = count - 1;
+      out = entries[start + pk];
+    }
+    st.lens_pixel[k] = out;
+  }
+}
+
+__global__ void k_hist_healpix(DevState st, uint64_t n, int what, int64_t nside, int source,
+                               unsigned long long* bins) {
+  const uint64_t npix = 12ull * nside * nside;
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < n;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    if (!pick(what, st.status[k])) continue;
+    uint64_t p;
+    if (source == 0)
+      p = (uint64_t)healpix_ring_pixel(nside, -st.ux[k], -st.uy[k], -st.uz[k]);
+    else
+      p = st.lens_pixel[k];
+    if (p < npix) atomicAdd(bins + p, 1ull);
+  }
+}
+
+crp_status scan_inplace(uint32_t* v, uint64_t n, uint32_t* total, cudaStream_t s) {
+  const uint64_t nb = (n + kScanBlock - 1) / kScanBlock;
+  uint32_t* sums = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * (nb + 1)));
+  if (!sums) {
+    set_error("lens: scan workspace allocation failed");
+    return CRP_E_OOM;
+  }
+  k_scan_blocks<<<(unsigned)nb, kScanBlock, 0, s>>>(v, n, sums);
+  k_scan_sums<<<1, 1, 0, s>>>(sums, (int)nb, total);
+  k_scan_add<<<(unsigned)nb, kScanBlock, 0, s>>>(v, n, sums);
+  const cudaError_t e = cudaStreamSynchronize(s);
+  dev_free(sums);
+  return e == cudaSuccess ? CRP_OK : fail_cuda(e, "lens: scan");
+}
+
+void lens_free(crp_lens* L) {
+  if (!L) return;
+  dev_free(L->col_start);
+  dev_free(L->entries);
+  dev_free(L->max_count);
+  delete L;
+}
+
+}  // namespace
+
+extern "C" {
+
+crp_status crp_lens_build(crp_context* ctx, const crp_grid* galaxy, const crp_modules* m,
+                          const crp_lens_desc* d, crp_lens** out, crp_stats* stats_out) {
+  if (!ctx || !galaxy || !m || !d || !out || !d->dirs || !d->E || !d->bin) {
+    set_error("crp_lens_build: NULL argument");
+    return CRP_E_INVALID;
+  }
+  *out = nullptr;
+  if (d->nside < 1 || d->nside > 8192 || d->n_bins < 1 || !(d->r_lo > 0.0) ||
+      !(d->r_hi > d->r_lo) || d->n_samples < 1) {
+    set_error("crp_lens_build: need 1 <= nside <= 8192, n_bins >= 1, 0 < r_lo < r_hi, samples");
+    return CRP_E_INVALID;
+  }
+  const int64_t npix = 12ll * d->nside * d->nside;
+  const int64_t n_cols = npix * d->n_bins;
+  if (n_cols >= 0xFFFFFFFFll || d->n_samples >= 0xFFFFFFFFll) {
+    set_error("crp_lens_build: too many columns or samples for 32-bit indices");
+    return CRP_E_INVALID;
+  }
+  if (!(m->flags & CRP_BORDER)) {
+    set_error("crp_lens_build: the modules must stop candidates at the border (CRP_BORDER)");
+    return CRP_E_INVALID;
+  }
+  for (int64_t k = 0; k < d->n_samples; ++k) {
+    if (d->bin[k] < 0 || d->bin[k] >= d->n_bins) {
+      set_error("crp_lens_build: sample %lld has bin %d outside 0..%d", (long long)k, d->bin[k],
+                d->n_bins - 1);
+      return CRP_E_INVALID;
+    }
+  }
+  DevState cst;
+  uint64_t unused_n = 0, seed = 0;
+  int device = 0;
+  context_pool(ctx, &cst, &unused_n, &device, &seed);
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != device) cudaSetDevice(device);
+
+  // back-track in a private pool so the caller's candidates stay untouched
+  const uint64_t n = (uint64_t)d->n_samples;
+  crp_context* bt = nullptr;
+  crp_status st = crp_context_create(device, seed, n, &bt);
+  std::vector<double> x(n, d->earth[0]), y(n, d->earth[1]), z(n, d->earth[2]);
+  std::vector<double> ux(n), uy(n), uz(n);
+  std::vector<int32_t> ones(n, 1), qneg(n, -1);
+  for (uint64_t k = 0; k < n; ++k) {
+    ux[k] = d->dirs[3 * k];
+    uy[k] = d->dirs[3 * k + 1];
+    uz[k] = d->dirs[3 * k + 2];
+  }
+  if (st == CRP_OK) {
+    crp_candidate_arrays a;
+    memset(&a, 0, sizeof(a));
+    a.x = x.data(); a.y = y.data(); a.z = z.data();
+    a.ux = ux.data(); a.uy = uy.data(); a.uz = uz.data();
+    a.E = d->E;
+    a.A = ones.data(); a.Z = ones.data(); a.q = qneg.data();
+    st = crp_candidates_inject(bt, &a, n, 0, nullptr);
+  }
+  crp_stats bstats;
+  memset(&bstats, 0, sizeof(bstats));
+  if (st == CRP_OK) st = crp_propagate(bt, galaxy, m, nullptr, &bstats);
+  if (stats_out) *stats_out = bstats;
+
+  crp_lens* L = nullptr;
+  uint32_t *key = nullptr, *earth = nullptr, *fill = nullptr, *dbin = nullptr, *total = nullptr;
+  if (st == CRP_OK) {
+    L = new (std::nothrow) crp_lens;
+    if (!L) {
+      st = CRP_E_OOM;
+      set_error("crp_lens_build: host allocation failed");
+    } else {
+      memset(L, 0, sizeof(*L));
+      L->device = device;
+      L->nside = d->nside;
+      L->n_bins = d->n_bins;
+      L->r_lo = d->r_lo;
+      L->r_hi = d->r_hi;
+      L->npix = npix;
+      L->n_cols = n_cols;
+      L->col_start = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * (n_cols + 1)));
+      L->max_count = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * d->n_bins));
+      key = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * n));
+      earth = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * n));
+      dbin = static_cast<uint32_t*>(dev_alloc(sizeof(int32_t) * n));
+      fill = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * (n_cols + 1)));
+      total = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t)));
+      if (!L->col_start || !L->max_count || !key || !earth || !dbin || !fill || !total) {
+        st = CRP_E_OOM;
+        set_error("crp_lens_build: device allocation failed");
+      }
+    }
+  }
+  if (st == CRP_OK) {
+    DevState bst;
+    uint64_t bn = 0, bseed = 0;
+    int bdev = 0;
+    context_pool(bt, &bst, &bn, &bdev, &bseed);
+    cudaError_t e = cudaMemcpy(dbin, d->bin, sizeof(int32_t) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(L->col_start, 0, sizeof(uint32_t) * (n_cols + 1));
+    if (e == cudaSuccess) {
+      k_lens_keys<<<blocks(n, 256), 256>>>(bst, n, (const int32_t*)dbin, d->nside, npix, key,
+                                           earth, L->col_start);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) st = fail_cuda(e, "crp_lens_build: keys");
+    if (st == CRP_OK) st = scan_inplace(L->col_start, n_cols + 1, total, nullptr);
+    uint32_t n_entries = 0;
+    if (st == CRP_OK) {
+      e = cudaMemcpy(&n_entries, total, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess) e = cudaMemcpy(fill, L->col_start, sizeof(uint32_t) * (n_cols + 1),
+                                           cudaMemcpyDeviceToDevice);
+      if (e != cudaSuccess) st = fail_cuda(e, "crp_lens_build: counts");
+    }
+    if (st == CRP_OK) {
+      L->n_entries = n_entries;
+      L->entries = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * (n_entries ? n_entries : 1)));
+      if (!L->entries) {
+        st = CRP_E_OOM;
+        set_error("crp_lens_build: entries allocation failed");
+      }
+    }
+    if (st == CRP_OK) {
+      k_lens_scatter<<<blocks(n, 256), 256>>>(key, earth, n, fill, L->entries);
+      k_lens_sort_columns<<<blocks(n_cols, 256), 256>>>(L->col_start, n_cols, L->entries);
+      k_lens_max<<<d->n_bins, 256>>>(L->col_start, npix, d->n_bins, L->max_count);
+      e = cudaDeviceSynchronize();
+      if (e != cudaSuccess) st = fail_cuda(e, "crp_lens_build: columns");
+    }
+  }
+  dev_free(key);
+  dev_free(earth);
+  dev_free(dbin);
+  dev_free(fill);
+  dev_free(total);
+  if (bt) crp_context_destroy(bt);
+  if (prev >= 0 && prev != device) cudaSetDevice(prev);
+  if (st != CRP_OK) {
+    lens_free(L);
+    return st;
+  }
+  *out = L;
+  return CRP_OK;
+}
+
+crp_status crp_lens_destroy(crp_lens* L) {
+  if (!L) return CRP_OK;
+  cudaDeviceSynchronize();
+  lens_free(L);
+  return CRP_OK;
+}
+
+crp_status crp_lens_copy_out(const crp_lens* L, uint32_t* col_start, uint32_t* entries,
+                             uint32_t* max_count, int64_t* n_entries) {
+  if (!L || !n_entries) {
+    set_error("crp_lens_copy_out: NULL argument");
+    return CRP_E_INVALID;
+  }
+  *n_entries = L->n_entries;
+  cudaError_t e = cudaSuccess;
+  if (col_start)
+    e = cudaMemcpy(col_start, L->col_start, sizeof(uint32_t) * (L->n_cols + 1),
+                   cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && entries && L->n_entries)
+    e = cudaMemcpy(entries, L->entries, sizeof(uint32_t) * L->n_entries, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && max_count)
+    e = cudaMemcpy(max_count, L->max_count, sizeof(uint32_t) * L->n_bins, cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? CRP_OK : fail_cuda(e, "crp_lens_copy_out");
+}
+
+crp_status crp_lens_apply(crp_context* ctx, const crp_lens* L, int32_t what, void* stream) {
+  if (!ctx || !L || what < CRP_COLLECT_ALL || what > CRP_COLLECT_AT_BORDER) {
+    set_error("crp_lens_apply: bad argument");
+    return CRP_E_INVALID;
+  }
+  DevState st;
+  uint64_t n = 0, seed = 0;
+  int device = 0;
+  context_pool(ctx, &st, &n, &device, &seed);
+  if (device != L->device) {
+    set_error("crp_lens_apply: lens and context are on different devices");
+    return CRP_E_INVALID;
+  }
+  if (n == 0) return CRP_OK;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != device) cudaSetDevice(device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const double lg_lo = series_log(L->r_lo);
+  const double inv = (double)L->n_bins / (series_log(L->r_hi) - lg_lo);
+  k_lens_apply<<<blocks(n, 256), 256, 0, s>>>(st, n, what, seed, L->nside, L->npix, L->n_bins,
+                                              lg_lo, inv, L->col_start, L->entries, L->max_count);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (prev >= 0 && prev != device) cudaSetDevice(prev);
+  return e == cudaSuccess ? CRP_OK : fail_cuda(e, "crp_lens_apply");
+}
+
+crp_status crp_histogram_healpix(crp_context* ctx, int32_t what, int32_t nside, int32_t source,
+                                 uint64_t* out, void* stream) {
+  if (!ctx || !out || nside < 1 || nside > 8192 || (source != 0 && source != 1) ||
+      what < CRP_COLLECT_ALL || what > CRP_COLLECT_AT_BORDER) {
+    set_error("crp_histogram_healpix: bad argument");
+    return CRP_E_INVALID;
+  }
+  const uint64_t npix = 12ull * nside * nside;
+  memset(out, 0, sizeof(uint64_t) * npix);
+  DevState st;
+  uint64_t n = 0, seed = 0;
+  int device = 0;
+  context_pool(ctx, &st, &n, &device, &seed);
+  if (n == 0) return CRP_OK;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != device) cudaSetDevice(device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned long long* bins = static_cast<unsigned long long*>(dev_alloc(8 * npix));
+  crp_status rc = CRP_OK;
+  if (!bins) {
+    set_error("crp_histogram_healpix: allocation failed");
+    rc = CRP_E_OOM;
+  } else {
+    cudaError_t e = cudaMemsetAsync(bins, 0, 8 * npix, s);
+    if (e == cudaSuccess) {
+      k_hist_healpix<<<blocks(n, 256), 256, 0, s>>>(st, n, what, nside, source, bins);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, bins, 8 * npix, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = fail_cuda(e, "crp_histogram_healpix");
+    dev_free(bins);
+  }
+  if (prev >= 0 && prev != device) cudaSetDevice(prev);
+  return rc;
+}
+
+}  // extern "C"

@@ -126,13 +126,13 @@ __device__ __forceinline__ void galactic_fp64(const KParams& p, const double x[3
   const double az = fabs(z);
   double b_r = 0.0, b_phi = 0.0;
   if (r >= p.disk_rmin && r <= p.disk_rmax) {
-    const double bd = p.disk_b * exp(-az / p.disk_hz);
+    const double bd = p.disk_b * series_exp(-az / p.disk_hz);
     b_r += bd * p.sin_pitch;
     b_phi += bd * p.cos_pitch;
   }
   if (z != 0.0) {
     const double dz = az - p.halo_z0;
-    const double bh = p.halo_b * exp(-dz * dz / (2.0 * p.halo_sigma * p.halo_sigma));
+    const double bh = p.halo_b * series_exp(-dz * dz / (2.0 * p.halo_sigma * p.halo_sigma));
     b_phi += z > 0.0 ? bh : -bh;
   }
   G[0] = b_r * cr - b_phi * sr;
