@@ -562,3 +562,61 @@ def test_lens_zero_field_is_identity(oracle):
     seen = out < npix
     assert seen.mean() > 0.3
     assert np.array_equal(out[seen], oracle.ang2pix_vec(nside, -u)[seen])
+
+
+# ---------------------------------------------------------------------------
+# MLP surrogate oracle
+# ---------------------------------------------------------------------------
+def _tiny_mlp():
+    import oracle.mlp as M
+    shapes = M.layer_shapes(4, 8, 2, 3)
+    g = np.random.default_rng(12)
+    flat = g.normal(scale=0.5, size=M.n_params(shapes))
+    x = g.normal(size=(7, 4))
+    t = g.normal(size=(7, 3))
+    t /= np.linalg.norm(t, axis=1, keepdims=True)
+    return M, shapes, flat, x, t
+
+
+def test_mlp_backward_matches_finite_differences(oracle):
+    M, shapes, flat, x, t = _tiny_mlp()
+    y, cache = M.forward(flat, shapes, x)
+    grad = M.backward(flat, shapes, cache, t)
+    eps = 1e-6
+    num = np.zeros_like(flat)
+    for k in range(len(flat)):
+        fp, fm = flat.copy(), flat.copy()
+        fp[k] += eps
+        fm[k] -= eps
+        num[k] = (M.loss(M.forward(fp, shapes, x)[0], t) -
+                  M.loss(M.forward(fm, shapes, x)[0], t)) / (2 * eps)
+    assert np.max(np.abs(grad - num)) < 1e-6 * max(1.0, np.max(np.abs(num)))
+
+
+def test_mlp_forward_explicit_loops(oracle):
+    M, shapes, flat, x, t = _tiny_mlp()
+    y, _ = M.forward(flat, shapes, x)
+    Ws, bs = M.unpack(flat, shapes)
+    for r in range(len(x)):
+        h = list(x[r])
+        for l, (W, b) in enumerate(zip(Ws, bs)):
+            out = []
+            for o in range(W.shape[0]):
+                acc = b[o]
+                for i in range(W.shape[1]):
+                    acc += W[o, i] * h[i]
+                out.append(max(acc, 0.0) if l < len(Ws) - 1 else acc)
+            h = out
+        nrm = math.sqrt(sum(v * v for v in h))
+        assert np.allclose(y[r], np.array(h) / nrm, rtol=0, atol=1e-13)
+
+
+def test_adam_first_step_and_bf16_rounding(oracle):
+    import oracle.mlp as M
+    g = np.array([0.5, -2.0, 1e-3])
+    p, m, v = M.adam(np.zeros(3), g, np.zeros(3), np.zeros(3), 1, lr=0.01)
+    # bias-corrected first step is -lr * g / (|g| + eps)
+    assert np.allclose(p, -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+    vals = M.bf16_round([1.0, 1 + 2 ** -8, 1 + 3 * 2 ** -8, -3.0e-3, 65504.0])
+    assert vals[0] == 1.0 and vals[1] == 1.0 and vals[2] == 1 + 2 ** -6
+    assert abs(vals[3] / -3.0e-3 - 1) < 2 ** -8
