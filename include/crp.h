@@ -54,6 +54,7 @@ typedef struct crp_context crp_context;
 typedef struct crp_grid crp_grid;
 typedef struct crp_tables crp_tables;
 typedef struct crp_lens crp_lens;
+typedef struct crp_mlp crp_mlp;
 
 /* Message describing the calling thread's last failed call ("" if none). */
 const char* crp_last_error(void);
@@ -337,6 +338,35 @@ crp_status crp_lens_apply(crp_context* ctx, const crp_lens* lens, int32_t what, 
 crp_status crp_lens_copy_out(const crp_lens* lens, uint32_t* col_start, uint32_t* entries,
                              uint32_t* max_count, int64_t* n_entries);
 crp_status crp_lens_destroy(crp_lens* lens);
+
+/* ------------------------------------------------------------------------
+ * Learned lens surrogate: an MLP that maps an arrival direction at Earth and
+ * the log rigidity to the direction at the galaxy border -- a stand-in for
+ * back-tracking (Sect. 4: forward and back-tracking through the galactic
+ * field) when building lenses.  The paper has no learned component.
+ * Inputs (n_x, n_y, n_z, log10(R / V) - 19, ...) FP32 [n][n_in]; n_hidden
+ * ReLU layers of width `hidden` (a multiple of 128); a linear 3-output
+ * normalised to a unit vector.  Loss mean(1 - y_hat . t).  Hidden-to-hidden
+ * layers run on the BF16 tensor cores with FP32 accumulation; master weights,
+ * gradients and Adam (beta 0.9 / 0.999, eps 1e-8, bias corrected) in FP32.
+ * Parameters packed [W1, b1, ..., W_L+1, b_L+1], W_l (n_out, n_in) row-major.
+ * Weights are initialised He-normal from Philox (tag 4, id = index), biases 0.
+ * ---------------------------------------------------------------------- */
+crp_status crp_mlp_create(crp_context* ctx, int32_t n_in, int32_t hidden, int32_t n_hidden,
+                          uint64_t seed, crp_mlp** out);
+crp_status crp_mlp_destroy(crp_mlp* mlp);
+int64_t crp_mlp_num_params(const crp_mlp* mlp);
+/* host FP32 arrays of crp_mlp_num_params entries (resets the Adam state) */
+crp_status crp_mlp_set_params(crp_mlp* mlp, const float* params);
+/* either pointer may be NULL; grad is the last train step's gradient */
+crp_status crp_mlp_get_params(const crp_mlp* mlp, float* params, float* grad);
+/* device pointers; n a multiple of 128; y_hat [n][3] */
+crp_status crp_mlp_forward(crp_mlp* mlp, const float* x, float* y_hat, int64_t n, void* stream);
+/* one Adam step on a batch (device x [n][n_in], t [n][3] unit targets; n a
+ * multiple of 128); lr = 0 computes the gradient only; loss_out (host, may
+ * be NULL) receives the batch loss and synchronises the stream */
+crp_status crp_mlp_train_step(crp_mlp* mlp, const float* x, const float* t, int64_t n, float lr,
+                              float* loss_out, void* stream);
 
 /* HEALPix RING arrival map of the selected records: source 0 counts the
  * arrival direction -u at the candidate (extragalactic sky), source 1 the

@@ -25,6 +25,7 @@ UNITS = {
     "propagate_mixed.cu": [],
     "hist_noalloc.cu": [],
     "lens.cu": [],
+    "mlp.cu": [],
 }
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

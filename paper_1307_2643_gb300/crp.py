@@ -119,6 +119,8 @@ SYMBOLS = (
     "crp_propagate", "crp_collect", "crp_histogram_energy", "crp_histogram_energy_noalloc",
     "crp_lens_build", "crp_lens_apply", "crp_lens_copy_out", "crp_lens_destroy",
     "crp_histogram_healpix",
+    "crp_mlp_create", "crp_mlp_destroy", "crp_mlp_num_params", "crp_mlp_set_params",
+    "crp_mlp_get_params", "crp_mlp_forward", "crp_mlp_train_step",
 )
 
 _lock = threading.Lock()
@@ -162,9 +164,17 @@ def lib():
             L.crp_lens_copy_out.argtypes = [p, p, p, p, C.POINTER(C.c_int64)]
             L.crp_lens_destroy.argtypes = [p]
             L.crp_histogram_healpix.argtypes = [p, i32, i32, i32, p, p]
+            L.crp_mlp_create.argtypes = [p, i32, i32, i32, u64, C.POINTER(p)]
+            L.crp_mlp_destroy.argtypes = [p]
+            L.crp_mlp_num_params.argtypes = [p]
+            L.crp_mlp_set_params.argtypes = [p, p]
+            L.crp_mlp_get_params.argtypes = [p, p, p]
+            L.crp_mlp_forward.argtypes = [p, p, p, C.c_int64, p]
+            L.crp_mlp_train_step.argtypes = [p, p, p, C.c_int64, C.c_float, p, p]
             for name in SYMBOLS:
                 if name not in ("crp_last_error", "crp_version"):
                     getattr(L, name).restype = st
+            L.crp_mlp_num_params.restype = C.c_int64
             _lib = L
     return _lib
 
@@ -360,6 +370,46 @@ def crp_histogram_healpix(ctx, what, nside, source, stream=None):
     out = np.zeros(12 * nside * nside, dtype=np.uint64)
     _check(lib().crp_histogram_healpix(ctx, what, nside, source, out.ctypes.data, stream))
     return out
+
+
+def crp_mlp_create(ctx, n_in=4, hidden=256, n_hidden=4, seed=0):
+    h = C.c_void_p()
+    _check(lib().crp_mlp_create(ctx, n_in, hidden, n_hidden, seed, C.byref(h)))
+    return h
+
+
+def crp_mlp_destroy(mlp):
+    _check(lib().crp_mlp_destroy(mlp))
+
+
+def crp_mlp_num_params(mlp):
+    return lib().crp_mlp_num_params(mlp)
+
+
+def crp_mlp_set_params(mlp, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    assert len(p) == crp_mlp_num_params(mlp)
+    _check(lib().crp_mlp_set_params(mlp, p.ctypes.data))
+
+
+def crp_mlp_get_params(mlp):
+    """(params, last gradient) as FP32 host arrays."""
+    n = crp_mlp_num_params(mlp)
+    p, g = np.zeros(n, np.float32), np.zeros(n, np.float32)
+    _check(lib().crp_mlp_get_params(mlp, p.ctypes.data, g.ctypes.data))
+    return p, g
+
+
+def crp_mlp_forward(mlp, x_dev, y_dev, n, stream=None):
+    """x_dev, y_dev: torch float32 device tensors [n, n_in], [n, 3]."""
+    _check(lib().crp_mlp_forward(mlp, _addr(x_dev), _addr(y_dev), n, stream))
+
+
+def crp_mlp_train_step(mlp, x_dev, t_dev, n, lr, stream=None, want_loss=True):
+    loss = C.c_float(0.0)
+    _check(lib().crp_mlp_train_step(mlp, _addr(x_dev), _addr(t_dev), n, lr,
+                                    C.byref(loss) if want_loss else None, stream))
+    return loss.value
 
 
 HIST_NOALLOC_MAX_BINS = 4096

@@ -1,0 +1,622 @@
+// mlp.cu -- MLP galactic-lens surrogate: BF16 tensor-core training and
+// inference with FP32 accumulation and FP32 master weights.
+//
+// Network: inputs (n_x, n_y, n_z, log10 R - 19) -> n_hidden ReLU layers of
+// width `hidden` -> linear 3-vector, normalised to the predicted direction at
+// the galaxy border.  Loss mean(1 - y_hat . t).  Adam (Kingma & Ba 2015) with
+// bias correction.  Parameters packed [W1, b1, W2, b2, ...], W_l (n_out, n_in)
+// row-major, FP32.
+//
+// The hidden-to-hidden layers are GEMMs C = A . Bt^T (A: M x K, Bt: N x K,
+// both bfloat16 row-major) on the tensor cores (mma.sync m16n8k16, bf16 in,
+// f32 accumulate), 128 x 128 x 32 block tiles, double-buffered cp.async
+// staging, shared rows padded to 40 elements so fragment loads hit 32
+// distinct banks.  Epilogues: bias + ReLU to bf16 (forward), ReLU mask to
+// bf16 (backward data), FP32 atomic accumulation (weight gradients, split K
+// over the batch).  The thin input (K = 4) and output (N = 3) layers, the
+// loss, transposes, bias sums and Adam are plain FP32 kernels.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "crp_internal.cuh"
+#include "device_common.cuh"
+
+namespace crp {
+void context_pool(const crp_context* c, DevState* st, uint64_t* n, int* device, uint64_t* seed);
+}  // namespace crp
+
+using namespace crp;
+
+struct crp_mlp {
+  int device;
+  int n_in, hidden, n_hidden, n_out;
+  int64_t n_params;
+  std::vector<int64_t> w_off, b_off;  // offsets of W_l and b_l in the packed vector
+  float* params;                      // FP32 master parameters
+  float* grad;
+  float* m;
+  float* v;
+  int64_t step;
+  std::vector<__nv_bfloat16*> wb, wbt;  // bf16 copies of hidden layers' W and W^T
+  // batch workspace
+  int64_t cap;
+  std::vector<__nv_bfloat16*> h;  // activations of each hidden layer [cap][hidden]
+  __nv_bfloat16 *dz, *dz2, *dzt, *ht;
+  float *y, *dy, *loss;
+};
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 32, PAD = 40, GEMM_THREADS = 256;
+
+enum Epi { EPI_BIAS_RELU = 0, EPI_MASK = 1, EPI_ATOMIC = 2 };
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// C (M x N) = A (M x K) . Bt (N x K)^T over k in [k0, k0 + kn).  M, N
+// multiples of 128, kn a multiple of 32; blockIdx.z selects the K split.
+template <int EPI>
+__global__ void __launch_bounds__(GEMM_THREADS)
+    k_gemm_bf16(const __nv_bfloat16* __restrict__ A, int lda, const __nv_bfloat16* __restrict__ Bt,
+                int ldb, int K, int splits, const float* __restrict__ bias,
+                const __nv_bfloat16* __restrict__ mask, __nv_bfloat16* __restrict__ out_bf,
+                float* __restrict__ out_f, int ldc) {
+  __shared__ __align__(16) __nv_bfloat16 As[2][BM][PAD];
+  __shared__ __align__(16) __nv_bfloat16 Bs[2][BN][PAD];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int wm = warp >> 2, wn = warp & 3;  // 2 x 4 warps, 64 x 32 each
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int kn = K / splits, kbeg = blockIdx.z * kn;
+  float acc[4][4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+
+  auto load_tile = [&](int buf, int k) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int chunk = tid + c * GEMM_THREADS;  // 512 chunks of 8 bf16
+      const int row = chunk >> 2, col = (chunk & 3) * 8;
+      cp_async16(&As[buf][row][col], A + (size_t)(m0 + row) * lda + k + col);
+      cp_async16(&Bs[buf][row][col], Bt + (size_t)(n0 + row) * ldb + k + col);
+    }
+    cp_async_commit();
+  };
+
+  const int nk = kn / BK;
+  load_tile(0, kbeg);
+  for (int it = 0; it < nk; ++it) {
+    const int buf = it & 1;
+    if (it + 1 < nk) {
+      load_tile(buf ^ 1, kbeg + (it + 1) * BK);
+      cp_async_wait1();
+    } else {
+      cp_async_wait0();
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; kk += 16) {
+      uint32_t af[4][4], bf[4][2];
+#pragma unroll
+      for (int mi = 0; mi < 4; ++mi) {
+        const int r = wm * 64 + mi * 16 + g;
+        af[mi][0] = *reinterpret_cast<const uint32_t*>(&As[buf][r][kk + 2 * t]);
+        af[mi][1] = *reinterpret_cast<const uint32_t*>(&As[buf][r + 8][kk + 2 * t]);
+        af[mi][2] = *reinterpret_cast<const uint32_t*>(&As[buf][r][kk + 2 * t + 8]);
+        af[mi][3] = *reinterpret_cast<const uint32_t*>(&As[buf][r + 8][kk + 2 * t + 8]);
+      }
+#pragma unroll
+      for (int ni = 0; ni < 4; ++ni) {
+        const int c = wn * 32 + ni * 8 + g;
+        bf[ni][0] = *reinterpret_cast<const uint32_t*>(&Bs[buf][c][kk + 2 * t]);
+        bf[ni][1] = *reinterpret_cast<const uint32_t*>(&Bs[buf][c][kk + 2 * t + 8]);
+      }
+#pragma unroll
+      for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], af[mi], bf[ni]);
+    }
+    __syncthreads();
+  }
+  // epilogue: c0,c1 at (row g, cols 2t, 2t+1); c2,c3 at (row g+8, same cols)
+#pragma unroll
+  for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const int row = m0 + wm * 64 + mi * 16 + g + half * 8;
+        const int col = n0 + wn * 32 + ni * 8 + 2 * t;
+        float v0 = acc[mi][ni][2 * half], v1 = acc[mi][ni][2 * half + 1];
+        if (EPI == EPI_BIAS_RELU) {
+          v0 = fmaxf(v0 + bias[col], 0.f);
+          v1 = fmaxf(v1 + bias[col + 1], 0.f);
+          *reinterpret_cast<__nv_bfloat162*>(out_bf + (size_t)row * ldc + col) =
+              __floats2bfloat162_rn(v0, v1);
+        } else if (EPI == EPI_MASK) {
+          const __nv_bfloat162 mk =
+              *reinterpret_cast<const __nv_bfloat162*>(mask + (size_t)row * ldc + col);
+          v0 = __bfloat162float(mk.x) > 0.f ? v0 : 0.f;
+          v1 = __bfloat162float(mk.y) > 0.f ? v1 : 0.f;
+          *reinterpret_cast<__nv_bfloat162*>(out_bf + (size_t)row * ldc + col) =
+              __floats2bfloat162_rn(v0, v1);
+        } else {
+          atomicAdd(out_f + (size_t)row * ldc + col, v0);
+          atomicAdd(out_f + (size_t)row * ldc + col + 1, v1);
+        }
+      }
+}
+
+// First layer (K = n_in, small): H1 = bf16(relu(x W1^T + b1)).
+__global__ void k_layer_in(const float* __restrict__ x, int n_in, int64_t n,
+                           const float* __restrict__ W, const float* __restrict__ b, int hidden,
+                           __nv_bfloat16* __restrict__ h) {
+  const int64_t total = n * hidden;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / hidden;
+    const int o = (int)(e % hidden);
+    float acc = b[o];
+    for (int i = 0; i < n_in; ++i) acc = fmaf(W[o * n_in + i], x[r * n_in + i], acc);
+    h[e] = __float2bfloat16_rn(fmaxf(acc, 0.f));
+  }
+}
+
+// Output layer and loss: y = h W^T + b (one warp per sample); y_hat = y/|y|;
+// when t is given, loss += 1 - y_hat.t and dy = -(t - (y_hat.t) y_hat)/|y|/n.
+__global__ void k_layer_out(const __nv_bfloat16* __restrict__ h, int64_t n, int hidden,
+                            const float* __restrict__ W, const float* __restrict__ b, int n_out,
+                            const float* __restrict__ t, float* __restrict__ y_hat,
+                            float* __restrict__ dy, float* __restrict__ loss) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = warp; r < n; r += nw) {
+    float y[3] = {0.f, 0.f, 0.f};
+    for (int i = lane; i < hidden; i += 32) {
+      const float hv = __bfloat162float(h[r * hidden + i]);
+      for (int c = 0; c < 3; ++c) y[c] = fmaf(W[c * hidden + i], hv, y[c]);
+    }
+    for (int c = 0; c < 3; ++c)
+      for (int o = 16; o > 0; o >>= 1) y[c] += __shfl_xor_sync(0xffffffffu, y[c], o);
+    if (lane == 0) {
+      for (int c = 0; c < 3; ++c) y[c] += b[c];
+      const float nrm = sqrtf(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
+      const float inv = nrm > 0.f ? 1.f / nrm : 0.f;
+      float yh[3] = {y[0] * inv, y[1] * inv, y[2] * inv};
+      if (y_hat)
+        for (int c = 0; c < 3; ++c) y_hat[r * 3 + c] = yh[c];
+      if (t) {
+        const float d = yh[0] * t[r * 3] + yh[1] * t[r * 3 + 1] + yh[2] * t[r * 3 + 2];
+        atomicAdd(loss, 1.f - d);
+        for (int c = 0; c < 3; ++c)
+          dy[r * 3 + c] = -(t[r * 3 + c] - d * yh[c]) * inv / (float)n;
+      }
+    }
+  }
+}
+
+// dH = dy W (per sample, FP32), masked by ReLU of h, to bf16 dz.
+__global__ void k_out_backward_data(const float* __restrict__ dy, int64_t n, int hidden,
+                                    const float* __restrict__ W, const __nv_bfloat16* __restrict__ h,
+                                    __nv_bfloat16* __restrict__ dz) {
+  const int64_t total = n * hidden;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / hidden;
+    const int i = (int)(e % hidden);
+    float v = dy[r * 3] * W[i] + dy[r * 3 + 1] * W[hidden + i] + dy[r * 3 + 2] * W[2 * hidden + i];
+    if (!(__bfloat162float(h[e]) > 0.f)) v = 0.f;
+    dz[e] = __float2bfloat16_rn(v);
+  }
+}
+
+// Gradient of a thin layer: dW[o][i] = sum_r dz[r][o] a[r][i], db[o] = sum_r dz[r][o]
+// with dz FP32 [n][no] (output layer) or bf16 (input layer), a bf16 [n][ni] or FP32.
+template <class DZ, class AT>
+__global__ void k_thin_grad(const DZ* __restrict__ dz, int no, const AT* __restrict__ a, int ni,
+                            int64_t n, float* __restrict__ dW, float* __restrict__ db) {
+  const int o = blockIdx.y, i = blockIdx.z;  // i == ni: bias
+  float acc = 0.f;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const float d = (float)dz[r * no + o];
+    acc += i < ni ? d * (float)a[r * ni + i] : d;
+  }
+  for (int s = 16; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);
+  __shared__ float sh[32];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float v = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.f;
+    for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
+    if (threadIdx.x == 0) atomicAdd(i < ni ? dW + o * ni + i : db + o, v);
+  }
+}
+
+// Column sums of a bf16 [n][cols] matrix into FP32 db (atomic).
+__global__ void k_colsum(const __nv_bfloat16* __restrict__ z, int64_t n, int cols,
+                         float* __restrict__ db) {
+  const int c = blockIdx.y * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  float acc = 0.f;
+  for (int64_t r = blockIdx.x; r < n; r += gridDim.x) acc += __bfloat162float(z[r * cols + c]);
+  atomicAdd(db + c, acc);
+}
+
+// Transpose a bf16 [rows][cols] matrix into [cols][rows] (32 x 32 tiles).
+__global__ void k_transpose(const __nv_bfloat16* __restrict__ in, int64_t rows, int cols,
+                            __nv_bfloat16* __restrict__ out) {
+  __shared__ __nv_bfloat16 tile[32][33];
+  const int64_t r0 = blockIdx.x * 32ll;
+  const int c0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y)
+    tile[k][threadIdx.x] = in[(r0 + k) * cols + c0 + threadIdx.x];
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y)
+    out[(int64_t)(c0 + k) * rows + r0 + threadIdx.x] = tile[threadIdx.x][k];
+}
+
+__global__ void k_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1,
+                       float b2, float eps, float c1, float c2) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+// bf16 copies W (hidden x hidden) and W^T of a hidden layer.
+__global__ void k_to_bf16_pair(const float* __restrict__ W, int n, __nv_bfloat16* __restrict__ wb,
+                               __nv_bfloat16* __restrict__ wbt) {
+  const int64_t total = (int64_t)n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int o = (int)(e / n), i = (int)(e % n);
+    const __nv_bfloat16 v = __float2bfloat16_rn(W[e]);
+    wb[e] = v;
+    wbt[(int64_t)i * n + o] = v;
+  }
+}
+
+// He-normal initialisation from Philox (tag 4, id = parameter index):
+// W ~ N(0, 2 / fan_in) for ReLU layers, N(0, 1 / fan_in) for the output.
+__global__ void k_init(float* p, int64_t n, const int64_t* off, const int* fan_in, const int* kind,
+                       int n_layers, uint64_t seed) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int l = 0;
+    while (l + 1 < n_layers * 2 && off[l + 1] <= k) ++l;
+    if (kind[l] == 1) {  // bias
+      p[k] = 0.f;
+      continue;
+    }
+    const Philox4 w = draw4(seed, 4u, (uint64_t)k, 0u);
+    const double u1 = u01_open(w.v0, w.v1), u2 = u01_open(w.v2, w.v3);
+    const double z = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+    const double var = (l / 2 == n_layers - 1 ? 1.0 : 2.0) / (double)fan_in[l];
+    p[k] = (float)(z * sqrt(var));
+  }
+}
+
+int nblk(int64_t n, int b) {
+  const int64_t g = (n + b - 1) / b;
+  return (int)(g < 1 ? 1 : (g > 65536 ? 65536 : g));
+}
+
+void free_ws(crp_mlp* M) {
+  for (auto* p : M->h) dev_free(p);
+  M->h.clear();
+  dev_free(M->dz);
+  dev_free(M->dz2);
+  dev_free(M->dzt);
+  dev_free(M->ht);
+  dev_free(M->y);
+  dev_free(M->dy);
+  dev_free(M->loss);
+  M->dz = M->dz2 = M->dzt = M->ht = nullptr;
+  M->y = M->dy = M->loss = nullptr;
+  M->cap = 0;
+}
+
+crp_status ensure_ws(crp_mlp* M, int64_t n) {
+  if (M->cap >= n) return CRP_OK;
+  free_ws(M);
+  const size_t hb = sizeof(__nv_bfloat16) * (size_t)n * M->hidden;
+  for (int l = 0; l < M->n_hidden; ++l) M->h.push_back(static_cast<__nv_bfloat16*>(dev_alloc(hb)));
+  M->dz = static_cast<__nv_bfloat16*>(dev_alloc(hb));
+  M->dz2 = static_cast<__nv_bfloat16*>(dev_alloc(hb));
+  M->dzt = static_cast<__nv_bfloat16*>(dev_alloc(hb));
+  M->ht = static_cast<__nv_bfloat16*>(dev_alloc(hb));
+  M->y = static_cast<float*>(dev_alloc(sizeof(float) * 3 * n));
+  M->dy = static_cast<float*>(dev_alloc(sizeof(float) * 3 * n));
+  M->loss = static_cast<float*>(dev_alloc(sizeof(float)));
+  bool ok = M->dz && M->dz2 && M->dzt && M->ht && M->y && M->dy && M->loss;
+  for (auto* p : M->h) ok = ok && p;
+  if (!ok) {
+    free_ws(M);
+    set_error("mlp: cannot allocate the workspace for %lld samples", (long long)n);
+    return CRP_E_OOM;
+  }
+  M->cap = n;
+  return CRP_OK;
+}
+
+crp_status refresh_bf16(crp_mlp* M, cudaStream_t s) {
+  for (int l = 1; l < M->n_hidden; ++l)
+    k_to_bf16_pair<<<nblk((int64_t)M->hidden * M->hidden, 256), 256, 0, s>>>(
+        M->params + M->w_off[l], M->hidden, M->wb[l], M->wbt[l]);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? CRP_OK : fail_cuda(e, "mlp: bf16 weights");
+}
+
+template <int EPI>
+void gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* Bt, int ldb, int64_t M, int N, int K,
+          int splits, const float* bias, const __nv_bfloat16* mask, __nv_bfloat16* out_bf,
+          float* out_f, int ldc, cudaStream_t s) {
+  dim3 grid((unsigned)(M / BM), (unsigned)(N / BN), (unsigned)splits);
+  k_gemm_bf16<EPI><<<grid, GEMM_THREADS, 0, s>>>(A, lda, Bt, ldb, K, splits, bias, mask, out_bf,
+                                                 out_f, ldc);
+}
+
+// Forward over n samples (n a multiple of 128): activations in M->h, the
+// normalised output in y_hat; with targets, the loss and dy as well.
+crp_status forward(crp_mlp* M, const float* x, int64_t n, const float* t, float* y_hat,
+                   cudaStream_t s) {
+  const int H = M->hidden;
+  k_layer_in<<<nblk(n * H, 256), 256, 0, s>>>(x, M->n_in, n, M->params + M->w_off[0],
+                                              M->params + M->b_off[0], H, M->h[0]);
+  for (int l = 1; l < M->n_hidden; ++l)
+    gemm<EPI_BIAS_RELU>(M->h[l - 1], H, M->wb[l], H, n, H, H, 1, M->params + M->b_off[l], nullptr,
+                        M->h[l], nullptr, H, s);
+  const int lo = M->n_hidden;
+  if (t) cudaMemsetAsync(M->loss, 0, sizeof(float), s);
+  k_layer_out<<<nblk(n * 32, 256), 256, 0, s>>>(M->h[lo - 1], n, H, M->params + M->w_off[lo],
+                                                M->params + M->b_off[lo], 3, t, y_hat, M->dy,
+                                                M->loss);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? CRP_OK : fail_cuda(e, "mlp: forward");
+}
+
+crp_status backward(crp_mlp* M, const float* x, int64_t n, cudaStream_t s) {
+  const int H = M->hidden, L = M->n_hidden;
+  cudaMemsetAsync(M->grad, 0, sizeof(float) * M->n_params, s);
+  // output layer
+  k_thin_grad<float, __nv_bfloat16><<<dim3(64, 3, H + 1), 256, 0, s>>>(
+      M->dy, 3, M->h[L - 1], H, n, M->grad + M->w_off[L], M->grad + M->b_off[L]);
+  k_out_backward_data<<<nblk(n * H, 256), 256, 0, s>>>(M->dy, n, H, M->params + M->w_off[L],
+                                                       M->h[L - 1], M->dz);
+  __nv_bfloat16* dz = M->dz;
+  __nv_bfloat16* dz_next = M->dz2;
+  const int splits = n >= 128 * 64 ? 32 : (int)(n / 128 < 1 ? 1 : n / 128);
+  for (int l = L - 1; l >= 1; --l) {
+    // W_l maps h[l-1] -> h[l]; dz holds dL/dz_l (bf16, [n][H])
+    const dim3 tb(32, 8);
+    k_transpose<<<dim3((unsigned)(n / 32), H / 32), tb, 0, s>>>(dz, n, H, M->dzt);
+    k_transpose<<<dim3((unsigned)(n / 32), H / 32), tb, 0, s>>>(M->h[l - 1], n, H, M->ht);
+    int sp = splits;
+    while (sp > 1 && (n / sp) % BK != 0) --sp;
+    gemm<EPI_ATOMIC>(M->dzt, (int)n, M->ht, (int)n, H, H, (int)n, sp, nullptr, nullptr, nullptr,
+                     M->grad + M->w_off[l], H, s);
+    k_colsum<<<dim3(256, (H + 255) / 256), 256, 0, s>>>(dz, n, H, M->grad + M->b_off[l]);
+    gemm<EPI_MASK>(dz, H, M->wbt[l], H, n, H, H, 1, nullptr, M->h[l - 1], dz_next, nullptr, H, s);
+    __nv_bfloat16* tmp = dz;
+    dz = dz_next;
+    dz_next = tmp;
+  }
+  // input layer: dz holds dL/dz_1
+  k_thin_grad<__nv_bfloat16, float><<<dim3(64, H, M->n_in + 1), 256, 0, s>>>(
+      dz, H, x, M->n_in, n, M->grad + M->w_off[0], M->grad + M->b_off[0]);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? CRP_OK : fail_cuda(e, "mlp: backward");
+}
+
+}  // namespace
+
+extern "C" {
+
+crp_status crp_mlp_create(crp_context* ctx, int32_t n_in, int32_t hidden, int32_t n_hidden,
+                          uint64_t seed, crp_mlp** out) {
+  if (!ctx || !out || n_in < 1 || n_in > 64 || hidden < 128 || hidden % 128 != 0 ||
+      hidden > 4096 || n_hidden < 1 || n_hidden > 16) {
+    set_error("crp_mlp_create: need 1 <= n_in <= 64, hidden a multiple of 128 (<= 4096), "
+              "1 <= n_hidden <= 16");
+    return CRP_E_INVALID;
+  }
+  *out = nullptr;
+  crp_mlp* M = new (std::nothrow) crp_mlp;
+  if (!M) {
+    set_error("crp_mlp_create: host allocation failed");
+    return CRP_E_OOM;
+  }
+  M->n_in = n_in;
+  M->hidden = hidden;
+  M->n_hidden = n_hidden;
+  M->n_out = 3;
+  M->step = 0;
+  M->cap = 0;
+  M->dz = M->dz2 = M->dzt = M->ht = nullptr;
+  M->y = M->dy = M->loss = nullptr;
+  {
+    DevState unused;
+    uint64_t n_unused = 0, seed_unused = 0;
+    context_pool(ctx, &unused, &n_unused, &M->device, &seed_unused);
+    cudaSetDevice(M->device);
+  }
+  int64_t off = 0;
+  std::vector<int64_t> offs;
+  std::vector<int> fan, kind;
+  for (int l = 0; l <= n_hidden; ++l) {
+    const int fi = l == 0 ? n_in : hidden;
+    const int fo = l == n_hidden ? 3 : hidden;
+    M->w_off.push_back(off);
+    offs.push_back(off);
+    fan.push_back(fi);
+    kind.push_back(0);
+    off += (int64_t)fo * fi;
+    M->b_off.push_back(off);
+    offs.push_back(off);
+    fan.push_back(fi);
+    kind.push_back(1);
+    off += fo;
+  }
+  M->n_params = off;
+  M->params = static_cast<float*>(dev_alloc(sizeof(float) * off));
+  M->grad = static_cast<float*>(dev_alloc(sizeof(float) * off));
+  M->m = static_cast<float*>(dev_alloc(sizeof(float) * off));
+  M->v = static_cast<float*>(dev_alloc(sizeof(float) * off));
+  M->wb.assign(n_hidden, nullptr);
+  M->wbt.assign(n_hidden, nullptr);
+  bool ok = M->params && M->grad && M->m && M->v;
+  for (int l = 1; l < n_hidden; ++l) {
+    M->wb[l] = static_cast<__nv_bfloat16*>(dev_alloc(sizeof(__nv_bfloat16) * hidden * hidden));
+    M->wbt[l] = static_cast<__nv_bfloat16*>(dev_alloc(sizeof(__nv_bfloat16) * hidden * hidden));
+    ok = ok && M->wb[l] && M->wbt[l];
+  }
+  int64_t* d_off = static_cast<int64_t*>(dev_alloc(sizeof(int64_t) * offs.size()));
+  int* d_fan = static_cast<int*>(dev_alloc(sizeof(int) * fan.size()));
+  int* d_kind = static_cast<int*>(dev_alloc(sizeof(int) * kind.size()));
+  crp_status st = CRP_OK;
+  if (!ok || !d_off || !d_fan || !d_kind) {
+    st = CRP_E_OOM;
+    set_error("crp_mlp_create: device allocation failed");
+  } else {
+    cudaMemcpy(d_off, offs.data(), sizeof(int64_t) * offs.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(d_fan, fan.data(), sizeof(int) * fan.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(d_kind, kind.data(), sizeof(int) * kind.size(), cudaMemcpyHostToDevice);
+    k_init<<<nblk(off, 256), 256>>>(M->params, off, d_off, d_fan, d_kind, n_hidden + 1, seed);
+    cudaMemset(M->m, 0, sizeof(float) * off);
+    cudaMemset(M->v, 0, sizeof(float) * off);
+    st = refresh_bf16(M, 0);
+    const cudaError_t e = cudaDeviceSynchronize();
+    if (st == CRP_OK && e != cudaSuccess) st = fail_cuda(e, "crp_mlp_create");
+  }
+  dev_free(d_off);
+  dev_free(d_fan);
+  dev_free(d_kind);
+  if (st != CRP_OK) {
+    crp_mlp_destroy(M);
+    return st;
+  }
+  *out = M;
+  return CRP_OK;
+}
+
+crp_status crp_mlp_destroy(crp_mlp* M) {
+  if (!M) return CRP_OK;
+  cudaDeviceSynchronize();
+  free_ws(M);
+  dev_free(M->params);
+  dev_free(M->grad);
+  dev_free(M->m);
+  dev_free(M->v);
+  for (auto* p : M->wb) dev_free(p);
+  for (auto* p : M->wbt) dev_free(p);
+  delete M;
+  return CRP_OK;
+}
+
+int64_t crp_mlp_num_params(const crp_mlp* M) { return M ? M->n_params : 0; }
+
+crp_status crp_mlp_set_params(crp_mlp* M, const float* host) {
+  if (!M || !host) {
+    set_error("crp_mlp_set_params: NULL argument");
+    return CRP_E_INVALID;
+  }
+  cudaError_t e = cudaMemcpy(M->params, host, sizeof(float) * M->n_params, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail_cuda(e, "crp_mlp_set_params");
+  cudaMemset(M->m, 0, sizeof(float) * M->n_params);
+  cudaMemset(M->v, 0, sizeof(float) * M->n_params);
+  M->step = 0;
+  crp_status st = refresh_bf16(M, 0);
+  e = cudaDeviceSynchronize();
+  return st != CRP_OK ? st : (e == cudaSuccess ? CRP_OK : fail_cuda(e, "crp_mlp_set_params"));
+}
+
+crp_status crp_mlp_get_params(const crp_mlp* M, float* host, float* host_grad) {
+  if (!M || (!host && !host_grad)) {
+    set_error("crp_mlp_get_params: NULL argument");
+    return CRP_E_INVALID;
+  }
+  cudaError_t e = cudaSuccess;
+  if (host) e = cudaMemcpy(host, M->params, sizeof(float) * M->n_params, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && host_grad)
+    e = cudaMemcpy(host_grad, M->grad, sizeof(float) * M->n_params, cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? CRP_OK : fail_cuda(e, "crp_mlp_get_params");
+}
+
+crp_status crp_mlp_forward(crp_mlp* M, const float* x, float* y_hat, int64_t n, void* stream) {
+  if (!M || !x || !y_hat || n < 0) {
+    set_error("crp_mlp_forward: bad argument");
+    return CRP_E_INVALID;
+  }
+  if (n == 0) return CRP_OK;
+  if (n % 128 != 0) {
+    set_error("crp_mlp_forward: n must be a multiple of 128 (got %lld)", (long long)n);
+    return CRP_E_INVALID;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t chunk = n < (1 << 20) ? n : (1 << 20);  // bounds the activation workspace
+  crp_status st = ensure_ws(M, chunk);
+  for (int64_t r0 = 0; st == CRP_OK && r0 < n; r0 += chunk) {
+    const int64_t m = n - r0 < chunk ? n - r0 : chunk;
+    st = forward(M, x + r0 * M->n_in, m, nullptr, y_hat + r0 * 3, s);
+  }
+  return st;
+}
+
+crp_status crp_mlp_train_step(crp_mlp* M, const float* x, const float* t, int64_t n, float lr,
+                              float* loss_out, void* stream) {
+  if (!M || !x || !t || n < 128 || n % 128 != 0 || !(lr >= 0.f)) {
+    set_error("crp_mlp_train_step: need a batch n >= 128, multiple of 128, lr >= 0");
+    return CRP_E_INVALID;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  crp_status st = ensure_ws(M, n);
+  if (st == CRP_OK) st = forward(M, x, n, t, nullptr, s);
+  if (st == CRP_OK) st = backward(M, x, n, s);
+  if (st == CRP_OK && lr > 0.f) {
+    M->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)M->step), c2 = 1.f - powf(b2, (float)M->step);
+    k_adam<<<nblk(M->n_params, 256), 256, 0, s>>>(M->params, M->grad, M->m, M->v, M->n_params, lr,
+                                                  b1, b2, 1e-8f, c1, c2);
+    st = refresh_bf16(M, s);
+  }
+  if (st == CRP_OK && loss_out) {
+    float l = 0.f;
+    cudaError_t e = cudaMemcpyAsync(&l, M->loss, sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_cuda(e, "crp_mlp_train_step");
+    *loss_out = l / (float)n;
+  }
+  return st;
+}
+
+}  // extern "C"

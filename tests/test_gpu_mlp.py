@@ -1,0 +1,132 @@
+"""MLP lens surrogate on the GPU against the fp64 oracle: forward and
+gradients on the same bf16-rounded hidden weights (the GPU keeps activations
+and backward signals in bf16, so agreement is to bf16 precision), the Adam
+update, and training on a smooth target."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+import oracle.mlp as M  # noqa: E402
+from paper_1307_2643_gb300 import crp  # noqa: E402
+
+SHAPES = M.layer_shapes(4, 256, 4, 3)
+
+
+@pytest.fixture(scope="module")
+def torch_dev():
+    import torch
+    from paper_1307_2643_gb300.build import build
+    build()
+    return torch
+
+
+def _params(seed=1):
+    g = np.random.default_rng(seed)
+    parts = []
+    for l, (o, i) in enumerate(SHAPES):
+        scale = np.sqrt((1.0 if l == len(SHAPES) - 1 else 2.0) / i)
+        parts += [g.normal(scale=scale, size=o * i), g.normal(scale=0.05, size=o)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def _oracle_view(p32):
+    """The parameters as the GPU uses them: hidden-to-hidden weights in bf16."""
+    flat = p32.astype(np.float64)
+    Ws, bs = M.unpack(flat.copy(), SHAPES)
+    for l in range(1, len(SHAPES) - 1):
+        Ws[l] = M.bf16_round(Ws[l])
+    return M.pack(Ws, bs)
+
+
+def _batch(n, seed):
+    g = np.random.default_rng(seed)
+    d = g.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    R = 10 ** g.uniform(18, 20, n)
+    x = M.inputs(d, R).astype(np.float32)
+    # smooth target: a rigidity-dependent rotation about z of the direction
+    ang = 0.8 * (20 - np.log10(R))
+    c, s = np.cos(ang), np.sin(ang)
+    t = np.stack([c * d[:, 0] - s * d[:, 1], s * d[:, 0] + c * d[:, 1], d[:, 2]], axis=1)
+    return x, t.astype(np.float32)
+
+
+def test_mlp_forward_matches_oracle(torch_dev):
+    torch = torch_dev
+    p = _params()
+    x, _ = _batch(1024, 2)
+    ctx = crp.crp_context_create(0, 1, 16)
+    try:
+        mlp = crp.crp_mlp_create(ctx, 4, 256, 4, 7)
+        assert crp.crp_mlp_num_params(mlp) == M.n_params(SHAPES)
+        crp.crp_mlp_set_params(mlp, p)
+        xd = torch.from_numpy(x).cuda()
+        yd = torch.zeros((1024, 3), dtype=torch.float32, device="cuda")
+        crp.crp_mlp_forward(mlp, xd, yd, 1024)
+        torch.cuda.synchronize()
+        y = yd.cpu().numpy().astype(np.float64)
+        crp.crp_mlp_destroy(mlp)
+    finally:
+        crp.crp_context_destroy(ctx)
+    ref, _ = M.forward(_oracle_view(p), SHAPES, x.astype(np.float64))
+    ang = M.angle_deg(y, ref)
+    assert np.median(ang) < 0.3 and np.max(ang) < 3.0, (np.median(ang), np.max(ang))
+
+
+def test_mlp_gradients_and_adam_match_oracle(torch_dev):
+    torch = torch_dev
+    p = _params(3)
+    x, t = _batch(2048, 4)
+    ctx = crp.crp_context_create(0, 1, 16)
+    try:
+        mlp = crp.crp_mlp_create(ctx, 4, 256, 4, 7)
+        crp.crp_mlp_set_params(mlp, p)
+        xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+        loss0 = crp.crp_mlp_train_step(mlp, xd, td, 2048, 0.0)
+        _, g = crp.crp_mlp_get_params(mlp)
+        crp.crp_mlp_train_step(mlp, xd, td, 2048, 1e-3)
+        p1, g1 = crp.crp_mlp_get_params(mlp)
+        crp.crp_mlp_destroy(mlp)
+    finally:
+        crp.crp_context_destroy(ctx)
+    flat = _oracle_view(p)
+    y, cache = M.forward(flat, SHAPES, x.astype(np.float64))
+    assert abs(loss0 - M.loss(y, t.astype(np.float64))) < 2e-3 * max(1.0, loss0)
+    ref = M.backward(flat, SHAPES, cache, t.astype(np.float64))
+    Wg, bg = M.unpack(g.astype(np.float64), SHAPES)
+    Wr, br = M.unpack(ref, SHAPES)
+    for l in range(len(SHAPES)):
+        for got, want in ((Wg[l], Wr[l]), (bg[l], br[l])):
+            rel = np.linalg.norm(got - want) / np.linalg.norm(want)
+            assert rel < 2e-2, (l, rel)
+    # Adam on the GPU's own gradient, first step
+    p_ref, _, _ = M.adam(p.astype(np.float64), g1.astype(np.float64), 0.0, 0.0, 1, 1e-3)
+    assert np.max(np.abs(p1 - p_ref)) < 1e-6 + 1e-5 * np.max(np.abs(p_ref))
+
+
+def test_mlp_training_learns_smooth_map(torch_dev):
+    torch = torch_dev
+    x, t = _batch(65536, 5)
+    xv, tv = _batch(4096, 6)
+    ctx = crp.crp_context_create(0, 1, 16)
+    try:
+        mlp = crp.crp_mlp_create(ctx, 4, 256, 4, 11)
+        xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+        first = None
+        for it in range(400):
+            lo = (it * 4096) % 65536
+            loss = crp.crp_mlp_train_step(mlp, xd[lo:lo + 4096], td[lo:lo + 4096], 4096, 2e-3,
+                                          want_loss=(it % 50 == 0))
+            if first is None:
+                first = loss
+        yd = torch.zeros((4096, 3), dtype=torch.float32, device="cuda")
+        crp.crp_mlp_forward(mlp, torch.from_numpy(xv).cuda(), yd, 4096)
+        torch.cuda.synchronize()
+        y = yd.cpu().numpy().astype(np.float64)
+        crp.crp_mlp_destroy(mlp)
+    finally:
+        crp.crp_context_destroy(ctx)
+    ang = M.angle_deg(y, tv.astype(np.float64))
+    assert first > 0.1
+    assert np.median(ang) < 3.0, np.median(ang)
