@@ -368,6 +368,13 @@ crp_status crp_mlp_forward(crp_mlp* mlp, const float* x, float* y_hat, int64_t n
 crp_status crp_mlp_train_step(crp_mlp* mlp, const float* x, const float* t, int64_t n, float lr,
                               float* loss_out, void* stream);
 
+/* A lens whose border directions come from the surrogate network instead
+ * of back-tracking: sample k's network input is (dirs[k], log10(E[k]/eV) - 19)
+ * and its border pixel is the pixel of the predicted direction; the columns
+ * are built as in crp_lens_build (d->earth is not used). */
+crp_status crp_lens_build_surrogate(crp_context* ctx, crp_mlp* mlp, const crp_lens_desc* d,
+                                    crp_lens** out);
+
 /* HEALPix RING arrival map of the selected records: source 0 counts the
  * arrival direction -u at the candidate (extragalactic sky), source 1 the
  * lens_pixel (sky at Earth; shadowed / not applied are skipped).  out: host

@@ -120,7 +120,7 @@ SYMBOLS = (
     "crp_lens_build", "crp_lens_apply", "crp_lens_copy_out", "crp_lens_destroy",
     "crp_histogram_healpix",
     "crp_mlp_create", "crp_mlp_destroy", "crp_mlp_num_params", "crp_mlp_set_params",
-    "crp_mlp_get_params", "crp_mlp_forward", "crp_mlp_train_step",
+    "crp_mlp_get_params", "crp_mlp_forward", "crp_mlp_train_step", "crp_lens_build_surrogate",
 )
 
 _lock = threading.Lock()
@@ -171,6 +171,7 @@ def lib():
             L.crp_mlp_get_params.argtypes = [p, p, p]
             L.crp_mlp_forward.argtypes = [p, p, p, C.c_int64, p]
             L.crp_mlp_train_step.argtypes = [p, p, p, C.c_int64, C.c_float, p, p]
+            L.crp_lens_build_surrogate.argtypes = [p, p, C.POINTER(LensDesc), C.POINTER(p)]
             for name in SYMBOLS:
                 if name not in ("crp_last_error", "crp_version"):
                     getattr(L, name).restype = st
@@ -345,6 +346,18 @@ def crp_lens_build(ctx, galaxy, modules: Modules, nside, n_bins, r_lo, r_hi, ear
     s = Stats()
     _check(lib().crp_lens_build(ctx, galaxy, C.byref(modules), C.byref(d), C.byref(h), C.byref(s)))
     return h, s
+
+
+def crp_lens_build_surrogate(ctx, mlp, nside, n_bins, r_lo, r_hi, dirs, E, bins):
+    dirs = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    bins = np.ascontiguousarray(bins, dtype=np.int32)
+    d = LensDesc()
+    d.nside, d.n_bins, d.r_lo, d.r_hi = nside, n_bins, r_lo, r_hi
+    d.dirs, d.E, d.bin, d.n_samples = dirs.ctypes.data, E.ctypes.data, bins.ctypes.data, len(E)
+    h = C.c_void_p()
+    _check(lib().crp_lens_build_surrogate(ctx, mlp, C.byref(d), C.byref(h)))
+    return h
 
 
 def crp_lens_apply(ctx, lens, what=COLLECT_ALL, stream=None):

@@ -232,6 +232,95 @@ void lens_free(crp_lens* L) {
   delete L;
 }
 
+
+// A lens shell with zeroed column counts (col_start doubles as the count
+// array until lens_columns scans it).
+crp_lens* lens_alloc(int device, const crp_lens_desc* d, int64_t npix, int64_t n_cols) {
+  crp_lens* L = new (std::nothrow) crp_lens;
+  if (!L) return nullptr;
+  memset(L, 0, sizeof(*L));
+  L->device = device;
+  L->nside = d->nside;
+  L->n_bins = d->n_bins;
+  L->r_lo = d->r_lo;
+  L->r_hi = d->r_hi;
+  L->npix = npix;
+  L->n_cols = n_cols;
+  L->col_start = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * (n_cols + 1)));
+  L->max_count = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * d->n_bins));
+  if (!L->col_start || !L->max_count ||
+      cudaMemset(L->col_start, 0, sizeof(uint32_t) * (n_cols + 1)) != cudaSuccess) {
+    lens_free(L);
+    return nullptr;
+  }
+  return L;
+}
+
+// Columns from per-sample keys (kNoKey: skipped) and Earth pixels, with the
+// per-column counts already accumulated in L->col_start: exclusive scan,
+// scatter, canonical order inside each column, largest count per bin.
+crp_status lens_columns(crp_lens* L, const uint32_t* key, const uint32_t* earth, uint64_t n) {
+  uint32_t* fill = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * (L->n_cols + 1)));
+  uint32_t* total = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t)));
+  crp_status st = CRP_OK;
+  if (!fill || !total) {
+    st = CRP_E_OOM;
+    set_error("lens: column workspace allocation failed");
+  }
+  if (st == CRP_OK) st = scan_inplace(L->col_start, L->n_cols + 1, total, nullptr);
+  uint32_t n_entries = 0;
+  if (st == CRP_OK) {
+    cudaError_t e = cudaMemcpy(&n_entries, total, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(fill, L->col_start, sizeof(uint32_t) * (L->n_cols + 1),
+                     cudaMemcpyDeviceToDevice);
+    if (e != cudaSuccess) st = fail_cuda(e, "lens: counts");
+  }
+  if (st == CRP_OK) {
+    L->n_entries = n_entries;
+    L->entries = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * (n_entries ? n_entries : 1)));
+    if (!L->entries) {
+      st = CRP_E_OOM;
+      set_error("lens: entries allocation failed");
+    }
+  }
+  if (st == CRP_OK) {
+    k_lens_scatter<<<blocks(n, 256), 256>>>(key, earth, n, fill, L->entries);
+    k_lens_sort_columns<<<blocks(L->n_cols, 256), 256>>>(L->col_start, L->n_cols, L->entries);
+    k_lens_max<<<L->n_bins, 256>>>(L->col_start, L->npix, L->n_bins, L->max_count);
+    const cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) st = fail_cuda(e, "lens: columns");
+  }
+  dev_free(fill);
+  dev_free(total);
+  return st;
+}
+
+// Surrogate lens inputs and keys: x = (n, log10 R - 19) per sample; after the
+// network, key = bin * npix + pixel(predicted border direction).
+__global__ void k_surrogate_inputs(const double* dirs, const double* E, int64_t n, float* x) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    x[4 * k] = (float)dirs[3 * k];
+    x[4 * k + 1] = (float)dirs[3 * k + 1];
+    x[4 * k + 2] = (float)dirs[3 * k + 2];
+    x[4 * k + 3] = (float)(log10(E[k]) - 19.0);
+  }
+}
+
+__global__ void k_surrogate_keys(const double* dirs, const float* y, const int32_t* bin,
+                                 int64_t n, int64_t nside, int64_t npix, uint32_t* key,
+                                 uint32_t* earth, uint32_t* counts) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    earth[k] = (uint32_t)healpix_ring_pixel(nside, dirs[3 * k], dirs[3 * k + 1], dirs[3 * k + 2]);
+    const int64_t j = healpix_ring_pixel(nside, y[3 * k], y[3 * k + 1], y[3 * k + 2]);
+    const uint32_t c = (uint32_t)((int64_t)bin[k] * npix + j);
+    key[k] = c;
+    atomicAdd(counts + c, 1u);
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -300,32 +389,14 @@ crp_status crp_lens_build(crp_context* ctx, const crp_grid* galaxy, const crp_mo
   if (stats_out) *stats_out = bstats;
 
   crp_lens* L = nullptr;
-  uint32_t *key = nullptr, *earth = nullptr, *fill = nullptr, *dbin = nullptr, *total = nullptr;
+  uint32_t *key = nullptr, *earth = nullptr, *dbin = nullptr;
   if (st == CRP_OK) {
-    L = new (std::nothrow) crp_lens;
-    if (!L) {
+    key = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * n));
+    earth = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * n));
+    dbin = static_cast<uint32_t*>(dev_alloc(sizeof(int32_t) * n));
+    if (!key || !earth || !dbin) {
       st = CRP_E_OOM;
-      set_error("crp_lens_build: host allocation failed");
-    } else {
-      memset(L, 0, sizeof(*L));
-      L->device = device;
-      L->nside = d->nside;
-      L->n_bins = d->n_bins;
-      L->r_lo = d->r_lo;
-      L->r_hi = d->r_hi;
-      L->npix = npix;
-      L->n_cols = n_cols;
-      L->col_start = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * (n_cols + 1)));
-      L->max_count = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * d->n_bins));
-      key = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * n));
-      earth = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * n));
-      dbin = static_cast<uint32_t*>(dev_alloc(sizeof(int32_t) * n));
-      fill = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * (n_cols + 1)));
-      total = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t)));
-      if (!L->col_start || !L->max_count || !key || !earth || !dbin || !fill || !total) {
-        st = CRP_E_OOM;
-        set_error("crp_lens_build: device allocation failed");
-      }
+      set_error("crp_lens_build: device allocation failed");
     }
   }
   if (st == CRP_OK) {
@@ -333,44 +404,114 @@ crp_status crp_lens_build(crp_context* ctx, const crp_grid* galaxy, const crp_mo
     uint64_t bn = 0, bseed = 0;
     int bdev = 0;
     context_pool(bt, &bst, &bn, &bdev, &bseed);
-    cudaError_t e = cudaMemcpy(dbin, d->bin, sizeof(int32_t) * n, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(L->col_start, 0, sizeof(uint32_t) * (n_cols + 1));
+    L = lens_alloc(device, d, npix, n_cols);
+    cudaError_t e = L ? cudaMemcpy(dbin, d->bin, sizeof(int32_t) * n, cudaMemcpyHostToDevice)
+                      : cudaErrorMemoryAllocation;
     if (e == cudaSuccess) {
       k_lens_keys<<<blocks(n, 256), 256>>>(bst, n, (const int32_t*)dbin, d->nside, npix, key,
                                            earth, L->col_start);
       e = cudaGetLastError();
     }
-    if (e != cudaSuccess) st = fail_cuda(e, "crp_lens_build: keys");
-    if (st == CRP_OK) st = scan_inplace(L->col_start, n_cols + 1, total, nullptr);
-    uint32_t n_entries = 0;
-    if (st == CRP_OK) {
-      e = cudaMemcpy(&n_entries, total, sizeof(uint32_t), cudaMemcpyDeviceToHost);
-      if (e == cudaSuccess) e = cudaMemcpy(fill, L->col_start, sizeof(uint32_t) * (n_cols + 1),
-                                           cudaMemcpyDeviceToDevice);
-      if (e != cudaSuccess) st = fail_cuda(e, "crp_lens_build: counts");
-    }
-    if (st == CRP_OK) {
-      L->n_entries = n_entries;
-      L->entries = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * (n_entries ? n_entries : 1)));
-      if (!L->entries) {
-        st = CRP_E_OOM;
-        set_error("crp_lens_build: entries allocation failed");
-      }
-    }
-    if (st == CRP_OK) {
-      k_lens_scatter<<<blocks(n, 256), 256>>>(key, earth, n, fill, L->entries);
-      k_lens_sort_columns<<<blocks(n_cols, 256), 256>>>(L->col_start, n_cols, L->entries);
-      k_lens_max<<<d->n_bins, 256>>>(L->col_start, npix, d->n_bins, L->max_count);
-      e = cudaDeviceSynchronize();
-      if (e != cudaSuccess) st = fail_cuda(e, "crp_lens_build: columns");
+    if (e != cudaSuccess) {
+      st = L ? fail_cuda(e, "crp_lens_build: keys") : CRP_E_OOM;
+      if (!L) set_error("crp_lens_build: device allocation failed");
+    } else {
+      st = lens_columns(L, key, earth, n);
     }
   }
   dev_free(key);
   dev_free(earth);
   dev_free(dbin);
-  dev_free(fill);
-  dev_free(total);
   if (bt) crp_context_destroy(bt);
+  if (prev >= 0 && prev != device) cudaSetDevice(prev);
+  if (st != CRP_OK) {
+    lens_free(L);
+    return st;
+  }
+  *out = L;
+  return CRP_OK;
+}
+
+crp_status crp_lens_build_surrogate(crp_context* ctx, crp_mlp* mlp, const crp_lens_desc* d,
+                                    crp_lens** out) {
+  if (!ctx || !mlp || !d || !out || !d->dirs || !d->E || !d->bin) {
+    set_error("crp_lens_build_surrogate: NULL argument");
+    return CRP_E_INVALID;
+  }
+  *out = nullptr;
+  if (d->nside < 1 || d->nside > 8192 || d->n_bins < 1 || !(d->r_lo > 0.0) ||
+      !(d->r_hi > d->r_lo) || d->n_samples < 1) {
+    set_error("crp_lens_build_surrogate: need 1 <= nside <= 8192, n_bins >= 1, 0 < r_lo < r_hi");
+    return CRP_E_INVALID;
+  }
+  const int64_t npix = 12ll * d->nside * d->nside;
+  const int64_t n_cols = npix * d->n_bins;
+  if (n_cols >= 0xFFFFFFFFll || d->n_samples >= 0xFFFFFFFFll) {
+    set_error("crp_lens_build_surrogate: too many columns or samples for 32-bit indices");
+    return CRP_E_INVALID;
+  }
+  for (int64_t k = 0; k < d->n_samples; ++k) {
+    if (d->bin[k] < 0 || d->bin[k] >= d->n_bins) {
+      set_error("crp_lens_build_surrogate: sample %lld has bin %d outside 0..%d", (long long)k,
+                d->bin[k], d->n_bins - 1);
+      return CRP_E_INVALID;
+    }
+  }
+  DevState cst;
+  uint64_t unused_n = 0, seed = 0;
+  int device = 0;
+  context_pool(ctx, &cst, &unused_n, &device, &seed);
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != device) cudaSetDevice(device);
+  const int64_t n = d->n_samples;
+  const int64_t n_pad = (n + 127) / 128 * 128;
+  double* ddirs = static_cast<double*>(dev_alloc(sizeof(double) * 3 * n));
+  double* dE = static_cast<double*>(dev_alloc(sizeof(double) * n));
+  int32_t* dbin = static_cast<int32_t*>(dev_alloc(sizeof(int32_t) * n));
+  float* x = static_cast<float*>(dev_alloc(sizeof(float) * 4 * n_pad));
+  float* y = static_cast<float*>(dev_alloc(sizeof(float) * 3 * n_pad));
+  uint32_t* key = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * n));
+  uint32_t* earth = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * n));
+  crp_status st = CRP_OK;
+  crp_lens* L = nullptr;
+  if (!ddirs || !dE || !dbin || !x || !y || !key || !earth) {
+    st = CRP_E_OOM;
+    set_error("crp_lens_build_surrogate: device allocation failed");
+  }
+  if (st == CRP_OK) {
+    cudaError_t e = cudaMemcpy(ddirs, d->dirs, sizeof(double) * 3 * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dE, d->E, sizeof(double) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dbin, d->bin, sizeof(int32_t) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(x, 0, sizeof(float) * 4 * n_pad);
+    if (e == cudaSuccess) {
+      k_surrogate_inputs<<<blocks(n, 256), 256>>>(ddirs, dE, n, x);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) st = fail_cuda(e, "crp_lens_build_surrogate: inputs");
+  }
+  if (st == CRP_OK) st = crp_mlp_forward(mlp, x, y, n_pad, nullptr);
+  if (st == CRP_OK) {
+    L = lens_alloc(device, d, npix, n_cols);
+    if (!L) {
+      st = CRP_E_OOM;
+      set_error("crp_lens_build_surrogate: lens allocation failed");
+    }
+  }
+  if (st == CRP_OK) {
+    k_surrogate_keys<<<blocks(n, 256), 256>>>(ddirs, y, dbin, n, d->nside, npix, key, earth,
+                                              L->col_start);
+    const cudaError_t e = cudaGetLastError();
+    st = e == cudaSuccess ? lens_columns(L, key, earth, (uint64_t)n)
+                          : fail_cuda(e, "crp_lens_build_surrogate: keys");
+  }
+  dev_free(ddirs);
+  dev_free(dE);
+  dev_free(dbin);
+  dev_free(x);
+  dev_free(y);
+  dev_free(key);
+  dev_free(earth);
   if (prev >= 0 && prev != device) cudaSetDevice(prev);
   if (st != CRP_OK) {
     lens_free(L);

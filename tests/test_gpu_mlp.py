@@ -130,3 +130,39 @@ def test_mlp_training_learns_smooth_map(torch_dev):
     ang = M.angle_deg(y, tv.astype(np.float64))
     assert first > 0.1
     assert np.median(ang) < 3.0, np.median(ang)
+
+
+def test_surrogate_lens_matches_oracle_network(torch_dev):
+    """Lens built from the network's predicted border directions: the same
+    column structure as a lens built from the fp64 oracle network's
+    predictions, up to bf16 rounding moving a few samples across pixel
+    edges."""
+    import oracle
+    import workloads
+    nside, nb = 4, 2
+    dirs, E, bins = workloads.lens_samples(nb, 192 * 4, 1e18, 1e20, 9)
+    p = _params(8)
+    ctx = crp.crp_context_create(0, 1, 16)
+    try:
+        mlp = crp.crp_mlp_create(ctx, 4, 256, 4, 7)
+        crp.crp_mlp_set_params(mlp, p)
+        lens = crp.crp_lens_build_surrogate(ctx, mlp, nside, nb, 1e18, 1e20, dirs, E, bins)
+        got = crp.crp_lens_copy_out(lens, nb * 12 * nside * nside, nb)
+        crp.crp_lens_destroy(lens)
+        crp.crp_mlp_destroy(mlp)
+    finally:
+        crp.crp_context_destroy(ctx)
+    x = np.concatenate([dirs.astype(np.float32), (np.log10(E) - 19.0).astype(np.float32)[:, None]],
+                       axis=1).astype(np.float64)
+    y, _ = M.forward(_oracle_view(p), SHAPES, x)
+    npix = 12 * nside * nside
+    key = bins.astype(np.int64) * npix + oracle.ang2pix_vec(nside, y)
+    counts = np.bincount(key, minlength=nb * npix)
+    got_counts = np.diff(got["col_start"].astype(np.int64))
+    assert got_counts.sum() == len(E)
+    assert np.abs(got_counts - counts).sum() <= 0.06 * len(E)
+    earth = oracle.ang2pix_vec(nside, dirs)
+    # every entry of a column is the Earth pixel of some sample of that column
+    for c in np.nonzero(got_counts)[0][:50]:
+        col = got["entries"][got["col_start"][c]:got["col_start"][c + 1]]
+        assert np.all(np.isin(col, earth[bins == c // npix]))
