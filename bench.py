@@ -52,6 +52,15 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--workload", choices=("mixed", "galactic"), default="mixed",
+                    help="mixed: the propagation benchmark; galactic: back-tracking, MLP "
+                         "surrogate training / inference and lens builds")
+    ap.add_argument("--n-train", type=int, default=9_000_000)
+    ap.add_argument("--n-test", type=int, default=1_000_000)
+    ap.add_argument("--epochs", type=int, default=32)
+    ap.add_argument("--batch", type=int, default=16384)
+    ap.add_argument("--lr", type=float, default=3e-3)
+    ap.add_argument("--lens-per-bin", type=int, default=49152)
     return ap.parse_args()
 
 
@@ -148,6 +157,10 @@ def flops_per_trial_mixed():
       fifth-order offset 8 x 3, direction 9 x 3, error 10 x 3        = 81
     """
     return 6 * (75 + 12) + 105 + 90 + 81
+
+
+# field bytes one Cash-Karp trial reads: 6 trilinear gathers x 8 nodes x 16 B
+GATHER_BYTES_PER_TRIAL_F32 = 6 * 8 * 16
 
 
 def run_ours(args):
@@ -256,23 +269,40 @@ def run_ours(args):
                 "mixed_over_fp64": value / world / (st64.accepted_steps / ft)}
 
     # ---- roofline of the propagate kernel ----------------------------------
+    # denominators measured on this device by the library's own probes
+    probe = crp.crp_measure_peaks(local)
     peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
     sm_mhz = clk.get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 1440.0
-    props = torch.cuda.get_device_properties(local)
-    n_sm = props.multi_processor_count
+    n_sm = probe["sm_count"]
     trials = acc + rej
-    flops = trials * flops_per_trial_mixed() if prec == crp.MIXED else None
     kern_s = kern_ms / 1e3
+    derived32 = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12   # FP32 FMA lanes x 2 flops x clock
+    gather_bytes = trials * GATHER_BYTES_PER_TRIAL_F32
     if prec == crp.MIXED:
-        peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12   # FP32 FMA lanes x 2 flops x clock
-        achieved = flops / kern_s / 1e12
+        achieved = trials * flops_per_trial_mixed() / kern_s / 1e12
+        peak = probe["fp32_tflops"]
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
-                "peak_source": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz "
-                               "(median SM clock sampled during the timed region)",
-                "flops_per_trial": flops_per_trial_mixed()}
+                "peak_source": "measured: crp_measure_peaks binary32 FMA probe "
+                               f"(derived {derived32:.1f} TFLOP/s = {n_sm} SMs x 128 lanes x 2 x "
+                               f"{sm_mhz:.0f} MHz)",
+                "flops_per_trial": flops_per_trial_mixed(),
+                "field_gather": {"bytes_per_trial": GATHER_BYTES_PER_TRIAL_F32,
+                                 "achieved_GBs": gather_bytes / kern_s / 1e9,
+                                 "l2_read_peak_GBs": probe["l2_read_gbs"],
+                                 "frac_of_l2_peak": gather_bytes / kern_s / 1e9 / probe["l2_read_gbs"]}}
     else:
-        roof = None
+        achieved = trials * flops_per_trial_mixed() / kern_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": probe["fp64_tflops"],
+                "unit": "TFLOP/s", "frac": achieved / probe["fp64_tflops"], "traffic": None,
+                "peak_source": "measured: crp_measure_peaks binary64 FMA probe",
+                "flops_per_trial": flops_per_trial_mixed()}
+    if fp64 is not None:
+        f_ach = (fp64["accepted_steps"] + fp64["rejected_trials"]) * flops_per_trial_mixed() \
+            / (fp64["kernel_ms"] / 1e3) / 1e12
+        fp64["roofline"] = {"bound": "alu", "achieved": f_ach, "peak": probe["fp64_tflops"],
+                            "unit": "TFLOP/s", "frac": f_ach / probe["fp64_tflops"],
+                            "peak_source": "measured: crp_measure_peaks binary64 FMA probe"}
 
     # ---- CPU baseline: the oracle on a bounded sample ----------------------
     cpu = None
@@ -298,6 +328,7 @@ def run_ours(args):
             "kernel_ms_per_step": kern_ms / args.steps,
             "gpu_launches": int(args.steps * 2 + launches * 2),
             "e2e": e2e, "fp64": fp64, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+            "measured_peaks": probe,
         }
         print(json.dumps(line))
 
@@ -376,9 +407,201 @@ def run_reference(args):
     }))
 
 
+def coarse_ring_map(hist, nside, n_bands=16, n_sectors=8):
+    """Sum a HEALPix RING map into n_bands latitude bands (by ring index) x
+    n_sectors longitude sectors (by position within the ring)."""
+    npix = 12 * nside * nside
+    p = np.arange(npix, dtype=np.int64)
+    ncap = 2 * nside * (nside - 1)
+    ring = np.empty(npix, np.int64)
+    first = np.empty(npix, np.int64)
+    length = np.empty(npix, np.int64)
+    north = p < ncap
+    i = np.floor((1 + np.sqrt(1 + 2 * p[north])) / 2).astype(np.int64)
+    i -= (2 * i * (i - 1) > p[north])
+    i += (2 * (i + 1) * i <= p[north])
+    ring[north], first[north], length[north] = i, 2 * i * (i - 1), 4 * i
+    eq = (p >= ncap) & (p < npix - ncap)
+    ie = (p[eq] - ncap) // (4 * nside) + nside
+    ring[eq], first[eq], length[eq] = ie, ncap + 4 * nside * (ie - nside), 4 * nside
+    south = p >= npix - ncap
+    ps = npix - 1 - p[south]
+    j = np.floor((1 + np.sqrt(1 + 2 * ps)) / 2).astype(np.int64)
+    j -= (2 * j * (j - 1) > ps)
+    j += (2 * (j + 1) * j <= ps)
+    ring[south], length[south] = 4 * nside - j, 4 * j
+    first[south] = npix - 2 * j * (j + 1)
+    band = (ring - 1) * n_bands // (4 * nside - 1)
+    sector = (p - first) * n_sectors // length
+    return np.bincount(band * n_sectors + sector, weights=hist, minlength=n_bands * n_sectors)
+
+
+def two_sample_chi2(a, b):
+    """Chi-square test that two histograms come from one distribution (their
+    totals may differ); cells empty in both are skipped."""
+    from scipy.stats import chi2 as chi2_dist
+    keep = (a + b) > 0
+    a, b = a[keep], b[keep]
+    na, nb = a.sum(), b.sum()
+    stat = float(np.sum((np.sqrt(nb / na) * a - np.sqrt(na / nb) * b) ** 2 / (a + b)))
+    dof = int(len(a) - 1)
+    return stat, dof, float(chi2_dist.sf(stat, dof))
+
+
+def run_galactic(args):
+    """Galactic workload: back-track antiprotons from Earth through the
+    synthetic galactic field (disk + halo + 256^3 random component), train the
+    BF16 MLP surrogate on the border directions, and build the nside-64,
+    100-bin lens by back-tracking and by the surrogate."""
+    import torch
+    from paper_1307_2643_gb300 import crp
+    from paper_1307_2643_gb300.build import build
+
+    torch.cuda.set_device(0)
+    build()
+    crp.use_torch_allocator(0)
+    w = workloads.GALACTIC_LENS
+    n_all = args.n_train + args.n_test
+    dx, lmin, org = workloads.galactic_grid_geometry(w["grid_n"][0], w["box"])
+    m = 2_000_000  # border candidates sent through both lenses
+    ctx = crp.crp_context_create(0, w["seed"], max(n_all, m) + 1024)
+    grid = crp.crp_grid_create(ctx, crp.grid_desc(w["grid_n"], dx, origin=org, dtype=crp.F32,
+                                                  source=crp.GRID_TURBULENT, lmin=lmin,
+                                                  lmax=w["lmax"], brms=w["brms"], seed=w["seed"]))
+    mods = crp.modules(precision=crp.MIXED, flags=crp.GALACTIC | crp.BORDER, tol=w["tol"],
+                       h_min=w["h_min"], h_max=w["h_max"], field_unit_T=crp.MICROGAUSS_T,
+                       length_unit_m=crp.KPC_M, border_radius=w["border_r"], galactic=w["disk"])
+    dirs, R = workloads.backtrack_directions(n_all, w["r_lo"], w["r_hi"], w["seed"] + 1)
+    inj = crp.host_injection(dict(x=np.full(n_all, w["earth"][0]), y=np.full(n_all, w["earth"][1]),
+                                  z=np.full(n_all, w["earth"][2]), ux=dirs[:, 0], uy=dirs[:, 1],
+                                  uz=dirs[:, 2], E=R, A=np.ones(n_all), Z=np.ones(n_all),
+                                  q=-np.ones(n_all)))
+    crp.crp_candidates_inject(ctx, crp.candidate_arrays(inj), n_all)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, st = crp.crp_propagate(ctx, grid, mods)
+    torch.cuda.synchronize()
+    t_bt = time.perf_counter() - t0
+    rec = crp.crp_collect(ctx, crp.COLLECT_ALL)
+    rec = rec[np.argsort(rec["id"], kind="stable")]
+    ok = rec["status"] == crp.AT_BORDER
+    # network inputs (direction at Earth, log10 R - 19), the surrogate's input convention
+    x_all = np.concatenate([dirs, (np.log10(R) - 19.0)[:, None]], axis=1).astype(np.float32)
+    t_all = rec["u"].astype(np.float32)
+    tr = np.nonzero(ok[: args.n_train])[0]
+    te = args.n_train + np.nonzero(ok[args.n_train:])[0]
+    # ---- training ---------------------------------------------------------
+    mlp = crp.crp_mlp_create(ctx, 4, 256, 4, w["seed"])
+    B = args.batch
+    g = workloads.rng(w["seed"] + 5)
+    shuf = tr[g.permutation(len(tr))]
+    n_batches = len(tr) // B
+    xd = torch.from_numpy(x_all[shuf[: n_batches * B]]).cuda()
+    td = torch.from_numpy(t_all[shuf[: n_batches * B]]).cuda()
+    steps, total = 0, args.epochs * n_batches
+    losses = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for ep in range(args.epochs):
+        for i, b in enumerate(g.permutation(n_batches)):
+            # linear warm-up over 200 steps, cosine decay to zero
+            lr = args.lr * 0.5 * (1 + np.cos(np.pi * steps / total)) * min(1.0, (steps + 1) / 200)
+            b0 = int(b) * B
+            loss = crp.crp_mlp_train_step(mlp, xd[b0:b0 + B], td[b0:b0 + B], B, lr,
+                                          want_loss=(i == n_batches - 1))
+            steps += 1
+        losses.append(round(loss, 5))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    # ---- held-out accuracy and inference throughput -----------------------
+    n_te = (len(te) // 128) * 128
+    xt = torch.from_numpy(x_all[te[:n_te]]).cuda()
+    yt = torch.zeros((n_te, 3), dtype=torch.float32, device="cuda")
+    crp.crp_mlp_forward(mlp, xt, yt, n_te)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    crp.crp_mlp_forward(mlp, xt, yt, n_te)
+    torch.cuda.synchronize()
+    t_inf = time.perf_counter() - t0
+    yh = yt.cpu().numpy().astype(np.float64)
+    tt = t_all[te[:n_te]].astype(np.float64)
+    cosang = np.sum(yh * tt, axis=1) / (np.linalg.norm(yh, axis=1) * np.linalg.norm(tt, axis=1))
+    ang = np.degrees(np.arccos(np.clip(cosang, -1.0, 1.0)))
+    Rt = R[te[:n_te]]
+    ident = np.degrees(np.arccos(np.clip(np.sum(dirs[te[:n_te]] * tt, axis=1)
+                                         / np.linalg.norm(tt, axis=1), -1.0, 1.0)))
+    q_edges = 10.0 ** np.arange(18.0, 20.01, 0.25)
+    by_q = {f"{np.log10(lo):.2f}-{np.log10(hi):.2f}":
+            [round(float(np.median(ang[(Rt >= lo) & (Rt < hi)])), 3),
+             round(float(np.median(ident[(Rt >= lo) & (Rt < hi)])), 3)]
+            for lo, hi in zip(q_edges[:-1], q_edges[1:])}
+    # ---- lens builds -------------------------------------------------------
+    ldirs, lE, lbins = workloads.lens_samples(w["n_bins"], args.lens_per_bin, w["r_lo"], w["r_hi"],
+                                              w["seed"] + 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lens_bt, lst = crp.crp_lens_build(ctx, grid, mods, w["nside"], w["n_bins"], w["r_lo"],
+                                      w["r_hi"], w["earth"], ldirs, lE, lbins)
+    torch.cuda.synchronize()
+    t_lens_bt = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    lens_sg = crp.crp_lens_build_surrogate(ctx, mlp, w["nside"], w["n_bins"], w["r_lo"],
+                                           w["r_hi"], ldirs, lE, lbins)
+    torch.cuda.synchronize()
+    t_lens_sg = time.perf_counter() - t0
+    # arrival maps of an isotropic border population through both lenses
+    bd, bR = workloads.backtrack_directions(m, w["r_lo"], w["r_hi"], w["seed"] + 4)
+    inj2 = crp.host_injection(dict(x=np.zeros(m), y=np.zeros(m), z=np.zeros(m), ux=bd[:, 0],
+                                   uy=bd[:, 1], uz=bd[:, 2], E=bR, A=np.ones(m), Z=np.ones(m)))
+    maps = {}
+    for name, lens in (("backtracked", lens_bt), ("surrogate", lens_sg)):
+        crp.crp_candidates_clear(ctx)
+        crp.crp_candidates_inject(ctx, crp.candidate_arrays(inj2), m)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        crp.crp_lens_apply(ctx, lens, crp.COLLECT_ALL)
+        torch.cuda.synchronize()
+        maps[name + "_apply_s"] = time.perf_counter() - t0
+        maps[name] = crp.crp_histogram_healpix(ctx, crp.COLLECT_ALL, w["nside"], 1).astype(np.float64)
+    a, b = maps["backtracked"], maps["surrogate"]
+    ca, cb = coarse_ring_map(a, w["nside"]), coarse_ring_map(b, w["nside"])
+    chi2, dof, pval = two_sample_chi2(ca, cb)
+    corr = float(np.corrcoef(ca, cb)[0, 1])
+    for lens in (lens_bt, lens_sg):
+        crp.crp_lens_destroy(lens)
+    crp.crp_mlp_destroy(mlp)
+    crp.crp_grid_destroy(grid)
+    crp.crp_context_destroy(ctx)
+    print(json.dumps({
+        "workload": w["name"], "metric": "galactic back-tracking and lens surrogate",
+        "backtrack": {"candidates": n_all, "accepted_steps": st.accepted_steps,
+                      "rejected_trials": st.rejected_trials, "seconds": t_bt,
+                      "steps_per_s": st.accepted_steps / t_bt,
+                      "at_border_fraction": float(ok.mean()), "precision": "mixed"},
+        "mlp": {"train_samples": int(len(tr)), "epochs": args.epochs, "batch": B, "steps": steps,
+                "train_seconds": t_train, "train_samples_per_s": steps * B / t_train,
+                "loss_per_epoch": losses, "test_samples": n_te,
+                "median_angle_deg": float(np.median(ang)),
+                "p90_angle_deg": float(np.percentile(ang, 90)),
+                "median_angle_deg_no_lens": float(np.median(ident)),
+                "median_angle_deg_by_log10R_net_vs_no_lens": by_q,
+                "inference_samples_per_s": n_te / t_inf},
+        "lens": {"nside": w["nside"], "n_bins": w["n_bins"], "samples": int(len(lE)),
+                 "build_backtrack_s": t_lens_bt, "build_surrogate_s": t_lens_sg,
+                 "backtrack_steps": lst.accepted_steps, "apply_s": {k: maps[k + "_apply_s"]
+                 for k in ("backtracked", "surrogate")},
+                 "map_cells": int(len(ca)), "map_chi2": chi2, "map_dof": dof, "map_p": pval,
+                 "map_correlation": corr,
+                 "observed_fraction": {"backtracked": float(a.sum() / m),
+                                       "surrogate": float(b.sum() / m)}},
+    }))
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "galactic":
+        run_galactic(a)
     else:
         run_ours(a)

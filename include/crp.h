@@ -387,6 +387,27 @@ crp_status crp_histogram_healpix(crp_context* ctx, int32_t what, int32_t nside, 
 crp_status crp_histogram_energy(crp_context* ctx, int32_t what, double e_lo, double e_hi,
                                 int32_t nbins, uint64_t* out, void* stream);
 
+/* Checkpoint / restore of a propagation.  Sect. 3 puts the whole state of a
+ * particle in its candidate (the stochastic-interaction states included);
+ * with per-candidate RNG counters the pool and the seed are therefore the
+ * whole state of a propagation, and a restored context continues it
+ * bit-identically (for instance after crp_propagate returned CRP_E_TIMEOUT).
+ *
+ * crp_checkpoint writes a self-describing image of the context into a host
+ * buffer: a header (magic, format version, seed, candidate count, element
+ * sizes, FNV-1a checksum of the payload) followed by each pool array's first
+ * `size` entries.  host_buf = NULL (or capacity 0) is a size query: *n_out
+ * receives the bytes needed.  A buffer smaller than that is CRP_E_INVALID.
+ * Synchronises `stream`; the caller owns the buffer.
+ *
+ * crp_restore replaces the context's candidates and seed by the image's.
+ * Rejected with CRP_E_INVALID (context unchanged): another format version,
+ * a truncated or corrupted image (checksum), or more candidates than the
+ * context's capacity.  Synchronises `stream`. */
+crp_status crp_checkpoint(crp_context* ctx, void* host_buf, size_t capacity, size_t* n_out,
+                          void* stream);
+crp_status crp_restore(crp_context* ctx, const void* host_buf, size_t n, void* stream);
+
 /* The same histogram without allocating anything.  This entry point has no
  * counterpart in the paper: it is for callers that cannot allocate device
  * memory while they run -- their device memory is handed out entirely by
@@ -404,6 +425,22 @@ crp_status crp_histogram_energy(crp_context* ctx, int32_t what, double e_lo, dou
  *     the array keeps the last call's counts, and calls that overlap on the
  *     GPU (other streams, other threads) race with each other.
  *   - Results equal crp_histogram_energy's.  Synchronises `stream`. */
+/* Measured roofline denominators of a device (no counterpart in the paper):
+ * binary32 and binary64 fused multiply-add throughput (2 flops per FMA;
+ * each thread runs 8 independent chains over a grid of 8 blocks of 256 per
+ * SM) and the read bandwidth of an L2-resident buffer (a quarter of the L2,
+ * read 64 times with 16-byte L2-only loads); best of three timed launches
+ * after a warm-up.  Allocates and frees one buffer of a quarter of the L2;
+ * runs on a private stream and synchronises it. */
+typedef struct crp_peaks {
+  double fp32_tflops;
+  double fp64_tflops;
+  double l2_read_gbs;
+  int32_t sm_count;
+  int32_t l2_bytes;
+} crp_peaks;
+crp_status crp_measure_peaks(int32_t device, crp_peaks* out);
+
 #define CRP_HIST_NOALLOC_MAX_BINS 4096
 crp_status crp_histogram_energy_noalloc(crp_context* ctx, int32_t what, double e_lo, double e_hi,
                                         int32_t nbins, uint64_t* out, void* stream);

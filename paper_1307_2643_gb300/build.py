@@ -26,6 +26,7 @@ UNITS = {
     "hist_noalloc.cu": [],
     "lens.cu": [],
     "mlp.cu": [],
+    "peaks.cu": [],
 }
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -83,6 +83,11 @@ class LensDesc(C.Structure):
                 ("E", C.c_void_p), ("bin", C.c_void_p), ("n_samples", C.c_int64)]
 
 
+class Peaks(C.Structure):
+    _fields_ = [("fp32_tflops", C.c_double), ("fp64_tflops", C.c_double),
+                ("l2_read_gbs", C.c_double), ("sm_count", C.c_int32), ("l2_bytes", C.c_int32)]
+
+
 class Stats(C.Structure):
     _fields_ = [("accepted_steps", C.c_uint64), ("rejected_trials", C.c_uint64),
                 ("rhs_evals", C.c_uint64), ("n_pion", C.c_uint64), ("n_pd", C.c_uint64),
@@ -121,6 +126,7 @@ SYMBOLS = (
     "crp_histogram_healpix",
     "crp_mlp_create", "crp_mlp_destroy", "crp_mlp_num_params", "crp_mlp_set_params",
     "crp_mlp_get_params", "crp_mlp_forward", "crp_mlp_train_step", "crp_lens_build_surrogate",
+    "crp_checkpoint", "crp_restore", "crp_measure_peaks",
 )
 
 _lock = threading.Lock()
@@ -172,6 +178,9 @@ def lib():
             L.crp_mlp_forward.argtypes = [p, p, p, C.c_int64, p]
             L.crp_mlp_train_step.argtypes = [p, p, p, C.c_int64, C.c_float, p, p]
             L.crp_lens_build_surrogate.argtypes = [p, p, C.POINTER(LensDesc), C.POINTER(p)]
+            L.crp_checkpoint.argtypes = [p, p, sz, C.POINTER(sz), p]
+            L.crp_restore.argtypes = [p, p, sz, p]
+            L.crp_measure_peaks.argtypes = [i32, C.POINTER(Peaks)]
             for name in SYMBOLS:
                 if name not in ("crp_last_error", "crp_version"):
                     getattr(L, name).restype = st
@@ -423,6 +432,28 @@ def crp_mlp_train_step(mlp, x_dev, t_dev, n, lr, stream=None, want_loss=True):
     _check(lib().crp_mlp_train_step(mlp, _addr(x_dev), _addr(t_dev), n, lr,
                                     C.byref(loss) if want_loss else None, stream))
     return loss.value
+
+
+def crp_checkpoint(ctx, stream=None):
+    """The context's state as a bytes-like numpy uint8 array."""
+    n = C.c_size_t()
+    _check(lib().crp_checkpoint(ctx, None, 0, C.byref(n), stream))
+    buf = np.zeros(n.value, np.uint8)
+    _check(lib().crp_checkpoint(ctx, buf.ctypes.data, n.value, C.byref(n), stream))
+    return buf
+
+
+def crp_restore(ctx, image, stream=None):
+    buf = np.ascontiguousarray(np.frombuffer(image, np.uint8) if isinstance(image, (bytes, bytearray))
+                               else image, dtype=np.uint8)
+    _check(lib().crp_restore(ctx, buf.ctypes.data, len(buf), stream))
+
+
+def crp_measure_peaks(device=0):
+    """dict(fp32_tflops, fp64_tflops, l2_read_gbs, sm_count, l2_bytes) measured on `device`."""
+    pk = Peaks()
+    _check(lib().crp_measure_peaks(device, C.byref(pk)))
+    return {k: getattr(pk, k) for k, _ in Peaks._fields_}
 
 
 HIST_NOALLOC_MAX_BINS = 4096

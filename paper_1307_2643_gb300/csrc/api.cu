@@ -90,6 +90,10 @@ struct crp_context {
   uint32_t* bins;         // counting-sort histogram (kSortBins + 1)
   int sm_count;
   cudaEvent_t ev0, ev1;
+  // the pool's arrays in layout order (checkpoint / restore walk this list)
+  void* arr_ptr[64];
+  uint32_t arr_elem[64];
+  int n_arr;
 };
 
 struct crp_grid {
@@ -112,12 +116,20 @@ constexpr size_t kAlign = 256;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
-// Lay out the SoA arrays of `cap` candidates inside one allocation.
-size_t layout_pool(char* base, size_t cap, DevState* st) {
+// Lay out the SoA arrays of `cap` candidates inside one allocation; with a
+// context, also list the arrays (pointer, element size) in layout order.
+size_t layout_pool(char* base, size_t cap, DevState* st, crp_context* list = nullptr) {
   size_t off = 0;
+  if (list) list->n_arr = 0;
   auto take = [&](auto** ptr, size_t elem) {
     using T = typename std::remove_pointer<typename std::remove_pointer<decltype(ptr)>::type>::type;
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "pool arrays hold 4- or 8-byte elements");
     if (base) *ptr = reinterpret_cast<T*>(base + off);
+    if (base && list) {
+      list->arr_ptr[list->n_arr] = base + off;
+      list->arr_elem[list->n_arr] = (uint32_t)elem;
+      ++list->n_arr;
+    }
     off += align_up(elem * cap);
   };
   DevState s;
@@ -158,7 +170,7 @@ crp_status ensure_pool(crp_context* c) {
     set_error("candidate pool: cannot allocate %zu bytes for capacity %zu", bytes, c->capacity);
     return CRP_E_OOM;
   }
-  layout_pool(static_cast<char*>(c->pool), c->capacity, &c->st);
+  layout_pool(static_cast<char*>(c->pool), c->capacity, &c->st, c);
   c->dc = static_cast<DevCounters*>(dev_alloc(sizeof(DevCounters)));
   c->queue[0] = static_cast<uint32_t*>(dev_alloc(c->capacity * sizeof(uint32_t)));
   c->queue[1] = static_cast<uint32_t*>(dev_alloc(c->capacity * sizeof(uint32_t)));
@@ -1133,6 +1145,140 @@ crp_status crp_histogram_energy(crp_context* c, int32_t what, double e_lo, doubl
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   dev_free(bins);
   return e == cudaSuccess ? CRP_OK : fail_cuda(e, "crp_histogram_energy");
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// checkpoint / restore: the pool is the whole state of a propagation (every
+// candidate carries its own RNG counters and free paths), so its first `size`
+// entries of every array, with the seed, resume bit-identically.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct CkptHeader {
+  char magic[8];
+  uint32_t version;
+  uint32_t n_arr;
+  uint64_t seed;
+  uint64_t size;
+  uint64_t payload;
+  uint64_t checksum;
+  uint32_t elem[64];
+};
+constexpr char kCkptMagic[8] = {'C', 'R', 'P', 'C', 'K', 'P', 'T', '1'};
+constexpr uint32_t kCkptVersion = 1;
+
+// FNV-1a over 32-bit words (every payload is a whole number of words).
+uint64_t ckpt_hash(const unsigned char* p, size_t bytes) {
+  uint64_t h = 0xcbf29ce484222325ull;
+  for (size_t k = 0; k + 4 <= bytes; k += 4) {
+    uint32_t w;
+    memcpy(&w, p + k, 4);
+    h = (h ^ w) * 0x100000001b3ull;
+  }
+  return h;
+}
+
+size_t ckpt_payload(const crp_context* c, uint64_t size) {
+  size_t b = 0;
+  for (int a = 0; a < c->n_arr; ++a) b += (size_t)c->arr_elem[a] * size;
+  return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+crp_status crp_checkpoint(crp_context* c, void* host_buf, size_t capacity, size_t* n_out,
+                          void* stream) {
+  if (!c || !n_out || (capacity && !host_buf)) {
+    set_error("crp_checkpoint: bad argument");
+    return CRP_E_INVALID;
+  }
+  DeviceGuard dg(c->device);
+  crp_status st = ensure_pool(c);
+  if (st != CRP_OK) return st;
+  const size_t need = sizeof(CkptHeader) + ckpt_payload(c, c->size);
+  *n_out = need;
+  if (!host_buf) return CRP_OK;  // size query
+  if (capacity < need) {
+    set_error("crp_checkpoint: buffer holds %zu bytes, %zu needed", capacity, need);
+    return CRP_E_INVALID;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned char* out = static_cast<unsigned char*>(host_buf);
+  unsigned char* p = out + sizeof(CkptHeader);
+  cudaError_t e = cudaSuccess;
+  for (int a = 0; a < c->n_arr && e == cudaSuccess; ++a) {
+    const size_t b = (size_t)c->arr_elem[a] * c->size;
+    if (b) e = cudaMemcpyAsync(p, c->arr_ptr[a], b, cudaMemcpyDeviceToHost, s);
+    p += b;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail_cuda(e, "crp_checkpoint");
+  CkptHeader h;
+  memset(&h, 0, sizeof(h));
+  memcpy(h.magic, kCkptMagic, 8);
+  h.version = kCkptVersion;
+  h.n_arr = (uint32_t)c->n_arr;
+  h.seed = c->seed;
+  h.size = c->size;
+  h.payload = need - sizeof(CkptHeader);
+  for (int a = 0; a < c->n_arr; ++a) h.elem[a] = c->arr_elem[a];
+  h.checksum = ckpt_hash(out + sizeof(CkptHeader), h.payload);
+  memcpy(out, &h, sizeof(h));
+  return CRP_OK;
+}
+
+crp_status crp_restore(crp_context* c, const void* host_buf, size_t n, void* stream) {
+  if (!c || !host_buf || n < sizeof(CkptHeader)) {
+    set_error("crp_restore: bad argument");
+    return CRP_E_INVALID;
+  }
+  DeviceGuard dg(c->device);
+  crp_status st = ensure_pool(c);
+  if (st != CRP_OK) return st;
+  CkptHeader h;
+  memcpy(&h, host_buf, sizeof(h));
+  const unsigned char* p = static_cast<const unsigned char*>(host_buf) + sizeof(CkptHeader);
+  if (memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != kCkptVersion ||
+      h.n_arr != (uint32_t)c->n_arr) {
+    set_error("crp_restore: not a checkpoint of this library version");
+    return CRP_E_INVALID;
+  }
+  for (int a = 0; a < c->n_arr; ++a) {
+    if (h.elem[a] != c->arr_elem[a]) {
+      set_error("crp_restore: array %d has element size %u, expected %u", a, h.elem[a],
+                c->arr_elem[a]);
+      return CRP_E_INVALID;
+    }
+  }
+  if (h.size > c->capacity) {
+    set_error("crp_restore: checkpoint holds %llu candidates, capacity is %zu",
+              (unsigned long long)h.size, c->capacity);
+    return CRP_E_INVALID;
+  }
+  if (h.payload != ckpt_payload(c, h.size) || n < sizeof(CkptHeader) + h.payload) {
+    set_error("crp_restore: truncated checkpoint");
+    return CRP_E_INVALID;
+  }
+  if (ckpt_hash(p, h.payload) != h.checksum) {
+    set_error("crp_restore: checksum mismatch");
+    return CRP_E_INVALID;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSuccess;
+  for (int a = 0; a < c->n_arr && e == cudaSuccess; ++a) {
+    const size_t b = (size_t)c->arr_elem[a] * h.size;
+    if (b) e = cudaMemcpyAsync(c->arr_ptr[a], p, b, cudaMemcpyHostToDevice, s);
+    p += b;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail_cuda(e, "crp_restore");
+  c->size = h.size;
+  c->seed = h.seed;
+  return CRP_OK;
 }
 
 }  // extern "C"

@@ -358,3 +358,62 @@ def test_mixed_interactions_statistics(field_f32_small, tables, interaction_ref)
     e = rel_err(prim_g["E"][same], prim_r["E"][same], floor=0.0)
     assert np.median(e) < 1e-5
     assert np.mean(prim_g["n_pion"][same] == prim_r["n_pion"][same]) > 0.95
+
+
+@pytest.mark.parametrize("precision", [crp.FP64, crp.MIXED])
+def test_checkpoint_restore_resumes_bit_identically(field_f32_small, tables, precision):
+    """Interrupt by a step budget and checkpoint; finish once in the same
+    context and once in a new context (other seed and capacity: the image
+    carries the seed) restored from the image.  Both give the same records;
+    on the binary64 path they also equal an uninterrupted run's (the mixed
+    path re-derives its binary32 cell coordinates when a candidate is
+    reloaded, so where it was interrupted is part of its history)."""
+    n, dx, B = field_f32_small
+    inj = crp.host_injection(_interaction_inputs(n_mixed=300, n_hot=60, seed=19))
+    m = len(inj["E"])
+    full, _, _ = run_gpu(B, n, dx, inj, precision=precision, dtype=crp.F32, tables=tables,
+                         flags=INTERACTION_FLAGS, observer_radius=1.0, **_interaction_kw())
+
+    def open_ctx(seed, cap):
+        ctx = crp.crp_context_create(0, seed, cap)
+        g = crp.crp_grid_create(ctx, crp.grid_desc(n, dx, dtype=crp.F32, data=B))
+        th = crp.crp_tables_from_host(ctx, crp.tables_desc(n=tables.n), tables.beta_pair,
+                                      tables.rate_pion, tables.rate_gdr)
+        M = crp.modules(precision=precision, tables=th, flags=INTERACTION_FLAGS,
+                        observer_radius=1.0, **_interaction_kw())
+        return ctx, g, M
+
+    ctx, g, M = open_ctx(1234, 64 * m)
+    try:
+        crp.crp_candidates_inject(ctx, crp.candidate_arrays(inj), m)
+        M.step_budget = 30000
+        status, st = crp.crp_propagate(ctx, g, M, raise_on_error=False)
+        assert status == crp.E_TIMEOUT and st.n_active > 0
+        image = crp.crp_checkpoint(ctx)
+        M.step_budget = 0
+        crp.crp_propagate(ctx, g, M)
+        same_ctx = np.sort(crp.crp_collect(ctx, crp.COLLECT_ALL), order="id")
+    finally:
+        crp.crp_context_destroy(ctx)
+    ctx, g, M = open_ctx(999, 80 * m)
+    try:
+        bad = image.copy()
+        bad[len(bad) // 2] ^= 0x40
+        for broken in (bad, image[:-4]):
+            with pytest.raises(crp.CrpError) as ei:
+                crp.crp_restore(ctx, broken)
+            assert ei.value.status == crp.E_INVALID
+        crp.crp_restore(ctx, image)
+        crp.crp_propagate(ctx, g, M)
+        restored = np.sort(crp.crp_collect(ctx, crp.COLLECT_ALL), order="id")
+        small = crp.crp_context_create(0, 1, 4)  # capacity below the image's candidates
+        try:
+            with pytest.raises(crp.CrpError):
+                crp.crp_restore(small, image)
+        finally:
+            crp.crp_context_destroy(small)
+    finally:
+        crp.crp_context_destroy(ctx)
+    assert restored.tobytes() == same_ctx.tobytes()
+    if precision == crp.FP64:
+        assert restored.tobytes() == full.tobytes()
