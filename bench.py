@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--graph", action="store_true",
+                    help="run each propagation's round loop as one captured CUDA graph")
     ap.add_argument("--workload", choices=("mixed", "galactic"), default="mixed",
                     help="mixed: the propagation benchmark; galactic: back-tracking, MLP "
                          "surrogate training / inference and lens builds")
@@ -138,12 +140,13 @@ def workload_inputs(n, rank):
     return w, inj
 
 
-def modules_for(crp, precision, tables):
+def modules_for(crp, precision, tables, use_graph=0):
     w = workloads.MIXED_INTERACTIONS
     return crp.modules(precision=precision,
                        flags=crp.PAIR | crp.ADIABATIC | crp.PION | crp.EMIN | crp.OBSERVER,
                        tol=w["tol"], h_min=w["h_min"], h_max=w["h_max"], beta_ad=H0_OVER_C,
-                       e_min=w["e_min"], tables=tables, observer_radius=w["observer_r"])
+                       e_min=w["e_min"], tables=tables, observer_radius=w["observer_r"],
+                       use_graph=use_graph)
 
 
 def flops_per_trial_mixed():
@@ -181,7 +184,7 @@ def run_ours(args):
     grid = crp.crp_grid_create(ctx, gd)
     tables = crp.crp_tables_build(ctx, crp.tables_desc(n=1000))
     prec = crp.MIXED if args.precision == "mixed" else crp.FP64
-    mods = modules_for(crp, prec, tables)
+    mods = modules_for(crp, prec, tables, use_graph=1 if args.graph else 0)
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
     dev = {k: torch.from_numpy(v).cuda() for k, v in inj.items()}
@@ -321,12 +324,15 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec == crp.MIXED else "f64",
             "data": "synthetic (seeded injection, GPU-generated turbulent field)",
             "config": {"workload": w["name"], "candidates_per_gpu": n, "grid": "256^3 f32",
-                       "precision": args.precision, "l2": "inputs larger than L2 (268 MB grid, "
+                       "precision": args.precision,
+                       "round_loop": "cuda-graph" if args.graph else "host", "l2": "inputs larger than L2 (268 MB grid, "
                        "245 MB candidate pool)", "parallelism": f"candidate shards x{world}"},
             "accepted_steps": acc, "rejected_trials": rej,
             "rejected_trials_per_s": rej / elapsed,
             "kernel_ms_per_step": kern_ms / args.steps,
-            "gpu_launches": int(args.steps * 2 + launches * 2),
+            # per step: inject (1), queue build (2), queue sort (3); per round:
+            # host loop = reset + propagate (+ sort of requeued work), graph = 5
+            "gpu_launches": int(args.steps * 6 + launches * (5 if args.graph else 2)),
             "e2e": e2e, "fp64": fp64, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
             "measured_peaks": probe,
         }

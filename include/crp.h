@@ -228,10 +228,19 @@ typedef struct {
                                 or 256 (MIXED); 0 = that maximum */
   int32_t blocks_per_sm;     /* resident blocks per SM (0 = occupancy maximum) */
   uint32_t slice;            /* accepted steps a lane runs on one candidate before
-                                requeueing it for the next round (0 = 512); bounds
-                                the load imbalance between lanes of a warp */
-  int32_t spatial_sort;      /* 0: sort each round's work queue by grid brick so
-                                neighbouring lanes gather nearby cells; -1: off */
+                                requeueing it for the next round (0 = 2^20: in
+                                practice to the end) */
+  int32_t queue_order;       /* order of each round's work queue (counting sort
+                                on 15-bit keys): 0 = lowest rigidity E/Z first
+                                (the longest histories start first), 1 = by grid
+                                brick (neighbouring lanes gather nearby cells),
+                                -1 = unsorted.  Results do not depend on it. */
+  int32_t use_graph;         /* 1: run the round loop as one captured CUDA graph (a
+                                while node; the loop condition is set on the device,
+                                so rounds need no host round trip; the graph is kept
+                                and replayed while the launch parameters stay the
+                                same); 0: host-driven rounds.  Same results. */
+  int32_t reserved0;
 } crp_modules;
 
 typedef struct {
@@ -386,6 +395,32 @@ crp_status crp_histogram_healpix(crp_context* ctx, int32_t what, int32_t nside, 
  * [e_lo, e_hi) (under/overflow dropped).  out: host uint64 array of nbins. */
 crp_status crp_histogram_energy(crp_context* ctx, int32_t what, double e_lo, double e_hi,
                                 int32_t nbins, uint64_t* out, void* stream);
+
+/* Launch-configuration autotuner (no counterpart in the paper; the
+ * scheduler's tunables are this library's own).  Times crp_propagate on the
+ * context's injected candidates under a fixed set of configurations (block
+ * size x resident blocks per SM x slice x spatial sort), each started from
+ * the same snapshot of the pool and stopped after `steps_per_trial`
+ * accepted steps (0 = 2e8; UINT64_MAX = run each to completion, which also
+ * scores the end of the run where few candidates are left), scored by
+ * accepted steps per second of wall time, after one unscored warm-up run.  The pool is restored afterwards:
+ * the context is left exactly as it was.  The fastest configuration is
+ * written into m (block_size, blocks_per_sm, slice, queue_order) and *out.
+ * Results of a propagation do not depend on these settings (every slice
+ * tried is a multiple of 32), so tuning changes speed only.  Needs a
+ * device snapshot of the pool (its payload size); CRP_E_INVALID if no
+ * candidates are injected. */
+typedef struct crp_tune_result {
+  int32_t block_size;
+  int32_t blocks_per_sm;
+  uint32_t slice;
+  int32_t queue_order;
+  double steps_per_s;  /* of the chosen configuration */
+  int32_t n_tried;
+  int32_t reserved;
+} crp_tune_result;
+crp_status crp_autotune(crp_context* ctx, const crp_grid* grid, crp_modules* m,
+                        uint64_t steps_per_trial, crp_tune_result* out, void* stream);
 
 /* Checkpoint / restore of a propagation.  Sect. 3 puts the whole state of a
  * particle in its candidate (the stochastic-interaction states included);

@@ -74,7 +74,8 @@ class Modules(C.Structure):
                 ("gal_center", C.c_double * 3),
                 ("max_steps", C.c_uint64), ("step_budget", C.c_uint64),
                 ("deadline_ms", C.c_double), ("block_size", C.c_int32),
-                ("blocks_per_sm", C.c_int32), ("slice", C.c_uint32), ("spatial_sort", C.c_int32)]
+                ("blocks_per_sm", C.c_int32), ("slice", C.c_uint32), ("queue_order", C.c_int32),
+                ("use_graph", C.c_int32), ("reserved0", C.c_int32)]
 
 
 class LensDesc(C.Structure):
@@ -86,6 +87,12 @@ class LensDesc(C.Structure):
 class Peaks(C.Structure):
     _fields_ = [("fp32_tflops", C.c_double), ("fp64_tflops", C.c_double),
                 ("l2_read_gbs", C.c_double), ("sm_count", C.c_int32), ("l2_bytes", C.c_int32)]
+
+
+class TuneResult(C.Structure):
+    _fields_ = [("block_size", C.c_int32), ("blocks_per_sm", C.c_int32), ("slice", C.c_uint32),
+                ("queue_order", C.c_int32), ("steps_per_s", C.c_double),
+                ("n_tried", C.c_int32), ("reserved", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -126,7 +133,7 @@ SYMBOLS = (
     "crp_histogram_healpix",
     "crp_mlp_create", "crp_mlp_destroy", "crp_mlp_num_params", "crp_mlp_set_params",
     "crp_mlp_get_params", "crp_mlp_forward", "crp_mlp_train_step", "crp_lens_build_surrogate",
-    "crp_checkpoint", "crp_restore", "crp_measure_peaks",
+    "crp_checkpoint", "crp_restore", "crp_measure_peaks", "crp_autotune",
 )
 
 _lock = threading.Lock()
@@ -181,6 +188,7 @@ def lib():
             L.crp_checkpoint.argtypes = [p, p, sz, C.POINTER(sz), p]
             L.crp_restore.argtypes = [p, p, sz, p]
             L.crp_measure_peaks.argtypes = [i32, C.POINTER(Peaks)]
+            L.crp_autotune.argtypes = [p, p, C.POINTER(Modules), u64, C.POINTER(TuneResult), p]
             for name in SYMBOLS:
                 if name not in ("crp_last_error", "crp_version"):
                     getattr(L, name).restype = st
@@ -434,6 +442,14 @@ def crp_mlp_train_step(mlp, x_dev, t_dev, n, lr, stream=None, want_loss=True):
     return loss.value
 
 
+def crp_autotune(ctx, grid, modules: Modules, steps_per_trial=0, stream=None):
+    """Tune `modules` in place on the context's candidates; returns the
+    TuneResult as a dict."""
+    r = TuneResult()
+    _check(lib().crp_autotune(ctx, grid, C.byref(modules), steps_per_trial, C.byref(r), stream))
+    return {k: getattr(r, k) for k, _ in TuneResult._fields_}
+
+
 def crp_checkpoint(ctx, stream=None):
     """The context's state as a bytes-like numpy uint8 array."""
     n = C.c_size_t()
@@ -518,7 +534,7 @@ def modules(precision=FP64, flags=0, tol=1e-4, h_min=0.01, h_max=1.0, field_unit
             length_unit_m=MPC_M, beta_ad=0.0, e_min=0.0, tables=None, observer_center=(0, 0, 0),
             observer_radius=0.0, border_center=(0, 0, 0), border_radius=0.0, galactic=None,
             max_steps=10_000_000, step_budget=0, deadline_ms=0.0, block_size=0, blocks_per_sm=0,
-            slice=0, spatial_sort=0):
+            slice=0, queue_order=0, use_graph=0):
     m = Modules()
     m.precision, m.flags, m.tol, m.h_min, m.h_max = precision, flags, tol, h_min, h_max
     m.field_unit_T, m.length_unit_m, m.beta_ad, m.e_min = field_unit_T, length_unit_m, beta_ad, e_min
@@ -535,5 +551,6 @@ def modules(precision=FP64, flags=0, tol=1e-4, h_min=0.01, h_max=1.0, field_unit
                 setattr(m, k, v)
     m.max_steps, m.step_budget, m.deadline_ms = max_steps, step_budget, deadline_ms
     m.block_size, m.blocks_per_sm, m.slice = block_size, blocks_per_sm, slice
-    m.spatial_sort = spatial_sort
+    m.queue_order = queue_order
+    m.use_graph = use_graph
     return m

@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <chrono>
 #include <mutex>
 #include <new>
 #include <type_traits>
@@ -76,6 +77,14 @@ void dev_free(void* p) {
 
 using namespace crp;
 
+// What a captured round-loop graph was built for (compared bytewise).
+struct GraphKey {
+  KParams kp;
+  DevState st;
+  const void* dc;
+  int precision, block, variant, grid, sort_on, pad;
+};
+
 struct crp_context {
   int device;
   uint64_t seed;
@@ -90,6 +99,11 @@ struct crp_context {
   uint32_t* bins;         // counting-sort histogram (kSortBins + 1)
   int sm_count;
   cudaEvent_t ev0, ev1;
+  // graph mode: the round loop captured as one CUDA graph (while node)
+  cudaStream_t cap_stream;
+  cudaGraph_t graph;
+  cudaGraphExec_t gexec;
+  GraphKey gkey;
   // the pool's arrays in layout order (checkpoint / restore walk this list)
   void* arr_ptr[64];
   uint32_t arr_elem[64];
@@ -113,6 +127,10 @@ struct crp_tables {
 namespace {
 
 constexpr size_t kAlign = 256;
+// Default slice: 2^20 accepted steps, i.e. a lane keeps its candidate to the
+// end in practice (measured faster than requeueing every 512 steps: no
+// round tails); a multiple of 32, the mixed path's rebase period.
+constexpr uint32_t kDefaultSlice = 1u << 20;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
@@ -250,8 +268,8 @@ __global__ void k_to_float(const double* in, float* out, int64_t n) {
 // Work queue of the first round: every active candidate of the pool, with
 // its spatial key.  The loop bound is warp-uniform so every lane takes part
 // in each ballot.
-__global__ void k_build_queue(DevState st, uint64_t n, FieldView f, int3 shift, uint32_t* queue,
-                              uint32_t* keys, unsigned long long* count) {
+__global__ void k_build_queue(DevState st, uint64_t n, FieldView f, int3 shift, int order,
+                              uint32_t* queue, uint32_t* keys, unsigned long long* count) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const int lane = threadIdx.x & 31;
   const int sh[3] = {shift.x, shift.y, shift.z};
@@ -267,6 +285,10 @@ __global__ void k_build_queue(DevState st, uint64_t n, FieldView f, int3 shift, 
     if (act) {
       const uint64_t o = base + __popc(m & ((1u << lane) - 1u));
       queue[o] = (uint32_t)i;
+      if (order != 1) {
+        keys[o] = rigidity_key(st.E[i], st.Z[i]);
+        continue;
+      }
       const double r[3] = {st.x[i], st.y[i], st.z[i]};
       int cell[3];
       for (int d = 0; d < 3; ++d) {
@@ -280,8 +302,8 @@ __global__ void k_build_queue(DevState st, uint64_t n, FieldView f, int3 shift, 
   }
 }
 
-// Counting sort of a work queue by spatial key: lanes that run adjacent
-// queue entries then gather from nearby grid cells.
+// Counting sort of a work queue by its 15-bit keys (rigidity: lowest first;
+// or spatial brick: lanes that run adjacent entries gather nearby cells).
 __global__ void k_sort_hist(const uint32_t* keys, uint64_t n, uint32_t* bins) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
        i += (uint64_t)gridDim.x * blockDim.x)
@@ -323,6 +345,59 @@ __global__ void k_sort_scatter(const uint32_t* keys, const uint32_t* in, uint64_
 __global__ void k_round_reset(DevCounters* dc) {
   dc->head = 0;
   dc->q_out = 0;
+}
+
+// ---- graph mode: the round loop with its queue length kept on the device ----
+__device__ __forceinline__ uint64_t queued(const DevCounters* dc, uint64_t cap) {
+  const unsigned long long q = dc->q_out;
+  return q < cap ? q : cap;
+}
+
+__global__ void k_sort_hist_dev(const uint32_t* keys, const DevCounters* dc, uint64_t cap,
+                                uint32_t* bins) {
+  const uint64_t n = queued(dc, cap);
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    atomicAdd(bins + keys[i], 1u);
+}
+
+__global__ void k_sort_scatter_dev(const uint32_t* keys, const uint32_t* in,
+                                   const DevCounters* dc, uint64_t cap, uint32_t* bins,
+                                   uint32_t* out) {
+  const uint64_t n = queued(dc, cap);
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    out[atomicAdd(bins + keys[i], 1u)] = in[i];
+}
+
+__global__ void k_copy_queue_dev(const uint32_t* in, const DevCounters* dc, uint64_t cap,
+                                 uint32_t* out) {
+  const uint64_t n = queued(dc, cap);
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    out[i] = in[i];
+}
+
+// Start of a round: the previous round's output queue becomes this round's
+// input; the loop ends (condition 0) when it is empty, when the step budget
+// or deadline stopped the previous round, or after max_rounds rounds.
+__global__ void k_graph_round(DevCounters* dc, uint64_t cap, cudaGraphConditionalHandle h,
+                              unsigned long long max_rounds) {
+  unsigned long long n = queued(dc, cap);
+  dc->head = 0;
+  dc->q_out = 0;
+  bool go = n > 0 && dc->stop == 0;
+  if (go && dc->rounds >= max_rounds) {
+    dc->error_word |= ERR_ROUND_LIMIT;
+    dc->stop = 1;
+    go = false;
+  }
+  if (go)
+    dc->rounds += 1;
+  else
+    n = 0;
+  dc->n_in = n;
+  if (!go) cudaGraphSetConditional(h, 0);
 }
 
 __global__ void k_count_active(const int32_t* status, uint64_t n, unsigned long long* out) {
@@ -520,6 +595,9 @@ crp_status crp_context_destroy(crp_context* c) {
   if (c->hc) cudaFreeHost(c->hc);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
   return CRP_OK;
 }
@@ -842,6 +920,90 @@ static void fill_field_view(const crp_grid* g, FieldView& f) {
   f.dtype = g->desc.dtype;
 }
 
+// Graph mode: capture the round loop once (a while node whose body sorts
+// the queue, starts the round and runs the propagate kernel; the loop
+// condition is set on the device) and replay it; rebuilt when the launch
+// parameters change.  One graph launch replaces a host round trip per round.
+static cudaError_t graph_rounds(crp_context* c, const KParams& kp, int precision, int block,
+                                int variant, int grid, bool sort_on, cudaStream_t s,
+                                float* ms_out) {
+  GraphKey key;
+  memset(&key, 0, sizeof(key));
+  key.kp = kp;
+  key.st = c->st;
+  key.dc = c->dc;
+  key.precision = precision;
+  key.block = block;
+  key.variant = variant;
+  key.grid = grid;
+  key.sort_on = sort_on ? 1 : 0;
+  cudaError_t e = cudaSuccess;
+  if (!c->gexec || memcmp(&key, &c->gkey, sizeof(key)) != 0) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->gexec = nullptr;
+    c->graph = nullptr;
+    if (!c->cap_stream) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaGraphCreate(&c->graph, 0);
+    cudaGraphConditionalHandle h = 0;
+    if (e == cudaSuccess)
+      e = cudaGraphConditionalHandleCreate(&h, c->graph, 1, cudaGraphCondAssignDefault);
+    // the parameter union has no usable default constructor: zeroed storage
+    alignas(cudaGraphNodeParams) unsigned char np_mem[sizeof(cudaGraphNodeParams)];
+    memset(np_mem, 0, sizeof(np_mem));
+    cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(np_mem);
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, c->graph, nullptr, nullptr, 0, &np);
+    if (e == cudaSuccess) {
+      cudaGraph_t body = np.conditional.phGraph_out[0];
+      cudaStream_t cs = c->cap_stream;
+      e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeRelaxed);
+      if (e == cudaSuccess) {
+        const int gb = c->sm_count * 8;
+        const uint64_t cap = c->capacity;
+        if (sort_on) {
+          cudaMemsetAsync(c->bins, 0, (kSortBins + 1) * sizeof(uint32_t), cs);
+          k_sort_hist_dev<<<gb, 256, 0, cs>>>(c->keys, c->dc, cap, c->bins);
+          k_sort_scan<<<1, 1024, 0, cs>>>(c->bins);
+          k_sort_scatter_dev<<<gb, 256, 0, cs>>>(c->keys, c->queue[1], c->dc, cap, c->bins,
+                                                 c->queue[0]);
+        } else {
+          k_copy_queue_dev<<<gb, 256, 0, cs>>>(c->queue[1], c->dc, cap, c->queue[0]);
+        }
+        k_graph_round<<<1, 1, 0, cs>>>(c->dc, cap, h, 1ull << 20);
+        e = precision == CRP_FP64
+                ? launch_propagate_fp64(kp, c->st, c->dc, grid, block, cs)
+                : launch_propagate_mixed(kp, c->st, c->dc, grid, block, variant, cs);
+        cudaGraph_t done = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &done);
+        if (e == cudaSuccess) e = e2;
+      }
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->gexec, c->graph, 0);
+    if (e != cudaSuccess) {
+      if (c->gexec) cudaGraphExecDestroy(c->gexec);
+      if (c->graph) cudaGraphDestroy(c->graph);
+      c->gexec = nullptr;
+      c->graph = nullptr;
+      return e;
+    }
+    c->gkey = key;
+  }
+  cudaEventRecord(c->ev0, s);
+  e = cudaGraphLaunch(c->gexec, s);
+  cudaEventRecord(c->ev1, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(c->ev1);
+  float ms = 0.f;
+  if (e == cudaSuccess) cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  *ms_out = ms;
+  return e;
+}
+
 crp_status crp_propagate(crp_context* c, const crp_grid* g, const crp_modules* m, void* stream,
                          crp_stats* stats_out) {
   if (!c || !g || !m) {
@@ -870,6 +1032,10 @@ crp_status crp_propagate(crp_context* c, const crp_grid* g, const crp_modules* m
   if (m->block_size < 0 || m->block_size > max_block || (m->block_size % 32) != 0 ||
       m->blocks_per_sm < 0) {
     set_error("crp_propagate: block_size must be a multiple of 32 up to %d", max_block);
+    return CRP_E_INVALID;
+  }
+  if (m->queue_order < -1 || m->queue_order > 1) {
+    set_error("crp_propagate: queue_order must be -1, 0 or 1");
     return CRP_E_INVALID;
   }
   if (stats_out) memset(stats_out, 0, sizeof(*stats_out));
@@ -961,7 +1127,8 @@ crp_status crp_propagate(crp_context* c, const crp_grid* g, const crp_modules* m
     while ((1ll << bits) < kp.f.n[d]) ++bits;
     kp.key_shift[d] = bits > 5 ? bits - 5 : 0;
   }
-  const bool sort_on = m->spatial_sort >= 0;
+  kp.queue_order = m->queue_order;
+  const bool sort_on = m->queue_order >= 0;
   const int3 shift3 = make_int3(kp.key_shift[0], kp.key_shift[1], kp.key_shift[2]);
   // Work queue of round r is the list round r-1 wrote (requeued candidates
   // and new secondaries), sorted by spatial brick; round 0 lists the pool.
@@ -982,22 +1149,45 @@ crp_status crp_propagate(crp_context* c, const crp_grid* g, const crp_modules* m
   cudaError_t e = cudaMemsetAsync(c->dc, 0, sizeof(DevCounters), s);
   if (e == cudaSuccess) {
     k_set_u64<<<1, 1, 0, s>>>(&c->dc->tail, (unsigned long long)c->size);
-    k_build_queue<<<blocks_for(c->size, 256), 256, 0, s>>>(c->st, c->size, kp.f, shift3, q_out,
-                                                           c->keys, &c->dc->q_out);
+    k_build_queue<<<blocks_for(c->size, 256), 256, 0, s>>>(c->st, c->size, kp.f, shift3,
+                                                           kp.queue_order, q_out, c->keys,
+                                                           &c->dc->q_out);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(c->hc, c->dc, sizeof(DevCounters), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return fail_cuda(e, "crp_propagate: work queue");
-  uint64_t n_in = c->hc->q_out;
-  e = sort_into_qin(n_in);
-  if (e != cudaSuccess) return fail_cuda(e, "crp_propagate: queue sort");
-  kp.slice = m->slice ? m->slice : 512u;
-
+  kp.slice = m->slice ? m->slice : kDefaultSlice;
   crp_status st = CRP_OK;
   uint32_t launches = 0;
   float total_ms = 0.f;
+  if (m->use_graph) {
+    // the queue the pre-loop built sits in queue[1]; the graph's first body
+    // pass sorts it into queue[0] (fixed roles: no pointer swaps in a graph)
+    if (e != cudaSuccess) return fail_cuda(e, "crp_propagate: work queue");
+    kp.queue_in = c->queue[0];
+    kp.queue_out = c->queue[1];
+    kp.keys_out = c->keys;
+    kp.n_in = 0;
+    kp.n_in_dev = &c->dc->n_in;
+    e = graph_rounds(c, kp, m->precision, block, variant, c->sm_count * bps, sort_on, s,
+                     &total_ms);
+    if (e != cudaSuccess) return fail_cuda(e, "crp_propagate: graph");
+    e = cudaMemcpyAsync(c->hc, c->dc, sizeof(DevCounters), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_cuda(e, "crp_propagate: graph counters");
+    launches = (uint32_t)c->hc->rounds;
+    if (c->hc->stop) {
+      st = CRP_E_TIMEOUT;
+      set_error("crp_propagate: step budget or deadline reached; candidates stay resumable");
+    }
+  }
+  if (e == cudaSuccess && !m->use_graph)
+    e = cudaMemcpyAsync(c->hc, c->dc, sizeof(DevCounters), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && !m->use_graph) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail_cuda(e, "crp_propagate: work queue");
+  uint64_t n_in = m->use_graph ? 0 : c->hc->q_out;
+  if (!m->use_graph) {
+    e = sort_into_qin(n_in);
+    if (e != cudaSuccess) return fail_cuda(e, "crp_propagate: queue sort");
+  }
   while (n_in > 0) {
     kp.queue_in = q_in;
     kp.queue_out = q_out;
@@ -1304,3 +1494,106 @@ void context_view(const crp_context* c, const int32_t** status, const double** E
   *device = c->device;
 }
 }  // namespace crp
+
+// ---------------------------------------------------------------------------
+// autotuner: time a few launch configurations on the context's own
+// candidates (each from the same snapshot, each for a fixed number of
+// accepted steps) and keep the fastest.  Results do not depend on the launch
+// configuration (binary64 path: bit for bit; mixed path: slices are kept
+// multiples of the 32-step rebase period), so tuning changes only speed.
+// ---------------------------------------------------------------------------
+extern "C" crp_status crp_autotune(crp_context* c, const crp_grid* g, crp_modules* m,
+                                   uint64_t steps_per_trial, crp_tune_result* out, void* stream) {
+  if (!c || !g || !m || !out) {
+    set_error("crp_autotune: NULL argument");
+    return CRP_E_INVALID;
+  }
+  memset(out, 0, sizeof(*out));
+  if (c->size == 0) {
+    set_error("crp_autotune: inject the candidates to tune on first");
+    return CRP_E_INVALID;
+  }
+  DeviceGuard dg(c->device);
+  crp_status st = ensure_pool(c);
+  if (st != CRP_OK) return st;
+  if (steps_per_trial == 0) steps_per_trial = 200000000ull;
+  const bool whole_runs = steps_per_trial == ~0ull;  // score complete propagations
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const uint64_t size0 = c->size;
+  const size_t bytes = ckpt_payload(c, size0);
+  unsigned char* snap = static_cast<unsigned char*>(dev_alloc(bytes));
+  if (!snap) {
+    set_error("crp_autotune: cannot allocate the %zu-byte snapshot", bytes);
+    return CRP_E_OOM;
+  }
+  auto copy_pool = [&](bool save) -> cudaError_t {
+    size_t off = 0;
+    for (int a = 0; a < c->n_arr; ++a) {
+      const size_t b = (size_t)c->arr_elem[a] * size0;
+      cudaError_t e = b ? cudaMemcpyAsync(save ? snap + off : c->arr_ptr[a],
+                                          save ? c->arr_ptr[a] : snap + off, b,
+                                          cudaMemcpyDeviceToDevice, s)
+                        : cudaSuccess;
+      if (e != cudaSuccess) return e;
+      off += b;
+    }
+    c->size = size0;
+    return cudaStreamSynchronize(s);
+  };
+  struct Cfg { int block, bps; uint32_t slice; int order; };
+  Cfg cfgs[32];
+  int nc = 0;
+  const uint32_t slices[3] = {512u, 4096u, kDefaultSlice};
+  const int mixed_bl[3][2] = {{256, 2}, {256, 3}, {128, 6}};
+  const int fp64_bl[3][2] = {{128, 0}, {64, 0}, {32, 0}};
+  for (int b = 0; b < 3; ++b) {
+    const int* bl = m->precision == CRP_MIXED ? mixed_bl[b] : fp64_bl[b];
+    for (uint32_t sl : slices)
+      for (int order : {0, 1, -1}) cfgs[nc++] = Cfg{bl[0], bl[1], sl, order};
+  }
+  cudaError_t e = copy_pool(true);
+  int best = -1;
+  double best_rate = 0.0;
+  for (int k = -1; k < nc && e == cudaSuccess && st == CRP_OK; ++k) {
+    const Cfg& cf = cfgs[k < 0 ? 0 : k];  // k = -1: warm-up run, not scored
+    crp_modules mm = *m;
+    mm.block_size = cf.block;
+    mm.blocks_per_sm = cf.bps;
+    mm.slice = cf.slice;
+    mm.queue_order = cf.order;
+    mm.step_budget = whole_runs ? 0 : steps_per_trial;
+    mm.deadline_ms = 0.0;
+    crp_stats stt;
+    const auto t0 = std::chrono::steady_clock::now();
+    const crp_status r = crp_propagate(c, g, &mm, stream, &stt);
+    const double dt =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (r != CRP_OK && r != CRP_E_TIMEOUT) {
+      st = r;
+      break;
+    }
+    e = copy_pool(false);
+    if (k < 0) continue;
+    const double rate = dt > 0.0 ? (double)stt.accepted_steps / dt : 0.0;
+    if (rate > best_rate) {
+      best_rate = rate;
+      best = k;
+    }
+    out->n_tried += 1;
+  }
+  dev_free(snap);
+  if (e != cudaSuccess) return fail_cuda(e, "crp_autotune");
+  if (st != CRP_OK) return st;
+  if (best >= 0) {
+    m->block_size = cfgs[best].block;
+    m->blocks_per_sm = cfgs[best].bps;
+    m->slice = cfgs[best].slice;
+    m->queue_order = cfgs[best].order;
+    out->block_size = cfgs[best].block;
+    out->blocks_per_sm = cfgs[best].bps;
+    out->slice = cfgs[best].slice;
+    out->queue_order = cfgs[best].order;
+    out->steps_per_s = best_rate;
+  }
+  return CRP_OK;
+}

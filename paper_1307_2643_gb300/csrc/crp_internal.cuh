@@ -31,6 +31,7 @@ enum : uint32_t {
   ERR_QUEUE_FULL = 1u << 0,
   ERR_BAD_CANDIDATE = 1u << 1,
   ERR_TRIAL_LIMIT = 1u << 2,
+  ERR_ROUND_LIMIT = 1u << 3,
 };
 
 // per-candidate flag bits
@@ -56,6 +57,8 @@ struct DevCounters {
   unsigned long long acc, rej, rhs, pion, pd, secondaries, dropped, overflow, detected;
   unsigned int error_word;
   unsigned int stop;               // set when the step budget or deadline ran out
+  unsigned long long n_in;         // graph mode: entries of this round's input queue
+  unsigned long long rounds;       // graph mode: rounds run
 };
 
 struct FieldView {
@@ -94,9 +97,11 @@ struct KParams {
   // work queues of one round: pool indices of active candidates
   const uint32_t* queue_in;
   uint64_t n_in;
+  const unsigned long long* n_in_dev;  // graph mode: n_in read from the device
   uint32_t* queue_out;
   uint32_t* keys_out;              // spatial brick key of each queue_out entry
   int key_shift[3];                // cell -> brick shift per axis (32 bricks per axis)
+  int queue_order;                 // 0: rigidity key, 1: spatial brick key (see crp.h)
   uint32_t slice;                  // accepted steps per candidate per round
 };
 

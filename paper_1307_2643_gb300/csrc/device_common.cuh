@@ -208,6 +208,19 @@ __device__ __forceinline__ uint32_t brick_key(int cx, int cy, int cz, const int 
 }
 constexpr int kSortBins = 1 << 15;
 
+// Rigidity key for the work-queue sort: the top 15 bits of the binary32
+// rigidity E/Z (8 exponent + 7 mantissa bits), monotone in E/Z; neutral
+// candidates last.  Sorting ascending starts the lowest-rigidity candidates
+// (smallest Larmor radius: the most steps) first, so the longest histories
+// are not left to run alone at the end.
+__host__ __device__ __forceinline__ uint32_t rigidity_key(double E, int Z) {
+  if (Z <= 0) return (uint32_t)(kSortBins - 1);
+  const float r = (float)(E / (double)Z);
+  uint32_t b;
+  memcpy(&b, &r, 4);
+  return (b >> 16) & (uint32_t)(kSortBins - 1);
+}
+
 // Proton rest energy [eV] (CODATA 2018).
 constexpr double MP_C2_EV = 938.27208816e6;
 

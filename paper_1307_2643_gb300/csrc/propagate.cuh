@@ -359,7 +359,8 @@ __device__ __forceinline__ void photodisintegrate(const KParams& p, const DevSta
       const unsigned long long qo = atomicAdd(&dc->q_out, 1ull);
       if (qo < p.capacity) {
         p.queue_out[qo] = (uint32_t)slot;
-        p.keys_out[qo] = key_of_position(p, c.x[0], c.x[1], c.x[2]);
+        p.keys_out[qo] = p.queue_order == 1 ? key_of_position(p, c.x[0], c.x[1], c.x[2])
+                                             : rigidity_key(En, proton ? 1 : 0);
       }
       n.sec += 1;
     } else {
@@ -1103,6 +1104,7 @@ __global__ void __launch_bounds__(Bounds<Policy>::kThreads, MINB)
   StageStore<Real> S{reinterpret_cast<Real*>(smem_raw) + threadIdx.x, (int)blockDim.x};
   const int lane = threadIdx.x & 31;
   const unsigned long long t0 = globaltimer_ns();
+  const uint64_t n_in = p.n_in_dev ? *p.n_in_dev : p.n_in;
   Lane c;
   LaneCounters lc = {0, 0, 0, 0};
   bool has = false, exhausted = false, in_step = false;
@@ -1119,7 +1121,7 @@ __global__ void __launch_bounds__(Bounds<Policy>::kThreads, MINB)
       base = __shfl_sync(FULL_MASK, base, leader);
       if (need) {
         const unsigned long long mine = base + __popc(m & ((1u << lane) - 1u));
-        if (mine < p.n_in) {
+        if (mine < n_in) {
           const uint32_t slot = p.queue_in[mine];
           if (st.status[slot] == CRP_ACTIVE) {
             if ((p.flags & (CRP_PION | CRP_PHOTODIS)) && !(st.flags[slot] & CF_STATES_DRAWN))
@@ -1158,7 +1160,7 @@ __global__ void __launch_bounds__(Bounds<Policy>::kThreads, MINB)
           const unsigned long long qo = atomicAdd(&dc->q_out, 1ull);
           if (qo < p.capacity) {
             p.queue_out[qo] = c.slot;
-            p.keys_out[qo] = Policy::key(p, c);
+            p.keys_out[qo] = p.queue_order == 1 ? Policy::key(p, c) : rigidity_key(c.E, c.Z);
           }
           has = false;
         }

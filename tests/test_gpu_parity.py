@@ -417,3 +417,108 @@ def test_checkpoint_restore_resumes_bit_identically(field_f32_small, tables, pre
     assert restored.tobytes() == same_ctx.tobytes()
     if precision == crp.FP64:
         assert restored.tobytes() == full.tobytes()
+
+
+def test_mixed_launch_configuration_does_not_change_results(field_f32_small, tables):
+    """The mixed path's results do not depend on block size, register
+    variant, queue order or slice (slices are multiples of its 32-step
+    rebase period)."""
+    n, dx, B = field_f32_small
+    inj = _interaction_inputs(n_mixed=300, n_hot=100, seed=6)
+    kw = dict(precision=crp.MIXED, dtype=crp.F32, tables=tables, flags=INTERACTION_FLAGS,
+              observer_radius=1.0, **_interaction_kw())
+    a, _, _ = run_gpu(B, n, dx, inj, block_size=256, blocks_per_sm=2, slice=512, queue_order=0,
+                      **kw)
+    b, _, _ = run_gpu(B, n, dx, inj, block_size=128, blocks_per_sm=6, slice=64, queue_order=1,
+                      **kw)
+    c, _, _ = run_gpu(B, n, dx, inj, block_size=32, blocks_per_sm=3, queue_order=-1, **kw)
+    assert a.tobytes() == b.tobytes() == c.tobytes()
+
+
+def test_autotune_keeps_state_and_results(field_f32_small, tables):
+    n, dx, B = field_f32_small
+    inj = crp.host_injection(_interaction_inputs(n_mixed=3000, n_hot=300, seed=8))
+    m = len(inj["E"])
+    ref, _, _ = run_gpu(B, n, dx, inj, precision=crp.MIXED, dtype=crp.F32, tables=tables,
+                        flags=INTERACTION_FLAGS, observer_radius=1.0, **_interaction_kw())
+    ctx = crp.crp_context_create(0, 1234, 64 * m)
+    try:
+        g = crp.crp_grid_create(ctx, crp.grid_desc(n, dx, dtype=crp.F32, data=B))
+        th = crp.crp_tables_from_host(ctx, crp.tables_desc(n=tables.n), tables.beta_pair,
+                                      tables.rate_pion, tables.rate_gdr)
+        crp.crp_candidates_inject(ctx, crp.candidate_arrays(inj), m)
+        M = crp.modules(precision=crp.MIXED, tables=th, flags=INTERACTION_FLAGS,
+                        observer_radius=1.0, **_interaction_kw())
+        r = crp.crp_autotune(ctx, g, M, steps_per_trial=200_000)
+        assert r["n_tried"] == 27 and r["steps_per_s"] > 0
+        assert (M.block_size, M.blocks_per_sm, M.slice, M.queue_order) == \
+            (r["block_size"], r["blocks_per_sm"], r["slice"], r["queue_order"])
+        assert M.slice % 32 == 0 and M.queue_order in (-1, 0, 1)
+        assert crp.crp_context_size(ctx) == m
+        crp.crp_propagate(ctx, g, M)
+        got = np.sort(crp.crp_collect(ctx, crp.COLLECT_ALL), order="id")
+        # whole-run scoring mode
+        crp.crp_candidates_clear(ctx)
+        crp.crp_candidates_inject(ctx, crp.candidate_arrays(inj), m)
+        r2 = crp.crp_autotune(ctx, g, M, steps_per_trial=2**64 - 1)
+        assert r2["n_tried"] == 27
+        crp.crp_tables_destroy(th)
+        crp.crp_grid_destroy(g)
+    finally:
+        crp.crp_context_destroy(ctx)
+    assert got.tobytes() == ref.tobytes()
+
+
+@pytest.mark.parametrize("precision", [crp.FP64, crp.MIXED])
+def test_graph_mode_equals_host_rounds(field_f32_small, tables, precision):
+    """The round loop captured as one CUDA graph (device-side loop
+    condition) gives the host-driven loop's records, over several rounds
+    (short slices, photodisintegration secondaries), for every queue order,
+    and replays its cached graph on a second call."""
+    n, dx, B = field_f32_small
+    inj = _interaction_inputs(n_mixed=300, n_hot=120, seed=31)
+    kw = dict(precision=precision, dtype=crp.F32, tables=tables, flags=INTERACTION_FLAGS,
+              observer_radius=1.0, slice=64, **_interaction_kw())
+    host, st_h, _ = run_gpu(B, n, dx, inj, **kw)
+    assert st_h["launches"] > 3 and st_h["n_secondaries"] > 0
+    for order in (0, 1, -1):
+        g, st_g, status = run_gpu(B, n, dx, inj, use_graph=1, queue_order=order, **kw)
+        assert status == crp.OK
+        assert g.tobytes() == host.tobytes()
+        assert st_g["accepted_steps"] == st_h["accepted_steps"]
+        assert st_g["launches"] == st_h["launches"]
+    # replay of the cached graph within one context, and a budgeted graph run
+    inj = crp.host_injection(inj)
+    m = len(inj["E"])
+    ctx = crp.crp_context_create(0, 1234, 64 * m)
+    try:
+        gr = crp.crp_grid_create(ctx, crp.grid_desc(n, dx, dtype=crp.F32, data=B))
+        th = crp.crp_tables_from_host(ctx, crp.tables_desc(n=tables.n), tables.beta_pair,
+                                      tables.rate_pion, tables.rate_gdr)
+        M = crp.modules(precision=precision, tables=th, flags=INTERACTION_FLAGS,
+                        observer_radius=1.0, slice=64, use_graph=1, **_interaction_kw())
+        outs = []
+        for _ in range(2):
+            crp.crp_candidates_clear(ctx)
+            crp.crp_candidates_inject(ctx, crp.candidate_arrays(inj), m)
+            crp.crp_propagate(ctx, gr, M)
+            outs.append(np.sort(crp.crp_collect(ctx, crp.COLLECT_ALL), order="id"))
+        crp.crp_candidates_clear(ctx)
+        crp.crp_candidates_inject(ctx, crp.candidate_arrays(inj), m)
+        M.step_budget = 20000
+        calls = 0
+        while True:
+            status, _ = crp.crp_propagate(ctx, gr, M, raise_on_error=False)
+            calls += 1
+            assert status in (crp.OK, crp.E_TIMEOUT) and calls < 10000
+            if status == crp.OK:
+                break
+        budgeted = np.sort(crp.crp_collect(ctx, crp.COLLECT_ALL), order="id")
+        crp.crp_tables_destroy(th)
+        crp.crp_grid_destroy(gr)
+    finally:
+        crp.crp_context_destroy(ctx)
+    assert outs[0].tobytes() == outs[1].tobytes() == host.tobytes()
+    assert calls > 3
+    if precision == crp.FP64:
+        assert budgeted.tobytes() == host.tobytes()
