@@ -109,7 +109,11 @@ typedef struct {
    * (x fastest, components Bx, By, Bz adjacent), element type data_dtype.  */
   const void* data;
   int32_t data_dtype;
-  int32_t reserved;
+  /* F32 grids: 0 = also store, per cell, its 8 corner vectors in one aligned
+   * 128-byte record (24 floats; 8x the node array), so that the mixed
+   * path's trilinear gather reads one cache line; -1 = nodes only.  When the
+   * records do not fit in memory the grid is created without them. */
+  int32_t cell_records;
   /* TURBULENT: Gaussian Fourier modes with 2pi/lmax <= |k| <= 2pi/lmin,
    * projected perpendicular to k (divergence free), power |B(k)|^2 ~ |k|^index
    * (index = -11/3 for Kolmogorov), inverse FFT, real part, mean removed,
@@ -395,6 +399,16 @@ crp_status crp_histogram_healpix(crp_context* ctx, int32_t what, int32_t nside, 
  * [e_lo, e_hi) (under/overflow dropped).  out: host uint64 array of nbins. */
 crp_status crp_histogram_energy(crp_context* ctx, int32_t what, double e_lo, double e_hi,
                                 int32_t nbins, uint64_t* out, void* stream);
+
+/* The magnetic field at n points (host arrays xyz [n][3] and B_out [n][3],
+ * binary64, the length and field units of the grid) exactly as the
+ * propagate kernels of m->precision evaluate it: the grid's trilinear
+ * interpolation (Sect. 4: grids for fast lookup) plus, with CRP_GALACTIC in
+ * m->flags, the analytic disk and halo field of m.  CRP_FP64: binary64 nested
+ * interpolation; CRP_MIXED: binary32 (from the cell polynomial records when
+ * the grid has them).  Synchronous. */
+crp_status crp_grid_sample(const crp_grid* grid, const crp_modules* m, int64_t n,
+                           const double* xyz, double* B_out);
 
 /* Launch-configuration autotuner (no counterpart in the paper; the
  * scheduler's tunables are this library's own).  Times crp_propagate on the

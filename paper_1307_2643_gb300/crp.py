@@ -41,7 +41,7 @@ class CrpError(RuntimeError):
 class GridDesc(C.Structure):
     _fields_ = [("n", C.c_int64 * 3), ("spacing", C.c_double), ("origin", C.c_double * 3),
                 ("dtype", C.c_int32), ("source", C.c_int32), ("data", C.c_void_p),
-                ("data_dtype", C.c_int32), ("reserved", C.c_int32),
+                ("data_dtype", C.c_int32), ("cell_records", C.c_int32),
                 ("lmin", C.c_double), ("lmax", C.c_double), ("brms", C.c_double),
                 ("spectral_index", C.c_double), ("seed", C.c_uint64)]
 
@@ -133,7 +133,7 @@ SYMBOLS = (
     "crp_histogram_healpix",
     "crp_mlp_create", "crp_mlp_destroy", "crp_mlp_num_params", "crp_mlp_set_params",
     "crp_mlp_get_params", "crp_mlp_forward", "crp_mlp_train_step", "crp_lens_build_surrogate",
-    "crp_checkpoint", "crp_restore", "crp_measure_peaks", "crp_autotune",
+    "crp_checkpoint", "crp_restore", "crp_measure_peaks", "crp_autotune", "crp_grid_sample",
 )
 
 _lock = threading.Lock()
@@ -188,6 +188,7 @@ def lib():
             L.crp_checkpoint.argtypes = [p, p, sz, C.POINTER(sz), p]
             L.crp_restore.argtypes = [p, p, sz, p]
             L.crp_measure_peaks.argtypes = [i32, C.POINTER(Peaks)]
+            L.crp_grid_sample.argtypes = [p, C.POINTER(Modules), C.c_int64, p, p]
             L.crp_autotune.argtypes = [p, p, C.POINTER(Modules), u64, C.POINTER(TuneResult), p]
             for name in SYMBOLS:
                 if name not in ("crp_last_error", "crp_version"):
@@ -269,6 +270,15 @@ def crp_grid_create(ctx, desc: GridDesc):
     h = C.c_void_p()
     _check(lib().crp_grid_create(ctx, C.byref(desc), C.byref(h)))
     return h
+
+
+def crp_grid_sample(grid, modules: Modules, xyz):
+    """Field [m, 3] at points xyz [m, 3] as the kernels of modules.precision see it."""
+    pts = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros_like(pts)
+    _check(lib().crp_grid_sample(grid, C.byref(modules), len(pts), pts.ctypes.data,
+                                 out.ctypes.data))
+    return out
 
 
 def crp_grid_destroy(grid):
@@ -507,7 +517,8 @@ def host_injection(inj: dict) -> dict:
 
 
 def grid_desc(n, spacing, origin=(0.0, 0.0, 0.0), dtype=F64, source=GRID_FROM_HOST, data=None,
-              data_dtype=F64, lmin=0.0, lmax=0.0, brms=0.0, spectral_index=-11.0 / 3.0, seed=0):
+              data_dtype=F64, lmin=0.0, lmax=0.0, brms=0.0, spectral_index=-11.0 / 3.0, seed=0,
+              cell_records=0):
     d = GridDesc()
     d.n[:] = n
     d.spacing = spacing
@@ -515,6 +526,7 @@ def grid_desc(n, spacing, origin=(0.0, 0.0, 0.0), dtype=F64, source=GRID_FROM_HO
     d.dtype, d.source = dtype, source
     d.data = _addr(data)
     d.data_dtype = data_dtype
+    d.cell_records = cell_records
     d.lmin, d.lmax, d.brms, d.spectral_index, d.seed = lmin, lmax, brms, spectral_index, seed
     return d
 

@@ -114,6 +114,7 @@ struct crp_grid {
   crp_context* ctx;
   crp_grid_desc desc;
   void* nodes;
+  void* cells;  // F32: per-cell corner records (8 float4 per cell), or null
   int64_t N;
 };
 
@@ -627,6 +628,10 @@ crp_status crp_grid_create(crp_context* c, const crp_grid_desc* d, crp_grid** ou
     set_error("crp_grid_create: at most 2^20 nodes per axis");
     return CRP_E_INVALID;
   }
+  if (d->cell_records != 0 && d->cell_records != -1) {
+    set_error("crp_grid_create: cell_records must be 0 or -1");
+    return CRP_E_INVALID;
+  }
   const int64_t N = d->n[0] * d->n[1] * d->n[2];
   if (d->source == CRP_GRID_TURBULENT) {
     if (!(d->lmin > 0.0) || !(d->lmax >= d->lmin) || !(d->brms >= 0.0)) {
@@ -685,7 +690,20 @@ crp_status crp_grid_create(crp_context* c, const crp_grid_desc* d, crp_grid** ou
     }
     dev_free(staging);
   }
+  gr->cells = nullptr;
+  if (st == CRP_OK && d->dtype == CRP_F32 && d->cell_records == 0) {
+    // optional: a grid without records still works (node gathers)
+    gr->cells = dev_alloc((size_t)N * 8 * sizeof(float4));
+    if (gr->cells) {
+      st = grid_cells(gr->nodes, d->n, gr->cells, s);
+      if (st == CRP_OK) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = fail_cuda(e, "crp_grid_create: cell records");
+      }
+    }
+  }
   if (st != CRP_OK) {
+    dev_free(gr->cells);
     dev_free(gr->nodes);
     delete gr;
     return st;
@@ -698,6 +716,7 @@ crp_status crp_grid_destroy(crp_grid* g) {
   if (!g) return CRP_OK;
   DeviceGuard dg(g->ctx->device);
   cudaDeviceSynchronize();
+  dev_free(g->cells);
   dev_free(g->nodes);
   delete g;
   return CRP_OK;
@@ -909,6 +928,7 @@ crp_status crp_candidates_clear(crp_context* c) {
 // ---------------------------------------------------------------------------
 static void fill_field_view(const crp_grid* g, FieldView& f) {
   f.data = g->nodes;
+  f.cells = static_cast<const float4*>(g->cells);
   for (int d = 0; d < 3; ++d) {
     f.n[d] = g->desc.n[d];
     f.mask[d] = (g->desc.n[d] & (g->desc.n[d] - 1)) == 0 ? g->desc.n[d] - 1 : -1;
@@ -918,6 +938,31 @@ static void fill_field_view(const crp_grid* g, FieldView& f) {
   f.inv_spacing = 1.0 / g->desc.spacing;
   f.inv_spacing_f = (float)f.inv_spacing;
   f.dtype = g->desc.dtype;
+}
+
+// Galactic-field parameters: binary64 values first, then the binary32
+// copies the mixed path uses.
+static void fill_galactic(const crp_modules* m, KParams& kp) {
+  for (int d = 0; d < 3; ++d) kp.gal_c[d] = m->gal_center[d];
+  kp.disk_b = m->disk_b;
+  kp.sin_pitch = sin(m->disk_pitch_rad);
+  kp.cos_pitch = cos(m->disk_pitch_rad);
+  kp.disk_hz = m->disk_hz;
+  kp.disk_rmin = m->disk_rmin;
+  kp.disk_rmax = m->disk_rmax;
+  kp.halo_b = m->halo_b;
+  kp.halo_z0 = m->halo_z0;
+  kp.halo_sigma = m->halo_sigma;
+  kp.gdisk_b = (float)kp.disk_b;
+  kp.gsin = (float)kp.sin_pitch;
+  kp.gcos = (float)kp.cos_pitch;
+  kp.ginv_hz = kp.disk_hz > 0.0 ? (float)(1.0 / kp.disk_hz) : 0.f;
+  kp.grmin = (float)kp.disk_rmin;
+  kp.grmax = (float)kp.disk_rmax;
+  kp.ghalo_b = (float)kp.halo_b;
+  kp.ghalo_z0 = (float)kp.halo_z0;
+  kp.ghalo_inv2s2 =
+      kp.halo_sigma > 0.0 ? (float)(1.0 / (2.0 * kp.halo_sigma * kp.halo_sigma)) : 0.f;
 }
 
 // Graph mode: capture the round loop once (a while node whose body sorts
@@ -1075,31 +1120,13 @@ crp_status crp_propagate(crp_context* c, const crp_grid* g, const crp_modules* m
   kp.beta_ad_f = (float)kp.beta_ad;
   kp.tab_lg0_f = (float)kp.tab_lg0;
   kp.tab_inv_dlg_f = (float)kp.tab_inv_dlg;
-  kp.gdisk_b = (float)m->disk_b;
-  kp.gsin = (float)kp.sin_pitch;
-  kp.gcos = (float)kp.cos_pitch;
-  kp.ginv_hz = m->disk_hz > 0.0 ? (float)(1.0 / m->disk_hz) : 0.f;
-  kp.grmin = (float)m->disk_rmin;
-  kp.grmax = (float)m->disk_rmax;
-  kp.ghalo_b = (float)m->halo_b;
-  kp.ghalo_z0 = (float)m->halo_z0;
-  kp.ghalo_inv2s2 = m->halo_sigma > 0.0 ? (float)(1.0 / (2.0 * m->halo_sigma * m->halo_sigma)) : 0.f;
+  fill_galactic(m, kp);
   for (int d = 0; d < 3; ++d) {
     kp.obs_c[d] = m->observer_center[d];
     kp.border_c[d] = m->border_center[d];
-    kp.gal_c[d] = m->gal_center[d];
   }
   kp.obs_r = m->observer_radius;
   kp.border_r = m->border_radius;
-  kp.disk_b = m->disk_b;
-  kp.sin_pitch = sin(m->disk_pitch_rad);
-  kp.cos_pitch = cos(m->disk_pitch_rad);
-  kp.disk_hz = m->disk_hz;
-  kp.disk_rmin = m->disk_rmin;
-  kp.disk_rmax = m->disk_rmax;
-  kp.halo_b = m->halo_b;
-  kp.halo_z0 = m->halo_z0;
-  kp.halo_sigma = m->halo_sigma;
   kp.max_steps = m->max_steps ? m->max_steps : 100000000ull;  // bound every candidate
   kp.step_budget = m->step_budget;
   kp.deadline_ns = m->deadline_ms > 0.0 ? (uint64_t)(m->deadline_ms * 1e6) : 0;
@@ -1596,4 +1623,44 @@ extern "C" crp_status crp_autotune(crp_context* c, const crp_grid* g, crp_module
     out->steps_per_s = best_rate;
   }
   return CRP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// field sampling: the interpolated field exactly as the propagate kernels
+// of the given precision evaluate it
+// ---------------------------------------------------------------------------
+extern "C" crp_status crp_grid_sample(const crp_grid* g, const crp_modules* m, int64_t n,
+                                      const double* xyz, double* B_out) {
+  if (!g || !m || n < 0 || (n && (!xyz || !B_out)) ||
+      (m->precision != CRP_FP64 && m->precision != CRP_MIXED)) {
+    set_error("crp_grid_sample: bad argument");
+    return CRP_E_INVALID;
+  }
+  if (n == 0) return CRP_OK;
+  DeviceGuard dg(g->ctx->device);
+  KParams kp;
+  memset(&kp, 0, sizeof(kp));
+  fill_field_view(g, kp.f);
+  kp.flags = m->flags & CRP_GALACTIC;
+  fill_galactic(m, kp);
+  const size_t bytes = (size_t)n * 3 * sizeof(double);
+  double* dx = static_cast<double*>(dev_alloc(bytes));
+  double* dB = static_cast<double*>(dev_alloc(bytes));
+  crp_status st = CRP_OK;
+  if (!dx || !dB) {
+    set_error("crp_grid_sample: device allocation failed");
+    st = CRP_E_OOM;
+  } else {
+    cudaStream_t s = 0;
+    cudaError_t e = cudaMemcpyAsync(dx, xyz, bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = m->precision == CRP_FP64 ? sample_field_fp64(kp, dx, n, dB, s)
+                                   : sample_field_mixed(kp, dx, n, dB, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(B_out, dB, bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = fail_cuda(e, "crp_grid_sample");
+  }
+  dev_free(dx);
+  dev_free(dB);
+  return st;
 }

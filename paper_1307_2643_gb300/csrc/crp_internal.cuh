@@ -63,6 +63,7 @@ struct DevCounters {
 
 struct FieldView {
   const void* data;                // float4 (F32) or DNode (F64) per node
+  const float4* cells;             // F32: 8 float4 per cell (corner vectors), or null
   int64_t n[3];
   int64_t mask[3];                 // n-1 when n is a power of two, else -1
   double origin[3];
@@ -115,6 +116,13 @@ cudaError_t occupancy_propagate_mixed(int dtype, int galactic, int variant, int 
                                       int* blocks_per_sm);
 // Dynamic shared memory of one propagate block (per-thread stage storage).
 size_t propagate_smem_fp64(int block);
+// The field the propagate kernels see, at n points (device arrays xyz [n][3]
+// and B [n][3], binary64): the binary64 path's interpolation, or the mixed
+// path's (binary32, from the position's cell and fraction).
+cudaError_t sample_field_fp64(const KParams& kp, const double* xyz, int64_t n, double* B,
+                              cudaStream_t s);
+cudaError_t sample_field_mixed(const KParams& kp, const double* xyz, int64_t n, double* B,
+                               cudaStream_t s);
 size_t propagate_smem_mixed(int block);
 
 }  // namespace crp

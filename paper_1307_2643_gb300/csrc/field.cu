@@ -172,9 +172,72 @@ int grid_blocks(int64_t N) {
   return (int)(b < 65536 ? b : 65536);
 }
 
+// Cell (i, j, k) record: the coefficients of the cell's trilinear
+// polynomial in the in-cell fractions (tx, ty, tz),
+//   B = c0 + c1 tx + c2 ty + c3 tz + c4 tx ty + c5 tx tz + c6 ty tz + c7 tx ty tz,
+// from the corner vectors v_(a + 2b + 4c) of nodes (i + a, j + b, k + c)
+// (periodic), formed in binary64 and rounded once to binary32; 24 floats
+// (coefficient-major, Bx By Bz) in 8 float4, the last two zero.
+__global__ void k_grid_cells(const float4* __restrict__ nodes, int64_t nx, int64_t ny, int64_t nz,
+                             float4* __restrict__ cells) {
+  const int64_t N = nx * ny * nz;
+  for (int64_t lin = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; lin < N;
+       lin += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = lin % nx, j = (lin / nx) % ny, k = lin / (nx * ny);
+    const int64_t i1 = i + 1 == nx ? 0 : i + 1, j1 = j + 1 == ny ? 0 : j + 1,
+                  k1 = k + 1 == nz ? 0 : k + 1;
+    const int64_t xs[2] = {i, i1}, ys[2] = {j, j1}, zs[2] = {k, k1};
+    double v[8][3];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const float4 b = nodes[(zs[c >> 2] * ny + ys[(c >> 1) & 1]) * nx + xs[c & 1]];
+      v[c][0] = b.x;
+      v[c][1] = b.y;
+      v[c][2] = b.z;
+    }
+    float q[32];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const double c0 = v[0][d];
+      const double c1 = v[1][d] - v[0][d];
+      const double c2 = v[2][d] - v[0][d];
+      const double c3 = v[4][d] - v[0][d];
+      const double c4 = v[3][d] - v[2][d] - v[1][d] + v[0][d];
+      const double c5 = v[5][d] - v[4][d] - v[1][d] + v[0][d];
+      const double c6 = v[6][d] - v[4][d] - v[2][d] + v[0][d];
+      const double c7 = v[7][d] - v[6][d] - v[5][d] - v[3][d] + v[4][d] + v[2][d] + v[1][d] -
+                        v[0][d];
+      q[d] = (float)c0;
+      q[3 + d] = (float)c1;
+      q[6 + d] = (float)c2;
+      q[9 + d] = (float)c3;
+      q[12 + d] = (float)c4;
+      q[15 + d] = (float)c5;
+      q[18 + d] = (float)c6;
+      q[21 + d] = (float)c7;
+    }
+#pragma unroll
+    for (int r = 24; r < 32; ++r) q[r] = 0.f;
+    float4* out = cells + 8 * lin;
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+      out[r] = make_float4(q[4 * r], q[4 * r + 1], q[4 * r + 2], q[4 * r + 3]);
+  }
+}
+
 }  // namespace
 
 size_t node_bytes(int dtype) { return dtype == CRP_F32 ? sizeof(float4) : sizeof(DNode); }
+
+crp_status grid_cells(const void* nodes, const int64_t n[3], void* cells, cudaStream_t s) {
+  const int64_t N = n[0] * n[1] * n[2];
+  int64_t g = (N + kBlock - 1) / kBlock;
+  if (g > 65535 * 8) g = 65535 * 8;
+  k_grid_cells<<<(unsigned)g, kBlock, 0, s>>>(static_cast<const float4*>(nodes), n[0], n[1],
+                                               n[2], static_cast<float4*>(cells));
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? CRP_OK : fail_cuda(e, "grid: cell records");
+}
 
 crp_status grid_pack(const void* src_dev, int src_dtype, int64_t N, int dtype, void* nodes,
                      cudaStream_t s) {

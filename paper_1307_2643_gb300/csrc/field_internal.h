@@ -14,6 +14,11 @@ crp_status grid_pack(const void* src_dev, int src_dtype, int64_t N, int dtype, v
                      cudaStream_t s);
 // Convert node storage into [N][3] float64 on the device.
 crp_status grid_unpack(const void* nodes, int dtype, int64_t N, double* dst_dev, cudaStream_t s);
+// Per-cell records of a binary32 node grid: cell (i, j, k) holds the 8
+// coefficients of its trilinear polynomial in the in-cell fractions (see
+// field.cu), 24 floats in 8 float4 (the last two zero): one aligned
+// 128-byte record per cell.
+crp_status grid_cells(const void* nodes, const int64_t n[3], void* cells, cudaStream_t s);
 // Generate the turbulent field of `d` into node storage (synchronises s).
 crp_status grid_turbulence(const crp_grid_desc* d, void* nodes, cudaStream_t s);
 // Fill the three rate tables (device arrays of d->n doubles) by quadrature.

@@ -841,30 +841,48 @@ struct PolicyMixedT {
     const int ix0 = wrap_int(c.cell[0] + (int)fx, nx, (int)f.mask[0]);
     const int iy0 = wrap_int(c.cell[1] + (int)fy, ny, (int)f.mask[1]);
     const int iz0 = wrap_int(c.cell[2] + (int)fz, nz, (int)f.mask[2]);
-    const int ix1 = ix0 + 1 == nx ? 0 : ix0 + 1;
-    const int iy1 = iy0 + 1 == ny ? 0 : iy0 + 1;
-    const int iz1 = iz0 + 1 == nz ? 0 : iz0 + 1;
-    const size_t snx = (size_t)nx, snxy = (size_t)nx * (size_t)ny;
-    const size_t r00 = (size_t)iz0 * snxy + (size_t)iy0 * snx;
-    const size_t r01 = (size_t)iz0 * snxy + (size_t)iy1 * snx;
-    const size_t r10 = (size_t)iz1 * snxy + (size_t)iy0 * snx;
-    const size_t r11 = (size_t)iz1 * snxy + (size_t)iy1 * snx;
-    const float4 v0 = Node<NodeT>::loadf(f.data, r00 + ix0);
-    const float4 v1 = Node<NodeT>::loadf(f.data, r00 + ix1);
-    const float4 v2 = Node<NodeT>::loadf(f.data, r01 + ix0);
-    const float4 v3 = Node<NodeT>::loadf(f.data, r01 + ix1);
-    const float4 v4 = Node<NodeT>::loadf(f.data, r10 + ix0);
-    const float4 v5 = Node<NodeT>::loadf(f.data, r10 + ix1);
-    const float4 v6 = Node<NodeT>::loadf(f.data, r11 + ix0);
-    const float4 v7 = Node<NodeT>::loadf(f.data, r11 + ix1);
-    auto lerp = [](float a, float b, float t) { return fmaf(t, b - a, a); };
     float3 B;
-    B.x = lerp(lerp(lerp(v0.x, v1.x, tx), lerp(v2.x, v3.x, tx), ty),
-               lerp(lerp(v4.x, v5.x, tx), lerp(v6.x, v7.x, tx), ty), tz);
-    B.y = lerp(lerp(lerp(v0.y, v1.y, tx), lerp(v2.y, v3.y, tx), ty),
-               lerp(lerp(v4.y, v5.y, tx), lerp(v6.y, v7.y, tx), ty), tz);
-    B.z = lerp(lerp(lerp(v0.z, v1.z, tx), lerp(v2.z, v3.z, tx), ty),
-               lerp(lerp(v4.z, v5.z, tx), lerp(v6.z, v7.z, tx), ty), tz);
+    if (std::is_same<NodeT, float4>::value && f.cells) {
+      // one aligned 128-byte record: the cell's trilinear polynomial,
+      // evaluated in Horner form (7 FMAs per component)
+      const float4* r = f.cells + 8 * (((size_t)iz0 * ny + (size_t)iy0) * nx + (size_t)ix0);
+      const float4 a0 = __ldg(r), a1 = __ldg(r + 1), a2 = __ldg(r + 2);
+      const float4 a3 = __ldg(r + 3), a4 = __ldg(r + 4), a5 = __ldg(r + 5);
+      // coefficient j of component d is float 3j + d of the record
+      auto horner = [&](float c0, float c1, float c2, float c3, float c4, float c5, float c6,
+                        float c7) {
+        const float xy = fmaf(fmaf(c7, tz, c4), ty, fmaf(c5, tz, c1));
+        const float y0 = fmaf(fmaf(c6, tz, c2), ty, fmaf(c3, tz, c0));
+        return fmaf(xy, tx, y0);
+      };
+      B.x = horner(a0.x, a0.w, a1.z, a2.y, a3.x, a3.w, a4.z, a5.y);
+      B.y = horner(a0.y, a1.x, a1.w, a2.z, a3.y, a4.x, a4.w, a5.z);
+      B.z = horner(a0.z, a1.y, a2.x, a2.w, a3.z, a4.y, a5.x, a5.w);
+    } else {
+      const int ix1 = ix0 + 1 == nx ? 0 : ix0 + 1;
+      const int iy1 = iy0 + 1 == ny ? 0 : iy0 + 1;
+      const int iz1 = iz0 + 1 == nz ? 0 : iz0 + 1;
+      const size_t snx = (size_t)nx, snxy = (size_t)nx * (size_t)ny;
+      const size_t r00 = (size_t)iz0 * snxy + (size_t)iy0 * snx;
+      const size_t r01 = (size_t)iz0 * snxy + (size_t)iy1 * snx;
+      const size_t r10 = (size_t)iz1 * snxy + (size_t)iy0 * snx;
+      const size_t r11 = (size_t)iz1 * snxy + (size_t)iy1 * snx;
+      const float4 v0 = Node<NodeT>::loadf(f.data, r00 + ix0);
+      const float4 v1 = Node<NodeT>::loadf(f.data, r00 + ix1);
+      const float4 v2 = Node<NodeT>::loadf(f.data, r01 + ix0);
+      const float4 v3 = Node<NodeT>::loadf(f.data, r01 + ix1);
+      const float4 v4 = Node<NodeT>::loadf(f.data, r10 + ix0);
+      const float4 v5 = Node<NodeT>::loadf(f.data, r10 + ix1);
+      const float4 v6 = Node<NodeT>::loadf(f.data, r11 + ix0);
+      const float4 v7 = Node<NodeT>::loadf(f.data, r11 + ix1);
+      auto lerp = [](float a, float b, float t) { return fmaf(t, b - a, a); };
+      B.x = lerp(lerp(lerp(v0.x, v1.x, tx), lerp(v2.x, v3.x, tx), ty),
+                 lerp(lerp(v4.x, v5.x, tx), lerp(v6.x, v7.x, tx), ty), tz);
+      B.y = lerp(lerp(lerp(v0.y, v1.y, tx), lerp(v2.y, v3.y, tx), ty),
+                 lerp(lerp(v4.y, v5.y, tx), lerp(v6.y, v7.y, tx), ty), tz);
+      B.z = lerp(lerp(lerp(v0.z, v1.z, tx), lerp(v2.z, v3.z, tx), ty),
+                 lerp(lerp(v4.z, v5.z, tx), lerp(v6.z, v7.z, tx), ty), tz);
+    }
     if constexpr (GAL) {
       const float3 G = galactic_f32(p, c.gal[0] + ox, c.gal[1] + oy, c.gal[2] + oz);
       B.x += G.x;

@@ -27,4 +27,40 @@ cudaError_t occupancy_propagate_mixed(int dtype, int galactic, int variant, int 
 
 size_t propagate_smem_mixed(int block) { return smem_bytes<PolicyMixed>(block); }
 
+namespace {
+template <class Policy, class NodeT>
+__global__ void k_sample_mixed(const KParams p, const double* xyz, int64_t n, double* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    typename Policy::Lane c;
+    c.x[0] = xyz[3 * i];
+    c.x[1] = xyz[3 * i + 1];
+    c.x[2] = xyz[3 * i + 2];
+    Policy::rebase(p, c);
+    const float3 B = Policy::template field<NodeT>(p, c, 0.f, 0.f, 0.f);
+    out[3 * i] = B.x;
+    out[3 * i + 1] = B.y;
+    out[3 * i + 2] = B.z;
+  }
+}
+
+template <class Policy>
+cudaError_t sample_policy(const KParams& kp, const double* xyz, int64_t n, double* B,
+                          cudaStream_t s) {
+  const int64_t g64 = (n + 255) / 256;
+  const unsigned g = (unsigned)(g64 < 1 ? 1 : (g64 > 65535 ? 65535 : g64));
+  if (kp.f.dtype == CRP_F32)
+    k_sample_mixed<Policy, float4><<<g, 256, 0, s>>>(kp, xyz, n, B);
+  else
+    k_sample_mixed<Policy, DNode><<<g, 256, 0, s>>>(kp, xyz, n, B);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t sample_field_mixed(const KParams& kp, const double* xyz, int64_t n, double* B,
+                               cudaStream_t s) {
+  return (kp.flags & CRP_GALACTIC) ? sample_policy<PolicyMixedGal>(kp, xyz, n, B, s)
+                                   : sample_policy<PolicyMixed>(kp, xyz, n, B, s);
+}
+
 }  // namespace crp

@@ -522,3 +522,48 @@ def test_graph_mode_equals_host_rounds(field_f32_small, tables, precision):
     assert calls > 3
     if precision == crp.FP64:
         assert budgeted.tobytes() == host.tobytes()
+
+
+@pytest.mark.parametrize("galactic", [False, True])
+def test_field_sampling_matches_oracle(galactic):
+    """The field the kernels see: binary64 sampling equals the oracle's
+    trilinear (+ analytic galactic) field bit for bit; binary32 sampling, from
+    the cell polynomial records or from the nodes, agrees to binary32
+    rounding (1e-5 of the field scale)."""
+    W = workloads.GALACTIC_LENS
+    n2 = (24, 20, 18)  # ragged, not powers of two: exercises every wrap
+    dx = 0.9
+    B = oracle.turbulent_field(n2, dx, 2 * dx, 8.0, 3.0, seed=5)
+    B32 = B.astype(np.float32).astype(np.float64)
+    g = np.random.default_rng(4)
+    pts = g.uniform(-25.0, 25.0, size=(4000, 3))
+    pts[:8] = [[0, 0, 0], [dx, 0, 0], [23 * dx, 19 * dx, 17 * dx], [-dx, -dx, -dx],
+               [24 * dx, 0, 0], [0.5 * dx, 0.5 * dx, 0.5 * dx], [-8.5, 0.0, 0.0], [3.0, 4.0, 1.0]]
+    flags = crp.GALACTIC if galactic else 0
+    gal = W["disk"] if galactic else None
+    P = oracle.make_params(grid_n=n2, spacing=dx, origin=(-10.0, -9.0, -8.0),
+                           field_unit_T=oracle.MICROGAUSS_T, length_unit_m=oracle.KPC_M,
+                           flags=oracle.GALACTIC if galactic else 0, galactic=gal)
+    ctx = crp.crp_context_create(0, 1, 16)
+    try:
+        for dtype, data, ref_field in ((crp.F64, B, B), (crp.F32, B32, B32)):
+            ref = oracle.field_at(P, ref_field, pts)
+            scale = np.sqrt(np.mean(np.sum(ref ** 2, axis=1)))
+            for cells in ((0, -1) if dtype == crp.F32 else (0,)):
+                gr = crp.crp_grid_create(ctx, crp.grid_desc(
+                    n2, dx, origin=(-10.0, -9.0, -8.0), dtype=dtype, data=data,
+                    data_dtype=crp.F64, cell_records=cells))
+                m64 = crp.modules(precision=crp.FP64, flags=flags, galactic=gal,
+                                  field_unit_T=crp.MICROGAUSS_T, length_unit_m=crp.KPC_M)
+                m32 = crp.modules(precision=crp.MIXED, flags=flags, galactic=gal,
+                                  field_unit_T=crp.MICROGAUSS_T, length_unit_m=crp.KPC_M)
+                got64 = crp.crp_grid_sample(gr, m64, pts)
+                got32 = crp.crp_grid_sample(gr, m32, pts)
+                crp.crp_grid_destroy(gr)
+                assert np.array_equal(got64, ref), (dtype, cells)
+                err = np.max(np.abs(got32 - ref))
+                assert err < 1e-5 * scale, (dtype, cells, err / scale)
+    finally:
+        crp.crp_context_destroy(ctx)
+
+
