@@ -929,6 +929,7 @@ crp_status crp_candidates_clear(crp_context* c) {
 static void fill_field_view(const crp_grid* g, FieldView& f) {
   f.data = g->nodes;
   f.cells = static_cast<const float4*>(g->cells);
+  f.cache_ok = g->N < 0xffffffffll ? 1 : 0;
   for (int d = 0; d < 3; ++d) {
     f.n[d] = g->desc.n[d];
     f.mask[d] = (g->desc.n[d] & (g->desc.n[d] - 1)) == 0 ? g->desc.n[d] - 1 : -1;

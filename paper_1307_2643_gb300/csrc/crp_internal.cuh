@@ -63,7 +63,8 @@ struct DevCounters {
 
 struct FieldView {
   const void* data;                // float4 (F32) or DNode (F64) per node
-  const float4* cells;             // F32: 8 float4 per cell (corner vectors), or null
+  const float4* cells;             // F32: 8 float4 per cell (polynomial records), or null
+  int cache_ok;                    // cell indices fit 32 bits (per-lane record cache usable)
   int64_t n[3];
   int64_t mask[3];                 // n-1 when n is a power of two, else -1
   double origin[3];

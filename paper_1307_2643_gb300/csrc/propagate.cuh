@@ -160,6 +160,10 @@ __device__ __forceinline__ float3 galactic_f32(const KParams& p, float rx, float
   return make_float3(b_r * cr - b_phi * sr, b_r * sr + b_phi * cr, 0.f);
 }
 
+// Dynamic shared memory of the propagate kernels (FP64: stage vectors;
+// mixed: per-lane cell-record cache).
+extern __shared__ __align__(16) unsigned char crp_dyn_smem[];
+
 // ---------------------------------------------------------------------------
 // FP64 field: trilinear on the periodic vertex-centred grid (nested lerps in
 // x, then y, then z), plus the analytic galactic part when enabled.
@@ -575,11 +579,13 @@ static __constant__ float c_a32[6][6] = {
 struct PolicyFP64 {
   using Real = double;
   static constexpr bool kSharedStages = true;
+  static constexpr size_t kSmemPerThread = kStageSlots * sizeof(double);
   struct Lane : LaneCore {
     double u[3];
     double cap_s, kappa, eps;
     double y5[6];
   };
+  __device__ __forceinline__ static void init_lane(Lane&) {}
 
   __device__ __forceinline__ static void load(const KParams& p, const DevState& st, uint32_t i,
                                               Lane& c) {
@@ -759,6 +765,9 @@ template <bool GAL>
 struct PolicyMixedT {
   using Real = float;
   static constexpr bool kSharedStages = false;
+  // per-lane cache of the last cell record gathered (6 float4, lane-interleaved)
+  static constexpr int kCacheF4 = 6;
+  static constexpr size_t kSmemPerThread = kCacheF4 * sizeof(float4);
   struct LaneGal {
     float gal[3];  // position relative to the galactic centre
   };
@@ -773,7 +782,10 @@ struct PolicyMixedT {
     float kap, d_obs, d_bord, err2, dx[3], u5[3];
     float3 k1;      // force at the start of the step
     int cap, since_rebase;
+    uint32_t cell_key;  // index of the cell record held in this lane's cache
   };
+
+  __device__ __forceinline__ static void init_lane(Lane& c) { c.cell_key = 0xffffffffu; }
 
   // Cell and fraction from the binary64 position (exact rebase).
   __device__ __forceinline__ static void rebase(const KParams& p, Lane& c) {
@@ -829,7 +841,7 @@ struct PolicyMixedT {
 
   // Field at the current position plus offset (ox, oy, oz) (length unit).
   template <class NodeT>
-  __device__ __forceinline__ static float3 field(const KParams& p, const Lane& c, float ox,
+  __device__ __forceinline__ static float3 field(const KParams& p, Lane& c, float ox,
                                                  float oy, float oz) {
     const FieldView& f = p.f;
     const float rx = fmaf(ox, f.inv_spacing_f, c.frac[0]);
@@ -845,9 +857,36 @@ struct PolicyMixedT {
     if (std::is_same<NodeT, float4>::value && f.cells) {
       // one aligned 128-byte record: the cell's trilinear polynomial,
       // evaluated in Horner form (7 FMAs per component)
-      const float4* r = f.cells + 8 * (((size_t)iz0 * ny + (size_t)iy0) * nx + (size_t)ix0);
-      const float4 a0 = __ldg(r), a1 = __ldg(r + 1), a2 = __ldg(r + 2);
-      const float4 a3 = __ldg(r + 3), a4 = __ldg(r + 4), a5 = __ldg(r + 5);
+      const size_t cell = ((size_t)iz0 * ny + (size_t)iy0) * nx + (size_t)ix0;
+      float4 a0, a1, a2, a3, a4, a5;
+      // consecutive stages and steps mostly stay in one cell: re-read the
+      // record from this lane's shared-memory copy (conflict-free, 4
+      // wavefronts per warp load) instead of a 32-line global gather
+      float4* cache = reinterpret_cast<float4*>(crp_dyn_smem) + threadIdx.x;
+      const int bs = blockDim.x;
+      if ((uint32_t)cell != c.cell_key || !f.cache_ok) {
+        const float4* r = f.cells + 8 * cell;
+        a0 = __ldg(r);
+        a1 = __ldg(r + 1);
+        a2 = __ldg(r + 2);
+        a3 = __ldg(r + 3);
+        a4 = __ldg(r + 4);
+        a5 = __ldg(r + 5);
+        cache[0] = a0;
+        cache[bs] = a1;
+        cache[2 * bs] = a2;
+        cache[3 * bs] = a3;
+        cache[4 * bs] = a4;
+        cache[5 * bs] = a5;
+        c.cell_key = (uint32_t)cell;
+      } else {
+        a0 = cache[0];
+        a1 = cache[bs];
+        a2 = cache[2 * bs];
+        a3 = cache[3 * bs];
+        a4 = cache[4 * bs];
+        a5 = cache[5 * bs];
+      }
       // coefficient j of component d is float 3j + d of the record
       auto horner = [&](float c0, float c1, float c2, float c3, float c4, float c5, float c6,
                         float c7) {
@@ -1124,6 +1163,7 @@ __global__ void __launch_bounds__(Bounds<Policy>::kThreads, MINB)
   const unsigned long long t0 = globaltimer_ns();
   const uint64_t n_in = p.n_in_dev ? *p.n_in_dev : p.n_in;
   Lane c;
+  Policy::init_lane(c);
   LaneCounters lc = {0, 0, 0, 0};
   bool has = false, exhausted = false, in_step = false;
   uint32_t slice_steps = 0;
@@ -1222,16 +1262,24 @@ __global__ void __launch_bounds__(Bounds<Policy>::kThreads, MINB)
 
 template <class Policy>
 size_t smem_bytes(int block) {
-  return Policy::kSharedStages ? (size_t)kStageSlots * (size_t)block * sizeof(typename Policy::Real)
-                               : 0;
+  return Policy::kSmemPerThread * (size_t)block;
 }
 
 template <class Policy, int MINB>
 cudaError_t launch_policy(const KParams& kp, const DevState& st, DevCounters* dc, int grid,
                           int block, cudaStream_t s) {
   const size_t sm = smem_bytes<Policy>(block);
-  // without shared stage storage, give the whole unified L1 to the gathers
-  const int carveout = sm ? -1 : 0;
+  // shared memory for MINB resident blocks (plus the 1 KB the system
+  // reserves per block); the rest of the unified L1 caches the gathers
+  int dev = 0, max_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  int carveout = -1;  // binary64 stages: driver default
+  if (!Policy::kSharedStages && max_sm > 0) {
+    const size_t need = (size_t)MINB * (sm + 1024);
+    carveout = (int)((100 * need + max_sm - 1) / max_sm);
+    if (carveout > 100) carveout = 100;
+  }
   if (kp.f.dtype == CRP_F32) {
     auto k = propagate_kernel<Policy, float4, MINB>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -33,6 +33,7 @@ __global__ void k_sample_mixed(const KParams p, const double* xyz, int64_t n, do
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     typename Policy::Lane c;
+    Policy::init_lane(c);
     c.x[0] = xyz[3 * i];
     c.x[1] = xyz[3 * i + 1];
     c.x[2] = xyz[3 * i + 2];
@@ -49,10 +50,11 @@ cudaError_t sample_policy(const KParams& kp, const double* xyz, int64_t n, doubl
                           cudaStream_t s) {
   const int64_t g64 = (n + 255) / 256;
   const unsigned g = (unsigned)(g64 < 1 ? 1 : (g64 > 65535 ? 65535 : g64));
+  const size_t sm = Policy::kSmemPerThread * 256;
   if (kp.f.dtype == CRP_F32)
-    k_sample_mixed<Policy, float4><<<g, 256, 0, s>>>(kp, xyz, n, B);
+    k_sample_mixed<Policy, float4><<<g, 256, sm, s>>>(kp, xyz, n, B);
   else
-    k_sample_mixed<Policy, DNode><<<g, 256, 0, s>>>(kp, xyz, n, B);
+    k_sample_mixed<Policy, DNode><<<g, 256, sm, s>>>(kp, xyz, n, B);
   return cudaGetLastError();
 }
 }  // namespace
