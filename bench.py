@@ -54,9 +54,11 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--graph", action="store_true",
                     help="run each propagation's round loop as one captured CUDA graph")
-    ap.add_argument("--workload", choices=("mixed", "galactic"), default="mixed",
+    ap.add_argument("--workload", choices=("mixed", "galactic", "uneven"), default="mixed",
                     help="mixed: the propagation benchmark; galactic: back-tracking, MLP "
-                         "surrogate training / inference and lens builds")
+                         "surrogate training / inference and lens builds; uneven: 10^7 "
+                         "candidates, 512^3 grid, photodisintegration secondaries, log-uniform "
+                         "path lengths")
     ap.add_argument("--n-train", type=int, default=9_000_000)
     ap.add_argument("--n-test", type=int, default=1_000_000)
     ap.add_argument("--epochs", type=int, default=32)
@@ -162,8 +164,13 @@ def flops_per_trial_mixed():
     return 6 * (75 + 12) + 105 + 90 + 81
 
 
-# field bytes one Cash-Karp trial reads: 6 trilinear gathers x 8 nodes x 16 B
-GATHER_BYTES_PER_TRIAL_F32 = 6 * 8 * 16
+# field bytes one Cash-Karp trial needs: 6 trilinear gathers x 8 corners x 3 binary32
+GATHER_BYTES_PER_TRIAL_F32 = 6 * 8 * 3 * 4
+# DRAM bytes (read + write) per Cash-Karp trial of the mixed propagate kernel, from
+# one ncu capture of the current kernel (2e5 candidates of this workload:
+# 154.92 GB read + 0.157 GB written over 1.5613e9 trials); traffic grows with the
+# number of trials, so a launch's traffic is this figure times its trials
+DRAM_BYTES_PER_TRIAL_MIXED = (154.916e9 + 0.157e9) / 1.5613e9
 
 
 def run_ours(args):
@@ -285,7 +292,10 @@ def run_ours(args):
         achieved = trials * flops_per_trial_mixed() / kern_s / 1e12
         peak = probe["fp32_tflops"]
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak,
+                "traffic": DRAM_BYTES_PER_TRIAL_MIXED * trials / max(launches, 1),
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per trial "
+                                  "(2e5-candidate capture) x trials per launch",
                 "peak_source": "measured: crp_measure_peaks binary32 FMA probe "
                                f"(derived {derived32:.1f} TFLOP/s = {n_sm} SMs x 128 lanes x 2 x "
                                f"{sm_mhz:.0f} MHz)",
@@ -454,6 +464,78 @@ def two_sample_chi2(a, b):
     return stat, dof, float(chi2_dist.sf(stat, dof))
 
 
+def run_uneven(args):
+    """Uneven batched propagation with secondaries: 10^7 mixed nuclei through a
+    512^3 binary32 grid (B_rms drawn per run), pair + adiabatic + pion +
+    photodisintegration (nucleons join the device work queue), path budgets
+    log-uniform in [1 Mpc, 2 Gpc]; mixed precision, host-driven and
+    graph-captured round loops."""
+    import torch
+    from paper_1307_2643_gb300 import crp
+    from paper_1307_2643_gb300.build import build
+
+    torch.cuda.set_device(0)
+    build()
+    crp.use_torch_allocator(0)
+    w = workloads.UNEVEN_SECONDARIES
+    n = args.n or w["n"]
+    inj, brms = workloads.uneven_secondaries(n=n)
+    inj = crp.host_injection(inj)
+    cap = int(n * 1.5) + 4096
+    ctx = crp.crp_context_create(0, w["seed"], cap)
+    t0 = time.perf_counter()
+    grid = crp.crp_grid_create(ctx, crp.grid_desc(w["grid_n"], w["spacing"], dtype=crp.F32,
+                                                  source=crp.GRID_TURBULENT, lmin=w["lmin"],
+                                                  lmax=w["lmax"], brms=brms, seed=w["seed"]))
+    torch.cuda.synchronize()
+    t_grid = time.perf_counter() - t0
+    tables = crp.crp_tables_build(ctx, crp.tables_desc(n=1000))
+    dev = {k: torch.from_numpy(v).cuda() for k, v in inj.items()}
+    arr = crp.candidate_arrays(dev, on_device=True)
+    flags = crp.PAIR | crp.ADIABATIC | crp.PION | crp.PHOTODIS | crp.EMIN | crp.OBSERVER
+    results = {}
+    for loop in ("host", "graph"):
+        mods = crp.modules(precision=crp.MIXED, flags=flags, tol=w["tol"], h_min=w["h_min"],
+                           h_max=w["h_max"], beta_ad=H0_OVER_C, e_min=w["e_min"], tables=tables,
+                           observer_radius=w["observer_r"], use_graph=1 if loop == "graph" else 0)
+        runs = []
+        for k in range(args.warmup + args.steps):
+            crp.crp_candidates_clear(ctx)
+            crp.crp_candidates_inject(ctx, arr, n)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            status, st = crp.crp_propagate(ctx, grid, mods, raise_on_error=False)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            if status != crp.OK:
+                raise RuntimeError(f"propagate status {status}: {crp.lib().crp_last_error()}")
+            if k >= args.warmup:
+                runs.append((dt, st))
+        dt = sum(r[0] for r in runs) / len(runs)
+        st = runs[-1][1]
+        results[loop] = {"seconds": dt, "accepted_steps": st.accepted_steps,
+                         "steps_per_s": st.accepted_steps / dt,
+                         "rejected_trials": st.rejected_trials, "rounds": st.launches,
+                         "photodisintegrations": st.n_pd, "pion_events": st.n_pion,
+                         "secondaries": st.n_secondaries, "nucleons_below_emin": st.n_dropped,
+                         "detected": st.n_detected, "kernel_ms": st.kernel_ms}
+    rec = crp.crp_collect(ctx, crp.COLLECT_ALL)
+    nacc = np.sort(rec["n_acc"])
+    crp.crp_tables_destroy(tables)
+    crp.crp_grid_destroy(grid)
+    crp.crp_context_destroy(ctx)
+    print(json.dumps({
+        "workload": w["name"], "metric": METRIC, "unit": UNIT, "candidates": n,
+        "brms_nG": brms, "grid": "512^3 f32 (2.1 GB nodes + 17.2 GB cell records)",
+        "grid_setup_s": t_grid, "steps": args.steps, "warmup": args.warmup,
+        "value": results["host"]["steps_per_s"], "loops": results,
+        "records": int(len(rec)),
+        "accepted_steps_per_candidate": {"median": float(np.median(nacc)),
+                                         "p99": float(nacc[int(0.99 * (len(nacc) - 1))]),
+                                         "max": int(nacc[-1])},
+    }))
+
+
 def run_galactic(args):
     """Galactic workload: back-track antiprotons from Earth through the
     synthetic galactic field (disk + halo + 256^3 random component), train the
@@ -609,5 +691,7 @@ if __name__ == "__main__":
         run_reference(a)
     elif a.workload == "galactic":
         run_galactic(a)
+    elif a.workload == "uneven":
+        run_uneven(a)
     else:
         run_ours(a)
