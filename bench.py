@@ -54,11 +54,12 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--graph", action="store_true",
                     help="run each propagation's round loop as one captured CUDA graph")
-    ap.add_argument("--workload", choices=("mixed", "galactic", "uneven"), default="mixed",
+    ap.add_argument("--workload", choices=("mixed", "galactic", "uneven", "e2e"), default="mixed",
                     help="mixed: the propagation benchmark; galactic: back-tracking, MLP "
                          "surrogate training / inference and lens builds; uneven: 10^7 "
                          "candidates, 512^3 grid, photodisintegration secondaries, log-uniform "
-                         "path lengths")
+                         "path lengths; e2e: 10^8 candidates through the mixed workload's "
+                         "field, then the galactic lens and its surrogate")
     ap.add_argument("--n-train", type=int, default=9_000_000)
     ap.add_argument("--n-test", type=int, default=1_000_000)
     ap.add_argument("--epochs", type=int, default=32)
@@ -536,11 +537,13 @@ def run_uneven(args):
     }))
 
 
-def run_galactic(args):
+def run_galactic(args, keep=False):
     """Galactic workload: back-track antiprotons from Earth through the
     synthetic galactic field (disk + halo + 256^3 random component), train the
     BF16 MLP surrogate on the border directions, and build the nside-64,
-    100-bin lens by back-tracking and by the surrogate."""
+    100-bin lens by back-tracking and by the surrogate.  With keep=True the
+    lenses (and the context that owns them) are returned for further use
+    instead of printed and released."""
     import torch
     from paper_1307_2643_gb300 import crp
     from paper_1307_2643_gb300.build import build
@@ -655,18 +658,13 @@ def run_galactic(args):
     ca, cb = coarse_ring_map(a, w["nside"]), coarse_ring_map(b, w["nside"])
     chi2, dof, pval = two_sample_chi2(ca, cb)
     corr = float(np.corrcoef(ca, cb)[0, 1])
-    for lens in (lens_bt, lens_sg):
-        crp.crp_lens_destroy(lens)
-    crp.crp_mlp_destroy(mlp)
-    crp.crp_grid_destroy(grid)
-    crp.crp_context_destroy(ctx)
-    print(json.dumps({
+    summary = {
         "workload": w["name"], "metric": "galactic back-tracking and lens surrogate",
         "backtrack": {"candidates": n_all, "accepted_steps": st.accepted_steps,
                       "rejected_trials": st.rejected_trials, "seconds": t_bt,
                       "steps_per_s": st.accepted_steps / t_bt,
                       "at_border_fraction": float(ok.mean()), "precision": "mixed"},
-        "mlp": {"train_samples": int(len(tr)), "epochs": args.epochs, "batch": B, "steps": steps,
+        "mlp": {"train_samples": int(n_batches * B), "epochs": args.epochs, "batch": B, "steps": steps,
                 "train_seconds": t_train, "train_samples_per_s": steps * B / t_train,
                 "loss_per_epoch": losses, "test_samples": n_te,
                 "median_angle_deg": float(np.median(ang)),
@@ -682,7 +680,95 @@ def run_galactic(args):
                  "map_correlation": corr,
                  "observed_fraction": {"backtracked": float(a.sum() / m),
                                        "surrogate": float(b.sum() / m)}},
-    }))
+    }
+    if keep:
+        return dict(ctx=ctx, grid=grid, mlp=mlp, lens_bt=lens_bt, lens_sg=lens_sg,
+                    summary=summary, t_lens_bt=t_lens_bt, t_lens_sg=t_lens_sg)
+    for lens in (lens_bt, lens_sg):
+        crp.crp_lens_destroy(lens)
+    crp.crp_mlp_destroy(mlp)
+    crp.crp_grid_destroy(grid)
+    crp.crp_context_destroy(ctx)
+    print(json.dumps(summary))
+
+
+def run_e2e(args):
+    """End to end at scale: 10^8 candidates of the mixed workload's
+    composition propagated through its 256^3 field to the observer sphere,
+    then mapped to Earth through the galactic lens built by back-tracking and
+    through the lens built from the trained surrogate; arrival maps, observed
+    spectra (two-sample KS) and the throughput of each path."""
+    import torch
+    from scipy.stats import ks_2samp
+    from paper_1307_2643_gb300 import crp
+
+    gal = run_galactic(args, keep=True)
+    w = workloads.MIXED_INTERACTIONS
+    n = args.n or 100_000_000
+    chunk = 10_000_000
+    ctx = crp.crp_context_create(0, w["seed"], n + 4096)
+    grid = crp.crp_grid_create(ctx, crp.grid_desc(w["grid_n"], w["spacing"], dtype=crp.F32,
+                                                  source=crp.GRID_TURBULENT, lmin=w["lmin"],
+                                                  lmax=w["lmax"], brms=w["brms"], seed=w["seed"]))
+    tables = crp.crp_tables_build(ctx, crp.tables_desc(n=1000))
+    t0 = time.perf_counter()
+    for k in range(0, n, chunk):
+        m = min(chunk, n - k)
+        inj = workloads.mixed_interactions(n=m, seed=w["seed"] + 1000 + k // chunk)
+        inj["id"] = inj["id"] + np.uint64(k)
+        inj = crp.host_injection(inj)
+        crp.crp_candidates_inject(ctx, crp.candidate_arrays(inj), m)
+    torch.cuda.synchronize()
+    t_inject = time.perf_counter() - t0
+    mods = modules_for(crp, crp.MIXED, tables)
+    t0 = time.perf_counter()
+    _, st = crp.crp_propagate(ctx, grid, mods)
+    torch.cuda.synchronize()
+    t_prop = time.perf_counter() - t0
+    nside = workloads.GALACTIC_LENS["nside"]
+    sky = crp.crp_histogram_healpix(ctx, crp.COLLECT_DETECTED, nside, 0).astype(np.float64)
+    paths = {}
+    for name in ("backtracked", "surrogate"):
+        lens = gal["lens_bt"] if name == "backtracked" else gal["lens_sg"]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        crp.crp_lens_apply(ctx, lens, crp.COLLECT_DETECTED)
+        torch.cuda.synchronize()
+        t_apply = time.perf_counter() - t0
+        hist = crp.crp_histogram_healpix(ctx, crp.COLLECT_DETECTED, nside, 1).astype(np.float64)
+        rec = crp.crp_collect(ctx, crp.COLLECT_DETECTED)
+        seen = rec["lens_pixel"] < 12 * nside * nside
+        paths[name] = dict(hist=hist, E=rec["E"][seen], t_apply=t_apply,
+                           observed=int(seen.sum()), detected=int(len(rec)))
+    a, b = paths["backtracked"], paths["surrogate"]
+    ca, cb = coarse_ring_map(a["hist"], nside), coarse_ring_map(b["hist"], nside)
+    chi2, dof, pval = two_sample_chi2(ca, cb)
+    ks = ks_2samp(a["E"], b["E"])
+    summary = {
+        "workload": "e2e_1e8_mixed_256cube_then_galactic_lens",
+        "metric": "end-to-end propagation + lens (plain vs surrogate)",
+        "extragalactic": {"candidates": n, "inject_s": t_inject, "seconds": t_prop,
+                          "accepted_steps": st.accepted_steps,
+                          "steps_per_s": st.accepted_steps / t_prop,
+                          "detected": int(st.n_detected), "pion_events": int(st.n_pion)},
+        "lens_build_s": {"backtracked": gal["t_lens_bt"], "surrogate": gal["t_lens_sg"]},
+        "lens_apply_s": {"backtracked": a["t_apply"], "surrogate": b["t_apply"]},
+        "observed_at_earth": {"backtracked": a["observed"], "surrogate": b["observed"]},
+        "arrival_map": {"cells": int(len(ca)), "chi2": chi2, "dof": dof, "p": pval,
+                        "correlation": float(np.corrcoef(ca, cb)[0, 1]),
+                        "sky_before_lens_events": float(sky.sum())},
+        "spectrum_ks": {"statistic": float(ks.statistic), "p": float(ks.pvalue)},
+        "galactic": gal["summary"],
+    }
+    crp.crp_tables_destroy(tables)
+    crp.crp_grid_destroy(grid)
+    crp.crp_context_destroy(ctx)
+    for lens in (gal["lens_bt"], gal["lens_sg"]):
+        crp.crp_lens_destroy(lens)
+    crp.crp_mlp_destroy(gal["mlp"])
+    crp.crp_grid_destroy(gal["grid"])
+    crp.crp_context_destroy(gal["ctx"])
+    print(json.dumps(summary))
 
 
 if __name__ == "__main__":
@@ -693,5 +779,7 @@ if __name__ == "__main__":
         run_galactic(a)
     elif a.workload == "uneven":
         run_uneven(a)
+    elif a.workload == "e2e":
+        run_e2e(a)
     else:
         run_ours(a)
