@@ -608,12 +608,19 @@ def run_galactic(args, keep=False):
     n_te = (len(te) // 128) * 128
     xt = torch.from_numpy(x_all[te[:n_te]]).cuda()
     yt = torch.zeros((n_te, 3), dtype=torch.float32, device="cuda")
-    crp.crp_mlp_forward(mlp, xt, yt, n_te)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    crp.crp_mlp_forward(mlp, xt, yt, n_te)
-    torch.cuda.synchronize()
-    t_inf = time.perf_counter() - t0
+    # inference throughput of both forward kernels (fused tensor-core, layered GEMMs)
+    t_paths = {}
+    for path, name in ((crp.MLP_PATH_LAYERED, "layered_mma_sync"),
+                       (crp.MLP_PATH_AUTO, "fused_tcgen05")):
+        crp.crp_mlp_set_forward_path(mlp, path)
+        crp.crp_mlp_forward(mlp, xt, yt, n_te)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(5):
+            crp.crp_mlp_forward(mlp, xt, yt, n_te)
+        torch.cuda.synchronize()
+        t_paths[name] = (time.perf_counter() - t0) / 5
+    t_inf = t_paths["fused_tcgen05"]
     yh = yt.cpu().numpy().astype(np.float64)
     tt = t_all[te[:n_te]].astype(np.float64)
     cosang = np.sum(yh * tt, axis=1) / (np.linalg.norm(yh, axis=1) * np.linalg.norm(tt, axis=1))
@@ -671,7 +678,10 @@ def run_galactic(args, keep=False):
                 "p90_angle_deg": float(np.percentile(ang, 90)),
                 "median_angle_deg_no_lens": float(np.median(ident)),
                 "median_angle_deg_by_log10R_net_vs_no_lens": by_q,
-                "inference_samples_per_s": n_te / t_inf},
+                "inference_samples_per_s": n_te / t_inf,
+                "inference_samples_per_s_by_kernel": {k: n_te / v for k, v in t_paths.items()},
+                "inference_tflops_by_kernel": {k: n_te * 2 * (4 * 256 + 3 * 256 * 256 + 256 * 3)
+                                               / v / 1e12 for k, v in t_paths.items()}},
         "lens": {"nside": w["nside"], "n_bins": w["n_bins"], "samples": int(len(lE)),
                  "build_backtrack_s": t_lens_bt, "build_surrogate_s": t_lens_sg,
                  "backtrack_steps": lst.accepted_steps, "apply_s": {k: maps[k + "_apply_s"]

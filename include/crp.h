@@ -373,8 +373,20 @@ int64_t crp_mlp_num_params(const crp_mlp* mlp);
 crp_status crp_mlp_set_params(crp_mlp* mlp, const float* params);
 /* either pointer may be NULL; grad is the last train step's gradient */
 crp_status crp_mlp_get_params(const crp_mlp* mlp, float* params, float* grad);
-/* device pointers; n a multiple of 128; y_hat [n][3] */
+/* device pointers; n a multiple of 128; y_hat [n][3].  With hidden = 256 and
+ * n_in <= 8 the default path is one fused kernel on the fifth-generation
+ * tensor cores (tcgen05 MMAs into TMEM, activations kept on chip; it
+ * synchronises the stream to read its completion flag and returns CRP_E_CUDA
+ * if a tensor-core wait timed out); otherwise, or when selected, one
+ * warp-level BF16 GEMM per hidden layer.  Both keep activations in bf16 and
+ * accumulate in FP32. */
 crp_status crp_mlp_forward(crp_mlp* mlp, const float* x, float* y_hat, int64_t n, void* stream);
+
+#define CRP_MLP_PATH_AUTO 0                /* fused tensor-core kernel when supported */
+#define CRP_MLP_PATH_TENSOR_CORE_FUSED 1   /* require it (CRP_E_INVALID if unsupported) */
+#define CRP_MLP_PATH_LAYERED 2             /* one GEMM launch per hidden layer */
+/* Forward kernel selection of crp_mlp_forward (training always runs layered). */
+crp_status crp_mlp_set_forward_path(crp_mlp* mlp, int32_t path);
 /* one Adam step on a batch (device x [n][n_in], t [n][3] unit targets; n a
  * multiple of 128); lr = 0 computes the gradient only; loss_out (host, may
  * be NULL) receives the batch loss and synchronises the stream */

@@ -26,6 +26,7 @@ UNITS = {
     "hist_noalloc.cu": [],
     "lens.cu": [],
     "mlp.cu": [],
+    "mlp_tc.cu": [],
     "peaks.cu": [],
 }
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -134,6 +134,7 @@ SYMBOLS = (
     "crp_mlp_create", "crp_mlp_destroy", "crp_mlp_num_params", "crp_mlp_set_params",
     "crp_mlp_get_params", "crp_mlp_forward", "crp_mlp_train_step", "crp_lens_build_surrogate",
     "crp_checkpoint", "crp_restore", "crp_measure_peaks", "crp_autotune", "crp_grid_sample",
+    "crp_mlp_set_forward_path",
 )
 
 _lock = threading.Lock()
@@ -189,6 +190,7 @@ def lib():
             L.crp_restore.argtypes = [p, p, sz, p]
             L.crp_measure_peaks.argtypes = [i32, C.POINTER(Peaks)]
             L.crp_grid_sample.argtypes = [p, C.POINTER(Modules), C.c_int64, p, p]
+            L.crp_mlp_set_forward_path.argtypes = [p, i32]
             L.crp_autotune.argtypes = [p, p, C.POINTER(Modules), u64, C.POINTER(TuneResult), p]
             for name in SYMBOLS:
                 if name not in ("crp_last_error", "crp_version"):
@@ -443,6 +445,13 @@ def crp_mlp_get_params(mlp):
 def crp_mlp_forward(mlp, x_dev, y_dev, n, stream=None):
     """x_dev, y_dev: torch float32 device tensors [n, n_in], [n, 3]."""
     _check(lib().crp_mlp_forward(mlp, _addr(x_dev), _addr(y_dev), n, stream))
+
+
+MLP_PATH_AUTO, MLP_PATH_TENSOR_CORE_FUSED, MLP_PATH_LAYERED = 0, 1, 2
+
+
+def crp_mlp_set_forward_path(mlp, path):
+    _check(lib().crp_mlp_set_forward_path(mlp, path))
 
 
 def crp_mlp_train_step(mlp, x_dev, t_dev, n, lr, stream=None, want_loss=True):

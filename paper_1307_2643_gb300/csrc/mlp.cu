@@ -24,6 +24,7 @@
 
 #include "crp_internal.cuh"
 #include "device_common.cuh"
+#include "mlp_tc.h"
 
 namespace crp {
 void context_pool(const crp_context* c, DevState* st, uint64_t* n, int* device, uint64_t* seed);
@@ -42,6 +43,10 @@ struct crp_mlp {
   float* v;
   int64_t step;
   std::vector<__nv_bfloat16*> wb, wbt;  // bf16 copies of hidden layers' W and W^T
+  std::vector<__nv_bfloat16*> wimg;     // bf16 core-matrix images for the tcgen05 forward
+  unsigned* tc_err;                     // tcgen05 forward: wait-timeout flag
+  int forward_path;                     // CRP_MLP_PATH_*
+  int sm_count;
   // batch workspace
   int64_t cap;
   std::vector<__nv_bfloat16*> h;  // activations of each hidden layer [cap][hidden]
@@ -292,9 +297,11 @@ __global__ void k_adam(float* p, const float* g, float* m, float* v, int64_t n, 
   }
 }
 
-// bf16 copies W (hidden x hidden) and W^T of a hidden layer.
+// bf16 copies W (hidden x hidden) and W^T of a hidden layer, and (when img
+// is given) W in the tensor-core operand image of the fused forward kernel:
+// element (o, i) at (o / 8) * (8 n) + (i / 8) * 64 + (o % 8) * 8 + i % 8.
 __global__ void k_to_bf16_pair(const float* __restrict__ W, int n, __nv_bfloat16* __restrict__ wb,
-                               __nv_bfloat16* __restrict__ wbt) {
+                               __nv_bfloat16* __restrict__ wbt, __nv_bfloat16* __restrict__ img) {
   const int64_t total = (int64_t)n * n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -302,6 +309,7 @@ __global__ void k_to_bf16_pair(const float* __restrict__ W, int n, __nv_bfloat16
     const __nv_bfloat16 v = __float2bfloat16_rn(W[e]);
     wb[e] = v;
     wbt[(int64_t)i * n + o] = v;
+    if (img) img[(int64_t)(o >> 3) * (8 * n) + (i >> 3) * 64 + (o & 7) * 8 + (i & 7)] = v;
   }
 }
 
@@ -371,7 +379,8 @@ crp_status ensure_ws(crp_mlp* M, int64_t n) {
 crp_status refresh_bf16(crp_mlp* M, cudaStream_t s) {
   for (int l = 1; l < M->n_hidden; ++l)
     k_to_bf16_pair<<<nblk((int64_t)M->hidden * M->hidden, 256), 256, 0, s>>>(
-        M->params + M->w_off[l], M->hidden, M->wb[l], M->wbt[l]);
+        M->params + M->w_off[l], M->hidden, M->wb[l], M->wbt[l],
+        M->wimg.empty() ? nullptr : M->wimg[l]);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? CRP_OK : fail_cuda(e, "mlp: bf16 weights");
 }
@@ -463,6 +472,9 @@ crp_status crp_mlp_create(crp_context* ctx, int32_t n_in, int32_t hidden, int32_
   M->cap = 0;
   M->dz = M->dz2 = M->dzt = M->ht = nullptr;
   M->y = M->dy = M->loss = nullptr;
+  M->tc_err = nullptr;
+  M->forward_path = CRP_MLP_PATH_AUTO;
+  M->sm_count = 0;
   {
     DevState unused;
     uint64_t n_unused = 0, seed_unused = 0;
@@ -494,10 +506,23 @@ crp_status crp_mlp_create(crp_context* ctx, int32_t n_in, int32_t hidden, int32_
   M->wb.assign(n_hidden, nullptr);
   M->wbt.assign(n_hidden, nullptr);
   bool ok = M->params && M->grad && M->m && M->v;
+  M->forward_path = CRP_MLP_PATH_AUTO;
+  cudaDeviceGetAttribute(&M->sm_count, cudaDevAttrMultiProcessorCount, M->device);
+  const bool tc = mlp_tc_supported(n_in, hidden, n_hidden, 3);
+  if (tc) {
+    M->wimg.assign(n_hidden, nullptr);
+    M->tc_err = static_cast<unsigned*>(dev_alloc(sizeof(unsigned)));
+    ok = ok && M->tc_err;
+    if (M->tc_err) cudaMemset(M->tc_err, 0, sizeof(unsigned));
+  }
   for (int l = 1; l < n_hidden; ++l) {
     M->wb[l] = static_cast<__nv_bfloat16*>(dev_alloc(sizeof(__nv_bfloat16) * hidden * hidden));
     M->wbt[l] = static_cast<__nv_bfloat16*>(dev_alloc(sizeof(__nv_bfloat16) * hidden * hidden));
     ok = ok && M->wb[l] && M->wbt[l];
+    if (tc) {
+      M->wimg[l] = static_cast<__nv_bfloat16*>(dev_alloc(sizeof(__nv_bfloat16) * hidden * hidden));
+      ok = ok && M->wimg[l];
+    }
   }
   int64_t* d_off = static_cast<int64_t*>(dev_alloc(sizeof(int64_t) * offs.size()));
   int* d_fan = static_cast<int*>(dev_alloc(sizeof(int) * fan.size()));
@@ -538,6 +563,8 @@ crp_status crp_mlp_destroy(crp_mlp* M) {
   dev_free(M->v);
   for (auto* p : M->wb) dev_free(p);
   for (auto* p : M->wbt) dev_free(p);
+  for (auto* p : M->wimg) dev_free(p);
+  dev_free(M->tc_err);
   delete M;
   return CRP_OK;
 }
@@ -582,6 +609,41 @@ crp_status crp_mlp_forward(crp_mlp* M, const float* x, float* y_hat, int64_t n, 
     return CRP_E_INVALID;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool tc_ok = !M->wimg.empty();
+  if (M->forward_path == CRP_MLP_PATH_TENSOR_CORE_FUSED && !tc_ok) {
+    set_error("crp_mlp_forward: the fused tensor-core path needs hidden = 256, n_in <= 8");
+    return CRP_E_INVALID;
+  }
+  if (tc_ok && M->forward_path != CRP_MLP_PATH_LAYERED) {
+    MlpTcParams P;
+    memset(&P, 0, sizeof(P));
+    P.x = x;
+    P.n_in = M->n_in;
+    P.n_gemm = M->n_hidden - 1;
+    P.n_tiles = n / 128;
+    P.W1 = M->params + M->w_off[0];
+    P.b1 = M->params + M->b_off[0];
+    for (int l = 1; l < M->n_hidden; ++l) {
+      P.Wimg[l - 1] = M->wimg[l];
+      P.bh[l - 1] = M->params + M->b_off[l];
+    }
+    P.Wout = M->params + M->w_off[M->n_hidden];
+    P.bout = M->params + M->b_off[M->n_hidden];
+    P.y = y_hat;
+    P.err = M->tc_err;
+    cudaError_t e = mlp_forward_tc(P, M->sm_count, s);
+    unsigned err = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, M->tc_err, sizeof(unsigned),
+                                              cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_cuda(e, "crp_mlp_forward: tensor-core forward");
+    if (err) {
+      cudaMemsetAsync(M->tc_err, 0, sizeof(unsigned), s);
+      set_error("crp_mlp_forward: a tensor-core completion wait timed out");
+      return CRP_E_CUDA;
+    }
+    return CRP_OK;
+  }
   const int64_t chunk = n < (1 << 20) ? n : (1 << 20);  // bounds the activation workspace
   crp_status st = ensure_ws(M, chunk);
   for (int64_t r0 = 0; st == CRP_OK && r0 < n; r0 += chunk) {
@@ -589,6 +651,19 @@ crp_status crp_mlp_forward(crp_mlp* M, const float* x, float* y_hat, int64_t n, 
     st = forward(M, x + r0 * M->n_in, m, nullptr, y_hat + r0 * 3, s);
   }
   return st;
+}
+
+crp_status crp_mlp_set_forward_path(crp_mlp* M, int32_t path) {
+  if (!M || path < CRP_MLP_PATH_AUTO || path > CRP_MLP_PATH_LAYERED) {
+    set_error("crp_mlp_set_forward_path: bad argument");
+    return CRP_E_INVALID;
+  }
+  if (path == CRP_MLP_PATH_TENSOR_CORE_FUSED && M->wimg.empty()) {
+    set_error("crp_mlp_set_forward_path: the fused tensor-core path needs hidden = 256, n_in <= 8");
+    return CRP_E_INVALID;
+  }
+  M->forward_path = path;
+  return CRP_OK;
 }
 
 crp_status crp_mlp_train_step(crp_mlp* M, const float* x, const float* t, int64_t n, float lr,

@@ -1,0 +1,307 @@
+// mlp_tc.cu -- fused forward pass of the MLP lens surrogate on the
+// fifth-generation tensor cores (tcgen05, TMEM accumulators).
+//
+// One CTA (two warpgroups, 256 threads) per tile of 128 samples, persistent
+// over tiles; thread t owns row t % 128 and, in the CUDA-core phases, the
+// columns of half t / 128.  The activations of a tile never leave the SM:
+//   * input layer (K = n_in, FP32 on the CUDA cores) -> bf16 tile A in shared
+//     memory (128 x 256, K-major core-matrix layout, 64 KB);
+//   * each hidden 256 -> 256 layer: its bf16 weights (already stored in the
+//     same core-matrix layout in global memory, 128 KB) are copied into
+//     shared tile B; one thread issues 16 tcgen05.mma (M 128, N 256, K 16,
+//     bf16 x bf16 -> FP32) into 256 TMEM columns and commits them to an
+//     mbarrier; every warp then reads its 32 TMEM lanes (rows) with
+//     tcgen05.ld, adds the bias, applies ReLU and writes the bf16 result back
+//     into tile A as the next layer's operand;
+//   * the last hidden layer's epilogue feeds the thin output layer (N = 3,
+//     FP32) and the normalisation directly.
+// Shared-memory operand layout (no swizzle, K-major): 8 x 8 bf16 core
+// matrices of 128 contiguous bytes (row r of the core matrix at 16 r); the
+// core matrix of rows 8g.. and columns 8j.. sits at g * SBO + j * LBO with
+// LBO = 128 B (next 8 columns, the K direction) and SBO = 4096 B (next 8
+// rows): row-group-major, so element (r, k) is at
+// (r / 8) * 4096 + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "crp_internal.cuh"
+#include "mlp_tc.h"
+
+namespace crp {
+namespace {
+
+constexpr int kRows = 128;     // samples per tile (MMA M)
+constexpr int kH = 256;        // hidden width (MMA N and total K)
+constexpr int kThreads = 256;  // two warpgroups; warp w reads TMEM lanes 32 (w % 4) ..
+constexpr int kMaxIn = 8;
+constexpr uint32_t kABytes = kRows * kH * 2;
+constexpr uint32_t kBBytes = kH * kH * 2;
+constexpr uint32_t kLbo = 128;             // next 8-column (K) group
+constexpr uint32_t kSbo = (kH / 8) * 128;  // next 8-row group: 4096
+constexpr uint32_t kTmemCols = 256;
+// small parameters staged once per CTA: W1 (padded to 8 inputs), b1, hidden
+// biases, W_out, b_out, and the second warpgroup's output-layer partial sums
+constexpr size_t kParFloats = kH * kMaxIn + kH + kMlpTcMaxGemm * kH + 3 * kH + 4 + 3 * kRows;
+constexpr size_t kSmem = 1024 + kABytes + kBBytes + 64 + kParFloats * 4;
+constexpr long long kSpinLimit = 1ll << 22;
+
+// tcgen05 instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B
+// bf16 (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N / 8 in
+// bits 17-22, M / 16 in bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kH >> 3) << 17) |
+                            ((uint32_t)(kRows >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor: start address, leading- and stride-
+// dimension byte offsets (all >> 4, 14 bits each), descriptor version 1
+// (bits 46-47), no swizzle (bits 61-63 = 0).
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+// Bounded wait for the mbarrier phase with the given parity.
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (long long it = 0; it < kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem)), "l"(gmem));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// NIN: compiled input count (4 for the surrogate's inputs); 0 = any n_in <= 8
+// (weights zero-padded to 8 inputs).
+template <int NIN>
+__global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const MlpTcParams P) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  unsigned char* base = tc_smem + ((1024u - (smem_u32(tc_smem) & 1023u)) & 1023u);
+  unsigned char* As = base;
+  unsigned char* Bs = base + kABytes;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(Bs + kBBytes);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
+  float* sW1 = reinterpret_cast<float*>(Bs + kBBytes + 64);  // [kH][kMaxIn]
+  float* sb1 = sW1 + kH * kMaxIn;
+  float* sbh = sb1 + kH;                       // [kMlpTcMaxGemm][kH]
+  float* sWo = sbh + kMlpTcMaxGemm * kH;       // [3][kH]
+  float* sbo = sWo + 3 * kH;                   // [4]
+  float* sy = sbo + 4;                         // [3][kRows]
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int r = tid & (kRows - 1);  // row of the tile this thread owns
+  const int g = tid >> 7;           // warpgroup: columns [128 g, 128 g + 128)
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  for (int e = tid; e < kH * kMaxIn; e += kThreads) {
+    const int o = e / kMaxIn, i = e % kMaxIn;
+    sW1[e] = i < P.n_in ? P.W1[o * P.n_in + i] : 0.f;
+  }
+  for (int e = tid; e < kH; e += kThreads) sb1[e] = P.b1[e];
+  for (int l = 0; l < P.n_gemm; ++l)
+    for (int e = tid; e < kH; e += kThreads) sbh[l * kH + e] = P.bh[l][e];
+  for (int e = tid; e < 3 * kH; e += kThreads) sWo[e] = P.Wout[e];
+  if (tid < 3) sbo[tid] = P.bout[tid];
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t tmem_warp = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+  uint32_t parity = 0;
+  bool failed = false;
+
+  for (int64_t tile = blockIdx.x; tile < P.n_tiles && !failed; tile += gridDim.x) {
+    const int64_t row = tile * kRows + r;
+    // ---- input layer (FP32): this warpgroup's 128 outputs of row r ----
+    constexpr int NI = NIN > 0 ? NIN : kMaxIn;  // inputs summed (zero-padded when NIN = 0)
+    float xin[kMaxIn];
+#pragma unroll
+    for (int i = 0; i < kMaxIn; ++i)
+      xin[i] = (NIN > 0 ? i < NIN : i < P.n_in) ? P.x[row * (NIN > 0 ? NIN : P.n_in) + i] : 0.f;
+#pragma unroll 2
+    for (int kc = 16 * g; kc < 16 * g + 16; ++kc) {
+      uint32_t w[4];
+#pragma unroll
+      for (int e = 0; e < 8; e += 2) {
+        float v[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int o = kc * 8 + e + q;
+          const float4* wr = reinterpret_cast<const float4*>(sW1 + o * kMaxIn);
+          const float4 w0 = wr[0];
+          float acc = sb1[o];
+          acc = fmaf(w0.x, xin[0], acc);
+          if (NI > 1) acc = fmaf(w0.y, xin[1], acc);
+          if (NI > 2) acc = fmaf(w0.z, xin[2], acc);
+          if (NI > 3) acc = fmaf(w0.w, xin[3], acc);
+          if (NI > 4) {
+            const float4 w1 = wr[1];
+            acc = fmaf(w1.x, xin[4], acc);
+            if (NI > 5) acc = fmaf(w1.y, xin[5], acc);
+            if (NI > 6) acc = fmaf(w1.z, xin[6], acc);
+            if (NI > 7) acc = fmaf(w1.w, xin[7], acc);
+          }
+          v[q] = fmaxf(acc, 0.f);
+        }
+        w[e / 2] = pack_bf16(v[0], v[1]);
+      }
+      *reinterpret_cast<uint4*>(As + (r >> 3) * kSbo + kc * kLbo + (r & 7) * 16) =
+          make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    // ---- hidden layers on the tensor cores ----
+    for (int l = 0; l < P.n_gemm; ++l) {
+      const unsigned char* src = reinterpret_cast<const unsigned char*>(P.Wimg[l]);
+      for (uint32_t c = tid; c < kBBytes / 16; c += kThreads) cp_async16(Bs + 16 * c, src + 16 * c);
+      asm volatile("cp.async.wait_all;\n" ::: "memory");
+      // generic-proxy writes of A and B -> visible to the tensor cores
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      if (tid == 0) {
+        const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+#pragma unroll 1
+        for (int k = 0; k < kH / 16; ++k)
+          mma_bf16(tmem, sdesc(a0 + 2u * k * kLbo, kLbo, kSbo), sdesc(b0 + 2u * k * kLbo, kLbo, kSbo),
+                   kIdesc, k > 0 ? 1u : 0u);
+        mma_commit(bar);
+      }
+      bool ok = bar_wait(bar, parity);
+      if (!ok) ok = bar_wait(bar, parity);  // a second bounded wait before giving up
+      parity ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicOr(P.err, 1u);
+        failed = true;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const float* bias = sbh + l * kH;
+      const bool last = l == P.n_gemm - 1;
+      float y0 = 0.f, y1 = 0.f, y2 = 0.f;
+#pragma unroll 1
+      for (int cc = 4 * g; cc < 4 * g + 4; ++cc) {
+        uint32_t v[32];
+        tmem_ld32(tmem_warp + (uint32_t)(cc * 32), v);
+        uint32_t w[16];
+#pragma unroll
+        for (int j = 0; j < 32; j += 2) {
+          const int col = cc * 32 + j;
+          const float h0 = fmaxf(__uint_as_float(v[j]) + bias[col], 0.f);
+          const float h1 = fmaxf(__uint_as_float(v[j + 1]) + bias[col + 1], 0.f);
+          w[j / 2] = pack_bf16(h0, h1);
+          if (last) {
+            const __nv_bfloat162 hb = *reinterpret_cast<const __nv_bfloat162*>(&w[j / 2]);
+            const float a = __low2float(hb), b = __high2float(hb);
+            y0 = fmaf(sWo[col], a, y0);
+            y0 = fmaf(sWo[col + 1], b, y0);
+            y1 = fmaf(sWo[kH + col], a, y1);
+            y1 = fmaf(sWo[kH + col + 1], b, y1);
+            y2 = fmaf(sWo[2 * kH + col], a, y2);
+            y2 = fmaf(sWo[2 * kH + col + 1], b, y2);
+          }
+        }
+        if (!last) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<uint4*>(As + (r >> 3) * kSbo + (cc * 4 + q) * kLbo + (r & 7) * 16) =
+                make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+        }
+      }
+      if (last && g == 1) {
+        sy[r] = y0;
+        sy[kRows + r] = y1;
+        sy[2 * kRows + r] = y2;
+      }
+      // TMEM reads done, A rewritten and partial sums posted before moving on
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      if (last && g == 0) {
+        y0 += sy[r] + sbo[0];
+        y1 += sy[kRows + r] + sbo[1];
+        y2 += sy[2 * kRows + r] + sbo[2];
+        const float nrm = sqrtf(y0 * y0 + y1 * y1 + y2 * y2);
+        const float inv = nrm > 0.f ? 1.f / nrm : 0.f;
+        P.y[row * 3] = y0 * inv;
+        P.y[row * 3 + 1] = y1 * inv;
+        P.y[row * 3 + 2] = y2 * inv;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(kTmemCols)
+                 : "memory");
+}
+
+}  // namespace
+
+size_t mlp_tc_weight_image_elems() { return (size_t)kH * kH; }
+
+bool mlp_tc_supported(int n_in, int hidden, int n_hidden, int n_out) {
+  return hidden == kH && n_in >= 1 && n_in <= 8 && n_out == 3 && n_hidden >= 2 &&
+         n_hidden - 1 <= kMlpTcMaxGemm;
+}
+
+cudaError_t mlp_forward_tc(const MlpTcParams& p, int sm_count, cudaStream_t s) {
+  auto k = p.n_in == 4 ? k_mlp_forward_tc<4> : k_mlp_forward_tc<0>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+  if (e != cudaSuccess) return e;
+  int64_t grid = p.n_tiles < sm_count ? p.n_tiles : sm_count;
+  if (grid < 1) return cudaSuccess;
+  k<<<(unsigned)grid, kThreads, kSmem, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace crp

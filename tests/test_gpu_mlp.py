@@ -166,3 +166,36 @@ def test_surrogate_lens_matches_oracle_network(torch_dev):
     for c in np.nonzero(got_counts)[0][:50]:
         col = got["entries"][got["col_start"][c]:got["col_start"][c + 1]]
         assert np.all(np.isin(col, earth[bins == c // npix]))
+
+
+@pytest.mark.parametrize("n", [4096, 128 * 400])
+def test_fused_tensor_core_forward_matches_layered(torch_dev, n):
+    """The fused tcgen05 forward (one kernel, activations on chip, persistent
+    over 32 or 400 tiles) against the layered GEMM path on the same weights,
+    and against the binary64 oracle."""
+    torch = torch_dev
+    p = _params(21)
+    x, _ = _batch(n, 22)
+    ctx = crp.crp_context_create(0, 1, 16)
+    try:
+        mlp = crp.crp_mlp_create(ctx, 4, 256, 4, 7)
+        crp.crp_mlp_set_params(mlp, p)
+        xd = torch.from_numpy(x).cuda()
+        out = {}
+        for path in (crp.MLP_PATH_TENSOR_CORE_FUSED, crp.MLP_PATH_LAYERED):
+            crp.crp_mlp_set_forward_path(mlp, path)
+            yd = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+            crp.crp_mlp_forward(mlp, xd, yd, n)
+            torch.cuda.synchronize()
+            out[path] = yd.cpu().numpy().astype(np.float64)
+        crp.crp_mlp_destroy(mlp)
+    finally:
+        crp.crp_context_destroy(ctx)
+    fused, layered = out[crp.MLP_PATH_TENSOR_CORE_FUSED], out[crp.MLP_PATH_LAYERED]
+    assert np.all(np.isfinite(fused))
+    assert np.allclose(np.linalg.norm(fused, axis=1), 1.0, atol=1e-5)
+    d = M.angle_deg(fused, layered)
+    assert np.median(d) < 0.05 and np.max(d) < 1.0, (np.median(d), np.max(d))
+    ref, _ = M.forward(_oracle_view(p), SHAPES, x.astype(np.float64))
+    a = M.angle_deg(fused, ref)
+    assert np.median(a) < 0.3 and np.max(a) < 3.0, (np.median(a), np.max(a))
