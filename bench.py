@@ -136,6 +136,19 @@ def setup_dist(args):
     return rank, world, local, dist
 
 
+def aggregate_ranks(dist, elapsed, steps):
+    """Whole-job figures: the slowest rank's time and the steps of all ranks
+    (each rank propagates its own shard; this is the only collective)."""
+    if not dist:
+        return elapsed, float(steps)
+    import torch
+    t = torch.tensor([elapsed], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    a = torch.tensor([float(steps)], dtype=torch.float64)
+    dist.all_reduce(a)
+    return float(t[0]), float(a[0])
+
+
 def workload_inputs(n, rank):
     w = workloads.MIXED_INTERACTIONS
     inj = workloads.mixed_interactions(n=n, seed=w["seed"] + 7919 * rank)
@@ -228,15 +241,7 @@ def run_ours(args):
     rej = sum(s.rejected_trials for s in stats)
     kern_ms = sum(s.kernel_ms for s in stats)
     launches = sum(s.launches for s in stats)
-    if dist:
-        t = torch.tensor([elapsed], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t[0])
-        a = torch.tensor([acc], dtype=torch.float64)
-        dist.all_reduce(a)
-        acc_all = float(a[0])
-    else:
-        acc_all = float(acc)
+    elapsed, acc_all = aggregate_ranks(dist, elapsed, acc)
     value = acc_all / elapsed
 
     # ---- end to end through the public API with host buffers ---------------

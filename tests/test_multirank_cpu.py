@@ -1,0 +1,57 @@
+"""The multi-rank bench path on CPU (gloo, world size 2): every rank draws its
+own candidate shard (disjoint ids, distinct draws, no data exchange), and
+the only collective turns per-rank times and step counts into whole-job
+figures (slowest rank's time, sum of steps)."""
+import os
+import socket
+
+import numpy as np
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import bench
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        _, inj = bench.workload_inputs(2000, rank)
+        elapsed, steps = bench.aggregate_ranks(dist, 1.0 + rank, 1000 * (rank + 1))
+        ids = torch.from_numpy(inj["id"].astype(np.int64))
+        gathered = [torch.zeros_like(ids) for _ in range(world)]
+        dist.all_gather(gathered, ids)  # test-side check only
+        e = torch.from_numpy(inj["E"])
+        energies = [torch.zeros_like(e) for _ in range(world)]
+        dist.all_gather(energies, e)
+        out[rank] = (elapsed, steps, [g.numpy() for g in gathered], [x.numpy() for x in energies])
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_shards_and_aggregation():
+    world = 2
+    port = _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    for r in range(world):
+        elapsed, steps, ids, energies = res[r]
+        assert elapsed == 2.0            # the slowest rank's time
+        assert steps == 3000.0           # the sum over ranks
+        assert len(np.intersect1d(ids[0], ids[1])) == 0
+        assert ids[1].min() == 2000 and ids[0].max() == 1999
+        assert not np.array_equal(energies[0], energies[1])
+
+
+def test_single_rank_aggregation_is_identity():
+    assert bench.aggregate_ranks(None, 1.5, 42) == (1.5, 42.0)
