@@ -182,9 +182,9 @@ def flops_per_trial_mixed():
 GATHER_BYTES_PER_TRIAL_F32 = 6 * 8 * 3 * 4
 # DRAM bytes (read + write) per Cash-Karp trial of the mixed propagate kernel, from
 # one ncu capture of the current kernel (2e5 candidates of this workload:
-# 154.92 GB read + 0.157 GB written over 1.5613e9 trials); traffic grows with the
+# 154.981 GB read + 0.157 GB written over 1.5611e9 trials); traffic grows with the
 # number of trials, so a launch's traffic is this figure times its trials
-DRAM_BYTES_PER_TRIAL_MIXED = (154.916e9 + 0.157e9) / 1.5613e9
+DRAM_BYTES_PER_TRIAL_MIXED = (154.981e9 + 0.157e9) / 1.5611e9
 
 
 def run_ours(args):

@@ -1099,6 +1099,7 @@ crp_status crp_propagate(crp_context* c, const crp_grid* g, const crp_modules* m
   kp.curv_k = 299792458.0 * m->field_unit_T * m->length_unit_m;
   kp.beta_ad = m->beta_ad;
   kp.e_min = m->e_min;
+  kp.e_min_guard_f = (float)(m->e_min * 1.0001);
   kp.flags = m->flags;
   kp.seed = c->seed;
   if (m->tables) {
@@ -1134,8 +1135,13 @@ crp_status crp_propagate(crp_context* c, const crp_grid* g, const crp_modules* m
   kp.capacity = c->capacity;
 
   const int block = m->block_size ? m->block_size : (m->precision == CRP_FP64 ? 128 : 256);
-  // mixed kernels come in two register budgets: 2 or 3 resident blocks of 256
-  const int variant = (m->blocks_per_sm >= 3 || (m->block_size && m->block_size <= 128)) ? 3 : 2;
+  // mixed kernels come in three register budgets: 256 x 2 resident blocks
+  // (128 registers), 128 x 5 (96) and 256 x 3 (80)
+  int variant = 2;
+  if (m->block_size && m->block_size <= 128)
+    variant = (m->blocks_per_sm == 0 || m->blocks_per_sm <= 5) ? 5 : 3;
+  else if (m->blocks_per_sm >= 3)
+    variant = 3;
   int bps = m->blocks_per_sm;
   if (!bps) {
     cudaError_t e = m->precision == CRP_FP64
@@ -1572,7 +1578,7 @@ extern "C" crp_status crp_autotune(crp_context* c, const crp_grid* g, crp_module
   Cfg cfgs[32];
   int nc = 0;
   const uint32_t slices[3] = {512u, 4096u, kDefaultSlice};
-  const int mixed_bl[3][2] = {{256, 2}, {256, 3}, {128, 6}};
+  const int mixed_bl[3][2] = {{256, 2}, {256, 3}, {128, 5}};
   const int fp64_bl[3][2] = {{128, 0}, {64, 0}, {32, 0}};
   for (int b = 0; b < 3; ++b) {
     const int* bl = m->precision == CRP_MIXED ? mixed_bl[b] : fp64_bl[b];

@@ -76,6 +76,7 @@ struct FieldView {
 struct KParams {
   FieldView f;
   double tol, tol2, h_min, h_max, curv_k, beta_ad, e_min;
+  float e_min_guard_f;  // binary32 E_min plus 1e-4: below it the exact test runs
   // binary32 copies for the mixed policy (converted once on the host)
   float tol2_f, inv_tol2_f, h_min_f, h_max_f, curv_k_f, beta_ad_f, tab_lg0_f, tab_inv_dlg_f;
   const float* t_beta_f;

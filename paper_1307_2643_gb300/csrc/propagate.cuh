@@ -740,7 +740,8 @@ struct PolicyFP64 {
     if (c.status == CRP_ACTIVE && c.budget == 0) c.status = CRP_BUDGET;
   }
 
-  __device__ __forceinline__ static void after_event(const DevState& st, Lane& c) {
+  __device__ __forceinline__ static void after_event(const KParams&, const DevState& st,
+                                                     Lane& c) {
     reload_event_fields(st, c);
   }
 
@@ -783,6 +784,13 @@ struct PolicyMixedT {
     float3 k1;      // force at the start of the step
     int cap, since_rebase;
     uint32_t cell_key;  // index of the cell record held in this lane's cache
+    // binary32 lower bound of the distance to the next length cap (s_max,
+    // pending free paths); the exact binary64 tests run only when it is
+    // below two proposed steps ("near")
+    float near_f;
+    bool near;
+    // energy losses since the last fold: E = E_fold * (1 - yl), yl in binary32
+    float yl, E_fold_f;
   };
 
   __device__ __forceinline__ static void init_lane(Lane& c) { c.cell_key = 0xffffffffu; }
@@ -828,10 +836,34 @@ struct PolicyMixedT {
     c.u[2] = (float)st.uz[i];
     c.hn = fminf(fmaxf((float)c.h, p.h_min_f), p.h_max_f);
     c.E_f = (float)c.E;
+    c.E_fold_f = c.E_f;
+    c.yl = 0.f;
     rebase(p, c);
     bounds(p, c);
+    set_near(p, c);
   }
+
+  // Lower bound (binary32, rounded down) of the distance to the nearest
+  // length cap: the end of the trajectory or a pending free path.
+  __device__ __forceinline__ static void set_near(const KParams& p, Lane& c) {
+    double d = c.s_max - c.s;
+    if ((p.flags & CRP_PION) && c.d_pion < d) d = c.d_pion;
+    if ((p.flags & CRP_PHOTODIS) && c.d_pd < d) d = c.d_pd;
+    c.near_f = __double2float_rd(d);
+  }
+
+  // Apply the losses accumulated since the last fold to the binary64 energy.
+  __device__ __forceinline__ static void fold_energy(Lane& c) {
+    if (c.yl != 0.f) {
+      c.E = c.E * (1.0 - (double)c.yl);
+      c.E_f = (float)c.E;
+      c.E_fold_f = c.E_f;
+      c.yl = 0.f;
+    }
+  }
+
   __device__ __forceinline__ static void store(const DevState& st, Lane& c) {
+    fold_energy(c);
     c.h = (double)c.hn;
     store_core(st, c);
     st.ux[c.slot] = (double)c.u[0];
@@ -941,21 +973,27 @@ struct PolicyMixedT {
   __device__ __forceinline__ static void begin_step(const KParams& p, Lane& c,
                                                     StageStore<float>&) {
     c.cap = CAP_NONE;
-    double h = (double)c.hn;
-    const double rem = c.s_max - c.s;
-    if (rem < h) {
-      h = rem;
-      c.cap = CAP_S;
+    c.hf = c.hn;
+    // near_f bounds every cap distance from below: at or above two proposed
+    // steps no cap can bind, and the binary64 comparisons are skipped
+    c.near = c.near_f < 2.f * c.hn;
+    if (c.near) {
+      double h = (double)c.hn;
+      const double rem = c.s_max - c.s;
+      if (rem < h) {
+        h = rem;
+        c.cap = CAP_S;
+      }
+      if ((p.flags & CRP_PION) && c.d_pion < h) {
+        h = c.d_pion;
+        c.cap = CAP_PION;
+      }
+      if ((p.flags & CRP_PHOTODIS) && c.d_pd < h) {
+        h = c.d_pd;
+        c.cap = CAP_PD;
+      }
+      if (c.cap != CAP_NONE) c.hf = (float)h;
     }
-    if ((p.flags & CRP_PION) && c.d_pion < h) {
-      h = c.d_pion;
-      c.cap = CAP_PION;
-    }
-    if ((p.flags & CRP_PHOTODIS) && c.d_pd < h) {
-      h = c.d_pd;
-      c.cap = CAP_PD;
-    }
-    c.hf = c.cap == CAP_NONE ? c.hn : (float)h;
     c.kap = (float)(c.q * c.Z) * p.curv_k_f / c.E_f;
     c.k1 = force(c.kap, c.u[0], c.u[1], c.u[2], field<NodeT>(p, c, 0.f, 0.f, 0.f));
     c.rejections = 0;
@@ -1085,23 +1123,33 @@ struct PolicyMixedT {
         beta = bp * (float)(c.Z * c.Z) / (float)c.A;
       }
       if (p.flags & CRP_ADIABATIC) beta += p.beta_ad_f;
-      c.E = c.E * (1.0 - (double)(beta * hf));
-      c.E_f = (float)c.E;
+      // (1 - yl)(1 - x) = 1 - (yl + x - x yl): yl stays small, so its binary32
+      // rounding is tiny against the energy; folded into binary64 every 32
+      // steps (with the rebase), at events and when the lane is stored
+      const float x = beta * hf;
+      c.yl = fmaf(-x, c.yl, c.yl + x);
+      c.E_f = c.E_fold_f * (1.f - c.yl);
     }
-    // stochastic interactions
+    if (c.since_rebase == 0) fold_energy(c);
+    // stochastic interactions (a free path can end only in a "near" step)
     const bool pion_on = (p.flags & CRP_PION) != 0;
     const bool pd_on = (p.flags & CRP_PHOTODIS) != 0;
     if (pion_on) c.d_pion = c.cap == CAP_PION ? 0.0 : c.d_pion - h;
     if (pd_on) c.d_pd = c.cap == CAP_PD ? 0.0 : c.d_pd - h;
-    if (pion_on && c.d_pion <= 0.0) return EV_PION;
-    if (pd_on && c.d_pd <= 0.0) return EV_PD;
+    c.near_f = __fsub_rd(c.near_f, hf);
+    if (c.near) {
+      if (pion_on && c.d_pion <= 0.0) return EV_PION;
+      if (pd_on && c.d_pd <= 0.0) return EV_PD;
+    }
     return EV_NONE;
   }
 
   __device__ __forceinline__ static void breaks(const KParams& p, Lane& c, LaneCounters& lc) {
-    if ((p.flags & CRP_EMIN) && c.E < p.e_min) {
+    // E_f is within 1e-6 of the energy, so the binary64 test runs only near E_min;
+    // s reaches s_max only in a "near" step
+    if ((p.flags & CRP_EMIN) && c.E_f < p.e_min_guard_f && c.E * (1.0 - (double)c.yl) < p.e_min) {
       c.status = CRP_BELOW_EMIN;
-    } else if (c.s >= c.s_max) {
+    } else if (c.near && c.s >= c.s_max) {
       c.status = CRP_MAX_LENGTH;
     } else if (c.crossed) {
       c.status = CRP_DETECTED;
@@ -1120,9 +1168,13 @@ struct PolicyMixedT {
     if (c.status == CRP_ACTIVE && c.budget == 0) c.status = CRP_BUDGET;
   }
 
-  __device__ __forceinline__ static void after_event(const DevState& st, Lane& c) {
+  __device__ __forceinline__ static void after_event(const KParams& p, const DevState& st,
+                                                     Lane& c) {
     reload_event_fields(st, c);
     c.E_f = (float)c.E;
+    c.E_fold_f = c.E_f;
+    c.yl = 0.f;
+    set_near(p, c);
   }
 
   __device__ __forceinline__ static void suspend(Lane& c) { c.hn = c.hf; }
@@ -1141,19 +1193,11 @@ using PolicyMixedGal = PolicyMixedT<true>;
 // iteration for the whole warp), then requeue still-active candidates for
 // the next round and take the next one.
 // ---------------------------------------------------------------------------
-// Threads per block of each policy; MINB, the resident blocks per SM the
-// register allocation is sized for, is a launch variant the tuner chooses.
-template <class Policy>
-struct Bounds {
-  static constexpr int kThreads = 256;
-};
-template <>
-struct Bounds<PolicyFP64> {
-  static constexpr int kThreads = 128;
-};
-
-template <class Policy, class NodeT, int MINB>
-__global__ void __launch_bounds__(Bounds<Policy>::kThreads, MINB)
+// THREADS (largest block) and MINB (resident blocks per SM the register
+// allocation is sized for) form a launch variant: registers per thread are
+// at most 65536 / (THREADS * MINB).
+template <class Policy, class NodeT, int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB)
     propagate_kernel(const KParams p, const DevState st, DevCounters* dc) {
   using Real = typename Policy::Real;
   using Lane = typename Policy::Lane;
@@ -1205,7 +1249,7 @@ __global__ void __launch_bounds__(Bounds<Policy>::kThreads, MINB)
         if (ev != EV_NONE) {
           Policy::store(st, c);
           slot_event(p, st, dc, c.slot, ev);
-          Policy::after_event(st, c);
+          Policy::after_event(p, st, c);
         }
         Policy::breaks(p, c, lc);
         in_step = false;
@@ -1265,7 +1309,7 @@ size_t smem_bytes(int block) {
   return Policy::kSmemPerThread * (size_t)block;
 }
 
-template <class Policy, int MINB>
+template <class Policy, int THREADS, int MINB>
 cudaError_t launch_policy(const KParams& kp, const DevState& st, DevCounters* dc, int grid,
                           int block, cudaStream_t s) {
   const size_t sm = smem_bytes<Policy>(block);
@@ -1281,12 +1325,12 @@ cudaError_t launch_policy(const KParams& kp, const DevState& st, DevCounters* dc
     if (carveout > 100) carveout = 100;
   }
   if (kp.f.dtype == CRP_F32) {
-    auto k = propagate_kernel<Policy, float4, MINB>;
+    auto k = propagate_kernel<Policy, float4, THREADS, MINB>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, carveout);
     k<<<grid, block, sm, s>>>(kp, st, dc);
   } else {
-    auto k = propagate_kernel<Policy, DNode, MINB>;
+    auto k = propagate_kernel<Policy, DNode, THREADS, MINB>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, carveout);
     k<<<grid, block, sm, s>>>(kp, st, dc);
@@ -1294,15 +1338,15 @@ cudaError_t launch_policy(const KParams& kp, const DevState& st, DevCounters* dc
   return cudaGetLastError();
 }
 
-template <class Policy, int MINB>
+template <class Policy, int THREADS, int MINB>
 cudaError_t occupancy_policy(int dtype, int block, int* bps) {
   const size_t sm = smem_bytes<Policy>(block);
   if (dtype == CRP_F32) {
-    auto k = propagate_kernel<Policy, float4, MINB>;
+    auto k = propagate_kernel<Policy, float4, THREADS, MINB>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k, block, sm);
   }
-  auto k = propagate_kernel<Policy, DNode, MINB>;
+  auto k = propagate_kernel<Policy, DNode, THREADS, MINB>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k, block, sm);
 }

@@ -5,24 +5,34 @@
 
 namespace crp {
 
-// Register-allocation variants: sized for 2 resident 256-thread blocks per
-// SM (no spills) or for 3 (more warps to hide gather latency).
+// Register-allocation variants (threads x resident blocks per SM): 2 = 256 x 2
+// (128 registers, no spills), 5 = 128 x 5 (96 registers), 3 = 256 x 3 (80).
+template <class P>
+cudaError_t launch_variant(const KParams& kp, const DevState& st, DevCounters* dc, int grid,
+                           int block, int variant, cudaStream_t s) {
+  if (variant == 3) return launch_policy<P, 256, 3>(kp, st, dc, grid, block, s);
+  if (variant == 5) return launch_policy<P, 128, 5>(kp, st, dc, grid, block, s);
+  return launch_policy<P, 256, 2>(kp, st, dc, grid, block, s);
+}
+
+template <class P>
+cudaError_t occupancy_variant(int dtype, int variant, int block, int* bps) {
+  if (variant == 3) return occupancy_policy<P, 256, 3>(dtype, block, bps);
+  if (variant == 5) return occupancy_policy<P, 128, 5>(dtype, block, bps);
+  return occupancy_policy<P, 256, 2>(dtype, block, bps);
+}
+
 cudaError_t launch_propagate_mixed(const KParams& kp, const DevState& st, DevCounters* dc,
                                    int grid, int block, int variant, cudaStream_t s) {
-  const bool gal = (kp.flags & CRP_GALACTIC) != 0;
-  if (variant == 3)
-    return gal ? launch_policy<PolicyMixedGal, 3>(kp, st, dc, grid, block, s)
-               : launch_policy<PolicyMixed, 3>(kp, st, dc, grid, block, s);
-  return gal ? launch_policy<PolicyMixedGal, 2>(kp, st, dc, grid, block, s)
-             : launch_policy<PolicyMixed, 2>(kp, st, dc, grid, block, s);
+  return (kp.flags & CRP_GALACTIC) ? launch_variant<PolicyMixedGal>(kp, st, dc, grid, block,
+                                                                    variant, s)
+                                   : launch_variant<PolicyMixed>(kp, st, dc, grid, block,
+                                                                 variant, s);
 }
 
 cudaError_t occupancy_propagate_mixed(int dtype, int galactic, int variant, int block, int* bps) {
-  if (variant == 3)
-    return galactic ? occupancy_policy<PolicyMixedGal, 3>(dtype, block, bps)
-                    : occupancy_policy<PolicyMixed, 3>(dtype, block, bps);
-  return galactic ? occupancy_policy<PolicyMixedGal, 2>(dtype, block, bps)
-                  : occupancy_policy<PolicyMixed, 2>(dtype, block, bps);
+  return galactic ? occupancy_variant<PolicyMixedGal>(dtype, variant, block, bps)
+                  : occupancy_variant<PolicyMixed>(dtype, variant, block, bps);
 }
 
 size_t propagate_smem_mixed(int block) { return smem_bytes<PolicyMixed>(block); }
