@@ -426,10 +426,11 @@ crp_status crp_grid_sample(const crp_grid* grid, const crp_modules* m, int64_t n
  * scheduler's tunables are this library's own).  Times crp_propagate on the
  * context's injected candidates under a fixed set of configurations (block
  * size x resident blocks per SM x slice x spatial sort), each started from
- * the same snapshot of the pool and stopped after `steps_per_trial`
- * accepted steps (0 = 2e8; UINT64_MAX = run each to completion, which also
- * scores the end of the run where few candidates are left), scored by
- * accepted steps per second of wall time, after one unscored warm-up run.  The pool is restored afterwards:
+ * the same snapshot of the pool and either run to completion
+ * (steps_per_trial 0 or UINT64_MAX: the default; it also scores the end of
+ * the run, where few candidates are left) or stopped after steps_per_trial
+ * accepted steps (steady state only), scored by accepted steps per second of
+ * wall time, after one unscored warm-up run.  The pool is restored afterwards:
  * the context is left exactly as it was.  The fastest configuration is
  * written into m (block_size, blocks_per_sm, slice, queue_order) and *out.
  * Results of a propagation do not depend on these settings (every slice

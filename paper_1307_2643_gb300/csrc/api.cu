@@ -1550,8 +1550,9 @@ extern "C" crp_status crp_autotune(crp_context* c, const crp_grid* g, crp_module
   DeviceGuard dg(c->device);
   crp_status st = ensure_pool(c);
   if (st != CRP_OK) return st;
-  if (steps_per_trial == 0) steps_per_trial = 200000000ull;
-  const bool whole_runs = steps_per_trial == ~0ull;  // score complete propagations
+  // 0 or UINT64_MAX: score complete propagations (what a caller runs; a fixed
+  // step budget sees only the steady state, not the end of the run)
+  const bool whole_runs = steps_per_trial == 0 || steps_per_trial == ~0ull;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const uint64_t size0 = c->size;
   const size_t bytes = ckpt_payload(c, size0);

@@ -157,6 +157,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const MlpTcParam
   const uint32_t tmem_warp = tmem + ((uint32_t)((warp & 3) * 32) << 16);
   uint32_t parity = 0;
   bool failed = false;
+  // weights of the first layer for the first tile; later copies are issued as
+  // soon as the previous MMAs have released tile B, so they overlap the epilogue
+  auto fetch_weights = [&](int l) {
+    const unsigned char* src = reinterpret_cast<const unsigned char*>(P.Wimg[l]);
+    for (uint32_t c = tid; c < kBBytes / 16; c += kThreads) cp_async16(Bs + 16 * c, src + 16 * c);
+  };
+  if (blockIdx.x < P.n_tiles) fetch_weights(0);
 
   for (int64_t tile = blockIdx.x; tile < P.n_tiles && !failed; tile += gridDim.x) {
     const int64_t row = tile * kRows + r;
@@ -170,14 +177,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const MlpTcParam
     for (int kc = 16 * g; kc < 16 * g + 16; ++kc) {
       uint32_t w[4];
 #pragma unroll
-      for (int e = 0; e < 8; e += 2) {
-        float v[2];
+      for (int e = 0; e < 8; e += 4) {
+        const float4 bb = *reinterpret_cast<const float4*>(sb1 + kc * 8 + e);
+        const float bq[4] = {bb.x, bb.y, bb.z, bb.w};
+        float v[4];
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < 4; ++q) {
           const int o = kc * 8 + e + q;
           const float4* wr = reinterpret_cast<const float4*>(sW1 + o * kMaxIn);
           const float4 w0 = wr[0];
-          float acc = sb1[o];
+          float acc = bq[q];
           acc = fmaf(w0.x, xin[0], acc);
           if (NI > 1) acc = fmaf(w0.y, xin[1], acc);
           if (NI > 2) acc = fmaf(w0.z, xin[2], acc);
@@ -192,15 +201,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const MlpTcParam
           v[q] = fmaxf(acc, 0.f);
         }
         w[e / 2] = pack_bf16(v[0], v[1]);
+        w[e / 2 + 1] = pack_bf16(v[2], v[3]);
       }
       *reinterpret_cast<uint4*>(As + (r >> 3) * kSbo + kc * kLbo + (r & 7) * 16) =
           make_uint4(w[0], w[1], w[2], w[3]);
     }
     // ---- hidden layers on the tensor cores ----
     for (int l = 0; l < P.n_gemm; ++l) {
-      const unsigned char* src = reinterpret_cast<const unsigned char*>(P.Wimg[l]);
-      for (uint32_t c = tid; c < kBBytes / 16; c += kThreads) cp_async16(Bs + 16 * c, src + 16 * c);
-      asm volatile("cp.async.wait_all;\n" ::: "memory");
+      asm volatile("cp.async.wait_all;\n" ::: "memory");  // this layer's weights are in B
       // generic-proxy writes of A and B -> visible to the tensor cores
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -223,6 +231,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const MlpTcParam
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      // the MMAs are complete: tile B is free for the next weights
+      if (l + 1 < P.n_gemm)
+        fetch_weights(l + 1);
+      else if (tile + gridDim.x < P.n_tiles)
+        fetch_weights(0);
       const float* bias = sbh + l * kH;
       const bool last = l == P.n_gemm - 1;
       float y0 = 0.f, y1 = 0.f, y2 = 0.f;
@@ -232,20 +245,35 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const MlpTcParam
         tmem_ld32(tmem_warp + (uint32_t)(cc * 32), v);
         uint32_t w[16];
 #pragma unroll
-        for (int j = 0; j < 32; j += 2) {
+        for (int j = 0; j < 32; j += 4) {
           const int col = cc * 32 + j;
-          const float h0 = fmaxf(__uint_as_float(v[j]) + bias[col], 0.f);
-          const float h1 = fmaxf(__uint_as_float(v[j + 1]) + bias[col + 1], 0.f);
+          const float4 b4 = *reinterpret_cast<const float4*>(bias + col);
+          const float h0 = fmaxf(__uint_as_float(v[j]) + b4.x, 0.f);
+          const float h1 = fmaxf(__uint_as_float(v[j + 1]) + b4.y, 0.f);
+          const float h2 = fmaxf(__uint_as_float(v[j + 2]) + b4.z, 0.f);
+          const float h3 = fmaxf(__uint_as_float(v[j + 3]) + b4.w, 0.f);
           w[j / 2] = pack_bf16(h0, h1);
+          w[j / 2 + 1] = pack_bf16(h2, h3);
           if (last) {
-            const __nv_bfloat162 hb = *reinterpret_cast<const __nv_bfloat162*>(&w[j / 2]);
-            const float a = __low2float(hb), b = __high2float(hb);
-            y0 = fmaf(sWo[col], a, y0);
-            y0 = fmaf(sWo[col + 1], b, y0);
-            y1 = fmaf(sWo[kH + col], a, y1);
-            y1 = fmaf(sWo[kH + col + 1], b, y1);
-            y2 = fmaf(sWo[2 * kH + col], a, y2);
-            y2 = fmaf(sWo[2 * kH + col + 1], b, y2);
+            const __nv_bfloat162 p01 = *reinterpret_cast<const __nv_bfloat162*>(&w[j / 2]);
+            const __nv_bfloat162 p23 = *reinterpret_cast<const __nv_bfloat162*>(&w[j / 2 + 1]);
+            const float a0 = __low2float(p01), a1 = __high2float(p01);
+            const float a2 = __low2float(p23), a3 = __high2float(p23);
+            const float4 wa = *reinterpret_cast<const float4*>(sWo + col);
+            const float4 wb = *reinterpret_cast<const float4*>(sWo + kH + col);
+            const float4 wc = *reinterpret_cast<const float4*>(sWo + 2 * kH + col);
+            y0 = fmaf(wa.x, a0, y0);
+            y0 = fmaf(wa.y, a1, y0);
+            y0 = fmaf(wa.z, a2, y0);
+            y0 = fmaf(wa.w, a3, y0);
+            y1 = fmaf(wb.x, a0, y1);
+            y1 = fmaf(wb.y, a1, y1);
+            y1 = fmaf(wb.z, a2, y1);
+            y1 = fmaf(wb.w, a3, y1);
+            y2 = fmaf(wc.x, a0, y2);
+            y2 = fmaf(wc.y, a1, y2);
+            y2 = fmaf(wc.z, a2, y2);
+            y2 = fmaf(wc.w, a3, y2);
           }
         }
         if (!last) {
@@ -276,6 +304,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const MlpTcParam
       }
     }
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");  // no copy outlives the kernel
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");

@@ -88,3 +88,20 @@ def test_fullsize_mixed_against_fp64(full_run):
     # detection counts agree statistically
     d64, dmx = (r64["status"] == crp.DETECTED).sum(), (rmx["status"] == crp.DETECTED).sum()
     assert abs(int(d64) - int(dmx)) <= 5 * np.sqrt(max(d64, 1)) + 5
+
+
+def test_fullsize_mixed_spectra_and_arrival_maps(full_run):
+    """Spectra and arrival maps of the mixed path against the FP64 path at
+    full size: two-sample KS on log E (all records and detected ones) and on
+    the arrival directions of the detected candidates."""
+    from scipy.stats import ks_2samp
+    _, _, _, _, out = full_run
+    r64, _ = out["fp64"]
+    rmx, _ = out["mixed"]
+    assert ks_2samp(np.log(rmx["E"]), np.log(r64["E"])).pvalue > 0.01
+    d64 = r64[r64["status"] == crp.DETECTED]
+    dmx = rmx[rmx["status"] == crp.DETECTED]
+    assert len(d64) > 100 and len(dmx) > 100
+    assert ks_2samp(np.log(dmx["E"]), np.log(d64["E"])).pvalue > 0.01
+    for comp in (lambda u: -u[:, 2], lambda u: np.arctan2(-u[:, 1], -u[:, 0])):
+        assert ks_2samp(comp(dmx["u"]), comp(d64["u"])).pvalue > 0.01

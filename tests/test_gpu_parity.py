@@ -358,6 +358,18 @@ def test_mixed_interactions_statistics(field_f32_small, tables, interaction_ref)
     e = rel_err(prim_g["E"][same], prim_r["E"][same], floor=0.0)
     assert np.median(e) < 1e-5
     assert np.mean(prim_g["n_pion"][same] == prim_r["n_pion"][same]) > 0.95
+    # arrival maps: final directions by distribution (cos theta, phi) and a
+    # HEALPix nside-4 map (two-sample chi-square)
+    from scipy.stats import chi2 as chi2_dist
+    for comp in (lambda u: u[:, 2], lambda u: np.arctan2(u[:, 1], u[:, 0])):
+        p = ks_2samp(comp(gpu["u"]), comp(ref["u"])).pvalue
+        assert p > 0.01, p
+    a = np.bincount(oracle.ang2pix_vec(4, gpu["u"]), minlength=192).astype(float)
+    b = np.bincount(oracle.ang2pix_vec(4, ref["u"]), minlength=192).astype(float)
+    keep = (a + b) > 0
+    a, b = a[keep], b[keep]
+    stat = np.sum((np.sqrt(b.sum() / a.sum()) * a - np.sqrt(a.sum() / b.sum()) * b) ** 2 / (a + b))
+    assert chi2_dist.sf(stat, len(a) - 1) > 0.01
 
 
 @pytest.mark.parametrize("precision", [crp.FP64, crp.MIXED])
