@@ -136,6 +136,13 @@ def setup_dist(args):
     return rank, world, local, dist
 
 
+def bench_config(w, n, world):
+    """The workload the metric is quoted on (the same for both arms)."""
+    return {"workload": w["name"], "candidates_per_gpu": n, "grid": "256^3 f32",
+            "l2": "inputs larger than L2 (268 MB grid, 245 MB candidate pool)",
+            "parallelism": f"candidate shards x{world}"}
+
+
 def aggregate_ranks(dist, elapsed, steps):
     """Whole-job figures: the slowest rank's time and the steps of all ranks
     (each rank propagates its own shard; this is the only collective)."""
@@ -339,10 +346,8 @@ def run_ours(args):
             "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec == crp.MIXED else "f64",
             "data": "synthetic (seeded injection, GPU-generated turbulent field)",
-            "config": {"workload": w["name"], "candidates_per_gpu": n, "grid": "256^3 f32",
-                       "precision": args.precision,
-                       "round_loop": "cuda-graph" if args.graph else "host", "l2": "inputs larger than L2 (268 MB grid, "
-                       "245 MB candidate pool)", "parallelism": f"candidate shards x{world}"},
+            "config": bench_config(w, n, world),
+            "precision": args.precision, "round_loop": "cuda-graph" if args.graph else "host",
             "accepted_steps": acc, "rejected_trials": rej,
             "rejected_trials_per_s": rej / elapsed,
             "kernel_ms_per_step": kern_ms / args.steps,
@@ -404,7 +409,9 @@ def run_reference(args):
                            oracle.OBSERVER, e_min=w["e_min"], beta_ad=H0_OVER_C,
                            seed=w["seed"], tables=T, obs_r=w["observer_r"])
     cores = len(os.sched_getaffinity(0))
-    per_step = max(16, min(n, 256))
+    # a bounded id-sample of the batch per step: histories are per id, so they
+    # are the full run's; 4096 keeps every host core busy for the whole step
+    per_step = max(16, min(n, 4096))
     rng = np.random.default_rng(2)
 
     def step(i):
@@ -422,7 +429,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": w["name"], "grid": "256^3 (float32 values)"},
+        "data": "synthetic", "config": bench_config(w, n, args.gpus), "precision": "fp64 (oracle)",
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{per_step} random candidates of the batch per step"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
