@@ -32,8 +32,11 @@ namespace {
 constexpr int kGL = 32;
 constexpr int kPanels = 64;
 
-__constant__ double c_gl_x[kGL];
-__constant__ double c_gl_w[kGL];
+// Gauss-Legendre rule on [-1, 1], computed on the host and passed to the
+// kernel by value (no per-device state to initialise).
+struct GLRule {
+  double x[kGL], w[kGL];
+};
 
 // Physical constants (CODATA 2018).
 constexpr double kMe = 0.51099895000e6;        // m_e c^2 [eV]
@@ -68,20 +71,20 @@ __device__ double phi_cz(double k) {
 
 // Composite Gauss-Legendre on [a, b] with kPanels equal panels.
 template <class F>
-__device__ double gl_composite(const F& f, double a, double b) {
+__device__ double gl_composite(const GLRule& gl, const F& f, double a, double b) {
   if (!(b > a)) return 0.0;
   const double w = (b - a) / kPanels;
   double total = 0.0;
   for (int p = 0; p < kPanels; ++p) {
     const double mid = a + (p + 0.5) * w, half = 0.5 * w;
     double s = 0.0;
-    for (int j = 0; j < kGL; ++j) s += c_gl_w[j] * f(mid + half * c_gl_x[j]);
+    for (int j = 0; j < kGL; ++j) s += gl.w[j] * f(mid + half * gl.x[j]);
     total += s * half;
   }
   return total;
 }
 
-__device__ double beta_pair_dev(double gamma, double kT) {
+__device__ double beta_pair_dev(const GLRule& gl, double gamma, double kT) {
   const double kmax = 1400.0 * gamma * kT / kMe;  // Planck factor below e^-700 beyond
   if (kmax <= 2.0) return 0.0;
   auto g = [&](double y) {
@@ -89,7 +92,8 @@ __device__ double beta_pair_dev(double gamma, double kT) {
     return planck(k * kMe / (2.0 * gamma), kT) * phi_cz(k) / k;  // k * n * phi / k^2
   };
   const double lo = log(2.0), mid = log(25.0), hi = log(kmax);
-  const double I = hi <= mid ? gl_composite(g, lo, hi) : gl_composite(g, lo, mid) + gl_composite(g, mid, hi);
+  const double I = hi <= mid ? gl_composite(gl, g, lo, hi)
+                             : gl_composite(gl, g, lo, mid) + gl_composite(gl, g, mid, hi);
   return kAlphaFS * kRe * kRe * kMe * kMe * I / (gamma * kMp);
 }
 
@@ -119,8 +123,8 @@ __device__ double gdr_inner_dev(double e, double peak, double ec, double w, doub
   return peak * w * w * (logs + ang);
 }
 
-__device__ double rate_gdr_dev(double gamma, double kT, double peak, double ec, double w,
-                               double lo, double hi) {
+__device__ double rate_gdr_dev(const GLRule& gl, double gamma, double kT, double peak, double ec,
+                               double w, double lo, double hi) {
   const double e_lo = lo / (2.0 * gamma), e_hi = 700.0 * kT;
   if (e_hi <= e_lo) return 0.0;
   auto g = [&](double y) {
@@ -128,21 +132,22 @@ __device__ double rate_gdr_dev(double gamma, double kT, double peak, double ec, 
     return planck(eps, kT) / eps * gdr_inner_dev(2.0 * gamma * eps, peak, ec, w, lo, hi);
   };
   const double ya = log(e_lo), yb = log(e_hi), ys = log(hi / (2.0 * gamma));
-  const double I = (ys > ya && ys < yb) ? gl_composite(g, ya, ys) + gl_composite(g, ys, yb)
-                                        : gl_composite(g, ya, yb);
+  const double I = (ys > ya && ys < yb) ? gl_composite(gl, g, ya, ys) + gl_composite(gl, g, ys, yb)
+                                        : gl_composite(gl, g, ya, yb);
   return I / (2.0 * gamma * gamma);
 }
 
-__global__ void k_tables(crp_tables_desc d, double* beta, double* pion, double* gdr) {
+__global__ void k_tables(crp_tables_desc d, const GLRule gl, double* beta, double* pion,
+                         double* gdr) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= d.n) return;
   const double l0 = log(d.gamma_lo), l1 = log(d.gamma_hi);
   const double gamma = exp(l0 + (l1 - l0) * (double)i / (double)(d.n - 1));
   const double kT = kBoltz * d.T_cmb;
   const double mb = 1.0e-31;
-  beta[i] = beta_pair_dev(gamma, kT) * d.length_unit_m;
+  beta[i] = beta_pair_dev(gl, gamma, kT) * d.length_unit_m;
   pion[i] = rate_pion_dev(gamma, kT, d.pion_sigma_mb * mb, d.pion_eth_eV) * d.length_unit_m;
-  gdr[i] = rate_gdr_dev(gamma, kT, d.gdr_peak_mb * mb, d.gdr_center_eV, 0.5 * d.gdr_fwhm_eV,
+  gdr[i] = rate_gdr_dev(gl, gamma, kT, d.gdr_peak_mb * mb, d.gdr_center_eV, 0.5 * d.gdr_fwhm_eV,
                         d.gdr_lo_eV, d.gdr_hi_eV) * d.length_unit_m;
 }
 
@@ -183,18 +188,18 @@ void legendre_rule(int n, std::vector<double>& x, std::vector<double>& w) {
 
 crp_status tables_compute(const crp_tables_desc* d, double* beta, double* pion, double* gdr,
                           cudaStream_t s) {
-  static bool rule_ready = false;
-  if (!rule_ready) {
+  GLRule gl;
+  {
     std::vector<double> x, w;
     legendre_rule(kGL, x, w);
-    cudaError_t e = cudaMemcpyToSymbol(c_gl_x, x.data(), sizeof(double) * kGL);
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_gl_w, w.data(), sizeof(double) * kGL);
-    if (e != cudaSuccess) return fail_cuda(e, "Gauss-Legendre constants");
-    rule_ready = true;
+    for (int j = 0; j < kGL; ++j) {
+      gl.x[j] = x[j];
+      gl.w[j] = w[j];
+    }
   }
   const int block = 64;
   const int grid = (int)((d->n + block - 1) / block);
-  k_tables<<<grid, block, 0, s>>>(*d, beta, pion, gdr);
+  k_tables<<<grid, block, 0, s>>>(*d, gl, beta, pion, gdr);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return e == cudaSuccess ? CRP_OK : fail_cuda(e, "table kernel");
