@@ -203,6 +203,12 @@ crp_status crp_candidates_clear(crp_context* ctx);
 #define CRP_OBSERVER (1u << 5)   /* observer sphere: detect on entry          */
 #define CRP_BORDER (1u << 6)     /* border sphere: stop on reaching it        */
 #define CRP_GALACTIC (1u << 7)   /* add the analytic galactic disk+halo field */
+/* free-neutron beta decay (stochastic, after photodisintegration in module
+ * order): a neutron (A = 1, Z = 0) decays after -ln(u) gamma c tau_n
+ * (tau_n = 878.4 s, gamma = E / m_n c^2) into a proton of the same Lorentz
+ * factor (E <- E m_p / m_n); every reset of the interaction states then
+ * draws one more uniform, for every species */
+#define CRP_DECAY (1u << 8)
 
 typedef struct {
   int32_t precision;         /* CRP_FP64 | CRP_MIXED */

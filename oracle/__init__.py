@@ -48,6 +48,7 @@ EMIN = 1 << 4
 OBSERVER = 1 << 5
 BORDER = 1 << 6
 GALACTIC = 1 << 7
+DECAY = 1 << 8
 
 
 def build(force: bool = False) -> str:
@@ -79,6 +80,7 @@ class Params(C.Structure):
         ("gal_halo_b", C.c_double), ("gal_halo_z0", C.c_double), ("gal_halo_sigma", C.c_double),
         ("gal_center", C.c_double * 3),
         ("max_steps", C.c_int64),
+        ("length_unit_m", C.c_double),
     ]
 
 
@@ -313,6 +315,7 @@ def make_params(*, grid_n, spacing, origin=(0.0, 0.0, 0.0), tol=1e-4, h_min=0.01
     P.n[:] = grid_n
     P.tol, P.h_min, P.h_max = tol, h_min, h_max
     P.curv_k = curvature_constant(field_unit_T, length_unit_m)
+    P.length_unit_m = length_unit_m
     P.beta_ad, P.e_min = beta_ad, e_min
     P.flags = flags
     P.seed = seed

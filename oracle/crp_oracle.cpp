@@ -44,6 +44,8 @@ namespace {
 const double kC = 299792458.0;                  // speed of light [m/s]
 const double kMeC2 = 0.51099895000e6;           // electron rest energy [eV]
 const double kMpC2 = 938.27208816e6;            // proton rest energy [eV]
+const double kMnC2 = 939.56542052e6;            // neutron rest energy [eV] (CODATA 2018)
+const double kTauN = 878.4;                     // free-neutron mean lifetime [s] (reading)
 const double kAlpha = 7.2973525693e-3;          // fine-structure constant
 const double kRe = 2.8179403262e-15;            // classical electron radius [m]
 const double kKB = 8.617333262e-5;              // Boltzmann constant [eV/K]
@@ -512,6 +514,7 @@ enum {
   ORC_OBSERVER = 1u << 5,
   ORC_BORDER = 1u << 6,
   ORC_GALACTIC = 1u << 7,   // add the analytic galactic disk + halo field
+  ORC_DECAY = 1u << 8,      // free-neutron beta decay
 };
 
 struct orc_params {
@@ -539,6 +542,7 @@ struct orc_params {
   double gal_halo_b, gal_halo_z0, gal_halo_sigma;
   double gal_center[3];
   int64_t max_steps;   // per-candidate accepted-step budget
+  double length_unit_m;  // metres per length unit (neutron decay length)
 };
 
 struct orc_record {
@@ -695,7 +699,7 @@ struct Cand {
   double x[3], u[3];
   double E, s, s_max, h;
   int A, Z, q;
-  double d_pion, d_pd;
+  double d_pion, d_pd, d_dec;
   bool states_drawn;
   uint32_t draws, events, generation, n_pion, n_pd, n_dropped;
   uint64_t n_acc, n_rej;
@@ -825,6 +829,9 @@ double draw_uniform(const Ctx& C, Cand& c) {
   return uniform_open(w.w[0], w.w[1]);
 }
 
+// Neutron decay length per eV of energy: c tau_n / (m_n c^2), in length units.
+double decay_k(const orc_params& P) { return kC * kTauN / kMnC2 / P.length_unit_m; }
+
 // Reset of all stochastic interaction states (Sect. 3: after an interaction
 // the states of all interactions are reset).  Each state is the remaining
 // free path d = -ln(u) / R(E), drawn at the candidate's current energy, in
@@ -841,6 +848,13 @@ void reset_states(const Ctx& C, Cand& c) {
     double u = draw_uniform(C, c);
     double R = c.A >= 2 ? (double)c.A * table_lookup(C, C.t_gdr, lng) : 0.0;
     c.d_pd = R > 0.0 ? -series_log(u) / R : INFINITY;
+  }
+  if (P.flags & ORC_DECAY) {
+    // free neutrons: decay length gamma c tau = (E / m_n c^2) c tau (reading:
+    // the uniform is drawn for every species, so draw counts depend on the
+    // module list only)
+    double u = draw_uniform(C, c);
+    c.d_dec = (c.A == 1 && c.Z == 0) ? -series_log(u) * (c.E * decay_k(P)) : INFINITY;
   }
   c.states_drawn = true;
 }
@@ -897,8 +911,9 @@ void propagate_one(const Ctx& C, Cand& c, std::vector<Cand>& out_secondaries) {
   const orc_params& P = *C.P;
   const bool pion_on = (P.flags & ORC_PION) != 0;
   const bool pd_on = (P.flags & ORC_PHOTODIS) != 0;
+  const bool dec_on = (P.flags & ORC_DECAY) != 0;
   while (c.status == ORC_ACTIVE) {
-    if ((pion_on || pd_on) && !c.states_drawn) reset_states(C, c);
+    if ((pion_on || pd_on || dec_on) && !c.states_drawn) reset_states(C, c);
     // ---- integration module: Cash-Karp trial steps until accepted ----
     double h = c.h;
     if (h > P.h_max) h = P.h_max;
@@ -906,6 +921,7 @@ void propagate_one(const Ctx& C, Cand& c, std::vector<Cand>& out_secondaries) {
     if (cap_s < h) h = cap_s;
     if (pion_on && c.d_pion < h) h = c.d_pion;
     if (pd_on && c.d_pd < h) h = c.d_pd;
+    if (dec_on && c.d_dec < h) h = c.d_dec;
     const double kappa = (double)(c.q * c.Z) * P.curv_k / c.E;
     double y[6] = {c.x[0], c.x[1], c.x[2], c.u[0], c.u[1], c.u[2]};
     double k1[6], k2[6], k3[6], k4[6], k5[6], k6[6], yt[6], y5[6];
@@ -968,9 +984,10 @@ void propagate_one(const Ctx& C, Cand& c, std::vector<Cand>& out_secondaries) {
       c.E = c.E * (1.0 - beta * h);
     }
     // ---- stochastic interactions: decrement, first in list fires ----
-    if (pion_on || pd_on) {
+    if (pion_on || pd_on || dec_on) {
       if (pion_on) c.d_pion = c.d_pion - h;
       if (pd_on) c.d_pd = c.d_pd - h;
+      if (dec_on) c.d_dec = c.d_dec - h;
       if (pion_on && c.d_pion <= 0.0) {
         // photo-pion event (reading): one nucleon loses inelasticity 0.2
         c.E = c.E - 0.2 * c.E / (double)c.A;
@@ -996,6 +1013,13 @@ void propagate_one(const Ctx& C, Cand& c, std::vector<Cand>& out_secondaries) {
         c.Z = c.Z - (proton ? 1 : 0);
         c.E = Ed;
         c.n_pd += 1;
+        c.events += 1;
+        reset_states(C, c);
+      } else if (dec_on && c.d_dec <= 0.0) {
+        // beta decay n -> p e nu (reading): the proton keeps the Lorentz
+        // factor; electron and antineutrino are not followed
+        c.Z = 1;
+        c.E = c.E * (kMpC2 / kMnC2);
         c.events += 1;
         reset_states(C, c);
       }

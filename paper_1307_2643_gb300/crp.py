@@ -22,7 +22,7 @@ OK, E_INVALID, E_OOM, E_CUDA, E_QUEUE_FULL, E_TIMEOUT, E_BOUNDS, E_STATE = 0, -1
 F32, F64 = 0, 1
 GRID_FROM_HOST, GRID_FROM_DEVICE, GRID_TURBULENT = 0, 1, 2
 FP64, MIXED = 0, 1
-PAIR, ADIABATIC, PION, PHOTODIS, EMIN, OBSERVER, BORDER, GALACTIC = (1 << i for i in range(8))
+PAIR, ADIABATIC, PION, PHOTODIS, EMIN, OBSERVER, BORDER, GALACTIC, DECAY = (1 << i for i in range(9))
 ACTIVE, BELOW_EMIN, MAX_LENGTH, DETECTED, AT_BORDER, BUDGET = range(6)
 COLLECT_ALL, COLLECT_FINISHED, COLLECT_DETECTED, COLLECT_ACTIVE, COLLECT_AT_BORDER = range(5)
 

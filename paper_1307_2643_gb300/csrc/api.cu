@@ -157,7 +157,7 @@ size_t layout_pool(char* base, size_t cap, DevState* st, crp_context* list = nul
   take(&s.x, 8); take(&s.y, 8); take(&s.z, 8);
   take(&s.ux, 8); take(&s.uy, 8); take(&s.uz, 8);
   take(&s.E, 8); take(&s.s, 8); take(&s.s_max, 8); take(&s.h, 8);
-  take(&s.d_pion, 8); take(&s.d_pd, 8);
+  take(&s.d_pion, 8); take(&s.d_pd, 8); take(&s.d_dec, 8);
   take(&s.x0, 8); take(&s.y0, 8); take(&s.z0, 8);
   take(&s.ux0, 8); take(&s.uy0, 8); take(&s.uz0, 8); take(&s.E0, 8);
   take(&s.n_acc, 8); take(&s.n_rej, 8);
@@ -244,6 +244,7 @@ __global__ void k_inject_init(DevState st, uint64_t base, uint64_t n, uint64_t f
     st.h[i] = (double)INFINITY;  // first trial step: h_max
     st.d_pion[i] = 0.0;
     st.d_pd[i] = 0.0;
+    st.d_dec[i] = 0.0;
     st.status[i] = CRP_ACTIVE;
     st.draws[i] = 0;
     st.events[i] = 0;
@@ -1100,6 +1101,8 @@ crp_status crp_propagate(crp_context* c, const crp_grid* g, const crp_modules* m
   kp.beta_ad = m->beta_ad;
   kp.e_min = m->e_min;
   kp.e_min_guard_f = (float)(m->e_min * 1.0001);
+  // free-neutron decay length per eV (tau_n = 878.4 s, m_n c^2 = 939.56542052 MeV)
+  kp.decay_k = 299792458.0 * 878.4 / 939.56542052e6 / m->length_unit_m;
   kp.flags = m->flags;
   kp.seed = c->seed;
   if (m->tables) {
@@ -1391,7 +1394,7 @@ struct CkptHeader {
   uint32_t elem[64];
 };
 constexpr char kCkptMagic[8] = {'C', 'R', 'P', 'C', 'K', 'P', 'T', '1'};
-constexpr uint32_t kCkptVersion = 1;
+constexpr uint32_t kCkptVersion = 2;
 
 // FNV-1a over 32-bit words (every payload is a whole number of words).
 uint64_t ckpt_hash(const unsigned char* p, size_t bytes) {

@@ -42,7 +42,7 @@ enum : uint32_t {
 struct DevState {
   uint64_t *id, *parent;
   double *x, *y, *z, *ux, *uy, *uz;
-  double *E, *s, *s_max, *h, *d_pion, *d_pd;
+  double *E, *s, *s_max, *h, *d_pion, *d_pd, *d_dec;
   double *x0, *y0, *z0, *ux0, *uy0, *uz0, *E0;
   uint64_t *n_acc, *n_rej;
   int32_t *A, *Z, *q, *A0, *Z0, *status;
@@ -77,6 +77,7 @@ struct KParams {
   FieldView f;
   double tol, tol2, h_min, h_max, curv_k, beta_ad, e_min;
   float e_min_guard_f;  // binary32 E_min plus 1e-4: below it the exact test runs
+  double decay_k;       // neutron decay length per eV: c tau_n / (m_n c^2) [length unit]
   // binary32 copies for the mixed policy (converted once on the host)
   float tol2_f, inv_tol2_f, h_min_f, h_max_f, curv_k_f, beta_ad_f, tab_lg0_f, tab_inv_dlg_f;
   const float* t_beta_f;

@@ -223,5 +223,6 @@ __host__ __device__ __forceinline__ uint32_t rigidity_key(double E, int Z) {
 
 // Proton rest energy [eV] (CODATA 2018).
 constexpr double MP_C2_EV = 938.27208816e6;
+constexpr double MN_C2_EV = 939.56542052e6;  // neutron rest energy (CODATA 2018)
 
 }  // namespace crp

@@ -264,7 +264,7 @@ __device__ __forceinline__ float table_f32(const KParams& p, const float* tab, f
 struct EvCore {
   uint64_t id, slot;
   double x[3];
-  double E, s, s_max, d_pion, d_pd;
+  double E, s, s_max, d_pion, d_pd, d_dec;
   int A, Z, q;
   uint32_t draws, events, n_pion, n_pd, n_dropped, flags;
 };
@@ -280,7 +280,7 @@ __device__ __forceinline__ double draw_u(const KParams& p, EvCore& c) {
 }
 
 // Remaining free path d = -ln(u) / R(E) per interaction, in module order
-// [pion production, photodisintegration], at the current energy.
+// [pion production, photodisintegration, neutron decay], at the current energy.
 __device__ __forceinline__ void reset_states(const KParams& p, EvCore& c) {
   const double lng = series_log(c.E / ((double)c.A * MP_C2_EV));
   if (p.flags & CRP_PION) {
@@ -293,7 +293,20 @@ __device__ __forceinline__ void reset_states(const KParams& p, EvCore& c) {
     const double R = c.A >= 2 ? (double)c.A * table_fp64(p, p.t_gdr, lng) : 0.0;
     c.d_pd = R > 0.0 ? -series_log(u) / R : (double)INFINITY;
   }
+  if (p.flags & CRP_DECAY) {
+    // free neutrons decay after -ln(u) gamma c tau; drawn for every species
+    const double u = draw_u(p, c);
+    c.d_dec = (c.A == 1 && c.Z == 0) ? -series_log(u) * (c.E * p.decay_k) : (double)INFINITY;
+  }
   c.flags |= CF_STATES_DRAWN;
+}
+
+// Neutron beta decay: n -> p e nu; the proton keeps the Lorentz factor.
+__device__ __forceinline__ void decay_event(const KParams& p, EvCore& c) {
+  c.Z = 1;
+  c.E = c.E * (MP_C2_EV / MN_C2_EV);
+  c.events += 1;
+  reset_states(p, c);
 }
 
 // Pion event: one nucleon loses the inelasticity 0.2 of its energy.
@@ -343,6 +356,7 @@ __device__ __forceinline__ void photodisintegrate(const KParams& p, const DevSta
       st.h[slot] = p.h_max;
       st.d_pion[slot] = 0.0;
       st.d_pd[slot] = 0.0;
+      st.d_dec[slot] = 0.0;
       st.A[slot] = 1;
       st.Z[slot] = proton ? 1 : 0;
       st.A0[slot] = 1;
@@ -384,7 +398,7 @@ __device__ __forceinline__ void photodisintegrate(const KParams& p, const DevSta
   reset_states(p, c);
 }
 
-enum : int { EV_NONE = 0, EV_PION = 1, EV_PD = 2, EV_DRAW = 3 };
+enum : int { EV_NONE = 0, EV_PION = 1, EV_PD = 2, EV_DRAW = 3, EV_DECAY = 4 };
 
 // Run one rare path on the slot: first free-path draw (EV_DRAW), a pion
 // event or a photodisintegration event.
@@ -401,6 +415,7 @@ static __device__ __noinline__ void slot_event(const KParams& p, const DevState&
   c.s_max = st.s_max[i];
   c.d_pion = st.d_pion[i];
   c.d_pd = st.d_pd[i];
+  c.d_dec = st.d_dec[i];
   c.A = st.A[i];
   c.Z = st.Z[i];
   c.q = st.q[i];
@@ -415,6 +430,8 @@ static __device__ __noinline__ void slot_event(const KParams& p, const DevState&
     pion_event(p, c, n);
   else if (kind == EV_PD)
     photodisintegrate(p, st, dc, c, n, st.ux[i], st.uy[i], st.uz[i]);
+  else if (kind == EV_DECAY)
+    decay_event(p, c);
   else
     reset_states(p, c);
   st.E[i] = c.E;
@@ -422,6 +439,7 @@ static __device__ __noinline__ void slot_event(const KParams& p, const DevState&
   st.Z[i] = c.Z;
   st.d_pion[i] = c.d_pion;
   st.d_pd[i] = c.d_pd;
+  st.d_dec[i] = c.d_dec;
   st.draws[i] = c.draws;
   st.events[i] = c.events;
   st.n_pion[i] = c.n_pion;
@@ -465,6 +483,8 @@ struct LaneCore {
   uint32_t slot;
   int A, Z, q, status;
   double x[3];
+  // d_pd holds the candidate's second stochastic free path: photodisintegration
+  // for nuclei, beta decay for free neutrons (the other one is infinite)
   double E, s, s_max, h, d_pion, d_pd;
   uint32_t dacc, drej;  // accepted steps / rejected trials since the last store
   uint32_t budget;      // accepted steps left before CRP_BUDGET
@@ -475,6 +495,14 @@ struct LaneCore {
 struct LaneCounters {
   uint32_t acc, rej, detected, pending_acc;
 };
+
+__device__ __forceinline__ bool is_neutron(const LaneCore& c) { return c.A == 1 && c.Z == 0; }
+
+// Is the lane's second free path (photodisintegration, or decay for a free
+// neutron) an active module?
+__device__ __forceinline__ bool second_on(const KParams& p, const LaneCore& c) {
+  return (p.flags & (is_neutron(c) ? CRP_DECAY : CRP_PHOTODIS)) != 0;
+}
 
 __device__ __forceinline__ void load_core(const KParams& p, const DevState& st, uint32_t i,
                                           LaneCore& c) {
@@ -487,9 +515,9 @@ __device__ __forceinline__ void load_core(const KParams& p, const DevState& st, 
   c.s_max = st.s_max[i];
   c.h = st.h[i];
   c.d_pion = st.d_pion[i];
-  c.d_pd = st.d_pd[i];
   c.A = st.A[i];
   c.Z = st.Z[i];
+  c.d_pd = is_neutron(c) ? st.d_dec[i] : st.d_pd[i];
   c.q = st.q[i];
   c.status = st.status[i];
   const uint64_t done = st.n_acc[i];
@@ -510,7 +538,10 @@ __device__ __forceinline__ void store_core(const DevState& st, LaneCore& c) {
   st.s[i] = c.s;
   st.h[i] = c.h;
   st.d_pion[i] = c.d_pion;
-  st.d_pd[i] = c.d_pd;
+  if (is_neutron(c))
+    st.d_dec[i] = c.d_pd;
+  else
+    st.d_pd[i] = c.d_pd;
   st.status[i] = c.status;
   st.n_acc[i] += c.dacc;
   st.n_rej[i] += c.drej;
@@ -525,7 +556,7 @@ __device__ __forceinline__ void reload_event_fields(const DevState& st, LaneCore
   c.A = st.A[i];
   c.Z = st.Z[i];
   c.d_pion = st.d_pion[i];
-  c.d_pd = st.d_pd[i];
+  c.d_pd = is_neutron(c) ? st.d_dec[i] : st.d_pd[i];
 }
 
 // One accepted step done: step budget bookkeeping.
@@ -622,7 +653,7 @@ struct PolicyFP64 {
     c.cap_s = c.s_max - c.s;
     if (c.cap_s < h) h = c.cap_s;
     if ((p.flags & CRP_PION) && c.d_pion < h) h = c.d_pion;
-    if ((p.flags & CRP_PHOTODIS) && c.d_pd < h) h = c.d_pd;
+    if (second_on(p, c) && c.d_pd < h) h = c.d_pd;
     c.h = h;  // trial step of this step
     c.kappa = (double)(c.q * c.Z) * p.curv_k / c.E;
     double k[3];
@@ -714,11 +745,11 @@ struct PolicyFP64 {
     }
     // stochastic interactions: the first in module order whose free path ran out
     const bool pion_on = (p.flags & CRP_PION) != 0;
-    const bool pd_on = (p.flags & CRP_PHOTODIS) != 0;
+    const bool pd_on = second_on(p, c);
     if (pion_on) c.d_pion = c.d_pion - h;
     if (pd_on) c.d_pd = c.d_pd - h;
     if (pion_on && c.d_pion <= 0.0) return EV_PION;
-    if (pd_on && c.d_pd <= 0.0) return EV_PD;
+    if (pd_on && c.d_pd <= 0.0) return is_neutron(c) ? EV_DECAY : EV_PD;
     return EV_NONE;
   }
 
@@ -848,7 +879,7 @@ struct PolicyMixedT {
   __device__ __forceinline__ static void set_near(const KParams& p, Lane& c) {
     double d = c.s_max - c.s;
     if ((p.flags & CRP_PION) && c.d_pion < d) d = c.d_pion;
-    if ((p.flags & CRP_PHOTODIS) && c.d_pd < d) d = c.d_pd;
+    if (second_on(p, c) && c.d_pd < d) d = c.d_pd;
     c.near_f = __double2float_rd(d);
   }
 
@@ -988,7 +1019,7 @@ struct PolicyMixedT {
         h = c.d_pion;
         c.cap = CAP_PION;
       }
-      if ((p.flags & CRP_PHOTODIS) && c.d_pd < h) {
+      if (second_on(p, c) && c.d_pd < h) {
         h = c.d_pd;
         c.cap = CAP_PD;
       }
@@ -1133,13 +1164,13 @@ struct PolicyMixedT {
     if (c.since_rebase == 0) fold_energy(c);
     // stochastic interactions (a free path can end only in a "near" step)
     const bool pion_on = (p.flags & CRP_PION) != 0;
-    const bool pd_on = (p.flags & CRP_PHOTODIS) != 0;
+    const bool pd_on = second_on(p, c);
     if (pion_on) c.d_pion = c.cap == CAP_PION ? 0.0 : c.d_pion - h;
     if (pd_on) c.d_pd = c.cap == CAP_PD ? 0.0 : c.d_pd - h;
     c.near_f = __fsub_rd(c.near_f, hf);
     if (c.near) {
       if (pion_on && c.d_pion <= 0.0) return EV_PION;
-      if (pd_on && c.d_pd <= 0.0) return EV_PD;
+      if (pd_on && c.d_pd <= 0.0) return is_neutron(c) ? EV_DECAY : EV_PD;
     }
     return EV_NONE;
   }
@@ -1226,7 +1257,8 @@ __global__ void __launch_bounds__(THREADS, MINB)
         if (mine < n_in) {
           const uint32_t slot = p.queue_in[mine];
           if (st.status[slot] == CRP_ACTIVE) {
-            if ((p.flags & (CRP_PION | CRP_PHOTODIS)) && !(st.flags[slot] & CF_STATES_DRAWN))
+            if ((p.flags & (CRP_PION | CRP_PHOTODIS | CRP_DECAY)) &&
+                !(st.flags[slot] & CF_STATES_DRAWN))
               slot_event(p, st, dc, slot, EV_DRAW);  // first free paths of this candidate
             Policy::load(p, st, slot, c);
             has = true;

@@ -176,6 +176,52 @@ def test_fp64_interactions_parity(field_f32_small, tables, interaction_ref):
     assert st["n_secondaries"] == int((ref["generation"] > 0).sum())
 
 
+def _decay_inputs(seed=41):
+    """Nuclei (some photodisintegrating into free neutrons) plus injected free
+    neutrons of 10^17.5 - 10^20 eV (decay lengths 3 kpc - 0.9 Mpc)."""
+    inj = _interaction_inputs(n_mixed=400, n_hot=160, seed=seed)
+    g = np.random.default_rng(seed)
+    m = 400
+    v = g.normal(size=(m, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    neu = dict(id=np.arange(10 ** 6, 10 ** 6 + m, dtype=np.uint64), x=g.uniform(-20, 20, m),
+               y=g.uniform(-20, 20, m), z=g.uniform(-20, 20, m), ux=v[:, 0].copy(),
+               uy=v[:, 1].copy(), uz=v[:, 2].copy(), E=10 ** g.uniform(17.5, 20.0, m),
+               A=np.ones(m, np.int32), Z=np.zeros(m, np.int32), q=np.ones(m, np.int32),
+               s_max=np.full(m, 40.0))
+    return {k: np.concatenate([inj[k], neu[k]]) for k in neu}
+
+
+def test_neutron_decay_parity(field_f32_small, tables):
+    """Neutron beta decay on top of pion production and photodisintegration:
+    the FP64 path equals the oracle (chains, decays of injected and of
+    secondary neutrons, every float within 1e-9); the mixed path decays the
+    same neutrons wherever its stopping condition agrees."""
+    n, dx, B = field_f32_small
+    inj = _decay_inputs()
+    flags = INTERACTION_FLAGS | crp.DECAY
+    P = oracle_params(n, dx, tables=tables, flags=flags, obs_r=1.0, **_interaction_kw())
+    ref = oracle.propagate(P, B, inj, tables=tables)
+    gpu, st, status = run_gpu(B, n, dx, inj, precision=crp.FP64, dtype=crp.F32, tables=tables,
+                              flags=flags, observer_radius=1.0, **_interaction_kw())
+    assert status == crp.OK
+    decayed = (ref["A0"] == 1) & (ref["Z0"] == 0) & (ref["Z"] == 1)
+    assert decayed.sum() > 100
+    assert ((ref["generation"] > 0) & (ref["Z0"] == 0) & (ref["Z"] == 1)).sum() > 0
+    assert_chains_equal(gpu, ref)
+    for f in ("x", "u", "E", "s", "x0", "u0", "E0"):
+        assert np.max(rel_err(gpu[f], ref[f])) < 1e-9, f
+    mx, _, status = run_gpu(B, n, dx, inj, precision=crp.MIXED, dtype=crp.F32, tables=tables,
+                            flags=flags, observer_radius=1.0, **_interaction_kw())
+    assert status == crp.OK
+    prim_r, prim_m = ref[ref["generation"] == 0], mx[mx["generation"] == 0]
+    assert np.array_equal(prim_r["id"], prim_m["id"])
+    neutrons = (prim_r["A0"] == 1) & (prim_r["Z0"] == 0)
+    same = neutrons & (prim_r["status"] == prim_m["status"])
+    assert same.sum() > 0.9 * neutrons.sum()
+    assert np.mean(prim_r["Z"][same] == prim_m["Z"][same]) > 0.99
+
+
 def test_launch_configuration_does_not_change_results(field_f32_small, tables):
     n, dx, B = field_f32_small
     inj = _interaction_inputs(n_mixed=300, n_hot=100, seed=5)

@@ -422,6 +422,40 @@ def test_photodisintegration_branching_and_lineage(oracle):
     assert len(np.unique(r["id"])) == len(r)
 
 
+def test_neutron_decay_survival_and_products(oracle):
+    """Free-neutron beta decay.  The decay length is gamma c tau: the textbook
+    figure is 9.2 kpc per EeV for tau = 886 s, i.e. 9.12 kpc for the
+    878.4 s lifetime used here, so at that path length a fraction 1 - 1/e of
+    the neutrons has decayed.  A decay product is a proton of the neutron's
+    Lorentz factor; protons and nuclei never decay; each reset of the
+    interaction states draws one uniform per active module."""
+    n = 6000
+    E = 1e18
+    L = 9.2 * (878.4 / 886.0) * 1e-3  # Mpc
+    inj = _one(E, A=1, Z=0, n=n, s_max=L)
+    P = oracle.make_params(grid_n=(4, 4, 4), spacing=1.0, flags=oracle.DECAY, seed=12,
+                           h_max=0.1 * L, h_min=1e-6)
+    r = oracle.propagate(P, np.zeros((4, 4, 4, 3)), inj)
+    decayed = r["Z"] == 1
+    frac = decayed.mean()
+    p = 1 - math.exp(-1)
+    assert abs(frac - p) < 4 * math.sqrt(p * (1 - p) / n) + 0.003, frac
+    m_n, m_p = 939.56542052e6, 938.27208816e6  # CODATA 2018 [eV]
+    gam_before = r["E0"][decayed] / m_n
+    gam_after = r["E"][decayed] / m_p
+    assert np.max(np.abs(gam_after / gam_before - 1)) < 1e-15
+    assert np.all(r["E"][~decayed] == E) and np.all(r["A"] == 1)
+    assert np.all(r["draws"] == 1 + decayed)
+    assert np.all(r["s"] == L)
+    # protons and iron never decay; one uniform drawn at the start
+    inj2 = _one(1e19, A=1, Z=1, n=50, s_max=1.0)
+    inj3 = _one(1e20, A=56, Z=26, n=50, s_max=1.0)
+    for inj_x in (inj2, inj3):
+        r2 = oracle.propagate(P, np.zeros((4, 4, 4, 3)), inj_x)
+        assert np.all(r2["Z"] == inj_x["Z"]) and np.all(r2["E"] == inj_x["E"])
+        assert np.all(r2["draws"] == 1)
+
+
 def test_observer_sphere_straight_lines(oracle):
     """Neutral particles fly straight: detection iff the line passes within R."""
     g = np.random.default_rng(9)
