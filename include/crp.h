@@ -136,7 +136,12 @@ crp_status crp_grid_copy_out(const crp_grid* grid, double* host_out);
  *   beta_pair[i]: (1/E) dE/dx of a proton by pair production on a blackbody
  *     of temperature T_cmb, from Blumenthal, Phys. Rev. D 1, 1596 (1970)
  *     with the phi(kappa) fit of Chodorowski, Zdziarski & Sikora, ApJ 400,
- *     181 (1992); a nucleus (A, Z) loses (Z^2 / A) beta_pair(Gamma).
+ *     181 (1992); a nucleus (A, Z) loses (Z^2 / A) beta_pair(Gamma).  With
+ *     irb_dilution[k] > 0 the background also holds a synthetic infrared /
+ *     optical light of dilute blackbodies (temperature irb_T_K[k], photon
+ *     density irb_dilution[k] times Planck's); the loss is linear in the
+ *     photon density, so each adds irb_dilution[k] times the blackbody beta
+ *     at irb_T_K[k].
  *   rate_pion[i]: photo-pion rate of one nucleon for a step cross section
  *     pion_sigma above the rest-frame photon energy pion_eth; a nucleus has
  *     A times that rate.
@@ -151,6 +156,8 @@ typedef struct {
   double T_cmb;              /* blackbody temperature [K] */
   double pion_sigma_mb, pion_eth_eV;
   double gdr_peak_mb, gdr_center_eV, gdr_fwhm_eV, gdr_lo_eV, gdr_hi_eV;
+  double irb_T_K[2];         /* synthetic infrared / optical components [K] */
+  double irb_dilution[2];    /* their dilution factors (0 = absent) */
 } crp_tables_desc;
 
 /* Compute the tables on the device (quadrature kernels). */

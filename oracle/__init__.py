@@ -122,7 +122,8 @@ def lib():
             L.orc_rate_gdr_nucleon.argtypes = [d, d, d, d, d, d, d]
             L.orc_rate_gdr_nucleon.restype = d
             L.orc_cash_karp_tableau.argtypes = [p]
-            L.orc_tables_build.argtypes = [i64, d, d, d, d, d, d, d, d, d, d, d, p, p, p, C.c_int]
+            L.orc_tables_build.argtypes = [i64, d, d, d, d, d, d, d, d, d, d, d, p, p, p, C.c_int,
+                                           C.c_int, p, p]
             L.orc_turbulence_modes.argtypes = [i64, i64, i64, d, d, d, d, u64, p]
             L.orc_propagate.argtypes = [C.POINTER(Params), p, p, p, p, i64] + [p] * 12 + \
                 [p, i64, C.POINTER(i64), C.c_int]
@@ -270,12 +271,18 @@ class Tables:
 
 def tables_build(n=1000, g_lo=1e6, g_hi=1e13, length_unit_m=MPC_M, T=2.725,
                  pion_sigma_mb=0.5, pion_eth_eV=145e6, gdr_peak_mb=1.5, gdr_ec_eV=20e6,
-                 gdr_fwhm_eV=6e6, gdr_lo_eV=8e6, gdr_hi_eV=150e6, nthreads=None) -> Tables:
+                 gdr_fwhm_eV=6e6, gdr_lo_eV=8e6, gdr_hi_eV=150e6, nthreads=None,
+                 irb=()) -> Tables:
+    """irb: ((T_k [K], dilution_k), ...) dilute blackbodies added to the
+    pair-production background (the synthetic infrared / optical light)."""
     nthreads = nthreads or os.cpu_count() or 1
     bp, rp, rg = np.zeros(n), np.zeros(n), np.zeros(n)
+    irb_T = np.array([t for t, _ in irb] or [0.0], dtype=np.float64)
+    irb_D = np.array([d for _, d in irb] or [0.0], dtype=np.float64)
     lib().orc_tables_build(n, g_lo, g_hi, length_unit_m, T, pion_sigma_mb, pion_eth_eV,
                            gdr_peak_mb, gdr_ec_eV, gdr_fwhm_eV, gdr_lo_eV, gdr_hi_eV,
-                           _ptr(bp), _ptr(rp), _ptr(rg), int(nthreads))
+                           _ptr(bp), _ptr(rp), _ptr(rg), int(nthreads), len(irb),
+                           _ptr(irb_T), _ptr(irb_D))
     return Tables(n, g_lo, g_hi, bp, rp, rg)
 
 

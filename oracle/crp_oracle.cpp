@@ -606,19 +606,26 @@ void orc_cash_karp_tableau(double* out) {
 }
 
 // Rate tables on n nodes uniform in ln(Gamma) over [ln g_lo, ln g_hi], in
-// units of 1/length_unit_m.  Pair: Blumenthal beta for a proton.  Pion:
-// nucleon rate for the step cross section.  GDR: per-nucleon rate.
+// units of 1/length_unit_m.  Pair: Blumenthal beta for a proton on the CMB
+// plus, for a synthetic infrared / optical background of n_irb dilute
+// blackbodies (temperature irb_T[k], dilution irb_D[k]), sum_k D_k times the
+// blackbody beta at T_k (the loss rate is linear in the photon density).
+// Pion: nucleon rate for the step cross section.  GDR: per-nucleon rate.
 void orc_tables_build(int64_t n, double g_lo, double g_hi, double length_unit_m, double T_cmb,
                       double pion_sigma_mb, double pion_eth_eV,
                       double gdr_peak_mb, double gdr_ec_eV, double gdr_fwhm_eV,
                       double gdr_lo_eV, double gdr_hi_eV,
-                      double* beta_pair, double* rate_pion, double* rate_gdr, int nthreads) {
+                      double* beta_pair, double* rate_pion, double* rate_gdr, int nthreads,
+                      int n_irb, const double* irb_T, const double* irb_D) {
   double kT = kKB * T_cmb;
   double lg0 = std::log(g_lo), lg1 = std::log(g_hi);
   auto work = [&](int64_t i0, int64_t i1) {
     for (int64_t i = i0; i < i1; ++i) {
       double gamma = std::exp(lg0 + (lg1 - lg0) * (double)i / (double)(n - 1));
-      beta_pair[i] = beta_pair_proton(gamma, kT) * length_unit_m;
+      double b = beta_pair_proton(gamma, kT);
+      for (int k = 0; k < n_irb; ++k)
+        if (irb_D[k] > 0.0) b = b + irb_D[k] * beta_pair_proton(gamma, kKB * irb_T[k]);
+      beta_pair[i] = b * length_unit_m;
       rate_pion[i] = rate_pion_nucleon(gamma, kT, pion_sigma_mb * kMillibarn, pion_eth_eV) * length_unit_m;
       rate_gdr[i] = rate_gdr_nucleon(gamma, kT, gdr_peak_mb * kMillibarn, gdr_ec_eV, 0.5 * gdr_fwhm_eV,
                                      gdr_lo_eV, gdr_hi_eV) * length_unit_m;

@@ -51,7 +51,8 @@ class TablesDesc(C.Structure):
                 ("length_unit_m", C.c_double), ("T_cmb", C.c_double),
                 ("pion_sigma_mb", C.c_double), ("pion_eth_eV", C.c_double),
                 ("gdr_peak_mb", C.c_double), ("gdr_center_eV", C.c_double),
-                ("gdr_fwhm_eV", C.c_double), ("gdr_lo_eV", C.c_double), ("gdr_hi_eV", C.c_double)]
+                ("gdr_fwhm_eV", C.c_double), ("gdr_lo_eV", C.c_double), ("gdr_hi_eV", C.c_double),
+                ("irb_T_K", C.c_double * 2), ("irb_dilution", C.c_double * 2)]
 
 
 class CandidateArrays(C.Structure):
@@ -542,12 +543,16 @@ def grid_desc(n, spacing, origin=(0.0, 0.0, 0.0), dtype=F64, source=GRID_FROM_HO
 
 def tables_desc(n=1000, gamma_lo=1e6, gamma_hi=1e13, length_unit_m=MPC_M, T_cmb=2.725,
                 pion_sigma_mb=0.5, pion_eth_eV=145e6, gdr_peak_mb=1.5, gdr_center_eV=20e6,
-                gdr_fwhm_eV=6e6, gdr_lo_eV=8e6, gdr_hi_eV=150e6):
+                gdr_fwhm_eV=6e6, gdr_lo_eV=8e6, gdr_hi_eV=150e6, irb=()):
+    """irb: up to two (T [K], dilution) dilute blackbodies added to the pair-
+    production background (synthetic infrared / optical light)."""
     d = TablesDesc()
     d.n, d.gamma_lo, d.gamma_hi, d.length_unit_m, d.T_cmb = n, gamma_lo, gamma_hi, length_unit_m, T_cmb
     d.pion_sigma_mb, d.pion_eth_eV = pion_sigma_mb, pion_eth_eV
     d.gdr_peak_mb, d.gdr_center_eV, d.gdr_fwhm_eV = gdr_peak_mb, gdr_center_eV, gdr_fwhm_eV
     d.gdr_lo_eV, d.gdr_hi_eV = gdr_lo_eV, gdr_hi_eV
+    for k, (T, D) in enumerate(irb):
+        d.irb_T_K[k], d.irb_dilution[k] = T, D
     return d
 
 

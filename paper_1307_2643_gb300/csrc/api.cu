@@ -751,6 +751,12 @@ static crp_status tables_check(const crp_tables_desc* d) {
     set_error("tables: need n >= 2, 0 < gamma_lo < gamma_hi, length_unit_m > 0");
     return CRP_E_INVALID;
   }
+  for (int k = 0; k < 2; ++k) {
+    if (!(d->irb_dilution[k] >= 0.0) || (d->irb_dilution[k] > 0.0 && !(d->irb_T_K[k] > 0.0))) {
+      set_error("tables: background component %d needs dilution >= 0 and T > 0", k);
+      return CRP_E_INVALID;
+    }
+  }
   return CRP_OK;
 }
 

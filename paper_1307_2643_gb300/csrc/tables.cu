@@ -145,7 +145,11 @@ __global__ void k_tables(crp_tables_desc d, const GLRule gl, double* beta, doubl
   const double gamma = exp(l0 + (l1 - l0) * (double)i / (double)(d.n - 1));
   const double kT = kBoltz * d.T_cmb;
   const double mb = 1.0e-31;
-  beta[i] = beta_pair_dev(gl, gamma, kT) * d.length_unit_m;
+  double b = beta_pair_dev(gl, gamma, kT);
+  for (int k = 0; k < 2; ++k)  // synthetic infrared / optical components
+    if (d.irb_dilution[k] > 0.0)
+      b = b + d.irb_dilution[k] * beta_pair_dev(gl, gamma, kBoltz * d.irb_T_K[k]);
+  beta[i] = b * d.length_unit_m;
   pion[i] = rate_pion_dev(gamma, kT, d.pion_sigma_mb * mb, d.pion_eth_eV) * d.length_unit_m;
   gdr[i] = rate_gdr_dev(gl, gamma, kT, d.gdr_peak_mb * mb, d.gdr_center_eV, 0.5 * d.gdr_fwhm_eV,
                         d.gdr_lo_eV, d.gdr_hi_eV) * d.length_unit_m;

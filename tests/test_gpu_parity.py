@@ -97,6 +97,50 @@ def test_tables_match_oracle(tables):
         assert np.max(rel_err(got[live], ref[live], floor=0.0)) < 1e-8
 
 
+def test_tables_with_synthetic_infrared_background_match_oracle():
+    """Pair table with the synthetic infrared / optical background (two dilute
+    blackbodies) built on the device against the oracle's, and the
+    propagation with it: FP64 path bit-exact with the oracle."""
+    irb = ((35.0, 8.5e-7), (4500.0, 3.1e-15))
+    ref = oracle.tables_build(n=400, irb=irb)
+    ctx = crp.crp_context_create(0, 1, 16)
+    try:
+        t = crp.crp_tables_build(ctx, crp.tables_desc(n=400, irb=irb))
+        beta, pion, gdr = crp.crp_tables_copy_out(t, 400)
+        crp.crp_tables_destroy(t)
+        with pytest.raises(crp.CrpError):
+            crp.crp_tables_build(ctx, crp.tables_desc(n=400, irb=((0.0, 1e-6),)))
+    finally:
+        crp.crp_context_destroy(ctx)
+    live = ref.beta_pair > 1e-200 * ref.beta_pair.max()
+    assert np.max(rel_err(beta[live], ref.beta_pair[live], floor=0.0)) < 1e-8
+    assert np.max(rel_err(pion, ref.rate_pion, floor=1e-300)) < 1e-8
+    # propagation with the background: protons of 1e17-1e18.5 eV, where the
+    # infrared light dominates the pair losses
+    n, dx = (16, 16, 16), 0.5
+    B = oracle.turbulent_field(n, dx, 1.0, 4.0, 1.0, seed=3)
+    g = np.random.default_rng(8)
+    m = 500
+    v = g.normal(size=(m, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    inj = dict(id=np.arange(m, dtype=np.uint64), x=np.zeros(m), y=np.zeros(m), z=np.zeros(m),
+               ux=v[:, 0].copy(), uy=v[:, 1].copy(), uz=v[:, 2].copy(),
+               E=10 ** g.uniform(17, 18.5, m), A=np.ones(m, np.int32), Z=np.ones(m, np.int32),
+               q=np.ones(m, np.int32), s_max=np.full(m, 30.0))
+    kw = dict(tol=1e-4, h_min=0.01, h_max=1.0)
+    P = oracle_params(n, dx, tables=ref, flags=oracle.PAIR, **kw)
+    r_irb = oracle.propagate(P, B, inj, tables=ref)
+    gpu, _, status = run_gpu(B, n, dx, inj, precision=crp.FP64, tables=ref, flags=crp.PAIR, **kw)
+    assert status == crp.OK
+    assert_chains_equal(gpu, r_irb)
+    for f in ("x", "u", "E", "s"):
+        assert np.max(rel_err(gpu[f], r_irb[f])) < 1e-9, f
+    plain = oracle.tables_build(n=400)
+    r_cmb = oracle.propagate(oracle_params(n, dx, tables=plain, flags=oracle.PAIR, **kw), B, inj,
+                             tables=plain)
+    assert np.all(r_irb["E"] <= r_cmb["E"]) and np.mean(r_irb["E"] < r_cmb["E"]) > 0.9
+
+
 # ---------------------------------------------------------------------------
 # FP64 path: bit-level agreement expected (same operation order, no FMA)
 # ---------------------------------------------------------------------------

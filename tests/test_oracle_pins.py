@@ -654,3 +654,38 @@ def test_adam_first_step_and_bf16_rounding(oracle):
     vals = M.bf16_round([1.0, 1 + 2 ** -8, 1 + 3 * 2 ** -8, -3.0e-3, 65504.0])
     assert vals[0] == 1.0 and vals[1] == 1.0 and vals[2] == 1 + 2 ** -6
     assert abs(vals[3] / -3.0e-3 - 1) < 2 ** -8
+
+
+def test_pair_loss_blackbody_temperature_scaling(oracle):
+    """For a Planck photon gas the Blumenthal loss depends on Gamma and T only
+    through Gamma T and an overall T^3 (substitute eps = kappa m_e c^2 / 2 Gamma
+    in the integral): beta(Gamma, T) = (T / T0)^3 beta(Gamma T / T0, T0)."""
+    T0 = 2.725
+    for T in (35.0, 4500.0):
+        for g in (3e5, 2e7, 1e9):
+            lhs = oracle.lib().orc_beta_pair_proton(g, T)
+            rhs = (T / T0) ** 3 * oracle.lib().orc_beta_pair_proton(g * T / T0, T0)
+            assert lhs > 0 and abs(lhs / rhs - 1) < 1e-8, (T, g, lhs, rhs)
+
+
+def test_pair_table_with_synthetic_infrared_background(oracle):
+    """The pair table with a background of dilute blackbodies equals the CMB
+    table plus sum_k D_k (T_k / T0)^3 beta_CMB(Gamma T_k / T0) (linearity in the
+    photon density plus the temperature scaling); the background matters only
+    below the CMB threshold region."""
+    irb = ((35.0, 8.5e-7), (4500.0, 3.1e-15))
+    n, g_lo, g_hi = 60, 1e6, 1e13
+    Tc = oracle.tables_build(n=n, g_lo=g_lo, g_hi=g_hi)
+    Ti = oracle.tables_build(n=n, g_lo=g_lo, g_hi=g_hi, irb=irb)
+    gam = np.exp(np.linspace(np.log(g_lo), np.log(g_hi), n))
+    extra = np.zeros(n)
+    for T, D in irb:
+        extra += D * (T / 2.725) ** 3 * np.array(
+            [oracle.lib().orc_beta_pair_proton(g * T / 2.725, 2.725) for g in gam])
+    extra *= oracle.MPC_M
+    assert np.allclose(Ti.beta_pair, Tc.beta_pair + extra, rtol=1e-8, atol=0)
+    # the infrared light adds losses below the CMB pair threshold and is
+    # negligible at the top of the range
+    assert Ti.beta_pair[5] > 1.5 * Tc.beta_pair[5]
+    assert Ti.beta_pair[-1] < 1.01 * Tc.beta_pair[-1]
+    assert np.array_equal(Ti.rate_pion, Tc.rate_pion)
