@@ -1151,3 +1151,349 @@ void orc_field_at(const orc_params* P, const double* grid, int64_t n, const doub
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// 1D mode with cosmology and the a-posteriori 3D cosmology correction
+// (Sect. 2 lists the 1D mode with cosmological effects; Sect. 4 "Cosmology in
+// 3D" gives the correction).  Readings, each stated once here:
+//  * flat Lambda-CDM: H(z) = H0 sqrt(Om (1+z)^3 + OL); lengths comoving;
+//  * the candidate moves toward the observer, its redshift falling to 0; a
+//    step is a redshift decrement dz, its comoving length dz / H(z - dz/2)
+//    (midpoint rule; H per length unit, i.e. H/c);
+//  * adiabatic loss: the exact redshift factor E <- E (1+z') / (1+z);
+//  * pair loss and interaction rates from the z = 0 tables: per comoving
+//    length (1+z)^2 rate((1+z) Gamma) (photon density (1+z)^3, energies
+//    (1+z), proper length = comoving / (1+z)); neutron decay 1 / ((1+z)
+//    gamma c tau);
+//  * stochastic states are remaining optical depths tau = -ln(u), reduced by
+//    rate * length; a step is capped where a depth would run out (the event
+//    then happens at its end), by dz_max, by a relative pair loss loss_max,
+//    and by z itself;
+//  * events, secondaries and lineage ids as in 3D; arrival at z = 0 is
+//    status "detected";
+//  * the correction places the 1D source at the redshift whose comoving
+//    distance is the 3D trajectory length (3D coordinates are comoving).
+// ===========================================================================
+struct orc_params1d {
+  uint32_t flags;     // ORC_PAIR | ORC_ADIABATIC | ORC_PION | ORC_PHOTODIS | ORC_EMIN | ORC_DECAY
+  uint32_t pad0;
+  uint64_t seed;
+  double e_min;       // [eV]
+  double H0;          // Hubble constant / c [1 / length unit]
+  double omega_m, omega_l;
+  double dz_max;      // largest redshift step
+  double loss_max;    // largest relative pair loss per step
+  double tab_lg0, tab_inv_dlg;
+  int64_t tab_n;
+  double length_unit_m;
+  int64_t max_steps;
+};
+
+namespace {
+
+const uint32_t kTagCosmology = 5;
+
+struct Ctx1d {
+  const orc_params1d* P;
+  const double* t_beta;
+  const double* t_pion;
+  const double* t_gdr;
+};
+
+double hubble(const orc_params1d& P, double z) {
+  const double a = 1.0 + z;
+  return P.H0 * std::sqrt(P.omega_m * a * a * a + P.omega_l);
+}
+
+double lookup1d(const orc_params1d& P, const double* tab, double lng) {
+  double t = (lng - P.tab_lg0) * P.tab_inv_dlg;
+  double tmax = (double)(P.tab_n - 1);
+  if (t < 0.0) t = 0.0;
+  if (t > tmax) t = tmax;
+  int64_t i = (int64_t)std::floor(t);
+  if (i > P.tab_n - 2) i = P.tab_n - 2;
+  double f = t - (double)i;
+  return tab[i] + f * (tab[i + 1] - tab[i]);
+}
+
+double draw1d(const Ctx1d& C, Cand& c) {
+  Words4 w = draw_words(C.P->seed, kTagInteraction, c.id, c.draws);
+  c.draws += 1;
+  return uniform_open(w.w[0], w.w[1]);
+}
+
+// optical depths in module order [pion, photodisintegration, decay]
+void reset1d(const Ctx1d& C, Cand& c) {
+  const uint32_t f = C.P->flags;
+  if (f & ORC_PION) c.d_pion = -series_log(draw1d(C, c));
+  if (f & ORC_PHOTODIS) c.d_pd = -series_log(draw1d(C, c));
+  if (f & ORC_DECAY) c.d_dec = -series_log(draw1d(C, c));
+  c.states_drawn = true;
+}
+
+struct Rates1d {
+  double beta, pion, pd, dec;  // per comoving length
+};
+
+Rates1d rates1d(const Ctx1d& C, const Cand& c, double z) {
+  const orc_params1d& P = *C.P;
+  Rates1d r = {0.0, 0.0, 0.0, 0.0};
+  const double a = 1.0 + z;
+  const double lng = series_log(a * gamma_of(c));
+  if (P.flags & ORC_PAIR)
+    r.beta = a * a * lookup1d(P, C.t_beta, lng) * (double)(c.Z * c.Z) / (double)c.A;
+  if (P.flags & ORC_PION) r.pion = a * a * (double)c.A * lookup1d(P, C.t_pion, lng);
+  if ((P.flags & ORC_PHOTODIS) && c.A >= 2)
+    r.pd = a * a * (double)c.A * lookup1d(P, C.t_gdr, lng);
+  if ((P.flags & ORC_DECAY) && c.A == 1 && c.Z == 0) {
+    const double k = kC * kTauN / kMnC2 / P.length_unit_m;
+    r.dec = 1.0 / (a * c.E * k);
+  }
+  return r;
+}
+
+void propagate_one_1d(const Ctx1d& C, Cand& c, std::vector<Cand>& out_secondaries) {
+  const orc_params1d& P = *C.P;
+  const bool pion_on = (P.flags & ORC_PION) != 0;
+  const bool pd_on = (P.flags & ORC_PHOTODIS) != 0;
+  const bool dec_on = (P.flags & ORC_DECAY) != 0;
+  while (c.status == ORC_ACTIVE) {
+    if ((pion_on || pd_on || dec_on) && !c.states_drawn) reset1d(C, c);
+    const double z = c.x[0];
+    const Rates1d r = rates1d(C, c, z);
+    const double H = hubble(P, z);
+    // redshift step: the smallest cap (0: none, 1: z, 2: pion, 3: pd, 4: decay)
+    double dz = P.dz_max;
+    int cap = 0;
+    if (r.beta > 0.0 && P.loss_max * H / r.beta < dz) dz = P.loss_max * H / r.beta;
+    if (z <= dz) {
+      dz = z;
+      cap = 1;
+    }
+    if (pion_on && r.pion > 0.0 && c.d_pion * H / r.pion < dz) {
+      dz = c.d_pion * H / r.pion;
+      cap = 2;
+    }
+    if (pd_on && r.pd > 0.0 && c.d_pd * H / r.pd < dz) {
+      dz = c.d_pd * H / r.pd;
+      cap = 3;
+    }
+    if (dec_on && r.dec > 0.0 && c.d_dec * H / r.dec < dz) {
+      dz = c.d_dec * H / r.dec;
+      cap = 4;
+    }
+    const double z1 = cap == 1 ? 0.0 : z - dz;
+    const double h = dz / hubble(P, z - 0.5 * dz);  // comoving length of the step
+    // continuous losses: pair (explicit, start-of-step rate), then the exact
+    // adiabatic redshift factor
+    if (P.flags & ORC_PAIR) c.E = c.E * (1.0 - r.beta * h);
+    if (P.flags & ORC_ADIABATIC) c.E = c.E * ((1.0 + z1) / (1.0 + z));
+    c.x[0] = z1;
+    c.s = c.s + h;
+    c.n_acc += 1;
+    // optical depths
+    if (pion_on) c.d_pion = cap == 2 ? 0.0 : c.d_pion - r.pion * h;
+    if (pd_on) c.d_pd = cap == 3 ? 0.0 : c.d_pd - r.pd * h;
+    if (dec_on) c.d_dec = cap == 4 ? 0.0 : c.d_dec - r.dec * h;
+    if (pion_on && c.d_pion <= 0.0) {
+      c.E = c.E - 0.2 * c.E / (double)c.A;
+      c.n_pion += 1;
+      c.events += 1;
+      reset1d(C, c);
+    } else if (pd_on && c.A >= 2 && c.d_pd <= 0.0) {
+      double u = draw1d(C, c);
+      bool proton = u < (double)c.Z / (double)c.A;
+      int Ad = c.A - 1;
+      if (proton && Ad >= 2 && c.Z - 1 == 0) proton = false;
+      if (!proton && Ad >= 2 && Ad - c.Z == 0) proton = true;
+      double En = c.E / (double)c.A;
+      double Ed = c.E * (double)Ad / (double)c.A;
+      Cand sec = make_secondary(c, 1, proton ? 1 : 0, En, 0.0);
+      sec.x[0] = c.x[0];
+      sec.x0[0] = c.x[0];
+      if (!(P.flags & ORC_EMIN) || En >= P.e_min)
+        out_secondaries.push_back(sec);
+      else
+        c.n_dropped += 1;
+      c.A = Ad;
+      c.Z = c.Z - (proton ? 1 : 0);
+      c.E = Ed;
+      c.n_pd += 1;
+      c.events += 1;
+      reset1d(C, c);
+    } else if (dec_on && c.A == 1 && c.Z == 0 && c.d_dec <= 0.0) {
+      c.Z = 1;
+      c.E = c.E * (kMpC2 / kMnC2);
+      c.events += 1;
+      reset1d(C, c);
+    }
+    if ((P.flags & ORC_EMIN) && c.E < P.e_min)
+      c.status = ORC_BELOW_EMIN;
+    else if (c.x[0] <= 0.0)
+      c.status = ORC_DETECTED;
+    if (c.status == ORC_ACTIVE && (int64_t)c.n_acc >= P.max_steps) c.status = ORC_BUDGET;
+  }
+}
+
+// Comoving distance (length units) to redshift z: integral of dz' / H(z')
+// (H per length unit) by composite Simpson with 4096 panels.
+double comoving_distance(const orc_params1d& P, double z) {
+  const int n = 4096;
+  const double w = z / n;
+  auto f = [&](double x) { return 1.0 / hubble(P, x); };
+  double sum = f(0.0) + f(z);
+  for (int i = 1; i < n; ++i) sum += (i % 2 ? 4.0 : 2.0) * f(i * w);
+  return sum * w / 3.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+// 1D propagation of n primaries from redshifts z_src (and every secondary,
+// depth first).  Records: x[0] = final redshift, x0[0] = starting redshift,
+// s = comoving length travelled, u = 0.  Return codes as orc_propagate.
+int orc_propagate_1d(const orc_params1d* P, const double* t_beta, const double* t_pion,
+                     const double* t_gdr, int64_t n, const uint64_t* id, const double* z_src,
+                     const double* E, const int32_t* A, const int32_t* Z, orc_record* out,
+                     int64_t out_cap, int64_t* n_out, int nthreads) {
+  if (!P || n < 0 || !n_out) return -2;
+  Ctx1d C = {P, t_beta, t_pion, t_gdr};
+  if (nthreads < 1) nthreads = 1;
+  std::vector<std::vector<orc_record>> per(n);
+  std::atomic<int64_t> next(0);
+  auto worker = [&]() {
+    std::vector<Cand> stack;
+    for (;;) {
+      int64_t i = next.fetch_add(1);
+      if (i >= n) break;
+      Cand c;
+      std::memset(&c, 0, sizeof(c));
+      c.id = id[i];
+      c.x[0] = z_src[i];
+      c.x0[0] = z_src[i];
+      c.E = E[i];
+      c.E0 = E[i];
+      c.A = A[i];
+      c.Z = Z[i];
+      c.A0 = A[i];
+      c.Z0 = Z[i];
+      c.q = 1;
+      c.status = ORC_ACTIVE;
+      stack.clear();
+      stack.push_back(c);
+      while (!stack.empty()) {
+        Cand cur = stack.back();
+        stack.pop_back();
+        std::vector<Cand> secs;
+        propagate_one_1d(C, cur, secs);
+        orc_record r;
+        to_record(cur, r);
+        per[i].push_back(r);
+        for (auto& s : secs) stack.push_back(s);
+      }
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 0; t < nthreads; ++t) th.emplace_back(worker);
+  for (auto& t : th) t.join();
+  int64_t total = 0;
+  for (auto& v : per) total += (int64_t)v.size();
+  *n_out = total;
+  if (total > out_cap) return -1;
+  int64_t k = 0;
+  for (auto& v : per)
+    for (auto& r : v) out[k++] = r;
+  return 0;
+}
+
+// Comoving distance (length units) to each redshift.
+void orc_comoving_distance(const orc_params1d* P, int64_t n, const double* z, double* out) {
+  for (int64_t i = 0; i < n; ++i) out[i] = comoving_distance(*P, z[i]);
+}
+
+// Redshift at comoving distance D (bisection to 1e-15 relative).
+void orc_redshift_of_distance(const orc_params1d* P, int64_t n, const double* D, double* out) {
+  for (int64_t i = 0; i < n; ++i) {
+    double lo = 0.0, hi = 1.0;
+    while (comoving_distance(*P, hi) < D[i] && hi < 1e6) hi *= 2.0;
+    for (int it = 0; it < 200 && hi - lo > 1e-15 * hi; ++it) {
+      double mid = 0.5 * (lo + hi);
+      if (comoving_distance(*P, mid) < D[i])
+        lo = mid;
+      else
+        hi = mid;
+    }
+    out[i] = 0.5 * (lo + hi);
+  }
+}
+
+// The a-posteriori correction (Sect. 4): particle i (id, injected E, A, Z)
+// is re-propagated in 1D from redshift z_src[i]; of its products that reach
+// z = 0, ordered by id, product k = min(floor(u n_k), n_k - 1) is taken, u
+// from Philox tag 5, counter (0, id).  Outputs its E, A, Z and n_k (0: no
+// product reaches the observer; E, A, Z then 0).
+int orc_cosmology_pick(const orc_params1d* P, const double* t_beta, const double* t_pion,
+                       const double* t_gdr, int64_t n, const uint64_t* id, const double* z_src,
+                       const double* E, const int32_t* A, const int32_t* Z, double* E_out,
+                       int32_t* A_out, int32_t* Z_out, int32_t* n_products, int nthreads) {
+  if (!P || n < 0) return -2;
+  Ctx1d C = {P, t_beta, t_pion, t_gdr};
+  if (nthreads < 1) nthreads = 1;
+  std::atomic<int64_t> next(0);
+  auto worker = [&]() {
+    std::vector<Cand> stack;
+    std::vector<Cand> arrived;
+    for (;;) {
+      int64_t i = next.fetch_add(1);
+      if (i >= n) break;
+      Cand c;
+      std::memset(&c, 0, sizeof(c));
+      c.id = id[i];
+      c.x[0] = z_src[i];
+      c.x0[0] = z_src[i];
+      c.E = E[i];
+      c.E0 = E[i];
+      c.A = A[i];
+      c.Z = Z[i];
+      c.A0 = A[i];
+      c.Z0 = Z[i];
+      c.q = 1;
+      c.status = ORC_ACTIVE;
+      stack.clear();
+      arrived.clear();
+      stack.push_back(c);
+      while (!stack.empty()) {
+        Cand cur = stack.back();
+        stack.pop_back();
+        std::vector<Cand> secs;
+        propagate_one_1d(C, cur, secs);
+        if (cur.status == ORC_DETECTED) arrived.push_back(cur);
+        for (auto& s : secs) stack.push_back(s);
+      }
+      std::sort(arrived.begin(), arrived.end(),
+                [](const Cand& a, const Cand& b) { return a.id < b.id; });
+      const int64_t nk = (int64_t)arrived.size();
+      n_products[i] = (int32_t)nk;
+      if (nk == 0) {
+        E_out[i] = 0.0;
+        A_out[i] = 0;
+        Z_out[i] = 0;
+        continue;
+      }
+      Words4 w = draw_words(P->seed, kTagCosmology, c.id, 0);
+      const double u = uniform_open(w.w[0], w.w[1]);
+      int64_t k = (int64_t)std::floor(u * (double)nk);
+      if (k > nk - 1) k = nk - 1;
+      E_out[i] = arrived[k].E;
+      A_out[i] = arrived[k].A;
+      Z_out[i] = arrived[k].Z;
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 0; t < nthreads; ++t) th.emplace_back(worker);
+  for (auto& t : th) t.join();
+  return 0;
+}
+
+}  // extern "C"

@@ -689,3 +689,100 @@ def test_pair_table_with_synthetic_infrared_background(oracle):
     assert Ti.beta_pair[5] > 1.5 * Tc.beta_pair[5]
     assert Ti.beta_pair[-1] < 1.01 * Tc.beta_pair[-1]
     assert np.array_equal(Ti.rate_pion, Tc.rate_pion)
+
+
+# ---------------------------------------------------------------------------
+# 1D mode with cosmology (flat Lambda-CDM, H0 = 67.3, Om = 0.315)
+# ---------------------------------------------------------------------------
+def _cosmo(oracle):
+    import oracle.cosmology as cm
+    return cm
+
+
+def test_1d_adiabatic_only_is_pure_redshift(oracle):
+    """Adiabatic expansion alone: the observed energy is E_src / (1 + z_src)
+    (photon-like redshift of an ultrarelativistic particle), and arrival is
+    at z = 0 after the comoving distance to z_src."""
+    cm = _cosmo(oracle)
+    from scipy.integrate import quad
+    P = cm.make_params1d(flags=oracle.ADIABATIC, dz_max=1e-3)
+    zs = np.array([0.01, 0.3, 1.0, 2.5])
+    inj = dict(id=np.arange(4, dtype=np.uint64), z=zs, E=np.full(4, 1e20),
+               A=np.ones(4, np.int32), Z=np.ones(4, np.int32))
+    r = cm.propagate_1d(P, inj)
+    assert np.all(r["status"] == oracle.DETECTED) and np.all(r["x"][:, 0] == 0.0)
+    assert np.max(np.abs(r["E"] * (1 + zs) / 1e20 - 1)) < 1e-14
+    # comoving distance against a library quadrature of c / H(z)
+    H0 = cm.H0_KM_S_MPC / cm.C_KM_S
+    Dc = np.array([quad(lambda x: 1 / (H0 * np.sqrt(0.315 * (1 + x) ** 3 + 0.685)), 0, z,
+                        epsabs=0, epsrel=1e-12)[0] for z in zs])
+    assert np.max(np.abs(r["s"] / Dc - 1)) < 1e-6
+
+
+def test_1d_comoving_distance(oracle):
+    """Comoving distance c int dz / H against a library quadrature, and its
+    inverse; 4000 Mpc comoving is z ~ 1.35 for these parameters."""
+    cm = _cosmo(oracle)
+    from scipy.integrate import quad
+    P = cm.make_params1d()
+    H0 = cm.H0_KM_S_MPC / cm.C_KM_S
+    zs = np.array([1e-3, 0.1, 0.5, 1.4, 3.0])
+    ref = np.array([quad(lambda x: 1 / (H0 * np.sqrt(0.315 * (1 + x) ** 3 + 0.685)),
+                         0, z, epsabs=0, epsrel=1e-13)[0] for z in zs])
+    got = cm.comoving_distance(P, zs)
+    assert np.max(np.abs(got / ref - 1)) < 1e-11
+    back = cm.redshift_of_distance(P, got)
+    assert np.max(np.abs(back / zs - 1)) < 1e-12
+    z4000 = cm.redshift_of_distance(P, [4000.0])[0]
+    assert 1.2 < z4000 < 1.5
+
+
+def test_1d_pair_loss_rate_is_hotter_cmb(oracle):
+    """At redshift z the CMB is a blackbody at T0 (1 + z): over a tiny step
+    the 1D relative pair loss per proper length equals the blackbody loss rate
+    at that temperature (direct quadrature), to the table's interpolation."""
+    cm = _cosmo(oracle)
+    T = oracle.tables_build(n=2000, g_lo=1e8, g_hi=1e13)
+    for z in (0.5, 2.0):
+        P = cm.make_params1d(tables=T, flags=oracle.PAIR, dz_max=1e-7, loss_max=1.0,
+                             max_steps=1)
+        E = 3e19
+        inj = dict(id=np.zeros(1, np.uint64), z=np.array([z]), E=np.array([E]),
+                   A=np.ones(1, np.int32), Z=np.ones(1, np.int32))
+        r = cm.propagate_1d(P, inj, tables=T)
+        dz = z - r["x"][0, 0]
+        h_com = r["s"][0]
+        proper = h_com / (1 + z)
+        loss = (1 - r["E"][0] / E) / proper                       # per proper Mpc
+        g = E / oracle.MP_C2_EV
+        direct = oracle.lib().orc_beta_pair_proton(g, 2.725 * (1 + z)) * oracle.MPC_M
+        assert dz > 0 and abs(loss / direct - 1) < 2e-4, (z, loss, direct)
+
+
+def test_1d_pion_optical_depth(oracle):
+    """Protons injected at z_src reach the observer without a pion event with
+    probability exp(-tau), tau = int (1+z)^2 R((1+z) Gamma(z)) dD_c (energy
+    redshifting only), here from a library quadrature of the same tables."""
+    cm = _cosmo(oracle)
+    from scipy.integrate import quad
+    T = oracle.tables_build(n=400, g_lo=1e9, g_hi=1e13)
+    n = 6000
+    z_src, E_src = 0.002, 1e20
+    P = cm.make_params1d(tables=T, flags=oracle.PION | oracle.ADIABATIC, seed=3, dz_max=1e-5)
+    inj = dict(id=np.arange(n, dtype=np.uint64), z=np.full(n, z_src), E=np.full(n, E_src),
+               A=np.ones(n, np.int32), Z=np.ones(n, np.int32))
+    r = cm.propagate_1d(P, inj, tables=T)
+    none = np.mean(r["n_pion"] == 0)
+    H0 = cm.H0_KM_S_MPC / cm.C_KM_S
+    lng = np.linspace(np.log(1e9), np.log(1e13), 400)
+
+    def integrand(z):
+        E = E_src * (1 + z) / (1 + z_src)
+        g = (1 + z) * E / oracle.MP_C2_EV
+        R = np.interp(np.log(g), lng, T.rate_pion)
+        return (1 + z) ** 2 * R / (H0 * np.sqrt(0.315 * (1 + z) ** 3 + 0.685))
+
+    tau = quad(integrand, 0, z_src, epsrel=1e-10)[0]
+    p = np.exp(-tau)
+    assert 0.2 < p < 0.9
+    assert abs(none - p) < 4 * np.sqrt(p * (1 - p) / n) + 2e-3, (none, p)
