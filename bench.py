@@ -54,12 +54,15 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--graph", action="store_true",
                     help="run each propagation's round loop as one captured CUDA graph")
-    ap.add_argument("--workload", choices=("mixed", "galactic", "uneven", "e2e"), default="mixed",
+    ap.add_argument("--workload", choices=("mixed", "galactic", "uneven", "e2e", "cosmology"),
+                    default="mixed",
                     help="mixed: the propagation benchmark; galactic: back-tracking, MLP "
                          "surrogate training / inference and lens builds; uneven: 10^7 "
                          "candidates, 512^3 grid, photodisintegration secondaries, log-uniform "
                          "path lengths; e2e: 10^8 candidates through the mixed workload's "
-                         "field, then the galactic lens and its surrogate")
+                         "field, then the galactic lens and its surrogate; cosmology: 1D mode "
+                         "with cosmology and the a-posteriori 3D correction (sources to "
+                         "4000 Mpc, index -2.2, protons and iron)")
     ap.add_argument("--n-train", type=int, default=9_000_000)
     ap.add_argument("--n-test", type=int, default=1_000_000)
     ap.add_argument("--epochs", type=int, default=32)
@@ -549,6 +552,107 @@ def run_uneven(args):
     }))
 
 
+def run_cosmology(args):
+    """1D mode with cosmology on the paper's comparison setup (sources uniform
+    in comoving volume up to 4000 Mpc, spectral index -2.2, pure protons and
+    pure iron): 1D throughput, and a 3D run without field corrected a
+    posteriori against the 1D spectrum."""
+    import torch
+    from scipy.stats import ks_2samp
+    from paper_1307_2643_gb300 import crp
+    from paper_1307_2643_gb300.build import build
+
+    torch.cuda.set_device(0)
+    build()
+    crp.use_torch_allocator(0)
+    n = args.n or 20_000  # sources per species (iron: up to 56 nucleons each)
+    g = workloads.rng(workloads.MASTER_SEED + 6)
+    out = {"workload": "cosmology_1d_4000Mpc_index2.2", "metric": "1D candidate-steps/s"}
+    flags = crp.PAIR | crp.ADIABATIC | crp.PION | crp.PHOTODIS | crp.DECAY | crp.EMIN
+    cos = crp.cosmology()
+    ctx = crp.crp_context_create(0, workloads.MASTER_SEED + 6, 64 * n)
+    tables = crp.crp_tables_build(ctx, crp.tables_desc(n=1000))
+    m1 = crp.modules(flags=flags, e_min=1e18, tables=tables)
+    for name, A, Z in (("proton", 1, 1), ("iron", 56, 26)):
+        d = 4000.0 * g.random(n) ** (1.0 / 3.0)
+        u = g.random(n)
+        lo, hi = 1e18, 1e21
+        E = lo * (1 - u * (1 - (lo / hi) ** 1.2)) ** (-1 / 1.2)
+        z = crp.crp_redshift_of_distance(cos, crp.MPC_M, d)
+        inj = crp.host_injection(dict(x=z, y=np.zeros(n), z=np.zeros(n), ux=np.zeros(n),
+                                      uy=np.zeros(n), uz=np.ones(n), E=E, A=np.full(n, A),
+                                      Z=np.full(n, Z)))
+        rates = []
+        for k in range(args.warmup + args.steps):
+            crp.crp_candidates_clear(ctx)
+            crp.crp_candidates_inject(ctx, crp.candidate_arrays(inj), n)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, st = crp.crp_propagate_1d(ctx, cos, m1)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            if k >= args.warmup:
+                rates.append(st.accepted_steps / dt)
+        out[name] = {"sources": n, "accepted_steps": st.accepted_steps,
+                     "steps_per_s": float(np.median(rates)), "detected": st.n_detected,
+                     "photodisintegrations": st.n_pd, "secondaries": st.n_secondaries,
+                     "rounds": st.launches}
+    # 3D without field, corrected a posteriori, against 1D (a bounded sample)
+    m = max(1000, n // 20)
+    d = np.sort(4000.0 * g.random(m) ** (1.0 / 3.0))
+    u = g.random(m)
+    E = 1e18 * (1 - u * (1 - (1e-3) ** 1.2)) ** (-1 / 1.2)
+    res = {}
+    grid = crp.crp_grid_create(ctx, crp.grid_desc((4, 4, 4), 1.0, dtype=crp.F64,
+                                                  data=np.zeros((4, 4, 4, 3))))
+    for name, A, Z in (("proton", 1, 1), ("iron", 56, 26)):
+        ids = np.arange(m, dtype=np.uint64)
+        crp.crp_candidates_clear(ctx)
+        inj = crp.host_injection(dict(id=ids, x=d + 1.0, y=np.zeros(m), z=np.zeros(m),
+                                      ux=-np.ones(m), uy=np.zeros(m), uz=np.zeros(m), E=E,
+                                      A=np.full(m, A), Z=np.full(m, Z)))
+        crp.crp_candidates_inject(ctx, crp.candidate_arrays(inj), m)
+        m3 = crp.modules(precision=crp.FP64, flags=crp.PAIR | crp.PION | crp.PHOTODIS |
+                         crp.DECAY | crp.EMIN | crp.OBSERVER, observer_radius=1.0, h_max=10.0,
+                         h_min=1e-3, e_min=1e18, tables=tables)
+        t0 = time.perf_counter()
+        crp.crp_propagate(ctx, grid, m3)
+        rec = crp.crp_collect(ctx, crp.COLLECT_ALL)
+        idx = {int(i): k for k, i in enumerate(rec["id"])}
+        det = np.nonzero(rec["status"] == crp.DETECTED)[0]
+        root = []
+        for k in det:
+            cur = k
+            while rec["generation"][cur] > 0:
+                cur = idx[int(rec["parent_id"][cur])]
+            root.append(cur)
+        src = rec[np.array(root, dtype=np.int64)]
+        r3 = rec[det]
+        Ec, _, _, nk = crp.crp_cosmology_correct(ctx, cos, m1, r3["id"], r3["s"] + 1.0, src["E0"],
+                                                 src["A0"], src["Z0"])
+        t_corr = time.perf_counter() - t0
+        crp.crp_candidates_clear(ctx)
+        zz = crp.crp_redshift_of_distance(cos, crp.MPC_M, d + 1.0)
+        inj1 = crp.host_injection(dict(id=ids, x=zz, y=np.zeros(m), z=np.zeros(m), ux=np.zeros(m),
+                                       uy=np.zeros(m), uz=np.ones(m), E=E, A=np.full(m, A),
+                                       Z=np.full(m, Z)))
+        crp.crp_candidates_inject(ctx, crp.candidate_arrays(inj1), m)
+        crp.crp_propagate_1d(ctx, cos, m1)
+        r1 = crp.crp_collect(ctx, crp.COLLECT_DETECTED)
+        corrected = Ec[nk > 0]
+        res[name] = {"sources": m, "observed_3d": int(len(r3)), "corrected": int(len(corrected)),
+                     "arrived_1d": int(len(r1)), "seconds_3d_plus_correction": t_corr,
+                     "ks_distance_corrected_vs_1d":
+                         float(ks_2samp(np.log(corrected), np.log(r1["E"])).statistic),
+                     "ks_distance_uncorrected_vs_1d":
+                         float(ks_2samp(np.log(r3["E"]), np.log(r1["E"])).statistic)}
+    out["correction"] = res
+    crp.crp_grid_destroy(grid)
+    crp.crp_tables_destroy(tables)
+    crp.crp_context_destroy(ctx)
+    print(json.dumps(out))
+
+
 def run_galactic(args, keep=False):
     """Galactic workload: back-track antiprotons from Earth through the
     synthetic galactic field (disk + halo + 256^3 random component), train the
@@ -803,5 +907,7 @@ if __name__ == "__main__":
         run_uneven(a)
     elif a.workload == "e2e":
         run_e2e(a)
+    elif a.workload == "cosmology":
+        run_cosmology(a)
     else:
         run_ours(a)

@@ -435,6 +435,58 @@ crp_status crp_histogram_energy(crp_context* ctx, int32_t what, double e_lo, dou
 crp_status crp_grid_sample(const crp_grid* grid, const crp_modules* m, int64_t n,
                            const double* xyz, double* B_out);
 
+/* ---------------------------------------------------------------------
+ * 1D mode with cosmology and the a-posteriori 3D cosmology correction.
+ * Sect. 2 lists the 1D mode with cosmological effects (redshift evolution
+ * of the photon backgrounds, adiabatic expansion); Sect. 4 ("Cosmology in
+ * 3D") corrects a 3D run made without cosmology by re-simulating each
+ * observed particle in 1D and substituting one of the 1D products.
+ * Flat Lambda-CDM.  In 1D a candidate's x holds its redshift; it moves
+ * toward the observer in redshift steps (see crp_propagate_1d).
+ * ------------------------------------------------------------------- */
+typedef struct {
+  double H0_km_s_Mpc;  /* 0 = 67.3 */
+  double omega_m;      /* 0 = 0.315 (omega_lambda = 1 - omega_m) */
+  double dz_max;       /* largest redshift step (0 = 1e-3) */
+  double loss_max;     /* largest relative pair loss per step (0 = 1e-3) */
+} crp_cosmology;
+
+/* Propagate the context's candidates in 1D: x = source redshift (y, z and
+ * the direction are carried but not used).  Uses from m: flags (CRP_PAIR,
+ * CRP_ADIABATIC, CRP_PION, CRP_PHOTODIS, CRP_DECAY, CRP_EMIN), e_min,
+ * tables (z = 0 rates), length_unit_m, max_steps.  A step lowers z by dz,
+ * the smallest of dz_max, the step of relative pair loss loss_max, z, and
+ * the step that uses up a stochastic process's remaining optical depth
+ * (-ln u at each reset; the event happens at the step's end); its comoving
+ * length is dz / H(z - dz/2).  Pair loss with the start-of-step rate, then
+ * the exact adiabatic factor (1+z')/(1+z); per comoving length a rate is
+ * (1+z)^2 times its table value at (1+z) Gamma (background (1+z)^3 denser,
+ * (1+z) hotter); free-neutron decay 1 / ((1+z) gamma c tau).  Arrival at
+ * z = 0: CRP_DETECTED.  Records: x = final redshift, x0 = starting redshift,
+ * s = comoving length travelled.  Binary64, one candidate per thread. */
+crp_status crp_propagate_1d(crp_context* ctx, const crp_cosmology* cosmo, const crp_modules* m,
+                            void* stream, crp_stats* stats_out);
+
+/* The a-posteriori correction for n particles observed in a 3D run without
+ * cosmology (host arrays): particle i, injected with energy E0[i] and
+ * species (A0[i], Z0[i]) and observed after trajectory length T[i] (length
+ * units, read as a comoving distance), is re-propagated in 1D from the
+ * redshift whose comoving distance is T[i] (seed of ctx, ids id[i]).  Of its
+ * products that reach z = 0, ordered by id, product k = min(floor(u n_k),
+ * n_k - 1) replaces it (u: Philox counter (0, tag 5, id)); E_out, A_out,
+ * Z_out receive it and n_products[i] = n_k (0: nothing arrives; outputs 0).
+ * Uses a private pool of n (max A0 + 1) candidates. */
+crp_status crp_cosmology_correct(crp_context* ctx, const crp_cosmology* cosmo,
+                                 const crp_modules* m, int64_t n, const uint64_t* id,
+                                 const double* T, const double* E0, const int32_t* A0,
+                                 const int32_t* Z0, double* E_out, int32_t* A_out,
+                                 int32_t* Z_out, int32_t* n_products);
+
+/* Redshift at comoving distance D[i] (length units of m) for the cosmology
+ * (Gauss-Legendre quadrature of 1 / H, bisection). */
+crp_status crp_redshift_of_distance(const crp_cosmology* cosmo, double length_unit_m, int64_t n,
+                                    const double* D, double* z_out);
+
 /* Launch-configuration autotuner (no counterpart in the paper; the
  * scheduler's tunables are this library's own).  Times crp_propagate on the
  * context's injected candidates under a fixed set of configurations (block

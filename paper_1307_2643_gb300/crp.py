@@ -85,6 +85,16 @@ class LensDesc(C.Structure):
                 ("E", C.c_void_p), ("bin", C.c_void_p), ("n_samples", C.c_int64)]
 
 
+class Cosmology(C.Structure):
+    _fields_ = [("H0_km_s_Mpc", C.c_double), ("omega_m", C.c_double), ("dz_max", C.c_double),
+                ("loss_max", C.c_double)]
+
+
+def cosmology(H0_km_s_Mpc=0.0, omega_m=0.0, dz_max=0.0, loss_max=0.0):
+    """Flat Lambda-CDM; zeros select 67.3 km/s/Mpc, 0.315, 1e-3, 1e-3."""
+    return Cosmology(H0_km_s_Mpc, omega_m, dz_max, loss_max)
+
+
 class Peaks(C.Structure):
     _fields_ = [("fp32_tflops", C.c_double), ("fp64_tflops", C.c_double),
                 ("l2_read_gbs", C.c_double), ("sm_count", C.c_int32), ("l2_bytes", C.c_int32)]
@@ -135,7 +145,8 @@ SYMBOLS = (
     "crp_mlp_create", "crp_mlp_destroy", "crp_mlp_num_params", "crp_mlp_set_params",
     "crp_mlp_get_params", "crp_mlp_forward", "crp_mlp_train_step", "crp_lens_build_surrogate",
     "crp_checkpoint", "crp_restore", "crp_measure_peaks", "crp_autotune", "crp_grid_sample",
-    "crp_mlp_set_forward_path",
+    "crp_mlp_set_forward_path", "crp_propagate_1d", "crp_cosmology_correct",
+    "crp_redshift_of_distance",
 )
 
 _lock = threading.Lock()
@@ -192,6 +203,12 @@ def lib():
             L.crp_measure_peaks.argtypes = [i32, C.POINTER(Peaks)]
             L.crp_grid_sample.argtypes = [p, C.POINTER(Modules), C.c_int64, p, p]
             L.crp_mlp_set_forward_path.argtypes = [p, i32]
+            L.crp_propagate_1d.argtypes = [p, C.POINTER(Cosmology), C.POINTER(Modules), p,
+                                           C.POINTER(Stats)]
+            L.crp_cosmology_correct.argtypes = [p, C.POINTER(Cosmology), C.POINTER(Modules),
+                                                C.c_int64] + [p] * 9
+            L.crp_redshift_of_distance.argtypes = [C.POINTER(Cosmology), C.c_double, C.c_int64,
+                                                   p, p]
             L.crp_autotune.argtypes = [p, p, C.POINTER(Modules), u64, C.POINTER(TuneResult), p]
             for name in SYMBOLS:
                 if name not in ("crp_last_error", "crp_version"):
@@ -462,6 +479,41 @@ def crp_mlp_train_step(mlp, x_dev, t_dev, n, lr, stream=None, want_loss=True):
     return loss.value
 
 
+def crp_propagate_1d(ctx, cosmo: Cosmology, modules: Modules, stream=None,
+                     raise_on_error=True):
+    """1D propagation of the context's candidates (x = source redshift)."""
+    s = Stats()
+    status = lib().crp_propagate_1d(ctx, C.byref(cosmo), C.byref(modules), stream, C.byref(s))
+    if raise_on_error:
+        _check(status)
+    return status, s
+
+
+def crp_cosmology_correct(ctx, cosmo: Cosmology, modules: Modules, ids, T, E0, A0, Z0):
+    """(E, A, Z, n_products) of the a-posteriori correction (host arrays)."""
+    ids = np.ascontiguousarray(ids, dtype=np.uint64)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    E0 = np.ascontiguousarray(E0, dtype=np.float64)
+    A0 = np.ascontiguousarray(A0, dtype=np.int32)
+    Z0 = np.ascontiguousarray(Z0, dtype=np.int32)
+    n = len(E0)
+    E, A, Z, nk = (np.zeros(n), np.zeros(n, np.int32), np.zeros(n, np.int32),
+                   np.zeros(n, np.int32))
+    _check(lib().crp_cosmology_correct(ctx, C.byref(cosmo), C.byref(modules), n, ids.ctypes.data,
+                                       T.ctypes.data, E0.ctypes.data, A0.ctypes.data,
+                                       Z0.ctypes.data, E.ctypes.data, A.ctypes.data,
+                                       Z.ctypes.data, nk.ctypes.data))
+    return E, A, Z, nk
+
+
+def crp_redshift_of_distance(cosmo: Cosmology, length_unit_m, D):
+    D = np.ascontiguousarray(D, dtype=np.float64).ravel()
+    out = np.zeros_like(D)
+    _check(lib().crp_redshift_of_distance(C.byref(cosmo), length_unit_m, len(D), D.ctypes.data,
+                                          out.ctypes.data))
+    return out
+
+
 def crp_autotune(ctx, grid, modules: Modules, steps_per_trial=0, stream=None):
     """Tune `modules` in place on the context's candidates; returns the
     TuneResult as a dict."""
@@ -509,11 +561,12 @@ def crp_histogram_energy_noalloc(ctx, what, e_lo, e_hi, nbins, stream=None):
 # ---------------------------------------------------------------------------
 def candidate_arrays(inj: dict, on_device=False):
     """CandidateArrays pointing at the arrays of `inj` (numpy on the host, or
-    torch tensors on the device).  Keep `inj` alive during the call."""
+    torch tensors on the device); the descriptor holds a reference to `inj`."""
     a = CandidateArrays()
     for k in ("id", "x", "y", "z", "ux", "uy", "uz", "E", "A", "Z", "q", "s_max"):
         setattr(a, k, _addr(inj.get(k)))
     a.on_device = 1 if on_device else 0
+    a._refs = inj  # the arrays live as long as the descriptor
     return a
 
 
@@ -534,6 +587,11 @@ def grid_desc(n, spacing, origin=(0.0, 0.0, 0.0), dtype=F64, source=GRID_FROM_HO
     d.spacing = spacing
     d.origin[:] = origin
     d.dtype, d.source = dtype, source
+    if isinstance(data, np.ndarray):
+        # C-contiguous, and referenced by the descriptor so the buffer outlives
+        # the caller's temporaries until crp_grid_create has copied it
+        data = np.ascontiguousarray(data)
+    d._data_ref = data
     d.data = _addr(data)
     d.data_dtype = data_dtype
     d.cell_records = cell_records

@@ -5,6 +5,9 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+#include <unordered_map>
+#include <vector>
 #include <chrono>
 #include <mutex>
 #include <new>
@@ -1681,3 +1684,286 @@ extern "C" crp_status crp_grid_sample(const crp_grid* g, const crp_modules* m, i
   dev_free(dB);
   return st;
 }
+
+// ---------------------------------------------------------------------------
+// 1D mode with cosmology and the a-posteriori correction
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Cosmo {
+  double H0, omega_m, omega_l, dz_max, loss_max;  // H0 per length unit (H0 / c)
+};
+
+Cosmo cosmo_of(const crp_cosmology* c, double length_unit_m) {
+  const double H0 = c && c->H0_km_s_Mpc > 0.0 ? c->H0_km_s_Mpc : 67.3;
+  const double om = c && c->omega_m > 0.0 ? c->omega_m : 0.315;
+  Cosmo k;
+  k.H0 = H0 / 299792.458 * (length_unit_m / 3.0856775814913673e22);
+  k.omega_m = om;
+  k.omega_l = 1.0 - om;
+  k.dz_max = c && c->dz_max > 0.0 ? c->dz_max : 1e-3;
+  k.loss_max = c && c->loss_max > 0.0 ? c->loss_max : 1e-3;
+  return k;
+}
+
+// Comoving distance to z: 16-point Gauss-Legendre on 64 panels of 1 / H.
+double comoving_distance(const Cosmo& k, double z, const std::vector<double>& x,
+                         const std::vector<double>& w) {
+  const int panels = 64;
+  const double width = z / panels;
+  double total = 0.0;
+  for (int p = 0; p < panels; ++p) {
+    const double mid = (p + 0.5) * width, half = 0.5 * width;
+    double s = 0.0;
+    for (size_t j = 0; j < x.size(); ++j) {
+      const double a = 1.0 + mid + half * x[j];
+      s += w[j] / (k.H0 * sqrt(k.omega_m * a * a * a + k.omega_l));
+    }
+    total += s * half;
+  }
+  return total;
+}
+
+// Redshift at comoving distance D: Newton's method on D(z) (dD/dz = 1/H)
+// inside a bracket that every iterate narrows, bisection when Newton leaves it.
+double redshift_at(const Cosmo& k, double D, const std::vector<double>& x,
+                   const std::vector<double>& w) {
+  if (D <= 0.0) return 0.0;
+  double lo = 0.0, hi = 1.0;
+  while (comoving_distance(k, hi, x, w) < D && hi < 1e6) hi *= 2.0;
+  double z = D * k.H0;  // small-z start
+  if (!(z > lo && z < hi)) z = 0.5 * (lo + hi);
+  for (int it = 0; it < 100; ++it) {
+    const double f = comoving_distance(k, z, x, w) - D;
+    if (f < 0.0)
+      lo = z;
+    else
+      hi = z;
+    const double a = 1.0 + z;
+    double zn = z - f * (k.H0 * sqrt(k.omega_m * a * a * a + k.omega_l));
+    if (!(zn > lo && zn < hi)) zn = 0.5 * (lo + hi);
+    if (fabs(zn - z) <= 1e-16 * (1.0 + z) || hi - lo <= 1e-16 * hi) return zn;
+    z = zn;
+  }
+  return z;
+}
+
+}  // namespace
+
+extern "C" {
+
+crp_status crp_redshift_of_distance(const crp_cosmology* cosmo, double length_unit_m, int64_t n,
+                                    const double* D, double* z_out) {
+  if (n < 0 || (n && (!D || !z_out)) || !(length_unit_m > 0.0)) {
+    set_error("crp_redshift_of_distance: bad argument");
+    return CRP_E_INVALID;
+  }
+  const Cosmo k = cosmo_of(cosmo, length_unit_m);
+  std::vector<double> x, w;
+  gauss_legendre(16, x, w);
+  for (int64_t i = 0; i < n; ++i) {
+    if (!(D[i] >= 0.0)) {
+      set_error("crp_redshift_of_distance: distances must be >= 0");
+      return CRP_E_INVALID;
+    }
+    z_out[i] = redshift_at(k, D[i], x, w);
+  }
+  return CRP_OK;
+}
+
+crp_status crp_propagate_1d(crp_context* c, const crp_cosmology* cosmo, const crp_modules* m,
+                            void* stream, crp_stats* stats_out) {
+  if (!c || !m) {
+    set_error("crp_propagate_1d: NULL argument");
+    return CRP_E_INVALID;
+  }
+  if ((m->flags & (CRP_PAIR | CRP_PION | CRP_PHOTODIS)) && !m->tables) {
+    set_error("crp_propagate_1d: PAIR / PION / PHOTODIS need tables");
+    return CRP_E_INVALID;
+  }
+  if (!(m->length_unit_m > 0.0)) {
+    set_error("crp_propagate_1d: length_unit_m must be > 0");
+    return CRP_E_INVALID;
+  }
+  if (stats_out) memset(stats_out, 0, sizeof(*stats_out));
+  if (c->size == 0) return CRP_OK;
+  DeviceGuard dg(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Cosmo k = cosmo_of(cosmo, m->length_unit_m);
+  K1dParams p;
+  memset(&p, 0, sizeof(p));
+  p.flags = m->flags;
+  p.seed = c->seed;
+  p.e_min = m->e_min;
+  p.H0 = k.H0;
+  p.omega_m = k.omega_m;
+  p.omega_l = k.omega_l;
+  p.dz_max = k.dz_max;
+  p.loss_max = k.loss_max;
+  if (m->tables) {
+    const crp_tables* t = m->tables;
+    p.t_beta = t->data;
+    p.t_pion = t->data + t->desc.n;
+    p.t_gdr = t->data + 2 * t->desc.n;
+    p.tab_lg0 = log(t->desc.gamma_lo);
+    p.tab_inv_dlg = (double)(t->desc.n - 1) / (log(t->desc.gamma_hi) - log(t->desc.gamma_lo));
+    p.tab_n = t->desc.n;
+  } else {
+    p.tab_n = 2;
+  }
+  p.decay_k = 299792458.0 * 878.4 / 939.56542052e6 / m->length_unit_m;
+  p.capacity = c->capacity;
+  p.max_steps = m->max_steps ? m->max_steps : 100000000ull;
+  const int block = 128;
+  const int grid = c->sm_count * 8;
+  uint32_t* q_in = c->queue[0];
+  uint32_t* q_out = c->queue[1];
+  const int3 shift3 = make_int3(0, 0, 0);
+  FieldView none;
+  memset(&none, 0, sizeof(none));
+  none.n[0] = none.n[1] = none.n[2] = 1;
+  cudaError_t e = cudaMemsetAsync(c->dc, 0, sizeof(DevCounters), s);
+  if (e == cudaSuccess) {
+    k_set_u64<<<1, 1, 0, s>>>(&c->dc->tail, (unsigned long long)c->size);
+    k_build_queue<<<blocks_for(c->size, 256), 256, 0, s>>>(c->st, c->size, none, shift3, -1,
+                                                           q_in, c->keys, &c->dc->q_out);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->hc, c->dc, sizeof(DevCounters), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail_cuda(e, "crp_propagate_1d: work queue");
+  uint64_t n_in = c->hc->q_out;
+  uint32_t rounds = 0;
+  float total_ms = 0.f;
+  while (n_in > 0) {
+    p.queue_in = q_in;
+    p.queue_out = q_out;
+    p.n_in = n_in;
+    k_round_reset<<<1, 1, 0, s>>>(c->dc);
+    cudaEventRecord(c->ev0, s);
+    e = launch_propagate_1d(p, c->st, c->dc, grid, block, s);
+    if (e != cudaSuccess) return fail_cuda(e, "crp_propagate_1d: launch");
+    cudaEventRecord(c->ev1, s);
+    rounds += 1;
+    e = cudaMemcpyAsync(c->hc, c->dc, sizeof(DevCounters), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_cuda(e, "crp_propagate_1d: kernel");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    total_ms += ms;
+    n_in = c->hc->q_out < c->capacity ? c->hc->q_out : c->capacity;
+    std::swap(q_in, q_out);
+  }
+  c->size = c->hc->tail < c->capacity ? c->hc->tail : c->capacity;
+  crp_status st = CRP_OK;
+  if (c->hc->overflow) {
+    st = CRP_E_QUEUE_FULL;
+    set_error("crp_propagate_1d: %llu secondaries did not fit the pool capacity %zu",
+              (unsigned long long)c->hc->overflow, c->capacity);
+  }
+  if (stats_out) {
+    stats_out->accepted_steps = c->hc->acc;
+    stats_out->n_pion = c->hc->pion;
+    stats_out->n_pd = c->hc->pd;
+    stats_out->n_secondaries = c->hc->secondaries;
+    stats_out->n_dropped = c->hc->dropped;
+    stats_out->n_overflow = c->hc->overflow;
+    stats_out->n_detected = c->hc->detected;
+    stats_out->kernel_ms = total_ms;
+    stats_out->launches = rounds;
+    stats_out->error_word = c->hc->error_word;
+  }
+  return st;
+}
+
+crp_status crp_cosmology_correct(crp_context* ctx, const crp_cosmology* cosmo,
+                                 const crp_modules* m, int64_t n, const uint64_t* id,
+                                 const double* T, const double* E0, const int32_t* A0,
+                                 const int32_t* Z0, double* E_out, int32_t* A_out,
+                                 int32_t* Z_out, int32_t* n_products) {
+  if (!ctx || !m || n < 0 ||
+      (n && (!id || !T || !E0 || !A0 || !Z0 || !E_out || !A_out || !Z_out || !n_products))) {
+    set_error("crp_cosmology_correct: bad argument");
+    return CRP_E_INVALID;
+  }
+  if (n == 0) return CRP_OK;
+  std::vector<double> z(n);
+  crp_status st = crp_redshift_of_distance(cosmo, m->length_unit_m, n, T, z.data());
+  if (st != CRP_OK) return st;
+  int32_t amax = 1;
+  for (int64_t i = 0; i < n; ++i) amax = A0[i] > amax ? A0[i] : amax;
+  crp_context* c = nullptr;
+  st = crp_context_create(ctx->device, ctx->seed, (size_t)n * (size_t)(amax + 1), &c);
+  if (st != CRP_OK) return st;
+  std::vector<double> zeros(n, 0.0), ones(n, 1.0);
+  std::vector<int32_t> q(n, 1);
+  crp_candidate_arrays a;
+  memset(&a, 0, sizeof(a));
+  a.id = id;
+  a.x = z.data();
+  a.y = zeros.data();
+  a.z = zeros.data();
+  a.ux = zeros.data();
+  a.uy = zeros.data();
+  a.uz = ones.data();
+  a.E = E0;
+  a.A = A0;
+  a.Z = Z0;
+  a.q = q.data();
+  a.on_device = 0;
+  st = crp_candidates_inject(c, &a, (size_t)n, 0, nullptr);
+  if (st == CRP_OK) st = crp_propagate_1d(c, cosmo, m, nullptr, nullptr);
+  std::vector<crp_record> rec;
+  if (st == CRP_OK) {
+    size_t cnt = 0;
+    st = crp_collect(c, CRP_COLLECT_ALL, nullptr, 0, &cnt, 0, nullptr);
+    if (st == CRP_OK) {
+      rec.resize(cnt);
+      st = crp_collect(c, CRP_COLLECT_ALL, rec.data(), cnt, &cnt, 0, nullptr);
+      rec.resize(cnt);
+    }
+  }
+  crp_context_destroy(c);
+  if (st != CRP_OK) return st;
+  // lineage root of every record: follow parent ids to a generation-0 record
+  std::unordered_map<uint64_t, size_t> by_id;
+  by_id.reserve(rec.size() * 2);
+  for (size_t r = 0; r < rec.size(); ++r) by_id[rec[r].id] = r;
+  std::unordered_map<uint64_t, std::vector<std::pair<uint64_t, size_t>>> products;
+  for (size_t r = 0; r < rec.size(); ++r) {
+    if (rec[r].status != CRP_DETECTED) continue;
+    size_t cur = r;
+    while (rec[cur].generation > 0) {
+      auto it = by_id.find(rec[cur].parent_id);
+      if (it == by_id.end()) break;
+      cur = it->second;
+    }
+    products[rec[cur].id].push_back({rec[r].id, r});
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    auto it = products.find(id[i]);
+    if (it == products.end() || it->second.empty()) {
+      n_products[i] = 0;
+      E_out[i] = 0.0;
+      A_out[i] = 0;
+      Z_out[i] = 0;
+      continue;
+    }
+    auto& v = it->second;
+    std::sort(v.begin(), v.end());
+    const int64_t nk = (int64_t)v.size();
+    const Philox4 w = draw4(ctx->seed, TAG_COSMOLOGY, id[i], 0);
+    const double u = u01_open(w.v0, w.v1);
+    int64_t k = (int64_t)floor(u * (double)nk);
+    if (k > nk - 1) k = nk - 1;
+    const crp_record& pick = rec[v[k].second];
+    n_products[i] = (int32_t)nk;
+    E_out[i] = pick.E;
+    A_out[i] = pick.A;
+    Z_out[i] = pick.Z;
+  }
+  return CRP_OK;
+}
+
+}  // extern "C"

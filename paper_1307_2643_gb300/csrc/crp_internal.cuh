@@ -109,6 +109,26 @@ struct KParams {
   uint32_t slice;                  // accepted steps per candidate per round
 };
 
+// 1D mode with cosmology (flat Lambda-CDM; lengths comoving; x holds the
+// candidate's redshift): parameters of one round.
+struct K1dParams {
+  uint32_t flags;
+  uint64_t seed;
+  double e_min;
+  double H0, omega_m, omega_l;  // H0 per length unit (H0 / c)
+  double dz_max, loss_max;
+  const double *t_beta, *t_pion, *t_gdr;
+  double tab_lg0, tab_inv_dlg;
+  int64_t tab_n;
+  double decay_k;
+  uint64_t capacity, max_steps;
+  const uint32_t* queue_in;
+  uint64_t n_in;
+  uint32_t* queue_out;
+};
+cudaError_t launch_propagate_1d(const K1dParams& p, const DevState& st, DevCounters* dc, int grid,
+                                int block, cudaStream_t s);
+
 // Launch one propagate round over the candidates listed in kp.queue_in.
 cudaError_t launch_propagate_fp64(const KParams& kp, const DevState& st, DevCounters* dc,
                                   int grid, int block, cudaStream_t s);

@@ -16,13 +16,21 @@ struct Philox4 {
   uint32_t v0, v1, v2, v3;
 };
 
-__device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
-                                                 uint32_t c3, uint32_t k0, uint32_t k1) {
+__host__ __device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+  return __umulhi(a, b);
+#else
+  return (uint32_t)(((uint64_t)a * (uint64_t)b) >> 32);
+#endif
+}
+
+__host__ __device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                          uint32_t c3, uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t hi_a = __umulhi(0xD2511F53u, c0);
+    const uint32_t hi_a = mulhi32(0xD2511F53u, c0);
     const uint32_t lo_a = 0xD2511F53u * c0;
-    const uint32_t hi_b = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t hi_b = mulhi32(0xCD9E8D57u, c2);
     const uint32_t lo_b = 0xCD9E8D57u * c2;
     const uint32_t n0 = hi_b ^ c1 ^ k0;
     const uint32_t n2 = hi_a ^ c3 ^ k1;
@@ -37,7 +45,7 @@ __device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint3
 }
 
 // Open-interval uniform from two words: (top 52 bits of hi:lo + 1/2) * 2^-52.
-__device__ __forceinline__ double u01_open(uint32_t lo, uint32_t hi) {
+__host__ __device__ __forceinline__ double u01_open(uint32_t lo, uint32_t hi) {
   const unsigned long long v = ((unsigned long long)hi << 32) | lo;
   return ((double)(v >> 12) + 0.5) * 2.220446049250313080847263336181640625e-16;
 }
@@ -45,16 +53,17 @@ __device__ __forceinline__ double u01_open(uint32_t lo, uint32_t hi) {
 // Stream tags of the counter (draw, tag, id_lo, id_hi).
 constexpr uint32_t TAG_FIELD = 1;
 constexpr uint32_t TAG_INTERACTION = 2;
+constexpr uint32_t TAG_COSMOLOGY = 5;  // a-posteriori correction: product pick
 
-__device__ __forceinline__ Philox4 draw4(uint64_t seed, uint32_t tag, uint64_t id,
-                                         uint32_t draw) {
+__host__ __device__ __forceinline__ Philox4 draw4(uint64_t seed, uint32_t tag, uint64_t id,
+                                                  uint32_t draw) {
   return philox4x32_10(draw, tag, (uint32_t)id, (uint32_t)(id >> 32), (uint32_t)seed,
                        (uint32_t)(seed >> 32));
 }
 
 // SplitMix64 finaliser (Steele, Lea, Flood, OOPSLA 2014) over a Weyl step:
 // id of the secondary of a parent's event number `ev`.
-__device__ __forceinline__ uint64_t lineage_id(uint64_t parent, uint32_t ev) {
+__host__ __device__ __forceinline__ uint64_t lineage_id(uint64_t parent, uint32_t ev) {
   uint64_t z = parent + 0x9E3779B97F4A7C15ull * ((uint64_t)ev + 1ull);
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/crp.h"
 
 namespace crp {
@@ -21,6 +23,8 @@ crp_status grid_unpack(const void* nodes, int dtype, int64_t N, double* dst_dev,
 crp_status grid_cells(const void* nodes, const int64_t n[3], void* cells, cudaStream_t s);
 // Generate the turbulent field of `d` into node storage (synchronises s).
 crp_status grid_turbulence(const crp_grid_desc* d, void* nodes, cudaStream_t s);
+// Gauss-Legendre nodes and weights on [-1, 1] (host).
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
 // Fill the three rate tables (device arrays of d->n doubles) by quadrature.
 crp_status tables_compute(const crp_tables_desc* d, double* beta, double* pion, double* gdr,
                           cudaStream_t s);

@@ -190,6 +190,10 @@ void legendre_rule(int n, std::vector<double>& x, std::vector<double>& w) {
 
 }  // namespace
 
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  legendre_rule(n, x, w);
+}
+
 crp_status tables_compute(const crp_tables_desc* d, double* beta, double* pion, double* gdr,
                           cudaStream_t s) {
   GLRule gl;

@@ -83,3 +83,25 @@ def test_context_create_without_gpu_fails_cleanly(crp):
     with pytest.raises(crp.CrpError):
         crp.crp_context_create(0, 1, 16)
     assert len(crp.lib().crp_last_error()) > 0
+
+
+def test_descriptors_keep_their_host_arrays_alive(crp):
+    """A descriptor built from a temporary array must keep that array: the
+    library copies it only later, at crp_grid_create / crp_candidates_inject."""
+    import gc
+    import weakref
+
+    import numpy as np
+
+    d = crp.grid_desc((2, 2, 2), 1.0, data=np.full((2, 2, 2, 3), 7.0))
+    ref = weakref.ref(d._data_ref)
+    gc.collect()
+    assert ref() is not None and d.data == ref().ctypes.data
+    assert float(np.ctypeslib.as_array((ctypes.c_double * 24).from_address(d.data))[5]) == 7.0
+
+    inj = crp.host_injection(dict(x=np.arange(4.0), E=np.ones(4)))
+    a = crp.candidate_arrays(inj)
+    wx = weakref.ref(inj["x"])
+    del inj
+    gc.collect()
+    assert wx() is not None and a.x == wx().ctypes.data
