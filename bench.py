@@ -565,7 +565,7 @@ def run_cosmology(args):
     torch.cuda.set_device(0)
     build()
     crp.use_torch_allocator(0)
-    n = args.n or 20_000  # sources per species (iron: up to 56 nucleons each)
+    n = args.n or 200_000  # sources per species (iron: up to 56 nucleons each)
     g = workloads.rng(workloads.MASTER_SEED + 6)
     out = {"workload": "cosmology_1d_4000Mpc_index2.2", "metric": "1D candidate-steps/s"}
     flags = crp.PAIR | crp.ADIABATIC | crp.PION | crp.PHOTODIS | crp.DECAY | crp.EMIN

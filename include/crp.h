@@ -483,7 +483,8 @@ crp_status crp_cosmology_correct(crp_context* ctx, const crp_cosmology* cosmo,
                                  int32_t* Z_out, int32_t* n_products);
 
 /* Redshift at comoving distance D[i] (length units of m) for the cosmology
- * (Gauss-Legendre quadrature of 1 / H, bisection). */
+ * (Gauss-Legendre quadrature of 1 / H; Newton iterations on D(z), kept
+ * inside a bracket by bisection). */
 crp_status crp_redshift_of_distance(const crp_cosmology* cosmo, double length_unit_m, int64_t n,
                                     const double* D, double* z_out);
 
