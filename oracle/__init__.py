@@ -49,6 +49,7 @@ OBSERVER = 1 << 5
 BORDER = 1 << 6
 GALACTIC = 1 << 7
 DECAY = 1 << 8
+GMF = 1 << 9
 
 
 def build(force: bool = False) -> str:
@@ -63,6 +64,32 @@ def build(force: bool = False) -> str:
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
+
+
+class Gmf(C.Structure):
+    """Analytic multi-arm galactic field (orc_gmf): arm strengths at r_in,
+    arm boundary radii on the phi = pi ray, pitch, ring, disk/halo transition,
+    toroidal halo, X field, spherical cuts."""
+    _fields_ = [
+        ("arm_b", C.c_double * 8), ("arm_rx", C.c_double * 8), ("pitch_rad", C.c_double),
+        ("ring_b", C.c_double), ("r_ring", C.c_double), ("r_in", C.c_double),
+        ("r_out", C.c_double), ("h_disk", C.c_double), ("w_disk", C.c_double),
+        ("halo_bn", C.c_double), ("halo_bs", C.c_double), ("halo_rn", C.c_double),
+        ("halo_rs", C.c_double), ("halo_wh", C.c_double), ("halo_z0", C.c_double),
+        ("x_b", C.c_double), ("x_theta_rad", C.c_double), ("x_rc", C.c_double),
+        ("x_r", C.c_double), ("r_cut_in", C.c_double), ("r_cut_out", C.c_double),
+    ]
+
+
+def make_gmf(**kw) -> Gmf:
+    """Gmf from keyword values (unset fields 0)."""
+    g = Gmf()
+    for k, v in kw.items():
+        if k in ("arm_b", "arm_rx"):
+            getattr(g, k)[:] = v
+        else:
+            setattr(g, k, v)
+    return g
 
 
 class Params(C.Structure):
@@ -81,6 +108,7 @@ class Params(C.Structure):
         ("gal_center", C.c_double * 3),
         ("max_steps", C.c_int64),
         ("length_unit_m", C.c_double),
+        ("gmf", Gmf),
     ]
 
 
@@ -129,6 +157,7 @@ def lib():
                 [p, i64, C.POINTER(i64), C.c_int]
             L.orc_propagate.restype = C.c_int
             L.orc_field_at.argtypes = [C.POINTER(Params), p, i64, p, p]
+            L.orc_series_atan2_vec.argtypes = [i64, p, p, p]
             L.orc_ang2pix.argtypes = [i64, d, d]
             L.orc_ang2pix.restype = i64
             L.orc_pix2ang.argtypes = [i64, i64, C.POINTER(d), C.POINTER(d)]
@@ -315,7 +344,7 @@ def make_params(*, grid_n, spacing, origin=(0.0, 0.0, 0.0), tol=1e-4, h_min=0.01
                 field_unit_T=NANOGAUSS_T, length_unit_m=MPC_M, flags=0, e_min=0.0,
                 beta_ad=0.0, seed=0, tables: Tables | None = None,
                 obs_c=(0.0, 0.0, 0.0), obs_r=0.0, border_c=(0.0, 0.0, 0.0), border_r=0.0,
-                galactic=None, max_steps=10_000_000) -> Params:
+                galactic=None, gmf: Gmf | None = None, max_steps=10_000_000) -> Params:
     P = Params()
     P.origin[:] = origin
     P.spacing = spacing
@@ -340,8 +369,26 @@ def make_params(*, grid_n, spacing, origin=(0.0, 0.0, 0.0), tol=1e-4, h_min=0.01
                 P.gal_center[:] = v
             else:
                 setattr(P, "gal_" + k, v)
+    if gmf is not None:
+        P.gmf = gmf
     P.max_steps = max_steps
     return P
+
+
+def gmf_at(gmf: Gmf, pts, center=(0.0, 0.0, 0.0)):
+    """The multi-arm galactic field alone at points [m, 3]."""
+    P = make_params(grid_n=(2, 2, 2), spacing=1.0, flags=GMF, gmf=gmf,
+                    galactic={"center": center})
+    return field_at(P, np.zeros((2, 2, 2, 3)), pts)
+
+
+def series_atan2(y, x):
+    """The arctangent both sides steer the spiral phase with."""
+    y = np.ascontiguousarray(y, dtype=np.float64).ravel()
+    x = np.ascontiguousarray(x, dtype=np.float64).ravel()
+    out = np.empty_like(y)
+    lib().orc_series_atan2_vec(len(y), _ptr(y), _ptr(x), _ptr(out))
+    return out
 
 
 def field_at(P: Params, field, pts):

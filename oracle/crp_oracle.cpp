@@ -197,6 +197,36 @@ double series_exp(double x) {
   return poly * scale;
 }
 
+// Arctangent of y/x in (-pi, pi], by argument halving and the Taylor series of
+// atan (reading: the spiral phase of the multi-arm galactic field is steered by
+// this one formula on both sides, for the reason given at series_log).
+//   t = min(|x|,|y|) / max(|x|,|y|) in [0, 1];
+//   three halvings atan t = 2 atan(t / (1 + sqrt(1 + t^2))) bring t below
+//   tan(pi/32) < 0.0985, where atan t = t - t^3/3 + t^5/5 - ... - t^15/15
+//   leaves a tail below 1e-17 t;
+//   then atan(1/t) = pi/2 - atan t, atan2(y, -x) = pi - atan2(y, x) and
+//   atan2(-y, x) = -atan2(y, x).  atan2(0, 0) = 0.
+double series_atan2(double y, double x) {
+  const double ax = std::fabs(x), ay = std::fabs(y);
+  if (ax == 0.0 && ay == 0.0) return 0.0;
+  const bool steep = ay > ax;
+  double t = steep ? ax / ay : ay / ax;
+  for (int i = 0; i < 3; ++i) t = t / (1.0 + std::sqrt(1.0 + t * t));
+  const double t2 = t * t;
+  double poly = -1.0 / 15.0;
+  poly = poly * t2 + 1.0 / 13.0;
+  poly = poly * t2 - 1.0 / 11.0;
+  poly = poly * t2 + 1.0 / 9.0;
+  poly = poly * t2 - 1.0 / 7.0;
+  poly = poly * t2 + 1.0 / 5.0;
+  poly = poly * t2 - 1.0 / 3.0;
+  poly = poly * t2 + 1.0;
+  double a = 8.0 * (t * poly);
+  if (steep) a = 0.5 * kPi - a;
+  if (x < 0.0) a = kPi - a;
+  return y < 0.0 ? -a : a;
+}
+
 // ---------------------------------------------------------------------------
 // HEALPix RING scheme (K. M. Gorski et al., "HEALPix: a framework for high
 // resolution discretization and fast analysis of data distributed on the
@@ -515,6 +545,21 @@ enum {
   ORC_BORDER = 1u << 6,
   ORC_GALACTIC = 1u << 7,   // add the analytic galactic disk + halo field
   ORC_DECAY = 1u << 8,      // free-neutron beta decay
+  ORC_GMF = 1u << 9,        // add the analytic multi-arm galactic field
+};
+
+// Parameters of the analytic multi-arm galactic field (units of the field
+// grid); the model is stated at gmf_field.
+struct orc_gmf {
+  double arm_b[8];      // arm field strengths at r = r_in
+  double arm_rx[8];     // radii where the arm boundaries cross phi = pi, ascending
+  double pitch_rad;     // spiral pitch angle p
+  double ring_b;        // azimuthal field of the ring r_ring <= r < r_in
+  double r_ring, r_in, r_out;
+  double h_disk, w_disk;                       // disk / halo transition
+  double halo_bn, halo_bs, halo_rn, halo_rs, halo_wh, halo_z0;
+  double x_b, x_theta_rad, x_rc, x_r;          // X-shaped poloidal field
+  double r_cut_in, r_cut_out;                  // spherical cuts (0: none)
 };
 
 struct orc_params {
@@ -543,6 +588,7 @@ struct orc_params {
   double gal_center[3];
   int64_t max_steps;   // per-candidate accepted-step budget
   double length_unit_m;  // metres per length unit (neutron decay length)
+  orc_gmf gmf;           // analytic multi-arm galactic field (ORC_GMF)
 };
 
 struct orc_record {
@@ -579,6 +625,9 @@ void orc_series_log_vec(int64_t n, const double* x, double* out) {
   for (int64_t i = 0; i < n; ++i) out[i] = series_log(x[i]);
 }
 double orc_series_exp(double x) { return series_exp(x); }
+void orc_series_atan2_vec(int64_t n, const double* y, const double* x, double* out) {
+  for (int64_t i = 0; i < n; ++i) out[i] = series_atan2(y[i], x[i]);
+}
 int64_t orc_ang2pix(int64_t nside, double z, double phi) { return healpix_ang2pix_ring(nside, z, phi); }
 void orc_pix2ang(int64_t nside, int64_t pix, double* z, double* phi) {
   healpix_pix2ang_ring(nside, pix, z, phi);
@@ -789,11 +838,116 @@ void galactic_field(const orc_params& P, const double x[3], double B[3]) {
   B[1] = b_r * sr + b_phi * cr;
 }
 
+// Analytic multi-arm galactic field of the Jansson-Farrar class (Sect. 4
+// names analytic galactic models, JF12 among them; the structure follows
+// R. Jansson and G. R. Farrar, ApJ 757:14, 2012, with the parameter values
+// left to the caller).  Galactocentric cylindrical (r, phi, z) about
+// gal_center, phi = atan2(y, x).  L(t, h, w) = 1 / (1 + exp(-2 (|t| - h) / w)).
+//  * disk, times (1 - L(z, h_disk, w_disk)):
+//      r_ring <= r < r_in:   B = ring_b phi_hat (molecular ring);
+//      r_in <= r <= r_out:   B = arm_b[j] (r_in / r) (sin p r_hat + cos p phi_hat)
+//    where j is the arm holding the logarithmic spiral through (r, phi): the
+//    spiral's field lines obey d ln r / d phi = tan p, so it crosses phi = pi
+//    at ln r_x = ln r + (pi - phi) tan p, and again at every multiple of
+//    2 pi tan p; brought into [ln arm_rx[0], ln arm_rx[0] + 2 pi tan p), r_x
+//    lies in [arm_rx[j], arm_rx[j+1]) (arm_rx[8] = arm_rx[0] e^{2 pi tan p}).
+//  * toroidal halo: B_phi = e^{-|z|/halo_z0} L(z, h_disk, w_disk) times
+//      halo_bn (1 - L(r, halo_rn, halo_wh)) for z >= 0,
+//      halo_bs (1 - L(r, halo_rs, halo_wh)) for z < 0.
+//  * X field: straight field lines in the (r, z) plane crossing the midplane
+//    at r_p, of strength B_X(r_p) = x_b e^{-r_p / x_r} there, flux conserved
+//    along each line.  Outside (r_p = r - |z| / tan x_theta >= x_rc) the lines
+//    have elevation x_theta and |B| = B_X(r_p) r_p / r; inside, the line
+//    through r_p has elevation atan(x_rc tan x_theta / r_p), so r_p = r f with
+//    f = x_rc / (x_rc + |z| / tan x_theta), and |B| = B_X(r_p) f^2.
+//    B_z = |B| sin(elevation), B_r = sign(z) |B| cos(elevation).
+//  * zero where x^2 + y^2 + z^2 < r_cut_in^2 or > r_cut_out^2 (a cut of 0 is off);
+//    on the axis r = 0 only B_z remains (reading).
+double logistic(double t, double h, double w) {
+  const double e = -2.0 * (std::fabs(t) - h) / w;
+  if (e > 700.0) return 0.0;
+  return 1.0 / (1.0 + series_exp(e));
+}
+
+int gmf_arm(const orc_gmf& G, double r, double phi) {
+  const double tan_p = std::tan(G.pitch_rad);
+  const double period = 2.0 * kPi * tan_p;
+  const double ln_r0 = std::log(G.arm_rx[0]);
+  double t = series_log(r) + (kPi - phi) * tan_p - ln_r0;
+  t = t - std::floor(t / period) * period;
+  if (t < 0.0) t = t + period;
+  if (t >= period) t = t - period;
+  int j = 7;
+  while (j > 0 && t < std::log(G.arm_rx[j]) - ln_r0) --j;
+  return j;
+}
+
+void gmf_field(const orc_params& P, const double x[3], double B[3]) {
+  const orc_gmf& G = P.gmf;
+  const double rx = x[0] - P.gal_center[0], ry = x[1] - P.gal_center[1];
+  const double z = x[2] - P.gal_center[2];
+  B[0] = 0.0; B[1] = 0.0; B[2] = 0.0;
+  const double R2 = rx * rx + ry * ry + z * z;
+  if (G.r_cut_in > 0.0 && R2 < G.r_cut_in * G.r_cut_in) return;
+  if (G.r_cut_out > 0.0 && R2 > G.r_cut_out * G.r_cut_out) return;
+  const double r = std::sqrt(rx * rx + ry * ry);
+  const double az = std::fabs(z);
+  const double l_disk = logistic(z, G.h_disk, G.w_disk);
+  double b_r = 0.0, b_phi = 0.0, b_z = 0.0;
+  if (r >= G.r_ring && r <= G.r_out && r > 0.0) {
+    if (r < G.r_in) {
+      b_phi += G.ring_b * (1.0 - l_disk);
+    } else {
+      const int j = gmf_arm(G, r, series_atan2(ry, rx));
+      const double bd = G.arm_b[j] * (G.r_in / r) * (1.0 - l_disk);
+      b_r += bd * std::sin(G.pitch_rad);
+      b_phi += bd * std::cos(G.pitch_rad);
+    }
+  }
+  const double bh = z >= 0.0 ? G.halo_bn * (1.0 - logistic(r, G.halo_rn, G.halo_wh))
+                             : G.halo_bs * (1.0 - logistic(r, G.halo_rs, G.halo_wh));
+  b_phi += series_exp(-az / G.halo_z0) * l_disk * bh;
+  if (G.x_b != 0.0) {
+    const double tan_t = std::tan(G.x_theta_rad);
+    const double rp_out = r - az / tan_t;
+    double bx, sin_e, cos_e;
+    if (rp_out >= G.x_rc) {
+      bx = G.x_b * series_exp(-rp_out / G.x_r) * (rp_out / r);
+      sin_e = std::sin(G.x_theta_rad);
+      cos_e = std::cos(G.x_theta_rad);
+    } else {
+      const double f = G.x_rc / (G.x_rc + az / tan_t);
+      const double rp = r * f;
+      bx = G.x_b * series_exp(-rp / G.x_r) * (f * f);
+      const double q = G.x_rc * tan_t;  // tan(elevation) = q / r_p
+      const double nrm = std::sqrt(rp * rp + q * q);
+      sin_e = q / nrm;
+      cos_e = rp / nrm;
+    }
+    b_z += bx * sin_e;
+    if (z > 0.0) b_r += bx * cos_e;
+    if (z < 0.0) b_r -= bx * cos_e;
+  }
+  if (r > 0.0) {
+    const double cr = rx / r, sr = ry / r;  // r_hat = (cr, sr), phi_hat = (-sr, cr)
+    B[0] = b_r * cr - b_phi * sr;
+    B[1] = b_r * sr + b_phi * cr;
+  }
+  B[2] = b_z;
+}
+
 void field_at(const Ctx& C, const double x[3], double B[3]) {
   grid_field(C, x, B);
   if (C.P->flags & ORC_GALACTIC) {
     double G[3];
     galactic_field(*C.P, x, G);
+    B[0] = B[0] + G[0];
+    B[1] = B[1] + G[1];
+    B[2] = B[2] + G[2];
+  }
+  if (C.P->flags & ORC_GMF) {
+    double G[3];
+    gmf_field(*C.P, x, G);
     B[0] = B[0] + G[0];
     B[1] = B[1] + G[1];
     B[2] = B[2] + G[2];

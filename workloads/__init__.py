@@ -144,6 +144,39 @@ GALACTIC_LENS = dict(       # back-tracking through a synthetic galactic field (
 )
 
 
+def flux_free_last_arm(arm_b7, arm_rx, pitch_rad):
+    """Eighth arm strength for which the spiral disk has no net radial flux
+    through a circle: at fixed r, arm j spans ln(rx[j+1] / rx[j]) / tan p in
+    azimuth (rx[8] = rx[0] e^{2 pi tan p}) with B_r = b_j (r_in / r) sin p, so
+    sum_j b_j ln(rx[j+1] / rx[j]) = 0 fixes b_8."""
+    rx = list(arm_rx) + [arm_rx[0] * np.exp(2.0 * np.pi * np.tan(pitch_rad))]
+    w = [np.log(rx[j + 1] / rx[j]) for j in range(8)]
+    return -sum(b * wj for b, wj in zip(arm_b7, w[:7])) / w[7]
+
+
+def multiarm_gmf_params():
+    """Synthetic parameters of the analytic multi-arm galactic field (kpc, uG):
+    eight logarithmic spiral arms (pitch 11.5 deg) between 5 and 20 kpc with a
+    ring inside, a north/south toroidal halo and an X-shaped poloidal field;
+    values chosen for this workload, not fitted to data."""
+    pitch = 11.5 * np.pi / 180.0
+    arm_rx = (5.0, 6.0, 7.0, 8.5, 10.0, 11.5, 13.0, 15.0)
+    arm_b7 = (0.5, 2.5, -1.0, -0.5, -2.0, -3.5, 0.5)
+    arm_b = arm_b7 + (flux_free_last_arm(arm_b7, arm_rx, pitch),)
+    return dict(arm_b=arm_b, arm_rx=arm_rx, pitch_rad=pitch, ring_b=0.2, r_ring=3.0,
+                r_in=5.0, r_out=20.0, h_disk=0.4, w_disk=0.25, halo_bn=1.2, halo_bs=-1.0,
+                halo_rn=9.0, halo_rs=15.0, halo_wh=0.2, halo_z0=5.0, x_b=4.0,
+                x_theta_rad=50.0 * np.pi / 180.0, x_rc=5.0, x_r=3.0, r_cut_in=1.0,
+                r_cut_out=20.0)
+
+
+GALACTIC_MULTIARM = dict(   # back-tracking through the analytic multi-arm field alone
+    name="galactic_backtrack_multiarm_analytic",
+    earth=(-8.5, 0.0, 0.0), border_r=20.0, tol=1e-4, h_min=0.001, h_max=0.05,
+    r_lo=1e18, r_hi=1e20, n_bins=100, nside=64, seed=MASTER_SEED + 7,
+)
+
+
 def galactic_grid_geometry(n=256, box=40.0):
     """Node spacing, lmin (= 2 spacings) and origin of a periodic random-field
     grid of n^3 nodes filling a cube of side `box` centred on the Galactic centre."""
