@@ -63,6 +63,10 @@ def parse():
                          "field, then the galactic lens and its surrogate; cosmology: 1D mode "
                          "with cosmology and the a-posteriori 3D correction (sources to "
                          "4000 Mpc, index -2.2, protons and iron)")
+    ap.add_argument("--galaxy", choices=("disk_halo_random", "multiarm", "multiarm_random"),
+                    default="disk_halo_random",
+                    help="galactic workload field: the disk + halo + random grid, the analytic "
+                         "multi-arm field alone, or the multi-arm field plus the random grid")
     ap.add_argument("--n-train", type=int, default=9_000_000)
     ap.add_argument("--n-test", type=int, default=1_000_000)
     ap.add_argument("--epochs", type=int, default=32)
@@ -667,17 +671,30 @@ def run_galactic(args, keep=False):
     torch.cuda.set_device(0)
     build()
     crp.use_torch_allocator(0)
-    w = workloads.GALACTIC_LENS
+    wr = workloads.GALACTIC_LENS  # the random component's grid
+    galaxy = getattr(args, "galaxy", "disk_halo_random")
+    w = wr if galaxy == "disk_halo_random" else workloads.GALACTIC_MULTIARM
+    wname = w["name"] + ("_random256" if galaxy == "multiarm_random" else "")
     n_all = args.n_train + args.n_test
-    dx, lmin, org = workloads.galactic_grid_geometry(w["grid_n"][0], w["box"])
+    dx, lmin, org = workloads.galactic_grid_geometry(wr["grid_n"][0], wr["box"])
     m = 2_000_000  # border candidates sent through both lenses
     ctx = crp.crp_context_create(0, w["seed"], max(n_all, m) + 1024)
-    grid = crp.crp_grid_create(ctx, crp.grid_desc(w["grid_n"], dx, origin=org, dtype=crp.F32,
-                                                  source=crp.GRID_TURBULENT, lmin=lmin,
-                                                  lmax=w["lmax"], brms=w["brms"], seed=w["seed"]))
-    mods = crp.modules(precision=crp.MIXED, flags=crp.GALACTIC | crp.BORDER, tol=w["tol"],
-                       h_min=w["h_min"], h_max=w["h_max"], field_unit_T=crp.MICROGAUSS_T,
-                       length_unit_m=crp.KPC_M, border_radius=w["border_r"], galactic=w["disk"])
+    if galaxy == "multiarm":  # the analytic field over an all-zero 4^3 grid
+        zn = (4, 4, 4)
+        grid = crp.crp_grid_create(ctx, crp.grid_desc(zn, 20.0, origin=(-40.0, -40.0, -40.0),
+                                                      dtype=crp.F32, data=np.zeros(zn + (3,))))
+    else:
+        grid = crp.crp_grid_create(ctx, crp.grid_desc(wr["grid_n"], dx, origin=org, dtype=crp.F32,
+                                                      source=crp.GRID_TURBULENT, lmin=lmin,
+                                                      lmax=wr["lmax"], brms=wr["brms"],
+                                                      seed=wr["seed"]))
+    if galaxy == "disk_halo_random":
+        analytic = dict(flags=crp.GALACTIC | crp.BORDER, galactic=w["disk"])
+    else:
+        analytic = dict(flags=crp.GMF | crp.BORDER, gmf=workloads.multiarm_gmf_params())
+    mods = crp.modules(precision=crp.MIXED, tol=w["tol"], h_min=w["h_min"], h_max=w["h_max"],
+                       field_unit_T=crp.MICROGAUSS_T, length_unit_m=crp.KPC_M,
+                       border_radius=w["border_r"], **analytic)
     dirs, R = workloads.backtrack_directions(n_all, w["r_lo"], w["r_hi"], w["seed"] + 1)
     inj = crp.host_injection(dict(x=np.full(n_all, w["earth"][0]), y=np.full(n_all, w["earth"][1]),
                                   z=np.full(n_all, w["earth"][2]), ux=dirs[:, 0], uy=dirs[:, 1],
@@ -782,7 +799,7 @@ def run_galactic(args, keep=False):
     chi2, dof, pval = two_sample_chi2(ca, cb)
     corr = float(np.corrcoef(ca, cb)[0, 1])
     summary = {
-        "workload": w["name"], "metric": "galactic back-tracking and lens surrogate",
+        "workload": wname, "metric": "galactic back-tracking and lens surrogate",
         "backtrack": {"candidates": n_all, "accepted_steps": st.accepted_steps,
                       "rejected_trials": st.rejected_trials, "seconds": t_bt,
                       "steps_per_s": st.accepted_steps / t_bt,

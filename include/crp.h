@@ -216,6 +216,51 @@ crp_status crp_candidates_clear(crp_context* ctx);
  * factor (E <- E m_p / m_n); every reset of the interaction states then
  * draws one more uniform, for every species */
 #define CRP_DECAY (1u << 8)
+/* add the analytic multi-arm galactic field of m->gmf (crp_gmf, below) */
+#define CRP_GMF (1u << 9)
+
+/* Analytic multi-arm galactic field of the Jansson-Farrar class (Sect. 4
+ * names analytic galactic field models, JF12 among them; the structure is
+ * that of R. Jansson and G. R. Farrar, ApJ 757:14, 2012, and the parameter
+ * values are the caller's).  Galactocentric cylindrical (r, phi, z) about
+ * m->gal_center, phi = atan2(y, x); lengths and fields in the units of
+ * crp_modules.  L(t, h, w) = 1 / (1 + exp(-2 (|t| - h) / w)).
+ *  disk, times (1 - L(z, h_disk, w_disk)):
+ *    r_ring <= r < r_in:  B = ring_b phi_hat (ring);
+ *    r_in <= r <= r_out:  B = arm_b[j] (r_in / r) (sin p r_hat + cos p phi_hat),
+ *      j = the arm holding the logarithmic spiral (d ln r / d phi = tan p)
+ *      through the point: the spiral crosses phi = pi at
+ *      ln r_x = ln r + (pi - phi) tan p (modulo 2 pi tan p), and arm j holds
+ *      r_x in [arm_rx[j], arm_rx[j+1]), arm_rx[8] = arm_rx[0] e^{2 pi tan p}.
+ *      Divergence-free when sum_j arm_b[j] ln(arm_rx[j+1] / arm_rx[j]) = 0.
+ *  toroidal halo: B_phi = e^{-|z|/halo_z0} L(z, h_disk, w_disk) times
+ *    halo_bn (1 - L(r, halo_rn, halo_wh)) for z >= 0, halo_bs (1 - L(r, halo_rs,
+ *    halo_wh)) for z < 0.
+ *  X field: straight lines in the (r, z) plane crossing the midplane at r_p
+ *    with strength x_b e^{-r_p / x_r} there, flux conserved along each line.
+ *    Where r_p = r - |z| / tan x_theta >= x_rc: elevation x_theta,
+ *    |B| = x_b e^{-r_p/x_r} r_p / r.  Elsewhere r_p = r f, f = x_rc / (x_rc +
+ *    |z| / tan x_theta), elevation atan(x_rc tan x_theta / r_p),
+ *    |B| = x_b e^{-r_p/x_r} f^2.  B_z = |B| sin(elev.), B_r = sign(z) |B| cos(elev.).
+ *  zero inside the sphere r_cut_in and outside r_cut_out (0: no cut); on the
+ *  axis r = 0 only B_z remains.
+ * Requirements (else CRP_E_INVALID): 0 < arm_rx[0] < ... < arm_rx[7] <
+ * arm_rx[0] e^{2 pi tan p}; 0 < |pitch_rad| < pi/2; w_disk, halo_wh, halo_z0 > 0;
+ * r_in > 0; if x_b != 0: 0 < x_theta_rad < pi/2, x_rc > 0, x_r > 0.
+ * The binary64 path evaluates every transcendental with the library's own
+ * series (logarithm, exponential, arctangent by argument halving), so its
+ * field is reproducible bit for bit. */
+typedef struct {
+  double arm_b[8];       /* arm strengths at r = r_in (field units) */
+  double arm_rx[8];      /* arm boundary radii on the phi = pi ray, ascending */
+  double pitch_rad;      /* spiral pitch p */
+  double ring_b;         /* ring field (r_ring <= r < r_in) */
+  double r_ring, r_in, r_out;
+  double h_disk, w_disk; /* disk / halo transition height and width */
+  double halo_bn, halo_bs, halo_rn, halo_rs, halo_wh, halo_z0;
+  double x_b, x_theta_rad, x_rc, x_r;
+  double r_cut_in, r_cut_out;
+} crp_gmf;
 
 typedef struct {
   int32_t precision;         /* CRP_FP64 | CRP_MIXED */
@@ -258,6 +303,8 @@ typedef struct {
                                 and replayed while the launch parameters stay the
                                 same); 0: host-driven rounds.  Same results. */
   int32_t reserved0;
+  const crp_gmf* gmf;        /* with CRP_GMF: the multi-arm field's parameters (host
+                                memory, read during the call); else ignored */
 } crp_modules;
 
 typedef struct {
@@ -429,7 +476,8 @@ crp_status crp_histogram_energy(crp_context* ctx, int32_t what, double e_lo, dou
  * binary64, the length and field units of the grid) exactly as the
  * propagate kernels of m->precision evaluate it: the grid's trilinear
  * interpolation (Sect. 4: grids for fast lookup) plus, with CRP_GALACTIC in
- * m->flags, the analytic disk and halo field of m.  CRP_FP64: binary64 nested
+ * m->flags, the analytic disk and halo field of m, and with CRP_GMF the
+ * multi-arm field of m->gmf.  CRP_FP64: binary64 nested
  * interpolation; CRP_MIXED: binary32 (from the cell polynomial records when
  * the grid has them).  Synchronous. */
 crp_status crp_grid_sample(const crp_grid* grid, const crp_modules* m, int64_t n,

@@ -22,7 +22,7 @@ OK, E_INVALID, E_OOM, E_CUDA, E_QUEUE_FULL, E_TIMEOUT, E_BOUNDS, E_STATE = 0, -1
 F32, F64 = 0, 1
 GRID_FROM_HOST, GRID_FROM_DEVICE, GRID_TURBULENT = 0, 1, 2
 FP64, MIXED = 0, 1
-PAIR, ADIABATIC, PION, PHOTODIS, EMIN, OBSERVER, BORDER, GALACTIC, DECAY = (1 << i for i in range(9))
+PAIR, ADIABATIC, PION, PHOTODIS, EMIN, OBSERVER, BORDER, GALACTIC, DECAY, GMF = (1 << i for i in range(10))
 ACTIVE, BELOW_EMIN, MAX_LENGTH, DETECTED, AT_BORDER, BUDGET = range(6)
 COLLECT_ALL, COLLECT_FINISHED, COLLECT_DETECTED, COLLECT_ACTIVE, COLLECT_AT_BORDER = range(5)
 
@@ -62,6 +62,28 @@ class CandidateArrays(C.Structure):
                 ("on_device", C.c_int32), ("reserved", C.c_int32)]
 
 
+class Gmf(C.Structure):
+    """crp_gmf: the analytic multi-arm galactic field's parameters."""
+    _fields_ = [("arm_b", C.c_double * 8), ("arm_rx", C.c_double * 8), ("pitch_rad", C.c_double),
+                ("ring_b", C.c_double), ("r_ring", C.c_double), ("r_in", C.c_double),
+                ("r_out", C.c_double), ("h_disk", C.c_double), ("w_disk", C.c_double),
+                ("halo_bn", C.c_double), ("halo_bs", C.c_double), ("halo_rn", C.c_double),
+                ("halo_rs", C.c_double), ("halo_wh", C.c_double), ("halo_z0", C.c_double),
+                ("x_b", C.c_double), ("x_theta_rad", C.c_double), ("x_rc", C.c_double),
+                ("x_r", C.c_double), ("r_cut_in", C.c_double), ("r_cut_out", C.c_double)]
+
+
+def gmf(**kw) -> Gmf:
+    """Gmf from keyword values (unset fields 0)."""
+    g = Gmf()
+    for k, v in kw.items():
+        if k in ("arm_b", "arm_rx"):
+            getattr(g, k)[:] = v
+        else:
+            setattr(g, k, v)
+    return g
+
+
 class Modules(C.Structure):
     _fields_ = [("precision", C.c_int32), ("flags", C.c_uint32), ("tol", C.c_double),
                 ("h_min", C.c_double), ("h_max", C.c_double), ("field_unit_T", C.c_double),
@@ -76,7 +98,7 @@ class Modules(C.Structure):
                 ("max_steps", C.c_uint64), ("step_budget", C.c_uint64),
                 ("deadline_ms", C.c_double), ("block_size", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("slice", C.c_uint32), ("queue_order", C.c_int32),
-                ("use_graph", C.c_int32), ("reserved0", C.c_int32)]
+                ("use_graph", C.c_int32), ("reserved0", C.c_int32), ("gmf", C.c_void_p)]
 
 
 class LensDesc(C.Structure):
@@ -618,7 +640,9 @@ def modules(precision=FP64, flags=0, tol=1e-4, h_min=0.01, h_max=1.0, field_unit
             length_unit_m=MPC_M, beta_ad=0.0, e_min=0.0, tables=None, observer_center=(0, 0, 0),
             observer_radius=0.0, border_center=(0, 0, 0), border_radius=0.0, galactic=None,
             max_steps=10_000_000, step_budget=0, deadline_ms=0.0, block_size=0, blocks_per_sm=0,
-            slice=0, queue_order=0, use_graph=0):
+            slice=0, queue_order=0, use_graph=0, gmf=None):
+    """crp_modules; `gmf` (a Gmf or a dict of its fields) is referenced by the
+    returned structure and read during each call that uses it."""
     m = Modules()
     m.precision, m.flags, m.tol, m.h_min, m.h_max = precision, flags, tol, h_min, h_max
     m.field_unit_T, m.length_unit_m, m.beta_ad, m.e_min = field_unit_T, length_unit_m, beta_ad, e_min
@@ -637,4 +661,8 @@ def modules(precision=FP64, flags=0, tol=1e-4, h_min=0.01, h_max=1.0, field_unit
     m.block_size, m.blocks_per_sm, m.slice = block_size, blocks_per_sm, slice
     m.queue_order = queue_order
     m.use_graph = use_graph
+    if gmf is not None:
+        g = gmf if isinstance(gmf, Gmf) else globals()["gmf"](**gmf)
+        m._gmf_ref = g
+        m.gmf = C.addressof(g)
     return m

@@ -976,6 +976,96 @@ static void fill_galactic(const crp_modules* m, KParams& kp) {
       kp.halo_sigma > 0.0 ? (float)(1.0 / (2.0 * kp.halo_sigma * kp.halo_sigma)) : 0.f;
 }
 
+// Multi-arm galactic field: validate m->gmf and convert it.  Each binary64
+// constant is the single expression the model's statement gives (so the
+// binary64 field is reproducible); binary32 copies and reciprocals follow.
+static crp_status fill_gmf(const crp_modules* m, KParams& kp, const char* who) {
+  memset(&kp.gm, 0, sizeof(kp.gm));
+  if (!(m->flags & CRP_GMF)) return CRP_OK;
+  const crp_gmf* g = m->gmf;
+  if (!g) {
+    set_error("%s: CRP_GMF without m->gmf", who);
+    return CRP_E_INVALID;
+  }
+  const double tan_p = tan(g->pitch_rad);
+  const double period = 2.0 * M_PI * tan_p;
+  bool ok = fabs(g->pitch_rad) > 0.0 && fabs(g->pitch_rad) < 0.5 * M_PI && g->arm_rx[0] > 0.0 &&
+            g->w_disk > 0.0 && g->halo_wh > 0.0 && g->halo_z0 > 0.0 && g->r_in > 0.0 &&
+            g->r_cut_in >= 0.0 && g->r_cut_out >= 0.0;
+  for (int j = 1; j < 8 && ok; ++j) ok = g->arm_rx[j] > g->arm_rx[j - 1];
+  ok = ok && tan_p > 0.0 && log(g->arm_rx[7]) - log(g->arm_rx[0]) < period;
+  if (ok && g->x_b != 0.0)
+    ok = g->x_theta_rad > 0.0 && g->x_theta_rad < 0.5 * M_PI && g->x_rc > 0.0 && g->x_r > 0.0;
+  for (int j = 0; j < 8 && ok; ++j) ok = std::isfinite(g->arm_b[j]);
+  if (!ok) {
+    set_error("%s: invalid crp_gmf (arm radii ascending within one spiral turn, "
+              "0 < pitch < pi/2, positive widths, scales and X-field geometry)", who);
+    return CRP_E_INVALID;
+  }
+  GmfView& v = kp.gm;
+  v.ln_r0 = log(g->arm_rx[0]);
+  for (int j = 0; j < 8; ++j) {
+    v.arm_b[j] = g->arm_b[j];
+    v.d_arm[j] = log(g->arm_rx[j]) - v.ln_r0;
+  }
+  v.tan_p = tan_p;
+  v.sin_p = sin(g->pitch_rad);
+  v.cos_p = cos(g->pitch_rad);
+  v.period = period;
+  v.ring_b = g->ring_b;
+  v.r_ring = g->r_ring;
+  v.r_in = g->r_in;
+  v.r_out = g->r_out;
+  v.h_disk = g->h_disk;
+  v.w_disk = g->w_disk;
+  v.halo_bn = g->halo_bn;
+  v.halo_bs = g->halo_bs;
+  v.halo_rn = g->halo_rn;
+  v.halo_rs = g->halo_rs;
+  v.halo_wh = g->halo_wh;
+  v.halo_z0 = g->halo_z0;
+  v.x_b = g->x_b;
+  v.tan_t = g->x_b != 0.0 ? tan(g->x_theta_rad) : 1.0;
+  v.sin_t = sin(g->x_theta_rad);
+  v.cos_t = cos(g->x_theta_rad);
+  v.x_rc = g->x_rc;
+  v.x_r = g->x_r;
+  v.cut_in2 = g->r_cut_in * g->r_cut_in;
+  v.cut_out2 = g->r_cut_out * g->r_cut_out;
+  for (int j = 0; j < 8; ++j) {
+    v.f_arm_b[j] = (float)v.arm_b[j];
+    v.f_d_arm[j] = (float)v.d_arm[j];
+  }
+  v.f_ln_r0 = (float)v.ln_r0;
+  v.f_tan_p = (float)tan_p;
+  v.f_sin_p = (float)v.sin_p;
+  v.f_cos_p = (float)v.cos_p;
+  v.f_period = (float)period;
+  v.f_inv_period = (float)(1.0 / period);
+  v.f_ring_b = (float)v.ring_b;
+  v.f_r_ring = (float)v.r_ring;
+  v.f_r_in = (float)v.r_in;
+  v.f_r_out = (float)v.r_out;
+  v.f_h_disk = (float)v.h_disk;
+  v.f_m2_inv_w_disk = (float)(-2.0 / v.w_disk);
+  v.f_halo_bn = (float)v.halo_bn;
+  v.f_halo_bs = (float)v.halo_bs;
+  v.f_halo_rn = (float)v.halo_rn;
+  v.f_halo_rs = (float)v.halo_rs;
+  v.f_m2_inv_halo_wh = (float)(-2.0 / v.halo_wh);
+  v.f_inv_halo_z0 = (float)(1.0 / v.halo_z0);
+  v.f_x_b = (float)v.x_b;
+  v.f_inv_tan_t = (float)(1.0 / v.tan_t);
+  v.f_sin_t = (float)v.sin_t;
+  v.f_cos_t = (float)v.cos_t;
+  v.f_x_rc = (float)v.x_rc;
+  v.f_inv_x_r = v.x_r > 0.0 ? (float)(1.0 / v.x_r) : 0.f;
+  v.f_q = (float)(v.x_rc * v.tan_t);
+  v.f_cut_in2 = (float)v.cut_in2;
+  v.f_cut_out2 = (float)v.cut_out2;
+  return CRP_OK;
+}
+
 // Graph mode: capture the round loop once (a while node whose body sorts
 // the queue, starts the round and runs the propagate kernel; the loop
 // condition is set on the device) and replay it; rebuilt when the launch
@@ -1135,6 +1225,7 @@ crp_status crp_propagate(crp_context* c, const crp_grid* g, const crp_modules* m
   kp.tab_lg0_f = (float)kp.tab_lg0;
   kp.tab_inv_dlg_f = (float)kp.tab_inv_dlg;
   fill_galactic(m, kp);
+  if (crp_status gs = fill_gmf(m, kp, "crp_propagate")) return gs;
   for (int d = 0; d < 3; ++d) {
     kp.obs_c[d] = m->observer_center[d];
     kp.border_c[d] = m->border_center[d];
@@ -1158,7 +1249,8 @@ crp_status crp_propagate(crp_context* c, const crp_grid* g, const crp_modules* m
   if (!bps) {
     cudaError_t e = m->precision == CRP_FP64
                         ? occupancy_propagate_fp64(kp.f.dtype, block, &bps)
-                        : occupancy_propagate_mixed(kp.f.dtype, (m->flags & CRP_GALACTIC) != 0,
+                        : occupancy_propagate_mixed(kp.f.dtype,
+                                                (m->flags & (CRP_GALACTIC | CRP_GMF)) != 0,
                                                 variant, block, &bps);
     if (e != cudaSuccess) return fail_cuda(e, "crp_propagate: occupancy query");
     if (bps < 1) bps = 1;
@@ -1661,8 +1753,9 @@ extern "C" crp_status crp_grid_sample(const crp_grid* g, const crp_modules* m, i
   KParams kp;
   memset(&kp, 0, sizeof(kp));
   fill_field_view(g, kp.f);
-  kp.flags = m->flags & CRP_GALACTIC;
+  kp.flags = m->flags & (CRP_GALACTIC | CRP_GMF);
   fill_galactic(m, kp);
+  if (crp_status gs = fill_gmf(m, kp, "crp_grid_sample")) return gs;
   const size_t bytes = (size_t)n * 3 * sizeof(double);
   double* dx = static_cast<double*>(dev_alloc(bytes));
   double* dB = static_cast<double*>(dev_alloc(bytes));

@@ -73,8 +73,30 @@ struct FieldView {
   int dtype;
 };
 
+// Multi-arm galactic field (CRP_GMF), converted once on the host: the
+// binary64 constants the FP64 policy evaluates with (each computed by the
+// same single expression as the model's definition states it), and binary32
+// copies for the mixed policy.
+struct GmfView {
+  double arm_b[8];
+  double d_arm[8];        // ln arm_rx[j] - ln arm_rx[0]
+  double ln_r0;           // ln arm_rx[0]
+  double tan_p, sin_p, cos_p, period;  // period = 2 pi tan p
+  double ring_b, r_ring, r_in, r_out, h_disk, w_disk;
+  double halo_bn, halo_bs, halo_rn, halo_rs, halo_wh, halo_z0;
+  double x_b, tan_t, sin_t, cos_t, x_rc, x_r;
+  double cut_in2, cut_out2;  // squared spherical cuts (0: none)
+  float f_arm_b[8], f_d_arm[8];
+  float f_ln_r0, f_tan_p, f_sin_p, f_cos_p, f_period, f_inv_period;
+  float f_ring_b, f_r_ring, f_r_in, f_r_out, f_h_disk, f_m2_inv_w_disk;
+  float f_halo_bn, f_halo_bs, f_halo_rn, f_halo_rs, f_m2_inv_halo_wh, f_inv_halo_z0;
+  float f_x_b, f_inv_tan_t, f_sin_t, f_cos_t, f_x_rc, f_inv_x_r, f_q;
+  float f_cut_in2, f_cut_out2;
+};
+
 struct KParams {
   FieldView f;
+  GmfView gm;
   double tol, tol2, h_min, h_max, curv_k, beta_ad, e_min;
   float e_min_guard_f;  // binary32 E_min plus 1e-4: below it the exact test runs
   double decay_k;       // neutron decay length per eV: c tau_n / (m_n c^2) [length unit]

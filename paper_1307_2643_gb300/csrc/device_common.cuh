@@ -169,6 +169,36 @@ __device__ __forceinline__ double series_exp(double x) {
   return poly * scale;
 }
 
+// Arctangent of y/x in (-pi, pi], step by step so that the binary64
+// multi-arm galactic field is reproducible: t = min(|x|,|y|) / max(|x|,|y|);
+// three halvings atan t = 2 atan(t / (1 + sqrt(1 + t^2))) leave t below
+// tan(pi/32) < 0.0985, where the Taylor series t - t^3/3 + ... - t^15/15
+// (Horner in t^2) has a tail below 1e-17 t; octant and quadrant by
+// atan(1/t) = pi/2 - atan t and atan2(y, -x) = pi - atan2(y, x);
+// atan2(0, 0) = 0.  Division and square root are the IEEE-rounded ones.
+__device__ __forceinline__ double series_atan2(double y, double x) {
+  const double ax = fabs(x), ay = fabs(y);
+  if (ax == 0.0 && ay == 0.0) return 0.0;
+  const bool steep = ay > ax;
+  double t = steep ? ax / ay : ay / ax;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) t = t / (1.0 + sqrt(1.0 + t * t));
+  const double t2 = t * t;
+  double poly = -1.0 / 15.0;
+  poly = poly * t2 + 1.0 / 13.0;
+  poly = poly * t2 - 1.0 / 11.0;
+  poly = poly * t2 + 1.0 / 9.0;
+  poly = poly * t2 - 1.0 / 7.0;
+  poly = poly * t2 + 1.0 / 5.0;
+  poly = poly * t2 - 1.0 / 3.0;
+  poly = poly * t2 + 1.0;
+  const double pi = 3.14159265358979323846;
+  double a = 8.0 * (t * poly);
+  if (steep) a = 0.5 * pi - a;
+  if (x < 0.0) a = pi - a;
+  return y < 0.0 ? -a : a;
+}
+
 // HEALPix RING pixel of a direction (Gorski et al., ApJ 622, 759, 2005):
 // 12 nside^2 equal-area pixels; polar caps |z| > 2/3 and the equatorial
 // belt, pixels numbered ring by ring from the north pole.

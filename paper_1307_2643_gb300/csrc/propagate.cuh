@@ -160,6 +160,142 @@ __device__ __forceinline__ float3 galactic_f32(const KParams& p, float rx, float
   return make_float3(b_r * cr - b_phi * sr, b_r * sr + b_phi * cr, 0.f);
 }
 
+// ---------------------------------------------------------------------------
+// Analytic multi-arm galactic field (CRP_GMF; the model is stated with
+// crp_gmf in crp.h).  Binary64: every operation in the order of the model's
+// statement, transcendentals by the series functions, so the field is
+// reproducible bit for bit.  Binary32: fast intrinsics, for the mixed policy.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double logistic_d(double t, double h, double w) {
+  const double e = -2.0 * (fabs(t) - h) / w;
+  if (e > 700.0) return 0.0;
+  return 1.0 / (1.0 + series_exp(e));
+}
+
+// Arm holding the logarithmic spiral through (r, phi): the spiral's crossing
+// of phi = pi, ln r_x = ln r + (pi - phi) tan p, reduced modulo 2 pi tan p
+// above ln arm_rx[0], and the last arm boundary at or below it.
+template <class T>
+__device__ __forceinline__ T arm_strength(const T (&arm_b)[8], const T (&d_arm)[8], T t) {
+  T b = arm_b[0];
+#pragma unroll
+  for (int j = 1; j < 8; ++j)
+    if (t >= d_arm[j]) b = arm_b[j];
+  return b;
+}
+
+__device__ __forceinline__ void gmf_fp64(const KParams& p, const double x[3], double G[3]) {
+  const GmfView& g = p.gm;
+  const double rx = x[0] - p.gal_c[0], ry = x[1] - p.gal_c[1], z = x[2] - p.gal_c[2];
+  G[0] = 0.0;
+  G[1] = 0.0;
+  G[2] = 0.0;
+  const double R2 = rx * rx + ry * ry + z * z;
+  if (g.cut_in2 > 0.0 && R2 < g.cut_in2) return;
+  if (g.cut_out2 > 0.0 && R2 > g.cut_out2) return;
+  const double r = sqrt(rx * rx + ry * ry);
+  const double az = fabs(z);
+  const double l_disk = logistic_d(z, g.h_disk, g.w_disk);
+  double b_r = 0.0, b_phi = 0.0, b_z = 0.0;
+  if (r >= g.r_ring && r <= g.r_out && r > 0.0) {
+    if (r < g.r_in) {
+      b_phi += g.ring_b * (1.0 - l_disk);
+    } else {
+      const double pi = 3.14159265358979323846;
+      const double phi = series_atan2(ry, rx);
+      double t = series_log(r) + (pi - phi) * g.tan_p - g.ln_r0;
+      t = t - floor(t / g.period) * g.period;
+      if (t < 0.0) t = t + g.period;
+      if (t >= g.period) t = t - g.period;
+      const double bd = arm_strength(g.arm_b, g.d_arm, t) * (g.r_in / r) * (1.0 - l_disk);
+      b_r += bd * g.sin_p;
+      b_phi += bd * g.cos_p;
+    }
+  }
+  const double bh = z >= 0.0 ? g.halo_bn * (1.0 - logistic_d(r, g.halo_rn, g.halo_wh))
+                             : g.halo_bs * (1.0 - logistic_d(r, g.halo_rs, g.halo_wh));
+  b_phi += series_exp(-az / g.halo_z0) * l_disk * bh;
+  if (g.x_b != 0.0) {
+    const double rp_out = r - az / g.tan_t;
+    double bx, sin_e, cos_e;
+    if (rp_out >= g.x_rc) {
+      bx = g.x_b * series_exp(-rp_out / g.x_r) * (rp_out / r);
+      sin_e = g.sin_t;
+      cos_e = g.cos_t;
+    } else {
+      const double f = g.x_rc / (g.x_rc + az / g.tan_t);
+      const double rp = r * f;
+      bx = g.x_b * series_exp(-rp / g.x_r) * (f * f);
+      const double q = g.x_rc * g.tan_t;  // tan(elevation) = q / r_p
+      const double nrm = sqrt(rp * rp + q * q);
+      sin_e = q / nrm;
+      cos_e = rp / nrm;
+    }
+    b_z += bx * sin_e;
+    if (z > 0.0) b_r += bx * cos_e;
+    if (z < 0.0) b_r -= bx * cos_e;
+  }
+  if (r > 0.0) {
+    const double cr = rx / r, sr = ry / r;
+    G[0] = b_r * cr - b_phi * sr;
+    G[1] = b_r * sr + b_phi * cr;
+  }
+  G[2] = b_z;
+}
+
+__device__ __forceinline__ float3 gmf_f32(const KParams& p, float rx, float ry, float z) {
+  const GmfView& g = p.gm;
+  const float rr2 = rx * rx + ry * ry;
+  const float R2 = rr2 + z * z;
+  if (R2 < g.f_cut_in2 || (g.f_cut_out2 > 0.f && R2 > g.f_cut_out2))
+    return make_float3(0.f, 0.f, 0.f);
+  const float az = fabsf(z);
+  // 1 / (1 + e^{-2 (|t| - h) / w}); an overflowing exponential gives 0
+  const float l_disk = 1.f / (1.f + __expf((az - g.f_h_disk) * g.f_m2_inv_w_disk));
+  float b_r = 0.f, b_phi = 0.f, b_z = 0.f;
+  const float ir = rr2 > 0.f ? rsqrtf(rr2) : 0.f;
+  const float r = rr2 * ir;
+  if (r >= g.f_r_ring && r <= g.f_r_out && r > 0.f) {
+    if (r < g.f_r_in) {
+      b_phi = g.f_ring_b * (1.f - l_disk);
+    } else {
+      const float phi = atan2f(ry, rx);
+      float t = __logf(r) + (3.14159265f - phi) * g.f_tan_p - g.f_ln_r0;
+      t -= floorf(t * g.f_inv_period) * g.f_period;
+      if (t < 0.f) t += g.f_period;
+      if (t >= g.f_period) t -= g.f_period;
+      const float bd = arm_strength(g.f_arm_b, g.f_d_arm, t) * (g.f_r_in * ir) * (1.f - l_disk);
+      b_r = bd * g.f_sin_p;
+      b_phi = bd * g.f_cos_p;
+    }
+  }
+  const bool north = z >= 0.f;
+  const float b0 = north ? g.f_halo_bn : g.f_halo_bs;
+  const float rh = north ? g.f_halo_rn : g.f_halo_rs;
+  const float bh = b0 * (1.f - 1.f / (1.f + __expf((r - rh) * g.f_m2_inv_halo_wh)));
+  b_phi += __expf(-az * g.f_inv_halo_z0) * l_disk * bh;
+  if (g.f_x_b != 0.f) {
+    const float rp_out = r - az * g.f_inv_tan_t;
+    float bx, sin_e, cos_e;
+    if (rp_out >= g.f_x_rc) {
+      bx = g.f_x_b * __expf(-rp_out * g.f_inv_x_r) * (rp_out * ir);
+      sin_e = g.f_sin_t;
+      cos_e = g.f_cos_t;
+    } else {
+      const float f = __fdividef(g.f_x_rc, g.f_x_rc + az * g.f_inv_tan_t);
+      const float rp = r * f;
+      bx = g.f_x_b * __expf(-rp * g.f_inv_x_r) * (f * f);
+      const float inrm = rsqrtf(rp * rp + g.f_q * g.f_q);
+      sin_e = g.f_q * inrm;
+      cos_e = rp * inrm;
+    }
+    b_z = bx * sin_e;
+    b_r += z > 0.f ? bx * cos_e : (z < 0.f ? -bx * cos_e : 0.f);
+  }
+  const float cr = rx * ir, sr = ry * ir;
+  return make_float3(b_r * cr - b_phi * sr, b_r * sr + b_phi * cr, b_z);
+}
+
 // Dynamic shared memory of the propagate kernels (FP64: stage vectors;
 // mixed: per-lane cell-record cache).
 extern __shared__ __align__(16) unsigned char crp_dyn_smem[];
@@ -208,6 +344,13 @@ __device__ __forceinline__ void field_fp64(const KParams& p, const double x[3], 
   if (p.flags & CRP_GALACTIC) {
     double G[3];
     galactic_fp64(p, x, G);
+    B[0] = B[0] + G[0];
+    B[1] = B[1] + G[1];
+    B[2] = B[2] + G[2];
+  }
+  if (p.flags & CRP_GMF) {
+    double G[3];
+    gmf_fp64(p, x, G);
     B[0] = B[0] + G[0];
     B[1] = B[1] + G[1];
     B[2] = B[2] + G[2];
@@ -986,10 +1129,19 @@ struct PolicyMixedT {
                  lerp(lerp(v4.z, v5.z, tx), lerp(v6.z, v7.z, tx), ty), tz);
     }
     if constexpr (GAL) {
-      const float3 G = galactic_f32(p, c.gal[0] + ox, c.gal[1] + oy, c.gal[2] + oz);
-      B.x += G.x;
-      B.y += G.y;
-      B.z += G.z;
+      const float gx = c.gal[0] + ox, gy = c.gal[1] + oy, gz = c.gal[2] + oz;
+      if (p.flags & CRP_GALACTIC) {
+        const float3 G = galactic_f32(p, gx, gy, gz);
+        B.x += G.x;
+        B.y += G.y;
+        B.z += G.z;
+      }
+      if (p.flags & CRP_GMF) {
+        const float3 G = gmf_f32(p, gx, gy, gz);
+        B.x += G.x;
+        B.y += G.y;
+        B.z += G.z;
+      }
     }
     return B;
   }

@@ -24,7 +24,7 @@ cudaError_t occupancy_variant(int dtype, int variant, int block, int* bps) {
 
 cudaError_t launch_propagate_mixed(const KParams& kp, const DevState& st, DevCounters* dc,
                                    int grid, int block, int variant, cudaStream_t s) {
-  return (kp.flags & CRP_GALACTIC) ? launch_variant<PolicyMixedGal>(kp, st, dc, grid, block,
+  return (kp.flags & (CRP_GALACTIC | CRP_GMF)) ? launch_variant<PolicyMixedGal>(kp, st, dc, grid, block,
                                                                     variant, s)
                                    : launch_variant<PolicyMixed>(kp, st, dc, grid, block,
                                                                  variant, s);
@@ -71,7 +71,7 @@ cudaError_t sample_policy(const KParams& kp, const double* xyz, int64_t n, doubl
 
 cudaError_t sample_field_mixed(const KParams& kp, const double* xyz, int64_t n, double* B,
                                cudaStream_t s) {
-  return (kp.flags & CRP_GALACTIC) ? sample_policy<PolicyMixedGal>(kp, xyz, n, B, s)
+  return (kp.flags & (CRP_GALACTIC | CRP_GMF)) ? sample_policy<PolicyMixedGal>(kp, xyz, n, B, s)
                                    : sample_policy<PolicyMixed>(kp, xyz, n, B, s);
 }
 

@@ -46,10 +46,11 @@ def test_struct_layouts_match_c(crp, tmp_path):
     prog = tmp_path / "sizes.c"
     prog.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "crp.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu\\n\","
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\","
         "sizeof(crp_grid_desc), sizeof(crp_tables_desc), sizeof(crp_candidate_arrays),"
         "sizeof(crp_modules), sizeof(crp_stats), sizeof(crp_record),"
-        "offsetof(crp_modules, tables), offsetof(crp_record, status));return 0;}\n")
+        "offsetof(crp_modules, tables), offsetof(crp_record, status),"
+        "sizeof(crp_gmf), offsetof(crp_modules, gmf), sizeof(crp_cosmology));return 0;}\n")
     exe = tmp_path / "sizes"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)],
                    check=True)
@@ -58,7 +59,8 @@ def test_struct_layouts_match_c(crp, tmp_path):
     want = [ctypes.sizeof(crp.GridDesc), ctypes.sizeof(crp.TablesDesc),
             ctypes.sizeof(crp.CandidateArrays), ctypes.sizeof(crp.Modules),
             ctypes.sizeof(crp.Stats), crp.RECORD_DTYPE.itemsize,
-            crp.Modules.tables.offset, crp.RECORD_DTYPE.fields["status"][1]]
+            crp.Modules.tables.offset, crp.RECORD_DTYPE.fields["status"][1],
+            ctypes.sizeof(crp.Gmf), crp.Modules.gmf.offset, ctypes.sizeof(crp.Cosmology)]
     assert got == want
 
 
