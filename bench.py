@@ -138,8 +138,11 @@ def setup_dist(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     dist = None
     if world > 1:
+        import torch
         import torch.distributed as dist
-        dist.init_process_group("gloo")
+        # host scalars over gloo; the device spectra over NCCL
+        backend = "cpu:gloo,cuda:nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
     return rank, world, local, dist
 
 
@@ -150,9 +153,22 @@ def bench_config(w, n, world):
             "parallelism": f"candidate shards x{world}"}
 
 
+SPECTRUM = dict(e_lo=1e18, e_hi=1e21, nbins=60)  # detected-energy histogram, 20 bins/decade
+
+
+def merge_spectrum(dist, hist):
+    """The data exchange of a multi-rank step: each rank propagates its own
+    candidate shard and histograms what its observer detected; the job's
+    spectrum is the sum over ranks (all-reduce, in place, on the histogram's
+    device)."""
+    if dist:
+        dist.all_reduce(hist)
+    return hist
+
+
 def aggregate_ranks(dist, elapsed, steps):
     """Whole-job figures: the slowest rank's time and the steps of all ranks
-    (each rank propagates its own shard; this is the only collective)."""
+    (each rank propagates its own shard)."""
     if not dist:
         return elapsed, float(steps)
     import torch
@@ -227,10 +243,15 @@ def run_ours(args):
     pinned = {k: torch.from_numpy(v).pin_memory() for k, v in inj.items()}
     arr_host = crp.candidate_arrays(pinned, on_device=False)
 
+    hist = torch.zeros(SPECTRUM["nbins"], dtype=torch.int64, device="cuda")
+
     def one_step(arrays):
         crp.crp_candidates_clear(ctx)
         crp.crp_candidates_inject(ctx, arrays, n, 0, sh)
         _, st = crp.crp_propagate(ctx, grid, mods, sh)
+        crp.crp_histogram_energy_device(ctx, crp.COLLECT_DETECTED, SPECTRUM["e_lo"],
+                                        SPECTRUM["e_hi"], SPECTRUM["nbins"], hist, stream=sh)
+        merge_spectrum(dist, hist)
         return st
 
     for _ in range(args.warmup):
@@ -358,9 +379,14 @@ def run_ours(args):
             "accepted_steps": acc, "rejected_trials": rej,
             "rejected_trials_per_s": rej / elapsed,
             "kernel_ms_per_step": kern_ms / args.steps,
-            # per step: inject (1), queue build (2), queue sort (3); per round:
-            # host loop = reset + propagate (+ sort of requeued work), graph = 5
-            "gpu_launches": int(args.steps * 6 + launches * (5 if args.graph else 2)),
+            # per step: inject (1), queue build (2), queue sort (3), detected-
+            # energy histogram (1); per round: host loop = reset + propagate
+            # (+ sort of requeued work), graph = 5
+            "gpu_launches": int(args.steps * 7 + launches * (5 if args.graph else 2)),
+            "spectrum": {"bins": SPECTRUM["nbins"], "e_lo_eV": SPECTRUM["e_lo"],
+                         "e_hi_eV": SPECTRUM["e_hi"], "detected_last_step": int(hist.sum()),
+                         "exchange": "sum over ranks on the device (NCCL all-reduce)"
+                                     if world > 1 else "single rank: none"},
             "e2e": e2e, "fp64": fp64, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
             "measured_peaks": probe,
         }

@@ -472,6 +472,15 @@ crp_status crp_histogram_healpix(crp_context* ctx, int32_t what, int32_t nside, 
 crp_status crp_histogram_energy(crp_context* ctx, int32_t what, double e_lo, double e_hi,
                                 int32_t nbins, uint64_t* out, void* stream);
 
+/* The same histogram counted into the caller's device array out_dev (nbins
+ * uint64 on the context's device, 8-byte aligned): cleared first, or added
+ * to when accumulate != 0.  Asynchronous on `stream`; no allocation, no
+ * synchronisation, so per-rank spectra can be merged on the device by a
+ * collective (sum) before anything returns to the host. */
+crp_status crp_histogram_energy_device(crp_context* ctx, int32_t what, double e_lo, double e_hi,
+                                       int32_t nbins, uint64_t* out_dev, int32_t accumulate,
+                                       void* stream);
+
 /* The magnetic field at n points (host arrays xyz [n][3] and B_out [n][3],
  * binary64, the length and field units of the grid) exactly as the
  * propagate kernels of m->precision evaluate it: the grid's trilinear

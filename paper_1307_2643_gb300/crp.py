@@ -162,6 +162,7 @@ SYMBOLS = (
     "crp_tables_build", "crp_tables_from_host", "crp_tables_copy_out", "crp_tables_destroy",
     "crp_candidates_inject", "crp_candidates_clear",
     "crp_propagate", "crp_collect", "crp_histogram_energy", "crp_histogram_energy_noalloc",
+    "crp_histogram_energy_device",
     "crp_lens_build", "crp_lens_apply", "crp_lens_copy_out", "crp_lens_destroy",
     "crp_histogram_healpix",
     "crp_mlp_create", "crp_mlp_destroy", "crp_mlp_num_params", "crp_mlp_set_params",
@@ -206,6 +207,8 @@ def lib():
             L.crp_collect.argtypes = [p, i32, p, sz, C.POINTER(sz), i32, p]
             L.crp_histogram_energy.argtypes = [p, i32, C.c_double, C.c_double, i32, p, p]
             L.crp_histogram_energy_noalloc.argtypes = [p, i32, C.c_double, C.c_double, i32, p, p]
+            L.crp_histogram_energy_device.argtypes = [p, i32, C.c_double, C.c_double, i32, p, i32,
+                                                      p]
             L.crp_lens_build.argtypes = [p, p, C.POINTER(Modules), C.POINTER(LensDesc), C.POINTER(p),
                                          C.POINTER(Stats)]
             L.crp_lens_apply.argtypes = [p, p, i32, p]
@@ -564,6 +567,15 @@ def crp_measure_peaks(device=0):
     pk = Peaks()
     _check(lib().crp_measure_peaks(device, C.byref(pk)))
     return {k: getattr(pk, k) for k, _ in Peaks._fields_}
+
+
+def crp_histogram_energy_device(ctx, what, e_lo, e_hi, nbins, out_dev, accumulate=False,
+                                stream=None):
+    """crp_histogram_energy into a device array (a torch int64/uint64 tensor of
+    nbins on the context's device); asynchronous on `stream`."""
+    _check(lib().crp_histogram_energy_device(ctx, what, e_lo, e_hi, nbins, _addr(out_dev),
+                                             1 if accumulate else 0, stream))
+    return out_dev
 
 
 HIST_NOALLOC_MAX_BINS = 4096

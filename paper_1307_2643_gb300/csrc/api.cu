@@ -1475,6 +1475,28 @@ crp_status crp_histogram_energy(crp_context* c, int32_t what, double e_lo, doubl
   return e == cudaSuccess ? CRP_OK : fail_cuda(e, "crp_histogram_energy");
 }
 
+crp_status crp_histogram_energy_device(crp_context* c, int32_t what, double e_lo, double e_hi,
+                                       int32_t nbins, uint64_t* out_dev, int32_t accumulate,
+                                       void* stream) {
+  if (!c || !out_dev || nbins < 1 || !(e_lo > 0.0) || !(e_hi > e_lo) ||
+      what < CRP_COLLECT_ALL || what > CRP_COLLECT_AT_BORDER) {
+    set_error("crp_histogram_energy_device: bad argument");
+    return CRP_E_INVALID;
+  }
+  DeviceGuard dg(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned long long* bins = reinterpret_cast<unsigned long long*>(out_dev);
+  cudaError_t e = cudaSuccess;
+  if (!accumulate) e = cudaMemsetAsync(bins, 0, 8 * (size_t)nbins, s);
+  if (e == cudaSuccess && c->size > 0) {
+    const double l0 = log(e_lo), inv = (double)nbins / (log(e_hi) - l0);
+    k_hist_energy<<<blocks_for(c->size, 256), 256, 0, s>>>(c->st.status, c->st.E, c->size, what,
+                                                           l0, inv, nbins, bins);
+    e = cudaGetLastError();
+  }
+  return e == cudaSuccess ? CRP_OK : fail_cuda(e, "crp_histogram_energy_device");
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

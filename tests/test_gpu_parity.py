@@ -669,3 +669,30 @@ def test_field_sampling_matches_oracle(galactic):
         crp.crp_context_destroy(ctx)
 
 
+
+
+def test_histogram_device_matches_host():
+    """crp_histogram_energy_device counts into a device array what
+    crp_histogram_energy returns on the host; accumulate adds; an empty pool
+    leaves the array cleared."""
+    import torch
+    n = 5000
+    inj = crp.host_injection(workloads.plain_small(n=n, seed=23))
+    inj["E"][:] = 10 ** np.random.default_rng(3).uniform(17.5, 21.5, n)
+    ctx = crp.crp_context_create(0, 5, n)
+    try:
+        crp.crp_candidates_inject(ctx, crp.candidate_arrays(inj), n)
+        ref = crp.crp_histogram_energy(ctx, crp.COLLECT_ALL, 1e18, 1e21, 60)
+        dev = torch.full((60,), 99, dtype=torch.int64, device="cuda")
+        crp.crp_histogram_energy_device(ctx, crp.COLLECT_ALL, 1e18, 1e21, 60, dev)
+        torch.cuda.synchronize()
+        assert np.array_equal(dev.cpu().numpy(), ref.astype(np.int64)) and 0 < ref.sum() < n
+        crp.crp_histogram_energy_device(ctx, crp.COLLECT_ALL, 1e18, 1e21, 60, dev, accumulate=True)
+        torch.cuda.synchronize()
+        assert np.array_equal(dev.cpu().numpy(), 2 * ref.astype(np.int64))
+        crp.crp_candidates_clear(ctx)
+        crp.crp_histogram_energy_device(ctx, crp.COLLECT_ALL, 1e18, 1e21, 60, dev)
+        torch.cuda.synchronize()
+        assert not dev.cpu().numpy().any()
+    finally:
+        crp.crp_context_destroy(ctx)

@@ -1,7 +1,7 @@
 """The multi-rank bench path on CPU (gloo, world size 2): every rank draws its
-own candidate shard (disjoint ids, distinct draws, no data exchange), and
-the only collective turns per-rank times and step counts into whole-job
-figures (slowest rank's time, sum of steps)."""
+own candidate shard (disjoint ids, distinct draws), the per-rank spectra are
+summed over ranks (the one data exchange), and per-rank times and step counts
+become whole-job figures (slowest rank's time, sum of steps)."""
 import os
 import socket
 
@@ -32,7 +32,13 @@ def _rank(rank, world, port, out):
         e = torch.from_numpy(inj["E"])
         energies = [torch.zeros_like(e) for _ in range(world)]
         dist.all_gather(energies, e)
-        out[rank] = (elapsed, steps, [g.numpy() for g in gathered], [x.numpy() for x in energies])
+        # the spectrum exchange: per-rank histograms summed over ranks
+        edges = np.geomspace(bench.SPECTRUM["e_lo"], bench.SPECTRUM["e_hi"],
+                             bench.SPECTRUM["nbins"] + 1)
+        hist = torch.from_numpy(np.histogram(inj["E"], edges)[0].astype(np.int64))
+        merged = bench.merge_spectrum(dist, hist.clone()).numpy()
+        out[rank] = (elapsed, steps, [g.numpy() for g in gathered], [x.numpy() for x in energies],
+                     merged, hist.numpy())
     finally:
         dist.destroy_process_group()
 
@@ -44,8 +50,11 @@ def test_two_rank_shards_and_aggregation():
         out = m.dict()
         mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
+    edges = np.geomspace(bench.SPECTRUM["e_lo"], bench.SPECTRUM["e_hi"], bench.SPECTRUM["nbins"] + 1)
     for r in range(world):
-        elapsed, steps, ids, energies = res[r]
+        elapsed, steps, ids, energies, merged, own = res[r]
+        assert np.array_equal(merged, np.histogram(np.concatenate(energies), edges)[0])
+        assert not np.array_equal(merged, own) and merged.sum() > own.sum() > 0
         assert elapsed == 2.0            # the slowest rank's time
         assert steps == 3000.0           # the sum over ranks
         assert len(np.intersect1d(ids[0], ids[1])) == 0
