@@ -20,6 +20,7 @@
 #include <string.h>
 
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "crp_internal.cuh"
@@ -52,6 +53,11 @@ struct crp_mlp {
   std::vector<__nv_bfloat16*> h;  // activations of each hidden layer [cap][hidden]
   __nv_bfloat16 *dz, *dz2, *dzt, *ht;
   float *y, *dy, *loss;
+  // tensor-core training workspace: transposed activations of the layers that
+  // feed a hidden GEMM, and two transposed backward signals [hidden][tcap]
+  int64_t tcap;
+  std::vector<__nv_bfloat16*> hT;
+  __nv_bfloat16 *dzT, *dzT2;
 };
 
 namespace {
@@ -174,21 +180,6 @@ __global__ void __launch_bounds__(GEMM_THREADS)
       }
 }
 
-// First layer (K = n_in, small): H1 = bf16(relu(x W1^T + b1)).
-__global__ void k_layer_in(const float* __restrict__ x, int n_in, int64_t n,
-                           const float* __restrict__ W, const float* __restrict__ b, int hidden,
-                           __nv_bfloat16* __restrict__ h) {
-  const int64_t total = n * hidden;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e / hidden;
-    const int o = (int)(e % hidden);
-    float acc = b[o];
-    for (int i = 0; i < n_in; ++i) acc = fmaf(W[o * n_in + i], x[r * n_in + i], acc);
-    h[e] = __float2bfloat16_rn(fmaxf(acc, 0.f));
-  }
-}
-
 // Output layer and loss: y = h W^T + b (one warp per sample); y_hat = y/|y|;
 // when t is given, loss += 1 - y_hat.t and dy = -(t - (y_hat.t) y_hat)/|y|/n.
 __global__ void k_layer_out(const __nv_bfloat16* __restrict__ h, int64_t n, int hidden,
@@ -198,6 +189,7 @@ __global__ void k_layer_out(const __nv_bfloat16* __restrict__ h, int64_t n, int 
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  float lsum = 0.f;  // this warp's loss terms (lane 0)
   for (int64_t r = warp; r < n; r += nw) {
     float y[3] = {0.f, 0.f, 0.f};
     for (int i = lane; i < hidden; i += 32) {
@@ -215,11 +207,38 @@ __global__ void k_layer_out(const __nv_bfloat16* __restrict__ h, int64_t n, int 
         for (int c = 0; c < 3; ++c) y_hat[r * 3 + c] = yh[c];
       if (t) {
         const float d = yh[0] * t[r * 3] + yh[1] * t[r * 3 + 1] + yh[2] * t[r * 3 + 2];
-        atomicAdd(loss, 1.f - d);
+        lsum += 1.f - d;
         for (int c = 0; c < 3; ++c)
           dy[r * 3 + c] = -(t[r * 3 + c] - d * yh[c]) * inv / (float)n;
       }
     }
+  }
+  if (t) {  // one atomic per block
+    __shared__ float part[32];
+    if (lane == 0) part[threadIdx.x >> 5] = lsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float b = 0.f;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += part[w];
+      atomicAdd(loss, b);
+    }
+  }
+}
+
+// ---- generic-shape kernels (any hidden width and input count); the fast
+// kernels below cover hidden a multiple of 256 with at most 8 inputs ----
+// First layer (K = n_in, small): H1 = bf16(relu(x W1^T + b1)).
+__global__ void k_layer_in(const float* __restrict__ x, int n_in, int64_t n,
+                           const float* __restrict__ W, const float* __restrict__ b, int hidden,
+                           __nv_bfloat16* __restrict__ h) {
+  const int64_t total = n * hidden;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / hidden;
+    const int o = (int)(e % hidden);
+    float acc = b[o];
+    for (int i = 0; i < n_in; ++i) acc = fmaf(W[o * n_in + i], x[r * n_in + i], acc);
+    h[e] = __float2bfloat16_rn(fmaxf(acc, 0.f));
   }
 }
 
@@ -269,6 +288,202 @@ __global__ void k_colsum(const __nv_bfloat16* __restrict__ z, int64_t n, int col
   float acc = 0.f;
   for (int64_t r = blockIdx.x; r < n; r += gridDim.x) acc += __bfloat162float(z[r * cols + c]);
   atomicAdd(db + c, acc);
+}
+
+// Column moments of a bf16 matrix Z [n][H] (H a multiple of 256) against a
+// thin FP32 matrix X [n][NX]: for every column c and i < NX,
+//   W[c * wc + i * wi] += sum_r Z[r][c] X[r][i],
+// and the bias sums: BX false: b[c] += sum_r Z[r][c]; BX true: b[i] +=
+// sum_r X[r][i].  Each warp takes rows r (stride: all warps of the grid) and
+// lane l the 8 columns 8 l .. 8 l + 7 of every 256-column group (one 16-byte
+// load per row); four rows are loaded before they are used.  The block's
+// warps are summed in shared memory and each sum is added once per block.
+template <int NX, bool BX>
+__global__ void __launch_bounds__(256) k_col_moments(const __nv_bfloat16* __restrict__ Z, int64_t n,
+                                                     int H, const float* __restrict__ X,
+                                                     float* __restrict__ W, int wc, int wi,
+                                                     float* __restrict__ b) {
+  constexpr int NQ = NX + 1;  // quantities per column: NX moments and the bias sum
+  __shared__ float part[8][256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t wstride = (int64_t)gridDim.x * 8;
+  for (int cg = 0; cg < H; cg += 256) {
+    float acc[8][NQ];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+#pragma unroll
+      for (int k = 0; k < NQ; ++k) acc[q][k] = 0.f;
+    float xs[NX > 0 ? NX : 1];  // BX: this warp's sums of X (lane 0)
+#pragma unroll
+    for (int k = 0; k < (NX > 0 ? NX : 1); ++k) xs[k] = 0.f;
+    for (int64_t r0 = blockIdx.x * 8 + warp; r0 < n; r0 += 4 * wstride) {
+      uint4 zq[4];
+      float xv[4][NX > 0 ? NX : 1];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t r = r0 + u * wstride;
+        zq[u] = r < n ? __ldg(reinterpret_cast<const uint4*>(Z + r * H + cg) + lane)
+                      : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int k = 0; k < NX; ++k) xv[u][k] = r < n ? __ldg(X + r * NX + k) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const __nv_bfloat16* zb = reinterpret_cast<const __nv_bfloat16*>(&zq[u]);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float z = __bfloat162float(zb[q]);
+#pragma unroll
+          for (int k = 0; k < NX; ++k) acc[q][k] = fmaf(z, xv[u][k], acc[q][k]);
+          acc[q][NX] += z;
+        }
+        if (BX)
+#pragma unroll
+          for (int k = 0; k < NX; ++k) xs[k] += xv[u][k];
+      }
+    }
+    // block sums, one quantity at a time through shared memory
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+      if (BX && k == NX) break;  // the bias comes from X below
+#pragma unroll
+      for (int q = 0; q < 8; ++q) part[warp][8 * lane + q] = acc[q][k];
+      __syncthreads();
+      float v = 0.f;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) v += part[w][threadIdx.x];
+      const int c = cg + threadIdx.x;
+      if (k < NX)
+        atomicAdd(W + (int64_t)c * wc + (int64_t)k * wi, v);
+      else
+        atomicAdd(b + c, v);
+      __syncthreads();
+    }
+    if (BX && cg == 0) {
+      if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NX; ++k) part[warp][k] = xs[k];
+      __syncthreads();
+      if (threadIdx.x < NX) {
+        float v = 0.f;
+        for (int w = 0; w < 8; ++w) v += part[w][threadIdx.x];
+        atomicAdd(b + threadIdx.x, v);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Writes the staged 32-row tile T (32 x 256 bf16 of columns cg ..) into the
+// transposed matrix outT [H][n]: thread t writes column cg + t, rows r0 ..
+// r0 + 31, as 64 contiguous bytes (rows past n are skipped).
+__device__ __forceinline__ void store_tile_transposed(const __nv_bfloat16 (*T)[264], int cg,
+                                                      int64_t r0, int64_t n,
+                                                      __nv_bfloat16* __restrict__ outT) {
+  __nv_bfloat16* dst = outT + (int64_t)(cg + threadIdx.x) * n + r0;
+  if (r0 + 32 <= n && n % 8 == 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      __align__(16) __nv_bfloat16 col[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) col[e] = T[8 * q + e][threadIdx.x];
+      reinterpret_cast<uint4*>(dst)[q] = *reinterpret_cast<const uint4*>(col);
+    }
+  } else {
+    for (int rr = 0; rr < 32 && r0 + rr < n; ++rr) dst[rr] = T[rr][threadIdx.x];
+  }
+}
+
+// First layer, hidden a multiple of 256 and n_in <= 8: h = bf16(relu(W1 x +
+// b1)).  A block of 8 warps takes 32 rows, one row per warp at a time; lane l
+// computes columns 8 l .. 8 l + 7 of each 256-column group (its weights held
+// in registers) and stores them as one 16-byte word.  With hT the tile is
+// staged in shared memory and written transposed.
+__global__ void __launch_bounds__(256) k_layer_in_tile(const float* __restrict__ x, int n_in,
+                                                       int64_t n, const float* __restrict__ W,
+                                                       const float* __restrict__ b, int hidden,
+                                                       __nv_bfloat16* __restrict__ h,
+                                                       __nv_bfloat16* __restrict__ hT) {
+  __shared__ __align__(16) __nv_bfloat16 T[32][264];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t r0 = blockIdx.x * 32ll;
+  for (int cg = 0; cg < hidden; cg += 256) {
+    const int c0 = cg + 8 * lane;
+    float w[8][8], bb[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      bb[q] = __ldg(b + c0 + q);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) w[q][i] = i < n_in ? __ldg(W + (c0 + q) * n_in + i) : 0.f;
+    }
+    for (int rr = warp; rr < 32; rr += 8) {
+      const int64_t r = r0 + rr;
+      if (r >= n) break;
+      float xin[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) xin[i] = i < n_in ? __ldg(x + r * n_in + i) : 0.f;
+      __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        float acc = bb[q];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          if (i < n_in) acc = fmaf(w[q][i], xin[i], acc);
+        v[q] = __float2bfloat16_rn(fmaxf(acc, 0.f));
+      }
+      *reinterpret_cast<uint4*>(h + r * hidden + c0) = *reinterpret_cast<const uint4*>(v);
+      if (hT) *reinterpret_cast<uint4*>(&T[rr][8 * lane]) = *reinterpret_cast<const uint4*>(v);
+    }
+    if (hT) {
+      __syncthreads();
+      store_tile_transposed(T, cg, r0, n, hT);
+      __syncthreads();
+    }
+  }
+}
+
+// Output layer backward, hidden a multiple of 256: dz[r][c] = bf16(dy_r .
+// W_out[:, c] where h[r][c] > 0, else 0), tiled as k_layer_in_tile, with dzT
+// (when given) written transposed.
+__global__ void __launch_bounds__(256) k_out_backward_tile(const float* __restrict__ dy, int64_t n,
+                                                           int hidden, const float* __restrict__ W,
+                                                           const __nv_bfloat16* __restrict__ h,
+                                                           __nv_bfloat16* __restrict__ dz,
+                                                           __nv_bfloat16* __restrict__ dzT) {
+  __shared__ __align__(16) __nv_bfloat16 T[32][264];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t r0 = blockIdx.x * 32ll;
+  for (int cg = 0; cg < hidden; cg += 256) {
+    const int c0 = cg + 8 * lane;
+    float w0[8], w1[8], w2[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      w0[q] = __ldg(W + c0 + q);
+      w1[q] = __ldg(W + hidden + c0 + q);
+      w2[q] = __ldg(W + 2 * hidden + c0 + q);
+    }
+    for (int rr = warp; rr < 32; rr += 8) {
+      const int64_t r = r0 + rr;
+      if (r >= n) break;
+      const float d0 = __ldg(dy + 3 * r), d1 = __ldg(dy + 3 * r + 1), d2 = __ldg(dy + 3 * r + 2);
+      const uint4 hq = __ldg(reinterpret_cast<const uint4*>(h + r * hidden + c0));
+      const __nv_bfloat16* hv = reinterpret_cast<const __nv_bfloat16*>(&hq);
+      __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        float g = d0 * w0[q] + d1 * w1[q] + d2 * w2[q];
+        if (!(__bfloat162float(hv[q]) > 0.f)) g = 0.f;
+        v[q] = __float2bfloat16_rn(g);
+      }
+      *reinterpret_cast<uint4*>(dz + r * hidden + c0) = *reinterpret_cast<const uint4*>(v);
+      if (dzT) *reinterpret_cast<uint4*>(&T[rr][8 * lane]) = *reinterpret_cast<const uint4*>(v);
+    }
+    if (dzT) {
+      __syncthreads();
+      store_tile_transposed(T, cg, r0, n, dzT);
+      __syncthreads();
+    }
+  }
 }
 
 // Transpose a bf16 [rows][cols] matrix into [cols][rows] (32 x 32 tiles).
@@ -353,6 +568,36 @@ void free_ws(crp_mlp* M) {
   M->cap = 0;
 }
 
+void free_tws(crp_mlp* M) {
+  for (auto* p : M->hT) dev_free(p);
+  M->hT.clear();
+  dev_free(M->dzT);
+  dev_free(M->dzT2);
+  M->dzT = M->dzT2 = nullptr;
+  M->tcap = 0;
+}
+
+// Transposed activations for the tensor-core training step (allocated only
+// when training on that path).
+crp_status ensure_tws(crp_mlp* M, int64_t n) {
+  if (M->tcap >= n) return CRP_OK;
+  free_tws(M);
+  const size_t hb = sizeof(__nv_bfloat16) * (size_t)n * M->hidden;
+  for (int l = 0; l + 1 < M->n_hidden; ++l)
+    M->hT.push_back(static_cast<__nv_bfloat16*>(dev_alloc(hb)));
+  M->dzT = static_cast<__nv_bfloat16*>(dev_alloc(hb));
+  M->dzT2 = static_cast<__nv_bfloat16*>(dev_alloc(hb));
+  bool ok = M->dzT && M->dzT2;
+  for (auto* p : M->hT) ok = ok && p;
+  if (!ok) {
+    free_tws(M);
+    set_error("mlp: cannot allocate the training workspace for %lld samples", (long long)n);
+    return CRP_E_OOM;
+  }
+  M->tcap = n;
+  return CRP_OK;
+}
+
 crp_status ensure_ws(crp_mlp* M, int64_t n) {
   if (M->cap >= n) return CRP_OK;
   free_ws(M);
@@ -385,6 +630,87 @@ crp_status refresh_bf16(crp_mlp* M, cudaStream_t s) {
   return e == cudaSuccess ? CRP_OK : fail_cuda(e, "mlp: bf16 weights");
 }
 
+// Launchers of the thin layers: the tiled / column-moment kernels when the
+// hidden width is a multiple of 256 and there are at most 8 inputs (the
+// surrogate's shape, and every shape the tensor-core path takes), the
+// generic kernels otherwise.
+bool fast_shape(const crp_mlp* M) { return M->hidden % 256 == 0 && M->n_in <= 8; }
+
+unsigned red_blocks(const crp_mlp* M) {
+  return (unsigned)(2 * (M->sm_count > 0 ? M->sm_count : 152));
+}
+
+void launch_layer_in(crp_mlp* M, const float* x, int64_t n, __nv_bfloat16* hT, cudaStream_t s) {
+  const float* W = M->params + M->w_off[0];
+  const float* b = M->params + M->b_off[0];
+  if (fast_shape(M))
+    k_layer_in_tile<<<(unsigned)((n + 31) / 32), 256, 0, s>>>(x, M->n_in, n, W, b, M->hidden,
+                                                               M->h[0], hT);
+  else
+    k_layer_in<<<nblk(n * M->hidden, 256), 256, 0, s>>>(x, M->n_in, n, W, b, M->hidden, M->h[0]);
+}
+
+void launch_out_backward(crp_mlp* M, int64_t n, __nv_bfloat16* dzT, cudaStream_t s) {
+  const int L = M->n_hidden, H = M->hidden;
+  const float* W = M->params + M->w_off[L];
+  if (fast_shape(M))
+    k_out_backward_tile<<<(unsigned)((n + 31) / 32), 256, 0, s>>>(M->dy, n, H, W, M->h[L - 1],
+                                                                   M->dz, dzT);
+  else
+    k_out_backward_data<<<nblk(n * H, 256), 256, 0, s>>>(M->dy, n, H, W, M->h[L - 1], M->dz);
+}
+
+// db += column sums of dz (a hidden layer's bias gradient)
+void launch_colsum(crp_mlp* M, const __nv_bfloat16* dz, int64_t n, float* db, cudaStream_t s) {
+  const int H = M->hidden;
+  if (fast_shape(M))
+    k_col_moments<0, false><<<red_blocks(M), 256, 0, s>>>(dz, n, H, nullptr, nullptr, 0, 0, db);
+  else
+    k_colsum<<<dim3(256, (H + 255) / 256), 256, 0, s>>>(dz, n, H, db);
+}
+
+// output layer: dW_out[o][c] = sum_r dy[r][o] h[r][c], db_out[o] = sum_r dy[r][o]
+void launch_grad_out(crp_mlp* M, int64_t n, cudaStream_t s) {
+  const int L = M->n_hidden, H = M->hidden;
+  float* gW = M->grad + M->w_off[L];
+  float* gb = M->grad + M->b_off[L];
+  if (fast_shape(M))
+    k_col_moments<3, true><<<red_blocks(M), 256, 0, s>>>(M->h[L - 1], n, H, M->dy, gW, 1, H, gb);
+  else
+    k_thin_grad<float, __nv_bfloat16><<<dim3(64, 3, H + 1), 256, 0, s>>>(M->dy, 3, M->h[L - 1], H,
+                                                                        n, gW, gb);
+}
+
+// input layer: dW1[c][i] = sum_r dz[r][c] x[r][i], db1[c] = sum_r dz[r][c]
+void launch_grad_in(crp_mlp* M, const __nv_bfloat16* dz, const float* x, int64_t n,
+                    cudaStream_t s) {
+  const int H = M->hidden, ni = M->n_in;
+  float* gW = M->grad + M->w_off[0];
+  float* gb = M->grad + M->b_off[0];
+  if (!fast_shape(M)) {
+    k_thin_grad<__nv_bfloat16, float><<<dim3(64, H, ni + 1), 256, 0, s>>>(dz, H, x, ni, n, gW, gb);
+    return;
+  }
+  const unsigned g = red_blocks(M);
+  switch (ni) {
+#define CRP_GRAD_IN(NI)                                                                  \
+  case NI:                                                                               \
+    k_col_moments<NI, false><<<g, 256, 0, s>>>(dz, n, H, x, gW, ni, 1, gb);              \
+    break;
+    CRP_GRAD_IN(1)
+    CRP_GRAD_IN(2)
+    CRP_GRAD_IN(3)
+    CRP_GRAD_IN(4)
+    CRP_GRAD_IN(5)
+    CRP_GRAD_IN(6)
+    CRP_GRAD_IN(7)
+    CRP_GRAD_IN(8)
+#undef CRP_GRAD_IN
+    default:
+      break;
+  }
+}
+
 template <int EPI>
 void gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* Bt, int ldb, int64_t M, int N, int K,
           int splits, const float* bias, const __nv_bfloat16* mask, __nv_bfloat16* out_bf,
@@ -395,15 +721,37 @@ void gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* Bt, int ldb, int
 }
 
 // Forward over n samples (n a multiple of 128): activations in M->h, the
-// normalised output in y_hat; with targets, the loss and dy as well.
+// normalised output in y_hat; with targets, the loss and dy as well.  tc: the
+// hidden GEMMs on the tensor cores (tcgen05), also writing the transposed
+// activations the weight gradients need; else the layered mma.sync GEMMs.
 crp_status forward(crp_mlp* M, const float* x, int64_t n, const float* t, float* y_hat,
-                   cudaStream_t s) {
+                   cudaStream_t s, bool tc = false) {
   const int H = M->hidden;
-  k_layer_in<<<nblk(n * H, 256), 256, 0, s>>>(x, M->n_in, n, M->params + M->w_off[0],
-                                              M->params + M->b_off[0], H, M->h[0]);
-  for (int l = 1; l < M->n_hidden; ++l)
-    gemm<EPI_BIAS_RELU>(M->h[l - 1], H, M->wb[l], H, n, H, H, 1, M->params + M->b_off[l], nullptr,
-                        M->h[l], nullptr, H, s);
+  launch_layer_in(M, x, n, tc ? M->hT[0] : nullptr, s);
+  for (int l = 1; l < M->n_hidden; ++l) {
+    if (tc) {
+      GemmTcParams g;
+      memset(&g, 0, sizeof(g));
+      g.A = M->h[l - 1];
+      g.lda = H;
+      g.B = M->wb[l];
+      g.ldb = H;
+      g.M = n;
+      g.K = H;
+      g.splits = 1;
+      g.bias = M->params + M->b_off[l];
+      g.out = M->h[l];
+      g.ldo = H;
+      g.out_t = l + 1 < M->n_hidden ? M->hT[l] : nullptr;  // feeds the next layer's dW
+      g.ldot = n;
+      g.err = M->tc_err;
+      const cudaError_t e = gemm_tc(GEMM_TC_BIAS_RELU, g, M->device, M->sm_count, s);
+      if (e != cudaSuccess) return fail_cuda(e, "mlp: tensor-core forward GEMM");
+    } else {
+      gemm<EPI_BIAS_RELU>(M->h[l - 1], H, M->wb[l], H, n, H, H, 1, M->params + M->b_off[l],
+                          nullptr, M->h[l], nullptr, H, s);
+    }
+  }
   const int lo = M->n_hidden;
   if (t) cudaMemsetAsync(M->loss, 0, sizeof(float), s);
   k_layer_out<<<nblk(n * 32, 256), 256, 0, s>>>(M->h[lo - 1], n, H, M->params + M->w_off[lo],
@@ -413,35 +761,76 @@ crp_status forward(crp_mlp* M, const float* x, int64_t n, const float* t, float*
   return e == cudaSuccess ? CRP_OK : fail_cuda(e, "mlp: forward");
 }
 
-crp_status backward(crp_mlp* M, const float* x, int64_t n, cudaStream_t s) {
+// Backward over the batch of the last forward: gradients (FP32, summed over
+// the batch) of every parameter into M->grad.  tc: weight gradients and
+// backward-data products on the tensor cores, reading the transposed signals
+// the epilogues wrote; else transposes plus the layered mma.sync GEMMs.
+crp_status backward(crp_mlp* M, const float* x, int64_t n, cudaStream_t s, bool tc = false) {
   const int H = M->hidden, L = M->n_hidden;
   cudaMemsetAsync(M->grad, 0, sizeof(float) * M->n_params, s);
   // output layer
-  k_thin_grad<float, __nv_bfloat16><<<dim3(64, 3, H + 1), 256, 0, s>>>(
-      M->dy, 3, M->h[L - 1], H, n, M->grad + M->w_off[L], M->grad + M->b_off[L]);
-  k_out_backward_data<<<nblk(n * H, 256), 256, 0, s>>>(M->dy, n, H, M->params + M->w_off[L],
-                                                       M->h[L - 1], M->dz);
+  launch_grad_out(M, n, s);
+  launch_out_backward(M, n, tc ? M->dzT : nullptr, s);
   __nv_bfloat16* dz = M->dz;
   __nv_bfloat16* dz_next = M->dz2;
+  __nv_bfloat16* dzT = M->dzT;
+  __nv_bfloat16* dzT_next = M->dzT2;
   const int splits = n >= 128 * 64 ? 32 : (int)(n / 128 < 1 ? 1 : n / 128);
   for (int l = L - 1; l >= 1; --l) {
     // W_l maps h[l-1] -> h[l]; dz holds dL/dz_l (bf16, [n][H])
-    const dim3 tb(32, 8);
-    k_transpose<<<dim3((unsigned)(n / 32), H / 32), tb, 0, s>>>(dz, n, H, M->dzt);
-    k_transpose<<<dim3((unsigned)(n / 32), H / 32), tb, 0, s>>>(M->h[l - 1], n, H, M->ht);
-    int sp = splits;
-    while (sp > 1 && (n / sp) % BK != 0) --sp;
-    gemm<EPI_ATOMIC>(M->dzt, (int)n, M->ht, (int)n, H, H, (int)n, sp, nullptr, nullptr, nullptr,
-                     M->grad + M->w_off[l], H, s);
-    k_colsum<<<dim3(256, (H + 255) / 256), 256, 0, s>>>(dz, n, H, M->grad + M->b_off[l]);
-    gemm<EPI_MASK>(dz, H, M->wbt[l], H, n, H, H, 1, nullptr, M->h[l - 1], dz_next, nullptr, H, s);
-    __nv_bfloat16* tmp = dz;
-    dz = dz_next;
-    dz_next = tmp;
+    if (tc) {
+      GemmTcParams g;
+      memset(&g, 0, sizeof(g));
+      g.err = M->tc_err;
+      // dW_l += dz_l^T h_{l-1}: A = dz_l^T [H][n], B = h_{l-1}^T [H][n], K = n split
+      g.A = dzT;
+      g.lda = n;
+      g.B = M->hT[l - 1];
+      g.ldb = n;
+      g.M = H;
+      g.K = n;
+      const int64_t sp = n / 256 < 1 ? 1 : n / 256;
+      const int64_t sp_max = M->sm_count / 2 > 1 ? M->sm_count / 2 : 1;
+      g.splits = (int)(sp < sp_max ? sp : sp_max);
+      g.out_f = M->grad + M->w_off[l];
+      g.ldf = H;
+      cudaError_t e = gemm_tc(GEMM_TC_ATOMIC, g, M->device, M->sm_count, s);
+      if (e != cudaSuccess) return fail_cuda(e, "mlp: tensor-core weight-gradient GEMM");
+      launch_colsum(M, dz, n, M->grad + M->b_off[l], s);
+      // dz_{l-1} = (dz_l W_l) masked by ReLU'(h_{l-1}): B = W_l^T [H][H]
+      memset(&g, 0, sizeof(g));
+      g.err = M->tc_err;
+      g.A = dz;
+      g.lda = H;
+      g.B = M->wbt[l];
+      g.ldb = H;
+      g.M = n;
+      g.K = H;
+      g.splits = 1;
+      g.mask = M->h[l - 1];
+      g.ldm = H;
+      g.out = dz_next;
+      g.ldo = H;
+      g.out_t = l > 1 ? dzT_next : nullptr;
+      g.ldot = n;
+      e = gemm_tc(GEMM_TC_MASK, g, M->device, M->sm_count, s);
+      if (e != cudaSuccess) return fail_cuda(e, "mlp: tensor-core backward-data GEMM");
+    } else {
+      const dim3 tb(32, 8);
+      k_transpose<<<dim3((unsigned)(n / 32), H / 32), tb, 0, s>>>(dz, n, H, M->dzt);
+      k_transpose<<<dim3((unsigned)(n / 32), H / 32), tb, 0, s>>>(M->h[l - 1], n, H, M->ht);
+      int sp = splits;
+      while (sp > 1 && (n / sp) % BK != 0) --sp;
+      gemm<EPI_ATOMIC>(M->dzt, (int)n, M->ht, (int)n, H, H, (int)n, sp, nullptr, nullptr, nullptr,
+                       M->grad + M->w_off[l], H, s);
+      launch_colsum(M, dz, n, M->grad + M->b_off[l], s);
+      gemm<EPI_MASK>(dz, H, M->wbt[l], H, n, H, H, 1, nullptr, M->h[l - 1], dz_next, nullptr, H, s);
+    }
+    std::swap(dz, dz_next);
+    std::swap(dzT, dzT_next);
   }
   // input layer: dz holds dL/dz_1
-  k_thin_grad<__nv_bfloat16, float><<<dim3(64, H, M->n_in + 1), 256, 0, s>>>(
-      dz, H, x, M->n_in, n, M->grad + M->w_off[0], M->grad + M->b_off[0]);
+  launch_grad_in(M, dz, x, n, s);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? CRP_OK : fail_cuda(e, "mlp: backward");
 }
@@ -472,6 +861,8 @@ crp_status crp_mlp_create(crp_context* ctx, int32_t n_in, int32_t hidden, int32_
   M->cap = 0;
   M->dz = M->dz2 = M->dzt = M->ht = nullptr;
   M->y = M->dy = M->loss = nullptr;
+  M->tcap = 0;
+  M->dzT = M->dzT2 = nullptr;
   M->tc_err = nullptr;
   M->forward_path = CRP_MLP_PATH_AUTO;
   M->sm_count = 0;
@@ -557,6 +948,7 @@ crp_status crp_mlp_destroy(crp_mlp* M) {
   if (!M) return CRP_OK;
   cudaDeviceSynchronize();
   free_ws(M);
+  free_tws(M);
   dev_free(M->params);
   dev_free(M->grad);
   dev_free(M->m);
@@ -673,9 +1065,13 @@ crp_status crp_mlp_train_step(crp_mlp* M, const float* x, const float* t, int64_
     return CRP_E_INVALID;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the tensor-core GEMMs whenever the fused forward is available and the
+  // layered path is not forced
+  const bool tc = !M->wimg.empty() && M->forward_path != CRP_MLP_PATH_LAYERED;
   crp_status st = ensure_ws(M, n);
-  if (st == CRP_OK) st = forward(M, x, n, t, nullptr, s);
-  if (st == CRP_OK) st = backward(M, x, n, s);
+  if (st == CRP_OK && tc) st = ensure_tws(M, n);
+  if (st == CRP_OK) st = forward(M, x, n, t, nullptr, s, tc);
+  if (st == CRP_OK) st = backward(M, x, n, s, tc);
   if (st == CRP_OK && lr > 0.f) {
     M->step += 1;
     const float b1 = 0.9f, b2 = 0.999f;
@@ -686,9 +1082,17 @@ crp_status crp_mlp_train_step(crp_mlp* M, const float* x, const float* t, int64_
   }
   if (st == CRP_OK && loss_out) {
     float l = 0.f;
+    unsigned err = 0;
     cudaError_t e = cudaMemcpyAsync(&l, M->loss, sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && tc)
+      e = cudaMemcpyAsync(&err, M->tc_err, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail_cuda(e, "crp_mlp_train_step");
+    if (err) {
+      cudaMemsetAsync(M->tc_err, 0, sizeof(unsigned), s);
+      set_error("crp_mlp_train_step: a tensor-core completion wait timed out");
+      return CRP_E_CUDA;
+    }
     *loss_out = l / (float)n;
   }
   return st;

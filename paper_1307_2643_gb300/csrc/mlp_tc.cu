@@ -24,6 +24,12 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include <cuda.h>
+
 #include "crp_internal.cuh"
 #include "mlp_tc.h"
 
@@ -314,7 +320,322 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const MlpTcParam
                  : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// Training GEMM: C[M][256] = A[M][K] B[256][K]^T on the tensor cores.
+// One CTA (256 threads) per SM, persistent over work items (a 128-row tile of
+// C and a range of K).  Per 256-wide K chunk one thread starts TMA copies of
+// the A rows (128 x kc) and the B rows (256 x kc) in 64-column boxes into the
+// 128-byte-swizzled K-major layout (rows of 128 bytes, 16-byte chunks XOR-ed
+// with the row index within each 1024-byte group of 8 rows), the CTA waits
+// for their bytes on an mbarrier, and the thread issues kc / 16 MMAs (M 128,
+// N 256, K 16) into 256 TMEM columns; after the last chunk every thread reads
+// its row's 128 accumulator columns back for the epilogue.  B stays resident
+// when there is one K chunk in all (the weights of a layer); the next item's
+// first chunk is copied while the epilogue runs.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kAtomA = kRows * 128;  // 64 columns of 128 rows: 16 KB
+constexpr uint32_t kAtomB = kH * 128;     // 64 columns of 256 rows: 32 KB
+constexpr size_t kGemmSmem = 1024 + 4 * kAtomA + 4 * kAtomB + 64;
+
+// Descriptor of a 128-byte-swizzled K-major operand: start address, leading
+// byte offset 16 (unused within a swizzle atom), 1024 bytes between groups
+// of 8 rows, version 1, swizzle mode 2 (128 B) in bits 61-63.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         (1ull << 46) | (2ull << 61);
+}
+
+__device__ __forceinline__ void bar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// One 2D TMA box (64 columns x the map's box rows) at column x, row y.
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"l"(p), "f"(a), "f"(b),
+               "f"(c), "f"(d)
+               : "memory");
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_gemm_tc(const GemmTcParams P, const __grid_constant__ CUtensorMap mapA,
+              const __grid_constant__ CUtensorMap mapB) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  unsigned char* base = tc_smem + ((1024u - (smem_u32(tc_smem) & 1023u)) & 1023u);
+  unsigned char* As = base;               // 4 boxes of 16 KB
+  unsigned char* Bs = base + 4 * kAtomA;  // 4 boxes of 32 KB
+  uint64_t* bar = reinterpret_cast<uint64_t*>(Bs + 4 * kAtomB);  // MMA completion
+  uint64_t* tbar = bar + 1;                                       // TMA bytes landed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int r = tid & (kRows - 1), g = tid >> 7;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(tbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t tmem_warp = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+
+  const int64_t m_tiles = P.M / kRows;
+  const int64_t items = m_tiles * P.splits;
+  const int64_t ks = ((P.K + P.splits - 1) / P.splits + 63) / 64 * 64;  // K per split
+  const bool b_resident = P.splits == 1 && P.K <= kH;
+  auto range = [&](int64_t item, int64_t& kb, int64_t& ke) {
+    kb = (item / m_tiles) * ks;
+    ke = kb + ks < P.K ? kb + ks : P.K;
+  };
+  // one thread starts the TMA boxes of a chunk (kc a multiple of 64)
+  auto issue = [&](int64_t item, int64_t c0, int kc, bool with_b) {
+    if (tid != 0) return;
+    const int boxes = kc / 64;
+    bar_expect_tx(tbar, (uint32_t)boxes * (kAtomA + (with_b ? kAtomB : 0u)));
+    const int y = (int)((item % m_tiles) * kRows);
+    for (int a = 0; a < boxes; ++a) tma_load_2d(As + a * kAtomA, &mapA, (int)c0 + 64 * a, y, tbar);
+    if (with_b)
+      for (int a = 0; a < boxes; ++a) tma_load_2d(Bs + a * kAtomB, &mapB, (int)c0 + 64 * a, 0, tbar);
+  };
+  uint32_t parity = 0, tparity = 0;
+  bool failed = false, b_loaded = false, prefetched = false;
+
+  for (int64_t item = blockIdx.x; item < items && !failed; item += gridDim.x) {
+    int64_t kb, ke;
+    range(item, kb, ke);
+    if (kb >= ke) continue;  // an empty split (the same for every thread)
+    const int64_t mt = item % m_tiles;
+    for (int64_t c0 = kb; c0 < ke; c0 += kH) {
+      const int kc = (int)(ke - c0 < kH ? ke - c0 : kH);
+      if (!prefetched) issue(item, c0, kc, !(b_resident && b_loaded));
+      prefetched = false;
+      b_loaded = true;
+      bool landed = bar_wait(tbar, tparity);  // the chunk's bytes are in shared memory
+      if (!landed) landed = bar_wait(tbar, tparity);
+      tparity ^= 1u;
+      if (__syncthreads_or(!landed)) {
+        if (tid == 0) atomicOr(P.err, 1u);
+        failed = true;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      if (tid == 0) {
+        const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+#pragma unroll 1
+        for (int k = 0; k < kc / 16; ++k) {
+          // K step k: box k / 4, 32 (k % 4) bytes into each 128-byte row
+          const uint32_t off_a = (uint32_t)(k >> 2) * kAtomA + 32u * (uint32_t)(k & 3);
+          const uint32_t off_b = (uint32_t)(k >> 2) * kAtomB + 32u * (uint32_t)(k & 3);
+          mma_bf16(tmem, sdesc_sw128(a0 + off_a), sdesc_sw128(b0 + off_b), kIdesc,
+                   (c0 > kb || k > 0) ? 1u : 0u);
+        }
+        mma_commit(bar);
+      }
+      bool ok = bar_wait(bar, parity);
+      if (!ok) ok = bar_wait(bar, parity);
+      parity ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicOr(P.err, 1u);
+        failed = true;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    }
+    if (failed) break;
+    // the operand tiles are free: copy the next item's first chunk now
+    const int64_t next = item + gridDim.x;
+    if (next < items) {
+      int64_t nb, ne;
+      range(next, nb, ne);
+      if (nb < ne) {
+        issue(next, nb, (int)(ne - nb < kH ? ne - nb : kH), !b_resident);
+        prefetched = true;
+      }
+    }
+    // ---- epilogue: row r of the tile, columns [128 g, 128 g + 128) ----
+    const int64_t row = mt * kRows + r;
+#pragma unroll 1
+    for (int cc = 4 * g; cc < 4 * g + 4; ++cc) {
+      uint32_t v[32];
+      tmem_ld32(tmem_warp + (uint32_t)(cc * 32), v);
+      const int col0 = cc * 32;
+      if constexpr (EPI == GEMM_TC_ATOMIC) {
+        float* dst = P.out_f + row * P.ldf + col0;
+#pragma unroll
+        for (int j = 0; j < 32; j += 4)
+          red_add_v4(dst + j, __uint_as_float(v[j]), __uint_as_float(v[j + 1]),
+                     __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
+      } else {
+        float f[32];
+        if constexpr (EPI == GEMM_TC_BIAS_RELU) {
+#pragma unroll
+          for (int j = 0; j < 32; j += 4) {
+            const float4 b4 = __ldg(reinterpret_cast<const float4*>(P.bias + col0 + j));
+            f[j] = fmaxf(__uint_as_float(v[j]) + b4.x, 0.f);
+            f[j + 1] = fmaxf(__uint_as_float(v[j + 1]) + b4.y, 0.f);
+            f[j + 2] = fmaxf(__uint_as_float(v[j + 2]) + b4.z, 0.f);
+            f[j + 3] = fmaxf(__uint_as_float(v[j + 3]) + b4.w, 0.f);
+          }
+        } else {
+          const uint4* mrow = reinterpret_cast<const uint4*>(P.mask + row * P.ldm + col0);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const uint4 mq = __ldg(mrow + q);
+            const uint32_t mw[4] = {mq.x, mq.y, mq.z, mq.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const __nv_bfloat162 m2 = *reinterpret_cast<const __nv_bfloat162*>(&mw[e]);
+              const int j = 8 * q + 2 * e;
+              f[j] = __low2float(m2) > 0.f ? __uint_as_float(v[j]) : 0.f;
+              f[j + 1] = __high2float(m2) > 0.f ? __uint_as_float(v[j + 1]) : 0.f;
+            }
+          }
+        }
+        uint32_t w[16];
+#pragma unroll
+        for (int j = 0; j < 32; j += 2) w[j / 2] = pack_bf16(f[j], f[j + 1]);
+        uint4* orow = reinterpret_cast<uint4*>(P.out + row * P.ldo + col0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) orow[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+        if (P.out_t) {
+          const __nv_bfloat16* wb = reinterpret_cast<const __nv_bfloat16*>(w);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) P.out_t[(int64_t)(col0 + j) * P.ldot + row] = wb[j];
+        }
+      }
+    }
+    // every TMEM read is done before the next item's MMAs overwrite it
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(kTmemCols)
+                 : "memory");
+}
+
 }  // namespace
+
+namespace {
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<EncodeTiledFn>(f);
+  }();
+  return fn;
+}
+
+// Tensor map of a row-major bf16 matrix (rows x cols, leading dimension ld
+// elements) read in boxes of 64 columns x box_rows rows, 128-byte swizzle.
+// Maps are cached by (address, shape, box): the training step reuses a few
+// fixed buffers.
+bool tensor_map(const __nv_bfloat16* base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+                CUtensorMap* out) {
+  struct Entry {
+    const void* base;
+    int64_t rows, cols, ld;
+    int box_rows;
+    CUtensorMap map;
+  };
+  static std::mutex mu;
+  static std::vector<Entry> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  for (const Entry& e : cache)
+    if (e.base == base && e.rows == rows && e.cols == cols && e.ld == ld && e.box_rows == box_rows) {
+      *out = e.map;
+      return true;
+    }
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  Entry e{base, rows, cols, ld, box_rows, {}};
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(__nv_bfloat16)};
+  const cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1u, 1u};
+  if (fn(&e.map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims,
+         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  if (cache.size() >= 64) cache.erase(cache.begin());
+  cache.push_back(e);
+  *out = e.map;
+  return true;
+}
+
+}  // namespace
+
+cudaError_t gemm_tc(int epi, const GemmTcParams& p, int device, int sm_count, cudaStream_t s) {
+  // TMA: 16-byte aligned bases, row pitches a multiple of 16 bytes; boxes of
+  // 64 columns, so K is a multiple of 64 (every box starts on a 128-byte
+  // boundary of its row)
+  const bool aligned = ((uintptr_t)p.A % 16 == 0) && ((uintptr_t)p.B % 16 == 0) &&
+                       p.lda % 8 == 0 && p.ldb % 8 == 0 && p.lda >= p.K && p.ldb >= p.K;
+  bool ok = aligned && p.M > 0 && p.M % kRows == 0 && p.K > 0 && p.K % 64 == 0 && p.splits >= 1 &&
+            p.err;
+  if (epi == GEMM_TC_ATOMIC)
+    ok = ok && p.out_f && (uintptr_t)p.out_f % 16 == 0 && p.ldf % 4 == 0;
+  else
+    ok = ok && p.out && (uintptr_t)p.out % 16 == 0 && p.ldo % 8 == 0 &&
+         (epi == GEMM_TC_BIAS_RELU ? (p.bias && (uintptr_t)p.bias % 16 == 0)
+                                   : (p.mask && (uintptr_t)p.mask % 16 == 0 && p.ldm % 8 == 0));
+  if (!ok || epi < GEMM_TC_BIAS_RELU || epi > GEMM_TC_ATOMIC) return cudaErrorInvalidValue;
+  CUtensorMap mapA, mapB;
+  if (!tensor_map(p.A, p.M, p.K, p.lda, kRows, &mapA) || !tensor_map(p.B, kH, p.K, p.ldb, kH, &mapB))
+    return cudaErrorInvalidValue;
+  auto k = epi == GEMM_TC_BIAS_RELU ? k_gemm_tc<GEMM_TC_BIAS_RELU>
+           : epi == GEMM_TC_MASK    ? k_gemm_tc<GEMM_TC_MASK>
+                                    : k_gemm_tc<GEMM_TC_ATOMIC>;
+  // the shared-memory opt-in is a per-device attribute of each kernel: set once
+  static std::atomic<uint64_t> set_mask[3];
+  const uint64_t bit = device >= 0 && device < 64 ? (1ull << device) : 0ull;
+  if (!bit || !(set_mask[epi].load() & bit)) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
+    if (e != cudaSuccess) return e;
+    set_mask[epi].fetch_or(bit);
+  }
+  const int64_t items = p.M / kRows * p.splits;
+  const int64_t grid = items < sm_count ? items : sm_count;
+  k<<<(unsigned)grid, kThreads, kGemmSmem, s>>>(p, mapA, mapB);
+  return cudaGetLastError();
+}
 
 size_t mlp_tc_weight_image_elems() { return (size_t)kH * kH; }
 

@@ -1,4 +1,5 @@
-// mlp_tc.h -- fused tensor-core (tcgen05) forward pass of the MLP surrogate.
+// mlp_tc.h -- tensor-core (tcgen05) kernels of the MLP surrogate: the fused
+// forward pass and the GEMMs of the training step.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -25,6 +26,35 @@ struct MlpTcParams {
   float* y;       // [n][3], unit vectors
   unsigned* err;  // set to 1 when a tensor-core wait timed out
 };
+
+// Tensor-core GEMM of the training step (tcgen05, FP32 accumulation in TMEM):
+// C[M][256] = A[M][K] B[256][K]^T with bf16 operands stored row-major (K
+// contiguous).  Work items are 128-row tiles of C times `splits` ranges of K;
+// each item's K range runs through 256-wide chunks.  Epilogues:
+//   GEMM_TC_BIAS_RELU  out = bf16(max(C + bias, 0))
+//   GEMM_TC_MASK       out = bf16(C where mask > 0, else 0)
+//   GEMM_TC_ATOMIC     out_f += C (vector reductions; split-K partial sums)
+// The first two also write out_t = out^T ([256][ldot]) when out_t is given.
+enum GemmTcEpi { GEMM_TC_BIAS_RELU = 0, GEMM_TC_MASK = 1, GEMM_TC_ATOMIC = 2 };
+struct GemmTcParams {
+  const __nv_bfloat16* A;
+  int64_t lda;
+  const __nv_bfloat16* B;
+  int64_t ldb;
+  int64_t M, K;  // M a multiple of 128, K a multiple of 16
+  int splits;
+  const float* bias;
+  const __nv_bfloat16* mask;
+  int64_t ldm;
+  __nv_bfloat16* out;
+  int64_t ldo;
+  __nv_bfloat16* out_t;
+  int64_t ldot;
+  float* out_f;
+  int64_t ldf;
+  unsigned* err;  // set to 1 when a tensor-core wait timed out
+};
+cudaError_t gemm_tc(int epi, const GemmTcParams& p, int device, int sm_count, cudaStream_t s);
 
 // Element count of one hidden layer's weight image (256 x 256).
 size_t mlp_tc_weight_image_elems();

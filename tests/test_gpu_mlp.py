@@ -199,3 +199,88 @@ def test_fused_tensor_core_forward_matches_layered(torch_dev, n):
     ref, _ = M.forward(_oracle_view(p), SHAPES, x.astype(np.float64))
     a = M.angle_deg(fused, ref)
     assert np.median(a) < 0.3 and np.max(a) < 3.0, (np.median(a), np.max(a))
+
+
+@pytest.mark.parametrize("n", [2048, 128 * 37, 16384])
+def test_tensor_core_training_gradients(torch_dev, n):
+    """The training step on the tcgen05 GEMMs (TMA operand boxes, weight
+    gradients split over K with vector reductions, transposed signals written
+    by the epilogues) against the layered mma.sync step and the binary64
+    oracle.  n = 128 * 37 gives K ranges of 320: two chunks per split, the
+    second 64 wide."""
+    torch = torch_dev
+    p = _params(31)
+    x, t = _batch(n, 32)
+    ctx = crp.crp_context_create(0, 1, 16)
+    grads, losses = {}, {}
+    try:
+        mlp = crp.crp_mlp_create(ctx, 4, 256, 4, 7)
+        xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+        for path in (crp.MLP_PATH_AUTO, crp.MLP_PATH_LAYERED):
+            crp.crp_mlp_set_forward_path(mlp, path)
+            crp.crp_mlp_set_params(mlp, p)
+            losses[path] = crp.crp_mlp_train_step(mlp, xd, td, n, 0.0)
+            grads[path] = crp.crp_mlp_get_params(mlp)[1].astype(np.float64)
+        crp.crp_mlp_destroy(mlp)
+    finally:
+        crp.crp_context_destroy(ctx)
+    flat = _oracle_view(p)
+    y, cache = M.forward(flat, SHAPES, x.astype(np.float64))
+    ref = M.backward(flat, SHAPES, cache, t.astype(np.float64))
+    lref = M.loss(y, t.astype(np.float64))
+    Wr, br = M.unpack(ref, SHAPES)
+    Wt, bt = M.unpack(grads[crp.MLP_PATH_AUTO], SHAPES)
+    Wl, bl = M.unpack(grads[crp.MLP_PATH_LAYERED], SHAPES)
+    for path in losses:
+        assert abs(losses[path] - lref) < 2e-3 * max(1.0, lref), (path, losses[path], lref)
+    for l in range(len(SHAPES)):
+        for tc, lay, want in ((Wt[l], Wl[l], Wr[l]), (bt[l], bl[l], br[l])):
+            nw = np.linalg.norm(want)
+            assert np.linalg.norm(tc - want) / nw < 2e-2, (l, "tc vs oracle")
+            assert np.linalg.norm(lay - want) / nw < 2e-2, (l, "layered vs oracle")
+            assert np.linalg.norm(tc - lay) / nw < 1e-2, (l, "tc vs layered")
+
+
+@pytest.mark.parametrize("n_in,hidden,n_hidden", [(4, 512, 3), (12, 384, 3)])
+def test_other_shapes_gradients_match_oracle(torch_dev, n_in, hidden, n_hidden):
+    """Shapes off the tensor-core path: hidden 512 with 4 inputs takes the
+    tiled thin-layer kernels over two 256-column groups, hidden 384 with 12
+    inputs the generic ones; both with the layered GEMMs."""
+    torch = torch_dev
+    shapes = M.layer_shapes(n_in, hidden, n_hidden, 3)
+    g = np.random.default_rng(41)
+    parts = []
+    for l, (o, i) in enumerate(shapes):
+        scale = np.sqrt((1.0 if l == len(shapes) - 1 else 2.0) / i)
+        parts += [g.normal(scale=scale, size=o * i), g.normal(scale=0.05, size=o)]
+    p = np.concatenate(parts).astype(np.float32)
+    n = 128 * 23
+    # the smooth target of _batch (a coherent gradient: with targets unrelated
+    # to the inputs the batch sum nearly cancels and bf16 rounding of the
+    # backward signals dominates the difference); extra inputs are noise
+    x, t = _batch(n, 42)
+    if n_in > 4:
+        x = np.concatenate([x, 0.5 * g.normal(size=(n, n_in - 4))], axis=1).astype(np.float32)
+    ctx = crp.crp_context_create(0, 1, 16)
+    try:
+        mlp = crp.crp_mlp_create(ctx, n_in, hidden, n_hidden, 7)
+        crp.crp_mlp_set_params(mlp, p)
+        xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+        loss = crp.crp_mlp_train_step(mlp, xd, td, n, 0.0)
+        grad = crp.crp_mlp_get_params(mlp)[1].astype(np.float64)
+        crp.crp_mlp_destroy(mlp)
+    finally:
+        crp.crp_context_destroy(ctx)
+    flat = p.astype(np.float64)
+    Ws, bs = M.unpack(flat.copy(), shapes)
+    for l in range(1, len(shapes) - 1):
+        Ws[l] = M.bf16_round(Ws[l])
+    flat = M.pack(Ws, bs)
+    y, cache = M.forward(flat, shapes, x.astype(np.float64))
+    assert abs(loss - M.loss(y, t.astype(np.float64))) < 2e-3 * max(1.0, loss)
+    ref = M.backward(flat, shapes, cache, t.astype(np.float64))
+    Wg, bg = M.unpack(grad, shapes)
+    Wr, br = M.unpack(ref, shapes)
+    for l in range(len(shapes)):
+        for got, want in ((Wg[l], Wr[l]), (bg[l], br[l])):
+            assert np.linalg.norm(got - want) / np.linalg.norm(want) < 2e-2, l
