@@ -445,13 +445,24 @@ crp_status crp_mlp_forward(crp_mlp* mlp, const float* x, float* y_hat, int64_t n
 #define CRP_MLP_PATH_AUTO 0                /* fused tensor-core kernel when supported */
 #define CRP_MLP_PATH_TENSOR_CORE_FUSED 1   /* require it (CRP_E_INVALID if unsupported) */
 #define CRP_MLP_PATH_LAYERED 2             /* one GEMM launch per hidden layer */
-/* Forward kernel selection of crp_mlp_forward (training always runs layered). */
+/* Kernel selection of crp_mlp_forward and crp_mlp_train_step.  With hidden =
+ * 256 and n_in <= 8, AUTO / TENSOR_CORE_FUSED train on the fifth-generation
+ * tensor cores (tcgen05 GEMMs fed by TMA, FP32 accumulation in TMEM); LAYERED
+ * (and every other shape) trains with warp-level mma.sync GEMMs. */
 crp_status crp_mlp_set_forward_path(crp_mlp* mlp, int32_t path);
 /* one Adam step on a batch (device x [n][n_in], t [n][3] unit targets; n a
  * multiple of 128); lr = 0 computes the gradient only; loss_out (host, may
- * be NULL) receives the batch loss and synchronises the stream */
+ * be NULL) receives the batch loss and synchronises the stream (and reports
+ * CRP_E_CUDA if a tensor-core wait of this or an earlier step timed out).
+ * On the tensor-core path an Adam step is replayed from a CUDA graph after
+ * its first call for a batch size (x and t are copied into staging buffers
+ * the graph reads); the workspace and staging buffers are shared by the
+ * MLP's calls, so steps on different streams must be ordered by the caller. */
 crp_status crp_mlp_train_step(crp_mlp* mlp, const float* x, const float* t, int64_t n, float lr,
                               float* loss_out, void* stream);
+/* enable != 0 (the default): graph replay of the training step as above;
+ * 0: every step launched kernel by kernel (the same arithmetic). */
+crp_status crp_mlp_set_train_graph(crp_mlp* mlp, int32_t enable);
 
 /* A lens whose border directions come from the surrogate network instead
  * of back-tracking: sample k's network input is (dirs[k], log10(E[k]/eV) - 19)

@@ -167,6 +167,7 @@ SYMBOLS = (
     "crp_histogram_healpix",
     "crp_mlp_create", "crp_mlp_destroy", "crp_mlp_num_params", "crp_mlp_set_params",
     "crp_mlp_get_params", "crp_mlp_forward", "crp_mlp_train_step", "crp_lens_build_surrogate",
+    "crp_mlp_set_train_graph",
     "crp_checkpoint", "crp_restore", "crp_measure_peaks", "crp_autotune", "crp_grid_sample",
     "crp_mlp_set_forward_path", "crp_propagate_1d", "crp_cosmology_correct",
     "crp_redshift_of_distance",
@@ -228,6 +229,7 @@ def lib():
             L.crp_measure_peaks.argtypes = [i32, C.POINTER(Peaks)]
             L.crp_grid_sample.argtypes = [p, C.POINTER(Modules), C.c_int64, p, p]
             L.crp_mlp_set_forward_path.argtypes = [p, i32]
+            L.crp_mlp_set_train_graph.argtypes = [p, i32]
             L.crp_propagate_1d.argtypes = [p, C.POINTER(Cosmology), C.POINTER(Modules), p,
                                            C.POINTER(Stats)]
             L.crp_cosmology_correct.argtypes = [p, C.POINTER(Cosmology), C.POINTER(Modules),
@@ -495,6 +497,10 @@ MLP_PATH_AUTO, MLP_PATH_TENSOR_CORE_FUSED, MLP_PATH_LAYERED = 0, 1, 2
 
 def crp_mlp_set_forward_path(mlp, path):
     _check(lib().crp_mlp_set_forward_path(mlp, path))
+
+
+def crp_mlp_set_train_graph(mlp, enable=True):
+    _check(lib().crp_mlp_set_train_graph(mlp, 1 if enable else 0))
 
 
 def crp_mlp_train_step(mlp, x_dev, t_dev, n, lr, stream=None, want_loss=True):

@@ -58,6 +58,18 @@ struct crp_mlp {
   int64_t tcap;
   std::vector<__nv_bfloat16*> hT;
   __nv_bfloat16 *dzT, *dzT2;
+  // the tensor-core training step as a CUDA graph, replayed with the Adam
+  // node's arguments updated; each step's x and t are first copied into the
+  // fixed staging buffers xs, ts the graph reads
+  bool use_graph;
+  cudaGraph_t tg_graph;  // the captured graph: its node handles address the exec's nodes
+  cudaGraphExec_t tg_exec;
+  cudaGraphNode_t tg_adam;
+  cudaKernelNodeParams tg_adam_params;
+  int64_t tg_n;
+  cudaStream_t tg_stream;  // private stream the graph is captured on
+  float *xs, *ts;
+  int64_t scap;
 };
 
 namespace {
@@ -405,16 +417,37 @@ __global__ void __launch_bounds__(256) k_layer_in_tile(const float* __restrict__
                                                        __nv_bfloat16* __restrict__ h,
                                                        __nv_bfloat16* __restrict__ hT) {
   __shared__ __align__(16) __nv_bfloat16 T[32][264];
+  __shared__ __align__(16) float sw[9][256];  // this column group's W1 (input-major), then b1
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t r0 = blockIdx.x * 32ll;
   for (int cg = 0; cg < hidden; cg += 256) {
+    // coalesced staging: W1 rows of this group, transposed to input-major
+    __syncthreads();
+    for (int e = threadIdx.x; e < 256 * n_in; e += 256) {
+      const int c = e / n_in, i = e - c * n_in;
+      sw[i][c] = W[(int64_t)(cg + c) * n_in + i];
+    }
+    sw[8][threadIdx.x] = b[cg + threadIdx.x];
+    __syncthreads();
     const int c0 = cg + 8 * lane;
     float w[8][8], bb[8];
+    {
+      const float4 b0 = *reinterpret_cast<const float4*>(&sw[8][8 * lane]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&sw[8][8 * lane + 4]);
+      bb[0] = b0.x, bb[1] = b0.y, bb[2] = b0.z, bb[3] = b0.w;
+      bb[4] = b1.x, bb[5] = b1.y, bb[6] = b1.z, bb[7] = b1.w;
+    }
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      bb[q] = __ldg(b + c0 + q);
+    for (int i = 0; i < 8; ++i) {
+      if (i < n_in) {
+        const float4 w0 = *reinterpret_cast<const float4*>(&sw[i][8 * lane]);
+        const float4 w1 = *reinterpret_cast<const float4*>(&sw[i][8 * lane + 4]);
+        w[0][i] = w0.x, w[1][i] = w0.y, w[2][i] = w0.z, w[3][i] = w0.w;
+        w[4][i] = w1.x, w[5][i] = w1.y, w[6][i] = w1.z, w[7][i] = w1.w;
+      } else {
 #pragma unroll
-      for (int i = 0; i < 8; ++i) w[q][i] = i < n_in ? __ldg(W + (c0 + q) * n_in + i) : 0.f;
+        for (int q = 0; q < 8; ++q) w[q][i] = 0.f;
+      }
     }
     for (int rr = warp; rr < 32; rr += 8) {
       const int64_t r = r0 + rr;
@@ -577,10 +610,40 @@ void free_tws(crp_mlp* M) {
   M->tcap = 0;
 }
 
+void drop_graph(crp_mlp* M) {
+  if (M->tg_exec) cudaGraphExecDestroy(M->tg_exec);
+  if (M->tg_graph) cudaGraphDestroy(M->tg_graph);
+  M->tg_exec = nullptr;
+  M->tg_graph = nullptr;
+  M->tg_adam = nullptr;
+  M->tg_n = 0;
+}
+
+// Staging buffers of the graph-replayed training step.
+crp_status ensure_stage(crp_mlp* M, int64_t n) {
+  if (M->scap >= n) return CRP_OK;
+  drop_graph(M);
+  dev_free(M->xs);
+  dev_free(M->ts);
+  M->xs = static_cast<float*>(dev_alloc(sizeof(float) * (size_t)n * M->n_in));
+  M->ts = static_cast<float*>(dev_alloc(sizeof(float) * (size_t)n * 3));
+  if (!M->xs || !M->ts) {
+    dev_free(M->xs);
+    dev_free(M->ts);
+    M->xs = M->ts = nullptr;
+    M->scap = 0;
+    set_error("mlp: cannot allocate the training staging buffers");
+    return CRP_E_OOM;
+  }
+  M->scap = n;
+  return CRP_OK;
+}
+
 // Transposed activations for the tensor-core training step (allocated only
 // when training on that path).
 crp_status ensure_tws(crp_mlp* M, int64_t n) {
   if (M->tcap >= n) return CRP_OK;
+  drop_graph(M);
   free_tws(M);
   const size_t hb = sizeof(__nv_bfloat16) * (size_t)n * M->hidden;
   for (int l = 0; l + 1 < M->n_hidden; ++l)
@@ -600,6 +663,7 @@ crp_status ensure_tws(crp_mlp* M, int64_t n) {
 
 crp_status ensure_ws(crp_mlp* M, int64_t n) {
   if (M->cap >= n) return CRP_OK;
+  drop_graph(M);
   free_ws(M);
   const size_t hb = sizeof(__nv_bfloat16) * (size_t)n * M->hidden;
   for (int l = 0; l < M->n_hidden; ++l) M->h.push_back(static_cast<__nv_bfloat16*>(dev_alloc(hb)));
@@ -835,6 +899,63 @@ crp_status backward(crp_mlp* M, const float* x, int64_t n, cudaStream_t s, bool 
   return e == cudaSuccess ? CRP_OK : fail_cuda(e, "mlp: backward");
 }
 
+// Record the tensor-core training step of n samples (reading the staging
+// buffers) as a graph on the private stream; nothing runs.  Any failure
+// leaves the step eager (and clears the error state it raised).
+void capture_train_graph(crp_mlp* M, int64_t n) {
+  drop_graph(M);
+  if (!M->tg_stream && cudaStreamCreateWithFlags(&M->tg_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    M->tg_stream = nullptr;
+    cudaGetLastError();
+    return;
+  }
+  cudaStream_t cs = M->tg_stream;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  crp_status st = forward(M, M->xs, n, M->ts, nullptr, cs, true);
+  if (st == CRP_OK) st = backward(M, M->xs, n, cs, true);
+  if (st == CRP_OK) {
+    k_adam<<<nblk(M->n_params, 256), 256, 0, cs>>>(M->params, M->grad, M->m, M->v, M->n_params,
+                                                   0.f, 0.9f, 0.999f, 1e-8f, 1.f, 1.f);
+    st = refresh_bf16(M, cs);
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+  cudaGraphNode_t adam = nullptr;
+  cudaKernelNodeParams ap;
+  memset(&ap, 0, sizeof(ap));
+  if (st == CRP_OK && ec == cudaSuccess && g) {
+    size_t count = 0;
+    cudaGraphGetNodes(g, nullptr, &count);
+    std::vector<cudaGraphNode_t> nodes(count);
+    if (count && cudaGraphGetNodes(g, nodes.data(), &count) == cudaSuccess) {
+      for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType ty;
+        if (cudaGraphNodeGetType(nd, &ty) != cudaSuccess || ty != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams p;
+        if (cudaGraphKernelNodeGetParams(nd, &p) == cudaSuccess &&
+            p.func == reinterpret_cast<void*>(k_adam)) {
+          adam = nd;
+          ap = p;
+        }
+      }
+    }
+    cudaGraphExec_t ex = nullptr;
+    if (adam && cudaGraphInstantiate(&ex, g, 0) == cudaSuccess) {
+      M->tg_graph = g;  // kept: tg_adam is one of its nodes
+      g = nullptr;
+      M->tg_exec = ex;
+      M->tg_adam = adam;
+      M->tg_adam_params = ap;
+      M->tg_n = n;
+    }
+  }
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();  // a failed capture only means eager steps
+}
+
 }  // namespace
 
 extern "C" {
@@ -863,6 +984,15 @@ crp_status crp_mlp_create(crp_context* ctx, int32_t n_in, int32_t hidden, int32_
   M->y = M->dy = M->loss = nullptr;
   M->tcap = 0;
   M->dzT = M->dzT2 = nullptr;
+  M->use_graph = true;
+  M->tg_graph = nullptr;
+  M->tg_exec = nullptr;
+  M->tg_adam = nullptr;
+  memset(&M->tg_adam_params, 0, sizeof(M->tg_adam_params));
+  M->tg_n = 0;
+  M->tg_stream = nullptr;
+  M->xs = M->ts = nullptr;
+  M->scap = 0;
   M->tc_err = nullptr;
   M->forward_path = CRP_MLP_PATH_AUTO;
   M->sm_count = 0;
@@ -947,6 +1077,10 @@ crp_status crp_mlp_create(crp_context* ctx, int32_t n_in, int32_t hidden, int32_
 crp_status crp_mlp_destroy(crp_mlp* M) {
   if (!M) return CRP_OK;
   cudaDeviceSynchronize();
+  drop_graph(M);
+  if (M->tg_stream) cudaStreamDestroy(M->tg_stream);
+  dev_free(M->xs);
+  dev_free(M->ts);
   free_ws(M);
   free_tws(M);
   dev_free(M->params);
@@ -1058,6 +1192,16 @@ crp_status crp_mlp_set_forward_path(crp_mlp* M, int32_t path) {
   return CRP_OK;
 }
 
+crp_status crp_mlp_set_train_graph(crp_mlp* M, int32_t enable) {
+  if (!M) {
+    set_error("crp_mlp_set_train_graph: NULL argument");
+    return CRP_E_INVALID;
+  }
+  M->use_graph = enable != 0;
+  if (!M->use_graph) drop_graph(M);
+  return CRP_OK;
+}
+
 crp_status crp_mlp_train_step(crp_mlp* M, const float* x, const float* t, int64_t n, float lr,
                               float* loss_out, void* stream) {
   if (!M || !x || !t || n < 128 || n % 128 != 0 || !(lr >= 0.f)) {
@@ -1070,15 +1214,41 @@ crp_status crp_mlp_train_step(crp_mlp* M, const float* x, const float* t, int64_
   const bool tc = !M->wimg.empty() && M->forward_path != CRP_MLP_PATH_LAYERED;
   crp_status st = ensure_ws(M, n);
   if (st == CRP_OK && tc) st = ensure_tws(M, n);
-  if (st == CRP_OK) st = forward(M, x, n, t, nullptr, s, tc);
-  if (st == CRP_OK) st = backward(M, x, n, s, tc);
-  if (st == CRP_OK && lr > 0.f) {
+  // graph replay: tensor-core path, an Adam step, a stream not being captured
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  const bool graph = tc && lr > 0.f && M->use_graph && cs == cudaStreamCaptureStatusNone;
+  if (st == CRP_OK && graph) st = ensure_stage(M, n);
+  if (st != CRP_OK) return st;
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  if (graph && M->tg_exec && M->tg_n == n) {
+    cudaError_t e = cudaMemcpyAsync(M->xs, x, sizeof(float) * (size_t)n * M->n_in,
+                                    cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(M->ts, t, sizeof(float) * (size_t)n * 3, cudaMemcpyDeviceToDevice, s);
     M->step += 1;
-    const float b1 = 0.9f, b2 = 0.999f;
-    const float c1 = 1.f - powf(b1, (float)M->step), c2 = 1.f - powf(b2, (float)M->step);
-    k_adam<<<nblk(M->n_params, 256), 256, 0, s>>>(M->params, M->grad, M->m, M->v, M->n_params, lr,
-                                                  b1, b2, 1e-8f, c1, c2);
-    st = refresh_bf16(M, s);
+    float c1 = 1.f - powf(b1, (float)M->step), c2 = 1.f - powf(b2, (float)M->step);
+    float lr_ = lr;
+    int64_t np = M->n_params;
+    void* args[] = {&M->params, &M->grad, &M->m, &M->v, &np, &lr_, (void*)&b1, (void*)&b2,
+                    (void*)&eps, &c1, &c2};
+    cudaKernelNodeParams kp = M->tg_adam_params;
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    if (e == cudaSuccess) e = cudaGraphExecKernelNodeSetParams(M->tg_exec, M->tg_adam, &kp);
+    if (e == cudaSuccess) e = cudaGraphLaunch(M->tg_exec, s);
+    if (e != cudaSuccess) return fail_cuda(e, "crp_mlp_train_step: graph replay");
+  } else {
+    st = forward(M, x, n, t, nullptr, s, tc);
+    if (st == CRP_OK) st = backward(M, x, n, s, tc);
+    if (st == CRP_OK && lr > 0.f) {
+      M->step += 1;
+      const float c1 = 1.f - powf(b1, (float)M->step), c2 = 1.f - powf(b2, (float)M->step);
+      k_adam<<<nblk(M->n_params, 256), 256, 0, s>>>(M->params, M->grad, M->m, M->v, M->n_params,
+                                                    lr, b1, b2, eps, c1, c2);
+      st = refresh_bf16(M, s);
+    }
+    if (st == CRP_OK && graph) capture_train_graph(M, n);  // for the next calls
   }
   if (st == CRP_OK && loss_out) {
     float l = 0.f;

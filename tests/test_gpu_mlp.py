@@ -284,3 +284,39 @@ def test_other_shapes_gradients_match_oracle(torch_dev, n_in, hidden, n_hidden):
     for l in range(len(shapes)):
         for got, want in ((Wg[l], Wr[l]), (bg[l], br[l])):
             assert np.linalg.norm(got - want) / np.linalg.norm(want) < 2e-2, l
+
+
+def test_train_graph_replay_matches_eager(torch_dev):
+    """The graph-replayed training step (staging copies, Adam node arguments
+    updated per step) follows the same trajectory as kernel-by-kernel steps:
+    six Adam steps over distinct batch slices, then parameters and loss."""
+    torch = torch_dev
+    p = _params(51)
+    n, nb = 2048, 3
+    x, t = _batch(n * nb, 52)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    ctx = crp.crp_context_create(0, 1, 16)
+    out = {}
+    try:
+        for graph in (True, False):
+            mlp = crp.crp_mlp_create(ctx, 4, 256, 4, 7)
+            crp.crp_mlp_set_train_graph(mlp, graph)
+            crp.crp_mlp_set_params(mlp, p)
+            losses = []
+            for k in range(6):
+                b = k % nb
+                losses.append(crp.crp_mlp_train_step(mlp, xd[b * n:(b + 1) * n],
+                                                      td[b * n:(b + 1) * n], n, 1e-3))
+            out[graph] = (crp.crp_mlp_get_params(mlp)[0].astype(np.float64), np.array(losses))
+            crp.crp_mlp_destroy(mlp)
+    finally:
+        crp.crp_context_destroy(ctx)
+    pg, lg = out[True]
+    pe, le = out[False]
+    # FP32 atomics sum in a different order from run to run, and Adam turns a
+    # gradient near zero into an update of about +-lr, so a few parameters may
+    # differ by up to 2 lr per step; the bulk agrees to rounding
+    d = np.abs(pg - pe)
+    assert np.median(d) < 1e-6 and np.percentile(d, 99.9) < 6 * 2e-3, (np.median(d), d.max())
+    assert np.allclose(lg, le, rtol=1e-3, atol=1e-6), (lg, le)
+    assert lg[-1] < lg[0]
