@@ -548,8 +548,18 @@ __global__ void k_adam(float* p, const float* g, float* m, float* v, int64_t n, 
 // bf16 copies W (hidden x hidden) and W^T of a hidden layer, and (when img
 // is given) W in the tensor-core operand image of the fused forward kernel:
 // element (o, i) at (o / 8) * (8 n) + (i / 8) * 64 + (o % 8) * 8 + i % 8.
-__global__ void k_to_bf16_pair(const float* __restrict__ W, int n, __nv_bfloat16* __restrict__ wb,
-                               __nv_bfloat16* __restrict__ wbt, __nv_bfloat16* __restrict__ img) {
+struct Bf16Jobs {
+  const float* W[16];
+  __nv_bfloat16* wb[16];
+  __nv_bfloat16* wbt[16];
+  __nv_bfloat16* img[16];
+};
+
+__global__ void k_to_bf16_pair(const Bf16Jobs jobs, int n) {
+  const float* __restrict__ W = jobs.W[blockIdx.y];
+  __nv_bfloat16* __restrict__ wb = jobs.wb[blockIdx.y];
+  __nv_bfloat16* __restrict__ wbt = jobs.wbt[blockIdx.y];
+  __nv_bfloat16* __restrict__ img = jobs.img[blockIdx.y];
   const int64_t total = (int64_t)n * n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -686,10 +696,21 @@ crp_status ensure_ws(crp_mlp* M, int64_t n) {
 }
 
 crp_status refresh_bf16(crp_mlp* M, cudaStream_t s) {
-  for (int l = 1; l < M->n_hidden; ++l)
-    k_to_bf16_pair<<<nblk((int64_t)M->hidden * M->hidden, 256), 256, 0, s>>>(
-        M->params + M->w_off[l], M->hidden, M->wb[l], M->wbt[l],
-        M->wimg.empty() ? nullptr : M->wimg[l]);
+  // every hidden layer in one launch (grid.y = layer), up to 16 layers
+  Bf16Jobs jobs;
+  memset(&jobs, 0, sizeof(jobs));
+  int nj = 0;
+  for (int l = 1; l < M->n_hidden && nj < 16; ++l, ++nj) {
+    jobs.W[nj] = M->params + M->w_off[l];
+    jobs.wb[nj] = M->wb[l];
+    jobs.wbt[nj] = M->wbt[l];
+    jobs.img[nj] = M->wimg.empty() ? nullptr : M->wimg[l];
+  }
+  if (nj > 0) {
+    const int64_t total = (int64_t)M->hidden * M->hidden;
+    const unsigned gx = (unsigned)((total + 255) / 256 < 1024 ? (total + 255) / 256 : 1024);
+    k_to_bf16_pair<<<dim3(gx, nj), 256, 0, s>>>(jobs, M->hidden);
+  }
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? CRP_OK : fail_cuda(e, "mlp: bf16 weights");
 }
@@ -858,9 +879,9 @@ crp_status backward(crp_mlp* M, const float* x, int64_t n, cudaStream_t s, bool 
       g.splits = (int)(sp < sp_max ? sp : sp_max);
       g.out_f = M->grad + M->w_off[l];
       g.ldf = H;
+      g.rowsum = M->grad + M->b_off[l];  // db_l: the rows of dz_l^T summed over the batch
       cudaError_t e = gemm_tc(GEMM_TC_ATOMIC, g, M->device, M->sm_count, s);
       if (e != cudaSuccess) return fail_cuda(e, "mlp: tensor-core weight-gradient GEMM");
-      launch_colsum(M, dz, n, M->grad + M->b_off[l], s);
       // dz_{l-1} = (dz_l W_l) masked by ReLU'(h_{l-1}): B = W_l^T [H][H]
       memset(&g, 0, sizeof(g));
       g.err = M->tc_err;

@@ -425,6 +425,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     range(item, kb, ke);
     if (kb >= ke) continue;  // an empty split (the same for every thread)
     const int64_t mt = item % m_tiles;
+    float row_acc = 0.f;
     for (int64_t c0 = kb; c0 < ke; c0 += kH) {
       const int kc = (int)(ke - c0 < kH ? ke - c0 : kH);
       if (!prefetched) issue(item, c0, kc, !(b_resident && b_loaded));
@@ -451,6 +452,24 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         mma_commit(bar);
       }
+      if (P.rowsum) {
+        // while the MMAs run: thread (row r, half g) sums 4 of the 8 16-byte
+        // chunks of its row in every box (the swizzle only permutes a row's
+        // chunks, so the sum needs no unswizzling)
+        for (int a = 0; a < kc / 64; ++a) {
+          const unsigned char* rp = As + a * kAtomA + r * 128 + g * 64;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const uint4 q = *reinterpret_cast<const uint4*>(rp + 16 * c);
+            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(&w[e]);
+              row_acc += __low2float(v) + __high2float(v);
+            }
+          }
+        }
+      }
       bool ok = bar_wait(bar, parity);
       if (!ok) ok = bar_wait(bar, parity);
       parity ^= 1u;
@@ -474,6 +493,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     // ---- epilogue: row r of the tile, columns [128 g, 128 g + 128) ----
     const int64_t row = mt * kRows + r;
+    if (P.rowsum) atomicAdd(P.rowsum + row, row_acc);
 #pragma unroll 1
     for (int cc = 4 * g; cc < 4 * g + 4; ++cc) {
       uint32_t v[32];

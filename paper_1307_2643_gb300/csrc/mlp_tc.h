@@ -34,7 +34,9 @@ struct MlpTcParams {
 //   GEMM_TC_BIAS_RELU  out = bf16(max(C + bias, 0))
 //   GEMM_TC_MASK       out = bf16(C where mask > 0, else 0)
 //   GEMM_TC_ATOMIC     out_f += C (vector reductions; split-K partial sums)
-// The first two also write out_t = out^T ([256][ldot]) when out_t is given.
+// The first two also write out_t = out^T ([256][ldot]) when out_t is given;
+// with rowsum, the row sums of A are added to it (the bias gradient when A is
+// a transposed backward signal).
 enum GemmTcEpi { GEMM_TC_BIAS_RELU = 0, GEMM_TC_MASK = 1, GEMM_TC_ATOMIC = 2 };
 struct GemmTcParams {
   const __nv_bfloat16* A;
@@ -52,6 +54,7 @@ struct GemmTcParams {
   int64_t ldot;
   float* out_f;
   int64_t ldf;
+  float* rowsum;  // optional: rowsum[m] += sum over the item's K range of A[m][k]
   unsigned* err;  // set to 1 when a tensor-core wait timed out
 };
 cudaError_t gemm_tc(int epi, const GemmTcParams& p, int device, int sm_count, cudaStream_t s);
