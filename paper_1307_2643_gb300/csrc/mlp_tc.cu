@@ -25,6 +25,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -361,16 +362,38 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-__device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
-  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"l"(p), "f"(a), "f"(b),
-               "f"(c), "f"(d)
-               : "memory");
+// Store / add one 2D box from shared memory to global through the TMA (bulk
+// async group of the issuing thread).
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];\n" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(x), "r"(y), "r"(smem_u32(src))
+      : "memory");
+}
+__device__ __forceinline__ void tma_reduce_add_2d(const CUtensorMap* map, int x, int y,
+                                                  const void* src) {
+  asm volatile(
+      "cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2}], "
+      "[%3];\n" ::"l"(reinterpret_cast<uint64_t>(map)),
+      "r"(x), "r"(y), "r"(smem_u32(src))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
 }
 
 template <int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const GemmTcParams P, const __grid_constant__ CUtensorMap mapA,
-              const __grid_constant__ CUtensorMap mapB) {
+              const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapO,
+              const __grid_constant__ CUtensorMap mapOT) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   unsigned char* base = tc_smem + ((1024u - (smem_u32(tc_smem) & 1023u)) & 1023u);
   unsigned char* As = base;               // 4 boxes of 16 KB
@@ -481,30 +504,25 @@ __global__ void __launch_bounds__(kThreads, 1)
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     }
     if (failed) break;
-    // the operand tiles are free: copy the next item's first chunk now
-    const int64_t next = item + gridDim.x;
-    if (next < items) {
-      int64_t nb, ne;
-      range(next, nb, ne);
-      if (nb < ne) {
-        issue(next, nb, (int)(ne - nb < kH ? ne - nb : kH), !b_resident);
-        prefetched = true;
-      }
-    }
-    // ---- epilogue: row r of the tile, columns [128 g, 128 g + 128) ----
+    // ---- epilogue, staged in the operand tiles (the MMAs are done with
+    // them): row r of the tile, columns [128 g, 128 g + 128), written into
+    // TMA store boxes in the 128-byte-swizzled layout (16-byte chunk j of a
+    // 128-byte box row y at position j ^ (y % 8)) ----
     const int64_t row = mt * kRows + r;
     if (P.rowsum) atomicAdd(P.rowsum + row, row_acc);
+    unsigned char* stage = base;
 #pragma unroll 1
     for (int cc = 4 * g; cc < 4 * g + 4; ++cc) {
       uint32_t v[32];
       tmem_ld32(tmem_warp + (uint32_t)(cc * 32), v);
       const int col0 = cc * 32;
       if constexpr (EPI == GEMM_TC_ATOMIC) {
-        float* dst = P.out_f + row * P.ldf + col0;
+        // FP32 box cc (32 columns): row r, chunks q = 0..7
+        unsigned char* rp = stage + cc * kAtomA + r * 128;
 #pragma unroll
-        for (int j = 0; j < 32; j += 4)
-          red_add_v4(dst + j, __uint_as_float(v[j]), __uint_as_float(v[j + 1]),
-                     __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
+        for (int q = 0; q < 8; ++q)
+          *reinterpret_cast<uint4*>(rp + 16 * (q ^ (r & 7))) =
+              make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
       } else {
         float f[32];
         if constexpr (EPI == GEMM_TC_BIAS_RELU) {
@@ -534,24 +552,67 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t w[16];
 #pragma unroll
         for (int j = 0; j < 32; j += 2) w[j / 2] = pack_bf16(f[j], f[j + 1]);
-        uint4* orow = reinterpret_cast<uint4*>(P.out + row * P.ldo + col0);
+        // row-major box cc / 2 (64 columns): chunks 4 (cc % 2) .. + 3 of row r
+        unsigned char* rp = stage + (cc >> 1) * kAtomA + r * 128;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) orow[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+        for (int q = 0; q < 4; ++q) {
+          const int j = 4 * (cc & 1) + q;
+          *reinterpret_cast<uint4*>(rp + 16 * (j ^ (r & 7))) =
+              make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+        }
         if (P.out_t) {
+          // transposed boxes (64 tile rows x 256 columns): box r / 64, box row
+          // = column c, element r % 64 of it
           const __nv_bfloat16* wb = reinterpret_cast<const __nv_bfloat16*>(w);
+          unsigned char* tb = stage + 4 * kAtomA + (r >> 6) * kAtomB;
+          const int p = r & 63;
 #pragma unroll
-          for (int j = 0; j < 32; ++j) P.out_t[(int64_t)(col0 + j) * P.ldot + row] = wb[j];
+          for (int jj = 0; jj < 32; ++jj) {
+            const int c = col0 + jj;
+            *reinterpret_cast<__nv_bfloat16*>(tb + c * 128 + 16 * ((p >> 3) ^ (c & 7)) +
+                                              2 * (p & 7)) = wb[jj];
+          }
         }
       }
     }
+    // staging written (generic proxy) -> visible to the TMA (async proxy);
     // every TMEM read is done before the next item's MMAs overwrite it
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (tid == 0) {
+      const int y = (int)(mt * kRows);
+      if constexpr (EPI == GEMM_TC_ATOMIC) {
+        for (int b = 0; b < 8; ++b) tma_reduce_add_2d(&mapO, 32 * b, y, stage + b * kAtomA);
+      } else {
+        for (int b = 0; b < 4; ++b) tma_store_2d(&mapO, 64 * b, y, stage + b * kAtomA);
+        if (P.out_t)
+          for (int b = 0; b < 2; ++b)
+            tma_store_2d(&mapOT, y + 64 * b, 0, stage + 4 * kAtomA + b * kAtomB);
+      }
+      bulk_commit();
+      bulk_wait_read();  // the staging may be overwritten once the TMA has read it
+    }
+    __syncthreads();
+    // the staging overwrote the B tile: the next item copies B again, and its
+    // first chunk is started now
+    b_loaded = false;
+    const int64_t next = item + gridDim.x;
+    if (next < items) {
+      int64_t nb, ne;
+      range(next, nb, ne);
+      if (nb < ne) {
+        issue(next, nb, (int)(ne - nb < kH ? ne - nb : kH), true);
+        prefetched = true;
+        b_loaded = true;
+      }
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (tid == 0) bulk_wait_all();  // every TMA store / reduction has completed
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
                  "r"(kTmemCols)
@@ -582,14 +643,15 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// Tensor map of a row-major bf16 matrix (rows x cols, leading dimension ld
-// elements) read in boxes of 64 columns x box_rows rows, 128-byte swizzle.
-// Maps are cached by (address, shape, box): the training step reuses a few
-// fixed buffers.
-bool tensor_map(const __nv_bfloat16* base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+// Tensor map of a row-major matrix (rows x cols, leading dimension ld
+// elements; bf16 or FP32) in boxes of 128 bytes of a row (64 bf16 or 32 FP32)
+// x box_rows rows, 128-byte swizzle.  Maps are cached by (address, type,
+// shape, box): the training step reuses a few fixed buffers.
+bool tensor_map(const void* base, bool f32, int64_t rows, int64_t cols, int64_t ld, int box_rows,
                 CUtensorMap* out) {
   struct Entry {
     const void* base;
+    bool f32;
     int64_t rows, cols, ld;
     int box_rows;
     CUtensorMap map;
@@ -598,20 +660,23 @@ bool tensor_map(const __nv_bfloat16* base, int64_t rows, int64_t cols, int64_t l
   static std::vector<Entry> cache;
   std::lock_guard<std::mutex> lock(mu);
   for (const Entry& e : cache)
-    if (e.base == base && e.rows == rows && e.cols == cols && e.ld == ld && e.box_rows == box_rows) {
+    if (e.base == base && e.f32 == f32 && e.rows == rows && e.cols == cols && e.ld == ld &&
+        e.box_rows == box_rows) {
       *out = e.map;
       return true;
     }
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
-  Entry e{base, rows, cols, ld, box_rows, {}};
+  Entry e{base, f32, rows, cols, ld, box_rows, {}};
+  const size_t esz = f32 ? 4 : 2;
   const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(__nv_bfloat16)};
-  const cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * esz};
+  const cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1u, 1u};
-  if (fn(&e.map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims,
-         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+  if (fn(&e.map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+         const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return false;
   if (cache.size() >= 64) cache.erase(cache.begin());
   cache.push_back(e);
@@ -630,15 +695,25 @@ cudaError_t gemm_tc(int epi, const GemmTcParams& p, int device, int sm_count, cu
   bool ok = aligned && p.M > 0 && p.M % kRows == 0 && p.K > 0 && p.K % 64 == 0 && p.splits >= 1 &&
             p.err;
   if (epi == GEMM_TC_ATOMIC)
-    ok = ok && p.out_f && (uintptr_t)p.out_f % 16 == 0 && p.ldf % 4 == 0;
+    ok = ok && p.out_f && (uintptr_t)p.out_f % 16 == 0 && p.ldf % 4 == 0 && p.ldf >= kH;
   else
-    ok = ok && p.out && (uintptr_t)p.out % 16 == 0 && p.ldo % 8 == 0 &&
+    ok = ok && p.out && (uintptr_t)p.out % 16 == 0 && p.ldo % 8 == 0 && p.ldo >= kH &&
+         (!p.out_t || ((uintptr_t)p.out_t % 16 == 0 && p.ldot % 8 == 0 && p.ldot >= p.M)) &&
          (epi == GEMM_TC_BIAS_RELU ? (p.bias && (uintptr_t)p.bias % 16 == 0)
                                    : (p.mask && (uintptr_t)p.mask % 16 == 0 && p.ldm % 8 == 0));
   if (!ok || epi < GEMM_TC_BIAS_RELU || epi > GEMM_TC_ATOMIC) return cudaErrorInvalidValue;
-  CUtensorMap mapA, mapB;
-  if (!tensor_map(p.A, p.M, p.K, p.lda, kRows, &mapA) || !tensor_map(p.B, kH, p.K, p.ldb, kH, &mapB))
-    return cudaErrorInvalidValue;
+  // operand maps (loads) and output maps (stores / reductions of the tile)
+  CUtensorMap mapA, mapB, mapO, mapOT;
+  memset(&mapOT, 0, sizeof(mapOT));
+  bool maps = tensor_map(p.A, false, p.M, p.K, p.lda, kRows, &mapA) &&
+              tensor_map(p.B, false, kH, p.K, p.ldb, kH, &mapB);
+  if (epi == GEMM_TC_ATOMIC) {
+    maps = maps && tensor_map(p.out_f, true, p.M, kH, p.ldf, kRows, &mapO);
+  } else {
+    maps = maps && tensor_map(p.out, false, p.M, kH, p.ldo, kRows, &mapO);
+    if (p.out_t) maps = maps && tensor_map(p.out_t, false, kH, p.M, p.ldot, kH, &mapOT);
+  }
+  if (!maps) return cudaErrorInvalidValue;
   auto k = epi == GEMM_TC_BIAS_RELU ? k_gemm_tc<GEMM_TC_BIAS_RELU>
            : epi == GEMM_TC_MASK    ? k_gemm_tc<GEMM_TC_MASK>
                                     : k_gemm_tc<GEMM_TC_ATOMIC>;
@@ -653,7 +728,7 @@ cudaError_t gemm_tc(int epi, const GemmTcParams& p, int device, int sm_count, cu
   }
   const int64_t items = p.M / kRows * p.splits;
   const int64_t grid = items < sm_count ? items : sm_count;
-  k<<<(unsigned)grid, kThreads, kGemmSmem, s>>>(p, mapA, mapB);
+  k<<<(unsigned)grid, kThreads, kGemmSmem, s>>>(p, mapA, mapB, mapO, mapOT);
   return cudaGetLastError();
 }
 
