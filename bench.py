@@ -54,7 +54,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--graph", action="store_true",
                     help="run each propagation's round loop as one captured CUDA graph")
-    ap.add_argument("--workload", choices=("mixed", "galactic", "uneven", "e2e", "cosmology"),
+    ap.add_argument("--workload", choices=("mixed", "galactic", "uneven", "e2e", "cosmology",
+                                           "train"),
                     default="mixed",
                     help="mixed: the propagation benchmark; galactic: back-tracking, MLP "
                          "surrogate training / inference and lens builds; uneven: 10^7 "
@@ -940,6 +941,61 @@ def run_e2e(args):
     print(json.dumps(summary))
 
 
+MLP_FLOPS_PER_SAMPLE_FWD = 2 * (4 * 256 + 3 * 256 * 256 + 256 * 3)  # 4 -> 256^3 -> 3
+
+
+def run_train(args):
+    """MLP lens surrogate training step (4 inputs, 4 hidden layers of 256, batch
+    16384, Adam) on synthetic inputs of the surrogate's shape (isotropic
+    directions, log10 R - 19 in [-1, 1], smooth targets): the tensor-core path
+    replayed from its CUDA graph against the layered mma.sync path.  Time per
+    step by CUDA events over `steps` steps after `warmup`."""
+    import torch
+    from paper_1307_2643_gb300 import crp
+    from paper_1307_2643_gb300.build import build
+
+    torch.cuda.set_device(0)
+    build()
+    crp.use_torch_allocator(0)
+    B, nb = 16384, 16
+    g = workloads.rng(workloads.MASTER_SEED + 8)
+    ux, uy, uz = workloads.isotropic(g, B * nb)
+    lr10 = g.uniform(-1.0, 1.0, B * nb)
+    x = np.stack([ux, uy, uz, lr10], axis=1).astype(np.float32)
+    ang = 0.8 * (1.0 - lr10)
+    t = np.stack([np.cos(ang) * ux - np.sin(ang) * uy, np.sin(ang) * ux + np.cos(ang) * uy, uz],
+                 axis=1).astype(np.float32)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    ctx = crp.crp_context_create(0, workloads.MASTER_SEED + 8, 1024)
+    out = {"workload": "mlp_train_4x256x4_batch16384", "metric": "training samples/s",
+           "flops_per_sample": 3 * MLP_FLOPS_PER_SAMPLE_FWD}
+    steps, warm = max(args.steps, 1) * 50, max(args.warmup, 1) * 10
+    for path, name in ((crp.MLP_PATH_AUTO, "tcgen05_graph"), (crp.MLP_PATH_LAYERED, "mma_sync")):
+        mlp = crp.crp_mlp_create(ctx, 4, 256, 4, workloads.MASTER_SEED + 8)
+        crp.crp_mlp_set_forward_path(mlp, path)
+        for k in range(warm):
+            b = k % nb
+            crp.crp_mlp_train_step(mlp, xd[b * B:(b + 1) * B], td[b * B:(b + 1) * B], B, 1e-3,
+                                   want_loss=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in range(steps):
+            b = k % nb
+            crp.crp_mlp_train_step(mlp, xd[b * B:(b + 1) * B], td[b * B:(b + 1) * B], B, 1e-3,
+                                   want_loss=False)
+        e1.record()
+        torch.cuda.synchronize()
+        dt = e0.elapsed_time(e1) / 1e3 / steps
+        loss = crp.crp_mlp_train_step(mlp, xd[:B], td[:B], B, 0.0)
+        out[name] = {"us_per_step": dt * 1e6, "samples_per_s": B / dt,
+                     "tflops": B * 3 * MLP_FLOPS_PER_SAMPLE_FWD / dt / 1e12, "steps": steps,
+                     "loss_after": loss}
+        crp.crp_mlp_destroy(mlp)
+    crp.crp_context_destroy(ctx)
+    print(json.dumps(out))
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
@@ -952,5 +1008,7 @@ if __name__ == "__main__":
         run_e2e(a)
     elif a.workload == "cosmology":
         run_cosmology(a)
+    elif a.workload == "train":
+        run_train(a)
     else:
         run_ours(a)
