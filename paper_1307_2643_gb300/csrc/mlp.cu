@@ -519,6 +519,123 @@ __global__ void __launch_bounds__(256) k_out_backward_tile(const float* __restri
   }
 }
 
+// Output layer of a training step in one pass over h = h_{L-1} (hidden 256):
+// per row, y = W_out h + b_out (warp sum), y_hat = y / |y|, the loss term
+// 1 - y_hat . t and dy = -(t - (y_hat . t) y_hat) / |y| / n; then dz =
+// bf16((dy . W_out[:, c]) where h[c] > 0) row-major and transposed, and the
+// output layer's gradients dW_out += dy h^T, db_out += dy summed over the
+// block's rows.  A block of 8 warps takes 128 rows in tiles of 32, one row per
+// warp at a time; lane l owns columns 8 l .. 8 l + 7.
+__global__ void __launch_bounds__(256) k_out_layer_train(
+    const __nv_bfloat16* __restrict__ h, int64_t n, const float* __restrict__ W,
+    const float* __restrict__ bo, const float* __restrict__ t, float* __restrict__ loss,
+    __nv_bfloat16* __restrict__ dz, __nv_bfloat16* __restrict__ dzT, float* __restrict__ gW,
+    float* __restrict__ gb) {
+  constexpr int H = 256;
+  __shared__ __align__(16) __nv_bfloat16 T[32][264];
+  __shared__ float part[8][H];
+  __shared__ float small[8][4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c0 = 8 * lane;
+  float w0[8], w1[8], w2[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    w0[q] = __ldg(W + c0 + q);
+    w1[q] = __ldg(W + H + c0 + q);
+    w2[q] = __ldg(W + 2 * H + c0 + q);
+  }
+  const float b0 = __ldg(bo), b1 = __ldg(bo + 1), b2 = __ldg(bo + 2);
+  const float inv_n = 1.f / (float)n;
+  float aw0[8], aw1[8], aw2[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) aw0[q] = aw1[q] = aw2[q] = 0.f;
+  float ab0 = 0.f, ab1 = 0.f, ab2 = 0.f, lsum = 0.f;
+  for (int tile = 0; tile < 4; ++tile) {
+    const int64_t r0 = blockIdx.x * 128ll + 32 * tile;
+    if (r0 >= n) break;
+    for (int rr = warp; rr < 32; rr += 8) {
+      const int64_t r = r0 + rr;
+      if (r >= n) break;
+      const uint4 hq = __ldg(reinterpret_cast<const uint4*>(h + r * H + c0));
+      const __nv_bfloat16* hb = reinterpret_cast<const __nv_bfloat16*>(&hq);
+      float hv[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) hv[q] = __bfloat162float(hb[q]);
+      float y0 = 0.f, y1 = 0.f, y2 = 0.f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        y0 = fmaf(w0[q], hv[q], y0);
+        y1 = fmaf(w1[q], hv[q], y1);
+        y2 = fmaf(w2[q], hv[q], y2);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        y0 += __shfl_xor_sync(0xffffffffu, y0, o);
+        y1 += __shfl_xor_sync(0xffffffffu, y1, o);
+        y2 += __shfl_xor_sync(0xffffffffu, y2, o);
+      }
+      y0 += b0;
+      y1 += b1;
+      y2 += b2;
+      const float nrm = sqrtf(y0 * y0 + y1 * y1 + y2 * y2);
+      const float inv = nrm > 0.f ? 1.f / nrm : 0.f;
+      const float yh0 = y0 * inv, yh1 = y1 * inv, yh2 = y2 * inv;
+      const float t0 = __ldg(t + 3 * r), t1 = __ldg(t + 3 * r + 1), t2 = __ldg(t + 3 * r + 2);
+      const float d = yh0 * t0 + yh1 * t1 + yh2 * t2;
+      const float dy0 = -(t0 - d * yh0) * inv * inv_n;
+      const float dy1 = -(t1 - d * yh1) * inv * inv_n;
+      const float dy2 = -(t2 - d * yh2) * inv * inv_n;
+      if (lane == 0) {
+        lsum += 1.f - d;
+        ab0 += dy0;
+        ab1 += dy1;
+        ab2 += dy2;
+      }
+      __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        float g = dy0 * w0[q] + dy1 * w1[q] + dy2 * w2[q];
+        if (!(hv[q] > 0.f)) g = 0.f;
+        v[q] = __float2bfloat16_rn(g);
+        aw0[q] = fmaf(dy0, hv[q], aw0[q]);
+        aw1[q] = fmaf(dy1, hv[q], aw1[q]);
+        aw2[q] = fmaf(dy2, hv[q], aw2[q]);
+      }
+      *reinterpret_cast<uint4*>(dz + r * H + c0) = *reinterpret_cast<const uint4*>(v);
+      *reinterpret_cast<uint4*>(&T[rr][c0]) = *reinterpret_cast<const uint4*>(v);
+    }
+    __syncthreads();
+    store_tile_transposed(T, 0, r0, n, dzT);
+    __syncthreads();
+  }
+  // block sums of the gradients, one output at a time through shared memory
+  auto block_sum = [&](const float (&a)[8], int o) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) part[warp][c0 + q] = a[q];
+    __syncthreads();
+    float v = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) v += part[w][threadIdx.x];
+    atomicAdd(gW + o * H + threadIdx.x, v);
+    __syncthreads();
+  };
+  block_sum(aw0, 0);
+  block_sum(aw1, 1);
+  block_sum(aw2, 2);
+  if (lane == 0) {
+    small[warp][0] = ab0;
+    small[warp][1] = ab1;
+    small[warp][2] = ab2;
+    small[warp][3] = lsum;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    float v = 0.f;
+    for (int w = 0; w < 8; ++w) v += small[w][threadIdx.x];
+    atomicAdd(threadIdx.x < 3 ? gb + threadIdx.x : loss, v);
+  }
+}
+
 // Transpose a bf16 [rows][cols] matrix into [cols][rows] (32 x 32 tiles).
 __global__ void k_transpose(const __nv_bfloat16* __restrict__ in, int64_t rows, int cols,
                             __nv_bfloat16* __restrict__ out) {
@@ -811,6 +928,9 @@ void gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* Bt, int ldb, int
 // activations the weight gradients need; else the layered mma.sync GEMMs.
 crp_status forward(crp_mlp* M, const float* x, int64_t n, const float* t, float* y_hat,
                    cudaStream_t s, bool tc = false) {
+  // training on the tensor-core path: the output layer (loss, dy and its
+  // backward) runs fused at the start of backward()
+  const bool fused_out = tc && t && !y_hat && M->hidden == 256;
   const int H = M->hidden;
   launch_layer_in(M, x, n, tc ? M->hT[0] : nullptr, s);
   for (int l = 1; l < M->n_hidden; ++l) {
@@ -839,9 +959,10 @@ crp_status forward(crp_mlp* M, const float* x, int64_t n, const float* t, float*
   }
   const int lo = M->n_hidden;
   if (t) cudaMemsetAsync(M->loss, 0, sizeof(float), s);
-  k_layer_out<<<nblk(n * 32, 256), 256, 0, s>>>(M->h[lo - 1], n, H, M->params + M->w_off[lo],
-                                                M->params + M->b_off[lo], 3, t, y_hat, M->dy,
-                                                M->loss);
+  if (!fused_out)
+    k_layer_out<<<nblk(n * 32, 256), 256, 0, s>>>(M->h[lo - 1], n, H, M->params + M->w_off[lo],
+                                                  M->params + M->b_off[lo], 3, t, y_hat, M->dy,
+                                                  M->loss);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? CRP_OK : fail_cuda(e, "mlp: forward");
 }
@@ -850,12 +971,19 @@ crp_status forward(crp_mlp* M, const float* x, int64_t n, const float* t, float*
 // the batch) of every parameter into M->grad.  tc: weight gradients and
 // backward-data products on the tensor cores, reading the transposed signals
 // the epilogues wrote; else transposes plus the layered mma.sync GEMMs.
-crp_status backward(crp_mlp* M, const float* x, int64_t n, cudaStream_t s, bool tc = false) {
+crp_status backward(crp_mlp* M, const float* x, const float* t, int64_t n, cudaStream_t s,
+                    bool tc = false) {
   const int H = M->hidden, L = M->n_hidden;
   cudaMemsetAsync(M->grad, 0, sizeof(float) * M->n_params, s);
   // output layer
-  launch_grad_out(M, n, s);
-  launch_out_backward(M, n, tc ? M->dzT : nullptr, s);
+  if (tc && H == 256) {  // forward() left the output layer to this fused pass
+    k_out_layer_train<<<(unsigned)((n + 127) / 128), 256, 0, s>>>(
+        M->h[L - 1], n, M->params + M->w_off[L], M->params + M->b_off[L], t, M->loss, M->dz,
+        M->dzT, M->grad + M->w_off[L], M->grad + M->b_off[L]);
+  } else {
+    launch_grad_out(M, n, s);
+    launch_out_backward(M, n, tc ? M->dzT : nullptr, s);
+  }
   __nv_bfloat16* dz = M->dz;
   __nv_bfloat16* dz_next = M->dz2;
   __nv_bfloat16* dzT = M->dzT;
@@ -898,6 +1026,12 @@ crp_status backward(crp_mlp* M, const float* x, int64_t n, cudaStream_t s, bool 
       g.ldo = H;
       g.out_t = l > 1 ? dzT_next : nullptr;
       g.ldot = n;
+      if (l == 1) {  // dz_0 feeds only the input layer's gradients: taken in this epilogue
+        g.xin = x;
+        g.n_in = M->n_in;
+        g.gw_in = M->grad + M->w_off[0];
+        g.gb_in = M->grad + M->b_off[0];
+      }
       e = gemm_tc(GEMM_TC_MASK, g, M->device, M->sm_count, s);
       if (e != cudaSuccess) return fail_cuda(e, "mlp: tensor-core backward-data GEMM");
     } else {
@@ -914,8 +1048,9 @@ crp_status backward(crp_mlp* M, const float* x, int64_t n, cudaStream_t s, bool 
     std::swap(dz, dz_next);
     std::swap(dzT, dzT_next);
   }
-  // input layer: dz holds dL/dz_1
-  launch_grad_in(M, dz, x, n, s);
+  // input layer: dz holds dL/dz_1 (on the tensor-core path the last
+  // backward-data GEMM has already added its gradients)
+  if (!tc) launch_grad_in(M, dz, x, n, s);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? CRP_OK : fail_cuda(e, "mlp: backward");
 }
@@ -936,7 +1071,7 @@ void capture_train_graph(crp_mlp* M, int64_t n) {
     return;
   }
   crp_status st = forward(M, M->xs, n, M->ts, nullptr, cs, true);
-  if (st == CRP_OK) st = backward(M, M->xs, n, cs, true);
+  if (st == CRP_OK) st = backward(M, M->xs, M->ts, n, cs, true);
   if (st == CRP_OK) {
     k_adam<<<nblk(M->n_params, 256), 256, 0, cs>>>(M->params, M->grad, M->m, M->v, M->n_params,
                                                    0.f, 0.9f, 0.999f, 1e-8f, 1.f, 1.f);
@@ -1261,7 +1396,7 @@ crp_status crp_mlp_train_step(crp_mlp* M, const float* x, const float* t, int64_
     if (e != cudaSuccess) return fail_cuda(e, "crp_mlp_train_step: graph replay");
   } else {
     st = forward(M, x, n, t, nullptr, s, tc);
-    if (st == CRP_OK) st = backward(M, x, n, s, tc);
+    if (st == CRP_OK) st = backward(M, x, t, n, s, tc);
     if (st == CRP_OK && lr > 0.f) {
       M->step += 1;
       const float c1 = 1.f - powf(b1, (float)M->step), c2 = 1.f - powf(b2, (float)M->step);

@@ -426,6 +426,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int64_t items = m_tiles * P.splits;
   const int64_t ks = ((P.K + P.splits - 1) / P.splits + 63) / 64 * 64;  // K per split
   const bool b_resident = P.splits == 1 && P.K <= kH;
+  auto row0_of = [&](int64_t mt_) { return mt_ * kRows; };
   auto range = [&](int64_t item, int64_t& kb, int64_t& ke) {
     kb = (item / m_tiles) * ks;
     ke = kb + ks < P.K ? kb + ks : P.K;
@@ -575,6 +576,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
+    // the input layer's gradients need this tile's inputs: staged after the
+    // output tiles (x rows of the tile, n_in <= 8 floats each)
+    float* xs_tile = reinterpret_cast<float*>(stage + 4 * kAtomA + 2 * kAtomB);
+    if (EPI == GEMM_TC_MASK && P.xin)
+      for (int e = tid; e < kRows * P.n_in; e += kThreads) xs_tile[e] = P.xin[row0_of(mt) * P.n_in + e];
     // staging written (generic proxy) -> visible to the TMA (async proxy);
     // every TMEM read is done before the next item's MMAs overwrite it
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -592,8 +598,30 @@ __global__ void __launch_bounds__(kThreads, 1)
             tma_store_2d(&mapOT, y + 64 * b, 0, stage + 4 * kAtomA + b * kAtomB);
       }
       bulk_commit();
-      bulk_wait_read();  // the staging may be overwritten once the TMA has read it
     }
+    if (EPI == GEMM_TC_MASK && P.xin) {
+      // column tid of the staged bf16 tile against the tile's inputs, read
+      // while the TMA stores it
+      const int c = tid;
+      const unsigned char* cb = stage + (c >> 6) * kAtomA + 2 * (c & 7);
+      const int cj = (c & 63) >> 3;
+      float aw[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, ab = 0.f;
+      const int ni = P.n_in;
+#pragma unroll 4
+      for (int rr = 0; rr < kRows; ++rr) {
+        const float z = __bfloat162float(
+            *reinterpret_cast<const __nv_bfloat16*>(cb + rr * 128 + 16 * (cj ^ (rr & 7))));
+        ab += z;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          if (i < ni) aw[i] = fmaf(z, xs_tile[rr * ni + i], aw[i]);
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (i < ni) atomicAdd(P.gw_in + c * ni + i, aw[i]);
+      atomicAdd(P.gb_in + c, ab);
+    }
+    if (tid == 0) bulk_wait_read();  // the staging may be overwritten once the TMA has read it
     __syncthreads();
     // the staging overwrote the B tile: the next item copies B again, and its
     // first chunk is started now
@@ -701,6 +729,7 @@ cudaError_t gemm_tc(int epi, const GemmTcParams& p, int device, int sm_count, cu
          (!p.out_t || ((uintptr_t)p.out_t % 16 == 0 && p.ldot % 8 == 0 && p.ldot >= p.M)) &&
          (epi == GEMM_TC_BIAS_RELU ? (p.bias && (uintptr_t)p.bias % 16 == 0)
                                    : (p.mask && (uintptr_t)p.mask % 16 == 0 && p.ldm % 8 == 0));
+  if (p.xin) ok = ok && epi == GEMM_TC_MASK && p.n_in >= 1 && p.n_in <= 8 && p.gw_in && p.gb_in;
   if (!ok || epi < GEMM_TC_BIAS_RELU || epi > GEMM_TC_ATOMIC) return cudaErrorInvalidValue;
   // operand maps (loads) and output maps (stores / reductions of the tile)
   CUtensorMap mapA, mapB, mapO, mapOT;

@@ -55,6 +55,13 @@ struct GemmTcParams {
   float* out_f;
   int64_t ldf;
   float* rowsum;  // optional: rowsum[m] += sum over the item's K range of A[m][k]
+  // optional, GEMM_TC_MASK: the input layer's gradients from the output tile
+  // (dz_0) and the inputs x [M][n_in] (n_in <= 8): gw_in[c][i] += sum_m
+  // out[m][c] x[m][i], gb_in[c] += sum_m out[m][c]
+  const float* xin;
+  int n_in;
+  float* gw_in;
+  float* gb_in;
   unsigned* err;  // set to 1 when a tensor-core wait timed out
 };
 cudaError_t gemm_tc(int epi, const GemmTcParams& p, int device, int sm_count, cudaStream_t s);
