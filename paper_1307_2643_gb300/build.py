@@ -23,6 +23,7 @@ UNITS = {
     "tables.cu": [],
     "propagate_fp64.cu": ["-fmad=false"],
     "propagate_mixed.cu": [],
+    "propagate_gmf.cu": [],
     "propagate_1d.cu": ["-fmad=false"],
     "hist_noalloc.cu": [],
     "lens.cu": [],

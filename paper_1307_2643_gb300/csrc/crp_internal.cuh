@@ -157,6 +157,11 @@ cudaError_t launch_propagate_fp64(const KParams& kp, const DevState& st, DevCoun
 cudaError_t launch_propagate_mixed(const KParams& kp, const DevState& st, DevCounters* dc,
                                    int grid, int block, int variant, cudaStream_t s);
 cudaError_t occupancy_propagate_fp64(int dtype, int block, int* blocks_per_sm);
+cudaError_t launch_propagate_mixed_gmf(const KParams& kp, const DevState& st, DevCounters* dc,
+                                       int grid, int block, int variant, cudaStream_t s);
+cudaError_t occupancy_propagate_mixed_gmf(int dtype, int variant, int block, int* bps);
+cudaError_t sample_field_mixed_gmf(const KParams& kp, const double* xyz, int64_t n, double* B,
+                                   cudaStream_t s);
 cudaError_t occupancy_propagate_mixed(int dtype, int galactic, int variant, int block,
                                       int* blocks_per_sm);
 // Dynamic shared memory of one propagate block (per-thread stage storage).

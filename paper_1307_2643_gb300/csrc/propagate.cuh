@@ -936,7 +936,7 @@ struct PolicyFP64 {
 // ---------------------------------------------------------------------------
 enum : int { CAP_NONE = 0, CAP_S = 1, CAP_PION = 2, CAP_PD = 3 };
 
-template <bool GAL>
+template <bool GAL, bool GMF = false>
 struct PolicyMixedT {
   using Real = float;
   static constexpr bool kSharedStages = false;
@@ -1136,11 +1136,13 @@ struct PolicyMixedT {
         B.y += G.y;
         B.z += G.z;
       }
-      if (p.flags & CRP_GMF) {
-        const float3 G = gmf_f32(p, gx, gy, gz);
-        B.x += G.x;
-        B.y += G.y;
-        B.z += G.z;
+      if constexpr (GMF) {
+        if (p.flags & CRP_GMF) {
+          const float3 G = gmf_f32(p, gx, gy, gz);
+          B.x += G.x;
+          B.y += G.y;
+          B.z += G.z;
+        }
       }
     }
     return B;
@@ -1368,7 +1370,8 @@ struct PolicyMixedT {
 };
 
 using PolicyMixed = PolicyMixedT<false>;
-using PolicyMixedGal = PolicyMixedT<true>;
+using PolicyMixedGal = PolicyMixedT<true>;         // analytic disk + halo
+using PolicyMixedGmf = PolicyMixedT<true, true>;   // plus the multi-arm field
 
 // ---------------------------------------------------------------------------
 // Persistent driver: lanes take candidates from the round's work queue, run
