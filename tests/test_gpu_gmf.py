@@ -133,3 +133,34 @@ def test_gmf_backtracking_mixed_vs_fp64():
     live = (h64 + h32) > 0
     chi2 = np.sum((h64[live] - h32[live]) ** 2 / (h64[live] + h32[live]))
     assert chi2 < 2.0 * live.sum(), (chi2, live.sum())
+
+
+def test_all_fields_together_fp64_matches_oracle():
+    """Random grid (32^3 Kolmogorov, periodic) + analytic disk and halo + the
+    multi-arm field, all at once: FP64 back-tracking bit for bit."""
+    WL = workloads.GALACTIC_LENS
+    n3 = (32, 32, 32)
+    dx, lmin, org = workloads.galactic_grid_geometry(32, WL["box"])
+    field = oracle.turbulent_field(n3, dx, lmin, 4.0 * lmin, 1.0, seed=WL["seed"])
+    inj = _antiprotons(256, W["seed"] + 9)
+    ctx = crp.crp_context_create(0, 7, 256 + 16)
+    try:
+        g = crp.crp_grid_create(ctx, crp.grid_desc(n3, dx, origin=org, dtype=crp.F64, data=field))
+        crp.crp_candidates_inject(ctx, crp.candidate_arrays(crp.host_injection(inj)), 256)
+        _, st = crp.crp_propagate(ctx, g, _mods(crp.FP64, flags=crp.GMF | crp.GALACTIC | crp.BORDER,
+                                                galactic=WL["disk"]))
+        gpu = crp.crp_collect(ctx, crp.COLLECT_ALL)
+        gpu = gpu[np.argsort(gpu["id"], kind="stable")]
+    finally:
+        crp.crp_context_destroy(ctx)
+    P = oracle.make_params(grid_n=n3, spacing=dx, origin=org, tol=W["tol"], h_min=W["h_min"],
+                           h_max=W["h_max"], field_unit_T=oracle.MICROGAUSS_T,
+                           length_unit_m=oracle.KPC_M,
+                           flags=oracle.GMF | oracle.GALACTIC | oracle.BORDER,
+                           border_r=W["border_r"], galactic=WL["disk"],
+                           gmf=oracle.make_gmf(**GMF), seed=7, max_steps=2_000_000)
+    ref = oracle.propagate(P, field, inj)
+    assert np.all(ref["status"] == oracle.AT_BORDER)
+    for f in ("x", "u", "E", "s", "n_acc", "n_rej", "status"):
+        assert np.array_equal(gpu[f], ref[f]), f
+    assert st.accepted_steps == int(ref["n_acc"].sum())
