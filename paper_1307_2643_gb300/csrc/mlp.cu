@@ -524,7 +524,7 @@ __global__ void __launch_bounds__(256) k_out_backward_tile(const float* __restri
 // 1 - y_hat . t and dy = -(t - (y_hat . t) y_hat) / |y| / n; then dz =
 // bf16((dy . W_out[:, c]) where h[c] > 0) row-major and transposed, and the
 // output layer's gradients dW_out += dy h^T, db_out += dy summed over the
-// block's rows.  A block of 8 warps takes 128 rows in tiles of 32, one row per
+// block's rows.  A block of 8 warps takes 64 rows in tiles of 32, one row per
 // warp at a time; lane l owns columns 8 l .. 8 l + 7.
 __global__ void __launch_bounds__(256) k_out_layer_train(
     const __nv_bfloat16* __restrict__ h, int64_t n, const float* __restrict__ W,
@@ -550,8 +550,8 @@ __global__ void __launch_bounds__(256) k_out_layer_train(
 #pragma unroll
   for (int q = 0; q < 8; ++q) aw0[q] = aw1[q] = aw2[q] = 0.f;
   float ab0 = 0.f, ab1 = 0.f, ab2 = 0.f, lsum = 0.f;
-  for (int tile = 0; tile < 4; ++tile) {
-    const int64_t r0 = blockIdx.x * 128ll + 32 * tile;
+  for (int tile = 0; tile < 2; ++tile) {
+    const int64_t r0 = blockIdx.x * 64ll + 32 * tile;
     if (r0 >= n) break;
     for (int rr = warp; rr < 32; rr += 8) {
       const int64_t r = r0 + rr;
@@ -977,7 +977,7 @@ crp_status backward(crp_mlp* M, const float* x, const float* t, int64_t n, cudaS
   cudaMemsetAsync(M->grad, 0, sizeof(float) * M->n_params, s);
   // output layer
   if (tc && H == 256) {  // forward() left the output layer to this fused pass
-    k_out_layer_train<<<(unsigned)((n + 127) / 128), 256, 0, s>>>(
+    k_out_layer_train<<<(unsigned)((n + 63) / 64), 256, 0, s>>>(
         M->h[L - 1], n, M->params + M->w_off[L], M->params + M->b_off[L], t, M->loss, M->dz,
         M->dzT, M->grad + M->w_off[L], M->grad + M->b_off[L]);
   } else {
