@@ -157,6 +157,13 @@ cudaError_t launch_propagate_fp64(const KParams& kp, const DevState& st, DevCoun
 cudaError_t launch_propagate_mixed(const KParams& kp, const DevState& st, DevCounters* dc,
                                    int grid, int block, int variant, cudaStream_t s);
 cudaError_t occupancy_propagate_fp64(int dtype, int block, int* blocks_per_sm);
+// Module list of the extragalactic propagation (pair production, adiabatic
+// loss, pion production, E_min, observer): with exactly these flags the mixed
+// kernel is taken from an instantiation that fixes them at compile time.
+constexpr uint32_t kEgalModules = CRP_PAIR | CRP_ADIABATIC | CRP_PION | CRP_EMIN | CRP_OBSERVER;
+cudaError_t launch_propagate_mixed_egal(const KParams& kp, const DevState& st, DevCounters* dc,
+                                        int grid, int block, cudaStream_t s);
+cudaError_t occupancy_propagate_mixed_egal(int dtype, int block, int* bps);
 cudaError_t launch_propagate_mixed_gmf(const KParams& kp, const DevState& st, DevCounters* dc,
                                        int grid, int block, int variant, cudaStream_t s);
 cudaError_t occupancy_propagate_mixed_gmf(int dtype, int variant, int block, int* bps);

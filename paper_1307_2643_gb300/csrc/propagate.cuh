@@ -643,8 +643,16 @@ __device__ __forceinline__ bool is_neutron(const LaneCore& c) { return c.A == 1 
 
 // Is the lane's second free path (photodisintegration, or decay for a free
 // neutron) an active module?
+// Module flags of a kernel: the run-time flags, or (FIX != 0) a module list
+// fixed at compile time, which lets the compiler drop the modules it leaves out.
+template <uint32_t FIX>
+__device__ __forceinline__ uint32_t mflags(const KParams& p) {
+  return FIX ? FIX : p.flags;
+}
+
+template <uint32_t FIX = 0>
 __device__ __forceinline__ bool second_on(const KParams& p, const LaneCore& c) {
-  return (p.flags & (is_neutron(c) ? CRP_DECAY : CRP_PHOTODIS)) != 0;
+  return (mflags<FIX>(p) & (is_neutron(c) ? CRP_DECAY : CRP_PHOTODIS)) != 0;
 }
 
 __device__ __forceinline__ void load_core(const KParams& p, const DevState& st, uint32_t i,
@@ -751,6 +759,7 @@ static __constant__ float c_a32[6][6] = {
 // arithmetic and its order are those of the reference formulation.
 // ---------------------------------------------------------------------------
 struct PolicyFP64 {
+  static constexpr uint32_t kFix = 0;  // run-time module flags
   using Real = double;
   static constexpr bool kSharedStages = true;
   static constexpr size_t kSmemPerThread = kStageSlots * sizeof(double);
@@ -936,8 +945,9 @@ struct PolicyFP64 {
 // ---------------------------------------------------------------------------
 enum : int { CAP_NONE = 0, CAP_S = 1, CAP_PION = 2, CAP_PD = 3 };
 
-template <bool GAL, bool GMF = false>
+template <bool GAL, bool GMF = false, uint32_t FIX = 0>
 struct PolicyMixedT {
+  static constexpr uint32_t kFix = FIX;  // compile-time module list (0: run-time flags)
   using Real = float;
   static constexpr bool kSharedStages = false;
   // per-lane cache of the last cell record gathered (6 float4, lane-interleaved)
@@ -989,12 +999,12 @@ struct PolicyMixedT {
   // once; then lowered by each step's length, so the exact binary64 test
   // runs only when a sphere can be reached in the coming step).
   __device__ __forceinline__ static void bounds(const KParams& p, Lane& c) {
-    if (p.flags & CRP_OBSERVER) {
+    if (mflags<FIX>(p) & CRP_OBSERVER) {
       const double a = c.x[0] - p.obs_c[0], b = c.x[1] - p.obs_c[1], d = c.x[2] - p.obs_c[2];
       const double r = sqrt(a * a + b * b + d * d);
       c.d_obs = (float)((r - p.obs_r) * (1.0 - 1e-6));
     }
-    if (p.flags & CRP_BORDER) {
+    if (mflags<FIX>(p) & CRP_BORDER) {
       const double a = c.x[0] - p.border_c[0], b = c.x[1] - p.border_c[1],
                    d = c.x[2] - p.border_c[2];
       const double r = sqrt(a * a + b * b + d * d);
@@ -1021,8 +1031,8 @@ struct PolicyMixedT {
   // length cap: the end of the trajectory or a pending free path.
   __device__ __forceinline__ static void set_near(const KParams& p, Lane& c) {
     double d = c.s_max - c.s;
-    if ((p.flags & CRP_PION) && c.d_pion < d) d = c.d_pion;
-    if (second_on(p, c) && c.d_pd < d) d = c.d_pd;
+    if ((mflags<FIX>(p) & CRP_PION) && c.d_pion < d) d = c.d_pion;
+    if (second_on<FIX>(p, c) && c.d_pd < d) d = c.d_pd;
     c.near_f = __double2float_rd(d);
   }
 
@@ -1130,14 +1140,14 @@ struct PolicyMixedT {
     }
     if constexpr (GAL) {
       const float gx = c.gal[0] + ox, gy = c.gal[1] + oy, gz = c.gal[2] + oz;
-      if (p.flags & CRP_GALACTIC) {
+      if (mflags<FIX>(p) & CRP_GALACTIC) {
         const float3 G = galactic_f32(p, gx, gy, gz);
         B.x += G.x;
         B.y += G.y;
         B.z += G.z;
       }
       if constexpr (GMF) {
-        if (p.flags & CRP_GMF) {
+        if (mflags<FIX>(p) & CRP_GMF) {
           const float3 G = gmf_f32(p, gx, gy, gz);
           B.x += G.x;
           B.y += G.y;
@@ -1169,11 +1179,11 @@ struct PolicyMixedT {
         h = rem;
         c.cap = CAP_S;
       }
-      if ((p.flags & CRP_PION) && c.d_pion < h) {
+      if ((mflags<FIX>(p) & CRP_PION) && c.d_pion < h) {
         h = c.d_pion;
         c.cap = CAP_PION;
       }
-      if (second_on(p, c) && c.d_pd < h) {
+      if (second_on<FIX>(p, c) && c.d_pd < h) {
         h = c.d_pd;
         c.cap = CAP_PD;
       }
@@ -1292,7 +1302,7 @@ struct PolicyMixedT {
     }
     // observer: exact binary64 segment test only when the sphere is in reach
     c.crossed = false;
-    if (p.flags & CRP_OBSERVER) {
+    if (mflags<FIX>(p) & CRP_OBSERVER) {
       c.d_obs -= 1.01f * hf;
       if (c.d_obs <= 0.f) {
         c.crossed = segment_enters(x_old, c.x, p.obs_c, p.obs_r);
@@ -1300,14 +1310,14 @@ struct PolicyMixedT {
       }
     }
     // continuous losses
-    if (p.flags & (CRP_PAIR | CRP_ADIABATIC)) {
+    if (mflags<FIX>(p) & (CRP_PAIR | CRP_ADIABATIC)) {
       float beta = 0.f;
-      if (p.flags & CRP_PAIR) {
+      if (mflags<FIX>(p) & CRP_PAIR) {
         const float g = c.E_f / ((float)c.A * (float)MP_C2_EV);
         const float bp = table_f32(p, p.t_beta_f, __logf(g));
         beta = bp * (float)(c.Z * c.Z) / (float)c.A;
       }
-      if (p.flags & CRP_ADIABATIC) beta += p.beta_ad_f;
+      if (mflags<FIX>(p) & CRP_ADIABATIC) beta += p.beta_ad_f;
       // (1 - yl)(1 - x) = 1 - (yl + x - x yl): yl stays small, so its binary32
       // rounding is tiny against the energy; folded into binary64 every 32
       // steps (with the rebase), at events and when the lane is stored
@@ -1317,8 +1327,8 @@ struct PolicyMixedT {
     }
     if (c.since_rebase == 0) fold_energy(c);
     // stochastic interactions (a free path can end only in a "near" step)
-    const bool pion_on = (p.flags & CRP_PION) != 0;
-    const bool pd_on = second_on(p, c);
+    const bool pion_on = (mflags<FIX>(p) & CRP_PION) != 0;
+    const bool pd_on = second_on<FIX>(p, c);
     if (pion_on) c.d_pion = c.cap == CAP_PION ? 0.0 : c.d_pion - h;
     if (pd_on) c.d_pd = c.cap == CAP_PD ? 0.0 : c.d_pd - h;
     c.near_f = __fsub_rd(c.near_f, hf);
@@ -1332,14 +1342,14 @@ struct PolicyMixedT {
   __device__ __forceinline__ static void breaks(const KParams& p, Lane& c, LaneCounters& lc) {
     // E_f is within 1e-6 of the energy, so the binary64 test runs only near E_min;
     // s reaches s_max only in a "near" step
-    if ((p.flags & CRP_EMIN) && c.E_f < p.e_min_guard_f && c.E * (1.0 - (double)c.yl) < p.e_min) {
+    if ((mflags<FIX>(p) & CRP_EMIN) && c.E_f < p.e_min_guard_f && c.E * (1.0 - (double)c.yl) < p.e_min) {
       c.status = CRP_BELOW_EMIN;
     } else if (c.near && c.s >= c.s_max) {
       c.status = CRP_MAX_LENGTH;
     } else if (c.crossed) {
       c.status = CRP_DETECTED;
       lc.detected += 1;
-    } else if (p.flags & CRP_BORDER) {
+    } else if (mflags<FIX>(p) & CRP_BORDER) {
       c.d_bord -= 1.01f * c.hf;
       if (c.d_bord <= 0.f) {
         const double dx = c.x[0] - p.border_c[0], dy = c.x[1] - p.border_c[1],
@@ -1372,6 +1382,9 @@ struct PolicyMixedT {
 using PolicyMixed = PolicyMixedT<false>;
 using PolicyMixedGal = PolicyMixedT<true>;         // analytic disk + halo
 using PolicyMixedGmf = PolicyMixedT<true, true>;   // plus the multi-arm field
+// the extragalactic module list (kEgalModules) fixed at compile time: the
+// other modules' code and registers drop out
+using PolicyMixedEgal = PolicyMixedT<false, false, kEgalModules>;
 
 // ---------------------------------------------------------------------------
 // Persistent driver: lanes take candidates from the round's work queue, run
@@ -1412,7 +1425,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
         if (mine < n_in) {
           const uint32_t slot = p.queue_in[mine];
           if (st.status[slot] == CRP_ACTIVE) {
-            if ((p.flags & (CRP_PION | CRP_PHOTODIS | CRP_DECAY)) &&
+            if ((mflags<Policy::kFix>(p) & (CRP_PION | CRP_PHOTODIS | CRP_DECAY)) &&
                 !(st.flags[slot] & CF_STATES_DRAWN))
               slot_event(p, st, dc, slot, EV_DRAW);  // first free paths of this candidate
             Policy::load(p, st, slot, c);
