@@ -211,11 +211,12 @@ def flops_per_trial_mixed():
 
 # field bytes one Cash-Karp trial needs: 6 trilinear gathers x 8 corners x 3 binary32
 GATHER_BYTES_PER_TRIAL_F32 = 6 * 8 * 3 * 4
-# DRAM bytes (read + write) per Cash-Karp trial of the mixed propagate kernel, from
-# one ncu capture of the current kernel (2e5 candidates of this workload:
-# 154.981 GB read + 0.157 GB written over 1.5611e9 trials); traffic grows with the
-# number of trials, so a launch's traffic is this figure times its trials
-DRAM_BYTES_PER_TRIAL_MIXED = (154.981e9 + 0.157e9) / 1.5611e9
+# DRAM bytes (read + write) per Cash-Karp trial of the mixed propagate kernel this
+# workload runs (its module list fixed at compile time), from one ncu capture (2e5
+# candidates of this workload: 154.627 GB read + 0.157 GB written over 1.5611e9
+# trials); traffic grows with the number of trials, so a launch's traffic is this
+# figure times its trials
+DRAM_BYTES_PER_TRIAL_MIXED = (154.627e9 + 0.157e9) / 1.5611e9
 
 
 def run_ours(args):

@@ -24,7 +24,7 @@ UNITS = {
     "propagate_fp64.cu": ["-fmad=false"],
     "propagate_mixed.cu": [],
     "propagate_gmf.cu": [],
-    "propagate_egal.cu": [],
+    "propagate_fixed.cu": [],
     "propagate_1d.cu": ["-fmad=false"],
     "hist_noalloc.cu": [],
     "lens.cu": [],

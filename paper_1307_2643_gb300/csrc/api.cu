@@ -1249,11 +1249,7 @@ crp_status crp_propagate(crp_context* c, const crp_grid* g, const crp_modules* m
   if (!bps) {
     cudaError_t e = m->precision == CRP_FP64
                         ? occupancy_propagate_fp64(kp.f.dtype, block, &bps)
-                        : occupancy_propagate_mixed(kp.f.dtype,
-                                                (m->flags & CRP_GMF)        ? 2
-                                                : (m->flags & CRP_GALACTIC) ? 1
-                                                : m->flags == kEgalModules  ? 3
-                                                                            : 0,
+                        : occupancy_propagate_mixed(kp.f.dtype, m->flags,
                                                 variant, block, &bps);
     if (e != cudaSuccess) return fail_cuda(e, "crp_propagate: occupancy query");
     if (bps < 1) bps = 1;

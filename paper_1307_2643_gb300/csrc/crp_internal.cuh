@@ -157,19 +157,24 @@ cudaError_t launch_propagate_fp64(const KParams& kp, const DevState& st, DevCoun
 cudaError_t launch_propagate_mixed(const KParams& kp, const DevState& st, DevCounters* dc,
                                    int grid, int block, int variant, cudaStream_t s);
 cudaError_t occupancy_propagate_fp64(int dtype, int block, int* blocks_per_sm);
-// Module list of the extragalactic propagation (pair production, adiabatic
-// loss, pion production, E_min, observer): with exactly these flags the mixed
-// kernel is taken from an instantiation that fixes them at compile time.
-constexpr uint32_t kEgalModules = CRP_PAIR | CRP_ADIABATIC | CRP_PION | CRP_EMIN | CRP_OBSERVER;
-cudaError_t launch_propagate_mixed_egal(const KParams& kp, const DevState& st, DevCounters* dc,
-                                        int grid, int block, cudaStream_t s);
-cudaError_t occupancy_propagate_mixed_egal(int dtype, int block, int* bps);
+// Module lists the mixed kernel is also instantiated for with the list fixed
+// at compile time (launch variant 256 x 2): extragalactic propagation, the
+// same with photodisintegration, and back-tracking through the analytic
+// disk + halo or the multi-arm galactic field to the border.
+constexpr uint32_t kModsEgal = CRP_PAIR | CRP_ADIABATIC | CRP_PION | CRP_EMIN | CRP_OBSERVER;
+constexpr uint32_t kModsEgalPd = kModsEgal | CRP_PHOTODIS;
+constexpr uint32_t kModsGalBack = CRP_GALACTIC | CRP_BORDER;
+constexpr uint32_t kModsGmfBack = CRP_GMF | CRP_BORDER;
+int fixed_modules_index(uint32_t flags);  // -1: no fixed instantiation
+cudaError_t launch_propagate_mixed_fixed(int index, const KParams& kp, const DevState& st,
+                                         DevCounters* dc, int grid, int block, cudaStream_t s);
+cudaError_t occupancy_propagate_mixed_fixed(int index, int dtype, int block, int* bps);
 cudaError_t launch_propagate_mixed_gmf(const KParams& kp, const DevState& st, DevCounters* dc,
                                        int grid, int block, int variant, cudaStream_t s);
 cudaError_t occupancy_propagate_mixed_gmf(int dtype, int variant, int block, int* bps);
 cudaError_t sample_field_mixed_gmf(const KParams& kp, const double* xyz, int64_t n, double* B,
                                    cudaStream_t s);
-cudaError_t occupancy_propagate_mixed(int dtype, int galactic, int variant, int block,
+cudaError_t occupancy_propagate_mixed(int dtype, uint32_t flags, int variant, int block,
                                       int* blocks_per_sm);
 // Dynamic shared memory of one propagate block (per-thread stage storage).
 size_t propagate_smem_fp64(int block);

@@ -1382,9 +1382,7 @@ struct PolicyMixedT {
 using PolicyMixed = PolicyMixedT<false>;
 using PolicyMixedGal = PolicyMixedT<true>;         // analytic disk + halo
 using PolicyMixedGmf = PolicyMixedT<true, true>;   // plus the multi-arm field
-// the extragalactic module list (kEgalModules) fixed at compile time: the
-// other modules' code and registers drop out
-using PolicyMixedEgal = PolicyMixedT<false, false, kEgalModules>;
+
 
 // ---------------------------------------------------------------------------
 // Persistent driver: lanes take candidates from the round's work queue, run

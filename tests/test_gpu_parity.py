@@ -528,9 +528,10 @@ EGAL_FLAGS = crp.PAIR | crp.ADIABATIC | crp.PION | crp.EMIN | crp.OBSERVER
 def test_mixed_launch_configuration_does_not_change_results(field_f32_small, tables, flags):
     """The mixed path's results do not depend on block size, register
     variant, queue order or slice (slices are multiples of its 32-step
-    rebase period).  With the extragalactic module list the 256 x 2 launch
-    runs the kernel that fixes the list at compile time, the others the
-    generic kernel: both give the same bytes."""
+    rebase period).  Both module lists here (with and without
+    photodisintegration) have kernels that fix the list at compile time: the
+    256 x 2 launch runs those, the other launches the generic kernel, and
+    all give the same bytes."""
     n, dx, B = field_f32_small
     inj = _interaction_inputs(n_mixed=300, n_hot=100, seed=6)
     kw = dict(precision=crp.MIXED, dtype=crp.F32, tables=tables, flags=flags,
