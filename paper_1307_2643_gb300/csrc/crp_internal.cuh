@@ -158,13 +158,10 @@ cudaError_t launch_propagate_mixed(const KParams& kp, const DevState& st, DevCou
                                    int grid, int block, int variant, cudaStream_t s);
 cudaError_t occupancy_propagate_fp64(int dtype, int block, int* blocks_per_sm);
 // Module lists the mixed kernel is also instantiated for with the list fixed
-// at compile time (launch variant 256 x 2): extragalactic propagation, the
-// same with photodisintegration, and back-tracking through the analytic
-// disk + halo or the multi-arm galactic field to the border.
+// at compile time (launch variant 256 x 2): extragalactic propagation with or
+// without photodisintegration.
 constexpr uint32_t kModsEgal = CRP_PAIR | CRP_ADIABATIC | CRP_PION | CRP_EMIN | CRP_OBSERVER;
 constexpr uint32_t kModsEgalPd = kModsEgal | CRP_PHOTODIS;
-constexpr uint32_t kModsGalBack = CRP_GALACTIC | CRP_BORDER;
-constexpr uint32_t kModsGmfBack = CRP_GMF | CRP_BORDER;
 int fixed_modules_index(uint32_t flags);  // -1: no fixed instantiation
 cudaError_t launch_propagate_mixed_fixed(int index, const KParams& kp, const DevState& st,
                                          DevCounters* dc, int grid, int block, cudaStream_t s);

@@ -165,30 +165,3 @@ def test_all_fields_together_fp64_matches_oracle():
         assert np.array_equal(gpu[f], ref[f]), f
     assert st.accepted_steps == int(ref["n_acc"].sum())
 
-
-@pytest.mark.parametrize("model", ["multiarm", "disk_halo"])
-def test_fixed_module_kernels_match_generic(model):
-    """Back-tracking to the border through either analytic field has a
-    mixed kernel with the module list fixed at compile time (the default
-    256 x 2 launch); the 256 x 3 launch runs the generic kernel.  Same bytes."""
-    WL = workloads.GALACTIC_LENS
-    inj = crp.host_injection(_antiprotons(3000, W["seed"] + 13))
-    n3 = (32, 32, 32)
-    dx, lmin, org = workloads.galactic_grid_geometry(32, WL["box"])
-    field = oracle.turbulent_field(n3, dx, lmin, 4.0 * lmin, 1.0, seed=WL["seed"]).astype(np.float32)
-    flags = (crp.GMF if model == "multiarm" else crp.GALACTIC) | crp.BORDER
-    out = []
-    for bps in (2, 3):
-        ctx = crp.crp_context_create(0, 7, 3000 + 16)
-        try:
-            g = crp.crp_grid_create(ctx, crp.grid_desc(n3, dx, origin=org, dtype=crp.F32,
-                                                       data=field, data_dtype=crp.F32))
-            crp.crp_candidates_inject(ctx, crp.candidate_arrays(inj), 3000)
-            crp.crp_propagate(ctx, g, _mods(crp.MIXED, flags=flags, galactic=WL["disk"],
-                                            block_size=256, blocks_per_sm=bps))
-            rec = crp.crp_collect(ctx, crp.COLLECT_ALL)
-            out.append(rec[np.argsort(rec["id"], kind="stable")])
-        finally:
-            crp.crp_context_destroy(ctx)
-    assert np.all(out[0]["status"] == crp.AT_BORDER)
-    assert out[0].tobytes() == out[1].tobytes()
