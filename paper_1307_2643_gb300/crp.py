@@ -500,6 +500,8 @@ def crp_mlp_set_forward_path(mlp, path):
 
 
 def crp_mlp_set_train_graph(mlp, enable=True):
+    """Graph replay of the tensor-core training step (default on); off: every
+    step launched kernel by kernel."""
     _check(lib().crp_mlp_set_train_graph(mlp, 1 if enable else 0))
 
 
@@ -538,6 +540,7 @@ def crp_cosmology_correct(ctx, cosmo: Cosmology, modules: Modules, ids, T, E0, A
 
 
 def crp_redshift_of_distance(cosmo: Cosmology, length_unit_m, D):
+    """Redshifts of comoving distances D (length units of length_unit_m metres)."""
     D = np.ascontiguousarray(D, dtype=np.float64).ravel()
     out = np.zeros_like(D)
     _check(lib().crp_redshift_of_distance(C.byref(cosmo), length_unit_m, len(D), D.ctypes.data,
