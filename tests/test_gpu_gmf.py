@@ -165,3 +165,42 @@ def test_all_fields_together_fp64_matches_oracle():
         assert np.array_equal(gpu[f], ref[f]), f
     assert st.accepted_steps == int(ref["n_acc"].sum())
 
+
+
+def test_invalid_gmf_and_histogram_arguments_are_rejected():
+    """Argument errors come back as CRP_E_INVALID before any kernel runs:
+    CRP_GMF without parameters, arm radii out of order or beyond one spiral
+    turn, a zero transition width, an X field without its geometry; and
+    device-histogram calls with bad bins or ranges."""
+    import torch
+    ctx = crp.crp_context_create(0, 1, 64)
+    try:
+        g = _zero_grid(ctx)
+        inj = crp.host_injection(_antiprotons(8, 1))
+        crp.crp_candidates_inject(ctx, crp.candidate_arrays(inj), 8)
+        m = crp.modules(precision=crp.FP64, flags=crp.GMF | crp.BORDER, border_radius=20.0,
+                        field_unit_T=crp.MICROGAUSS_T, length_unit_m=crp.KPC_M)
+        with pytest.raises(crp.CrpError, match="gmf"):
+            crp.crp_propagate(ctx, g, m)
+        bad = [dict(arm_rx=tuple(reversed(GMF["arm_rx"]))),
+               dict(arm_rx=GMF["arm_rx"][:7] + (GMF["arm_rx"][0] * 10.0,)),
+               dict(w_disk=0.0),
+               dict(x_rc=0.0)]
+        for over in bad:
+            p = dict(GMF)
+            p.update(over)
+            m = crp.modules(precision=crp.FP64, flags=crp.GMF | crp.BORDER, border_radius=20.0,
+                            field_unit_T=crp.MICROGAUSS_T, length_unit_m=crp.KPC_M, gmf=p)
+            with pytest.raises(crp.CrpError) as e:
+                crp.crp_propagate(ctx, g, m)
+            assert e.value.status == crp.E_INVALID, over
+        # nothing ran: the candidates are still active and at Earth
+        rec = crp.crp_collect(ctx, crp.COLLECT_ALL)
+        assert np.all(rec["status"] == crp.ACTIVE) and np.all(rec["s"] == 0.0)
+        h = torch.zeros(8, dtype=torch.int64, device="cuda")
+        for args in ((crp.COLLECT_ALL, 1e18, 1e21, 0), (crp.COLLECT_ALL, 1e21, 1e18, 8),
+                     (crp.COLLECT_ALL, 0.0, 1e18, 8), (99, 1e18, 1e21, 8)):
+            with pytest.raises(crp.CrpError):
+                crp.crp_histogram_energy_device(ctx, *args, h)
+    finally:
+        crp.crp_context_destroy(ctx)
