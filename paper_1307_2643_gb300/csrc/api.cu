@@ -1267,8 +1267,8 @@ crp_status crp_propagate(crp_context* c, const crp_grid* g, const crp_modules* m
   kp.queue_order = m->queue_order;
   const bool sort_on = m->queue_order >= 0;
   const int3 shift3 = make_int3(kp.key_shift[0], kp.key_shift[1], kp.key_shift[2]);
-  // Work queue of round r is the list round r-1 wrote (requeued candidates
-  // and new secondaries), sorted by spatial brick; round 0 lists the pool.
+  // Work queue of refill pass r is the list pass r-1 wrote (requeued candidates
+  // and new secondaries), sorted by spatial brick; pass 0 lists the pool.
   uint32_t* q_in = c->queue[0];
   uint32_t* q_out = c->queue[1];
   auto sort_into_qin = [&](uint64_t n) -> cudaError_t {

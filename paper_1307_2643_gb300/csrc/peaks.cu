@@ -1,5 +1,5 @@
 // Measured arithmetic and L2 peaks of the current GPU: the roofline
-// denominators the propagation kernels are judged against (binary32 and
+// denominators the propagation kernels are measured against (binary32 and
 // binary64 fused multiply-add issue, and L2-resident read bandwidth).
 //
 // Each probe is a plain kernel whose work is known exactly:

@@ -2,7 +2,7 @@
 GPU end to end: antiprotons back-tracked by the library through the analytic
 multi-arm galactic field give (arrival direction, rigidity) -> border
 direction samples; the BF16 network is trained on them by the library's own
-kernels and judged on held-out samples against the plain map without a lens
+kernels and evaluated on held-out samples against the plain map without a lens
 (border direction = arrival direction) and against the back-tracked truth."""
 import numpy as np
 import pytest
