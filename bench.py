@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--graph", action="store_true",
                     help="run each propagation's round loop as one captured CUDA graph")
     ap.add_argument("--workload", choices=("mixed", "galactic", "uneven", "e2e", "cosmology",
-                                           "train"),
+                                           "train", "lens"),
                     default="mixed",
                     help="mixed: the propagation benchmark; galactic: back-tracking, MLP "
                          "surrogate training / inference and lens builds; uneven: 10^7 "
@@ -63,7 +63,8 @@ def parse():
                          "path lengths; e2e: 10^8 candidates through the mixed workload's "
                          "field, then the galactic lens and its surrogate; cosmology: 1D mode "
                          "with cosmology and the a-posteriori 3D correction (sources to "
-                         "4000 Mpc, index -2.2, protons and iron)")
+                         "4000 Mpc, index -2.2, protons and iron); lens: lens application "
+                         "(nside 64, 100 rigidity bins) to --n candidates (default 2^24)")
     ap.add_argument("--galaxy", choices=("disk_halo_random", "multiarm", "multiarm_random"),
                     default="disk_halo_random",
                     help="galactic workload field: the disk + halo + random grid, the analytic "
@@ -997,6 +998,75 @@ def run_train(args):
     print(json.dumps(out))
 
 
+LENS_HBM_BYTES_PER_CANDIDATE = 4 + 4 + 8 + 24 + 8 + 4   # status, Z, E, u, id read; pixel written
+
+
+def run_lens(args):
+    """Lens application alone: a lens of the galactic workload's shape (nside
+    64, 100 rigidity bins, 49152 samples per bin, built by back-tracking
+    through a zero field, so every column holds its own pixel), applied to
+    n candidates of isotropic direction and log-uniform rigidity.  Timed with
+    CUDA events on the launching stream, L2 flushed before every launch."""
+    import torch
+    from paper_1307_2643_gb300 import crp
+    from paper_1307_2643_gb300.build import build
+    build()
+    crp.use_torch_allocator(0)
+    W = workloads.GALACTIC_LENS
+    n = args.n or (1 << 24)
+    nside, nb = W["nside"], W["n_bins"]
+    ctx = crp.crp_context_create(0, 7, max(n, 16))
+    zn = (4, 4, 4)
+    g = crp.crp_grid_create(ctx, crp.grid_desc(zn, 20.0, origin=(-40.0, -40.0, -40.0),
+                                               dtype=crp.F32, data=np.zeros(zn + (3,))))
+    mods = crp.modules(precision=crp.MIXED, flags=crp.BORDER, tol=W["tol"], h_min=W["h_min"],
+                       h_max=W["h_max"], field_unit_T=crp.MICROGAUSS_T, length_unit_m=crp.KPC_M,
+                       border_radius=W["border_r"], max_steps=2_000_000)
+    dirs, E, bins = workloads.lens_samples(nb, args.lens_per_bin, W["r_lo"], W["r_hi"], W["seed"])
+    lens, _ = crp.crp_lens_build(ctx, g, mods, nside, nb, W["r_lo"], W["r_hi"], W["earth"],
+                                 dirs, E, bins)
+    d, R = workloads.backtrack_directions(n, W["r_lo"], W["r_hi"], W["seed"] + 5)
+    inj = crp.host_injection(dict(x=np.zeros(n), y=np.zeros(n), z=np.zeros(n), ux=d[:, 0],
+                                  uy=d[:, 1], uz=d[:, 2], E=R, A=np.ones(n), Z=np.ones(n)))
+    crp.crp_candidates_inject(ctx, crp.candidate_arrays(inj), n)
+    s = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        crp.crp_lens_apply(ctx, lens, crp.COLLECT_ALL, s.cuda_stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
+    ts = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        crp.crp_lens_apply(ctx, lens, crp.COLLECT_ALL, s.cuda_stream)
+        e1.record(s)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    clocks = clk.stop()
+    rec = crp.crp_collect(ctx, crp.COLLECT_ALL)
+    observed = float(np.mean(rec["lens_pixel"] < 12 * nside * nside))
+    probe = crp.crp_measure_peaks(torch.cuda.current_device())
+    crp.crp_lens_destroy(lens)
+    crp.crp_grid_destroy(g)
+    crp.crp_context_destroy(ctx)
+    t = statistics.median(ts)
+    peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
+    hbm = peaks.get("hbm_gbs")
+    ach = n * LENS_HBM_BYTES_PER_CANDIDATE / t / 1e9
+    print(json.dumps({
+        "workload": f"lens_apply_nside{nside}_{nb}bins", "metric": "lens applications/s",
+        "value": n / t, "unit": "candidates/s", "candidates": n, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t * 1e3, "observed_fraction": observed,
+        "lens_samples": len(E), "l2": "256 MB buffer written before every launch",
+        "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                     "frac": ach / hbm if hbm else None,
+                     "bytes_per_candidate": LENS_HBM_BYTES_PER_CANDIDATE,
+                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else None},
+        "fp64_peak_tflops_measured": probe["fp64_tflops"], "clocks": clocks,
+        "gpu_launches": args.steps}))
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
@@ -1011,5 +1081,7 @@ if __name__ == "__main__":
         run_cosmology(a)
     elif a.workload == "train":
         run_train(a)
+    elif a.workload == "lens":
+        run_lens(a)
     else:
         run_ours(a)
