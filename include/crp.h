@@ -386,7 +386,10 @@ crp_status crp_collect(crp_context* ctx, int32_t what, crp_record* out, size_t c
  * observed if u1 * max_b < count_j (max_b: largest column count of the
  * bin), at Earth pixel entries[min(floor(u2 count_j), count_j - 1)];
  * otherwise lens_pixel = CRP_LENS_NOT_OBSERVED.  Neutral candidates get
- * CRP_LENS_NOT_APPLIED.  The result is in crp_record.lens_pixel.
+ * CRP_LENS_NOT_APPLIED.  The result is in crp_record.lens_pixel.  Every
+ * decision (pixel, bin, observed, pick) is that of binary64 arithmetic; the
+ * library takes it in binary32 where an error bound shows the two agree and
+ * in binary64 otherwise.
  * ---------------------------------------------------------------------- */
 #define CRP_LENS_NOT_APPLIED 0xFFFFFFFFu
 #define CRP_LENS_NOT_OBSERVED 0xFFFFFFFEu

@@ -233,6 +233,103 @@ __device__ __forceinline__ int64_t healpix_ring_pixel(int64_t nside, double ux, 
   return npix - 2 * ir * (ir + 1) + ip;
 }
 
+// floor(a) of a binary32 value a within `guard` of the exact value it
+// stands for: true when no integer lies within `guard` of a, so that the
+// exact value has the same floor (false for NaN, infinities and |a| >= 2^23,
+// where a - floor(a) is 0).  32-bit conversion: |a| < 2^23 when true.
+__device__ __forceinline__ bool floor_sure(float a, float guard, int* out) {
+  const float fl = floorf(a);
+  const float f = a - fl;  // exact for |a| < 2^23
+  *out = (int)fl;
+  return f >= guard && f <= 1.f - guard;
+}
+
+// binary32 value of a binary64 x with the significand truncated to 24 bits
+// (relative error below 2^-23), by integer operations on its bits: +-0 below
+// the normal binary32 range, +-infinity above it, NaN for NaN.
+__device__ __forceinline__ float f32_trunc(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) {
+    const bool nan = e == 2047 - 1023 + 127 && (((hi & 0xfffffu) | lo) != 0u);
+    return __uint_as_float(sign | (nan ? 0x7fc00000u : 0x7f800000u));
+  }
+  return __uint_as_float(sign | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+}
+
+// 1 - |z| for 1/2 <= |z| <= 1 (exact in binary64: the integer
+// 2^52 - significand bits, times 2^-53), rounded to binary32 from its two
+// 32-bit halves (relative error below 2^-23).
+__device__ __forceinline__ float one_minus_abs_f32(double z) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(z) & 0x7fffffffffffffffull;
+  if (b >= 0x3ff0000000000000ull) return 0.f;  // |z| = 1
+  const unsigned long long d = (1ull << 52) - (b & 0x000fffffffffffffull);
+  const float v = (float)(unsigned)(d >> 32) * 4294967296.f + (float)(unsigned)d;
+  return v * 1.1102230246251565404e-16f;  // 2^-53
+}
+
+// The same pixel as healpix_ring_pixel of (ux, uy, uz), or of its opposite
+// for NEG, with the floors taken in binary32 and binary64 used only within a
+// guard band of a pixel boundary.  Error of every binary32 floor argument
+// against its exact value, for nside <= 8192: inputs truncated to binary32
+// (2^-23 relative), atan2f (3 ulp), the phase t = phi / (pi/2) (< 1.6e-6 in
+// all), then the products with nside and the ring index (< nside * 2.5e-6 in
+// all; the cap formula's 1 - |z| is formed exactly before rounding).  The
+// guard, nside * 2e-5 (2e-5 for the phase itself), is 8x that; outside it
+// the binary32 floor equals the exact floor and so the binary64 one, inside
+// it the binary64 path decides.  Only 32-bit integer conversions and
+// binary32 arithmetic run outside the guard band.
+template <bool NEG>
+__device__ __forceinline__ int64_t healpix_ring_pixel_guarded(int64_t nside, double ux,
+                                                              double uy, double uz) {
+  const float sg = NEG ? -1.f : 1.f;
+  const float fx = sg * f32_trunc(ux), fy = sg * f32_trunc(uy), fz = sg * f32_trunc(uz);
+  const int ns_i = (int)nside;
+  const float ns = (float)ns_i;
+  const float g = 2e-5f * ns;
+  float phi = atan2f(fy, fx);
+  if (phi < 0.f) phi += 6.28318530717958647692f;
+  const float tt = phi / 1.57079632679489661923f;
+  int itt;
+  bool ok = floor_sure(tt, 2e-5f, &itt);
+  const float za = fabsf(fz);
+  ok = ok && fabsf(za - 2.f / 3.f) > 1e-6f;
+  int64_t pix = 0;
+  if (ok) {
+    if (za <= 2.f / 3.f) {
+      const float t1 = ns * (0.5f + tt);
+      const float t2 = ns * fz * 0.75f;
+      int jp, jm;
+      ok = floor_sure(t1 - t2, g, &jp) & floor_sure(t1 + t2, g, &jm);
+      const int ir = ns_i + 1 + jp - jm;
+      const int kshift = 1 - (ir & 1);
+      int ip = (jp + jm - ns_i + kshift + 1) / 2;
+      ip = ((ip % (4 * ns_i)) + 4 * ns_i) % (4 * ns_i);
+      pix = 2 * nside * (nside - 1) + (int64_t)(ir - 1) * 4 * nside + ip;
+    } else {
+      const float tp = tt - (float)itt;
+      const float tmp = ns * sqrtf(3.f * one_minus_abs_f32(uz));
+      int jp, jm, ip;
+      ok = floor_sure(tp * tmp, g, &jp) & floor_sure((1.f - tp) * tmp, g, &jm);
+      const int ir = jp + jm + 1;
+      ok = ok & floor_sure(tt * (float)ir, g, &ip);
+      if (ok) {
+        ip = ((ip % (4 * ir)) + 4 * ir) % (4 * ir);
+        // the sign of z from its bits: z > +0 exactly when the int64 is > 0
+        const bool north = NEG ? __double_as_longlong(uz) < 0 && (__double_as_longlong(uz) << 1) != 0
+                               : __double_as_longlong(uz) > 0;
+        pix = north ? 2 * (int64_t)ir * (ir - 1) + ip
+                    : 12 * nside * nside - 2 * (int64_t)ir * (ir + 1) + ip;
+      }
+    }
+  }
+  if (ok) return pix;
+  return NEG ? healpix_ring_pixel(nside, -ux, -uy, -uz) : healpix_ring_pixel(nside, ux, uy, uz);
+}
+
 // Spatial key of a grid cell for the work-queue sort: the cell's brick
 // (cell >> shift, 32 bricks per axis) in Morton order, 15 bits.
 __device__ __forceinline__ uint32_t brick_key(int cx, int cy, int cz, const int shift[3]) {

@@ -13,6 +13,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <cmath>
+
 #include <new>
 #include <vector>
 
@@ -56,12 +58,12 @@ __global__ void k_lens_keys(DevState st, uint64_t n, const int32_t* bin, int64_t
                             int64_t npix, uint32_t* key, uint32_t* earth, uint32_t* counts) {
   for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < n;
        k += (uint64_t)gridDim.x * blockDim.x) {
-    earth[k] = (uint32_t)healpix_ring_pixel(nside, st.ux0[k], st.uy0[k], st.uz0[k]);
+    earth[k] = (uint32_t)healpix_ring_pixel_guarded<false>(nside, st.ux0[k], st.uy0[k], st.uz0[k]);
     if (st.status[k] != CRP_AT_BORDER) {
       key[k] = kNoKey;
       continue;
     }
-    const int64_t j = healpix_ring_pixel(nside, st.ux[k], st.uy[k], st.uz[k]);
+    const int64_t j = healpix_ring_pixel_guarded<false>(nside, st.ux[k], st.uy[k], st.uz[k]);
     const uint32_t c = (uint32_t)((int64_t)bin[k] * npix + j);
     key[k] = c;
     atomicAdd(counts + c, 1u);
@@ -159,8 +161,50 @@ __device__ __forceinline__ bool pick(int what, int status) {
   return false;
 }
 
+// Rigidity bin of R = E / Z in binary64: floor((ln R - ln r_lo) * inv_dlg),
+// clamped to [0, n_bins - 1].
+__device__ __forceinline__ int64_t lens_bin_f64(double E, int Z, double lg_lo, double inv_dlg,
+                                                int n_bins) {
+  const double R = E / (double)Z;
+  const double t = (series_log(R) - lg_lo) * inv_dlg;
+  double bf = floor(t);
+  if (!(bf >= 0.0)) bf = 0.0;
+  if (bf > (double)(n_bins - 1)) bf = (double)(n_bins - 1);
+  return (int64_t)bf;
+}
+
+// The same bin from t = ln(R / r_lo) * inv_dlg in binary32, when its error
+// bound leaves no doubt.  Error of t against the exact value: R / r_lo
+// formed in binary32 from E truncated to binary32 (3e-7 relative in all),
+// logf (1 ulp), the product with inv_dlg: below inv_dlg * 1.3e-6 + |t| *
+// 1.2e-7.  Guard: inv_dlg * 1e-5 + |t| * 1e-6 + 1e-6, 7x that.  False when
+// undecided.
+__device__ __forceinline__ bool lens_bin_f32(double E, int Z, float inv_rlo_f, float inv_f,
+                                             int n_bins, int* b) {
+  const float x = (f32_trunc(E) * inv_rlo_f) / (float)Z;
+  const float t = logf(x) * inv_f;
+  const float g = inv_f * 1e-5f + fabsf(t) * 1e-6f + 1e-6f;
+  if (t + g < 0.f) {
+    *b = 0;
+    return true;
+  }
+  if (t - g >= (float)(n_bins - 1)) {
+    *b = n_bins - 1;
+    return true;
+  }
+  return floor_sure(t, g, b);
+}
+
+// Apply the lens (Sect. 4, transformation matrices by rigidity bin): bin b
+// of R = E / Z, column j = pixel of the arrival direction -u; with the two
+// uniforms (u1, u2) of Philox draw 0, tag 3 of the candidate's id it is
+// observed when u1 * max_count_b < count_j, at the Earth pixel
+// entries[min(floor(u2 * count_j), count_j - 1)] of the column.  Each integer
+// decision is first taken in binary32 with a guard from its error bound and
+// in binary64 only inside the guard, so the result is the binary64 one.
 __global__ void k_lens_apply(DevState st, uint64_t n, int what, uint64_t seed, int64_t nside,
                              int64_t npix, int n_bins, double lg_lo, double inv_dlg,
+                             float inv_rlo_f, float inv_f, int use_f32,
                              const uint32_t* col_start, const uint32_t* entries,
                              const uint32_t* max_count) {
   for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < n;
@@ -171,24 +215,40 @@ __global__ void k_lens_apply(DevState st, uint64_t n, int what, uint64_t seed, i
       st.lens_pixel[k] = kNotApplied;
       continue;
     }
-    const double R = st.E[k] / (double)Z;
-    const double t = (series_log(R) - lg_lo) * inv_dlg;
-    double bf = floor(t);
-    if (!(bf >= 0.0)) bf = 0.0;
-    if (bf > (double)(n_bins - 1)) bf = (double)(n_bins - 1);
-    const int64_t b = (int64_t)bf;
-    const int64_t j = healpix_ring_pixel(nside, -st.ux[k], -st.uy[k], -st.uz[k]);
+    const double E = st.E[k];
+    int b32;
+    const int64_t b = use_f32 && lens_bin_f32(E, Z, inv_rlo_f, inv_f, n_bins, &b32)
+                          ? (int64_t)b32
+                          : lens_bin_f64(E, Z, lg_lo, inv_dlg, n_bins);
+    const int64_t j = healpix_ring_pixel_guarded<true>(nside, st.ux[k], st.uy[k], st.uz[k]);
     const int64_t col = b * npix + j;
     const uint32_t start = col_start[col];
-    const int64_t count = (int64_t)(col_start[col + 1] - start);
-    const double mx = (double)max_count[b];
-    const Philox4 w = draw4(seed, 3u, st.id[k], 0u);
-    const double u1 = u01_open(w.v0, w.v1), u2 = u01_open(w.v2, w.v3);
+    const uint32_t count = col_start[col + 1] - start;
     uint32_t out = kNotObserved;
-    if (count > 0 && u1 * mx < (double)count) {
-      int64_t pk = (int64_t)(u2 * (double)count);
-      if (pk > count - 1) pk = count - 1;
-      out = entries[start + pk];
+    if (count > 0) {
+      const uint32_t mxi = max_count[b];
+      const Philox4 w = draw4(seed, 3u, st.id[k], 0u);
+      // u1 lies in [h1, h1 + 2^-24) with h1 its top 24 bits (exact in
+      // binary32): u1 * max_count is known to 2.4e-7 * max_count
+      const float mxf = (float)mxi, cf = (float)count;
+      const float p1 = (float)(w.v1 >> 8) * 5.9604644775390625e-8f * mxf;
+      bool observed;
+      if (fabsf(p1 - cf) > 2e-6f * mxf)
+        observed = p1 < cf;
+      else
+        observed = u01_open(w.v0, w.v1) * (double)mxi < (double)count;
+      if (observed) {
+        int pk32;
+        int64_t pk;
+        const float p2 = (float)(w.v3 >> 8) * 5.9604644775390625e-8f * cf;
+        if (floor_sure(p2, 2e-6f * cf, &pk32)) {
+          pk = pk32;
+        } else {
+          pk = (int64_t)(u01_open(w.v2, w.v3) * (double)count);
+          if (pk > (int64_t)count - 1) pk = (int64_t)count - 1;
+        }
+        out = entries[start + pk];
+      }
     }
     st.lens_pixel[k] = out;
   }
@@ -202,7 +262,7 @@ __global__ void k_hist_healpix(DevState st, uint64_t n, int what, int64_t nside,
     if (!pick(what, st.status[k])) continue;
     uint64_t p;
     if (source == 0)
-      p = (uint64_t)healpix_ring_pixel(nside, -st.ux[k], -st.uy[k], -st.uz[k]);
+      p = (uint64_t)healpix_ring_pixel_guarded<true>(nside, st.ux[k], st.uy[k], st.uz[k]);
     else
       p = st.lens_pixel[k];
     if (p < npix) atomicAdd(bins + p, 1ull);
@@ -313,8 +373,10 @@ __global__ void k_surrogate_keys(const double* dirs, const float* y, const int32
                                  uint32_t* earth, uint32_t* counts) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
-    earth[k] = (uint32_t)healpix_ring_pixel(nside, dirs[3 * k], dirs[3 * k + 1], dirs[3 * k + 2]);
-    const int64_t j = healpix_ring_pixel(nside, y[3 * k], y[3 * k + 1], y[3 * k + 2]);
+    earth[k] = (uint32_t)healpix_ring_pixel_guarded<false>(nside, dirs[3 * k], dirs[3 * k + 1],
+                                                     dirs[3 * k + 2]);
+    const int64_t j =
+        healpix_ring_pixel_guarded<false>(nside, y[3 * k], y[3 * k + 1], y[3 * k + 2]);
     const uint32_t c = (uint32_t)((int64_t)bin[k] * npix + j);
     key[k] = c;
     atomicAdd(counts + c, 1u);
@@ -566,8 +628,12 @@ crp_status crp_lens_apply(crp_context* ctx, const crp_lens* L, int32_t what, voi
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const double lg_lo = series_log(L->r_lo);
   const double inv = (double)L->n_bins / (series_log(L->r_hi) - lg_lo);
+  // binary32 bin decisions need 1 / r_lo and inv_dlg as normal binary32 numbers
+  const float inv_rlo_f = (float)(1.0 / L->r_lo), inv_f = (float)inv;
+  const int use_f32 = std::isnormal(inv_rlo_f) && std::isnormal(inv_f) ? 1 : 0;
   k_lens_apply<<<blocks(n, 256), 256, 0, s>>>(st, n, what, seed, L->nside, L->npix, L->n_bins,
-                                              lg_lo, inv, L->col_start, L->entries, L->max_count);
+                                              lg_lo, inv, inv_rlo_f, inv_f, use_f32,
+                                              L->col_start, L->entries, L->max_count);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (prev >= 0 && prev != device) cudaSetDevice(prev);

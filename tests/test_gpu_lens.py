@@ -138,3 +138,102 @@ def test_lens_apply_matches_oracle(setup):
     npix = 12 * NSIDE * NSIDE
     assert np.array_equal(hist_earth, np.bincount(want[observed], minlength=npix))
     assert np.array_equal(hist_sky, np.bincount(oracle.ang2pix_vec(NSIDE, -u), minlength=npix))
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_1307_2643_gb300.build import build
+    build()
+    oracle.build()
+
+
+def _unit(g, m):
+    u = g.normal(size=(m, 3))
+    return u / np.linalg.norm(u, axis=1, keepdims=True)
+
+
+def _boundary_directions(nside):
+    """Pixel centres, the cap / belt border z = +-2/3, the poles and the
+    azimuths 0, pi/2, pi, 3 pi/2 (where the binary32 decisions fall back)."""
+    out = []
+    if 12 * nside * nside <= 50_000:
+        for p in range(12 * nside * nside):
+            z, ph = oracle.pix2ang(nside, p)
+            s = np.sqrt(1.0 - z * z)
+            out.append([s * np.cos(ph), s * np.sin(ph), z])
+    for z in (2 / 3, -2 / 3, np.nextafter(2 / 3, 1), np.nextafter(2 / 3, 0), 1.0, -1.0, 0.0,
+              1 - 1e-12, -1 + 1e-12, 1e-300, -1e-300):
+        for ph in (0.0, 1e-12, -1e-12, np.pi / 2, np.pi, -np.pi, 1.5 * np.pi, np.nextafter(np.pi, 0)):
+            s = np.sqrt(max(0.0, 1 - z * z))
+            out.append([s * np.cos(ph), s * np.sin(ph), z])
+    return np.array(out)
+
+
+@pytest.mark.parametrize("nside", [1, 4, 64, 1024])
+def test_healpix_pixels_match_oracle(built, nside):
+    """Arrival-direction pixels at several resolutions against the oracle's
+    binary64 HEALPix, on 2^21 random and boundary directions (the histogram
+    of -u over the pool)."""
+    g = np.random.default_rng(nside)
+    b = _boundary_directions(nside)
+    u = np.concatenate([_unit(g, 1 << 21), -b])
+    m = len(u)
+    inj = dict(x=np.zeros(m), y=np.zeros(m), z=np.zeros(m), ux=u[:, 0].copy(), uy=u[:, 1].copy(),
+               uz=u[:, 2].copy(), E=np.full(m, 1e19), A=np.ones(m, np.int32),
+               Z=np.ones(m, np.int32))
+    ctx = crp.crp_context_create(0, 1, m)
+    try:
+        crp.crp_candidates_inject(ctx, crp.candidate_arrays(crp.host_injection(inj)), m)
+        got = crp.crp_histogram_healpix(ctx, crp.COLLECT_ALL, nside, 0)
+    finally:
+        crp.crp_context_destroy(ctx)
+    want = np.bincount(oracle.ang2pix_vec(nside, -u), minlength=12 * nside * nside)
+    assert np.array_equal(got, want)
+
+
+def test_lens_apply_at_scale_matches_oracle(built):
+    """The lens application at the galactic workload's resolution (nside 64,
+    100 rigidity bins) on 2^20 candidates: random directions, protons to
+    iron, rigidities across and beyond the binned range and on the bin edges;
+    every Earth pixel equals the oracle's application of the same lens."""
+    nside, nb = W["nside"], W["n_bins"]
+    npix = 12 * nside * nside
+    dirs, E, bins = workloads.lens_samples(nb, 2 * npix // 8, W["r_lo"], W["r_hi"], W["seed"])
+    g = np.random.default_rng(17)
+    m = 1 << 20
+    u = _unit(g, m)
+    Z = g.choice(np.array([0, 1, 1, 2, 7, 26], np.int32), m)
+    R = np.exp(g.uniform(np.log(W["r_lo"]) - 1.0, np.log(W["r_hi"]) + 1.0, m))
+    edges = np.exp(np.linspace(np.log(W["r_lo"]), np.log(W["r_hi"]), nb + 1))
+    k = 4 * len(edges)
+    R[:k] = np.repeat(edges, 4) * np.tile([1.0, 1 - 1e-15, 1 + 1e-15, 1 + 1e-7], len(edges))
+    Ev = R * np.maximum(Z, 1)
+    A = np.select([Z == 26, Z == 7, Z == 2], [56, 14, 4], 1).astype(np.int32)
+    ids = np.arange(7, 7 + m, dtype=np.uint64)
+    seed = 99
+    ctx = crp.crp_context_create(0, seed, max(m, len(E)) + 16)
+    try:
+        zn = (4, 4, 4)
+        gr = crp.crp_grid_create(ctx, crp.grid_desc(zn, 20.0, origin=(-40.0, -40.0, -40.0),
+                                                    dtype=crp.F32, data=np.zeros(zn + (3,))))
+        mods = crp.modules(precision=crp.MIXED, flags=crp.BORDER, tol=W["tol"], h_min=W["h_min"],
+                           h_max=W["h_max"], field_unit_T=crp.MICROGAUSS_T,
+                           length_unit_m=crp.KPC_M, border_radius=W["border_r"],
+                           max_steps=2_000_000)
+        lens, _ = crp.crp_lens_build(ctx, gr, mods, nside, nb, W["r_lo"], W["r_hi"], W["earth"],
+                                     dirs, E, bins)
+        L = crp.crp_lens_copy_out(lens, nb * npix, nb)
+        crp.crp_candidates_clear(ctx)
+        inj = dict(id=ids, x=np.zeros(m), y=np.zeros(m), z=np.zeros(m), ux=u[:, 0].copy(),
+                   uy=u[:, 1].copy(), uz=u[:, 2].copy(), E=Ev, A=A, Z=Z)
+        crp.crp_candidates_inject(ctx, crp.candidate_arrays(crp.host_injection(inj)), m)
+        crp.crp_lens_apply(ctx, lens, crp.COLLECT_ALL)
+        rec = np.sort(crp.crp_collect(ctx, crp.COLLECT_ALL), order="id")
+        crp.crp_lens_destroy(lens)
+    finally:
+        crp.crp_context_destroy(ctx)
+    want = olens.apply(L, nside, W["r_lo"], W["r_hi"], nb, seed, ids, u, Ev, Z)
+    assert np.array_equal(rec["lens_pixel"], want)
+    seen = want < npix
+    # a quarter of a sample per column on average: most columns are empty
+    assert 0.01 < seen.mean() < 0.9 and np.all(want[Z == 0] == olens.NOT_APPLIED)
