@@ -278,9 +278,9 @@ __device__ __forceinline__ float one_minus_abs_f32(double z) {
 // (2^-23 relative), atan2f (3 ulp), the phase t = phi / (pi/2) (< 1.6e-6 in
 // all), then the products with nside and the ring index (< nside * 2.5e-6 in
 // all; the cap formula's 1 - |z| is formed exactly before rounding).  The
-// guard, nside * 2e-5 (2e-5 for the phase itself), is 8x that; outside it
-// the binary32 floor equals the exact floor and so the binary64 one, inside
-// it the binary64 path decides.  Only 32-bit integer conversions and
+// guard, nside * 1e-5, is 4x that (2e-5 for the phase itself, 12x); outside
+// it the binary32 floor equals the exact floor and so the binary64 one,
+// inside it the binary64 path decides.  Only 32-bit integer conversions and
 // binary32 arithmetic run outside the guard band.
 template <bool NEG>
 __device__ __forceinline__ int64_t healpix_ring_pixel_guarded(int64_t nside, double ux,
@@ -289,7 +289,7 @@ __device__ __forceinline__ int64_t healpix_ring_pixel_guarded(int64_t nside, dou
   const float fx = sg * f32_trunc(ux), fy = sg * f32_trunc(uy), fz = sg * f32_trunc(uz);
   const int ns_i = (int)nside;
   const float ns = (float)ns_i;
-  const float g = 2e-5f * ns;
+  const float g = 1e-5f * ns;
   float phi = atan2f(fy, fx);
   if (phi < 0.f) phi += 6.28318530717958647692f;
   const float tt = phi / 1.57079632679489661923f;
