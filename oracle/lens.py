@@ -23,10 +23,13 @@ observed at Earth.  Readings (the paper gives no construction):
   its id it is observed if u1 * max_count_b < count_j, at Earth pixel
   entries[min(floor(u2 * count_j), count_j - 1)] of the sorted column.
 
-Parity of the lens build is pinned by the zero-field case (straight lines:
-the lens is the identity on pixels) and by exact agreement of its integer
-structure; the absolute physics of the synthetic galactic field is
-"parity unpinned" beyond the propagation pins.
+Pins: the build by the zero-field case (straight lines: the lens is the
+identity on pixels); the application by a hand-made lens whose outcome
+frequencies match the column-normalised matrix (chi-square), with rigidity
+bins by E / Z, clamping and bin edges; the synthetic disk + halo field the
+lens is built through by its own pins (log-spiral field lines, vertical
+profiles, halo parity and divergence).  Its values are those of the
+synthetic model, not of a measured galactic field.
 """
 from __future__ import annotations
 
