@@ -620,9 +620,11 @@ crp_status crp_restore(crp_context* ctx, const void* host_buf, size_t n, void* s
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture on the device.
- *   - Every call shares the one array: the call clears the bins it uses,
- *     the array keeps the last call's counts, and calls that overlap on the
- *     GPU (other streams, other threads) race with each other.
+ *   - Every call shares the one array of its device: the call clears the
+ *     bins it uses and the array keeps the last call's counts.  Calls in one
+ *     process are serialised per device (a lock held from the clearing to
+ *     the end of the copy back), so calls from other threads or streams
+ *     wait rather than race; each process has its own array.
  *   - Results equal crp_histogram_energy's.  Synchronises `stream`. */
 /* Measured roofline denominators of a device (no counterpart in the paper):
  * binary32 and binary64 fused multiply-add throughput (2 flops per FMA;

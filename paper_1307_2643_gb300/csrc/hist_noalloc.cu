@@ -28,6 +28,10 @@ static __device__ __align__(256) unsigned long long g_noalloc_bins[CRP_HIST_NOAL
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 unsigned long long* g_bins_addr[kMaxDevices] = {nullptr};
+// One call at a time per device: a call holds its device's lock from the
+// clearing of the bins to the end of the copy back, so calls from several
+// threads or streams of this process never share the array on the GPU.
+std::mutex g_call_mu[kMaxDevices];
 
 __device__ __forceinline__ bool record_selected(int what, int status) {
   switch (what) {
@@ -94,6 +98,7 @@ extern "C" crp_status crp_histogram_energy_noalloc(crp_context* ctx, int32_t wha
   unsigned long long* bins = nullptr;
   crp_status st = bins_address(device, &bins);
   if (st == CRP_OK) {
+    std::lock_guard<std::mutex> call_lock(g_call_mu[device]);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const double l0 = log(e_lo), inv = (double)nbins / (log(e_hi) - l0);
     cudaError_t e = cudaMemsetAsync(bins, 0, sizeof(unsigned long long) * (size_t)nbins, s);
