@@ -257,6 +257,29 @@ def test_turbulence_spectrum(oracle):
     assert abs(slope - (-11.0 / 3.0)) < 0.15, slope
 
 
+def test_turbulence_correlation_length(oracle):
+    """Correlation length of the generated field against the closed form of
+    Harari, Mollerach & Roulet (JHEP 03 (2002) 045) for a Kolmogorov band
+    [lmin, lmax]: L_c = (lmax/2) (a-1)/a (1 - r^a) / (1 - r^(a-1)), a = 5/3,
+    r = lmin/lmax.  For an isotropic field L_c = pi sum |B(k)|^2/|k| /
+    sum |B(k)|^2 over the modes, so this ties the generator's wavenumber
+    convention (k = 2 pi / wavelength) to an external formula.  A 64^3 box
+    holds few modes near 2 pi / lmax, so the agreement is approximate."""
+    a = 5.0 / 3.0
+    for (N, dx, lmin, lmax, seed) in ((64, 0.25, 0.5, 8.0, 3), (64, 0.25, 0.5, 4.0, 4)):
+        B = oracle.turbulent_field((N, N, N), dx, lmin, lmax, 1.0, seed=seed)
+        Bk = np.stack([np.fft.fftn(B[..., c]) for c in range(3)], axis=-1)
+        f = np.fft.fftfreq(N) * N
+        mz, my, mx = np.meshgrid(f, f, f, indexing="ij")
+        kk = 2 * np.pi / (N * dx) * np.sqrt(mx * mx + my * my + mz * mz)
+        P = np.sum(np.abs(Bk) ** 2, axis=-1)
+        live = kk > 0
+        lc = np.pi * np.sum(P[live] / kk[live]) / np.sum(P[live])
+        r = lmin / lmax
+        want = lmax / 2 * (a - 1) / a * (1 - r ** a) / (1 - r ** (a - 1))
+        assert abs(lc / want - 1.0) < 0.12, (lc, want)
+
+
 def test_turbulence_seed_dependence(oracle):
     a = oracle.turbulent_field((16, 16, 16), 0.25, 0.5, 4.0, 1.0, seed=1)
     b = oracle.turbulent_field((16, 16, 16), 0.25, 0.5, 4.0, 1.0, seed=1)
