@@ -408,6 +408,13 @@ def test_pion_free_paths_are_exponential(oracle):
     assert abs(none - math.exp(-1)) < 4 * sd
     # one uniform per reset, reset at start and after each event
     assert np.all(r["draws"] == 1 + r["n_pion"])
+    # the survival function at other lengths: the same ids draw the same first
+    # free path, so these are points of one empirical distribution
+    for x in (0.1, 0.5, 2.0, 3.0):
+        inj_x = _one(g * oracle.MP_C2_EV, A=1, Z=0, n=n, s_max=x / R)
+        rx = oracle.propagate(P, _uniform_field(), inj_x, tables=T)
+        px = math.exp(-x)
+        assert abs(np.mean(rx["n_pion"] == 0) - px) < 4 * math.sqrt(px * (1 - px) / n), x
 
 
 def test_photodisintegration_branching_and_lineage(oracle):
