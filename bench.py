@@ -411,19 +411,30 @@ def cpu_baseline(inj, grid_host, seconds=15.0):
     cores = len(os.sched_getaffinity(0))
     rng = np.random.default_rng(1)
     order = rng.permutation(len(inj["E"]))
-    steps, done, t_used, chunk = 0, 0, 0.0, 64
-    while t_used < seconds and done < len(order):
-        idx = np.sort(order[done:done + chunk])
-        sub = workloads.subsample(inj, idx)
-        t0 = time.perf_counter()
-        r = oracle.propagate(P, grid_host, sub, tables=T, nthreads=cores)
-        t_used += time.perf_counter() - t0
-        steps += int(r["n_acc"].sum())
-        done += len(idx)
-        chunk = min(4096, chunk * 2)
+
+    def timed(threads, budget, start):
+        steps, done, t_used, chunk = 0, start, 0.0, 64
+        while t_used < budget and done < len(order):
+            idx = np.sort(order[done:done + chunk])
+            sub = workloads.subsample(inj, idx)
+            t0 = time.perf_counter()
+            r = oracle.propagate(P, grid_host, sub, tables=T, nthreads=threads)
+            t_used += time.perf_counter() - t0
+            steps += int(r["n_acc"].sum())
+            done += len(idx)
+            chunk = min(4096 if threads > 1 else 256, chunk * 2)
+        return steps, done - start, t_used
+
+    # all host cores for two thirds of the budget, then one thread on the
+    # following ids for the rest
+    steps, done, t_used = timed(cores, seconds * 2.0 / 3.0, 0)
+    s1, d1, t1 = timed(1, seconds / 3.0, done)
     return {"value": steps / t_used, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{done} candidates drawn by id from the same 10^6-candidate batch, "
-                      f"{steps} accepted steps in {t_used:.1f} s"}
+                      f"{steps} accepted steps in {t_used:.1f} s",
+            "single_thread": {"value": s1 / t1 if t1 > 0 else None, "unit": UNIT, "cores": 1,
+                              "sample": f"the next {d1} candidates of the same draw, "
+                                        f"{s1} accepted steps in {t1:.1f} s"}}
 
 
 def run_reference(args):
