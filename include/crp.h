@@ -553,6 +553,20 @@ crp_status crp_cosmology_correct(crp_context* ctx, const crp_cosmology* cosmo,
                                  const int32_t* Z0, double* E_out, int32_t* A_out,
                                  int32_t* Z_out, int32_t* n_products);
 
+/* The pick step of crp_cosmology_correct alone, from given source redshifts
+ * (Sect. 4, "Cosmology in 3D"): particle i is re-propagated in 1D from
+ * redshift z_src[i] (host array, finite and >= 0, else CRP_E_INVALID) with
+ * energy E0[i] and species (A0[i], Z0[i]), and replaced by one of its
+ * products that reach z = 0 exactly as crp_cosmology_correct describes.
+ * crp_cosmology_correct is crp_redshift_of_distance followed by this call.
+ * Host arrays, caller-owned; uses a private pool of n (max A0 + 1)
+ * candidates on the context's device and seed. */
+crp_status crp_cosmology_pick(crp_context* ctx, const crp_cosmology* cosmo,
+                              const crp_modules* m, int64_t n, const uint64_t* id,
+                              const double* z_src, const double* E0, const int32_t* A0,
+                              const int32_t* Z0, double* E_out, int32_t* A_out,
+                              int32_t* Z_out, int32_t* n_products);
+
 /* Redshift at comoving distance D[i] (length units of m) for the cosmology
  * (Gauss-Legendre quadrature of 1 / H; Newton iterations on D(z), kept
  * inside a bracket by bisection). */
@@ -607,25 +621,6 @@ crp_status crp_checkpoint(crp_context* ctx, void* host_buf, size_t capacity, siz
                           void* stream);
 crp_status crp_restore(crp_context* ctx, const void* host_buf, size_t n, void* stream);
 
-/* The same histogram without allocating anything.  This entry point has no
- * counterpart in the paper: it is for callers that cannot allocate device
- * memory while they run -- their device memory is handed out entirely by
- * another allocator, an allocation failure part way through is not
- * acceptable to them, or they must avoid the device-wide synchronisation
- * that freeing memory can cause.  It calls no cudaMalloc, cudaFree or other
- * allocating routine: the bins are one fixed device array of
- * CRP_HIST_NOALLOC_MAX_BINS 64-bit counters (32 KiB), present on every GPU
- * that loads the library until the process exits.
- *   - nbins above CRP_HIST_NOALLOC_MAX_BINS is rejected with CRP_E_INVALID.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture on the device.
- *   - Every call shares the one array of its device: the call clears the
- *     bins it uses and the array keeps the last call's counts.  Calls in one
- *     process are serialised per device (a lock held from the clearing to
- *     the end of the copy back), so calls from other threads or streams
- *     wait rather than race; each process has its own array.
- *   - Results equal crp_histogram_energy's.  Synchronises `stream`. */
 /* Measured roofline denominators of a device (no counterpart in the paper):
  * binary32 and binary64 fused multiply-add throughput (2 flops per FMA;
  * each thread runs 8 independent chains over a grid of 8 blocks of 256 per
@@ -642,6 +637,25 @@ typedef struct crp_peaks {
 } crp_peaks;
 crp_status crp_measure_peaks(int32_t device, crp_peaks* out);
 
+/* The energy histogram of crp_histogram_energy, counted without allocating
+ * anything.  This entry point has no counterpart in the paper: it is for
+ * callers that cannot allocate device memory while they run -- their device
+ * memory is handed out entirely by another allocator, an allocation failure part way through is not
+ * acceptable to them, or they must avoid the device-wide synchronisation
+ * that freeing memory can cause.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine: the bins are one fixed device array of
+ * CRP_HIST_NOALLOC_MAX_BINS 64-bit counters (32 KiB), present on every GPU
+ * that loads the library until the process exits.
+ *   - nbins above CRP_HIST_NOALLOC_MAX_BINS is rejected with CRP_E_INVALID.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture on the device.
+ *   - Every call shares the one array of its device: the call clears the
+ *     bins it uses and the array keeps the last call's counts.  Calls in one
+ *     process are serialised per device (a lock held from the clearing to
+ *     the end of the copy back), so calls from other threads or streams
+ *     wait rather than race; each process has its own array.
+ *   - Results equal crp_histogram_energy's.  Synchronises `stream`. */
 #define CRP_HIST_NOALLOC_MAX_BINS 4096
 crp_status crp_histogram_energy_noalloc(crp_context* ctx, int32_t what, double e_lo, double e_hi,
                                         int32_t nbins, uint64_t* out, void* stream);

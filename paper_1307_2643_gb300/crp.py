@@ -169,7 +169,7 @@ SYMBOLS = (
     "crp_mlp_get_params", "crp_mlp_forward", "crp_mlp_train_step", "crp_lens_build_surrogate",
     "crp_mlp_set_train_graph",
     "crp_checkpoint", "crp_restore", "crp_measure_peaks", "crp_autotune", "crp_grid_sample",
-    "crp_mlp_set_forward_path", "crp_propagate_1d", "crp_cosmology_correct",
+    "crp_mlp_set_forward_path", "crp_propagate_1d", "crp_cosmology_correct", "crp_cosmology_pick",
     "crp_redshift_of_distance",
 )
 
@@ -234,6 +234,8 @@ def lib():
                                            C.POINTER(Stats)]
             L.crp_cosmology_correct.argtypes = [p, C.POINTER(Cosmology), C.POINTER(Modules),
                                                 C.c_int64] + [p] * 9
+            L.crp_cosmology_pick.argtypes = [p, C.POINTER(Cosmology), C.POINTER(Modules),
+                                             C.c_int64] + [p] * 9
             L.crp_redshift_of_distance.argtypes = [C.POINTER(Cosmology), C.c_double, C.c_int64,
                                                    p, p]
             L.crp_autotune.argtypes = [p, p, C.POINTER(Modules), u64, C.POINTER(TuneResult), p]
@@ -522,21 +524,30 @@ def crp_propagate_1d(ctx, cosmo: Cosmology, modules: Modules, stream=None,
     return status, s
 
 
-def crp_cosmology_correct(ctx, cosmo: Cosmology, modules: Modules, ids, T, E0, A0, Z0):
-    """(E, A, Z, n_products) of the a-posteriori correction (host arrays)."""
+def _correction(fn, ctx, cosmo, modules, ids, src, E0, A0, Z0):
     ids = np.ascontiguousarray(ids, dtype=np.uint64)
-    T = np.ascontiguousarray(T, dtype=np.float64)
+    src = np.ascontiguousarray(src, dtype=np.float64)
     E0 = np.ascontiguousarray(E0, dtype=np.float64)
     A0 = np.ascontiguousarray(A0, dtype=np.int32)
     Z0 = np.ascontiguousarray(Z0, dtype=np.int32)
     n = len(E0)
     E, A, Z, nk = (np.zeros(n), np.zeros(n, np.int32), np.zeros(n, np.int32),
                    np.zeros(n, np.int32))
-    _check(lib().crp_cosmology_correct(ctx, C.byref(cosmo), C.byref(modules), n, ids.ctypes.data,
-                                       T.ctypes.data, E0.ctypes.data, A0.ctypes.data,
-                                       Z0.ctypes.data, E.ctypes.data, A.ctypes.data,
-                                       Z.ctypes.data, nk.ctypes.data))
+    _check(fn(ctx, C.byref(cosmo), C.byref(modules), n, ids.ctypes.data, src.ctypes.data,
+              E0.ctypes.data, A0.ctypes.data, Z0.ctypes.data, E.ctypes.data, A.ctypes.data,
+              Z.ctypes.data, nk.ctypes.data))
     return E, A, Z, nk
+
+
+def crp_cosmology_correct(ctx, cosmo: Cosmology, modules: Modules, ids, T, E0, A0, Z0):
+    """(E, A, Z, n_products) of the a-posteriori correction (host arrays)."""
+    return _correction(lib().crp_cosmology_correct, ctx, cosmo, modules, ids, T, E0, A0, Z0)
+
+
+def crp_cosmology_pick(ctx, cosmo: Cosmology, modules: Modules, ids, z_src, E0, A0, Z0):
+    """(E, A, Z, n_products) of the correction's pick from given source
+    redshifts (host arrays)."""
+    return _correction(lib().crp_cosmology_pick, ctx, cosmo, modules, ids, z_src, E0, A0, Z0)
 
 
 def crp_redshift_of_distance(cosmo: Cosmology, length_unit_m, D):

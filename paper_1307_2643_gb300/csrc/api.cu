@@ -1991,20 +1991,27 @@ crp_status crp_propagate_1d(crp_context* c, const crp_cosmology* cosmo, const cr
   return st;
 }
 
-crp_status crp_cosmology_correct(crp_context* ctx, const crp_cosmology* cosmo,
-                                 const crp_modules* m, int64_t n, const uint64_t* id,
-                                 const double* T, const double* E0, const int32_t* A0,
-                                 const int32_t* Z0, double* E_out, int32_t* A_out,
-                                 int32_t* Z_out, int32_t* n_products) {
+crp_status crp_cosmology_pick(crp_context* ctx, const crp_cosmology* cosmo,
+                              const crp_modules* m, int64_t n, const uint64_t* id,
+                              const double* z_src, const double* E0, const int32_t* A0,
+                              const int32_t* Z0, double* E_out, int32_t* A_out,
+                              int32_t* Z_out, int32_t* n_products) {
   if (!ctx || !m || n < 0 ||
-      (n && (!id || !T || !E0 || !A0 || !Z0 || !E_out || !A_out || !Z_out || !n_products))) {
-    set_error("crp_cosmology_correct: bad argument");
+      (n && (!id || !z_src || !E0 || !A0 || !Z0 || !E_out || !A_out || !Z_out ||
+             !n_products))) {
+    set_error("crp_cosmology_pick: bad argument");
     return CRP_E_INVALID;
   }
   if (n == 0) return CRP_OK;
-  std::vector<double> z(n);
-  crp_status st = crp_redshift_of_distance(cosmo, m->length_unit_m, n, T, z.data());
-  if (st != CRP_OK) return st;
+  for (int64_t i = 0; i < n; ++i) {
+    if (!(z_src[i] >= 0.0) || !std::isfinite(z_src[i])) {
+      set_error("crp_cosmology_pick: source redshift %lld is %g (must be finite and >= 0)",
+                (long long)i, z_src[i]);
+      return CRP_E_INVALID;
+    }
+  }
+  std::vector<double> z(z_src, z_src + n);
+  crp_status st = CRP_OK;
   int32_t amax = 1;
   for (int64_t i = 0; i < n; ++i) amax = A0[i] > amax ? A0[i] : amax;
   crp_context* c = nullptr;
@@ -2078,6 +2085,24 @@ crp_status crp_cosmology_correct(crp_context* ctx, const crp_cosmology* cosmo,
     Z_out[i] = pick.Z;
   }
   return CRP_OK;
+}
+
+crp_status crp_cosmology_correct(crp_context* ctx, const crp_cosmology* cosmo,
+                                 const crp_modules* m, int64_t n, const uint64_t* id,
+                                 const double* T, const double* E0, const int32_t* A0,
+                                 const int32_t* Z0, double* E_out, int32_t* A_out,
+                                 int32_t* Z_out, int32_t* n_products) {
+  if (!ctx || !m || n < 0 ||
+      (n && (!id || !T || !E0 || !A0 || !Z0 || !E_out || !A_out || !Z_out || !n_products))) {
+    set_error("crp_cosmology_correct: bad argument");
+    return CRP_E_INVALID;
+  }
+  if (n == 0) return CRP_OK;
+  std::vector<double> z(n);
+  crp_status st = crp_redshift_of_distance(cosmo, m->length_unit_m, n, T, z.data());
+  if (st != CRP_OK) return st;
+  return crp_cosmology_pick(ctx, cosmo, m, n, id, z.data(), E0, A0, Z0, E_out, A_out, Z_out,
+                            n_products);
 }
 
 }  // extern "C"

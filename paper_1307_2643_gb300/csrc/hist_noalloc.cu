@@ -94,7 +94,12 @@ extern "C" crp_status crp_histogram_energy_noalloc(crp_context* ctx, int32_t wha
   context_view(ctx, &status, &E, &n, &device);
   int prev = -1;
   cudaGetDevice(&prev);
-  if (prev != device) cudaSetDevice(device);
+  if (prev != device) {
+    // the symbol address below is per device: resolve it only with the
+    // context's device current, never on whatever device a failed switch left
+    const cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return fail_cuda(e, "crp_histogram_energy_noalloc: cudaSetDevice");
+  }
   unsigned long long* bins = nullptr;
   crp_status st = bins_address(device, &bins);
   if (st == CRP_OK) {

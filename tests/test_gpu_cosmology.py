@@ -80,31 +80,76 @@ def test_redshift_of_distance_matches_oracle():
     assert np.max(np.abs(got / ref - 1)) < 1e-12
 
 
-def test_correction_matches_oracle_pick(tables):
-    n = 2000
+def _correction_inputs(n=2000):
     g = np.random.default_rng(9)
     ids = np.arange(n, dtype=np.uint64) + 100
     T = g.uniform(5.0, 800.0, n)
     A0 = np.where(g.random(n) < 0.5, 56, 1).astype(np.int32)
     Z0 = np.where(A0 == 56, 26, 1).astype(np.int32)
     E0 = 10 ** g.uniform(18.0, 21.0, n) * np.where(A0 == 56, 10.0, 1.0)
+    return ids, T, E0, A0, Z0
+
+
+def _library_correction(tables, fn, *args):
     ctx = crp.crp_context_create(0, 21, 16)
     try:
         th = crp.crp_tables_from_host(ctx, crp.tables_desc(n=tables.n), tables.beta_pair,
                                       tables.rate_pion, tables.rate_gdr)
         m = crp.modules(flags=FLAGS, e_min=E_MIN, tables=th)
-        E, A, Z, nk = crp.crp_cosmology_correct(ctx, crp.cosmology(), m, ids, T, E0, A0, Z0)
+        out = fn(ctx, crp.cosmology(), m, *args)
         crp.crp_tables_destroy(th)
     finally:
         crp.crp_context_destroy(ctx)
+    return out
+
+
+def test_correction_pick_matches_oracle_bit_for_bit(tables):
+    """The correction's pick from one source-redshift array (the oracle's
+    redshifts of the trajectory lengths) on both sides: every 1D history is
+    bit-exact, so the product counts, the picked species and the picked
+    energies are equal bit for bit."""
+    ids, T, E0, A0, Z0 = _correction_inputs()
     P = ocm.make_params1d(tables=tables, flags=OFLAGS, seed=21, e_min=E_MIN)
     z = ocm.redshift_of_distance(P, T)
+    E, A, Z, nk = _library_correction(tables, crp.crp_cosmology_pick, ids, z, E0, A0, Z0)
     Er, Ar, Zr, nr = ocm.cosmology_pick(P, ids, z, E0, A0, Z0, tables=tables)
-    # the source redshifts agree to 1e-12; histories agree except at knife edges
+    assert np.array_equal(nk, nr)
+    assert np.array_equal(A, Ar) and np.array_equal(Z, Zr)
+    assert np.array_equal(E, Er)
+    assert (nr > 1).sum() > 100 and (nr == 0).sum() > 0 and (nr == 1).sum() > 0
+
+
+def test_correction_through_library_redshifts(tables):
+    """crp_cosmology_correct places each source with the library's own
+    redshift of the trajectory length (Newton iterations inside a bracket),
+    the oracle with bisection; the two redshifts agree to 1e-12, and the
+    correction equals the library's pick from its own redshifts exactly.
+    Against the oracle's pick from the oracle's redshifts only histories at
+    a knife edge (an event decided by the last 1e-12 of the source
+    distance) may branch."""
+    ids, T, E0, A0, Z0 = _correction_inputs()
+    zl = crp.crp_redshift_of_distance(crp.cosmology(), crp.MPC_M, T)
+    P = ocm.make_params1d(tables=tables, flags=OFLAGS, seed=21, e_min=E_MIN)
+    zo = ocm.redshift_of_distance(P, T)
+    assert np.max(np.abs(zl / zo - 1)) < 1e-12
+    E, A, Z, nk = _library_correction(tables, crp.crp_cosmology_correct, ids, T, E0, A0, Z0)
+    El, Al, Zl, nl = _library_correction(tables, crp.crp_cosmology_pick, ids, zl, E0, A0, Z0)
+    for a, b in ((E, El), (A, Al), (Z, Zl), (nk, nl)):
+        assert np.array_equal(a, b)
+    Er, Ar, Zr, nr = ocm.cosmology_pick(P, ids, zo, E0, A0, Z0, tables=tables)
     same = (nk == nr) & (A == Ar) & (Z == Zr)
     assert same.mean() > 0.995
     assert np.max(rel_err(E[same & (nk > 0)], Er[same & (nk > 0)], floor=0.0)) < 1e-9
-    assert (nr > 1).sum() > 100 and (nr == 0).sum() > 0
+
+
+def test_correction_pick_rejects_bad_redshifts(tables):
+    ids, T, E0, A0, Z0 = _correction_inputs(8)
+    for bad in (-1e-3, np.nan, np.inf):
+        z = np.full(8, 0.1)
+        z[3] = bad
+        with pytest.raises(crp.CrpError) as e:
+            _library_correction(tables, crp.crp_cosmology_pick, ids, z, E0, A0, Z0)
+        assert e.value.status == crp.E_INVALID
 
 
 def _roots(rec):

@@ -105,3 +105,44 @@ def test_fullsize_mixed_spectra_and_arrival_maps(full_run):
     assert ks_2samp(np.log(dmx["E"]), np.log(d64["E"])).pvalue > 0.01
     for comp in (lambda u: -u[:, 2], lambda u: np.arctan2(-u[:, 1], -u[:, 0])):
         assert ks_2samp(comp(dmx["u"]), comp(d64["u"])).pvalue > 0.01
+
+
+def test_plain_1e4_protons_64cube_fp64_bit_exact():
+    """The plain small workload at its stated size: all 10^4 protons (E^-2 on
+    10^19-10^20 eV, isotropic from the origin) through the 64^3 binary64
+    Kolmogorov grid (250 kpc spacing, lmin 0.5, lmax 8 Mpc, B_rms 1 nG),
+    tol 1e-4, h in [10 kpc, 1 Mpc], stopped at 50 Mpc, binary64 on both
+    sides: every record field equals the oracle's bit for bit."""
+    from paper_1307_2643_gb300.build import build
+    build()
+    oracle.build()
+    w = workloads.PLAIN_SMALL
+    field = oracle.turbulent_field(w["grid_n"], w["spacing"], w["lmin"], w["lmax"], w["brms"],
+                                   seed=w["seed"])
+    inj = crp.host_injection(workloads.plain_small())
+    n = len(inj["E"])
+    assert n == 10_000
+    ctx = crp.crp_context_create(0, w["seed"], n + 64)
+    try:
+        g = crp.crp_grid_create(ctx, crp.grid_desc(w["grid_n"], w["spacing"], dtype=crp.F64,
+                                                   data=field))
+        crp.crp_candidates_inject(ctx, crp.candidate_arrays(inj), n)
+        m = crp.modules(precision=crp.FP64, tol=w["tol"], h_min=w["h_min"], h_max=w["h_max"])
+        status, st = crp.crp_propagate(ctx, g, m)
+        assert status == crp.OK
+        rec = np.sort(crp.crp_collect(ctx, crp.COLLECT_ALL), order="id")
+        crp.crp_grid_destroy(g)
+    finally:
+        crp.crp_context_destroy(ctx)
+    P = oracle.make_params(grid_n=w["grid_n"], spacing=w["spacing"], tol=w["tol"],
+                           h_min=w["h_min"], h_max=w["h_max"], seed=w["seed"])
+    ref = oracle.propagate(P, field, inj)
+    assert len(rec) == len(ref) == n
+    for f in EXACT_FIELDS + ("n_acc", "n_rej"):
+        assert np.array_equal(rec[f], ref[f]), f
+    for f in ("x", "u", "E", "s", "x0", "u0", "E0"):
+        assert np.max(rel_err(rec[f], ref[f])) < 1e-9, f
+        assert np.array_equal(rec[f], ref[f]), f   # measured: bit for bit
+    assert np.all(rec["status"] == crp.MAX_LENGTH)
+    assert st.accepted_steps == int(ref["n_acc"].sum())
+    assert st.rejected_trials == int(ref["n_rej"].sum())

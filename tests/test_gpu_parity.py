@@ -383,30 +383,60 @@ def _pos_err(a, b):
     return np.linalg.norm(a["x"] - b["x"], axis=1) / np.maximum(1.0, np.linalg.norm(b["x"], axis=1))
 
 
+FLOOR_AXES = ((0.267, 0.535, 0.802), (0.9, -0.3, 0.1), (-0.2, 0.7, -0.6))
+FLOOR_GATE = 2e-6
+
+
+def _kicked(inj, delta, axis):
+    """Injection with each direction turned by delta[i] radians (to first
+    order) about an axis perpendicular to it and to `axis`."""
+    p = dict(inj)
+    u = np.stack([p["ux"], p["uy"], p["uz"]], 1)
+    v = np.cross(u, np.asarray(axis, dtype=np.float64))
+    v /= np.linalg.norm(v, axis=1)[:, None]
+    u2 = u + delta[:, None] * v
+    u2 /= np.linalg.norm(u2, axis=1)[:, None]
+    p["ux"], p["uy"], p["uz"] = [np.ascontiguousarray(u2[:, k]) for k in range(3)]
+    return p
+
+
 @pytest.fixture(scope="module")
 def ballistic_refs(field64):
     """Oracle at the operating tolerance, at a resolving tolerance, and a
-    tol = 1e-10 reference ("truth") for 1e19-1e20 eV protons over 50 Mpc."""
+    tol = 1e-10 reference ("truth") for 1e19-1e20 eV protons over 50 Mpc;
+    and, per tolerance, each candidate's chaos floor: the largest endpoint
+    change of the oracle's own history when the initial direction is turned
+    by 2^-24 sqrt(N) radians (N: the candidate's accepted steps), about
+    three different axes.  2^-24 is the binary32 unit roundoff and sqrt(N)
+    the random-walk growth of one rounding per step, so the floor is the
+    endpoint spread the method itself shows under binary32-sized
+    perturbations."""
     n, dx, B = field64
     B32 = B.astype(np.float32).astype(np.float64)
     inj = _plain(3001)
-    refs = {}
+    refs, floors = {}, {}
     for tol, hmin in ((1e-4, 0.01), (1e-8, 1e-4), (1e-10, 1e-4)):
-        refs[tol] = oracle.propagate(oracle_params(n, dx, tol=tol, h_min=hmin, h_max=1.0), B32, inj)
-    return B32, inj, refs
+        P = oracle_params(n, dx, tol=tol, h_min=hmin, h_max=1.0)
+        refs[tol] = oracle.propagate(P, B32, inj)
+        if tol >= 1e-8:
+            delta = 2.0 ** -24 * np.sqrt(refs[tol]["n_acc"].astype(np.float64))
+            floors[tol] = np.max([_pos_err(oracle.propagate(P, B32, _kicked(inj, delta, a)),
+                                           refs[tol]) for a in FLOOR_AXES], axis=0)
+    return B32, inj, refs, floors
 
 
 @pytest.mark.parametrize("tol,hmin", [(1e-4, 0.01), (1e-8, 1e-4)])
 def test_mixed_equal_error(field64, ballistic_refs, tol, hmin):
     """Mixed precision at equal error: against a tol = 1e-10 reference the
     mixed path's endpoint errors have the same distribution as the FP64
-    method's own discretization errors at the same tolerance.  (Per-candidate
-    agreement with the FP64 path is bounded by that discretization error: the
-    step controller turns any rounding-level difference -- even a 1-ulp
-    change of the initial direction in FP64 -- into a different step
-    sequence.)"""
+    method's own discretization errors at the same tolerance.  Per
+    candidate: wherever the chaos floor (see ballistic_refs) is at most
+    2e-6, the mixed endpoint is within 1e-5 of the FP64 endpoint; where the
+    floor is larger the method itself does not fix the endpoint to 1e-5
+    (the step controller turns a rounding-level difference into another
+    step sequence) and only the distribution is compared."""
     n, dx, _ = field64
-    B32, inj, refs = ballistic_refs
+    B32, inj, refs, floors = ballistic_refs
     gpu, st, status = run_gpu(B32, n, dx, inj, precision=crp.MIXED, dtype=crp.F32, tol=tol,
                               h_min=hmin, h_max=1.0)
     assert status == crp.OK
@@ -417,11 +447,18 @@ def test_mixed_equal_error(field64, ballistic_refs, tol, hmin):
     assert np.median(e_mx) <= 1.5 * np.median(e_64) + 1e-9, (np.median(e_mx), np.median(e_64))
     assert np.percentile(e_mx, 90) <= 2.0 * np.percentile(e_64, 90) + 1e-9
     assert abs(int(gpu["n_acc"].sum()) - int(ref["n_acc"].sum())) < 0.01 * ref["n_acc"].sum()
+    # per candidate, where the chaos floor allows 1e-5
+    e = _pos_err(gpu, ref)
+    gated = floors[tol] <= FLOOR_GATE
+    report = (f"tol {tol}: {gated.sum()} of {len(e)} candidates gated; gated max "
+              f"{e[gated].max() if gated.any() else 0:.3g}; ungated median "
+              f"{np.median(e[~gated]):.3g}, p90 {np.percentile(e[~gated], 90):.3g}, "
+              f"within 1e-5 {np.mean(e[~gated] <= 1e-5):.3f}")
+    print(report)
+    assert np.all(e[gated] <= 1e-5), report
     if tol <= 1e-8:
-        # where the method resolves 1e-5, the mixed path meets it per candidate
-        e = _pos_err(gpu, ref)
-        assert np.median(e) < 5e-6, np.median(e)
-        assert np.mean(e <= 1e-5) >= 0.8, np.mean(e <= 1e-5)
+        # where the method resolves 1e-5 the gate is not vacuous
+        assert gated.sum() >= 0.1 * len(e), report
 
 
 def test_mixed_interactions_statistics(field_f32_small, tables, interaction_ref):
