@@ -158,16 +158,42 @@ def bench_config(w, n, world):
 
 
 SPECTRUM = dict(e_lo=1e18, e_hi=1e21, nbins=60)  # detected-energy histogram, 20 bins/decade
+ARRIVAL_NSIDE = 64                               # HEALPix map of the detected arrival directions
 
 
-def merge_spectrum(dist, hist):
+def merge_histogram(dist, hist):
     """The data exchange of a multi-rank step: each rank propagates its own
-    candidate shard and histograms what its observer detected; the job's
-    spectrum is the sum over ranks (all-reduce, in place, on the histogram's
-    device)."""
+    candidate shard and histograms what its observer detected (spectrum and
+    arrival map); the job's histogram is the sum over ranks (all-reduce, in
+    place, on the histogram's device)."""
     if dist:
         dist.all_reduce(hist)
     return hist
+
+
+merge_spectrum = merge_histogram
+
+
+def gather_records(dist, rec):
+    """The detected records of every rank, on every rank, sorted by id: the
+    one gather of the multi-rank data plane (host buffers over the CPU
+    group).  Candidate ids are disjoint across ranks."""
+    if not dist:
+        return np.sort(rec, order="id")
+    import torch
+    world = dist.get_world_size()
+    n = torch.tensor([len(rec)], dtype=torch.int64)
+    counts = [torch.zeros_like(n) for _ in range(world)]
+    dist.all_gather(counts, n)
+    counts = [int(c[0]) for c in counts]
+    item = rec.dtype.itemsize
+    buf = torch.zeros(max(counts) * item, dtype=torch.uint8)
+    if len(rec):
+        buf[:len(rec) * item] = torch.from_numpy(np.ascontiguousarray(rec).view(np.uint8).copy())
+    bufs = [torch.zeros_like(buf) for _ in range(world)]
+    dist.all_gather(bufs, buf)
+    parts = [b.numpy()[:c * item].view(rec.dtype) for b, c in zip(bufs, counts)]
+    return np.sort(np.concatenate(parts), order="id")
 
 
 def aggregate_ranks(dist, elapsed, steps):
@@ -329,6 +355,7 @@ def run_ours(args):
     arr_host = crp.candidate_arrays(pinned, on_device=False)
 
     hist = torch.zeros(SPECTRUM["nbins"], dtype=torch.int64, device="cuda")
+    amap = torch.zeros(12 * ARRIVAL_NSIDE ** 2, dtype=torch.int64, device="cuda")
 
     def one_step(arrays):
         crp.crp_candidates_clear(ctx)
@@ -336,7 +363,10 @@ def run_ours(args):
         _, st = crp.crp_propagate(ctx, grid, mods, sh)
         crp.crp_histogram_energy_device(ctx, crp.COLLECT_DETECTED, SPECTRUM["e_lo"],
                                         SPECTRUM["e_hi"], SPECTRUM["nbins"], hist, stream=sh)
-        merge_spectrum(dist, hist)
+        crp.crp_histogram_healpix_device(ctx, crp.COLLECT_DETECTED, ARRIVAL_NSIDE, 0, amap,
+                                         stream=sh)
+        merge_histogram(dist, hist)
+        merge_histogram(dist, amap)
         return st
 
     for _ in range(args.warmup):
@@ -363,8 +393,10 @@ def run_ours(args):
     launches = sum(s.launches for s in stats)
     elapsed, acc_all = aggregate_ranks(dist, elapsed, acc)
     value = acc_all / elapsed
-    # the last timed step's records (outside the timed region)
+    # the last timed step's records (outside the timed region), and the job's
+    # detected records gathered from every rank
     rec_main = np.sort(crp.crp_collect(ctx, crp.COLLECT_ALL), order="id")
+    detected = gather_records(dist, rec_main[rec_main["status"] == crp.DETECTED])
 
     # ---- end to end through the public API with host buffers ---------------
     e2e = None
@@ -488,13 +520,21 @@ def run_ours(args):
             "rejected_trials_per_s": rej / elapsed,
             "kernel_ms_per_step": kern_ms / args.steps,
             # per step: inject (1), queue build (2), queue sort (3), detected-
-            # energy histogram (1); per round: host loop = reset + propagate
-            # (+ sort of requeued work), graph = 5
-            "gpu_launches": int(args.steps * 7 + launches * (5 if args.graph else 2)),
+            # energy histogram (1), arrival map (1); per round: host loop =
+            # reset + propagate (+ sort of requeued work), graph = 5
+            "gpu_launches": int(args.steps * 8 + launches * (5 if args.graph else 2)),
             "spectrum": {"bins": SPECTRUM["nbins"], "e_lo_eV": SPECTRUM["e_lo"],
                          "e_hi_eV": SPECTRUM["e_hi"], "detected_last_step": int(hist.sum()),
                          "exchange": "sum over ranks on the device (NCCL all-reduce)"
                                      if world > 1 else "single rank: none"},
+            "arrival_map": {"nside": ARRIVAL_NSIDE, "detected_last_step": int(amap.sum()),
+                            "exchange": "sum over ranks on the device (NCCL all-reduce)"
+                                        if world > 1 else "single rank: none"},
+            "detected_records": {"gathered": int(len(detected)),
+                                 "unique_ids": bool(len(np.unique(detected["id"]))
+                                                    == len(detected)),
+                                 "exchange": "all-gather of host records (gloo)"
+                                             if world > 1 else "single rank: none"},
             "e2e": e2e, "fp64": fp64, "mixed_vs_fp64": equal_error, "roofline": roof,
             "cpu_baseline": cpu, "clocks": clk, "measured_peaks": probe,
         }

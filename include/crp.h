@@ -481,6 +481,17 @@ crp_status crp_lens_build_surrogate(crp_context* ctx, crp_mlp* mlp, const crp_le
 crp_status crp_histogram_healpix(crp_context* ctx, int32_t what, int32_t nside, int32_t source,
                                  uint64_t* out, void* stream);
 
+/* The same map counted into the caller's device array out_dev (12 nside^2
+ * uint64 on the context's device, 8-byte aligned, else CRP_E_INVALID):
+ * cleared first, or added to when accumulate != 0.  Asynchronous on
+ * `stream`; no allocation, no synchronisation.  The candidates are
+ * independent (Sect. 3), so the map of a job sharded over ranks by
+ * candidate is the sum of the ranks' maps: a collective (sum) over these
+ * arrays merges them on the devices. */
+crp_status crp_histogram_healpix_device(crp_context* ctx, int32_t what, int32_t nside,
+                                        int32_t source, uint64_t* out_dev, int32_t accumulate,
+                                        void* stream);
+
 /* Histogram over the selected records: nbins log-uniform bins of E over
  * [e_lo, e_hi) (under/overflow dropped).  out: host uint64 array of nbins. */
 crp_status crp_histogram_energy(crp_context* ctx, int32_t what, double e_lo, double e_hi,

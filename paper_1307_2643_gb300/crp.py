@@ -164,7 +164,7 @@ SYMBOLS = (
     "crp_propagate", "crp_collect", "crp_histogram_energy", "crp_histogram_energy_noalloc",
     "crp_histogram_energy_device",
     "crp_lens_build", "crp_lens_apply", "crp_lens_copy_out", "crp_lens_destroy",
-    "crp_histogram_healpix",
+    "crp_histogram_healpix", "crp_histogram_healpix_device",
     "crp_mlp_create", "crp_mlp_destroy", "crp_mlp_num_params", "crp_mlp_set_params",
     "crp_mlp_get_params", "crp_mlp_forward", "crp_mlp_train_step", "crp_lens_build_surrogate",
     "crp_mlp_set_train_graph",
@@ -216,6 +216,7 @@ def lib():
             L.crp_lens_copy_out.argtypes = [p, p, p, p, C.POINTER(C.c_int64)]
             L.crp_lens_destroy.argtypes = [p]
             L.crp_histogram_healpix.argtypes = [p, i32, i32, i32, p, p]
+            L.crp_histogram_healpix_device.argtypes = [p, i32, i32, i32, p, i32, p]
             L.crp_mlp_create.argtypes = [p, i32, i32, i32, u64, C.POINTER(p)]
             L.crp_mlp_destroy.argtypes = [p]
             L.crp_mlp_num_params.argtypes = [p]
@@ -595,6 +596,15 @@ def crp_histogram_energy_device(ctx, what, e_lo, e_hi, nbins, out_dev, accumulat
     nbins on the context's device); asynchronous on `stream`."""
     _check(lib().crp_histogram_energy_device(ctx, what, e_lo, e_hi, nbins, _addr(out_dev),
                                              1 if accumulate else 0, stream))
+    return out_dev
+
+
+def crp_histogram_healpix_device(ctx, what, nside, source, out_dev, accumulate=False,
+                                 stream=None):
+    """crp_histogram_healpix into a device array (a torch int64/uint64 tensor of
+    12 nside^2 on the context's device); asynchronous on `stream`."""
+    _check(lib().crp_histogram_healpix_device(ctx, what, nside, source, _addr(out_dev),
+                                              1 if accumulate else 0, stream))
     return out_dev
 
 

@@ -678,4 +678,37 @@ crp_status crp_histogram_healpix(crp_context* ctx, int32_t what, int32_t nside, 
   return rc;
 }
 
+
+crp_status crp_histogram_healpix_device(crp_context* ctx, int32_t what, int32_t nside,
+                                        int32_t source, uint64_t* out_dev, int32_t accumulate,
+                                        void* stream) {
+  if (!ctx || !out_dev || nside < 1 || nside > 8192 || (source != 0 && source != 1) ||
+      what < CRP_COLLECT_ALL || what > CRP_COLLECT_AT_BORDER ||
+      (reinterpret_cast<uintptr_t>(out_dev) & 7u)) {
+    set_error("crp_histogram_healpix_device: bad argument");
+    return CRP_E_INVALID;
+  }
+  const uint64_t npix = 12ull * nside * nside;
+  DevState st;
+  uint64_t n = 0, seed = 0;
+  int device = 0;
+  context_pool(ctx, &st, &n, &device, &seed);
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != device) {
+    const cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return fail_cuda(e, "crp_histogram_healpix_device: cudaSetDevice");
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned long long* bins = reinterpret_cast<unsigned long long*>(out_dev);
+  cudaError_t e = cudaSuccess;
+  if (!accumulate) e = cudaMemsetAsync(bins, 0, 8 * npix, s);
+  if (e == cudaSuccess && n > 0) {
+    k_hist_healpix<<<blocks(n, 256), 256, 0, s>>>(st, n, what, nside, source, bins);
+    e = cudaGetLastError();
+  }
+  if (prev >= 0 && prev != device) cudaSetDevice(prev);
+  return e == cudaSuccess ? CRP_OK : fail_cuda(e, "crp_histogram_healpix_device");
+}
+
 }  // extern "C"
