@@ -109,6 +109,7 @@ class Params(C.Structure):
         ("max_steps", C.c_int64),
         ("length_unit_m", C.c_double),
         ("gmf", Gmf),
+        ("nuc_tab", C.c_void_p), ("nuc_amax", C.c_int64),
     ]
 
 
@@ -344,7 +345,12 @@ def make_params(*, grid_n, spacing, origin=(0.0, 0.0, 0.0), tol=1e-4, h_min=0.01
                 field_unit_T=NANOGAUSS_T, length_unit_m=MPC_M, flags=0, e_min=0.0,
                 beta_ad=0.0, seed=0, tables: Tables | None = None,
                 obs_c=(0.0, 0.0, 0.0), obs_r=0.0, border_c=(0.0, 0.0, 0.0), border_r=0.0,
-                galactic=None, gmf: Gmf | None = None, max_steps=10_000_000) -> Params:
+                galactic=None, gmf: Gmf | None = None, max_steps=10_000_000,
+                decay_table=None) -> Params:
+    """decay_table: unstable nuclei for the DECAY module, a dict of arrays A, Z
+    (A >= 2), tau_s (rest-frame mean lifetime, seconds) and branching [n, 4]
+    (beta-, beta+, neutron emission, proton emission); nuclides not listed
+    are stable."""
     P = Params()
     P.origin[:] = origin
     P.spacing = spacing
@@ -372,7 +378,28 @@ def make_params(*, grid_n, spacing, origin=(0.0, 0.0, 0.0), tol=1e-4, h_min=0.01
     if gmf is not None:
         P.gmf = gmf
     P.max_steps = max_steps
+    if decay_table is not None:
+        tab = nuclide_table(decay_table)
+        P._nuc_ref = tab
+        P.nuc_tab = tab.ctypes.data
+        P.nuc_amax = int(round((np.sqrt(8 * len(tab) // 5 + 1) - 3) / 2))
     return P
+
+
+def nuclide_table(decay_table) -> np.ndarray:
+    """The oracle's dense lookup of a decay table: for 0 <= Z <= A <= A_max,
+    entry A (A + 1) / 2 + Z holds [tau_s, b_beta-, b_beta+, b_n, b_p]
+    (unlisted nuclides: infinite lifetime, all fractions 0)."""
+    A = np.asarray(decay_table["A"], dtype=np.int64)
+    Z = np.asarray(decay_table["Z"], dtype=np.int64)
+    amax = int(A.max()) if len(A) else 2
+    n = (amax + 1) * (amax + 2) // 2
+    tab = np.zeros((n, 5))
+    tab[:, 0] = np.inf
+    idx = A * (A + 1) // 2 + Z
+    tab[idx, 0] = np.asarray(decay_table["tau_s"], dtype=np.float64)
+    tab[idx, 1:] = np.asarray(decay_table["branching"], dtype=np.float64)
+    return np.ascontiguousarray(tab.reshape(-1))
 
 
 def gmf_at(gmf: Gmf, pts, center=(0.0, 0.0, 0.0)):

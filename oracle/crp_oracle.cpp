@@ -589,6 +589,12 @@ struct orc_params {
   int64_t max_steps;   // per-candidate accepted-step budget
   double length_unit_m;  // metres per length unit (neutron decay length)
   orc_gmf gmf;           // analytic multi-arm galactic field (ORC_GMF)
+  // unstable nuclei (ORC_DECAY; NULL: only free neutrons decay): for
+  // 0 <= Z <= A <= nuc_amax, the 5 doubles at nuc_tab + 5 (A (A+1) / 2 + Z)
+  // are the rest-frame mean lifetime [s] (infinite: stable) and the
+  // branching fractions of beta-, beta+, neutron emission, proton emission
+  const double* nuc_tab;
+  int64_t nuc_amax;
 };
 
 struct orc_record {
@@ -993,6 +999,19 @@ double draw_uniform(const Ctx& C, Cand& c) {
 // Neutron decay length per eV of energy: c tau_n / (m_n c^2), in length units.
 double decay_k(const orc_params& P) { return kC * kTauN / kMnC2 / P.length_unit_m; }
 
+// Table entry of nuclide (A, Z) with A >= 2 ([tau, b_beta-, b_beta+, b_n, b_p]),
+// or NULL when the table has none (stable).
+const double* nuclide(const orc_params& P, int A, int Z) {
+  if (!P.nuc_tab || A < 2 || A > P.nuc_amax || Z < 0 || Z > A) return nullptr;
+  return P.nuc_tab + 5 * ((int64_t)A * (A + 1) / 2 + Z);
+}
+
+// Decay length per eV of energy of a nucleus of mass A m_p and lifetime tau:
+// c tau / (A m_p c^2), in length units.
+double nuc_decay_k(const orc_params& P, int A, double tau) {
+  return kC * tau / ((double)A * kMpC2) / P.length_unit_m;
+}
+
 // Reset of all stochastic interaction states (Sect. 3: after an interaction
 // the states of all interactions are reset).  Each state is the remaining
 // free path d = -ln(u) / R(E), drawn at the candidate's current energy, in
@@ -1013,9 +1032,16 @@ void reset_states(const Ctx& C, Cand& c) {
   if (P.flags & ORC_DECAY) {
     // free neutrons: decay length gamma c tau = (E / m_n c^2) c tau (reading:
     // the uniform is drawn for every species, so draw counts depend on the
-    // module list only)
+    // module list only); an unstable nucleus of the table: gamma c tau with
+    // gamma = E / (A m_p c^2)
     double u = draw_uniform(C, c);
-    c.d_dec = (c.A == 1 && c.Z == 0) ? -series_log(u) * (c.E * decay_k(P)) : INFINITY;
+    if (c.A == 1 && c.Z == 0) {
+      c.d_dec = -series_log(u) * (c.E * decay_k(P));
+    } else {
+      const double* e = nuclide(P, c.A, c.Z);
+      c.d_dec = (e && std::isfinite(e[0])) ? -series_log(u) * (c.E * nuc_decay_k(P, c.A, e[0]))
+                                           : INFINITY;
+    }
   }
   c.states_drawn = true;
 }
@@ -1177,10 +1203,48 @@ void propagate_one(const Ctx& C, Cand& c, std::vector<Cand>& out_secondaries) {
         c.events += 1;
         reset_states(C, c);
       } else if (dec_on && c.d_dec <= 0.0) {
-        // beta decay n -> p e nu (reading): the proton keeps the Lorentz
-        // factor; electron and antineutrino are not followed
-        c.Z = 1;
-        c.E = c.E * (kMpC2 / kMnC2);
+        if (c.A == 1 && c.Z == 0) {
+          // beta decay n -> p e nu (reading): the proton keeps the Lorentz
+          // factor; electron and antineutrino are not followed
+          c.Z = 1;
+          c.E = c.E * (kMpC2 / kMnC2);
+        } else {
+          // unstable nucleus (reading): the channel is the first whose
+          // cumulative branching fraction exceeds a uniform draw (order
+          // beta-, beta+, n, p; past the last sum, the last channel with a
+          // non-zero fraction).  beta-+: Z +- 1, the nucleus (mass A m_p)
+          // keeps its energy, the leptons are not followed.  Nucleon
+          // emission: as in photodisintegration, the nucleon carries E / A
+          // and the daughter E (A - 1) / A.
+          const double* e = nuclide(P, c.A, c.Z);
+          double u = draw_uniform(C, c);
+          int ch = -1, last = 0;
+          double acc = 0.0;
+          for (int k = 0; k < 4; ++k) {
+            acc = acc + e[1 + k];
+            if (e[1 + k] > 0.0) last = k;
+            if (ch < 0 && u < acc) ch = k;
+          }
+          if (ch < 0) ch = last;
+          if (ch == 0) {
+            c.Z = c.Z + 1;
+          } else if (ch == 1) {
+            c.Z = c.Z - 1;
+          } else {
+            const bool proton = ch == 3;
+            const int Ad = c.A - 1;
+            double En = c.E / (double)c.A;
+            double Ed = c.E * (double)Ad / (double)c.A;
+            Cand sec = make_secondary(c, 1, proton ? 1 : 0, En, P.h_max);
+            if (!(P.flags & ORC_EMIN) || En >= P.e_min)
+              out_secondaries.push_back(sec);
+            else
+              c.n_dropped += 1;
+            c.A = Ad;
+            c.Z = c.Z - (proton ? 1 : 0);
+            c.E = Ed;
+          }
+        }
         c.events += 1;
         reset_states(C, c);
       }

@@ -202,3 +202,52 @@ def backtrack_directions(n, r_lo, r_hi, seed):
     ux, uy, uz = isotropic(g, n)
     R = np.exp(g.uniform(np.log(r_lo), np.log(r_hi), n))
     return np.stack([ux, uy, uz], axis=1), R
+
+
+def beta_stability_z(A):
+    """Charge of the beta-stability line at mass number A: Green's
+    approximation Z = A / (1.98 + 0.0155 A^(2/3)) (from the semi-empirical
+    mass formula)."""
+    A = np.asarray(A, dtype=np.float64)
+    return A / (1.98 + 0.0155 * A ** (2.0 / 3.0))
+
+
+def synthetic_decay_table(a_max=56, tau0_s=1.0e6, decades_per_charge=2.0, width=1.0,
+                          drip=3.0):
+    """Synthetic lifetimes and branchings of unstable nuclei (input data; the
+    measured tables are not in the container).  For 2 <= A <= a_max and
+    1 <= Z <= A - 1, with D = Z - Z_s(A) the distance from the beta-stability
+    line: stable for |D| <= width; otherwise the rest-frame mean lifetime is
+    tau0_s * 10^(-decades_per_charge (|D| - width)) seconds, and the nucleus
+    beta decays toward the line (beta+ for D > 0, beta- for D < 0) except for
+    a fraction min(0.9, 0.3 (|D| - drip)) beyond |D| > drip, which emits a
+    nucleon (proton for D > 0, neutron for D < 0).  A channel whose daughter
+    would have Z' = 0 or N' = 0 with A' >= 2 is left out.  Returns dict(A, Z,
+    tau_s, branching [n, 4]: beta-, beta+, neutron emission, proton
+    emission) of the unstable nuclides only."""
+    rows = []
+    for A in range(2, a_max + 1):
+        zs = float(beta_stability_z(A))
+        for Z in range(1, A):
+            D = Z - zs
+            if abs(D) <= width:
+                continue
+            tau = tau0_s * 10.0 ** (-decades_per_charge * (abs(D) - width))
+            f_nuc = min(0.9, 0.3 * (abs(D) - drip)) if abs(D) > drip else 0.0
+            b = np.zeros(4)
+            if D > 0:
+                b[1], b[3] = 1.0 - f_nuc, f_nuc
+            else:
+                b[0], b[2] = 1.0 - f_nuc, f_nuc
+            # daughters: beta- (A, Z+1), beta+ (A, Z-1), n (A-1, Z), p (A-1, Z-1)
+            for k, (Ad, Zd) in enumerate(((A, Z + 1), (A, Z - 1), (A - 1, Z), (A - 1, Z - 1))):
+                if b[k] > 0 and Ad >= 2 and (Zd <= 0 or Zd >= Ad):
+                    b[k] = 0.0
+            if b.sum() == 0.0:
+                continue
+            b /= b.sum()
+            rows.append((A, Z, tau, b))
+    return dict(A=np.array([r[0] for r in rows], np.int32),
+                Z=np.array([r[1] for r in rows], np.int32),
+                tau_s=np.array([r[2] for r in rows]),
+                branching=np.array([r[3] for r in rows]))
