@@ -170,6 +170,29 @@ crp_status crp_tables_copy_out(const crp_tables* t, double* beta_pair, double* r
                                double* rate_gdr);
 crp_status crp_tables_destroy(crp_tables* t);
 
+/* Decay of unstable nuclei (Sect. 2 lists nuclear decay among the
+ * interactions; the paper gives no table).  Attaches a nuclide table to t:
+ * n host entries (A[i], Z[i]), 2 <= A <= CRP_DECAY_MAX_A, 1 <= Z <= A - 1,
+ * each listed once, with the rest-frame mean lifetime tau_s[i] > 0 [s] and
+ * the branching fractions branching[4 i + k] >= 0 of k = 0 beta- (Z + 1),
+ * 1 beta+ (Z - 1), 2 neutron emission (A - 1), 3 proton emission (A - 1,
+ * Z - 1), summing to 1 within 1e-9; a channel with a non-zero fraction
+ * whose daughter would have Z' = 0 or N' = 0 with A' >= 2 is rejected
+ * (CRP_E_INVALID, the table unchanged).  Nuclides not listed are stable.
+ * n = 0 removes the table.  The caller keeps its arrays; synchronous.
+ * With CRP_DECAY in the modules and this table present, crp_propagate
+ * decays the listed nuclei as a stochastic state reset with the others: the
+ * free path is -ln(u) gamma c tau with gamma = E / (A m_p c^2); at the event
+ * one uniform picks the channel as the first whose cumulative fraction (in
+ * the order above) exceeds it, else the last channel with a non-zero
+ * fraction; beta decays keep the energy (mass A m_p; the leptons are not
+ * followed), nucleon emission gives the nucleon E / A and the daughter
+ * E (A - 1) / A and appends the nucleon as a secondary (like
+ * photodisintegration).  The 1D mode rejects such tables with CRP_DECAY. */
+#define CRP_DECAY_MAX_A 64
+crp_status crp_tables_set_decay(crp_tables* t, int64_t n, const int32_t* A, const int32_t* Z,
+                                const double* tau_s, const double* branching);
+
 /* ------------------------------------------------------------------------
  * Candidates (Sect. 3, source model: position, spectrum, composition).
  * Structure of arrays, n entries each, host or device memory (on_device).

@@ -25,6 +25,8 @@ UNITS = {
     "propagate_mixed.cu": [],
     "propagate_gmf.cu": [],
     "propagate_fixed.cu": [],
+    "propagate_nuc_fp64.cu": ["-fmad=false"],
+    "propagate_nuc_mixed.cu": [],
     "propagate_1d.cu": ["-fmad=false"],
     "hist_noalloc.cu": [],
     "lens.cu": [],

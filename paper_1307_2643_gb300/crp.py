@@ -160,6 +160,7 @@ SYMBOLS = (
     "crp_context_create", "crp_context_destroy", "crp_context_size",
     "crp_grid_create", "crp_grid_destroy", "crp_grid_copy_out",
     "crp_tables_build", "crp_tables_from_host", "crp_tables_copy_out", "crp_tables_destroy",
+    "crp_tables_set_decay",
     "crp_candidates_inject", "crp_candidates_clear",
     "crp_propagate", "crp_collect", "crp_histogram_energy", "crp_histogram_energy_noalloc",
     "crp_histogram_energy_device",
@@ -202,6 +203,7 @@ def lib():
             L.crp_tables_from_host.argtypes = [p, C.POINTER(TablesDesc), p, p, p, C.POINTER(p)]
             L.crp_tables_copy_out.argtypes = [p, p, p, p]
             L.crp_tables_destroy.argtypes = [p]
+            L.crp_tables_set_decay.argtypes = [p, C.c_int64, p, p, p, p]
             L.crp_candidates_inject.argtypes = [p, C.POINTER(CandidateArrays), sz, u64, p]
             L.crp_candidates_clear.argtypes = [p]
             L.crp_propagate.argtypes = [p, p, C.POINTER(Modules), p, C.POINTER(Stats)]
@@ -363,6 +365,20 @@ def crp_tables_copy_out(tables, n):
 
 def crp_tables_destroy(tables):
     _check(lib().crp_tables_destroy(tables))
+
+
+def crp_tables_set_decay(tables, decay_table=None):
+    """Attach a nuclide table (dict of A, Z, tau_s, branching [n, 4]) to
+    `tables`, or remove it (None)."""
+    if decay_table is None:
+        _check(lib().crp_tables_set_decay(tables, 0, None, None, None, None))
+        return
+    A = np.ascontiguousarray(decay_table["A"], dtype=np.int32)
+    Z = np.ascontiguousarray(decay_table["Z"], dtype=np.int32)
+    tau = np.ascontiguousarray(decay_table["tau_s"], dtype=np.float64)
+    b = np.ascontiguousarray(decay_table["branching"], dtype=np.float64).reshape(-1, 4)
+    _check(lib().crp_tables_set_decay(tables, len(A), A.ctypes.data, Z.ctypes.data,
+                                      tau.ctypes.data, b.ctypes.data))
 
 
 def crp_candidates_inject(ctx, arrays: CandidateArrays, n, first_id=0, stream=None):

@@ -126,6 +126,8 @@ struct crp_tables {
   crp_tables_desc desc;
   double* data;   // beta | pion | gdr, n each
   float* data_f;  // binary32 copy of the three tables
+  double* nuc;    // unstable nuclei (crp_tables_set_decay), or null
+  int32_t nuc_amax;
 };
 
 namespace {
@@ -768,6 +770,8 @@ static crp_tables* tables_alloc(crp_context* c, const crp_tables_desc* d) {
   if (!t) return nullptr;
   t->ctx = c;
   t->desc = *d;
+  t->nuc = nullptr;
+  t->nuc_amax = 0;
   t->data = static_cast<double*>(dev_alloc(3 * (size_t)d->n * sizeof(double)));
   t->data_f = static_cast<float*>(dev_alloc(3 * (size_t)d->n * sizeof(float)));
   if (!t->data || !t->data_f) {
@@ -861,7 +865,96 @@ crp_status crp_tables_destroy(crp_tables* t) {
   cudaDeviceSynchronize();
   dev_free(t->data);
   dev_free(t->data_f);
+  dev_free(t->nuc);
   delete t;
+  return CRP_OK;
+}
+
+crp_status crp_tables_set_decay(crp_tables* t, int64_t n, const int32_t* A, const int32_t* Z,
+                                const double* tau_s, const double* branching) {
+  if (!t || n < 0 || (n > 0 && (!A || !Z || !tau_s || !branching))) {
+    set_error("crp_tables_set_decay: bad argument");
+    return CRP_E_INVALID;
+  }
+  int32_t amax = 2;
+  for (int64_t i = 0; i < n; ++i) {
+    const int a = A[i], z = Z[i];
+    if (a < 2 || a > CRP_DECAY_MAX_A || z < 1 || z > a - 1) {
+      set_error("crp_tables_set_decay: entry %lld: (A, Z) = (%d, %d) outside 2 <= A <= %d, "
+                "1 <= Z <= A - 1", (long long)i, a, z, CRP_DECAY_MAX_A);
+      return CRP_E_INVALID;
+    }
+    if (!(tau_s[i] > 0.0)) {
+      set_error("crp_tables_set_decay: entry %lld: lifetime %g must be > 0", (long long)i,
+                tau_s[i]);
+      return CRP_E_INVALID;
+    }
+    const double* b = branching + 4 * i;
+    double sum = 0.0;
+    // daughters of beta-, beta+, neutron emission, proton emission
+    const int da[4] = {a, a, a - 1, a - 1}, dz[4] = {z + 1, z - 1, z, z - 1};
+    for (int k = 0; k < 4; ++k) {
+      if (!(b[k] >= 0.0) || !std::isfinite(b[k])) {
+        set_error("crp_tables_set_decay: entry %lld: branching fraction %d is %g", (long long)i,
+                  k, b[k]);
+        return CRP_E_INVALID;
+      }
+      if (b[k] > 0.0 && da[k] >= 2 && (dz[k] < 1 || dz[k] > da[k] - 1)) {
+        set_error("crp_tables_set_decay: entry %lld: channel %d of (%d, %d) would make (%d, %d)",
+                  (long long)i, k, a, z, da[k], dz[k]);
+        return CRP_E_INVALID;
+      }
+      sum += b[k];
+    }
+    if (!(fabs(sum - 1.0) <= 1e-9)) {
+      set_error("crp_tables_set_decay: entry %lld: branching fractions sum to %.17g", (long long)i,
+                sum);
+      return CRP_E_INVALID;
+    }
+    if (a > amax) amax = a;
+  }
+  const int64_t slots = (int64_t)(amax + 1) * (amax + 2) / 2;
+  std::vector<double> h((size_t)(slots * kNucEntry), 0.0);
+  std::vector<char> seen((size_t)slots, 0);
+  for (int64_t k = 0; k < slots; ++k) h[(size_t)(k * kNucEntry)] = (double)INFINITY;
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t k = (int64_t)A[i] * (A[i] + 1) / 2 + Z[i];
+    if (seen[(size_t)k]) {
+      set_error("crp_tables_set_decay: (A, Z) = (%d, %d) listed twice", A[i], Z[i]);
+      return CRP_E_INVALID;
+    }
+    seen[(size_t)k] = 1;
+    const double* b = branching + 4 * i;
+    double* e = h.data() + k * kNucEntry;
+    // cumulative fractions, summed left to right
+    const double c1 = b[0], c2 = c1 + b[1], c3 = c2 + b[2];
+    int past = 3;
+    if (!(b[3] > 0.0)) past = b[2] > 0.0 ? 2 : (b[1] > 0.0 ? 1 : 0);
+    e[0] = tau_s[i];
+    e[1] = c1;
+    e[2] = c2;
+    e[3] = c3;
+    e[4] = (double)past;
+  }
+  DeviceGuard g(t->ctx->device);
+  double* d = nullptr;
+  if (n > 0) {
+    d = static_cast<double*>(dev_alloc(h.size() * sizeof(double)));
+    if (!d) {
+      set_error("crp_tables_set_decay: allocation failed");
+      return CRP_E_OOM;
+    }
+    const cudaError_t e = cudaMemcpy(d, h.data(), h.size() * sizeof(double),
+                                     cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      dev_free(d);
+      return fail_cuda(e, "crp_tables_set_decay");
+    }
+  }
+  cudaDeviceSynchronize();
+  dev_free(t->nuc);
+  t->nuc = d;
+  t->nuc_amax = n > 0 ? amax : 0;
   return CRP_OK;
 }
 
@@ -1202,8 +1295,13 @@ crp_status crp_propagate(crp_context* c, const crp_grid* g, const crp_modules* m
   kp.e_min_guard_f = (float)(m->e_min * 1.0001);
   // free-neutron decay length per eV (tau_n = 878.4 s, m_n c^2 = 939.56542052 MeV)
   kp.decay_k = 299792458.0 * 878.4 / 939.56542052e6 / m->length_unit_m;
+  kp.length_unit_m = m->length_unit_m;
   kp.flags = m->flags;
   kp.seed = c->seed;
+  if (m->tables && m->tables->nuc && (m->flags & CRP_DECAY)) {
+    kp.nuc_tab = m->tables->nuc;
+    kp.nuc_amax = m->tables->nuc_amax;
+  }
   if (m->tables) {
     const crp_tables* t = m->tables;
     kp.t_beta = t->data;
@@ -1248,9 +1346,9 @@ crp_status crp_propagate(crp_context* c, const crp_grid* g, const crp_modules* m
   int bps = m->blocks_per_sm;
   if (!bps) {
     cudaError_t e = m->precision == CRP_FP64
-                        ? occupancy_propagate_fp64(kp.f.dtype, block, &bps)
+                        ? occupancy_propagate_fp64(kp.f.dtype, block, &bps, kp.nuc_tab != nullptr)
                         : occupancy_propagate_mixed(kp.f.dtype, m->flags,
-                                                variant, block, &bps);
+                                                variant, block, &bps, kp.nuc_tab != nullptr);
     if (e != cudaSuccess) return fail_cuda(e, "crp_propagate: occupancy query");
     if (bps < 1) bps = 1;
   }
@@ -1897,6 +1995,11 @@ crp_status crp_propagate_1d(crp_context* c, const crp_cosmology* cosmo, const cr
   }
   if (!(m->length_unit_m > 0.0)) {
     set_error("crp_propagate_1d: length_unit_m must be > 0");
+    return CRP_E_INVALID;
+  }
+  if ((m->flags & CRP_DECAY) && m->tables && m->tables->nuc) {
+    set_error("crp_propagate_1d: the 1D mode decays free neutrons only; use tables without a "
+              "nuclide table (crp_tables_set_decay with n = 0)");
     return CRP_E_INVALID;
   }
   if (stats_out) memset(stats_out, 0, sizeof(*stats_out));

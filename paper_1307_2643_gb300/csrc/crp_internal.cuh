@@ -34,6 +34,12 @@ enum : uint32_t {
   ERR_ROUND_LIMIT = 1u << 3,
 };
 
+// Nuclide table entry: rest-frame lifetime [s] (infinite: stable), the
+// cumulative branching fractions after beta-, beta+ and neutron emission, and
+// the channel taken by a uniform at or past the last sum (proton emission if
+// its fraction is non-zero, else the last channel with a non-zero fraction).
+constexpr int kNucEntry = 5;
+
 // per-candidate flag bits
 enum : uint32_t {
   CF_STATES_DRAWN = 1u << 0,
@@ -100,6 +106,11 @@ struct KParams {
   double tol, tol2, h_min, h_max, curv_k, beta_ad, e_min;
   float e_min_guard_f;  // binary32 E_min plus 1e-4: below it the exact test runs
   double decay_k;       // neutron decay length per eV: c tau_n / (m_n c^2) [length unit]
+  double length_unit_m;  // metres per length unit (nuclear decay lengths)
+  // unstable nuclei (CRP_DECAY with a nuclide table; null otherwise): kNucEntry
+  // doubles per nuclide 0 <= Z <= A <= nuc_amax at A (A + 1) / 2 + Z
+  const double* nuc_tab;
+  int32_t nuc_amax;
   // binary32 copies for the mixed policy (converted once on the host)
   float tol2_f, inv_tol2_f, h_min_f, h_max_f, curv_k_f, beta_ad_f, tab_lg0_f, tab_inv_dlg_f;
   const float* t_beta_f;
@@ -156,7 +167,15 @@ cudaError_t launch_propagate_fp64(const KParams& kp, const DevState& st, DevCoun
                                   int grid, int block, cudaStream_t s);
 cudaError_t launch_propagate_mixed(const KParams& kp, const DevState& st, DevCounters* dc,
                                    int grid, int block, int variant, cudaStream_t s);
-cudaError_t occupancy_propagate_fp64(int dtype, int block, int* blocks_per_sm);
+cudaError_t occupancy_propagate_fp64(int dtype, int block, int* blocks_per_sm, bool nuc);
+// Kernels with the decay of unstable nuclei as a third free path (a nuclide
+// table is in use); the mixed ones in the 256 x 2 launch variant only.
+cudaError_t launch_propagate_fp64_nuc(const KParams& kp, const DevState& st, DevCounters* dc,
+                                      int grid, int block, cudaStream_t s);
+cudaError_t occupancy_propagate_fp64_nuc(int dtype, int block, int* blocks_per_sm);
+cudaError_t launch_propagate_mixed_nuc(const KParams& kp, const DevState& st, DevCounters* dc,
+                                       int grid, int block, cudaStream_t s);
+cudaError_t occupancy_propagate_mixed_nuc(int dtype, uint32_t flags, int block, int* bps);
 // Module lists the mixed kernel is also instantiated for with the list fixed
 // at compile time (launch variant 256 x 2): extragalactic propagation with or
 // without photodisintegration.
@@ -172,7 +191,7 @@ cudaError_t occupancy_propagate_mixed_gmf(int dtype, int variant, int block, int
 cudaError_t sample_field_mixed_gmf(const KParams& kp, const double* xyz, int64_t n, double* B,
                                    cudaStream_t s);
 cudaError_t occupancy_propagate_mixed(int dtype, uint32_t flags, int variant, int block,
-                                      int* blocks_per_sm);
+                                      int* blocks_per_sm, bool nuc);
 // Dynamic shared memory of one propagate block (per-thread stage storage).
 size_t propagate_smem_fp64(int block);
 // The field the propagate kernels see, at n points (device arrays xyz [n][3]

@@ -422,8 +422,19 @@ __device__ __forceinline__ double draw_u(const KParams& p, EvCore& c) {
   return u01_open(w.v0, w.v1);
 }
 
+// Table entry of an unstable nucleus (A >= 2): [tau (s), cumulative branching
+// after beta-, after beta+, after neutron emission, channel past the last
+// sum], or null (stable, or no table).
+__device__ __forceinline__ const double* nuclide(const KParams& p, int A, int Z) {
+  if (!p.nuc_tab || A < 2 || A > p.nuc_amax || Z < 0 || Z > A) return nullptr;
+  return p.nuc_tab + kNucEntry * ((int64_t)A * (A + 1) / 2 + Z);
+}
+
 // Remaining free path d = -ln(u) / R(E) per interaction, in module order
-// [pion production, photodisintegration, neutron decay], at the current energy.
+// [pion production, photodisintegration, decay], at the current energy.
+// NUC: kernels launched with a nuclide table; the others never see one, and
+// their rare paths are compiled without it.
+template <bool NUC>
 __device__ __forceinline__ void reset_states(const KParams& p, EvCore& c) {
   const double lng = series_log(c.E / ((double)c.A * MP_C2_EV));
   if (p.flags & CRP_PION) {
@@ -437,44 +448,55 @@ __device__ __forceinline__ void reset_states(const KParams& p, EvCore& c) {
     c.d_pd = R > 0.0 ? -series_log(u) / R : (double)INFINITY;
   }
   if (p.flags & CRP_DECAY) {
-    // free neutrons decay after -ln(u) gamma c tau; drawn for every species
+    // free neutrons decay after -ln(u) gamma c tau; drawn for every species.
+    // With a nuclide table, an unstable nucleus after -ln(u) gamma c tau with
+    // gamma = E / (A m_p c^2).
     const double u = draw_u(p, c);
-    c.d_dec = (c.A == 1 && c.Z == 0) ? -series_log(u) * (c.E * p.decay_k) : (double)INFINITY;
+    if (c.A == 1 && c.Z == 0) {
+      c.d_dec = -series_log(u) * (c.E * p.decay_k);
+    } else if (!NUC) {
+      c.d_dec = (double)INFINITY;
+    } else {
+      const double* e = nuclide(p, c.A, c.Z);
+      c.d_dec = (e && e[0] < (double)INFINITY)
+                    ? -series_log(u) *
+                          (c.E * (299792458.0 * e[0] / ((double)c.A * MP_C2_EV) / p.length_unit_m))
+                    : (double)INFINITY;
+    }
   }
   c.flags |= CF_STATES_DRAWN;
 }
 
 // Neutron beta decay: n -> p e nu; the proton keeps the Lorentz factor.
+template <bool NUC>
 __device__ __forceinline__ void decay_event(const KParams& p, EvCore& c) {
   c.Z = 1;
   c.E = c.E * (MP_C2_EV / MN_C2_EV);
   c.events += 1;
-  reset_states(p, c);
+  reset_states<NUC>(p, c);
 }
 
 // Pion event: one nucleon loses the inelasticity 0.2 of its energy.
+template <bool NUC>
 __device__ __forceinline__ void pion_event(const KParams& p, EvCore& c, EvCounts& n) {
   c.E = c.E - 0.2 * c.E / (double)c.A;
   c.n_pion += 1;
   c.events += 1;
   n.pion += 1;
-  reset_states(p, c);
+  reset_states<NUC>(p, c);
 }
 
 // Single-nucleon emission: proton with probability Z/A (kept away from
 // Z' = 0 or N' = 0 daughters with A' >= 2); the nucleon carries E/A, the
 // daughter E (A-1)/A; the nucleon is appended to the pool, and to the next
 // round's work queue, when E/A >= e_min.
-__device__ __forceinline__ void photodisintegrate(const KParams& p, const DevState& st,
-                                                  DevCounters* dc, EvCore& c, EvCounts& n,
-                                                  double ux, double uy, double uz) {
-  const double u = draw_u(p, c);
-  bool proton = u < (double)c.Z / (double)c.A;
-  const int Ad = c.A - 1;
-  if (proton && Ad >= 2 && c.Z - 1 == 0) proton = false;
-  if (!proton && Ad >= 2 && Ad - c.Z == 0) proton = true;
-  const double En = c.E / (double)c.A;
-  const double Ed = c.E * (double)Ad / (double)c.A;
+// Append an emitted nucleon of energy En at the candidate's position,
+// direction and trajectory length (lineage id from the candidate's event
+// count), and queue it for the next round; below e_min it is only counted.
+__device__ __forceinline__ void emit_nucleon(const KParams& p, const DevState& st,
+                                             DevCounters* dc, EvCore& c, EvCounts& n,
+                                             bool proton, double En, double ux, double uy,
+                                             double uz) {
   if (!(p.flags & CRP_EMIN) || En >= p.e_min) {
     const unsigned long long slot = atomicAdd(&dc->tail, 1ull);
     if (slot < p.capacity) {
@@ -532,19 +554,64 @@ __device__ __forceinline__ void photodisintegrate(const KParams& p, const DevSta
     c.n_dropped += 1;
     n.dropped += 1;
   }
+}
+
+template <bool NUC>
+__device__ __forceinline__ void photodisintegrate(const KParams& p, const DevState& st,
+                                                  DevCounters* dc, EvCore& c, EvCounts& n,
+                                                  double ux, double uy, double uz) {
+  const double u = draw_u(p, c);
+  bool proton = u < (double)c.Z / (double)c.A;
+  const int Ad = c.A - 1;
+  if (proton && Ad >= 2 && c.Z - 1 == 0) proton = false;
+  if (!proton && Ad >= 2 && Ad - c.Z == 0) proton = true;
+  const double En = c.E / (double)c.A;
+  const double Ed = c.E * (double)Ad / (double)c.A;
+  emit_nucleon(p, st, dc, c, n, proton, En, ux, uy, uz);
   c.A = Ad;
   c.Z = c.Z - (proton ? 1 : 0);
   c.E = Ed;
   c.n_pd += 1;
   c.events += 1;
   n.pd += 1;
-  reset_states(p, c);
+  reset_states<NUC>(p, c);
+}
+
+// Decay of an unstable nucleus: one uniform picks the channel by the
+// cumulative branching fractions (beta-, beta+, neutron emission, proton
+// emission).  beta-+ change Z by +-1 and keep the energy (mass A m_p; the
+// leptons are not followed); nucleon emission splits the energy as
+// photodisintegration does (nucleon E / A, daughter E (A - 1) / A).
+template <bool NUC>
+__device__ __forceinline__ void nuclear_decay(const KParams& p, const DevState& st,
+                                              DevCounters* dc, EvCore& c, EvCounts& n,
+                                              double ux, double uy, double uz) {
+  const double* e = nuclide(p, c.A, c.Z);
+  const double u = draw_u(p, c);
+  const int ch = u < e[1] ? 0 : (u < e[2] ? 1 : (u < e[3] ? 2 : (int)e[4]));
+  if (ch == 0) {
+    c.Z = c.Z + 1;
+  } else if (ch == 1) {
+    c.Z = c.Z - 1;
+  } else {
+    const bool proton = ch == 3;
+    const int Ad = c.A - 1;
+    const double En = c.E / (double)c.A;
+    const double Ed = c.E * (double)Ad / (double)c.A;
+    emit_nucleon(p, st, dc, c, n, proton, En, ux, uy, uz);
+    c.A = Ad;
+    c.Z = c.Z - (proton ? 1 : 0);
+    c.E = Ed;
+  }
+  c.events += 1;
+  reset_states<NUC>(p, c);
 }
 
 enum : int { EV_NONE = 0, EV_PION = 1, EV_PD = 2, EV_DRAW = 3, EV_DECAY = 4 };
 
 // Run one rare path on the slot: first free-path draw (EV_DRAW), a pion
-// event or a photodisintegration event.
+// event, a photodisintegration event or a decay.
+template <bool NUC>
 static __device__ __noinline__ void slot_event(const KParams& p, const DevState& st, DevCounters* dc,
                                         uint64_t i, int kind) {
   EvCore c;
@@ -570,13 +637,15 @@ static __device__ __noinline__ void slot_event(const KParams& p, const DevState&
   c.flags = st.flags[i];
   EvCounts n = {0, 0, 0, 0};
   if (kind == EV_PION)
-    pion_event(p, c, n);
+    pion_event<NUC>(p, c, n);
   else if (kind == EV_PD)
-    photodisintegrate(p, st, dc, c, n, st.ux[i], st.uy[i], st.uz[i]);
+    photodisintegrate<NUC>(p, st, dc, c, n, st.ux[i], st.uy[i], st.uz[i]);
+  else if (kind == EV_DECAY && (!NUC || (c.A == 1 && c.Z == 0)))
+    decay_event<NUC>(p, c);
   else if (kind == EV_DECAY)
-    decay_event(p, c);
+    nuclear_decay<NUC>(p, st, dc, c, n, st.ux[i], st.uy[i], st.uz[i]);
   else
-    reset_states(p, c);
+    reset_states<NUC>(p, c);
   st.E[i] = c.E;
   st.A[i] = c.A;
   st.Z[i] = c.Z;
@@ -627,8 +696,10 @@ struct LaneCore {
   int A, Z, q, status;
   double x[3];
   // d_pd holds the candidate's second stochastic free path: photodisintegration
-  // for nuclei, beta decay for free neutrons (the other one is infinite)
-  double E, s, s_max, h, d_pion, d_pd;
+  // for nuclei, beta decay for free neutrons (the other one is infinite);
+  // d_nd the decay of an unstable nucleus (kernels built with a nuclide table
+  // only)
+  double E, s, s_max, h, d_pion, d_pd, d_nd;
   uint32_t dacc, drej;  // accepted steps / rejected trials since the last store
   uint32_t budget;      // accepted steps left before CRP_BUDGET
   int rejections;       // rejected trials of the current step
@@ -655,6 +726,14 @@ __device__ __forceinline__ bool second_on(const KParams& p, const LaneCore& c) {
   return (mflags<FIX>(p) & (is_neutron(c) ? CRP_DECAY : CRP_PHOTODIS)) != 0;
 }
 
+// Is the lane's third free path (decay of a nucleus) active?  Only kernels
+// instantiated with NUC (launched when a nuclide table is in use) hold it.
+template <bool NUC, uint32_t FIX = 0>
+__device__ __forceinline__ bool nuc_on(const KParams& p, const LaneCore& c) {
+  return NUC && (mflags<FIX>(p) & CRP_DECAY) != 0 && c.A >= 2;
+}
+
+template <bool NUC = false>
 __device__ __forceinline__ void load_core(const KParams& p, const DevState& st, uint32_t i,
                                           LaneCore& c) {
   c.slot = i;
@@ -669,6 +748,7 @@ __device__ __forceinline__ void load_core(const KParams& p, const DevState& st, 
   c.A = st.A[i];
   c.Z = st.Z[i];
   c.d_pd = is_neutron(c) ? st.d_dec[i] : st.d_pd[i];
+  if (NUC) c.d_nd = c.A >= 2 ? st.d_dec[i] : (double)INFINITY;
   c.q = st.q[i];
   c.status = st.status[i];
   const uint64_t done = st.n_acc[i];
@@ -680,6 +760,7 @@ __device__ __forceinline__ void load_core(const KParams& p, const DevState& st, 
   c.crossed = false;
 }
 
+template <bool NUC = false>
 __device__ __forceinline__ void store_core(const DevState& st, LaneCore& c) {
   const uint32_t i = c.slot;
   st.x[i] = c.x[0];
@@ -693,6 +774,7 @@ __device__ __forceinline__ void store_core(const DevState& st, LaneCore& c) {
     st.d_dec[i] = c.d_pd;
   else
     st.d_pd[i] = c.d_pd;
+  if (NUC && c.A >= 2) st.d_dec[i] = c.d_nd;
   st.status[i] = c.status;
   st.n_acc[i] += c.dacc;
   st.n_rej[i] += c.drej;
@@ -701,6 +783,7 @@ __device__ __forceinline__ void store_core(const DevState& st, LaneCore& c) {
 }
 
 // Fields a rare path may change.
+template <bool NUC = false>
 __device__ __forceinline__ void reload_event_fields(const DevState& st, LaneCore& c) {
   const uint32_t i = c.slot;
   c.E = st.E[i];
@@ -708,6 +791,7 @@ __device__ __forceinline__ void reload_event_fields(const DevState& st, LaneCore
   c.Z = st.Z[i];
   c.d_pion = st.d_pion[i];
   c.d_pd = is_neutron(c) ? st.d_dec[i] : st.d_pd[i];
+  if (NUC) c.d_nd = c.A >= 2 ? st.d_dec[i] : (double)INFINITY;
 }
 
 // One accepted step done: step budget bookkeeping.
@@ -758,8 +842,10 @@ static __constant__ float c_a32[6][6] = {
 // cycle so that a warp advances one Cash-Karp trial per iteration; the
 // arithmetic and its order are those of the reference formulation.
 // ---------------------------------------------------------------------------
-struct PolicyFP64 {
+template <bool NUC>
+struct PolicyFP64T {
   static constexpr uint32_t kFix = 0;  // run-time module flags
+  static constexpr bool kNuc = NUC;    // nuclear decay as a third free path
   using Real = double;
   static constexpr bool kSharedStages = true;
   static constexpr size_t kSmemPerThread = kStageSlots * sizeof(double);
@@ -772,13 +858,13 @@ struct PolicyFP64 {
 
   __device__ __forceinline__ static void load(const KParams& p, const DevState& st, uint32_t i,
                                               Lane& c) {
-    load_core(p, st, i, c);
+    load_core<NUC>(p, st, i, c);
     c.u[0] = st.ux[i];
     c.u[1] = st.uy[i];
     c.u[2] = st.uz[i];
   }
   __device__ __forceinline__ static void store(const DevState& st, Lane& c) {
-    store_core(st, c);
+    store_core<NUC>(st, c);
     st.ux[c.slot] = c.u[0];
     st.uy[c.slot] = c.u[1];
     st.uz[c.slot] = c.u[2];
@@ -806,6 +892,7 @@ struct PolicyFP64 {
     if (c.cap_s < h) h = c.cap_s;
     if ((p.flags & CRP_PION) && c.d_pion < h) h = c.d_pion;
     if (second_on(p, c) && c.d_pd < h) h = c.d_pd;
+    if (nuc_on<NUC>(p, c) && c.d_nd < h) h = c.d_nd;
     c.h = h;  // trial step of this step
     c.kappa = (double)(c.q * c.Z) * p.curv_k / c.E;
     double k[3];
@@ -898,10 +985,13 @@ struct PolicyFP64 {
     // stochastic interactions: the first in module order whose free path ran out
     const bool pion_on = (p.flags & CRP_PION) != 0;
     const bool pd_on = second_on(p, c);
+    const bool nd_on = nuc_on<NUC>(p, c);
     if (pion_on) c.d_pion = c.d_pion - h;
     if (pd_on) c.d_pd = c.d_pd - h;
+    if (nd_on) c.d_nd = c.d_nd - h;
     if (pion_on && c.d_pion <= 0.0) return EV_PION;
     if (pd_on && c.d_pd <= 0.0) return is_neutron(c) ? EV_DECAY : EV_PD;
+    if (nd_on && c.d_nd <= 0.0) return EV_DECAY;
     return EV_NONE;
   }
 
@@ -925,7 +1015,7 @@ struct PolicyFP64 {
 
   __device__ __forceinline__ static void after_event(const KParams&, const DevState& st,
                                                      Lane& c) {
-    reload_event_fields(st, c);
+    reload_event_fields<NUC>(st, c);
   }
 
   __device__ __forceinline__ static uint32_t key(const KParams& p, const Lane& c) {
@@ -943,11 +1033,12 @@ struct PolicyFP64 {
 // error norm (decided in binary64 near the tolerance).  GAL adds the
 // analytic galactic field.
 // ---------------------------------------------------------------------------
-enum : int { CAP_NONE = 0, CAP_S = 1, CAP_PION = 2, CAP_PD = 3 };
+enum : int { CAP_NONE = 0, CAP_S = 1, CAP_PION = 2, CAP_PD = 3, CAP_ND = 4 };
 
-template <bool GAL, bool GMF = false, uint32_t FIX = 0>
+template <bool GAL, bool GMF = false, uint32_t FIX = 0, bool NUC = false>
 struct PolicyMixedT {
   static constexpr uint32_t kFix = FIX;  // compile-time module list (0: run-time flags)
+  static constexpr bool kNuc = NUC;      // nuclear decay as a third free path
   using Real = float;
   static constexpr bool kSharedStages = false;
   // per-lane cache of the last cell record gathered (6 float4, lane-interleaved)
@@ -1014,7 +1105,7 @@ struct PolicyMixedT {
 
   __device__ __forceinline__ static void load(const KParams& p, const DevState& st, uint32_t i,
                                               Lane& c) {
-    load_core(p, st, i, c);
+    load_core<NUC>(p, st, i, c);
     c.u[0] = (float)st.ux[i];
     c.u[1] = (float)st.uy[i];
     c.u[2] = (float)st.uz[i];
@@ -1033,6 +1124,7 @@ struct PolicyMixedT {
     double d = c.s_max - c.s;
     if ((mflags<FIX>(p) & CRP_PION) && c.d_pion < d) d = c.d_pion;
     if (second_on<FIX>(p, c) && c.d_pd < d) d = c.d_pd;
+    if (nuc_on<NUC, FIX>(p, c) && c.d_nd < d) d = c.d_nd;
     c.near_f = __double2float_rd(d);
   }
 
@@ -1049,7 +1141,7 @@ struct PolicyMixedT {
   __device__ __forceinline__ static void store(const DevState& st, Lane& c) {
     fold_energy(c);
     c.h = (double)c.hn;
-    store_core(st, c);
+    store_core<NUC>(st, c);
     st.ux[c.slot] = (double)c.u[0];
     st.uy[c.slot] = (double)c.u[1];
     st.uz[c.slot] = (double)c.u[2];
@@ -1186,6 +1278,10 @@ struct PolicyMixedT {
       if (second_on<FIX>(p, c) && c.d_pd < h) {
         h = c.d_pd;
         c.cap = CAP_PD;
+      }
+      if (nuc_on<NUC, FIX>(p, c) && c.d_nd < h) {
+        h = c.d_nd;
+        c.cap = CAP_ND;
       }
       if (c.cap != CAP_NONE) c.hf = (float)h;
     }
@@ -1329,12 +1425,15 @@ struct PolicyMixedT {
     // stochastic interactions (a free path can end only in a "near" step)
     const bool pion_on = (mflags<FIX>(p) & CRP_PION) != 0;
     const bool pd_on = second_on<FIX>(p, c);
+    const bool nd_on = nuc_on<NUC, FIX>(p, c);
     if (pion_on) c.d_pion = c.cap == CAP_PION ? 0.0 : c.d_pion - h;
     if (pd_on) c.d_pd = c.cap == CAP_PD ? 0.0 : c.d_pd - h;
+    if (nd_on) c.d_nd = c.cap == CAP_ND ? 0.0 : c.d_nd - h;
     c.near_f = __fsub_rd(c.near_f, hf);
     if (c.near) {
       if (pion_on && c.d_pion <= 0.0) return EV_PION;
       if (pd_on && c.d_pd <= 0.0) return is_neutron(c) ? EV_DECAY : EV_PD;
+      if (nd_on && c.d_nd <= 0.0) return EV_DECAY;
     }
     return EV_NONE;
   }
@@ -1365,7 +1464,7 @@ struct PolicyMixedT {
 
   __device__ __forceinline__ static void after_event(const KParams& p, const DevState& st,
                                                      Lane& c) {
-    reload_event_fields(st, c);
+    reload_event_fields<NUC>(st, c);
     c.E_f = (float)c.E;
     c.E_fold_f = c.E_f;
     c.yl = 0.f;
@@ -1382,6 +1481,12 @@ struct PolicyMixedT {
 using PolicyMixed = PolicyMixedT<false>;
 using PolicyMixedGal = PolicyMixedT<true>;         // analytic disk + halo
 using PolicyMixedGmf = PolicyMixedT<true, true>;   // plus the multi-arm field
+using PolicyFP64 = PolicyFP64T<false>;
+// with a nuclide table: the decay of unstable nuclei as a third free path
+using PolicyFP64Nuc = PolicyFP64T<true>;
+using PolicyMixedNuc = PolicyMixedT<false, false, 0, true>;
+using PolicyMixedGalNuc = PolicyMixedT<true, false, 0, true>;
+using PolicyMixedGmfNuc = PolicyMixedT<true, true, 0, true>;
 
 
 // ---------------------------------------------------------------------------
@@ -1425,7 +1530,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
           if (st.status[slot] == CRP_ACTIVE) {
             if ((mflags<Policy::kFix>(p) & (CRP_PION | CRP_PHOTODIS | CRP_DECAY)) &&
                 !(st.flags[slot] & CF_STATES_DRAWN))
-              slot_event(p, st, dc, slot, EV_DRAW);  // first free paths of this candidate
+              slot_event<Policy::kNuc>(p, st, dc, slot, EV_DRAW);  // first free paths
             Policy::load(p, st, slot, c);
             has = true;
             in_step = false;
@@ -1446,7 +1551,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
         const int ev = Policy::finish_step(p, c, lc);
         if (ev != EV_NONE) {
           Policy::store(st, c);
-          slot_event(p, st, dc, c.slot, ev);
+          slot_event<Policy::kNuc>(p, st, dc, c.slot, ev);
           Policy::after_event(p, st, c);
         }
         Policy::breaks(p, c, lc);

@@ -6,10 +6,12 @@ namespace crp {
 
 cudaError_t launch_propagate_fp64(const KParams& kp, const DevState& st, DevCounters* dc,
                                   int grid, int block, cudaStream_t s) {
+  if (kp.nuc_tab) return launch_propagate_fp64_nuc(kp, st, dc, grid, block, s);
   return launch_policy<PolicyFP64, 128, 2>(kp, st, dc, grid, block, s);
 }
 
-cudaError_t occupancy_propagate_fp64(int dtype, int block, int* bps) {
+cudaError_t occupancy_propagate_fp64(int dtype, int block, int* bps, bool nuc) {
+  if (nuc) return occupancy_propagate_fp64_nuc(dtype, block, bps);
   return occupancy_policy<PolicyFP64, 128, 2>(dtype, block, bps);
 }
 

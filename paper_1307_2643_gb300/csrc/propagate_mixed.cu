@@ -8,6 +8,7 @@ namespace crp {
 
 cudaError_t launch_propagate_mixed(const KParams& kp, const DevState& st, DevCounters* dc,
                                    int grid, int block, int variant, cudaStream_t s) {
+  if (kp.nuc_tab) return launch_propagate_mixed_nuc(kp, st, dc, grid, block, s);
   if (variant == 2) {
     const int fx = fixed_modules_index(kp.flags);
     if (fx >= 0) return launch_propagate_mixed_fixed(fx, kp, st, dc, grid, block, s);
@@ -19,7 +20,9 @@ cudaError_t launch_propagate_mixed(const KParams& kp, const DevState& st, DevCou
 }
 
 // the kernel launch_propagate_mixed would run for these flags and variant
-cudaError_t occupancy_propagate_mixed(int dtype, uint32_t flags, int variant, int block, int* bps) {
+cudaError_t occupancy_propagate_mixed(int dtype, uint32_t flags, int variant, int block, int* bps,
+                                      bool nuc) {
+  if (nuc) return occupancy_propagate_mixed_nuc(dtype, flags, block, bps);
   if (variant == 2) {
     const int fx = fixed_modules_index(flags);
     if (fx >= 0) return occupancy_propagate_mixed_fixed(fx, dtype, block, bps);
