@@ -13,6 +13,18 @@ primitives.  Parameters are packed as [W1, b1, W2, b2, ...] with W_l of shape
 
 Pins: central finite differences of the loss against the backward pass, and
 an explicit-loop forward on a tiny network.
+
+bf16 mode (``bf16=True`` in forward / backward): the same network with the
+values rounded to bfloat16 at the points where the GPU stores them in that
+format, everything else binary64: the hidden-to-hidden weights; every
+hidden activation h_l = bf16(ReLU(z_l)) (z_l from the rounded inputs, the
+thin first layer from the binary32 inputs and weights); the output layer
+reads the rounded last activation; in the backward pass every hidden
+backward signal dz_l = bf16((dz_{l+1} W_{l+1}) masked by h_l > 0), and
+dy = dL/dy of the output layer stays unrounded.  The weight and bias
+gradients are the binary64 products and sums of those rounded values.  The
+rounding itself (round to nearest even, through binary32 like the GPU's
+binary32 accumulators) is pinned by its own test.
 """
 from __future__ import annotations
 
@@ -52,8 +64,18 @@ def bf16_round(a):
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def forward(flat, shapes, x):
-    """Returns (y_hat [n, 3] unit vectors, cache)."""
+def bf16_weights(flat, shapes):
+    """The parameters with the hidden-to-hidden weights rounded to bf16 (the
+    first and the output layer's weights and every bias unrounded)."""
+    Ws, bs = unpack(np.array(flat, dtype=np.float64), shapes)
+    for l in range(1, len(shapes) - 1):
+        Ws[l] = bf16_round(Ws[l])
+    return pack(Ws, bs)
+
+
+def forward(flat, shapes, x, bf16=False):
+    """Returns (y_hat [n, 3] unit vectors, cache).  bf16: see the module
+    docstring (the caller passes bf16_weights(flat) to round the weights)."""
     Ws, bs = unpack(flat, shapes)
     hs, zs = [x], []
     h = x
@@ -61,6 +83,8 @@ def forward(flat, shapes, x):
         z = h @ W.T + b
         zs.append(z)
         h = np.maximum(z, 0.0) if l < len(Ws) - 1 else z
+        if bf16 and l < len(Ws) - 1:
+            h = bf16_round(h)
         hs.append(h)
     y = hs[-1]
     norm = np.linalg.norm(y, axis=1, keepdims=True)
@@ -71,8 +95,9 @@ def loss(y_hat, t):
     return float(np.mean(1.0 - np.sum(y_hat * t, axis=1)))
 
 
-def backward(flat, shapes, cache, t):
-    """Gradient of mean(1 - y_hat . t) with respect to the packed parameters."""
+def backward(flat, shapes, cache, t, bf16=False):
+    """Gradient of mean(1 - y_hat . t) with respect to the packed parameters.
+    bf16: the hidden backward signals rounded (see the module docstring)."""
     Ws, bs = unpack(flat, shapes)
     hs, zs, norm = cache["hs"], cache["zs"], cache["norm"]
     n = len(t)
@@ -88,6 +113,8 @@ def backward(flat, shapes, cache, t):
         if l > 0:
             dh = dz @ Ws[l]
             dz = dh * (zs[l - 1] > 0.0)
+            if bf16:
+                dz = bf16_round(dz)
     return pack(dWs, dbs)
 
 

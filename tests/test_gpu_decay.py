@@ -132,8 +132,9 @@ def test_without_table_only_neutrons_decay(setup):
     P = oracle.make_params(grid_n=n, spacing=dx, tol=1e-4, h_min=1e-3, h_max=0.5, flags=OFLAGS,
                            e_min=E_MIN, beta_ad=H0_OVER_C, seed=606, tables=tabs)
     ref0 = oracle.propagate(P, field.astype(np.float64), inj, tables=tabs)
-    assert rec.tobytes() == ref0.tobytes() or all(
-        np.array_equal(rec[f], ref0[f]) for f in rec.dtype.names)
+    assert len(rec) == len(ref0)
+    for f in EXACT_FIELDS + ("n_acc", "x", "u", "E", "s"):
+        assert np.array_equal(rec[f], ref0[f]), f
     prim = rec[rec["generation"] == 0]
     assert np.all((prim["n_pd"] > 0) | ((prim["A"] == prim["A0"]) & (prim["Z"] == prim["Z0"])))
 
