@@ -1,7 +1,11 @@
-"""MLP lens surrogate on the GPU against the fp64 oracle: forward and
-gradients on the same bf16-rounded hidden weights (the GPU keeps activations
-and backward signals in bf16, so agreement is to bf16 precision), the Adam
-update, and training on a smooth target."""
+"""MLP lens surrogate on the GPU against the oracle in its bf16 mode: the
+oracle rounds to bfloat16 exactly where the kernels store that format
+(hidden weights, hidden activations, hidden backward signals) and computes
+everything else in binary64.  What remains between the two is the order of
+the kernels' binary32 sums, which moves a value across a bfloat16 rounding
+boundary now and then; so outputs and every gradient element are compared
+within a bfloat16 ulp of their scale (2^-8 relative), not by aggregate
+norms.  Also: the Adam update, and training on a smooth target."""
 import numpy as np
 import pytest
 
@@ -30,13 +34,50 @@ def _params(seed=1):
     return np.concatenate(parts).astype(np.float32)
 
 
-def _oracle_view(p32):
+ULP = 2.0 ** -8   # bfloat16 relative spacing (8 significand bits)
+
+
+def _oracle_view(p32, shapes=SHAPES):
     """The parameters as the GPU uses them: hidden-to-hidden weights in bf16."""
-    flat = p32.astype(np.float64)
-    Ws, bs = M.unpack(flat.copy(), SHAPES)
-    for l in range(1, len(SHAPES) - 1):
-        Ws[l] = M.bf16_round(Ws[l])
-    return M.pack(Ws, bs)
+    return M.bf16_weights(p32.astype(np.float64), shapes)
+
+
+def assert_outputs_close(y, ref):
+    """Unit-vector outputs, element by element: every component within one
+    bf16 ulp of a unit-size value (2^-7), 99.9 % within 2^-9, the median
+    within 2^-16 (binary32 summation order)."""
+    d = np.abs(y - ref)
+    assert d.max() <= 2 * ULP, d.max() / ULP
+    assert np.percentile(d, 99.9) <= ULP / 2, np.percentile(d, 99.9) / ULP
+    assert np.median(d) <= 2.0 ** -16, np.median(d)
+
+
+def assert_gradients_close(grad, flat, shapes, cache, t, x):
+    """Every gradient element within one bf16 ulp of its scale, the sum of
+    absolute terms S = |dz|^T |h| (plus 1e-3 of the tensor's largest S,
+    for elements whose terms all vanish in the oracle); every tensor within
+    2e-3 in norm."""
+    Ws, bs = M.unpack(flat, shapes)
+    hs, zs, norm = cache["hs"], cache["zs"], cache["norm"]
+    n = len(t)
+    yh = hs[-1] / norm
+    dz = -(t - np.sum(yh * t, axis=1, keepdims=True) * yh) / norm / n
+    ref = M.backward(flat, shapes, cache, t, bf16=True)
+    Wr, br = M.unpack(ref, shapes)
+    Wg, bg = M.unpack(grad, shapes)
+    worst = 0.0
+    for l in range(len(shapes) - 1, -1, -1):
+        S = np.abs(dz).T @ np.abs(hs[l])
+        Sb = np.abs(dz).sum(axis=0)
+        for got, want, scale in ((Wg[l], Wr[l], S), (bg[l], br[l], Sb)):
+            tol = ULP * (scale + 1e-3 * scale.max())
+            r = np.abs(got - want) / tol
+            worst = max(worst, float(r.max()))
+            assert np.all(r <= 1.0), (l, float(r.max()), np.unravel_index(r.argmax(), r.shape))
+            assert np.linalg.norm(got - want) <= 2e-3 * np.linalg.norm(want), l
+        if l > 0:
+            dz = M.bf16_round((dz @ Ws[l]) * (zs[l - 1] > 0.0))
+    return worst
 
 
 def _batch(n, seed):
@@ -69,9 +110,8 @@ def test_mlp_forward_matches_oracle(torch_dev):
         crp.crp_mlp_destroy(mlp)
     finally:
         crp.crp_context_destroy(ctx)
-    ref, _ = M.forward(_oracle_view(p), SHAPES, x.astype(np.float64))
-    ang = M.angle_deg(y, ref)
-    assert np.median(ang) < 0.3 and np.max(ang) < 3.0, (np.median(ang), np.max(ang))
+    ref, _ = M.forward(_oracle_view(p), SHAPES, x.astype(np.float64), bf16=True)
+    assert_outputs_close(y, ref)
 
 
 def test_mlp_gradients_and_adam_match_oracle(torch_dev):
@@ -91,15 +131,9 @@ def test_mlp_gradients_and_adam_match_oracle(torch_dev):
     finally:
         crp.crp_context_destroy(ctx)
     flat = _oracle_view(p)
-    y, cache = M.forward(flat, SHAPES, x.astype(np.float64))
-    assert abs(loss0 - M.loss(y, t.astype(np.float64))) < 2e-3 * max(1.0, loss0)
-    ref = M.backward(flat, SHAPES, cache, t.astype(np.float64))
-    Wg, bg = M.unpack(g.astype(np.float64), SHAPES)
-    Wr, br = M.unpack(ref, SHAPES)
-    for l in range(len(SHAPES)):
-        for got, want in ((Wg[l], Wr[l]), (bg[l], br[l])):
-            rel = np.linalg.norm(got - want) / np.linalg.norm(want)
-            assert rel < 2e-2, (l, rel)
+    y, cache = M.forward(flat, SHAPES, x.astype(np.float64), bf16=True)
+    assert abs(loss0 - M.loss(y, t.astype(np.float64))) < 1e-4 * max(1.0, loss0)
+    assert_gradients_close(g.astype(np.float64), flat, SHAPES, cache, t.astype(np.float64), x)
     # Adam on the GPU's own gradient, first step
     p_ref, _, _ = M.adam(p.astype(np.float64), g1.astype(np.float64), 0.0, 0.0, 1, 1e-3)
     assert np.max(np.abs(p1 - p_ref)) < 1e-6 + 1e-5 * np.max(np.abs(p_ref))
@@ -154,13 +188,15 @@ def test_surrogate_lens_matches_oracle_network(torch_dev):
         crp.crp_context_destroy(ctx)
     x = np.concatenate([dirs.astype(np.float32), (np.log10(E) - 19.0).astype(np.float32)[:, None]],
                        axis=1).astype(np.float64)
-    y, _ = M.forward(_oracle_view(p), SHAPES, x)
+    y, _ = M.forward(_oracle_view(p), SHAPES, x, bf16=True)
     npix = 12 * nside * nside
     key = bins.astype(np.int64) * npix + oracle.ang2pix_vec(nside, y)
     counts = np.bincount(key, minlength=nb * npix)
     got_counts = np.diff(got["col_start"].astype(np.int64))
     assert got_counts.sum() == len(E)
-    assert np.abs(got_counts - counts).sum() <= 0.06 * len(E)
+    # a prediction moves across a pixel edge only where it lies within a
+    # bf16 ulp of that edge
+    assert np.abs(got_counts - counts).sum() <= 0.005 * len(E), np.abs(got_counts - counts).sum()
     earth = oracle.ang2pix_vec(nside, dirs)
     # every entry of a column is the Earth pixel of some sample of that column
     for c in np.nonzero(got_counts)[0][:50]:
@@ -194,11 +230,10 @@ def test_fused_tensor_core_forward_matches_layered(torch_dev, n):
     fused, layered = out[crp.MLP_PATH_TENSOR_CORE_FUSED], out[crp.MLP_PATH_LAYERED]
     assert np.all(np.isfinite(fused))
     assert np.allclose(np.linalg.norm(fused, axis=1), 1.0, atol=1e-5)
-    d = M.angle_deg(fused, layered)
-    assert np.median(d) < 0.05 and np.max(d) < 1.0, (np.median(d), np.max(d))
-    ref, _ = M.forward(_oracle_view(p), SHAPES, x.astype(np.float64))
-    a = M.angle_deg(fused, ref)
-    assert np.median(a) < 0.3 and np.max(a) < 3.0, (np.median(a), np.max(a))
+    assert_outputs_close(fused, layered)
+    ref, _ = M.forward(_oracle_view(p), SHAPES, x.astype(np.float64), bf16=True)
+    assert_outputs_close(fused, ref)
+    assert_outputs_close(layered, ref)
 
 
 @pytest.mark.parametrize("n", [2048, 128 * 37, 16384])
@@ -225,20 +260,12 @@ def test_tensor_core_training_gradients(torch_dev, n):
     finally:
         crp.crp_context_destroy(ctx)
     flat = _oracle_view(p)
-    y, cache = M.forward(flat, SHAPES, x.astype(np.float64))
-    ref = M.backward(flat, SHAPES, cache, t.astype(np.float64))
+    y, cache = M.forward(flat, SHAPES, x.astype(np.float64), bf16=True)
     lref = M.loss(y, t.astype(np.float64))
-    Wr, br = M.unpack(ref, SHAPES)
-    Wt, bt = M.unpack(grads[crp.MLP_PATH_AUTO], SHAPES)
-    Wl, bl = M.unpack(grads[crp.MLP_PATH_LAYERED], SHAPES)
     for path in losses:
-        assert abs(losses[path] - lref) < 2e-3 * max(1.0, lref), (path, losses[path], lref)
-    for l in range(len(SHAPES)):
-        for tc, lay, want in ((Wt[l], Wl[l], Wr[l]), (bt[l], bl[l], br[l])):
-            nw = np.linalg.norm(want)
-            assert np.linalg.norm(tc - want) / nw < 2e-2, (l, "tc vs oracle")
-            assert np.linalg.norm(lay - want) / nw < 2e-2, (l, "layered vs oracle")
-            assert np.linalg.norm(tc - lay) / nw < 1e-2, (l, "tc vs layered")
+        assert abs(losses[path] - lref) < 1e-4 * max(1.0, lref), (path, losses[path], lref)
+        worst = assert_gradients_close(grads[path], flat, SHAPES, cache, t.astype(np.float64), x)
+        print(f"n {n} path {path}: worst element / tolerance {worst:.3f}")
 
 
 @pytest.mark.parametrize("n_in,hidden,n_hidden", [(4, 512, 3), (12, 384, 3)])
@@ -271,19 +298,11 @@ def test_other_shapes_gradients_match_oracle(torch_dev, n_in, hidden, n_hidden):
         crp.crp_mlp_destroy(mlp)
     finally:
         crp.crp_context_destroy(ctx)
-    flat = p.astype(np.float64)
-    Ws, bs = M.unpack(flat.copy(), shapes)
-    for l in range(1, len(shapes) - 1):
-        Ws[l] = M.bf16_round(Ws[l])
-    flat = M.pack(Ws, bs)
-    y, cache = M.forward(flat, shapes, x.astype(np.float64))
-    assert abs(loss - M.loss(y, t.astype(np.float64))) < 2e-3 * max(1.0, loss)
-    ref = M.backward(flat, shapes, cache, t.astype(np.float64))
-    Wg, bg = M.unpack(grad, shapes)
-    Wr, br = M.unpack(ref, shapes)
-    for l in range(len(shapes)):
-        for got, want in ((Wg[l], Wr[l]), (bg[l], br[l])):
-            assert np.linalg.norm(got - want) / np.linalg.norm(want) < 2e-2, l
+    flat = _oracle_view(p, shapes)
+    y, cache = M.forward(flat, shapes, x.astype(np.float64), bf16=True)
+    assert abs(loss - M.loss(y, t.astype(np.float64))) < 1e-4 * max(1.0, loss)
+    worst = assert_gradients_close(grad, flat, shapes, cache, t.astype(np.float64), x)
+    print(f"shape ({n_in}, {hidden}, {n_hidden}): worst element / tolerance {worst:.3f}")
 
 
 def test_train_graph_replay_matches_eager(torch_dev):

@@ -816,3 +816,73 @@ def test_1d_pion_optical_depth(oracle):
     p = np.exp(-tau)
     assert 0.2 < p < 0.9
     assert abs(none - p) < 4 * np.sqrt(p * (1 - p) / n) + 2e-3, (none, p)
+
+
+def test_bf16_rounding_against_torch(oracle):
+    """The oracle's bfloat16 rounding against PyTorch's binary32 -> bfloat16
+    conversion (round to nearest, ties to even) on values spanning the range,
+    the rounding ties, and subnormals."""
+    import torch
+    import oracle.mlp as M
+    g = np.random.default_rng(5)
+    x = np.concatenate([g.normal(size=20000) * 10.0 ** g.uniform(-30, 30, 20000),
+                        1 + np.arange(-512, 512) * 2.0 ** -9,            # ties and neighbours
+                        np.array([0.0, -0.0, 1e-40, -1e-40, 3.0e38])]).astype(np.float32)
+    want = torch.from_numpy(x).to(torch.bfloat16).to(torch.float32).numpy().astype(np.float64)
+    got = M.bf16_round(x.astype(np.float64))
+    assert np.array_equal(got, want)
+
+
+def test_mlp_bf16_mode_explicit_loops(oracle):
+    """bf16 mode on a tiny network, restated as explicit loops: the hidden
+    weights, every hidden activation and every hidden backward signal are
+    rounded, the first / output layers' weights, the biases, the output and
+    dy are not."""
+    M, shapes, flat0, x, t = _tiny_mlp()
+    flat = M.bf16_weights(flat0, shapes)
+    Ws, bs = M.unpack(flat, shapes)
+    W0, b0 = M.unpack(flat0, shapes)
+    L = len(Ws)
+    for l in range(L):
+        want = M.bf16_round(W0[l]) if 0 < l < L - 1 else W0[l]
+        assert np.array_equal(Ws[l], want) and np.array_equal(bs[l], b0[l])
+        assert not np.array_equal(W0[l], M.bf16_round(W0[l]))   # rounding is visible
+    y, cache = M.forward(flat, shapes, x, bf16=True)
+    grad = M.backward(flat, shapes, cache, t, bf16=True)
+    gW, gb = M.unpack(grad, shapes)
+    n = len(x)
+    acts_all, dzs_all = [], []
+    for r in range(n):
+        hs = [list(x[r])]
+        for l, (W, b) in enumerate(zip(Ws, bs)):
+            out = []
+            for o in range(W.shape[0]):
+                acc = b[o]
+                for i in range(W.shape[1]):
+                    acc += W[o, i] * hs[-1][i]
+                if l < L - 1:
+                    acc = float(M.bf16_round(max(acc, 0.0)))
+                out.append(acc)
+            hs.append(out)
+        nrm = math.sqrt(sum(v * v for v in hs[-1]))
+        yh = [v / nrm for v in hs[-1]]
+        assert np.allclose(y[r], yh, rtol=0, atol=1e-13)
+        d = sum(a * b for a, b in zip(yh, t[r]))
+        dz = [-(t[r][k] - d * yh[k]) / nrm / n for k in range(3)]
+        dzs = [None] * L
+        dzs[L - 1] = dz
+        for l in range(L - 1, 0, -1):
+            W = Ws[l]
+            prev = []
+            for i in range(W.shape[1]):
+                acc = sum(dzs[l][o] * W[o, i] for o in range(W.shape[0]))
+                prev.append(float(M.bf16_round(acc if hs[l][i] > 0.0 else 0.0)))
+            dzs[l - 1] = prev
+        acts_all.append(hs)
+        dzs_all.append(dzs)
+    for l in range(L):
+        for o in range(Ws[l].shape[0]):
+            assert abs(gb[l][o] - sum(dzs_all[r][l][o] for r in range(n))) < 1e-13
+            for i in range(Ws[l].shape[1]):
+                want = sum(dzs_all[r][l][o] * acts_all[r][l][i] for r in range(n))
+                assert abs(gW[l][o, i] - want) < 1e-13
