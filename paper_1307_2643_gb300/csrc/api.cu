@@ -1277,6 +1277,11 @@ crp_status crp_propagate(crp_context* c, const crp_grid* g, const crp_modules* m
     set_error("crp_propagate: queue_order must be -1, 0 or 1");
     return CRP_E_INVALID;
   }
+  if (m->precision == CRP_MIXED && !(m->h_max / g->desc.spacing < 1048576.0)) {
+    set_error("crp_propagate: the mixed path needs a step to span fewer than 2^20 grid cells "
+              "(h_max / spacing = %g)", m->h_max / g->desc.spacing);
+    return CRP_E_INVALID;
+  }
   if (stats_out) memset(stats_out, 0, sizeof(*stats_out));
   if (c->size == 0) return CRP_OK;
   DeviceGuard dg(c->device);

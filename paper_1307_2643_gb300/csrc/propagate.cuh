@@ -94,6 +94,19 @@ __device__ __forceinline__ int64_t wrap_fl(double fl, int64_t n, int64_t mask) {
   return i;
 }
 
+// floor(r) for |r| < 2^22 without a conversion instruction: r + 1.5 * 2^23
+// lies in [2^23, 2^24), where the binary32 spacing is 1, so the sum rounded
+// toward -inf is 1.5 * 2^23 + floor(r) exactly; it gives floor(r) as a float
+// (fl) and, from its bit pattern, as an integer.  Both equal floorf(r) and
+// (int)floorf(r).  Outside that range the integer is meaningless but
+// wrap_int still maps it into the grid.
+__device__ __forceinline__ int floor_small(float r, float& fl) {
+  constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+  const float s = __fadd_rd(r, kMagic);
+  fl = s - kMagic;
+  return __float_as_int(s) - 0x4B400000;  // bit pattern of 1.5 * 2^23
+}
+
 __device__ __forceinline__ int wrap_int(int i, int n, int mask) {
   if (mask >= 0) return i & mask;
   i = i % n;
@@ -1155,12 +1168,15 @@ struct PolicyMixedT {
     const float rx = fmaf(ox, f.inv_spacing_f, c.frac[0]);
     const float ry = fmaf(oy, f.inv_spacing_f, c.frac[1]);
     const float rz = fmaf(oz, f.inv_spacing_f, c.frac[2]);
-    const float fx = floorf(rx), fy = floorf(ry), fz = floorf(rz);
+    // the offsets span fewer than 2^20 cells (checked on the host), so the
+    // in-cell coordinates stay within floor_small's range
+    float fx, fy, fz;
+    const int jx = floor_small(rx, fx), jy = floor_small(ry, fy), jz = floor_small(rz, fz);
     const float tx = rx - fx, ty = ry - fy, tz = rz - fz;
     const int nx = (int)f.n[0], ny = (int)f.n[1], nz = (int)f.n[2];
-    const int ix0 = wrap_int(c.cell[0] + (int)fx, nx, (int)f.mask[0]);
-    const int iy0 = wrap_int(c.cell[1] + (int)fy, ny, (int)f.mask[1]);
-    const int iz0 = wrap_int(c.cell[2] + (int)fz, nz, (int)f.mask[2]);
+    const int ix0 = wrap_int(c.cell[0] + jx, nx, (int)f.mask[0]);
+    const int iy0 = wrap_int(c.cell[1] + jy, ny, (int)f.mask[1]);
+    const int iz0 = wrap_int(c.cell[2] + jz, nz, (int)f.mask[2]);
     float3 B;
     if (std::is_same<NodeT, float4>::value && f.cells) {
       // one aligned 128-byte record: the cell's trilinear polynomial,
@@ -1387,9 +1403,10 @@ struct PolicyMixedT {
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         const float r = fmaf(c.dx[d], p.f.inv_spacing_f, c.frac[d]);
-        const float fl = floorf(r);
+        float fl;
+        const int j = floor_small(r, fl);
         c.frac[d] = r - fl;
-        c.cell[d] = wrap_int(c.cell[d] + (int)fl, (int)p.f.n[d], (int)p.f.mask[d]);
+        c.cell[d] = wrap_int(c.cell[d] + j, (int)p.f.n[d], (int)p.f.mask[d]);
       }
       if constexpr (GAL) {
 #pragma unroll
