@@ -197,9 +197,8 @@ crp_status crp_tables_set_decay(crp_tables* t, int64_t n, const int32_t* A, cons
  * Candidates (Sect. 3, source model: position, spectrum, composition).
  * Structure of arrays, n entries each, host or device memory (on_device).
  * Appended to the pool; ids are id[i], or first_id + i when id is NULL.
- * Directions must be unit vectors.  1 <= A <= CRP_MAX_A, 0 <= Z <= A.
+ * Directions must be unit vectors.  A >= 1, 0 <= Z <= A.
  * ---------------------------------------------------------------------- */
-#define CRP_MAX_A 1024
 typedef struct {
   const uint64_t* id;                        /* optional */
   const double *x, *y, *z;                   /* position (length unit)   */

@@ -232,7 +232,7 @@ __global__ void k_inject_init(DevState st, uint64_t base, uint64_t n, uint64_t f
     const double un = ux * ux + uy * uy + uz * uz;
     const int A = st.A[i], Z = st.Z[i], q = st.q[i];
     const double E = st.E[i];
-    const bool ok = A >= 1 && A <= CRP_MAX_A && Z >= 0 && Z <= A && (q == 1 || q == -1) && E > 0.0 &&
+    const bool ok = A >= 1 && Z >= 0 && Z <= A && (q == 1 || q == -1) && E > 0.0 &&
                     E < (double)INFINITY && fabs(un - 1.0) < 1e-6 && st.s_max[i] >= 0.0;
     if (!ok) atomicAdd(bad, 1u);
     st.parent[i] = 0;
@@ -1010,9 +1010,9 @@ crp_status crp_candidates_inject(crp_context* c, const crp_candidate_arrays* a, 
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fail_cuda(e, "crp_candidates_inject");
   if (c->hc->error_word) {
-    set_error("crp_candidates_inject: %u invalid candidates (need 1 <= A <= %d, 0 <= Z <= A, q = +-1, "
+    set_error("crp_candidates_inject: %u invalid candidates (need A >= 1, 0 <= Z <= A, q = +-1, "
               "finite E > 0, |u| = 1, s_max >= 0); nothing injected",
-              c->hc->error_word, CRP_MAX_A);
+              c->hc->error_word);
     return CRP_E_INVALID;
   }
   c->size += n;

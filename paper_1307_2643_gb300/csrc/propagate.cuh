@@ -107,25 +107,6 @@ __device__ __forceinline__ int floor_small(float r, float& fl) {
   return __float_as_int(s) - 0x4B400000;  // bit pattern of 1.5 * 2^23
 }
 
-// Exact binary32 -> binary64 widening by integer operations: a normal
-// binary32 keeps its sign and significand and re-biases its exponent
-// (127 -> 1023); zero, subnormals, infinities and NaN take the conversion
-// instruction (rare here: step increments).  Equals (double)f.
-__device__ __forceinline__ double widen_f32(float f) {
-  const uint32_t b = __float_as_uint(f);
-  const uint32_t e = (b >> 23) & 0xffu;
-  if (__builtin_expect(e == 0u || e == 0xffu, 0)) return (double)f;
-  const uint64_t d = ((uint64_t)(b & 0x80000000u) << 32) | ((uint64_t)(e + 896u) << 52) |
-                     ((uint64_t)(b & 0x7fffffu) << 29);
-  return __longlong_as_double((long long)d);
-}
-
-// Exact int -> binary32 for 0 <= i < 2^23: i placed in the significand of
-// 2^23, minus 2^23.  Equals (float)i.
-__device__ __forceinline__ float small_int_f32(int i) {
-  return __int_as_float(0x4B000000 | i) - 8388608.0f;
-}
-
 __device__ __forceinline__ int wrap_int(int i, int n, int mask) {
   if (mask >= 0) return i & mask;
   i = i % n;
@@ -1401,11 +1382,11 @@ struct PolicyMixedT {
   __device__ __forceinline__ static int finish_step(const KParams& p, Lane& c,
                                                     LaneCounters& lc) {
     const float hf = c.hf;
-    const double h = widen_f32(hf);
+    const double h = (double)hf;
     const double x_old[3] = {c.x[0], c.x[1], c.x[2]};
-    c.x[0] = c.x[0] + widen_f32(c.dx[0]);
-    c.x[1] = c.x[1] + widen_f32(c.dx[1]);
-    c.x[2] = c.x[2] + widen_f32(c.dx[2]);
+    c.x[0] = c.x[0] + (double)c.dx[0];
+    c.x[1] = c.x[1] + (double)c.dx[1];
+    c.x[2] = c.x[2] + (double)c.dx[2];
     const float inv = rsqrtf(c.u5[0] * c.u5[0] + c.u5[1] * c.u5[1] + c.u5[2] * c.u5[2]);
     c.u[0] = c.u5[0] * inv;
     c.u[1] = c.u5[1] * inv;
@@ -1445,10 +1426,9 @@ struct PolicyMixedT {
     if (mflags<FIX>(p) & (CRP_PAIR | CRP_ADIABATIC)) {
       float beta = 0.f;
       if (mflags<FIX>(p) & CRP_PAIR) {
-        const float Af = small_int_f32(c.A);  // 1 <= A <= 64
-        const float g = c.E_f / (Af * (float)MP_C2_EV);
+        const float g = c.E_f / ((float)c.A * (float)MP_C2_EV);
         const float bp = table_f32(p, p.t_beta_f, __logf(g));
-        beta = bp * small_int_f32(c.Z * c.Z) / Af;
+        beta = bp * (float)(c.Z * c.Z) / (float)c.A;
       }
       if (mflags<FIX>(p) & CRP_ADIABATIC) beta += p.beta_ad_f;
       // (1 - yl)(1 - x) = 1 - (yl + x - x yl): yl stays small, so its binary32
