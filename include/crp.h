@@ -199,6 +199,10 @@ crp_status crp_tables_set_decay(crp_tables* t, int64_t n, const int32_t* A, cons
  * Appended to the pool; ids are id[i], or first_id + i when id is NULL.
  * Directions must be unit vectors.  A >= 1, 0 <= Z <= A.
  * ---------------------------------------------------------------------- */
+/* Accepted steps between the mixed path's exact rebases of a candidate's
+ * binary32 cell coordinates on its binary64 position. */
+#define CRP_MIXED_REBASE_STEPS 128
+
 typedef struct {
   const uint64_t* id;                        /* optional */
   const double *x, *y, *z;                   /* position (length unit)   */
@@ -314,7 +318,10 @@ typedef struct {
   int32_t blocks_per_sm;     /* resident blocks per SM (0 = occupancy maximum) */
   uint32_t slice;            /* accepted steps a lane runs on one candidate before
                                 requeueing it for the next round (0 = 2^20: in
-                                practice to the end) */
+                                practice to the end); the mixed path rounds it up
+                                to a multiple of CRP_MIXED_REBASE_STEPS, its period
+                                of exact rebases, so that results do not depend
+                                on it */
   int32_t queue_order;       /* order of each round's work queue (counting sort
                                 on 15-bit keys): 0 = lowest rigidity E/Z first
                                 (the longest histories start first), 1 = by grid
@@ -619,7 +626,7 @@ crp_status crp_redshift_of_distance(const crp_cosmology* cosmo, double length_un
  * the context is left exactly as it was.  The fastest configuration is
  * written into m (block_size, blocks_per_sm, slice, queue_order) and *out.
  * Results of a propagation do not depend on these settings (every slice
- * tried is a multiple of 32), so tuning changes speed only.  Needs a
+ * tried is a multiple of CRP_MIXED_REBASE_STEPS), so tuning changes speed only.  Needs a
  * device snapshot of the pool (its payload size); CRP_E_INVALID if no
  * candidates are injected. */
 typedef struct crp_tune_result {

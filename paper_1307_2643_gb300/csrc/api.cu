@@ -135,7 +135,7 @@ namespace {
 constexpr size_t kAlign = 256;
 // Default slice: 2^20 accepted steps, i.e. a lane keeps its candidate to the
 // end in practice (measured faster than requeueing every 512 steps: no
-// round tails); a multiple of 32, the mixed path's rebase period.
+// round tails); a multiple of the mixed path's rebase period.
 constexpr uint32_t kDefaultSlice = 1u << 20;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
@@ -1395,6 +1395,11 @@ crp_status crp_propagate(crp_context* c, const crp_grid* g, const crp_modules* m
     e = cudaGetLastError();
   }
   kp.slice = m->slice ? m->slice : kDefaultSlice;
+  if (m->precision == CRP_MIXED && kp.slice % CRP_MIXED_REBASE_STEPS) {
+    const uint64_t up = ((uint64_t)kp.slice / CRP_MIXED_REBASE_STEPS + 1) * CRP_MIXED_REBASE_STEPS;
+    kp.slice = up > 0xffffffffull ? (0xffffffffu / CRP_MIXED_REBASE_STEPS) * CRP_MIXED_REBASE_STEPS
+                                  : (uint32_t)up;
+  }
   crp_status st = CRP_OK;
   uint32_t launches = 0;
   float total_ms = 0.f;
@@ -1762,7 +1767,7 @@ void context_view(const crp_context* c, const int32_t** status, const double** E
 // candidates (each from the same snapshot, each for a fixed number of
 // accepted steps) and keep the fastest.  Results do not depend on the launch
 // configuration (binary64 path: bit for bit; mixed path: slices are kept
-// multiples of the 32-step rebase period), so tuning changes only speed.
+// multiples of the mixed path's rebase period), so tuning changes only speed.
 // ---------------------------------------------------------------------------
 extern "C" crp_status crp_autotune(crp_context* c, const crp_grid* g, crp_modules* m,
                                    uint64_t steps_per_trial, crp_tune_result* out, void* stream) {

@@ -1048,6 +1048,17 @@ struct PolicyFP64T {
 // ---------------------------------------------------------------------------
 enum : int { CAP_NONE = 0, CAP_S = 1, CAP_PION = 2, CAP_PD = 3, CAP_ND = 4 };
 
+// Accepted steps between exact rebases of a lane's binary32 cell coordinates
+// on its binary64 position (and folds of its binary32 energy losses).  Each
+// step adds one binary32 rounding (<= 2^-24 of a cell) to the in-cell
+// coordinates, so after 128 steps they are within about 10^-6 of a cell of
+// the binary64 position.  A rebase is about twenty binary64 operations that
+// only the rebasing lanes of a warp execute, so a shorter period spends the
+// binary64 pipe on nearly empty warp instructions.  Slices are rounded up to
+// multiples of this period, so the rebase points depend only on each
+// candidate's step count.
+constexpr int kRebasePeriod = CRP_MIXED_REBASE_STEPS;
+
 template <bool GAL, bool GMF = false, uint32_t FIX = 0, bool NUC = false>
 struct PolicyMixedT {
   static constexpr uint32_t kFix = FIX;  // compile-time module list (0: run-time flags)
@@ -1397,7 +1408,7 @@ struct PolicyMixedT {
     c.hn = fminf(fmaxf(hf * grow, p.h_min_f), p.h_max_f);
     count_step(c, lc);
     // field-lookup coordinate: advance in binary32, exact rebase every 32 steps
-    if (++c.since_rebase >= 32) {
+    if (++c.since_rebase >= kRebasePeriod) {
       rebase(p, c);
     } else {
 #pragma unroll

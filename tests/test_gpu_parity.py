@@ -564,8 +564,8 @@ EGAL_FLAGS = crp.PAIR | crp.ADIABATIC | crp.PION | crp.EMIN | crp.OBSERVER
 @pytest.mark.parametrize("flags", [INTERACTION_FLAGS, EGAL_FLAGS])
 def test_mixed_launch_configuration_does_not_change_results(field_f32_small, tables, flags):
     """The mixed path's results do not depend on block size, register
-    variant, queue order or slice (slices are multiples of its 32-step
-    rebase period).  Both module lists here (with and without
+    variant, queue order or slice (the library rounds slices up to multiples
+    of its rebase period, so the 64-step slice here runs as 128).  Both module lists here (with and without
     photodisintegration) have kernels that fix the list at compile time: the
     256 x 2 launch runs those, the other launches the generic kernel, and
     all give the same bytes."""
