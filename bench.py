@@ -1385,7 +1385,7 @@ def run_lens(args):
                      "bytes_per_candidate": LENS_HBM_BYTES_PER_CANDIDATE,
                      "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else None},
         "fp64_peak_tflops_measured": probe["fp64_tflops"], "clocks": clocks,
-        "gpu_launches": args.steps}))
+        "gpu_launches": 2 * args.steps}))
 
 if __name__ == "__main__":
     a = parse()

@@ -1751,6 +1751,14 @@ void context_pool(const crp_context* c, DevState* st, uint64_t* n, int* device, 
   *seed = c->seed;
 }
 
+// Work space of a context for other translation units: one index list of
+// pool capacity (the first work queue, free outside crp_propagate) and a
+// device counter.
+void context_scratch(const crp_context* c, uint32_t** list, unsigned long long** counter) {
+  *list = c->queue[0];
+  *counter = c->dc ? &c->dc->lens_fallback : nullptr;
+}
+
 // Read-only view of a context's pool for other translation units of the
 // library (status and energy arrays, pool size, device).
 void context_view(const crp_context* c, const int32_t** status, const double** E, uint64_t* n,

@@ -65,6 +65,7 @@ struct DevCounters {
   unsigned int stop;               // set when the step budget or deadline ran out
   unsigned long long n_in;         // graph mode: entries of this round's input queue
   unsigned long long rounds;       // graph mode: rounds run
+  unsigned long long lens_fallback;  // lens application: candidates left to binary64
 };
 
 struct FieldView {

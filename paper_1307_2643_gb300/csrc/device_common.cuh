@@ -282,9 +282,12 @@ __device__ __forceinline__ float one_minus_abs_f32(double z) {
 // it the binary32 floor equals the exact floor and so the binary64 one,
 // inside it the binary64 path decides.  Only 32-bit integer conversions and
 // binary32 arithmetic run outside the guard band.
+// The binary32 part of healpix_ring_pixel_guarded: true, with the pixel, when
+// every floor it takes is outside its guard band (the pixel then equals the
+// binary64 one); false when the binary64 computation must decide.
 template <bool NEG>
-__device__ __forceinline__ int64_t healpix_ring_pixel_guarded(int64_t nside, double ux,
-                                                              double uy, double uz) {
+__device__ __forceinline__ bool healpix_ring_pixel_try(int64_t nside, double ux, double uy,
+                                                       double uz, int64_t* out) {
   const float sg = NEG ? -1.f : 1.f;
   const float fx = sg * f32_trunc(ux), fy = sg * f32_trunc(uy), fz = sg * f32_trunc(uz);
   const int ns_i = (int)nside;
@@ -326,7 +329,16 @@ __device__ __forceinline__ int64_t healpix_ring_pixel_guarded(int64_t nside, dou
       }
     }
   }
-  if (ok) return pix;
+  *out = pix;
+  return ok;
+}
+
+// The pixel: the binary32 part's when it is sure, else the binary64 one.
+template <bool NEG>
+__device__ __forceinline__ int64_t healpix_ring_pixel_guarded(int64_t nside, double ux,
+                                                              double uy, double uz) {
+  int64_t pix;
+  if (healpix_ring_pixel_try<NEG>(nside, ux, uy, uz, &pix)) return pix;
   return NEG ? healpix_ring_pixel(nside, -ux, -uy, -uz) : healpix_ring_pixel(nside, ux, uy, uz);
 }
 

@@ -25,6 +25,7 @@ namespace crp {
 void context_view(const crp_context* c, const int32_t** status, const double** E, uint64_t* n,
                   int* device);
 void context_pool(const crp_context* c, DevState* st, uint64_t* n, int* device, uint64_t* seed);
+void context_scratch(const crp_context* c, uint32_t** list, unsigned long long** counter);
 }  // namespace crp
 
 using namespace crp;
@@ -202,54 +203,104 @@ __device__ __forceinline__ bool lens_bin_f32(double E, int Z, float inv_rlo_f, f
 // entries[min(floor(u2 * count_j), count_j - 1)] of the column.  Each integer
 // decision is first taken in binary32 with a guard from its error bound and
 // in binary64 only inside the guard, so the result is the binary64 one.
-__global__ void k_lens_apply(DevState st, uint64_t n, int what, uint64_t seed, int64_t nside,
-                             int64_t npix, int n_bins, double lg_lo, double inv_dlg,
-                             float inv_rlo_f, float inv_f, int use_f32,
-                             const uint32_t* col_start, const uint32_t* entries,
-                             const uint32_t* max_count) {
-  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < n;
-       k += (uint64_t)gridDim.x * blockDim.x) {
-    if (!pick(what, st.status[k])) continue;
-    const int Z = st.Z[k];
-    if (Z <= 0) {
-      st.lens_pixel[k] = kNotApplied;
-      continue;
-    }
-    const double E = st.E[k];
-    int b32;
-    const int64_t b = use_f32 && lens_bin_f32(E, Z, inv_rlo_f, inv_f, n_bins, &b32)
-                          ? (int64_t)b32
-                          : lens_bin_f64(E, Z, lg_lo, inv_dlg, n_bins);
-    const int64_t j = healpix_ring_pixel_guarded<true>(nside, st.ux[k], st.uy[k], st.uz[k]);
-    const int64_t col = b * npix + j;
-    const uint32_t start = col_start[col];
-    const uint32_t count = col_start[col + 1] - start;
-    uint32_t out = kNotObserved;
-    if (count > 0) {
-      const uint32_t mxi = max_count[b];
-      const Philox4 w = draw4(seed, 3u, st.id[k], 0u);
-      // u1 lies in [h1, h1 + 2^-24) with h1 its top 24 bits (exact in
-      // binary32): u1 * max_count is known to 2.4e-7 * max_count
-      const float mxf = (float)mxi, cf = (float)count;
-      const float p1 = (float)(w.v1 >> 8) * 5.9604644775390625e-8f * mxf;
-      bool observed;
-      if (fabsf(p1 - cf) > 2e-6f * mxf)
-        observed = p1 < cf;
-      else
-        observed = u01_open(w.v0, w.v1) * (double)mxi < (double)count;
-      if (observed) {
-        int pk32;
-        int64_t pk;
-        const float p2 = (float)(w.v3 >> 8) * 5.9604644775390625e-8f * cf;
-        if (floor_sure(p2, 2e-6f * cf, &pk32)) {
-          pk = pk32;
-        } else {
-          pk = (int64_t)(u01_open(w.v2, w.v3) * (double)count);
-          if (pk > (int64_t)count - 1) pk = (int64_t)count - 1;
+// Lens application in two passes.  The first decides, in binary32, every
+// candidate whose decisions (rigidity bin, border pixel, observed or not,
+// pick) are all outside their guard bands -- each such decision equals the
+// binary64 one -- and appends the others to a list (one atomic per warp).
+// The second runs the binary64 decisions over that list with full warps, so
+// no warp of the first pass waits on binary64 code.
+struct LensArgs {
+  uint64_t seed;
+  int64_t nside, npix;
+  int n_bins, use_f32;
+  double lg_lo, inv_dlg;
+  float inv_rlo_f, inv_f;
+  const uint32_t* col_start;
+  const uint32_t* entries;
+  const uint32_t* max_count;
+};
+
+// The Earth pixel from a column (start, count): observed when u1 max_count <
+// count, then entry floor(u2 count) (binary64 decisions).
+__device__ __forceinline__ uint32_t lens_pick_f64(const LensArgs& a, const Philox4& w,
+                                                  uint32_t start, uint32_t count, uint32_t mxi) {
+  if (!(u01_open(w.v0, w.v1) * (double)mxi < (double)count)) return kNotObserved;
+  int64_t pk = (int64_t)(u01_open(w.v2, w.v3) * (double)count);
+  if (pk > (int64_t)count - 1) pk = (int64_t)count - 1;
+  return a.entries[start + pk];
+}
+
+__global__ void k_lens_apply_f32(DevState st, uint64_t n, int what, LensArgs a,
+                                 uint32_t* fallback, unsigned long long* n_fallback) {
+  const int lane = threadIdx.x & 31;
+  for (uint64_t base = blockIdx.x * (uint64_t)blockDim.x; base < n;
+       base += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = base + threadIdx.x;
+    bool defer = false;
+    if (k < n && pick(what, st.status[k])) {
+      const int Z = st.Z[k];
+      if (Z <= 0) {
+        st.lens_pixel[k] = kNotApplied;
+      } else {
+        int b, pk32;
+        int64_t j;
+        bool sure = a.use_f32 && lens_bin_f32(st.E[k], Z, a.inv_rlo_f, a.inv_f, a.n_bins, &b);
+        sure = sure && healpix_ring_pixel_try<true>(a.nside, st.ux[k], st.uy[k], st.uz[k], &j);
+        if (sure) {
+          const int64_t col = (int64_t)b * a.npix + j;
+          const uint32_t start = a.col_start[col];
+          const uint32_t count = a.col_start[col + 1] - start;
+          uint32_t out = kNotObserved;
+          if (count > 0) {
+            const uint32_t mxi = a.max_count[b];
+            const Philox4 w = draw4(a.seed, 3u, st.id[k], 0u);
+            // u1 lies in [h1, h1 + 2^-24) with h1 its top 24 bits (exact in
+            // binary32): u1 * max_count is known to 2.4e-7 * max_count
+            const float mxf = (float)mxi, cf = (float)count;
+            const float p1 = (float)(w.v1 >> 8) * 5.9604644775390625e-8f * mxf;
+            if (fabsf(p1 - cf) > 2e-6f * mxf) {
+              if (p1 < cf) {
+                const float p2 = (float)(w.v3 >> 8) * 5.9604644775390625e-8f * cf;
+                if (floor_sure(p2, 2e-6f * cf, &pk32))
+                  out = a.entries[start + pk32];
+                else
+                  sure = false;
+              }
+            } else {
+              sure = false;
+            }
+          }
+          if (sure) st.lens_pixel[k] = out;
         }
-        out = entries[start + pk];
+        defer = !sure;
       }
     }
+    // append the undecided candidates of this warp to the list
+    const unsigned m = __ballot_sync(0xffffffffu, defer);
+    if (m) {
+      unsigned long long slot = 0;
+      const int leader = __ffs(m) - 1;
+      if (lane == leader) slot = atomicAdd(n_fallback, (unsigned long long)__popc(m));
+      slot = __shfl_sync(0xffffffffu, slot, leader);
+      if (defer) fallback[slot + __popc(m & ((1u << lane) - 1u))] = (uint32_t)k;
+    }
+  }
+}
+
+__global__ void k_lens_apply_f64(DevState st, LensArgs a, const uint32_t* fallback,
+                                 const unsigned long long* n_fallback) {
+  const uint64_t m = *n_fallback;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = fallback[i];
+    const int64_t b = lens_bin_f64(st.E[k], st.Z[k], a.lg_lo, a.inv_dlg, a.n_bins);
+    const int64_t j = healpix_ring_pixel(a.nside, -st.ux[k], -st.uy[k], -st.uz[k]);
+    const int64_t col = b * a.npix + j;
+    const uint32_t start = a.col_start[col];
+    const uint32_t count = a.col_start[col + 1] - start;
+    uint32_t out = kNotObserved;
+    if (count > 0) out = lens_pick_f64(a, draw4(a.seed, 3u, st.id[k], 0u), start, count,
+                                       a.max_count[b]);
     st.lens_pixel[k] = out;
   }
 }
@@ -631,10 +682,33 @@ crp_status crp_lens_apply(crp_context* ctx, const crp_lens* L, int32_t what, voi
   // binary32 bin decisions need 1 / r_lo and inv_dlg as normal binary32 numbers
   const float inv_rlo_f = (float)(1.0 / L->r_lo), inv_f = (float)inv;
   const int use_f32 = std::isnormal(inv_rlo_f) && std::isnormal(inv_f) ? 1 : 0;
-  k_lens_apply<<<blocks(n, 256), 256, 0, s>>>(st, n, what, seed, L->nside, L->npix, L->n_bins,
-                                              lg_lo, inv, inv_rlo_f, inv_f, use_f32,
-                                              L->col_start, L->entries, L->max_count);
-  cudaError_t e = cudaGetLastError();
+  LensArgs a;
+  a.seed = seed;
+  a.nside = L->nside;
+  a.npix = L->npix;
+  a.n_bins = L->n_bins;
+  a.use_f32 = use_f32;
+  a.lg_lo = lg_lo;
+  a.inv_dlg = inv;
+  a.inv_rlo_f = inv_rlo_f;
+  a.inv_f = inv_f;
+  a.col_start = L->col_start;
+  a.entries = L->entries;
+  a.max_count = L->max_count;
+  uint32_t* list = nullptr;
+  unsigned long long* cnt = nullptr;
+  context_scratch(ctx, &list, &cnt);
+  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) {
+    k_lens_apply_f32<<<blocks(n, 256), 256, 0, s>>>(st, n, what, a, list, cnt);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    k_lens_apply_f64<<<(unsigned)(sms > 0 ? sms : 1) * 4, 256, 0, s>>>(st, a, list, cnt);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (prev >= 0 && prev != device) cudaSetDevice(prev);
   return e == cudaSuccess ? CRP_OK : fail_cuda(e, "crp_lens_apply");
