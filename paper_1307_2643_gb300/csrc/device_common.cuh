@@ -310,7 +310,10 @@ __device__ __forceinline__ bool healpix_ring_pixel_try(int64_t nside, double ux,
       const int ir = ns_i + 1 + jp - jm;
       const int kshift = 1 - (ir & 1);
       int ip = (jp + jm - ns_i + kshift + 1) / 2;
-      ip = ((ip % (4 * ns_i)) + 4 * ns_i) % (4 * ns_i);
+      // jp, jm in [0, 5 nside] put ip in [-nside / 2, 4.5 nside + 1], inside
+      // [-M, 2M) for M = 4 nside: one conditional add or subtract is ip mod M
+      const int M = 4 * ns_i;
+      ip = ip < 0 ? ip + M : (ip >= M ? ip - M : ip);
       pix = 2 * nside * (nside - 1) + (int64_t)(ir - 1) * 4 * nside + ip;
     } else {
       const float tp = tt - (float)itt;
@@ -320,7 +323,9 @@ __device__ __forceinline__ bool healpix_ring_pixel_try(int64_t nside, double ux,
       const int ir = jp + jm + 1;
       ok = ok & floor_sure(tt * (float)ir, g, &ip);
       if (ok) {
-        ip = ((ip % (4 * ir)) + 4 * ir) % (4 * ir);
+        // tt in [0, 4] puts ip in [0, 4 ir]: ip mod 4 ir by one subtraction
+        if (ip >= 4 * ir) ip -= 4 * ir;
+        if (ip < 0) ip += 4 * ir;
         // the sign of z from its bits: z > +0 exactly when the int64 is > 0
         const bool north = NEG ? __double_as_longlong(uz) < 0 && (__double_as_longlong(uz) << 1) != 0
                                : __double_as_longlong(uz) > 0;
