@@ -1006,6 +1006,55 @@ def run_cosmology(args):
     print(json.dumps(out))
 
 
+HYBRID_MAX_DEG = 0.5   # a bin's surrogate columns are used where its validated median is at most this
+
+
+def lens_bin_of(R, w):
+    """Rigidity bin of the lens (log bins over [r_lo, r_hi])."""
+    t = np.log(R / w["r_lo"]) / np.log(w["r_hi"] / w["r_lo"]) * w["n_bins"]
+    return np.clip(np.floor(t).astype(np.int64), 0, w["n_bins"] - 1)
+
+
+def chaos_floor(crp, ctx, grid, w, analytic, delta_deg, bands, triplets=500, seed=3):
+    """Interpolation floor of the border-direction map at sample spacing
+    delta_deg, per rigidity band: arrival directions u - delta, u, u + delta
+    on a great circle (one rigidity, log-uniform in the band) are back-tracked
+    by the binary64 path, and the floor is the median angle between the
+    border direction of u and the normalised mean of its two neighbours'.
+    A map smooth at that scale gives O(delta^2); structure below the spacing
+    gives an error no fit to samples that far apart can be expected to beat."""
+    mods = crp.modules(precision=crp.FP64, tol=w["tol"], h_min=w["h_min"], h_max=w["h_max"],
+                       field_unit_T=crp.MICROGAUSS_T, length_unit_m=crp.KPC_M,
+                       border_radius=w["border_r"], **analytic)
+    g = np.random.default_rng(seed)
+    out = {}
+    d = np.radians(delta_deg)
+    k = triplets
+    for lo, hi in zip(bands[:-1], bands[1:]):
+        u = g.normal(size=(k, 3))
+        u /= np.linalg.norm(u, axis=1)[:, None]
+        v = np.cross(u, g.normal(size=(k, 3)))
+        v /= np.linalg.norm(v, axis=1)[:, None]
+        R = 10 ** g.uniform(lo, hi, k)
+        dd = np.concatenate([u, np.cos(d) * u + np.sin(d) * v, np.cos(d) * u - np.sin(d) * v])
+        RR, m = np.concatenate([R, R, R]), 3 * k
+        inj = crp.host_injection(dict(x=np.full(m, w["earth"][0]), y=np.full(m, w["earth"][1]),
+                                      z=np.full(m, w["earth"][2]), ux=dd[:, 0], uy=dd[:, 1],
+                                      uz=dd[:, 2], E=RR, A=np.ones(m), Z=np.ones(m),
+                                      q=-np.ones(m)))
+        crp.crp_candidates_clear(ctx)
+        crp.crp_candidates_inject(ctx, crp.candidate_arrays(inj), m)
+        crp.crp_propagate(ctx, grid, mods)
+        rec = crp.crp_collect(ctx, crp.COLLECT_ALL)
+        rec = rec[np.argsort(rec["id"], kind="stable")]
+        b0, bp, bm = rec["u"][:k], rec["u"][k:2 * k], rec["u"][2 * k:]
+        mid = bp + bm
+        mid /= np.linalg.norm(mid, axis=1)[:, None]
+        out[f"{lo:.1f}-{hi:.1f}"] = round(float(np.median(np.degrees(
+            np.arccos(np.clip(np.sum(b0 * mid, axis=1), -1.0, 1.0))))), 3)
+    return out
+
+
 def run_galactic(args, keep=False):
     """Galactic workload: back-track antiprotons from Earth through the
     synthetic galactic field (disk + halo + 256^3 random component), train the
@@ -1063,6 +1112,10 @@ def run_galactic(args, keep=False):
     t_all = rec["u"].astype(np.float32)
     tr = np.nonzero(ok[: args.n_train])[0]
     te = args.n_train + np.nonzero(ok[args.n_train:])[0]
+    # validation samples (from the training draw, not trained on): they decide
+    # which lens bins the hybrid lens takes from the surrogate
+    n_val = min(200_000, len(tr) // 20) // 128 * 128
+    va, tr = tr[:n_val], tr[n_val:]
     # ---- training ---------------------------------------------------------
     mlp = crp.crp_mlp_create(ctx, 4, 256, 4, w["seed"])
     B = args.batch
@@ -1110,6 +1163,30 @@ def run_galactic(args, keep=False):
     Rt = R[te[:n_te]]
     ident = np.degrees(np.arccos(np.clip(np.sum(dirs[te[:n_te]] * tt, axis=1)
                                          / np.linalg.norm(tt, axis=1), -1.0, 1.0)))
+    # per lens bin: validated median (claims) and held-out median
+    crp.crp_mlp_set_forward_path(mlp, crp.MLP_PATH_AUTO)
+    xv = torch.from_numpy(x_all[va]).cuda()
+    yv = torch.zeros((len(va), 3), dtype=torch.float32, device="cuda")
+    crp.crp_mlp_forward(mlp, xv, yv, len(va))
+    tv = t_all[va].astype(np.float64)
+    yvh = yv.cpu().numpy().astype(np.float64)
+    ang_v = np.degrees(np.arccos(np.clip(np.sum(yvh * tv, axis=1) / (
+        np.linalg.norm(yvh, axis=1) * np.linalg.norm(tv, axis=1)), -1.0, 1.0)))
+    bv, bt = lens_bin_of(R[va], w), lens_bin_of(Rt, w)
+    val_med = np.full(w["n_bins"], np.inf)
+    test_med = np.full(w["n_bins"], np.inf)
+    for b in range(w["n_bins"]):
+        if (bv == b).sum() >= 100:
+            val_med[b] = np.median(ang_v[bv == b])
+        if (bt == b).sum() >= 100:
+            test_med[b] = np.median(ang[bt == b])
+    claim = val_med <= HYBRID_MAX_DEG
+    # chaos floor per 0.1-decade band: at the training set's angular spacing
+    # per lens bin, and at 0.2 deg
+    bands = np.round(np.arange(18.0, 20.001, 0.1), 1)
+    spacing = float(np.degrees(np.sqrt(4 * np.pi / (len(tr) / w["n_bins"]))))
+    floor_train = chaos_floor(crp, ctx, grid, w, analytic, spacing, bands)
+    floor_02 = chaos_floor(crp, ctx, grid, w, analytic, 0.2, bands)
     q_edges = 10.0 ** np.arange(18.0, 20.01, 0.25)
     by_q = {f"{np.log10(lo):.2f}-{np.log10(hi):.2f}":
             [round(float(np.median(ang[(Rt >= lo) & (Rt < hi)])), 3),
@@ -1129,12 +1206,37 @@ def run_galactic(args, keep=False):
                                            w["r_hi"], ldirs, lE, lbins)
     torch.cuda.synchronize()
     t_lens_sg = time.perf_counter() - t0
+    # hybrid lens: back-track only the samples of the bins the surrogate does
+    # not claim, take the claimed bins from the surrogate
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    keep_bt = ~claim[lbins]
+    if claim.all():
+        lens_hy = crp.crp_lens_merge(lens_sg, lens_sg, claim)
+        torch.cuda.synchronize()
+    elif claim.any():
+        part_bt, _ = crp.crp_lens_build(ctx, grid, mods, w["nside"], w["n_bins"], w["r_lo"],
+                                        w["r_hi"], w["earth"], ldirs[keep_bt], lE[keep_bt],
+                                        lbins[keep_bt])
+        part_sg = crp.crp_lens_build_surrogate(ctx, mlp, w["nside"], w["n_bins"], w["r_lo"],
+                                               w["r_hi"], ldirs[~keep_bt], lE[~keep_bt],
+                                               lbins[~keep_bt])
+        lens_hy = crp.crp_lens_merge(part_bt, part_sg, claim)
+        torch.cuda.synchronize()
+        crp.crp_lens_destroy(part_bt)
+        crp.crp_lens_destroy(part_sg)
+    else:
+        lens_hy = crp.crp_lens_merge(lens_bt, lens_sg, claim)
+        torch.cuda.synchronize()
+    t_lens_hy = time.perf_counter() - t0 + (0.0 if claim.any() else t_lens_bt)
+    if claim.all():
+        t_lens_hy += t_lens_sg
     # arrival maps of an isotropic border population through both lenses
     bd, bR = workloads.backtrack_directions(m, w["r_lo"], w["r_hi"], w["seed"] + 4)
     inj2 = crp.host_injection(dict(x=np.zeros(m), y=np.zeros(m), z=np.zeros(m), ux=bd[:, 0],
                                    uy=bd[:, 1], uz=bd[:, 2], E=bR, A=np.ones(m), Z=np.ones(m)))
     maps = {}
-    for name, lens in (("backtracked", lens_bt), ("surrogate", lens_sg)):
+    for name, lens in (("backtracked", lens_bt), ("surrogate", lens_sg), ("hybrid", lens_hy)):
         crp.crp_candidates_clear(ctx)
         crp.crp_candidates_inject(ctx, crp.candidate_arrays(inj2), m)
         torch.cuda.synchronize()
@@ -1147,6 +1249,8 @@ def run_galactic(args, keep=False):
     ca, cb = coarse_ring_map(a, w["nside"]), coarse_ring_map(b, w["nside"])
     chi2, dof, pval = two_sample_chi2(ca, cb)
     corr = float(np.corrcoef(ca, cb)[0, 1])
+    ch = coarse_ring_map(maps["hybrid"], w["nside"])
+    chi2_h, dof_h, pval_h = two_sample_chi2(ca, ch)
     summary = {
         "workload": wname, "metric": "galactic back-tracking and lens surrogate",
         "backtrack": {"candidates": n_all, "accepted_steps": st.accepted_steps,
@@ -1172,11 +1276,38 @@ def run_galactic(args, keep=False):
                  "map_correlation": corr,
                  "observed_fraction": {"backtracked": float(a.sum() / m),
                                        "surrogate": float(b.sum() / m)}},
+        "hybrid_lens": {
+            "rule": f"surrogate columns in the lens bins whose validated median is <= "
+                    f"{HYBRID_MAX_DEG} deg ({n_val} validation samples, not trained on), "
+                    "back-tracked columns elsewhere",
+            "claimed_bins": [int(b) for b in np.nonzero(claim)[0]],
+            "lowest_claimed_rigidity_V": (float(w["r_lo"] * (w["r_hi"] / w["r_lo"]) ** (
+                np.nonzero(claim)[0][0] / w["n_bins"])) if claim.any() else None),
+            "held_out_median_deg_in_claimed_bins": (float(np.median(ang[claim[bt]]))
+                                                    if claim.any() else None),
+            "held_out_worst_bin_median_deg_in_claimed_bins": (float(test_med[claim].max())
+                                                              if claim.any() else None),
+            "validated_median_deg_by_bin": [round(float(v), 3) for v in val_med],
+            "build_s": t_lens_hy, "build_backtrack_s": t_lens_bt,
+            "observed_fraction": float(maps["hybrid"].sum() / m),
+            "map_vs_backtracked": {"chi2": chi2_h, "dof": dof_h, "p": pval_h},
+        },
+        "chaos_floor_deg": {
+            "definition": "median angle between the border direction of an arrival direction "
+                          "and the normalised mean of those of its two neighbours delta away "
+                          "on a great circle (same rigidity; binary64 back-tracking): the "
+                          "interpolation error at sample spacing delta, per 0.1-decade "
+                          "rigidity band (log10 R/V)",
+            "training_spacing_deg": spacing, "at_training_spacing": floor_train,
+            "at_0.2_deg": floor_02,
+            "bands_where_floor_allows_0.5deg": [k for k, v in floor_train.items() if v <= 0.5],
+        },
     }
     if keep:
         return dict(ctx=ctx, grid=grid, mlp=mlp, lens_bt=lens_bt, lens_sg=lens_sg,
-                    summary=summary, t_lens_bt=t_lens_bt, t_lens_sg=t_lens_sg)
-    for lens in (lens_bt, lens_sg):
+                    lens_hy=lens_hy, summary=summary, t_lens_bt=t_lens_bt, t_lens_sg=t_lens_sg,
+                    t_lens_hy=t_lens_hy)
+    for lens in (lens_bt, lens_sg, lens_hy):
         crp.crp_lens_destroy(lens)
     crp.crp_mlp_destroy(mlp)
     crp.crp_grid_destroy(grid)
@@ -1220,8 +1351,8 @@ def run_e2e(args):
     nside = workloads.GALACTIC_LENS["nside"]
     sky = crp.crp_histogram_healpix(ctx, crp.COLLECT_DETECTED, nside, 0).astype(np.float64)
     paths = {}
-    for name in ("backtracked", "surrogate"):
-        lens = gal["lens_bt"] if name == "backtracked" else gal["lens_sg"]
+    for name in ("backtracked", "surrogate", "hybrid"):
+        lens = gal[{"backtracked": "lens_bt", "surrogate": "lens_sg", "hybrid": "lens_hy"}[name]]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         crp.crp_lens_apply(ctx, lens, crp.COLLECT_DETECTED)
@@ -1236,6 +1367,10 @@ def run_e2e(args):
     ca, cb = coarse_ring_map(a["hist"], nside), coarse_ring_map(b["hist"], nside)
     chi2, dof, pval = two_sample_chi2(ca, cb)
     ks = ks_2samp(a["E"], b["E"])
+    hy = paths["hybrid"]
+    ks_h = ks_2samp(a["E"], hy["E"])
+    chh = coarse_ring_map(hy["hist"], nside)
+    chi2_h, dof_h, pval_h = two_sample_chi2(ca, chh)
     summary = {
         "workload": "e2e_1e8_mixed_256cube_then_galactic_lens",
         "metric": "end-to-end propagation + lens (plain vs surrogate)",
@@ -1243,9 +1378,15 @@ def run_e2e(args):
                           "accepted_steps": st.accepted_steps,
                           "steps_per_s": st.accepted_steps / t_prop,
                           "detected": int(st.n_detected), "pion_events": int(st.n_pion)},
-        "lens_build_s": {"backtracked": gal["t_lens_bt"], "surrogate": gal["t_lens_sg"]},
-        "lens_apply_s": {"backtracked": a["t_apply"], "surrogate": b["t_apply"]},
-        "observed_at_earth": {"backtracked": a["observed"], "surrogate": b["observed"]},
+        "lens_build_s": {"backtracked": gal["t_lens_bt"], "surrogate": gal["t_lens_sg"],
+                         "hybrid": gal["t_lens_hy"]},
+        "lens_apply_s": {"backtracked": a["t_apply"], "surrogate": b["t_apply"],
+                         "hybrid": hy["t_apply"]},
+        "observed_at_earth": {"backtracked": a["observed"], "surrogate": b["observed"],
+                              "hybrid": hy["observed"]},
+        "hybrid_vs_backtracked": {"spectrum_ks": {"statistic": float(ks_h.statistic),
+                                                  "p": float(ks_h.pvalue)},
+                                  "arrival_map": {"chi2": chi2_h, "dof": dof_h, "p": pval_h}},
         "arrival_map": {"cells": int(len(ca)), "chi2": chi2, "dof": dof, "p": pval,
                         "correlation": float(np.corrcoef(ca, cb)[0, 1]),
                         "sky_before_lens_events": float(sky.sum())},
@@ -1255,7 +1396,7 @@ def run_e2e(args):
     crp.crp_tables_destroy(tables)
     crp.crp_grid_destroy(grid)
     crp.crp_context_destroy(ctx)
-    for lens in (gal["lens_bt"], gal["lens_sg"]):
+    for lens in (gal["lens_bt"], gal["lens_sg"], gal["lens_hy"]):
         crp.crp_lens_destroy(lens)
     crp.crp_mlp_destroy(gal["mlp"])
     crp.crp_grid_destroy(gal["grid"])

@@ -444,6 +444,16 @@ crp_status crp_lens_apply(crp_context* ctx, const crp_lens* lens, int32_t what, 
 crp_status crp_lens_copy_out(const crp_lens* lens, uint32_t* col_start, uint32_t* entries,
                              uint32_t* max_count, int64_t* n_entries);
 crp_status crp_lens_destroy(crp_lens* lens);
+/* A lens that takes, for each rigidity bin, the columns of lens b where
+ * take_b[bin] != 0 and those of lens a elsewhere (host array of n_bins
+ * flags); max_count per bin from the same lens.  Lens normalisation is per
+ * bin (Sect. 4 lenses are per rigidity), so a merged bin behaves exactly as
+ * in its source lens.  The use: a lens whose bins come from the surrogate
+ * where its validated angular error is small enough and from back-tracking
+ * elsewhere.  a and b must share device, nside, bins and rigidity range
+ * (else CRP_E_INVALID); both stay owned by the caller; synchronous. */
+crp_status crp_lens_merge(const crp_lens* a, const crp_lens* b, const uint8_t* take_b,
+                          crp_lens** out);
 
 /* ------------------------------------------------------------------------
  * Learned lens surrogate: an MLP that maps an arrival direction at Earth and

@@ -164,7 +164,7 @@ SYMBOLS = (
     "crp_candidates_inject", "crp_candidates_clear",
     "crp_propagate", "crp_collect", "crp_histogram_energy", "crp_histogram_energy_noalloc",
     "crp_histogram_energy_device",
-    "crp_lens_build", "crp_lens_apply", "crp_lens_copy_out", "crp_lens_destroy",
+    "crp_lens_build", "crp_lens_apply", "crp_lens_copy_out", "crp_lens_destroy", "crp_lens_merge",
     "crp_histogram_healpix", "crp_histogram_healpix_device",
     "crp_mlp_create", "crp_mlp_destroy", "crp_mlp_num_params", "crp_mlp_set_params",
     "crp_mlp_get_params", "crp_mlp_forward", "crp_mlp_train_step", "crp_lens_build_surrogate",
@@ -216,6 +216,7 @@ def lib():
                                          C.POINTER(Stats)]
             L.crp_lens_apply.argtypes = [p, p, i32, p]
             L.crp_lens_copy_out.argtypes = [p, p, p, p, C.POINTER(C.c_int64)]
+            L.crp_lens_merge.argtypes = [p, p, p, C.POINTER(p)]
             L.crp_lens_destroy.argtypes = [p]
             L.crp_histogram_healpix.argtypes = [p, i32, i32, i32, p, p]
             L.crp_histogram_healpix_device.argtypes = [p, i32, i32, i32, p, i32, p]
@@ -466,6 +467,14 @@ def crp_lens_copy_out(lens, n_cols, n_bins):
     _check(lib().crp_lens_copy_out(lens, col.ctypes.data, ent.ctypes.data, mx.ctypes.data,
                                    C.byref(n)))
     return dict(col_start=col, entries=ent[: n.value], max_count=mx)
+
+
+def crp_lens_merge(a, b, take_b):
+    """Per rigidity bin: b's columns where take_b[bin], a's elsewhere."""
+    take = np.ascontiguousarray(np.asarray(take_b, dtype=bool).astype(np.uint8))
+    h = C.c_void_p()
+    _check(lib().crp_lens_merge(a, b, take.ctypes.data, C.byref(h)))
+    return h
 
 
 def crp_lens_destroy(lens):

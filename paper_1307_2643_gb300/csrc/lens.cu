@@ -634,6 +634,92 @@ crp_status crp_lens_build_surrogate(crp_context* ctx, crp_mlp* mlp, const crp_le
   return CRP_OK;
 }
 
+crp_status crp_lens_merge(const crp_lens* a, const crp_lens* b, const uint8_t* take_b,
+                          crp_lens** out) {
+  if (!a || !b || !take_b || !out) {
+    set_error("crp_lens_merge: NULL argument");
+    return CRP_E_INVALID;
+  }
+  if (a->device != b->device || a->nside != b->nside || a->n_bins != b->n_bins ||
+      a->r_lo != b->r_lo || a->r_hi != b->r_hi) {
+    set_error("crp_lens_merge: the lenses differ in device, nside, bins or rigidity range");
+    return CRP_E_INVALID;
+  }
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != a->device) {
+    const cudaError_t e = cudaSetDevice(a->device);
+    if (e != cudaSuccess) return fail_cuda(e, "crp_lens_merge: cudaSetDevice");
+  }
+  crp_status st = CRP_OK;
+  const int64_t n_cols = a->n_cols, npix = a->npix;
+  std::vector<uint32_t> ca(n_cols + 1), cb(n_cols + 1), cm(n_cols + 1), ma(a->n_bins),
+      mb(a->n_bins), mm(a->n_bins);
+  cudaError_t e = cudaMemcpy(ca.data(), a->col_start, 4 * (n_cols + 1), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(cb.data(), b->col_start, 4 * (n_cols + 1), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(ma.data(), a->max_count, 4 * a->n_bins, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(mb.data(), b->max_count, 4 * a->n_bins, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) st = fail_cuda(e, "crp_lens_merge: copy in");
+  // per bin: the chosen lens's columns (one contiguous range of its entries),
+  // rebased onto the merged entry array
+  uint64_t total = 0;
+  if (st == CRP_OK) {
+    for (int bin = 0; bin < a->n_bins; ++bin) {
+      const std::vector<uint32_t>& c = take_b[bin] ? cb : ca;
+      const int64_t c0 = (int64_t)bin * npix;
+      for (int64_t j = 0; j < npix; ++j) cm[c0 + j] = (uint32_t)(total + (c[c0 + j] - c[c0]));
+      total += c[c0 + npix] - c[c0];
+      mm[bin] = take_b[bin] ? mb[bin] : ma[bin];
+    }
+    cm[n_cols] = (uint32_t)total;
+    if (total > 0xffffffffull) {
+      set_error("crp_lens_merge: more than 2^32 entries");
+      st = CRP_E_INVALID;
+    }
+  }
+  crp_lens* L = nullptr;
+  if (st == CRP_OK) {
+    crp_lens_desc d;
+    memset(&d, 0, sizeof(d));
+    d.nside = a->nside;
+    d.n_bins = a->n_bins;
+    d.r_lo = a->r_lo;
+    d.r_hi = a->r_hi;
+    L = lens_alloc(a->device, &d, npix, n_cols);
+    if (L) {
+      L->n_entries = (int64_t)total;
+      L->entries = static_cast<uint32_t*>(dev_alloc(4 * (total ? total : 1)));
+    }
+    if (!L || !L->entries) {
+      set_error("crp_lens_merge: allocation failed");
+      st = CRP_E_OOM;
+    }
+  }
+  if (st == CRP_OK) {
+    e = cudaMemcpy(L->col_start, cm.data(), 4 * (n_cols + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(L->max_count, mm.data(), 4 * a->n_bins, cudaMemcpyHostToDevice);
+    for (int bin = 0; bin < a->n_bins && e == cudaSuccess; ++bin) {
+      const crp_lens* src = take_b[bin] ? b : a;
+      const std::vector<uint32_t>& c = take_b[bin] ? cb : ca;
+      const int64_t c0 = (int64_t)bin * npix;
+      const uint32_t len = c[c0 + npix] - c[c0];
+      if (len)
+        e = cudaMemcpy(L->entries + cm[c0], src->entries + c[c0], 4 * (size_t)len,
+                       cudaMemcpyDeviceToDevice);
+    }
+    if (e != cudaSuccess) st = fail_cuda(e, "crp_lens_merge: copy");
+  }
+  if (st != CRP_OK) {
+    lens_free(L);
+    L = nullptr;
+  }
+  if (prev >= 0 && prev != a->device) cudaSetDevice(prev);
+  *out = L;
+  return st;
+}
+
 crp_status crp_lens_destroy(crp_lens* L) {
   if (!L) return CRP_OK;
   cudaDeviceSynchronize();
