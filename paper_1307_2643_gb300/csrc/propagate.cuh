@@ -1065,11 +1065,9 @@ struct PolicyMixedT {
   static constexpr bool kNuc = NUC;      // nuclear decay as a third free path
   using Real = float;
   static constexpr bool kSharedStages = false;
-  // per-lane cache of the last two cell records gathered (2 slots of 6 float4,
-  // lane-interleaved); records are copied into a slot asynchronously
+  // per-lane cache of the last cell record gathered (6 float4, lane-interleaved)
   static constexpr int kCacheF4 = 6;
-  static constexpr int kSlots = 2;
-  static constexpr size_t kSmemPerThread = kSlots * kCacheF4 * sizeof(float4);
+  static constexpr size_t kSmemPerThread = kCacheF4 * sizeof(float4);
   struct LaneGal {
     float gal[3];  // position relative to the galactic centre
   };
@@ -1084,8 +1082,7 @@ struct PolicyMixedT {
     float kap, d_obs, d_bord, err2, dx[3], u5[3];
     float3 k1;      // force at the start of the step
     int cap, since_rebase;
-    uint32_t cell_key[2];  // index of the cell record held in each cache slot
-    int mru;               // slot used last
+    uint32_t cell_key;  // index of the cell record held in this lane's cache
     // binary32 lower bound of the distance to the next length cap (s_max,
     // pending free paths); the exact binary64 tests run only when it is
     // below two proposed steps ("near")
@@ -1095,23 +1092,7 @@ struct PolicyMixedT {
     float yl, E_fold_f;
   };
 
-  __device__ __forceinline__ static void init_lane(Lane& c) {
-    c.cell_key[0] = c.cell_key[1] = 0xffffffffu;
-    c.mru = 0;
-  }
-
-  // A field evaluation in flight: the in-cell fractions and the cache slot
-  // whose record is being copied (slot >= 0), or the field itself when it was
-  // evaluated at issue (slot < 0); plus the analytic galactic field, computed
-  // at issue while the record is in flight.
-  struct LaneGalField {
-    float3 G;
-  };
-  struct LaneNoGalField {};
-  struct Pending : std::conditional<GAL, LaneGalField, LaneNoGalField>::type {
-    float a, b, c;  // fractions tx, ty, tz (slot >= 0) or field Bx, By, Bz (slot < 0)
-    int slot;
-  };
+  __device__ __forceinline__ static void init_lane(Lane& c) { c.cell_key = 0xffffffffu; }
 
   // Cell and fraction from the binary64 position (exact rebase).
   __device__ __forceinline__ static void rebase(const KParams& p, Lane& c) {
@@ -1190,18 +1171,10 @@ struct PolicyMixedT {
     st.uz[c.slot] = (double)c.u[2];
   }
 
-  // Field at the current position plus offset (ox, oy, oz) (length unit), in
-  // two halves so that a stage's record can be in flight while an earlier
-  // stage is evaluated.  issue(): cell and in-cell fractions; with cell
-  // records, the record is found in one of the lane's two shared-memory slots
-  // or copied into one (cp.async, one commit group per issue, so every issue
-  // opens exactly one group) -- never into `avoid`, the slot of another
-  // evaluation in flight; without records (or with cell indices beyond 32
-  // bits) the field is evaluated at once.  resolve<W>(): waits until at most
-  // W groups are outstanding and evaluates the record (Horner form).
+  // Field at the current position plus offset (ox, oy, oz) (length unit).
   template <class NodeT>
-  __device__ __forceinline__ static void issue(const KParams& p, Lane& c, float ox, float oy,
-                                               float oz, int avoid, Pending& q) {
+  __device__ __forceinline__ static float3 field(const KParams& p, Lane& c, float ox,
+                                                 float oy, float oz) {
     const FieldView& f = p.f;
     const float rx = fmaf(ox, f.inv_spacing_f, c.frac[0]);
     const float ry = fmaf(oy, f.inv_spacing_f, c.frac[1]);
@@ -1215,56 +1188,50 @@ struct PolicyMixedT {
     const int ix0 = wrap_int(c.cell[0] + jx, nx, (int)f.mask[0]);
     const int iy0 = wrap_int(c.cell[1] + jy, ny, (int)f.mask[1]);
     const int iz0 = wrap_int(c.cell[2] + jz, nz, (int)f.mask[2]);
-    if constexpr (GAL) {
-      const float gx = c.gal[0] + ox, gy = c.gal[1] + oy, gz = c.gal[2] + oz;
-      float3 G = make_float3(0.f, 0.f, 0.f);
-      if (mflags<FIX>(p) & CRP_GALACTIC) G = galactic_f32(p, gx, gy, gz);
-      if constexpr (GMF) {
-        if (mflags<FIX>(p) & CRP_GMF) {
-          const float3 H = gmf_f32(p, gx, gy, gz);
-          G.x += H.x;
-          G.y += H.y;
-          G.z += H.z;
-        }
-      }
-      q.G = G;
-    }
-    if (std::is_same<NodeT, float4>::value && f.cells && f.cache_ok) {
-      const size_t cell = ((size_t)iz0 * ny + (size_t)iy0) * nx + (size_t)ix0;
-      const uint32_t key = (uint32_t)cell;
-      int slot;
-      if (key == c.cell_key[0]) {
-        slot = 0;
-      } else if (key == c.cell_key[1]) {
-        slot = 1;
-      } else {
-        slot = avoid >= 0 ? 1 - avoid : 1 - c.mru;
-        const float4* r = f.cells + 8 * cell;
-        float4* dst = reinterpret_cast<float4*>(crp_dyn_smem) + threadIdx.x +
-                      (size_t)slot * kCacheF4 * blockDim.x;
-        const int bs = blockDim.x;
-#pragma unroll
-        for (int k = 0; k < kCacheF4; ++k) {
-          const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + k * bs);
-          asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(r + k)
-                       : "memory");
-        }
-        c.cell_key[slot] = key;
-      }
-      asm volatile("cp.async.commit_group;\n" ::: "memory");
-      c.mru = slot;
-      q.slot = slot;
-      q.a = tx;
-      q.b = ty;
-      q.c = tz;
-      return;
-    }
     float3 B;
     if (std::is_same<NodeT, float4>::value && f.cells) {
+      // one aligned 128-byte record: the cell's trilinear polynomial,
+      // evaluated in Horner form (7 FMAs per component)
       const size_t cell = ((size_t)iz0 * ny + (size_t)iy0) * nx + (size_t)ix0;
-      const float4* r = f.cells + 8 * cell;
-      B = horner_record(__ldg(r), __ldg(r + 1), __ldg(r + 2), __ldg(r + 3), __ldg(r + 4),
-                        __ldg(r + 5), tx, ty, tz);
+      float4 a0, a1, a2, a3, a4, a5;
+      // consecutive stages and steps mostly stay in one cell: re-read the
+      // record from this lane's shared-memory copy (conflict-free, 4
+      // wavefronts per warp load) instead of a 32-line global gather
+      float4* cache = reinterpret_cast<float4*>(crp_dyn_smem) + threadIdx.x;
+      const int bs = blockDim.x;
+      if ((uint32_t)cell != c.cell_key || !f.cache_ok) {
+        const float4* r = f.cells + 8 * cell;
+        a0 = __ldg(r);
+        a1 = __ldg(r + 1);
+        a2 = __ldg(r + 2);
+        a3 = __ldg(r + 3);
+        a4 = __ldg(r + 4);
+        a5 = __ldg(r + 5);
+        cache[0] = a0;
+        cache[bs] = a1;
+        cache[2 * bs] = a2;
+        cache[3 * bs] = a3;
+        cache[4 * bs] = a4;
+        cache[5 * bs] = a5;
+        c.cell_key = (uint32_t)cell;
+      } else {
+        a0 = cache[0];
+        a1 = cache[bs];
+        a2 = cache[2 * bs];
+        a3 = cache[3 * bs];
+        a4 = cache[4 * bs];
+        a5 = cache[5 * bs];
+      }
+      // coefficient j of component d is float 3j + d of the record
+      auto horner = [&](float c0, float c1, float c2, float c3, float c4, float c5, float c6,
+                        float c7) {
+        const float xy = fmaf(fmaf(c7, tz, c4), ty, fmaf(c5, tz, c1));
+        const float y0 = fmaf(fmaf(c6, tz, c2), ty, fmaf(c3, tz, c0));
+        return fmaf(xy, tx, y0);
+      };
+      B.x = horner(a0.x, a0.w, a1.z, a2.y, a3.x, a3.w, a4.z, a5.y);
+      B.y = horner(a0.y, a1.x, a1.w, a2.z, a3.y, a4.x, a4.w, a5.z);
+      B.z = horner(a0.z, a1.y, a2.x, a2.w, a3.z, a4.y, a5.x, a5.w);
     } else {
       const int ix1 = ix0 + 1 == nx ? 0 : ix0 + 1;
       const int iy1 = iy0 + 1 == ny ? 0 : iy0 + 1;
@@ -1290,58 +1257,24 @@ struct PolicyMixedT {
       B.z = lerp(lerp(lerp(v0.z, v1.z, tx), lerp(v2.z, v3.z, tx), ty),
                  lerp(lerp(v4.z, v5.z, tx), lerp(v6.z, v7.z, tx), ty), tz);
     }
-    q.slot = -1;
-    q.a = B.x;
-    q.b = B.y;
-    q.c = B.z;
-  }
-
-  // The cell's trilinear polynomial in Horner form: coefficient j of
-  // component d is float 3j + d of the record (7 FMAs per component).
-  __device__ __forceinline__ static float3 horner_record(float4 a0, float4 a1, float4 a2,
-                                                         float4 a3, float4 a4, float4 a5,
-                                                         float tx, float ty, float tz) {
-    auto horner = [&](float c0, float c1, float c2, float c3, float c4, float c5, float c6,
-                      float c7) {
-      const float xy = fmaf(fmaf(c7, tz, c4), ty, fmaf(c5, tz, c1));
-      const float y0 = fmaf(fmaf(c6, tz, c2), ty, fmaf(c3, tz, c0));
-      return fmaf(xy, tx, y0);
-    };
-    float3 B;
-    B.x = horner(a0.x, a0.w, a1.z, a2.y, a3.x, a3.w, a4.z, a5.y);
-    B.y = horner(a0.y, a1.x, a1.w, a2.z, a3.y, a4.x, a4.w, a5.z);
-    B.z = horner(a0.z, a1.y, a2.x, a2.w, a3.z, a4.y, a5.x, a5.w);
-    return B;
-  }
-
-  template <int W>
-  __device__ __forceinline__ static float3 resolve(const Pending& q) {
-    float3 B;
-    if (q.slot >= 0) {
-      asm volatile("cp.async.wait_group %0;\n" ::"n"(W) : "memory");
-      const float4* cache = reinterpret_cast<const float4*>(crp_dyn_smem) + threadIdx.x +
-                            (size_t)q.slot * kCacheF4 * blockDim.x;
-      const int bs = blockDim.x;
-      B = horner_record(cache[0], cache[bs], cache[2 * bs], cache[3 * bs], cache[4 * bs],
-                        cache[5 * bs], q.a, q.b, q.c);
-    } else {
-      B = make_float3(q.a, q.b, q.c);
-    }
     if constexpr (GAL) {
-      B.x += q.G.x;
-      B.y += q.G.y;
-      B.z += q.G.z;
+      const float gx = c.gal[0] + ox, gy = c.gal[1] + oy, gz = c.gal[2] + oz;
+      if (mflags<FIX>(p) & CRP_GALACTIC) {
+        const float3 G = galactic_f32(p, gx, gy, gz);
+        B.x += G.x;
+        B.y += G.y;
+        B.z += G.z;
+      }
+      if constexpr (GMF) {
+        if (mflags<FIX>(p) & CRP_GMF) {
+          const float3 G = gmf_f32(p, gx, gy, gz);
+          B.x += G.x;
+          B.y += G.y;
+          B.z += G.z;
+        }
+      }
     }
     return B;
-  }
-
-  // The field at one offset, at once.
-  template <class NodeT>
-  __device__ __forceinline__ static float3 field(const KParams& p, Lane& c, float ox,
-                                                 float oy, float oz) {
-    Pending q;
-    issue<NodeT>(p, c, ox, oy, oz, -1, q);
-    return resolve<0>(q);
   }
 
   __device__ __forceinline__ static float3 force(float kap, float ux, float uy, float uz,
@@ -1408,32 +1341,22 @@ struct PolicyMixedT {
     auto madd = [](float a, float3 x, float3 y) {
       return make_float3(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z));
     };
-    // Stage j's position offset h * osum_j needs the stage directions u_1 ..
-    // u_{j-1} only, and u_i needs k_1 .. k_{i-1}: the gathers of stages 2 and 3
-    // can both start with k1 known, that of stage 4 once k2 is, 5 once k3 is, 6
-    // once k4 is.  So each stage's gather is issued one stage ahead (at most
-    // two in flight), and a trial waits for three gather latencies, not five.
-    // The arithmetic of every expression is the sequential one's.
-    auto issue_at = [&](float3 osum, int avoid, Pending& q) {
-      issue<NodeT>(p, c, h * osum.x, h * osum.y, h * osum.z, avoid, q);
+    auto stage = [&](float3 osum, float3 ksum, float3& u_out) {
+      u_out = madd(h, ksum, u1);
+      return force(kap, u_out.x, u_out.y, u_out.z,
+                   field<NodeT>(p, c, h * osum.x, h * osum.y, h * osum.z));
     };
-    Pending q2, q3, q4, q5, q6;
-    const float3 u2 = madd(h, make_float3(A21 * k1.x, A21 * k1.y, A21 * k1.z), u1);
-    issue_at(make_float3(A21 * u1.x, A21 * u1.y, A21 * u1.z), -1, q2);
-    issue_at(comb(A31, u1, A32, u2), q2.slot, q3);
-    const float3 k2 = force(kap, u2.x, u2.y, u2.z, resolve<1>(q2));
-    const float3 u3 = madd(h, comb(A31, k1, A32, k2), u1);
-    issue_at(madd(A43, u3, comb(A41, u1, A42, u2)), q3.slot, q4);
-    const float3 k3 = force(kap, u3.x, u3.y, u3.z, resolve<1>(q3));
-    const float3 u4 = madd(h, madd(A43, k3, comb(A41, k1, A42, k2)), u1);
-    issue_at(madd(A54, u4, madd(A53, u3, comb(A51, u1, A52, u2))), q4.slot, q5);
-    const float3 k4 = force(kap, u4.x, u4.y, u4.z, resolve<1>(q4));
-    const float3 u5 = madd(h, madd(A54, k4, madd(A53, k3, comb(A51, k1, A52, k2))), u1);
-    issue_at(madd(A65, u5, madd(A64, u4, madd(A63, u3, comb(A61, u1, A62, u2)))), q5.slot, q6);
-    const float3 k5 = force(kap, u5.x, u5.y, u5.z, resolve<1>(q5));
-    const float3 u6 =
-        madd(h, madd(A65, k5, madd(A64, k4, madd(A63, k3, comb(A61, k1, A62, k2)))), u1);
-    const float3 k6 = force(kap, u6.x, u6.y, u6.z, resolve<0>(q6));
+    float3 u2, u3, u4, u5, u6;
+    const float3 k2 = stage(make_float3(A21 * u1.x, A21 * u1.y, A21 * u1.z),
+                            make_float3(A21 * k1.x, A21 * k1.y, A21 * k1.z), u2);
+    const float3 k3 = stage(comb(A31, u1, A32, u2), comb(A31, k1, A32, k2), u3);
+    const float3 k4 = stage(madd(A43, u3, comb(A41, u1, A42, u2)),
+                            madd(A43, k3, comb(A41, k1, A42, k2)), u4);
+    const float3 k5 = stage(madd(A54, u4, madd(A53, u3, comb(A51, u1, A52, u2))),
+                            madd(A54, k4, madd(A53, k3, comb(A51, k1, A52, k2))), u5);
+    const float3 k6 =
+        stage(madd(A65, u5, madd(A64, u4, madd(A63, u3, comb(A61, u1, A62, u2)))),
+              madd(A65, k5, madd(A64, k4, madd(A63, k3, comb(A61, k1, A62, k2)))), u6);
     const float3 dsum = madd(W6, u6, madd(W4, u4, comb(W1, u1, W3, u3)));
     const float3 usum = madd(W6, k6, madd(W4, k4, comb(W1, k1, W3, k3)));
     const float3 esum = madd(D6, k6, madd(D5, k5, madd(D4, k4, comb(D1, k1, D3, k3))));
