@@ -932,6 +932,33 @@ crp_status forward(crp_mlp* M, const float* x, int64_t n, const float* t, float*
   // backward) runs fused at the start of backward()
   const bool fused_out = tc && t && !y_hat && M->hidden == 256;
   const int H = M->hidden;
+  if (fused_out) {
+    // every hidden layer in one persistent tcgen05 kernel, storing each
+    // activation and the transposes the weight gradients read
+    MlpTcParams P;
+    memset(&P, 0, sizeof(P));
+    P.x = x;
+    P.n_in = M->n_in;
+    P.n_gemm = M->n_hidden - 1;
+    P.n_tiles = n / 128;
+    P.W1 = M->params + M->w_off[0];
+    P.b1 = M->params + M->b_off[0];
+    for (int l = 1; l < M->n_hidden; ++l) {
+      P.Wimg[l - 1] = M->wimg[l];
+      P.bh[l - 1] = M->params + M->b_off[l];
+    }
+    P.Wout = M->params + M->w_off[M->n_hidden];  // staged by the kernel, unused here
+    P.bout = M->params + M->b_off[M->n_hidden];
+    for (int l = 0; l < M->n_hidden; ++l) {
+      P.h[l] = M->h[l];
+      P.hT[l] = l + 1 < M->n_hidden ? M->hT[l] : nullptr;
+    }
+    P.ldt = n;
+    P.err = M->tc_err;
+    cudaError_t e = cudaMemsetAsync(M->loss, 0, sizeof(float), s);
+    if (e == cudaSuccess) e = mlp_forward_tc_train(P, M->sm_count, s);
+    return e == cudaSuccess ? CRP_OK : fail_cuda(e, "mlp: tensor-core training forward");
+  }
   launch_layer_in(M, x, n, tc ? M->hT[0] : nullptr, s);
   for (int l = 1; l < M->n_hidden; ++l) {
     if (tc) {

@@ -117,9 +117,29 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 
+// Store row `row`'s bf16 values of columns c0 .. c0 + 8 q - 1 (packed pairs w)
+// into h (row-major, ld 256: q 16-byte stores) and, when hT is given, into the
+// transpose (ld ldt: one 2-byte store per column; a warp's 32 consecutive rows
+// make each column's stores one contiguous 64-byte run).
+template <int Q>
+__device__ __forceinline__ void store_activation(const uint32_t* w, int64_t row, int c0,
+                                                 __nv_bfloat16* h, __nv_bfloat16* hT,
+                                                 int64_t ldt) {
+  uint4* dst = reinterpret_cast<uint4*>(h + row * kH + c0);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) dst[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+  if (hT) {
+    unsigned short* t = reinterpret_cast<unsigned short*>(hT);
+#pragma unroll
+    for (int j = 0; j < 8 * Q; ++j)
+      t[(int64_t)(c0 + j) * ldt + row] = (unsigned short)(w[j / 2] >> (16 * (j & 1)));
+  }
+}
+
 // NIN: compiled input count (4 for the surrogate's inputs); 0 = any n_in <= 8
-// (weights zero-padded to 8 inputs).
-template <int NIN>
+// (weights zero-padded to 8 inputs).  TRAIN: the forward pass of a training
+// step -- every hidden activation stored (store_activation), no output layer.
+template <int NIN, bool TRAIN>
 __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const MlpTcParams P) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   unsigned char* base = tc_smem + ((1024u - (smem_u32(tc_smem) & 1023u)) & 1023u);
@@ -210,6 +230,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const MlpTcParam
         w[e / 2] = pack_bf16(v[0], v[1]);
         w[e / 2 + 1] = pack_bf16(v[2], v[3]);
       }
+      if (TRAIN) store_activation<1>(w, row, kc * 8, P.h[0], P.hT[0], P.ldt);
       *reinterpret_cast<uint4*>(As + (r >> 3) * kSbo + kc * kLbo + (r & 7) * 16) =
           make_uint4(w[0], w[1], w[2], w[3]);
     }
@@ -261,7 +282,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const MlpTcParam
           const float h3 = fmaxf(__uint_as_float(v[j + 3]) + b4.w, 0.f);
           w[j / 2] = pack_bf16(h0, h1);
           w[j / 2 + 1] = pack_bf16(h2, h3);
-          if (last) {
+          if (last && !TRAIN) {
             const __nv_bfloat162 p01 = *reinterpret_cast<const __nv_bfloat162*>(&w[j / 2]);
             const __nv_bfloat162 p23 = *reinterpret_cast<const __nv_bfloat162*>(&w[j / 2 + 1]);
             const float a0 = __low2float(p01), a1 = __high2float(p01);
@@ -283,6 +304,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const MlpTcParam
             y2 = fmaf(wc.w, a3, y2);
           }
         }
+        if (TRAIN) store_activation<4>(w, row, cc * 32, P.h[l + 1], P.hT[l + 1], P.ldt);
         if (!last) {
 #pragma unroll
           for (int q = 0; q < 4; ++q)
@@ -290,7 +312,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const MlpTcParam
                 make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
         }
       }
-      if (last && g == 1) {
+      if (last && g == 1 && !TRAIN) {
         sy[r] = y0;
         sy[kRows + r] = y1;
         sy[2 * kRows + r] = y2;
@@ -299,7 +321,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const MlpTcParam
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       __syncthreads();
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      if (last && g == 0) {
+      if (last && g == 0 && !TRAIN) {
         y0 += sy[r] + sbo[0];
         y1 += sy[kRows + r] + sbo[1];
         y2 += sy[2 * kRows + r] + sbo[2];
@@ -768,14 +790,23 @@ bool mlp_tc_supported(int n_in, int hidden, int n_hidden, int n_out) {
          n_hidden - 1 <= kMlpTcMaxGemm;
 }
 
-cudaError_t mlp_forward_tc(const MlpTcParams& p, int sm_count, cudaStream_t s) {
-  auto k = p.n_in == 4 ? k_mlp_forward_tc<4> : k_mlp_forward_tc<0>;
+template <bool TRAIN>
+cudaError_t launch_forward_tc(const MlpTcParams& p, int sm_count, cudaStream_t s) {
+  auto k = p.n_in == 4 ? k_mlp_forward_tc<4, TRAIN> : k_mlp_forward_tc<0, TRAIN>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
   if (e != cudaSuccess) return e;
   int64_t grid = p.n_tiles < sm_count ? p.n_tiles : sm_count;
   if (grid < 1) return cudaSuccess;
   k<<<(unsigned)grid, kThreads, kSmem, s>>>(p);
   return cudaGetLastError();
+}
+
+cudaError_t mlp_forward_tc(const MlpTcParams& p, int sm_count, cudaStream_t s) {
+  return launch_forward_tc<false>(p, sm_count, s);
+}
+
+cudaError_t mlp_forward_tc_train(const MlpTcParams& p, int sm_count, cudaStream_t s) {
+  return launch_forward_tc<true>(p, sm_count, s);
 }
 
 }  // namespace crp

@@ -25,6 +25,13 @@ struct MlpTcParams {
   const float* bout;
   float* y;       // [n][3], unit vectors
   unsigned* err;  // set to 1 when a tensor-core wait timed out
+  // training forward (mlp_forward_tc_train): the hidden activations h[l]
+  // ([n][256] bf16, l = 0 the input layer's, l = k + 1 hidden GEMM k's) and
+  // their transposes hT[l] ([256][ldt] bf16, null where not needed); no
+  // output layer
+  __nv_bfloat16* h[kMlpTcMaxGemm + 1];
+  __nv_bfloat16* hT[kMlpTcMaxGemm + 1];
+  int64_t ldt;
 };
 
 // Tensor-core GEMM of the training step (tcgen05, FP32 accumulation in TMEM):
@@ -70,5 +77,8 @@ cudaError_t gemm_tc(int epi, const GemmTcParams& p, int device, int sm_count, cu
 size_t mlp_tc_weight_image_elems();
 bool mlp_tc_supported(int n_in, int hidden, int n_hidden, int n_out);
 cudaError_t mlp_forward_tc(const MlpTcParams& p, int sm_count, cudaStream_t s);
+// The forward pass of a training step on the same kernel: stores every hidden
+// activation (and the transposes p.hT asks for) instead of the output layer.
+cudaError_t mlp_forward_tc_train(const MlpTcParams& p, int sm_count, cudaStream_t s);
 
 }  // namespace crp
