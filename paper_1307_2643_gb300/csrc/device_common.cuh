@@ -28,6 +28,7 @@ __host__ __device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t 
                                                           uint32_t c3, uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
+    // each 32 x 32 -> 64-bit product in one wide multiply
     const uint32_t hi_a = mulhi32(0xD2511F53u, c0);
     const uint32_t lo_a = 0xD2511F53u * c0;
     const uint32_t hi_b = mulhi32(0xCD9E8D57u, c2);
@@ -271,17 +272,55 @@ __device__ __forceinline__ float one_minus_abs_f32(double z) {
   return v * 1.1102230246251565404e-16f;  // 2^-53
 }
 
+// The phase t = phi / (pi/2) in [0, 4) of phi = atan2(y, x) mod 2 pi, in
+// binary32 without atan2f or a division by pi/2.  The first-octant part is
+// g = (2/pi) atan(r), r = min(|x|, |y|) / max(|x|, |y|) in [0, 1], as r P(r^2)
+// with P of degree 7: a least-squares fit of (2/pi) atan(r) / r on Chebyshev
+// nodes in r^2, reweighted (Lawson's iteration) towards the minimax error
+// of r P(r^2).  Its coefficients, rounded to binary32, are within 4.5e-8 of
+// (2/pi) atan(r) on [0, 1] in exact arithmetic; the binary32 Horner steps
+// add at most 1.5e-7 (each fma rounds by 2^-24 of a partial sum below 0.64,
+// the partial sums' errors shrink by r^2 <= 1).  The octant and quadrant
+// then give t = off + sgn g in one fma (half an ulp below 4: 1.2e-7), and
+// the quotient r by __fdividef (2 ulp) moves g by at most 7.6e-8.  In all,
+// |t - exact| < 3.9e-7 for binary32 x and y (none is subnormal: f32_trunc
+// flushes those to zero).  Both zero gives t = 0, as atan2(0, 0) = 0.
+__device__ __forceinline__ float phase_quarter_turns(float x, float y) {
+  const float ax = fabsf(x), ay = fabsf(y);
+  const float mn = fminf(ax, ay), mx = fmaxf(ax, ay);
+  const float r = mx > 0.f ? __fdividef(mn, mx) : 0.f;
+  const float s = r * r;
+  float p = -0.002581184497103095f;
+  p = fmaf(p, s, 0.01391826756298542f);
+  p = fmaf(p, s, -0.03559470921754837f);
+  p = fmaf(p, s, 0.06138399615883827f);
+  p = fmaf(p, s, -0.08854503184556961f);
+  p = fmaf(p, s, 0.12698377668857574f);
+  p = fmaf(p, s, -0.21218448877334595f);
+  p = fmaf(p, s, 0.6366193294525146f);
+  const float g = p * r;
+  // quadrant (x >= 0, y >= 0): a; (x < 0, y >= 0): 2 - a; (x < 0, y < 0):
+  // 2 + a; (x >= 0, y < 0): 4 - a; with a = g, or 1 - g above the diagonal
+  const bool west = x < 0.f, south = y < 0.f;
+  const float base = west ? 2.f : (south ? 4.f : 0.f);
+  const float sg = west == south ? 1.f : -1.f;
+  const bool steep = ay > ax;
+  return fmaf(steep ? -sg : sg, g, steep ? base + sg : base);
+}
+
 // The same pixel as healpix_ring_pixel of (ux, uy, uz), or of its opposite
 // for NEG, with the floors taken in binary32 and binary64 used only within a
 // guard band of a pixel boundary.  Error of every binary32 floor argument
 // against its exact value, for nside <= 8192: inputs truncated to binary32
-// (2^-23 relative), atan2f (3 ulp), the phase t = phi / (pi/2) (< 1.6e-6 in
-// all), then the products with nside and the ring index (< nside * 2.5e-6 in
-// all; the cap formula's 1 - |z| is formed exactly before rounding).  The
-// guard, nside * 1e-5, is 4x that (2e-5 for the phase itself, 12x); outside
-// it the binary32 floor equals the exact floor and so the binary64 one,
-// inside it the binary64 path decides.  Only 32-bit integer conversions and
-// binary32 arithmetic run outside the guard band.
+// (2^-23 relative: 7.6e-8 on the phase), the phase itself (3.9e-7, see
+// phase_quarter_turns), so t within 4.7e-7; then 0.5 + t (2.4e-7), the
+// products with nside and the ring index and the sums and differences of
+// the floor arguments (< nside * 1.5e-6 in all; the cap formula's 1 - |z|
+// is formed exactly before rounding).  The guard, nside * 6e-6, is 4x
+// that (2e-5 for the phase itself, 40x); outside it the binary32 floor
+// equals the exact floor and so the binary64 one, inside it the binary64
+// path decides.  Only 32-bit integer conversions and binary32 arithmetic
+// run outside the guard band.
 // The binary32 part of healpix_ring_pixel_guarded: true, with the pixel, when
 // every floor it takes is outside its guard band (the pixel then equals the
 // binary64 one); false when the binary64 computation must decide.
@@ -292,15 +331,14 @@ __device__ __forceinline__ bool healpix_ring_pixel_try(int64_t nside, double ux,
   const float fx = sg * f32_trunc(ux), fy = sg * f32_trunc(uy), fz = sg * f32_trunc(uz);
   const int ns_i = (int)nside;
   const float ns = (float)ns_i;
-  const float g = 1e-5f * ns;
-  float phi = atan2f(fy, fx);
-  if (phi < 0.f) phi += 6.28318530717958647692f;
-  const float tt = phi / 1.57079632679489661923f;
+  const float g = 6e-6f * ns;
+  const float tt = phase_quarter_turns(fx, fy);
   int itt;
   bool ok = floor_sure(tt, 2e-5f, &itt);
   const float za = fabsf(fz);
   ok = ok && fabsf(za - 2.f / 3.f) > 1e-6f;
-  int64_t pix = 0;
+  // pixel indices below 12 nside^2 <= 805,306,368 for nside <= 8192: 32-bit
+  int pix = 0;
   if (ok) {
     if (za <= 2.f / 3.f) {
       const float t1 = ns * (0.5f + tt);
@@ -314,7 +352,7 @@ __device__ __forceinline__ bool healpix_ring_pixel_try(int64_t nside, double ux,
       // [-M, 2M) for M = 4 nside: one conditional add or subtract is ip mod M
       const int M = 4 * ns_i;
       ip = ip < 0 ? ip + M : (ip >= M ? ip - M : ip);
-      pix = 2 * nside * (nside - 1) + (int64_t)(ir - 1) * 4 * nside + ip;
+      pix = 2 * ns_i * (ns_i - 1) + (ir - 1) * 4 * ns_i + ip;
     } else {
       const float tp = tt - (float)itt;
       const float tmp = ns * sqrtf(3.f * one_minus_abs_f32(uz));
@@ -329,8 +367,7 @@ __device__ __forceinline__ bool healpix_ring_pixel_try(int64_t nside, double ux,
         // the sign of z from its bits: z > +0 exactly when the int64 is > 0
         const bool north = NEG ? __double_as_longlong(uz) < 0 && (__double_as_longlong(uz) << 1) != 0
                                : __double_as_longlong(uz) > 0;
-        pix = north ? 2 * (int64_t)ir * (ir - 1) + ip
-                    : 12 * nside * nside - 2 * (int64_t)ir * (ir + 1) + ip;
+        pix = north ? 2 * ir * (ir - 1) + ip : 12 * ns_i * ns_i - 2 * ir * (ir + 1) + ip;
       }
     }
   }

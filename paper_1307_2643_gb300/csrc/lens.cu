@@ -230,50 +230,96 @@ __device__ __forceinline__ uint32_t lens_pick_f64(const LensArgs& a, const Philo
   return a.entries[start + pk];
 }
 
-__global__ void k_lens_apply_f32(DevState st, uint64_t n, int what, LensArgs a,
-                                 uint32_t* fallback, unsigned long long* n_fallback) {
+// The binary32 decisions of one selected candidate: its lens pixel written
+// when every decision is sure; false (written nothing) when it must go to
+// the binary64 pass.  The candidate's uniforms do not depend on the lens, so
+// Philox runs before the column lookups, while they are in flight.
+__device__ __forceinline__ bool lens_decide_f32(const LensArgs& a, int Z, double E, double ux,
+                                                double uy, double uz, uint64_t id,
+                                                uint32_t* pixel_out) {
+  if (Z <= 0) {
+    *pixel_out = kNotApplied;
+    return true;
+  }
+  int b, pk32;
+  int64_t j;
+  bool sure = a.use_f32 && lens_bin_f32(E, Z, a.inv_rlo_f, a.inv_f, a.n_bins, &b);
+  sure = sure && healpix_ring_pixel_try<true>(a.nside, ux, uy, uz, &j);
+  if (!sure) return false;
+  // column keys are 32-bit (the lens build checks n_bins * npix < 2^32)
+  const uint32_t col = (uint32_t)b * (uint32_t)a.npix + (uint32_t)j;
+  const uint32_t start = a.col_start[col];
+  const uint32_t count = a.col_start[col + 1] - start;
+  const uint32_t mxi = a.max_count[b];
+  const Philox4 w = draw4(a.seed, 3u, id, 0u);
+  uint32_t out = kNotObserved;
+  if (count > 0) {
+    // u1 lies in [h1, h1 + 2^-24) with h1 its top 24 bits (exact in
+    // binary32): u1 * max_count is known to 2.4e-7 * max_count
+    const float mxf = (float)mxi, cf = (float)count;
+    const float p1 = (float)(w.v1 >> 8) * 5.9604644775390625e-8f * mxf;
+    if (!(fabsf(p1 - cf) > 2e-6f * mxf)) return false;
+    if (p1 < cf) {
+      const float p2 = (float)(w.v3 >> 8) * 5.9604644775390625e-8f * cf;
+      if (!floor_sure(p2, 2e-6f * cf, &pk32)) return false;
+      out = a.entries[start + pk32];
+    }
+  }
+  *pixel_out = out;
+  return true;
+}
+
+// First pass, a persistent grid: each thread walks its candidates with a
+// stride of the grid, holding the next candidate's inputs in registers while
+// it decides the current one (its status two candidates ahead, so that the
+// other inputs are read only for selected candidates without waiting), and
+// appends the undecided ones to the list (one atomic per warp).  WHAT is the
+// status filter (for CRP_COLLECT_ALL no status is read); indices are 32-bit
+// (the host checks n < 2^31, as the list of undecided indices needs).
+template <int WHAT>
+__global__ void k_lens_apply_f32(DevState st, uint32_t n, LensArgs a, uint32_t* fallback,
+                                 unsigned long long* n_fallback) {
+  constexpr int what = WHAT;
   const int lane = threadIdx.x & 31;
-  for (uint64_t base = blockIdx.x * (uint64_t)blockDim.x; base < n;
-       base += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t k = base + threadIdx.x;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  uint32_t base = blockIdx.x * blockDim.x;
+  uint32_t k = base + threadIdx.x;
+  // current candidate
+  // the candidate arrays are read once: streaming loads (evict first), so
+  // that the lens tables stay in L2
+  bool sel = k < n && pick(what, __ldcs(st.status + k));
+  int Z = 0;
+  double E = 0.0, ux = 0.0, uy = 0.0, uz = 0.0;
+  uint64_t id = 0;
+  if (sel) {
+    Z = __ldcs(st.Z + k);
+    E = __ldcs(st.E + k);
+    ux = __ldcs(st.ux + k);
+    uy = __ldcs(st.uy + k);
+    uz = __ldcs(st.uz + k);
+    id = __ldcs(reinterpret_cast<const unsigned long long*>(st.id) + k);
+  }
+  // the next candidate's status
+  bool sel_next = k + stride < n && pick(what, __ldcs(st.status + k + stride));
+  for (; base < n; base += stride) {
+    const uint32_t kn = k + stride, knn = kn + stride;
+    int Z2 = 0;
+    double E2 = 0.0, ux2 = 0.0, uy2 = 0.0, uz2 = 0.0;
+    uint64_t id2 = 0;
+    if (sel_next) {
+      Z2 = __ldcs(st.Z + kn);
+      E2 = __ldcs(st.E + kn);
+      ux2 = __ldcs(st.ux + kn);
+      uy2 = __ldcs(st.uy + kn);
+      uz2 = __ldcs(st.uz + kn);
+      id2 = __ldcs(reinterpret_cast<const unsigned long long*>(st.id) + kn);
+    }
+    const bool sel_nn = knn < n && pick(what, __ldcs(st.status + knn));
     bool defer = false;
-    if (k < n && pick(what, st.status[k])) {
-      const int Z = st.Z[k];
-      if (Z <= 0) {
-        st.lens_pixel[k] = kNotApplied;
-      } else {
-        int b, pk32;
-        int64_t j;
-        bool sure = a.use_f32 && lens_bin_f32(st.E[k], Z, a.inv_rlo_f, a.inv_f, a.n_bins, &b);
-        sure = sure && healpix_ring_pixel_try<true>(a.nside, st.ux[k], st.uy[k], st.uz[k], &j);
-        if (sure) {
-          const int64_t col = (int64_t)b * a.npix + j;
-          const uint32_t start = a.col_start[col];
-          const uint32_t count = a.col_start[col + 1] - start;
-          uint32_t out = kNotObserved;
-          if (count > 0) {
-            const uint32_t mxi = a.max_count[b];
-            const Philox4 w = draw4(a.seed, 3u, st.id[k], 0u);
-            // u1 lies in [h1, h1 + 2^-24) with h1 its top 24 bits (exact in
-            // binary32): u1 * max_count is known to 2.4e-7 * max_count
-            const float mxf = (float)mxi, cf = (float)count;
-            const float p1 = (float)(w.v1 >> 8) * 5.9604644775390625e-8f * mxf;
-            if (fabsf(p1 - cf) > 2e-6f * mxf) {
-              if (p1 < cf) {
-                const float p2 = (float)(w.v3 >> 8) * 5.9604644775390625e-8f * cf;
-                if (floor_sure(p2, 2e-6f * cf, &pk32))
-                  out = a.entries[start + pk32];
-                else
-                  sure = false;
-              }
-            } else {
-              sure = false;
-            }
-          }
-          if (sure) st.lens_pixel[k] = out;
-        }
-        defer = !sure;
-      }
+    if (sel) {
+      uint32_t out;
+      defer = !lens_decide_f32(a, Z, E, ux, uy, uz, id, &out);
+      if (!defer) __stcs(st.lens_pixel + k, out);
     }
     // append the undecided candidates of this warp to the list
     const unsigned m = __ballot_sync(0xffffffffu, defer);
@@ -282,8 +328,17 @@ __global__ void k_lens_apply_f32(DevState st, uint64_t n, int what, LensArgs a,
       const int leader = __ffs(m) - 1;
       if (lane == leader) slot = atomicAdd(n_fallback, (unsigned long long)__popc(m));
       slot = __shfl_sync(0xffffffffu, slot, leader);
-      if (defer) fallback[slot + __popc(m & ((1u << lane) - 1u))] = (uint32_t)k;
+      if (defer) fallback[slot + __popc(m & ((1u << lane) - 1u))] = k;
     }
+    k = kn;
+    sel = sel_next;
+    sel_next = sel_nn;
+    Z = Z2;
+    E = E2;
+    ux = ux2;
+    uy = uy2;
+    uz = uz2;
+    id = id2;
   }
 }
 
@@ -759,6 +814,10 @@ crp_status crp_lens_apply(crp_context* ctx, const crp_lens* L, int32_t what, voi
     return CRP_E_INVALID;
   }
   if (n == 0) return CRP_OK;
+  if (n >= (1ull << 31)) {
+    set_error("crp_lens_apply: %llu candidates; at most 2^31 - 1", (unsigned long long)n);
+    return CRP_E_INVALID;
+  }
   int prev = -1;
   cudaGetDevice(&prev);
   if (prev != device) cudaSetDevice(device);
@@ -784,14 +843,36 @@ crp_status crp_lens_apply(crp_context* ctx, const crp_lens* L, int32_t what, voi
   uint32_t* list = nullptr;
   unsigned long long* cnt = nullptr;
   context_scratch(ctx, &list, &cnt);
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s);
   if (e == cudaSuccess) {
-    k_lens_apply_f32<<<blocks(n, 256), 256, 0, s>>>(st, n, what, a, list, cnt);
+    // 32 blocks of 256 per SM: several candidates per thread, so that the
+    // next one's inputs load while this one is decided
+    const uint64_t g = (uint64_t)(sms > 0 ? sms : 1) * 32;
+    const uint64_t need = blocks(n, 256);
+    const unsigned grid = (unsigned)(need < g ? need : g);
+    const uint32_t n32 = (uint32_t)n;
+    switch (what) {
+      case CRP_COLLECT_ALL:
+        k_lens_apply_f32<CRP_COLLECT_ALL><<<grid, 256, 0, s>>>(st, n32, a, list, cnt);
+        break;
+      case CRP_COLLECT_FINISHED:
+        k_lens_apply_f32<CRP_COLLECT_FINISHED><<<grid, 256, 0, s>>>(st, n32, a, list, cnt);
+        break;
+      case CRP_COLLECT_DETECTED:
+        k_lens_apply_f32<CRP_COLLECT_DETECTED><<<grid, 256, 0, s>>>(st, n32, a, list, cnt);
+        break;
+      case CRP_COLLECT_ACTIVE:
+        k_lens_apply_f32<CRP_COLLECT_ACTIVE><<<grid, 256, 0, s>>>(st, n32, a, list, cnt);
+        break;
+      default:
+        k_lens_apply_f32<CRP_COLLECT_AT_BORDER><<<grid, 256, 0, s>>>(st, n32, a, list, cnt);
+        break;
+    }
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     k_lens_apply_f64<<<(unsigned)(sms > 0 ? sms : 1) * 4, 256, 0, s>>>(st, a, list, cnt);
     e = cudaGetLastError();
   }

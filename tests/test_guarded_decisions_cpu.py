@@ -7,10 +7,54 @@ and checks, against the oracle's binary64 decisions, that (1) every decision
 the guards call sure is the binary64 one and (2) the largest binary32 error
 seen stays well inside the guard.  The GPU tests check the kernels
 themselves pixel by pixel."""
+import os
+import re
+
 import numpy as np
 import pytest
 
 f32 = np.float32
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                      "paper_1307_2643_gb300", "csrc", "device_common.cuh")
+
+
+def _phase_coefficients():
+    """The binary32 coefficients of the kernel's phase polynomial, highest
+    degree first, read from its source so that the test checks what is
+    compiled."""
+    src = open(HEADER).read()
+    body = src[src.index("float phase_quarter_turns("):]
+    body = body[:body.index("\n}\n")]
+    first = re.search(r"float p = (-?[0-9.e+-]+)f;", body).group(1)
+    rest = re.findall(r"p = fmaf\(p, s, (-?[0-9.e+-]+)f\);", body)
+    return [f32(float(c)) for c in [first] + rest]
+
+
+def _fma32(a, b, c):
+    """binary32 fma: the product is exact in binary64, one rounding of the sum
+    (a binary64 rounding first, harmless at the bounds tested)."""
+    return (np.asarray(a, np.float64) * np.asarray(b, np.float64)
+            + np.asarray(c, np.float64)).astype(f32)
+
+
+def _phase32(x, y):
+    """The kernel's phase in quarter turns, t in [0, 4), in binary32 (the
+    quotient correctly rounded here; __fdividef's 2 ulp are in the bound)."""
+    C = _phase_coefficients()
+    ax, ay = np.abs(x), np.abs(y)
+    mn, mx = np.minimum(ax, ay), np.maximum(ax, ay)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        r = np.where(mx > 0, (mn / np.where(mx > 0, mx, f32(1))).astype(f32), f32(0)).astype(f32)
+    s = (r * r).astype(f32)
+    p = np.full_like(s, C[0])
+    for c in C[1:]:
+        p = _fma32(p, s, c)
+    g = (p * r).astype(f32)
+    west, south = x < 0, y < 0
+    base = np.where(west, f32(2), np.where(south, f32(4), f32(0))).astype(f32)
+    sg = np.where(west == south, f32(1), f32(-1)).astype(f32)
+    steep = ay > ax
+    return _fma32(np.where(steep, -sg, sg), g, np.where(steep, (base + sg).astype(f32), base))
 
 
 def _trunc32(x):
@@ -34,13 +78,11 @@ def _floor_sure(a, g):
     return fl.astype(np.int64), (f >= g) & (f <= f32(1) - g)
 
 
-def _pixel_guarded(ns, u, guard_per_nside=1e-5):
+def _pixel_guarded(ns, u, guard_per_nside=6e-6):
     fx, fy, fz = _trunc32(u[:, 0]), _trunc32(u[:, 1]), _trunc32(u[:, 2])
     nsf = f32(ns)
     g = f32(guard_per_nside) * nsf
-    phi = np.arctan2(fy, fx).astype(f32)
-    phi = np.where(phi < 0, (phi + f32(6.28318530717958647692)).astype(f32), phi)
-    tt = (phi / f32(1.57079632679489661923)).astype(f32)
+    tt = _phase32(fx, fy)
     itt, ok = _floor_sure(tt, f32(2e-5))
     za = np.abs(fz)
     ok &= np.abs((za - f32(2.0 / 3.0)).astype(f32)) > f32(1e-6)
@@ -102,9 +144,36 @@ def test_guarded_pixels_agree_with_binary64(oracle, nside):
     want = oracle.ang2pix_vec(nside, u)
     pix, ok, err_over_ns = _pixel_guarded(nside, u)
     assert np.array_equal(pix[ok], want[ok])
-    # the kernel's guard is nside * 1e-5, its error bound nside * 2.5e-6
-    assert err_over_ns < 2.5e-6 and err_over_ns < 1e-5 / 3
+    # the kernel's guard is nside * 6e-6, its error bound nside * 1.5e-6
+    assert err_over_ns < 1.5e-6 and err_over_ns < 6e-6 / 3
     assert ok[:500_000].mean() > (0.99 if nside <= 64 else 0.9)
+
+
+def test_phase_polynomial_within_its_bound():
+    """(2/pi) atan(r) ~ r P(r^2) on [0, 1]: within 4.5e-8 with the binary32
+    coefficients in exact (binary64) arithmetic; the whole binary32 phase
+    within 3.9e-7 of the exact phase of its binary32 inputs, on directions of
+    every octant, the axes and the diagonals."""
+    C = [float(c) for c in _phase_coefficients()]
+    assert len(C) == 8
+    r = np.linspace(0.0, 1.0, 2_000_001)
+    p = np.zeros_like(r)
+    for c in C:
+        p = p * r * r + c
+    assert np.max(np.abs(r * p - (2 / np.pi) * np.arctan(r))) < 4.5e-8
+    g = np.random.default_rng(11)
+    ph = np.concatenate([g.uniform(-np.pi, np.pi, 2_000_000),
+                         np.arange(-8, 9) * np.pi / 8,
+                         np.arange(-8, 9) * np.pi / 8 + 1e-9])
+    rad = np.concatenate([np.ones(2_000_000), g.uniform(1e-6, 1, 34)])
+    x, y = (rad * np.cos(ph)).astype(f32), (rad * np.sin(ph)).astype(f32)
+    t = _phase32(x, y).astype(np.float64)
+    exact = np.arctan2(y.astype(np.float64), x.astype(np.float64))
+    exact = np.where(exact < 0, exact + 2 * np.pi, exact) / (np.pi / 2)
+    err = np.abs(t - exact)
+    err = np.minimum(err, np.abs(err - 4))  # 4 and 0 are the same phase
+    assert err.max() < 3.9e-7
+    assert np.all((t >= 0) & (t <= 4))
 
 
 def test_guarded_bins_agree_with_binary64(oracle):
