@@ -174,17 +174,20 @@ __device__ __forceinline__ int64_t lens_bin_f64(double E, int Z, double lg_lo, d
   return (int64_t)bf;
 }
 
-// The same bin from t = ln(R / r_lo) * inv_dlg in binary32, when its error
-// bound leaves no doubt.  Error of t against the exact value: R / r_lo
-// formed in binary32 from E truncated to binary32 (3e-7 relative in all),
-// logf (1 ulp), the product with inv_dlg: below inv_dlg * 1.3e-6 + |t| *
-// 1.2e-7.  Guard: inv_dlg * 1e-5 + |t| * 1e-6 + 1e-6, 7x that.  False when
-// undecided.
+// The same bin from t = log2(R / r_lo) * inv_dlg ln 2 in binary32, when its
+// error bound leaves no doubt.  Error of t against the exact value: R / r_lo
+// formed in binary32 from E truncated to binary32 (2^-23), 1 / r_lo and the
+// product (2^-24 each) and __fdividef (2 ulp), 4.8e-7 relative in all, so
+// inv_dlg * 4.8e-7 on t; __log2f (CUDA's bound: 2^-22 absolute on [0.5, 2],
+// 2 ulp elsewhere): inv_dlg * 1.7e-7 + |t| * 2.4e-7; the factor inv_dlg ln 2
+// and the product (2^-24 each): |t| * 1.2e-7.  Below inv_dlg * 6.5e-7 + |t| *
+// 3.6e-7 in all; the guard inv_dlg * 1e-5 + |t| * 1.5e-6 + 1e-6 is 15x and
+// 4x that.  False when undecided.
 __device__ __forceinline__ bool lens_bin_f32(double E, int Z, float inv_rlo_f, float inv_f,
-                                             int n_bins, int* b) {
-  const float x = (f32_trunc(E) * inv_rlo_f) / (float)Z;
-  const float t = logf(x) * inv_f;
-  const float g = inv_f * 1e-5f + fabsf(t) * 1e-6f + 1e-6f;
+                                             float inv2_f, int n_bins, int* b) {
+  const float x = __fdividef(f32_trunc(E) * inv_rlo_f, (float)Z);
+  const float t = __log2f(x) * inv2_f;
+  const float g = inv_f * 1e-5f + fabsf(t) * 1.5e-6f + 1e-6f;
   if (t + g < 0.f) {
     *b = 0;
     return true;
@@ -214,7 +217,7 @@ struct LensArgs {
   int64_t nside, npix;
   int n_bins, use_f32;
   double lg_lo, inv_dlg;
-  float inv_rlo_f, inv_f;
+  float inv_rlo_f, inv_f, inv2_f;  // 1 / r_lo, inv_dlg and inv_dlg ln 2 in binary32
   const uint32_t* col_start;
   const uint32_t* entries;
   const uint32_t* max_count;
@@ -230,6 +233,27 @@ __device__ __forceinline__ uint32_t lens_pick_f64(const LensArgs& a, const Philo
   return a.entries[start + pk];
 }
 
+// The pick in binary32 when its guards leave no doubt (the binary64 pick's
+// result then); false when undecided.  u1 lies in [h1, h1 + 2^-24) with h1
+// its top 24 bits (exact in binary32): u1 * max_count is known to 2.4e-7 *
+// max_count, and likewise u2 * count.
+__device__ __forceinline__ bool lens_pick_try_f32(const LensArgs& a, const Philox4& w,
+                                                  uint32_t start, uint32_t count, uint32_t mxi,
+                                                  uint32_t* out) {
+  const float mxf = (float)mxi, cf = (float)count;
+  const float p1 = (float)(w.v1 >> 8) * 5.9604644775390625e-8f * mxf;
+  if (!(fabsf(p1 - cf) > 2e-6f * mxf)) return false;
+  if (!(p1 < cf)) {
+    *out = kNotObserved;
+    return true;
+  }
+  const float p2 = (float)(w.v3 >> 8) * 5.9604644775390625e-8f * cf;
+  int pk32;
+  if (!floor_sure(p2, 2e-6f * cf, &pk32)) return false;
+  *out = a.entries[start + pk32];
+  return true;
+}
+
 // The binary32 decisions of one selected candidate: its lens pixel written
 // when every decision is sure; false (written nothing) when it must go to
 // the binary64 pass.  The candidate's uniforms do not depend on the lens, so
@@ -241,9 +265,9 @@ __device__ __forceinline__ bool lens_decide_f32(const LensArgs& a, int Z, double
     *pixel_out = kNotApplied;
     return true;
   }
-  int b, pk32;
+  int b;
   int64_t j;
-  bool sure = a.use_f32 && lens_bin_f32(E, Z, a.inv_rlo_f, a.inv_f, a.n_bins, &b);
+  bool sure = a.use_f32 && lens_bin_f32(E, Z, a.inv_rlo_f, a.inv_f, a.inv2_f, a.n_bins, &b);
   sure = sure && healpix_ring_pixel_try<true>(a.nside, ux, uy, uz, &j);
   if (!sure) return false;
   // column keys are 32-bit (the lens build checks n_bins * npix < 2^32)
@@ -253,18 +277,7 @@ __device__ __forceinline__ bool lens_decide_f32(const LensArgs& a, int Z, double
   const uint32_t mxi = a.max_count[b];
   const Philox4 w = draw4(a.seed, 3u, id, 0u);
   uint32_t out = kNotObserved;
-  if (count > 0) {
-    // u1 lies in [h1, h1 + 2^-24) with h1 its top 24 bits (exact in
-    // binary32): u1 * max_count is known to 2.4e-7 * max_count
-    const float mxf = (float)mxi, cf = (float)count;
-    const float p1 = (float)(w.v1 >> 8) * 5.9604644775390625e-8f * mxf;
-    if (!(fabsf(p1 - cf) > 2e-6f * mxf)) return false;
-    if (p1 < cf) {
-      const float p2 = (float)(w.v3 >> 8) * 5.9604644775390625e-8f * cf;
-      if (!floor_sure(p2, 2e-6f * cf, &pk32)) return false;
-      out = a.entries[start + pk32];
-    }
-  }
+  if (count > 0 && !lens_pick_try_f32(a, w, start, count, mxi, &out)) return false;
   *pixel_out = out;
   return true;
 }
@@ -348,14 +361,27 @@ __global__ void k_lens_apply_f64(DevState st, LensArgs a, const uint32_t* fallba
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
        i += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t k = fallback[i];
-    const int64_t b = lens_bin_f64(st.E[k], st.Z[k], a.lg_lo, a.inv_dlg, a.n_bins);
-    const int64_t j = healpix_ring_pixel(a.nside, -st.ux[k], -st.uy[k], -st.uz[k]);
+    // each decision again in binary32 first (deterministic: the same sure
+    // results as the first pass); binary64 only for those inside their guard
+    const double E = st.E[k], ux = st.ux[k], uy = st.uy[k], uz = st.uz[k];
+    const int Z = st.Z[k];
+    int b32;
+    const int64_t b = a.use_f32 && lens_bin_f32(E, Z, a.inv_rlo_f, a.inv_f, a.inv2_f, a.n_bins, &b32)
+                          ? (int64_t)b32
+                          : lens_bin_f64(E, Z, a.lg_lo, a.inv_dlg, a.n_bins);
+    int64_t j;
+    if (!healpix_ring_pixel_try<true>(a.nside, ux, uy, uz, &j))
+      j = healpix_ring_pixel(a.nside, -ux, -uy, -uz);
     const int64_t col = b * a.npix + j;
     const uint32_t start = a.col_start[col];
     const uint32_t count = a.col_start[col + 1] - start;
     uint32_t out = kNotObserved;
-    if (count > 0) out = lens_pick_f64(a, draw4(a.seed, 3u, st.id[k], 0u), start, count,
-                                       a.max_count[b]);
+    if (count > 0) {
+      const Philox4 w = draw4(a.seed, 3u, st.id[k], 0u);
+      const uint32_t mxi = a.max_count[b];
+      if (!lens_pick_try_f32(a, w, start, count, mxi, &out))
+        out = lens_pick_f64(a, w, start, count, mxi);
+    }
     st.lens_pixel[k] = out;
   }
 }
@@ -826,7 +852,9 @@ crp_status crp_lens_apply(crp_context* ctx, const crp_lens* L, int32_t what, voi
   const double inv = (double)L->n_bins / (series_log(L->r_hi) - lg_lo);
   // binary32 bin decisions need 1 / r_lo and inv_dlg as normal binary32 numbers
   const float inv_rlo_f = (float)(1.0 / L->r_lo), inv_f = (float)inv;
-  const int use_f32 = std::isnormal(inv_rlo_f) && std::isnormal(inv_f) ? 1 : 0;
+  const float inv2_f = (float)(inv * 0.693147180559945309417);
+  const int use_f32 =
+      std::isnormal(inv_rlo_f) && std::isnormal(inv_f) && std::isnormal(inv2_f) ? 1 : 0;
   LensArgs a;
   a.seed = seed;
   a.nside = L->nside;
@@ -837,6 +865,7 @@ crp_status crp_lens_apply(crp_context* ctx, const crp_lens* L, int32_t what, voi
   a.inv_dlg = inv;
   a.inv_rlo_f = inv_rlo_f;
   a.inv_f = inv_f;
+  a.inv2_f = inv2_f;
   a.col_start = L->col_start;
   a.entries = L->entries;
   a.max_count = L->max_count;

@@ -149,6 +149,30 @@ def test_guarded_pixels_agree_with_binary64(oracle, nside):
     assert ok[:500_000].mean() > (0.99 if nside <= 64 else 0.9)
 
 
+def test_unit_range_truncation_matches_the_general_one():
+    """f32_trunc_unit's shortcut for |x| < 2 (the upper word shifted left by
+    three with three bits of the lower word, rebiased by 384 << 23) gives the
+    same binary32 as the general truncation, and +-0 below 2^-126."""
+    g = np.random.default_rng(5)
+    x = np.concatenate([g.uniform(-2, 2, 1_000_000), g.normal(size=1000) * 1e-30,
+                        np.ldexp(1.0, np.arange(-130, 1)), -np.ldexp(1.0, np.arange(-130, 1)),
+                        [0.0, -0.0, 1.0, -1.0, np.nextafter(2.0, 0), -np.nextafter(2.0, 0),
+                         np.nextafter(1.0, 2), np.ldexp(1.0, -126), np.nextafter(np.ldexp(1.0, -126), 0)]])
+    b = x.view(np.uint64)
+    hi = (b >> np.uint64(32)).astype(np.uint32)
+    lo = (b & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    sign = hi & np.uint32(0x80000000)
+    ah = hi & np.uint32(0x7FFFFFFF)
+    assert np.all(ah < np.uint32(0x40000000))
+    funnel = ((hi.astype(np.uint64) << np.uint64(3)) | (lo.astype(np.uint64) >> np.uint64(29)))
+    m = ((funnel & np.uint64(0xFFFFFFFF)) - np.uint64(384 << 23)) & np.uint64(0xFFFFFFFF)
+    bits = np.where(ah < np.uint32(897 << 20), sign, sign | m.astype(np.uint32)).astype(np.uint32)
+    got = bits.view(np.float32)
+    want = np.where(np.abs(x) < np.ldexp(1.0, -126), np.copysign(0.0, x), x)
+    want = _trunc32(want)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
 def test_phase_polynomial_within_its_bound():
     """(2/pi) atan(r) ~ r P(r^2) on [0, 1]: within 4.5e-8 with the binary32
     coefficients in exact (binary64) arithmetic; the whole binary32 phase
@@ -190,9 +214,11 @@ def test_guarded_bins_agree_with_binary64(oracle):
         inv = nb / (oracle.series_log(r_hi) - lg_lo)
         t = (oracle.series_log_vec(E / Z) - lg_lo) * inv
         want = np.clip(np.floor(t), 0, nb - 1).astype(np.int64)
+        # the kernel: __fdividef and __log2f (modelled correctly rounded here;
+        # their documented error is in the kernel's bound), times inv ln 2
         x = ((_trunc32(E) * f32(1.0 / r_lo)).astype(f32) / Z.astype(f32)).astype(f32)
-        tf = (np.log(x).astype(f32) * f32(inv)).astype(f32)
-        gg = (f32(inv) * f32(1e-5) + np.abs(tf) * f32(1e-6) + f32(1e-6)).astype(f32)
+        tf = (np.log2(x).astype(f32) * f32(inv * np.log(2.0))).astype(f32)
+        gg = (f32(inv) * f32(1e-5) + np.abs(tf) * f32(1.5e-6) + f32(1e-6)).astype(f32)
         b, ok = _floor_sure(tf, gg)
         lo, hi = (tf + gg) < 0, (tf - gg) >= f32(nb - 1)
         b = np.where(lo, 0, np.where(hi, nb - 1, b))
@@ -200,7 +226,7 @@ def test_guarded_bins_agree_with_binary64(oracle):
         assert np.array_equal(b[ok], want[ok])
         inside = np.abs(t) < nb + 5
         err = np.abs(tf.astype(np.float64) - t)[inside]
-        bound = float(inv) * 1.3e-6 + np.abs(t[inside]) * 1.2e-7
+        bound = float(inv) * 6.5e-7 + np.abs(t[inside]) * 3.6e-7
         assert np.all(err <= bound)
         assert ok[k:].mean() > 0.99
 
