@@ -45,6 +45,7 @@ struct crp_mlp {
   int64_t step;
   std::vector<__nv_bfloat16*> wb, wbt;  // bf16 copies of hidden layers' W and W^T
   std::vector<__nv_bfloat16*> wimg;     // bf16 core-matrix images for the tcgen05 forward
+  std::vector<__nv_bfloat16*> wimgT;    // the same images of W^T (one-kernel training step)
   unsigned* tc_err;                     // tcgen05 forward: wait-timeout flag
   int forward_path;                     // CRP_MLP_PATH_*
   int sm_count;
@@ -54,10 +55,11 @@ struct crp_mlp {
   __nv_bfloat16 *dz, *dz2, *dzt, *ht;
   float *y, *dy, *loss;
   // tensor-core training workspace: transposed activations of the layers that
-  // feed a hidden GEMM, and two transposed backward signals [hidden][tcap]
+  // feed a hidden GEMM, and transposed backward signals [hidden][tcap] (two,
+  // or three for the one-kernel training step)
   int64_t tcap;
   std::vector<__nv_bfloat16*> hT;
-  __nv_bfloat16 *dzT, *dzT2;
+  __nv_bfloat16 *dzT, *dzT2, *dzT3;
   // the tensor-core training step as a CUDA graph, replayed with the Adam
   // node's arguments updated; each step's x and t are first copied into the
   // fixed staging buffers xs, ts the graph reads
@@ -663,13 +665,16 @@ __global__ void k_adam(float* p, const float* g, float* m, float* v, int64_t n, 
 }
 
 // bf16 copies W (hidden x hidden) and W^T of a hidden layer, and (when img
-// is given) W in the tensor-core operand image of the fused forward kernel:
-// element (o, i) at (o / 8) * (8 n) + (i / 8) * 64 + (o % 8) * 8 + i % 8.
+// is given) W in the tensor-core operand image of the fused kernels:
+// element (o, i) at (o / 8) * (8 n) + (i / 8) * 64 + (o % 8) * 8 + i % 8, and
+// W^T in the same image (imgT): element (o, i) of W at
+// (i / 8) * (8 n) + (o / 8) * 64 + (i % 8) * 8 + o % 8.
 struct Bf16Jobs {
   const float* W[16];
   __nv_bfloat16* wb[16];
   __nv_bfloat16* wbt[16];
   __nv_bfloat16* img[16];
+  __nv_bfloat16* imgT[16];
 };
 
 __global__ void k_to_bf16_pair(const Bf16Jobs jobs, int n) {
@@ -677,6 +682,7 @@ __global__ void k_to_bf16_pair(const Bf16Jobs jobs, int n) {
   __nv_bfloat16* __restrict__ wb = jobs.wb[blockIdx.y];
   __nv_bfloat16* __restrict__ wbt = jobs.wbt[blockIdx.y];
   __nv_bfloat16* __restrict__ img = jobs.img[blockIdx.y];
+  __nv_bfloat16* __restrict__ imgT = jobs.imgT[blockIdx.y];
   const int64_t total = (int64_t)n * n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -685,6 +691,7 @@ __global__ void k_to_bf16_pair(const Bf16Jobs jobs, int n) {
     wb[e] = v;
     wbt[(int64_t)i * n + o] = v;
     if (img) img[(int64_t)(o >> 3) * (8 * n) + (i >> 3) * 64 + (o & 7) * 8 + (i & 7)] = v;
+    if (imgT) imgT[(int64_t)(i >> 3) * (8 * n) + (o >> 3) * 64 + (i & 7) * 8 + (o & 7)] = v;
   }
 }
 
@@ -733,7 +740,8 @@ void free_tws(crp_mlp* M) {
   M->hT.clear();
   dev_free(M->dzT);
   dev_free(M->dzT2);
-  M->dzT = M->dzT2 = nullptr;
+  dev_free(M->dzT3);
+  M->dzT = M->dzT2 = M->dzT3 = nullptr;
   M->tcap = 0;
 }
 
@@ -766,6 +774,12 @@ crp_status ensure_stage(crp_mlp* M, int64_t n) {
   return CRP_OK;
 }
 
+// The one-kernel training step applies: the tensor-core shapes with three
+// hidden-to-hidden layers (the surrogate's 4 x 256).
+bool train_fused_ok(const crp_mlp* M) {
+  return !M->wimg.empty() && M->hidden == 256 && M->n_hidden - 1 == kMlpTrainGemm;
+}
+
 // Transposed activations for the tensor-core training step (allocated only
 // when training on that path).
 crp_status ensure_tws(crp_mlp* M, int64_t n) {
@@ -777,7 +791,8 @@ crp_status ensure_tws(crp_mlp* M, int64_t n) {
     M->hT.push_back(static_cast<__nv_bfloat16*>(dev_alloc(hb)));
   M->dzT = static_cast<__nv_bfloat16*>(dev_alloc(hb));
   M->dzT2 = static_cast<__nv_bfloat16*>(dev_alloc(hb));
-  bool ok = M->dzT && M->dzT2;
+  if (train_fused_ok(M)) M->dzT3 = static_cast<__nv_bfloat16*>(dev_alloc(hb));
+  bool ok = M->dzT && M->dzT2 && (M->dzT3 || !train_fused_ok(M));
   for (auto* p : M->hT) ok = ok && p;
   if (!ok) {
     free_tws(M);
@@ -822,6 +837,7 @@ crp_status refresh_bf16(crp_mlp* M, cudaStream_t s) {
     jobs.wb[nj] = M->wb[l];
     jobs.wbt[nj] = M->wbt[l];
     jobs.img[nj] = M->wimg.empty() ? nullptr : M->wimg[l];
+    jobs.imgT[nj] = M->wimgT.empty() ? nullptr : M->wimgT[l];
   }
   if (nj > 0) {
     const int64_t total = (int64_t)M->hidden * M->hidden;
@@ -1082,6 +1098,76 @@ crp_status backward(crp_mlp* M, const float* x, const float* t, int64_t n, cudaS
   return e == cudaSuccess ? CRP_OK : fail_cuda(e, "mlp: backward");
 }
 
+// Gradients of one training step on the tensor cores with the per-sample work
+// in one kernel (forward, output layer and loss, backward signals, the input
+// and output layers' gradients), then the hidden layers' weight gradients
+// dW_l = dz_l^T h_{l-1} and bias sums as split-K GEMMs over the transposed
+// signals that kernel wrote.
+crp_status train_fused(crp_mlp* M, const float* x, const float* t, int64_t n, cudaStream_t s) {
+  const int H = M->hidden, L = M->n_hidden;
+  cudaError_t e = cudaMemsetAsync(M->grad, 0, sizeof(float) * M->n_params, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(M->loss, 0, sizeof(float), s);
+  MlpTrainTcParams P;
+  memset(&P, 0, sizeof(P));
+  P.x = x;
+  P.t = t;
+  P.n_in = M->n_in;
+  P.n = n;
+  P.n_tiles = n / 128;
+  P.W1 = M->params + M->w_off[0];
+  P.b1 = M->params + M->b_off[0];
+  for (int l = 1; l < L; ++l) {
+    P.Wimg[l - 1] = M->wimg[l];
+    P.WimgT[l - 1] = M->wimgT[l];
+    P.bh[l - 1] = M->params + M->b_off[l];
+  }
+  P.Wout = M->params + M->w_off[L];
+  P.bout = M->params + M->b_off[L];
+  for (int l = 0; l + 1 < L; ++l) P.hT[l] = M->hT[l];
+  __nv_bfloat16* sig[kMlpTrainGemm] = {M->dzT, M->dzT2, M->dzT3};
+  for (int l = L - 1, k = 0; l >= 1; --l, ++k) P.dzT[l] = sig[k];
+  P.ldt = n;
+  P.loss = M->loss;
+  P.gW1 = M->grad + M->w_off[0];
+  P.gb1 = M->grad + M->b_off[0];
+  P.gWout = M->grad + M->w_off[L];
+  P.gbout = M->grad + M->b_off[L];
+  P.err = M->tc_err;
+  if (e == cudaSuccess) e = mlp_train_tc(P, M->sm_count, s);
+  if (e != cudaSuccess) return fail_cuda(e, "mlp: tensor-core training kernel");
+  for (int l = L - 1; l >= 1; --l) {
+    // dW_l += dz_l^T h_{l-1}: A = dz_l^T [H][n], B = h_{l-1}^T [H][n], K = n split
+    GemmTcParams g;
+    memset(&g, 0, sizeof(g));
+    g.err = M->tc_err;
+    g.A = P.dzT[l];
+    g.lda = n;
+    g.B = M->hT[l - 1];
+    g.ldb = n;
+    g.M = H;
+    g.K = n;
+    const int64_t sp = n / 256 < 1 ? 1 : n / 256;
+    const int64_t sp_max = M->sm_count / 2 > 1 ? M->sm_count / 2 : 1;
+    g.splits = (int)(sp < sp_max ? sp : sp_max);
+    g.out_f = M->grad + M->w_off[l];
+    g.ldf = H;
+    g.rowsum = M->grad + M->b_off[l];  // db_l: the rows of dz_l^T summed over the batch
+    e = gemm_tc(GEMM_TC_ATOMIC, g, M->device, M->sm_count, s);
+    if (e != cudaSuccess) return fail_cuda(e, "mlp: tensor-core weight-gradient GEMM");
+  }
+  return CRP_OK;
+}
+
+// Gradients of one training step: the one-kernel form where it applies, else
+// the forward and backward passes.
+crp_status step_gradients(crp_mlp* M, const float* x, const float* t, int64_t n, cudaStream_t s,
+                          bool tc) {
+  if (tc && train_fused_ok(M)) return train_fused(M, x, t, n, s);
+  crp_status st = forward(M, x, n, t, nullptr, s, tc);
+  if (st == CRP_OK) st = backward(M, x, t, n, s, tc);
+  return st;
+}
+
 // Record the tensor-core training step of n samples (reading the staging
 // buffers) as a graph on the private stream; nothing runs.  Any failure
 // leaves the step eager (and clears the error state it raised).
@@ -1097,8 +1183,7 @@ void capture_train_graph(crp_mlp* M, int64_t n) {
     cudaGetLastError();
     return;
   }
-  crp_status st = forward(M, M->xs, n, M->ts, nullptr, cs, true);
-  if (st == CRP_OK) st = backward(M, M->xs, M->ts, n, cs, true);
+  crp_status st = step_gradients(M, M->xs, M->ts, n, cs, true);
   if (st == CRP_OK) {
     k_adam<<<nblk(M->n_params, 256), 256, 0, cs>>>(M->params, M->grad, M->m, M->v, M->n_params,
                                                    0.f, 0.9f, 0.999f, 1e-8f, 1.f, 1.f);
@@ -1166,7 +1251,7 @@ crp_status crp_mlp_create(crp_context* ctx, int32_t n_in, int32_t hidden, int32_
   M->dz = M->dz2 = M->dzt = M->ht = nullptr;
   M->y = M->dy = M->loss = nullptr;
   M->tcap = 0;
-  M->dzT = M->dzT2 = nullptr;
+  M->dzT = M->dzT2 = M->dzT3 = nullptr;
   M->use_graph = true;
   M->tg_graph = nullptr;
   M->tg_exec = nullptr;
@@ -1215,6 +1300,7 @@ crp_status crp_mlp_create(crp_context* ctx, int32_t n_in, int32_t hidden, int32_
   const bool tc = mlp_tc_supported(n_in, hidden, n_hidden, 3);
   if (tc) {
     M->wimg.assign(n_hidden, nullptr);
+    M->wimgT.assign(n_hidden, nullptr);
     M->tc_err = static_cast<unsigned*>(dev_alloc(sizeof(unsigned)));
     ok = ok && M->tc_err;
     if (M->tc_err) cudaMemset(M->tc_err, 0, sizeof(unsigned));
@@ -1225,7 +1311,8 @@ crp_status crp_mlp_create(crp_context* ctx, int32_t n_in, int32_t hidden, int32_
     ok = ok && M->wb[l] && M->wbt[l];
     if (tc) {
       M->wimg[l] = static_cast<__nv_bfloat16*>(dev_alloc(sizeof(__nv_bfloat16) * hidden * hidden));
-      ok = ok && M->wimg[l];
+      M->wimgT[l] = static_cast<__nv_bfloat16*>(dev_alloc(sizeof(__nv_bfloat16) * hidden * hidden));
+      ok = ok && M->wimg[l] && M->wimgT[l];
     }
   }
   int64_t* d_off = static_cast<int64_t*>(dev_alloc(sizeof(int64_t) * offs.size()));
@@ -1273,6 +1360,7 @@ crp_status crp_mlp_destroy(crp_mlp* M) {
   for (auto* p : M->wb) dev_free(p);
   for (auto* p : M->wbt) dev_free(p);
   for (auto* p : M->wimg) dev_free(p);
+  for (auto* p : M->wimgT) dev_free(p);
   dev_free(M->tc_err);
   delete M;
   return CRP_OK;
@@ -1422,8 +1510,7 @@ crp_status crp_mlp_train_step(crp_mlp* M, const float* x, const float* t, int64_
     if (e == cudaSuccess) e = cudaGraphLaunch(M->tg_exec, s);
     if (e != cudaSuccess) return fail_cuda(e, "crp_mlp_train_step: graph replay");
   } else {
-    st = forward(M, x, n, t, nullptr, s, tc);
-    if (st == CRP_OK) st = backward(M, x, t, n, s, tc);
+    st = step_gradients(M, x, t, n, s, tc);
     if (st == CRP_OK && lr > 0.f) {
       M->step += 1;
       const float c1 = 1.f - powf(b1, (float)M->step), c2 = 1.f - powf(b2, (float)M->step);

@@ -344,6 +344,436 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const MlpTcParam
 }
 
 // ---------------------------------------------------------------------------
+// A whole training step's per-sample work in one kernel (hidden 256, three
+// hidden-to-hidden layers), with the forward kernel's layout and thread roles.
+// Per tile of 128 samples:
+//   * input layer -> h_0 (tile A); GEMMs with W_1 .. W_3 -> h_1 .. h_3 (bias,
+//     ReLU); h_0 .. h_2 also written transposed for the weight gradients, and
+//     their ReLU masks kept as bits in registers (thread (row r, half g):
+//     bit k of word q is column 128 g + 32 q + k);
+//   * output layer on the CUDA cores: y = W_out h_3 + b_out from the two
+//     warpgroups' partial sums, y_hat = y / |y|, the loss term 1 - y_hat . t
+//     and dy = -(t - (y_hat . t) y_hat) / |y| / n; per column c the output
+//     layer's gradients sum_r dy[r] h_3[r][c]; then
+//     dz_3 = bf16((dy . W_out[:, c]) where h_3 > 0), in place in tile A;
+//   * GEMMs with W_3^T, W_2^T, W_1^T (images of the transposed weights) ->
+//     dz_2, dz_1, dz_0 = bf16(C where h_{l-1} > 0) in tile A (dz_3 .. dz_1 also
+//     written transposed for the weight gradients);
+//   * per column c the input layer's gradients sum_r dz_0[r][c] x[r][i] and
+//     sum_r dz_0[r][c].
+// The six weight images of a tile are copied into tile B in that order, each
+// as soon as the previous GEMM's MMAs have completed.  Gradient partial sums
+// stay in registers over the CTA's tiles and are added to global memory once.
+// The values are rounded to bf16 where the layered training step rounds them
+// (activations, backward signals), so the two give the same step up to the
+// order of FP32 summation.
+// ---------------------------------------------------------------------------
+constexpr size_t kTrainFloats = kH * kMaxIn + kH + kMlpTrainGemm * kH + 3 * kH + 4 + 6 * kRows +
+                                3 * kRows + kRows + kRows * kMaxIn;
+constexpr size_t kTrainSmem = 1024 + kABytes + kBBytes + 64 + kTrainFloats * 4;
+static_assert(kTrainSmem <= 232448, "shared memory of the training kernel");
+
+// Transposed store of row `row`'s bf16 values (packed pairs w) of columns
+// c0 .. c0 + n - 1: one 2-byte store per column (a warp's 32 consecutive rows
+// make each column's stores one contiguous 64-byte run).
+__device__ __forceinline__ void store_transposed(const uint32_t* w, int n, int64_t row, int c0,
+                                                 __nv_bfloat16* T, int64_t ldt) {
+  unsigned short* t = reinterpret_cast<unsigned short*>(T);
+#pragma unroll
+  for (int j = 0; j < n; ++j)
+    t[(int64_t)(c0 + j) * ldt + row] = (unsigned short)(w[j / 2] >> (16 * (j & 1)));
+}
+
+// Bits of the positive values among 2 nw packed bf16 (bit 2 e: low half of
+// w[e], bit 2 e + 1: high half); a bf16 is positive when its 16 bits, as a
+// signed integer, are.
+__device__ __forceinline__ uint32_t positive_bits(const uint32_t* w, int nw) {
+  uint32_t m = 0;
+#pragma unroll
+  for (int e = 0; e < nw; ++e) {
+    m |= (uint32_t)((short)(w[e] & 0xffffu) > 0) << (2 * e);
+    m |= (uint32_t)((short)(w[e] >> 16) > 0) << (2 * e + 1);
+  }
+  return m;
+}
+
+// Word q of a 4-word register array without dynamic indexing.
+__device__ __forceinline__ uint32_t word_of(const uint32_t (&m)[4], int q) {
+  return q == 0 ? m[0] : (q == 1 ? m[1] : (q == 2 ? m[2] : m[3]));
+}
+__device__ __forceinline__ void set_word(uint32_t (&m)[4], int q, uint32_t v) {
+  m[0] = q == 0 ? v : m[0];
+  m[1] = q == 1 ? v : m[1];
+  m[2] = q == 2 ? v : m[2];
+  m[3] = q == 3 ? v : m[3];
+}
+
+template <int NIN>
+__global__ void __launch_bounds__(kThreads, 1) k_mlp_train_tc(const MlpTrainTcParams P) {
+  constexpr int NG = kMlpTrainGemm;
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  unsigned char* base = tc_smem + ((1024u - (smem_u32(tc_smem) & 1023u)) & 1023u);
+  unsigned char* As = base;
+  unsigned char* Bs = base + kABytes;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(Bs + kBBytes);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
+  float* sW1 = reinterpret_cast<float*>(Bs + kBBytes + 64);  // [kH][kMaxIn]
+  float* sb1 = sW1 + kH * kMaxIn;
+  float* sbh = sb1 + kH;        // [NG][kH]
+  float* sWo = sbh + NG * kH;   // [3][kH]
+  float* sbo = sWo + 3 * kH;    // [4]
+  float* sy = sbo + 4;          // [2 halves][3][kRows] output-layer partial sums
+  float* sdy = sy + 6 * kRows;  // [3][kRows]
+  float* sl = sdy + 3 * kRows;  // [kRows] loss terms
+  float* sx = sl + kRows;       // [kRows][kMaxIn] the tile's inputs
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int r = tid & (kRows - 1);  // row of the tile this thread owns
+  const int g = tid >> 7;           // warpgroup: columns [128 g, 128 g + 128)
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  for (int e = tid; e < kH * kMaxIn; e += kThreads) {
+    const int o = e / kMaxIn, i = e % kMaxIn;
+    sW1[e] = i < P.n_in ? P.W1[o * P.n_in + i] : 0.f;
+  }
+  for (int e = tid; e < kH; e += kThreads) sb1[e] = P.b1[e];
+  for (int l = 0; l < NG; ++l)
+    for (int e = tid; e < kH; e += kThreads) sbh[l * kH + e] = P.bh[l][e];
+  for (int e = tid; e < 3 * kH; e += kThreads) sWo[e] = P.Wout[e];
+  if (tid < 3) sbo[tid] = P.bout[tid];
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t tmem_warp = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+  uint32_t parity = 0;
+  bool failed = false;
+  const float inv_n = 1.f / (float)P.n;
+  // the tile's weight schedule: W_1 .. W_NG, then W_NG^T .. W_1^T
+  auto fetch = [&](int s) {
+    const unsigned char* src = reinterpret_cast<const unsigned char*>(
+        s < NG ? P.Wimg[s] : P.WimgT[2 * NG - 1 - s]);
+    for (uint32_t c = tid; c < kBBytes / 16; c += kThreads) cp_async16(Bs + 16 * c, src + 16 * c);
+  };
+  if (blockIdx.x < P.n_tiles) fetch(0);
+  // step s of the schedule on tiles A and B: wait for its weights, 16 MMAs,
+  // wait for their completion (bounded), start copying the next weights;
+  // false on a timed-out wait
+  auto gemm_step = [&](int s, bool more_tiles) -> bool {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    // generic-proxy writes of A and B -> visible to the tensor cores
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (tid == 0) {
+      const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+#pragma unroll 1
+      for (int k = 0; k < kH / 16; ++k)
+        mma_bf16(tmem, sdesc(a0 + 2u * k * kLbo, kLbo, kSbo), sdesc(b0 + 2u * k * kLbo, kLbo, kSbo),
+                 kIdesc, k > 0 ? 1u : 0u);
+      mma_commit(bar);
+    }
+    bool ok = bar_wait(bar, parity);
+    if (!ok) ok = bar_wait(bar, parity);  // a second bounded wait before giving up
+    parity ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicOr(P.err, 1u);
+      return false;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    // the MMAs are complete: tile B is free for the next weights
+    if (s + 1 < 2 * NG)
+      fetch(s + 1);
+    else if (more_tiles)
+      fetch(0);
+    return true;
+  };
+  auto after_epilogue = [&]() {
+    // TMEM reads done and tile A rewritten before the next MMAs
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  };
+  // gradient partial sums over this CTA's tiles: output and input layer of
+  // column tid; tid 0..2: db_out, tid 3: the loss
+  float go0 = 0.f, go1 = 0.f, go2 = 0.f, gib = 0.f, gsmall = 0.f;
+  float gi[kMaxIn];
+#pragma unroll
+  for (int i = 0; i < kMaxIn; ++i) gi[i] = 0.f;
+
+  for (int64_t tile = blockIdx.x; tile < P.n_tiles && !failed; tile += gridDim.x) {
+    const int64_t row = tile * kRows + r;
+    const bool more = tile + gridDim.x < P.n_tiles;
+    uint32_t mk[NG][4];  // ReLU masks of h_0 .. h_{NG-1}
+    // ---- input layer (FP32): this warpgroup's 128 outputs of row r ----
+    constexpr int NI = NIN > 0 ? NIN : kMaxIn;
+    float xin[kMaxIn];
+#pragma unroll
+    for (int i = 0; i < kMaxIn; ++i)
+      xin[i] = (NIN > 0 ? i < NIN : i < P.n_in) ? P.x[row * (NIN > 0 ? NIN : P.n_in) + i] : 0.f;
+    if (g == 0) {
+#pragma unroll
+      for (int i = 0; i < kMaxIn; ++i) sx[r * kMaxIn + i] = xin[i];
+    }
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {
+      uint32_t mq = 0;
+#pragma unroll 2
+      for (int kk = 0; kk < 4; ++kk) {
+        const int kc = 16 * g + 4 * q + kk;
+        uint32_t w[4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 4) {
+          const float4 bb = *reinterpret_cast<const float4*>(sb1 + kc * 8 + e);
+          const float bq[4] = {bb.x, bb.y, bb.z, bb.w};
+          float v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int o = kc * 8 + e + u;
+            const float4* wr = reinterpret_cast<const float4*>(sW1 + o * kMaxIn);
+            const float4 w0 = wr[0];
+            float acc = bq[u];
+            acc = fmaf(w0.x, xin[0], acc);
+            if (NI > 1) acc = fmaf(w0.y, xin[1], acc);
+            if (NI > 2) acc = fmaf(w0.z, xin[2], acc);
+            if (NI > 3) acc = fmaf(w0.w, xin[3], acc);
+            if (NI > 4) {
+              const float4 w1 = wr[1];
+              acc = fmaf(w1.x, xin[4], acc);
+              if (NI > 5) acc = fmaf(w1.y, xin[5], acc);
+              if (NI > 6) acc = fmaf(w1.z, xin[6], acc);
+              if (NI > 7) acc = fmaf(w1.w, xin[7], acc);
+            }
+            v[u] = fmaxf(acc, 0.f);
+          }
+          w[e / 2] = pack_bf16(v[0], v[1]);
+          w[e / 2 + 1] = pack_bf16(v[2], v[3]);
+        }
+        *reinterpret_cast<uint4*>(As + (r >> 3) * kSbo + kc * kLbo + (r & 7) * 16) =
+            make_uint4(w[0], w[1], w[2], w[3]);
+        store_transposed(w, 8, row, kc * 8, P.hT[0], P.ldt);
+        mq |= positive_bits(w, 4) << (8 * kk);
+      }
+      set_word(mk[0], q, mq);
+    }
+    // ---- forward: the hidden layers on the tensor cores ----
+    float y0 = 0.f, y1 = 0.f, y2 = 0.f;
+#pragma unroll
+    for (int j = 0; j < NG; ++j) {
+      if (!gemm_step(j, more)) {
+        failed = true;
+        break;
+      }
+      const float* bias = sbh + j * kH;
+      const bool last = j == NG - 1;
+#pragma unroll 1
+      for (int q = 0; q < 4; ++q) {
+        const int cc = 4 * g + q;
+        uint32_t v[32];
+        tmem_ld32(tmem_warp + (uint32_t)(cc * 32), v);
+        uint32_t w[16];
+#pragma unroll
+        for (int jj = 0; jj < 32; jj += 4) {
+          const int col = cc * 32 + jj;
+          const float4 b4 = *reinterpret_cast<const float4*>(bias + col);
+          w[jj / 2] = pack_bf16(fmaxf(__uint_as_float(v[jj]) + b4.x, 0.f),
+                                fmaxf(__uint_as_float(v[jj + 1]) + b4.y, 0.f));
+          w[jj / 2 + 1] = pack_bf16(fmaxf(__uint_as_float(v[jj + 2]) + b4.z, 0.f),
+                                    fmaxf(__uint_as_float(v[jj + 3]) + b4.w, 0.f));
+          if (last) {
+            // the output layer reads the bf16-rounded activations
+            const __nv_bfloat162 p01 = *reinterpret_cast<const __nv_bfloat162*>(&w[jj / 2]);
+            const __nv_bfloat162 p23 = *reinterpret_cast<const __nv_bfloat162*>(&w[jj / 2 + 1]);
+            const float a0 = __low2float(p01), a1 = __high2float(p01);
+            const float a2 = __low2float(p23), a3 = __high2float(p23);
+            const float4 wa = *reinterpret_cast<const float4*>(sWo + col);
+            const float4 wb = *reinterpret_cast<const float4*>(sWo + kH + col);
+            const float4 wc = *reinterpret_cast<const float4*>(sWo + 2 * kH + col);
+            y0 = fmaf(wa.x, a0, y0);
+            y0 = fmaf(wa.y, a1, y0);
+            y0 = fmaf(wa.z, a2, y0);
+            y0 = fmaf(wa.w, a3, y0);
+            y1 = fmaf(wb.x, a0, y1);
+            y1 = fmaf(wb.y, a1, y1);
+            y1 = fmaf(wb.z, a2, y1);
+            y1 = fmaf(wb.w, a3, y1);
+            y2 = fmaf(wc.x, a0, y2);
+            y2 = fmaf(wc.y, a1, y2);
+            y2 = fmaf(wc.z, a2, y2);
+            y2 = fmaf(wc.w, a3, y2);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          *reinterpret_cast<uint4*>(As + (r >> 3) * kSbo + (cc * 4 + u) * kLbo + (r & 7) * 16) =
+              make_uint4(w[4 * u], w[4 * u + 1], w[4 * u + 2], w[4 * u + 3]);
+        if (!last) {
+          store_transposed(w, 32, row, cc * 32, P.hT[j + 1], P.ldt);
+          set_word(mk[j + 1], q, positive_bits(w, 16));
+        }
+      }
+      after_epilogue();
+    }
+    if (failed) break;
+    // ---- output layer, loss and dy (CUDA cores) ----
+    sy[(3 * g) * kRows + r] = y0;
+    sy[(3 * g + 1) * kRows + r] = y1;
+    sy[(3 * g + 2) * kRows + r] = y2;
+    __syncthreads();
+    // both halves form the same y: (partial of half 0 + partial of half 1) + b
+    const float Y0 = (sy[r] + sy[3 * kRows + r]) + sbo[0];
+    const float Y1 = (sy[kRows + r] + sy[4 * kRows + r]) + sbo[1];
+    const float Y2 = (sy[2 * kRows + r] + sy[5 * kRows + r]) + sbo[2];
+    const float nrm = sqrtf(Y0 * Y0 + Y1 * Y1 + Y2 * Y2);
+    const float inv = nrm > 0.f ? 1.f / nrm : 0.f;
+    const float yh0 = Y0 * inv, yh1 = Y1 * inv, yh2 = Y2 * inv;
+    const float t0 = P.t[row * 3], t1 = P.t[row * 3 + 1], t2 = P.t[row * 3 + 2];
+    const float d = yh0 * t0 + yh1 * t1 + yh2 * t2;
+    const float dy0 = -(t0 - d * yh0) * inv * inv_n;
+    const float dy1 = -(t1 - d * yh1) * inv * inv_n;
+    const float dy2 = -(t2 - d * yh2) * inv * inv_n;
+    if (g == 0) {
+      sdy[r] = dy0;
+      sdy[kRows + r] = dy1;
+      sdy[2 * kRows + r] = dy2;
+      sl[r] = 1.f - d;
+    }
+    __syncthreads();
+    {
+      // column tid: the output layer's weight gradients over the tile's rows.
+      // Column passes start at row tid / 8: a warp's four 8-column chunks
+      // then sit in four different rows of their core matrices (different
+      // banks) instead of one
+      const unsigned char* cb = As + (tid >> 3) * kLbo + (tid & 7) * 2;
+      const int skew = tid >> 3;
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll 4
+      for (int rr = 0; rr < kRows; ++rr) {
+        const int R = (rr + skew) & (kRows - 1);
+        const float hv = __bfloat162float(
+            *reinterpret_cast<const __nv_bfloat16*>(cb + (R >> 3) * kSbo + (R & 7) * 16));
+        a0 = fmaf(sdy[R], hv, a0);
+        a1 = fmaf(sdy[kRows + R], hv, a1);
+        a2 = fmaf(sdy[2 * kRows + R], hv, a2);
+      }
+      go0 += a0;
+      go1 += a1;
+      go2 += a2;
+      if (tid < 4) {
+        const float* src = tid < 3 ? sdy + tid * kRows : sl;
+        float sacc = 0.f;
+        for (int rr = 0; rr < kRows; ++rr) sacc += src[rr];
+        gsmall += sacc;
+      }
+    }
+    __syncthreads();  // every column has read h_3 before it is overwritten
+    // dz_3 = bf16((dy . W_out[:, c]) where h_3 > 0), in place in tile A
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {
+      const int cc = 4 * g + q;
+      uint32_t w[16];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        uint4* ap = reinterpret_cast<uint4*>(As + (r >> 3) * kSbo + (cc * 4 + u) * kLbo + (r & 7) * 16);
+        const uint4 hq = *ap;
+        const uint32_t hw[4] = {hq.x, hq.y, hq.z, hq.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int c0 = (cc * 4 + u) * 8 + 2 * e;
+          const float z0 = fmaf(dy2, sWo[2 * kH + c0], fmaf(dy1, sWo[kH + c0], dy0 * sWo[c0]));
+          const float z1 =
+              fmaf(dy2, sWo[2 * kH + c0 + 1], fmaf(dy1, sWo[kH + c0 + 1], dy0 * sWo[c0 + 1]));
+          w[4 * u + e] = pack_bf16((short)(hw[e] & 0xffffu) > 0 ? z0 : 0.f,
+                                   (short)(hw[e] >> 16) > 0 ? z1 : 0.f);
+        }
+        *ap = make_uint4(w[4 * u], w[4 * u + 1], w[4 * u + 2], w[4 * u + 3]);
+      }
+      store_transposed(w, 32, row, cc * 32, P.dzT[NG], P.ldt);
+    }
+    // ---- backward: dz_{l-1} = (dz_l W_l) where h_{l-1} > 0, l = NG .. 1 ----
+#pragma unroll
+    for (int j = NG - 1; j >= 0; --j) {
+      if (!gemm_step(2 * NG - 1 - j, more)) {
+        failed = true;
+        break;
+      }
+#pragma unroll 1
+      for (int q = 0; q < 4; ++q) {
+        const int cc = 4 * g + q;
+        uint32_t v[32];
+        tmem_ld32(tmem_warp + (uint32_t)(cc * 32), v);
+        const uint32_t mw = word_of(mk[j], q);
+        uint32_t w[16];
+#pragma unroll
+        for (int jj = 0; jj < 32; jj += 2)
+          w[jj / 2] = pack_bf16((mw >> jj) & 1u ? __uint_as_float(v[jj]) : 0.f,
+                                (mw >> (jj + 1)) & 1u ? __uint_as_float(v[jj + 1]) : 0.f);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          *reinterpret_cast<uint4*>(As + (r >> 3) * kSbo + (cc * 4 + u) * kLbo + (r & 7) * 16) =
+              make_uint4(w[4 * u], w[4 * u + 1], w[4 * u + 2], w[4 * u + 3]);
+        if (j >= 1) store_transposed(w, 32, row, cc * 32, P.dzT[j], P.ldt);
+      }
+      after_epilogue();
+    }
+    if (failed) break;
+    {
+      // column tid: the input layer's gradients from dz_0 and the tile's inputs
+      const unsigned char* cb = As + (tid >> 3) * kLbo + (tid & 7) * 2;
+      const int skew = tid >> 3;
+      float aw[kMaxIn], ab = 0.f;
+#pragma unroll
+      for (int i = 0; i < kMaxIn; ++i) aw[i] = 0.f;
+#pragma unroll 4
+      for (int rr = 0; rr < kRows; ++rr) {
+        const int R = (rr + skew) & (kRows - 1);
+        const float z = __bfloat162float(
+            *reinterpret_cast<const __nv_bfloat16*>(cb + (R >> 3) * kSbo + (R & 7) * 16));
+        ab += z;
+#pragma unroll
+        for (int i = 0; i < NI; ++i) aw[i] = fmaf(z, sx[R * kMaxIn + i], aw[i]);
+      }
+#pragma unroll
+      for (int i = 0; i < NI; ++i) gi[i] += aw[i];
+      gib += ab;
+    }
+    __syncthreads();  // tile A and the staged inputs are rewritten by the next tile
+  }
+  if (!failed) {
+    atomicAdd(P.gWout + tid, go0);
+    atomicAdd(P.gWout + kH + tid, go1);
+    atomicAdd(P.gWout + 2 * kH + tid, go2);
+    constexpr int NI = NIN > 0 ? NIN : kMaxIn;
+#pragma unroll
+    for (int i = 0; i < NI; ++i)
+      if (i < P.n_in) atomicAdd(P.gW1 + tid * P.n_in + i, gi[i]);
+    atomicAdd(P.gb1 + tid, gib);
+    if (tid < 3)
+      atomicAdd(P.gbout + tid, gsmall);
+    else if (tid == 3)
+      atomicAdd(P.loss, gsmall);
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");  // no copy outlives the kernel
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(kTmemCols)
+                 : "memory");
+}
+
+// ---------------------------------------------------------------------------
 // Training GEMM: C[M][256] = A[M][K] B[256][K]^T on the tensor cores.
 // One CTA (256 threads) per SM, persistent over work items (a 128-row tile of
 // C and a range of K).  Per 256-wide K chunk one thread starts TMA copies of
@@ -807,6 +1237,17 @@ cudaError_t mlp_forward_tc(const MlpTcParams& p, int sm_count, cudaStream_t s) {
 
 cudaError_t mlp_forward_tc_train(const MlpTcParams& p, int sm_count, cudaStream_t s) {
   return launch_forward_tc<true>(p, sm_count, s);
+}
+
+cudaError_t mlp_train_tc(const MlpTrainTcParams& p, int sm_count, cudaStream_t s) {
+  auto k = p.n_in == 4 ? k_mlp_train_tc<4> : k_mlp_train_tc<0>;
+  cudaError_t e =
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrainSmem);
+  if (e != cudaSuccess) return e;
+  int64_t grid = p.n_tiles < sm_count ? p.n_tiles : sm_count;
+  if (grid < 1) return cudaSuccess;
+  k<<<(unsigned)grid, kThreads, kTrainSmem, s>>>(p);
+  return cudaGetLastError();
 }
 
 }  // namespace crp

@@ -73,6 +73,40 @@ struct GemmTcParams {
 };
 cudaError_t gemm_tc(int epi, const GemmTcParams& p, int device, int sm_count, cudaStream_t s);
 
+// One training step's forward pass, output layer, loss and backward signals
+// in one persistent tcgen05 kernel (hidden 256, three hidden-to-hidden
+// layers): per tile of 128 samples the activations and backward signals stay
+// in shared memory, the ReLU masks in registers; written out are the
+// transposed activations h_0 .. h_2 and backward signals dz_1 .. dz_3 the
+// weight-gradient GEMMs read, and the output and input layers' gradients.
+constexpr int kMlpTrainGemm = 3;
+struct MlpTrainTcParams {
+  const float* x;  // [n][n_in]
+  const float* t;  // [n][3] target unit vectors
+  int n_in;
+  int64_t n, n_tiles;  // n = 128 n_tiles
+  const float* W1;     // [256][n_in]
+  const float* b1;
+  // forward images of the hidden weights W_{k+1} (as MlpTcParams::Wimg) and
+  // images of their transposes: element (o, i) of W at
+  // (i / 8) * 2048 + (o / 8) * 64 + (i % 8) * 8 + o % 8
+  const __nv_bfloat16* Wimg[kMlpTrainGemm];
+  const __nv_bfloat16* WimgT[kMlpTrainGemm];
+  const float* bh[kMlpTrainGemm];
+  const float* Wout;  // [3][256]
+  const float* bout;
+  __nv_bfloat16* hT[kMlpTrainGemm];       // h_0 .. h_2 transposed, [256][ldt]
+  __nv_bfloat16* dzT[kMlpTrainGemm + 1];  // dz_1 .. dz_3 transposed (index = layer; 0 unused)
+  int64_t ldt;
+  float* loss;   // += sum over the batch of 1 - y_hat . t
+  float* gW1;    // [256][n_in] +=
+  float* gb1;    // [256] +=
+  float* gWout;  // [3][256] +=
+  float* gbout;  // [3] +=
+  unsigned* err;  // set to 1 when a tensor-core wait timed out
+};
+cudaError_t mlp_train_tc(const MlpTrainTcParams& p, int sm_count, cudaStream_t s);
+
 // Element count of one hidden layer's weight image (256 x 256).
 size_t mlp_tc_weight_image_elems();
 bool mlp_tc_supported(int n_in, int hidden, int n_hidden, int n_out);

@@ -270,11 +270,11 @@ def test_fused_tensor_core_forward_matches_layered(torch_dev, n):
 
 @pytest.mark.parametrize("n", [2048, 128 * 37, 16384])
 def test_tensor_core_training_gradients(torch_dev, n):
-    """The training step on the tcgen05 GEMMs (TMA operand boxes, weight
-    gradients split over K with vector reductions, transposed signals written
-    by the epilogues) against the layered mma.sync step and the binary64
-    oracle.  n = 128 * 37 gives K ranges of 320: two chunks per split, the
-    second 64 wide."""
+    """The training step on the tensor cores (the one-kernel forward, output
+    layer and backward signals, then the weight-gradient GEMMs: TMA operand
+    boxes, split over K with vector reductions) against the layered mma.sync
+    step and the binary64 oracle.  n = 128 * 37 gives K ranges of 320: two
+    chunks per split, the second 64 wide."""
     torch = torch_dev
     p = _params(31)
     x, t = _batch(int(1.25 * n), 32)
@@ -300,6 +300,41 @@ def test_tensor_core_training_gradients(torch_dev, n):
         assert abs(losses[path] - lref) < 1e-4 * max(1.0, lref), (path, losses[path], lref)
         worst = assert_gradients_close(grads[path], flat, SHAPES, cache, t.astype(np.float64), x)
         print(f"n {n} path {path}: worst element / tolerance {worst:.3f}")
+
+
+@pytest.mark.parametrize("n_hidden", [2, 3, 5])
+def test_tensor_core_training_other_depths(torch_dev, n_hidden):
+    """Hidden 256 with 1, 2 or 4 hidden-to-hidden layers: the tensor-core
+    training step as a fused forward kernel plus the output-layer kernel and
+    the backward GEMMs (the one-kernel step covers 3 such layers), against the
+    bf16-mode oracle."""
+    torch = torch_dev
+    shapes = M.layer_shapes(4, 256, n_hidden, 3)
+    g = np.random.default_rng(50 + n_hidden)
+    parts = []
+    for l, (o, i) in enumerate(shapes):
+        scale = np.sqrt((1.0 if l == len(shapes) - 1 else 2.0) / i)
+        parts += [g.normal(scale=scale, size=o * i), g.normal(scale=0.05, size=o)]
+    p = np.concatenate(parts).astype(np.float32)
+    n = 128 * 21
+    x, t = _batch(int(1.3 * n), 60 + n_hidden)
+    keep = unambiguous(_oracle_view(p, shapes), shapes, x, n)
+    x, t = np.ascontiguousarray(x[keep]), np.ascontiguousarray(t[keep])
+    ctx = crp.crp_context_create(0, 1, 16)
+    try:
+        mlp = crp.crp_mlp_create(ctx, 4, 256, n_hidden, 7)
+        crp.crp_mlp_set_params(mlp, p)
+        xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+        loss = crp.crp_mlp_train_step(mlp, xd, td, n, 0.0)
+        grad = crp.crp_mlp_get_params(mlp)[1].astype(np.float64)
+        crp.crp_mlp_destroy(mlp)
+    finally:
+        crp.crp_context_destroy(ctx)
+    flat = _oracle_view(p, shapes)
+    y, cache = M.forward(flat, shapes, x.astype(np.float64), bf16=True)
+    assert abs(loss - M.loss(y, t.astype(np.float64))) < 1e-4 * max(1.0, loss)
+    worst = assert_gradients_close(grad, flat, shapes, cache, t.astype(np.float64), x)
+    print(f"n_hidden {n_hidden}: worst element / tolerance {worst:.3f}")
 
 
 @pytest.mark.parametrize("n_in,hidden,n_hidden", [(4, 512, 3), (12, 384, 3)])
