@@ -1135,9 +1135,12 @@ crp_status train_fused(crp_mlp* M, const float* x, const float* t, int64_t n, cu
   P.err = M->tc_err;
   if (e == cudaSuccess) e = mlp_train_tc(P, M->sm_count, s);
   if (e != cudaSuccess) return fail_cuda(e, "mlp: tensor-core training kernel");
+  // the layers' weight gradients are independent: one launch for all three
+  GemmTcParams gs[kMlpTrainGemm];
+  int ng = 0;
   for (int l = L - 1; l >= 1; --l) {
     // dW_l += dz_l^T h_{l-1}: A = dz_l^T [H][n], B = h_{l-1}^T [H][n], K = n split
-    GemmTcParams g;
+    GemmTcParams& g = gs[ng++];
     memset(&g, 0, sizeof(g));
     g.err = M->tc_err;
     g.A = P.dzT[l];
@@ -1152,9 +1155,9 @@ crp_status train_fused(crp_mlp* M, const float* x, const float* t, int64_t n, cu
     g.out_f = M->grad + M->w_off[l];
     g.ldf = H;
     g.rowsum = M->grad + M->b_off[l];  // db_l: the rows of dz_l^T summed over the batch
-    e = gemm_tc(GEMM_TC_ATOMIC, g, M->device, M->sm_count, s);
-    if (e != cudaSuccess) return fail_cuda(e, "mlp: tensor-core weight-gradient GEMM");
   }
+  e = gemm_tc_batch_atomic(gs, ng, M->device, M->sm_count, s);
+  if (e != cudaSuccess) return fail_cuda(e, "mlp: tensor-core weight-gradient GEMMs");
   return CRP_OK;
 }
 

@@ -841,11 +841,20 @@ __device__ __forceinline__ void bulk_wait_all() {
   asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
 }
 
+// Tensor maps of up to kGemmBatch problems of one shape (the same M, K,
+// splits and epilogue), run as one launch: problem q's operands, output and
+// row sums.  Work items are numbered problem by problem.
+constexpr int kGemmBatch = 3;
+struct GemmTcMaps {
+  CUtensorMap a[kGemmBatch], b[kGemmBatch], o[kGemmBatch];
+  CUtensorMap ot;
+  float* rowsum[kGemmBatch];
+  int n_problems;
+};
+
 template <int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_gemm_tc(const GemmTcParams P, const __grid_constant__ CUtensorMap mapA,
-              const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapO,
-              const __grid_constant__ CUtensorMap mapOT) {
+    k_gemm_tc(const GemmTcParams P, const __grid_constant__ GemmTcMaps maps) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   unsigned char* base = tc_smem + ((1024u - (smem_u32(tc_smem) & 1023u)) & 1023u);
   unsigned char* As = base;               // 4 boxes of 16 KB
@@ -875,23 +884,27 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem_warp = tmem + ((uint32_t)((warp & 3) * 32) << 16);
 
   const int64_t m_tiles = P.M / kRows;
-  const int64_t items = m_tiles * P.splits;
+  const int64_t per = m_tiles * P.splits;  // items of one problem
+  const int64_t items = per * maps.n_problems;
   const int64_t ks = ((P.K + P.splits - 1) / P.splits + 63) / 64 * 64;  // K per split
-  const bool b_resident = P.splits == 1 && P.K <= kH;
+  const bool b_resident = P.splits == 1 && P.K <= kH && maps.n_problems == 1;
   auto row0_of = [&](int64_t mt_) { return mt_ * kRows; };
   auto range = [&](int64_t item, int64_t& kb, int64_t& ke) {
-    kb = (item / m_tiles) * ks;
+    kb = ((item % per) / m_tiles) * ks;
     ke = kb + ks < P.K ? kb + ks : P.K;
   };
   // one thread starts the TMA boxes of a chunk (kc a multiple of 64)
   auto issue = [&](int64_t item, int64_t c0, int kc, bool with_b) {
     if (tid != 0) return;
+    const int q = (int)(item / per);
     const int boxes = kc / 64;
     bar_expect_tx(tbar, (uint32_t)boxes * (kAtomA + (with_b ? kAtomB : 0u)));
-    const int y = (int)((item % m_tiles) * kRows);
-    for (int a = 0; a < boxes; ++a) tma_load_2d(As + a * kAtomA, &mapA, (int)c0 + 64 * a, y, tbar);
+    const int y = (int)(((item % per) % m_tiles) * kRows);
+    for (int a = 0; a < boxes; ++a)
+      tma_load_2d(As + a * kAtomA, &maps.a[q], (int)c0 + 64 * a, y, tbar);
     if (with_b)
-      for (int a = 0; a < boxes; ++a) tma_load_2d(Bs + a * kAtomB, &mapB, (int)c0 + 64 * a, 0, tbar);
+      for (int a = 0; a < boxes; ++a)
+        tma_load_2d(Bs + a * kAtomB, &maps.b[q], (int)c0 + 64 * a, 0, tbar);
   };
   uint32_t parity = 0, tparity = 0;
   bool failed = false, b_loaded = false, prefetched = false;
@@ -900,7 +913,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     int64_t kb, ke;
     range(item, kb, ke);
     if (kb >= ke) continue;  // an empty split (the same for every thread)
-    const int64_t mt = item % m_tiles;
+    const int q = (int)(item / per);
+    const int64_t mt = (item % per) % m_tiles;
+    float* const rowsum = maps.rowsum[q];
     float row_acc = 0.f;
     for (int64_t c0 = kb; c0 < ke; c0 += kH) {
       const int kc = (int)(ke - c0 < kH ? ke - c0 : kH);
@@ -928,7 +943,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         mma_commit(bar);
       }
-      if (P.rowsum) {
+      if (rowsum) {
         // while the MMAs run: thread (row r, half g) sums 4 of the 8 16-byte
         // chunks of its row in every box (the swizzle only permutes a row's
         // chunks, so the sum needs no unswizzling)
@@ -962,7 +977,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // TMA store boxes in the 128-byte-swizzled layout (16-byte chunk j of a
     // 128-byte box row y at position j ^ (y % 8)) ----
     const int64_t row = mt * kRows + r;
-    if (P.rowsum) atomicAdd(P.rowsum + row, row_acc);
+    if (rowsum) atomicAdd(rowsum + row, row_acc);
     unsigned char* stage = base;
 #pragma unroll 1
     for (int cc = 4 * g; cc < 4 * g + 4; ++cc) {
@@ -1042,12 +1057,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (tid == 0) {
       const int y = (int)(mt * kRows);
       if constexpr (EPI == GEMM_TC_ATOMIC) {
-        for (int b = 0; b < 8; ++b) tma_reduce_add_2d(&mapO, 32 * b, y, stage + b * kAtomA);
+        for (int b = 0; b < 8; ++b) tma_reduce_add_2d(&maps.o[q], 32 * b, y, stage + b * kAtomA);
       } else {
-        for (int b = 0; b < 4; ++b) tma_store_2d(&mapO, 64 * b, y, stage + b * kAtomA);
+        for (int b = 0; b < 4; ++b) tma_store_2d(&maps.o[q], 64 * b, y, stage + b * kAtomA);
         if (P.out_t)
           for (int b = 0; b < 2; ++b)
-            tma_store_2d(&mapOT, y + 64 * b, 0, stage + 4 * kAtomA + b * kAtomB);
+            tma_store_2d(&maps.ot, y + 64 * b, 0, stage + 4 * kAtomA + b * kAtomB);
       }
       bulk_commit();
     }
@@ -1184,15 +1199,17 @@ cudaError_t gemm_tc(int epi, const GemmTcParams& p, int device, int sm_count, cu
   if (p.xin) ok = ok && epi == GEMM_TC_MASK && p.n_in >= 1 && p.n_in <= 8 && p.gw_in && p.gb_in;
   if (!ok || epi < GEMM_TC_BIAS_RELU || epi > GEMM_TC_ATOMIC) return cudaErrorInvalidValue;
   // operand maps (loads) and output maps (stores / reductions of the tile)
-  CUtensorMap mapA, mapB, mapO, mapOT;
-  memset(&mapOT, 0, sizeof(mapOT));
-  bool maps = tensor_map(p.A, false, p.M, p.K, p.lda, kRows, &mapA) &&
-              tensor_map(p.B, false, kH, p.K, p.ldb, kH, &mapB);
+  GemmTcMaps tm;
+  memset(&tm, 0, sizeof(tm));
+  tm.n_problems = 1;
+  tm.rowsum[0] = p.rowsum;
+  bool maps = tensor_map(p.A, false, p.M, p.K, p.lda, kRows, &tm.a[0]) &&
+              tensor_map(p.B, false, kH, p.K, p.ldb, kH, &tm.b[0]);
   if (epi == GEMM_TC_ATOMIC) {
-    maps = maps && tensor_map(p.out_f, true, p.M, kH, p.ldf, kRows, &mapO);
+    maps = maps && tensor_map(p.out_f, true, p.M, kH, p.ldf, kRows, &tm.o[0]);
   } else {
-    maps = maps && tensor_map(p.out, false, p.M, kH, p.ldo, kRows, &mapO);
-    if (p.out_t) maps = maps && tensor_map(p.out_t, false, kH, p.M, p.ldot, kH, &mapOT);
+    maps = maps && tensor_map(p.out, false, p.M, kH, p.ldo, kRows, &tm.o[0]);
+    if (p.out_t) maps = maps && tensor_map(p.out_t, false, kH, p.M, p.ldot, kH, &tm.ot);
   }
   if (!maps) return cudaErrorInvalidValue;
   auto k = epi == GEMM_TC_BIAS_RELU ? k_gemm_tc<GEMM_TC_BIAS_RELU>
@@ -1209,7 +1226,39 @@ cudaError_t gemm_tc(int epi, const GemmTcParams& p, int device, int sm_count, cu
   }
   const int64_t items = p.M / kRows * p.splits;
   const int64_t grid = items < sm_count ? items : sm_count;
-  k<<<(unsigned)grid, kThreads, kGemmSmem, s>>>(p, mapA, mapB, mapO, mapOT);
+  k<<<(unsigned)grid, kThreads, kGemmSmem, s>>>(p, tm);
+  return cudaGetLastError();
+}
+
+cudaError_t gemm_tc_batch_atomic(const GemmTcParams* ps, int np, int device, int sm_count,
+                                 cudaStream_t s) {
+  if (np < 1 || np > kGemmBatch) return cudaErrorInvalidValue;
+  if (np == 1) return gemm_tc(GEMM_TC_ATOMIC, ps[0], device, sm_count, s);
+  GemmTcMaps tm;
+  memset(&tm, 0, sizeof(tm));
+  tm.n_problems = np;
+  const GemmTcParams& p0 = ps[0];
+  for (int q = 0; q < np; ++q) {
+    const GemmTcParams& p = ps[q];
+    // one shape for all: the kernel derives items and K ranges from p0
+    const bool ok = p.M == p0.M && p.K == p0.K && p.splits == p0.splits && p.err == p0.err &&
+                    ((uintptr_t)p.A % 16 == 0) && ((uintptr_t)p.B % 16 == 0) && p.lda % 8 == 0 &&
+                    p.ldb % 8 == 0 && p.lda >= p.K && p.ldb >= p.K && p.M > 0 && p.M % kRows == 0 &&
+                    p.K > 0 && p.K % 64 == 0 && p.splits >= 1 && p.err && p.out_f &&
+                    (uintptr_t)p.out_f % 16 == 0 && p.ldf % 4 == 0 && p.ldf >= kH && !p.xin;
+    if (!ok) return cudaErrorInvalidValue;
+    tm.rowsum[q] = p.rowsum;
+    if (!tensor_map(p.A, false, p.M, p.K, p.lda, kRows, &tm.a[q]) ||
+        !tensor_map(p.B, false, kH, p.K, p.ldb, kH, &tm.b[q]) ||
+        !tensor_map(p.out_f, true, p.M, kH, p.ldf, kRows, &tm.o[q]))
+      return cudaErrorInvalidValue;
+  }
+  auto k = k_gemm_tc<GEMM_TC_ATOMIC>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
+  if (e != cudaSuccess) return e;
+  const int64_t items = p0.M / kRows * p0.splits * np;
+  const int64_t grid = items < sm_count ? items : sm_count;
+  k<<<(unsigned)grid, kThreads, kGemmSmem, s>>>(p0, tm);
   return cudaGetLastError();
 }
 
