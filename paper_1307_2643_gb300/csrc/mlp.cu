@@ -651,19 +651,6 @@ __global__ void k_transpose(const __nv_bfloat16* __restrict__ in, int64_t rows, 
     out[(int64_t)(c0 + k) * rows + r0 + threadIdx.x] = tile[threadIdx.x][k];
 }
 
-__global__ void k_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1,
-                       float b2, float eps, float c1, float c2) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-  }
-}
-
 // bf16 copies W (hidden x hidden) and W^T of a hidden layer, and (when img
 // is given) W in the tensor-core operand image of the fused kernels:
 // element (o, i) at (o / 8) * (8 n) + (i / 8) * 64 + (o % 8) * 8 + i % 8, and
@@ -676,6 +663,37 @@ struct Bf16Jobs {
   __nv_bfloat16* img[16];
   __nv_bfloat16* imgT[16];
 };
+
+// Adam step of every parameter; a parameter of a hidden weight matrix
+// (nj jobs, hn x hn each) also goes to that layer's bf16 copies and images,
+// so no separate conversion pass follows the step.
+__global__ void k_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1,
+                       float b2, float eps, float c1, float c2, const Bf16Jobs jobs, int nj,
+                       int hn) {
+  const int64_t nn = (int64_t)hn * hn;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] = pi;
+    for (int j = 0; j < nj; ++j) {
+      const int64_t e = (p + i) - jobs.W[j];
+      if (e < 0 || e >= nn) continue;
+      const int o = (int)(e / hn), ii = (int)(e % hn);
+      const __nv_bfloat16 bv = __float2bfloat16_rn(pi);
+      jobs.wb[j][e] = bv;
+      jobs.wbt[j][(int64_t)ii * hn + o] = bv;
+      if (jobs.img[j])
+        jobs.img[j][(int64_t)(o >> 3) * (8 * hn) + (ii >> 3) * 64 + (o & 7) * 8 + (ii & 7)] = bv;
+      if (jobs.imgT[j])
+        jobs.imgT[j][(int64_t)(ii >> 3) * (8 * hn) + (o >> 3) * 64 + (ii & 7) * 8 + (o & 7)] = bv;
+    }
+  }
+}
 
 __global__ void k_to_bf16_pair(const Bf16Jobs jobs, int n) {
   const float* __restrict__ W = jobs.W[blockIdx.y];
@@ -827,18 +845,24 @@ crp_status ensure_ws(crp_mlp* M, int64_t n) {
   return CRP_OK;
 }
 
+// The bf16 conversion jobs of the hidden layers (at most 16); returns their count.
+int bf16_jobs(const crp_mlp* M, Bf16Jobs* jobs) {
+  memset(jobs, 0, sizeof(*jobs));
+  int nj = 0;
+  for (int l = 1; l < M->n_hidden && nj < 16; ++l, ++nj) {
+    jobs->W[nj] = M->params + M->w_off[l];
+    jobs->wb[nj] = M->wb[l];
+    jobs->wbt[nj] = M->wbt[l];
+    jobs->img[nj] = M->wimg.empty() ? nullptr : M->wimg[l];
+    jobs->imgT[nj] = M->wimgT.empty() ? nullptr : M->wimgT[l];
+  }
+  return nj;
+}
+
 crp_status refresh_bf16(crp_mlp* M, cudaStream_t s) {
   // every hidden layer in one launch (grid.y = layer), up to 16 layers
   Bf16Jobs jobs;
-  memset(&jobs, 0, sizeof(jobs));
-  int nj = 0;
-  for (int l = 1; l < M->n_hidden && nj < 16; ++l, ++nj) {
-    jobs.W[nj] = M->params + M->w_off[l];
-    jobs.wb[nj] = M->wb[l];
-    jobs.wbt[nj] = M->wbt[l];
-    jobs.img[nj] = M->wimg.empty() ? nullptr : M->wimg[l];
-    jobs.imgT[nj] = M->wimgT.empty() ? nullptr : M->wimgT[l];
-  }
+  const int nj = bf16_jobs(M, &jobs);
   if (nj > 0) {
     const int64_t total = (int64_t)M->hidden * M->hidden;
     const unsigned gx = (unsigned)((total + 255) / 256 < 1024 ? (total + 255) / 256 : 1024);
@@ -1188,9 +1212,12 @@ void capture_train_graph(crp_mlp* M, int64_t n) {
   }
   crp_status st = step_gradients(M, M->xs, M->ts, n, cs, true);
   if (st == CRP_OK) {
+    Bf16Jobs jobs;
+    const int nj = bf16_jobs(M, &jobs);
     k_adam<<<nblk(M->n_params, 256), 256, 0, cs>>>(M->params, M->grad, M->m, M->v, M->n_params,
-                                                   0.f, 0.9f, 0.999f, 1e-8f, 1.f, 1.f);
-    st = refresh_bf16(M, cs);
+                                                   0.f, 0.9f, 0.999f, 1e-8f, 1.f, 1.f, jobs, nj,
+                                                   M->hidden);
+    if (cudaGetLastError() != cudaSuccess) st = CRP_E_CUDA;
   }
   cudaGraph_t g = nullptr;
   const cudaError_t ec = cudaStreamEndCapture(cs, &g);
@@ -1504,8 +1531,10 @@ crp_status crp_mlp_train_step(crp_mlp* M, const float* x, const float* t, int64_
     float c1 = 1.f - powf(b1, (float)M->step), c2 = 1.f - powf(b2, (float)M->step);
     float lr_ = lr;
     int64_t np = M->n_params;
+    Bf16Jobs jobs;
+    int nj = bf16_jobs(M, &jobs), hn = M->hidden;
     void* args[] = {&M->params, &M->grad, &M->m, &M->v, &np, &lr_, (void*)&b1, (void*)&b2,
-                    (void*)&eps, &c1, &c2};
+                    (void*)&eps, &c1, &c2, &jobs, &nj, &hn};
     cudaKernelNodeParams kp = M->tg_adam_params;
     kp.kernelParams = args;
     kp.extra = nullptr;
@@ -1517,9 +1546,12 @@ crp_status crp_mlp_train_step(crp_mlp* M, const float* x, const float* t, int64_
     if (st == CRP_OK && lr > 0.f) {
       M->step += 1;
       const float c1 = 1.f - powf(b1, (float)M->step), c2 = 1.f - powf(b2, (float)M->step);
+      Bf16Jobs jobs;
+      const int nj = bf16_jobs(M, &jobs);
       k_adam<<<nblk(M->n_params, 256), 256, 0, s>>>(M->params, M->grad, M->m, M->v, M->n_params,
-                                                    lr, b1, b2, eps, c1, c2);
-      st = refresh_bf16(M, s);
+                                                    lr, b1, b2, eps, c1, c2, jobs, nj, M->hidden);
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) st = fail_cuda(e, "crp_mlp_train_step: Adam");
     }
     if (st == CRP_OK && graph) capture_train_graph(M, n);  // for the next calls
   }
