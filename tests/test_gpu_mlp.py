@@ -302,14 +302,15 @@ def test_tensor_core_training_gradients(torch_dev, n):
         print(f"n {n} path {path}: worst element / tolerance {worst:.3f}")
 
 
-@pytest.mark.parametrize("n_hidden", [2, 3, 5])
-def test_tensor_core_training_other_depths(torch_dev, n_hidden):
+@pytest.mark.parametrize("n_in,n_hidden", [(4, 2), (4, 3), (4, 5), (7, 4)])
+def test_tensor_core_training_other_depths(torch_dev, n_in, n_hidden):
     """Hidden 256 with 1, 2 or 4 hidden-to-hidden layers: the tensor-core
     training step as a fused forward kernel plus the output-layer kernel and
-    the backward GEMMs (the one-kernel step covers 3 such layers), against the
-    bf16-mode oracle."""
+    the backward GEMMs (the one-kernel step covers 3 such layers); and the
+    one-kernel step with 7 inputs (its generic input-count instantiation);
+    against the bf16-mode oracle."""
     torch = torch_dev
-    shapes = M.layer_shapes(4, 256, n_hidden, 3)
+    shapes = M.layer_shapes(n_in, 256, n_hidden, 3)
     g = np.random.default_rng(50 + n_hidden)
     parts = []
     for l, (o, i) in enumerate(shapes):
@@ -318,11 +319,13 @@ def test_tensor_core_training_other_depths(torch_dev, n_hidden):
     p = np.concatenate(parts).astype(np.float32)
     n = 128 * 21
     x, t = _batch(int(1.3 * n), 60 + n_hidden)
+    if n_in > 4:
+        x = np.concatenate([x, 0.5 * g.normal(size=(len(x), n_in - 4))], axis=1).astype(np.float32)
     keep = unambiguous(_oracle_view(p, shapes), shapes, x, n)
     x, t = np.ascontiguousarray(x[keep]), np.ascontiguousarray(t[keep])
     ctx = crp.crp_context_create(0, 1, 16)
     try:
-        mlp = crp.crp_mlp_create(ctx, 4, 256, n_hidden, 7)
+        mlp = crp.crp_mlp_create(ctx, n_in, 256, n_hidden, 7)
         crp.crp_mlp_set_params(mlp, p)
         xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
         loss = crp.crp_mlp_train_step(mlp, xd, td, n, 0.0)
@@ -334,7 +337,7 @@ def test_tensor_core_training_other_depths(torch_dev, n_hidden):
     y, cache = M.forward(flat, shapes, x.astype(np.float64), bf16=True)
     assert abs(loss - M.loss(y, t.astype(np.float64))) < 1e-4 * max(1.0, loss)
     worst = assert_gradients_close(grad, flat, shapes, cache, t.astype(np.float64), x)
-    print(f"n_hidden {n_hidden}: worst element / tolerance {worst:.3f}")
+    print(f"n_in {n_in} n_hidden {n_hidden}: worst element / tolerance {worst:.3f}")
 
 
 @pytest.mark.parametrize("n_in,hidden,n_hidden", [(4, 512, 3), (12, 384, 3)])
