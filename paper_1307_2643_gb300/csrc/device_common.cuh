@@ -328,11 +328,14 @@ __device__ __forceinline__ float phase_quarter_turns(float x, float y) {
 // guard band of a pixel boundary.  Error of every binary32 floor argument
 // against its exact value, for nside <= 8192: inputs truncated to binary32
 // (2^-23 relative: 7.6e-8 on the phase), the phase itself (3.9e-7, see
-// phase_quarter_turns), so t within 4.7e-7; then 0.5 + t (2.4e-7), the
-// products with nside and the ring index and the sums and differences of
-// the floor arguments (< nside * 1.5e-6 in all; the cap formula's 1 - |z|
-// is formed exactly before rounding).  The guard, nside * 6e-6, is 4x
-// that (2e-5 for the phase itself, 40x); outside it the binary32 floor
+// phase_quarter_turns), so t within 4.7e-7.  Equatorial belt: the floor
+// arguments nside t + nside (0.5 -+ 0.75 z) are one fma each (one rounding,
+// 2^-24 of 5 nside), with nside (0.5 -+ 0.75 z) from z truncated (6e-8
+// nside) and two roundings (1.2e-7 nside): < nside * 9.5e-7.  Polar caps:
+// t - floor(t) exact, the cap formula's 1 - |z| formed exactly before its
+// rounding, the products with nside, sqrt and the ring index: < nside *
+// 9e-7.  The guard, nside * 4e-6, is 4.2x the larger (2e-5 for the phase
+// itself, 40x); outside it the binary32 floor
 // equals the exact floor and so the binary64 one, inside it the binary64
 // path decides.  Only 32-bit integer conversions and binary32 arithmetic
 // run outside the guard band.
@@ -347,7 +350,7 @@ __device__ __forceinline__ bool healpix_ring_pixel_try(int64_t nside, double ux,
               fz = sg * f32_trunc_unit(uz);
   const int ns_i = (int)nside;
   const float ns = (float)ns_i;
-  const float g = 6e-6f * ns;
+  const float g = 4e-6f * ns;
   const float tt = phase_quarter_turns(fx, fy);
   int itt;
   bool ok = floor_sure(tt, 2e-5f, &itt);
@@ -357,10 +360,10 @@ __device__ __forceinline__ bool healpix_ring_pixel_try(int64_t nside, double ux,
   int pix = 0;
   if (ok) {
     if (za <= 2.f / 3.f) {
-      const float t1 = ns * (0.5f + tt);
-      const float t2 = ns * fz * 0.75f;
+      // nside (0.5 + t) -+ 0.75 nside z, each with one rounding of the sum
+      const float vm = ns * fmaf(-0.75f, fz, 0.5f), vp = ns * fmaf(0.75f, fz, 0.5f);
       int jp, jm;
-      ok = floor_sure(t1 - t2, g, &jp) & floor_sure(t1 + t2, g, &jm);
+      ok = floor_sure(fmaf(ns, tt, vm), g, &jp) & floor_sure(fmaf(ns, tt, vp), g, &jm);
       const int ir = ns_i + 1 + jp - jm;
       const int kshift = 1 - (ir & 1);
       int ip = (jp + jm - ns_i + kshift + 1) / 2;

@@ -78,7 +78,7 @@ def _floor_sure(a, g):
     return fl.astype(np.int64), (f >= g) & (f <= f32(1) - g)
 
 
-def _pixel_guarded(ns, u, guard_per_nside=6e-6):
+def _pixel_guarded(ns, u, guard_per_nside=4e-6):
     fx, fy, fz = _trunc32(u[:, 0]), _trunc32(u[:, 1]), _trunc32(u[:, 2])
     nsf = f32(ns)
     g = f32(guard_per_nside) * nsf
@@ -87,9 +87,9 @@ def _pixel_guarded(ns, u, guard_per_nside=6e-6):
     za = np.abs(fz)
     ok &= np.abs((za - f32(2.0 / 3.0)).astype(f32)) > f32(1e-6)
     eq = za <= f32(2.0 / 3.0)
-    t1 = (nsf * (f32(0.5) + tt).astype(f32)).astype(f32)
-    t2 = ((nsf * fz).astype(f32) * f32(0.75)).astype(f32)
-    a1, a2 = (t1 - t2).astype(f32), (t1 + t2).astype(f32)
+    vm = (nsf * _fma32(f32(-0.75), fz, f32(0.5))).astype(f32)
+    vp = (nsf * _fma32(f32(0.75), fz, f32(0.5))).astype(f32)
+    a1, a2 = _fma32(nsf, tt, vm), _fma32(nsf, tt, vp)
     jp, o1 = _floor_sure(a1, g)
     jm, o2 = _floor_sure(a2, g)
     ir = ns + 1 + jp - jm
@@ -144,8 +144,8 @@ def test_guarded_pixels_agree_with_binary64(oracle, nside):
     want = oracle.ang2pix_vec(nside, u)
     pix, ok, err_over_ns = _pixel_guarded(nside, u)
     assert np.array_equal(pix[ok], want[ok])
-    # the kernel's guard is nside * 6e-6, its error bound nside * 1.5e-6
-    assert err_over_ns < 1.5e-6 and err_over_ns < 6e-6 / 3
+    # the kernel's guard is nside * 4e-6, its error bound nside * 9.5e-7
+    assert err_over_ns < 9.5e-7 and err_over_ns < 4e-6 / 3
     assert ok[:500_000].mean() > (0.99 if nside <= 64 else 0.9)
 
 
