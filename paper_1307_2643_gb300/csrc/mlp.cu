@@ -1180,7 +1180,7 @@ crp_status train_fused(crp_mlp* M, const float* x, const float* t, int64_t n, cu
     g.ldf = H;
     g.rowsum = M->grad + M->b_off[l];  // db_l: the rows of dz_l^T summed over the batch
   }
-  e = gemm_tc_batch_atomic(gs, ng, M->device, M->sm_count, s);
+  e = wgrad_tc(gs, ng, M->sm_count, s);
   if (e != cudaSuccess) return fail_cuda(e, "mlp: tensor-core weight-gradient GEMMs");
   return CRP_OK;
 }

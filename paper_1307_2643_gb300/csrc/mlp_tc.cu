@@ -841,20 +841,11 @@ __device__ __forceinline__ void bulk_wait_all() {
   asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
 }
 
-// Tensor maps of up to kGemmBatch problems of one shape (the same M, K,
-// splits and epilogue), run as one launch: problem q's operands, output and
-// row sums.  Work items are numbered problem by problem.
-constexpr int kGemmBatch = 3;
-struct GemmTcMaps {
-  CUtensorMap a[kGemmBatch], b[kGemmBatch], o[kGemmBatch];
-  CUtensorMap ot;
-  float* rowsum[kGemmBatch];
-  int n_problems;
-};
-
 template <int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_gemm_tc(const GemmTcParams P, const __grid_constant__ GemmTcMaps maps) {
+    k_gemm_tc(const GemmTcParams P, const __grid_constant__ CUtensorMap mapA,
+              const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapO,
+              const __grid_constant__ CUtensorMap mapOT) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   unsigned char* base = tc_smem + ((1024u - (smem_u32(tc_smem) & 1023u)) & 1023u);
   unsigned char* As = base;               // 4 boxes of 16 KB
@@ -884,27 +875,23 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem_warp = tmem + ((uint32_t)((warp & 3) * 32) << 16);
 
   const int64_t m_tiles = P.M / kRows;
-  const int64_t per = m_tiles * P.splits;  // items of one problem
-  const int64_t items = per * maps.n_problems;
+  const int64_t items = m_tiles * P.splits;
   const int64_t ks = ((P.K + P.splits - 1) / P.splits + 63) / 64 * 64;  // K per split
-  const bool b_resident = P.splits == 1 && P.K <= kH && maps.n_problems == 1;
+  const bool b_resident = P.splits == 1 && P.K <= kH;
   auto row0_of = [&](int64_t mt_) { return mt_ * kRows; };
   auto range = [&](int64_t item, int64_t& kb, int64_t& ke) {
-    kb = ((item % per) / m_tiles) * ks;
+    kb = (item / m_tiles) * ks;
     ke = kb + ks < P.K ? kb + ks : P.K;
   };
   // one thread starts the TMA boxes of a chunk (kc a multiple of 64)
   auto issue = [&](int64_t item, int64_t c0, int kc, bool with_b) {
     if (tid != 0) return;
-    const int q = (int)(item / per);
     const int boxes = kc / 64;
     bar_expect_tx(tbar, (uint32_t)boxes * (kAtomA + (with_b ? kAtomB : 0u)));
-    const int y = (int)(((item % per) % m_tiles) * kRows);
-    for (int a = 0; a < boxes; ++a)
-      tma_load_2d(As + a * kAtomA, &maps.a[q], (int)c0 + 64 * a, y, tbar);
+    const int y = (int)((item % m_tiles) * kRows);
+    for (int a = 0; a < boxes; ++a) tma_load_2d(As + a * kAtomA, &mapA, (int)c0 + 64 * a, y, tbar);
     if (with_b)
-      for (int a = 0; a < boxes; ++a)
-        tma_load_2d(Bs + a * kAtomB, &maps.b[q], (int)c0 + 64 * a, 0, tbar);
+      for (int a = 0; a < boxes; ++a) tma_load_2d(Bs + a * kAtomB, &mapB, (int)c0 + 64 * a, 0, tbar);
   };
   uint32_t parity = 0, tparity = 0;
   bool failed = false, b_loaded = false, prefetched = false;
@@ -913,9 +900,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     int64_t kb, ke;
     range(item, kb, ke);
     if (kb >= ke) continue;  // an empty split (the same for every thread)
-    const int q = (int)(item / per);
-    const int64_t mt = (item % per) % m_tiles;
-    float* const rowsum = maps.rowsum[q];
+    const int64_t mt = item % m_tiles;
+    float* const rowsum = P.rowsum;
     float row_acc = 0.f;
     for (int64_t c0 = kb; c0 < ke; c0 += kH) {
       const int kc = (int)(ke - c0 < kH ? ke - c0 : kH);
@@ -1057,12 +1043,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (tid == 0) {
       const int y = (int)(mt * kRows);
       if constexpr (EPI == GEMM_TC_ATOMIC) {
-        for (int b = 0; b < 8; ++b) tma_reduce_add_2d(&maps.o[q], 32 * b, y, stage + b * kAtomA);
+        for (int b = 0; b < 8; ++b) tma_reduce_add_2d(&mapO, 32 * b, y, stage + b * kAtomA);
       } else {
-        for (int b = 0; b < 4; ++b) tma_store_2d(&maps.o[q], 64 * b, y, stage + b * kAtomA);
+        for (int b = 0; b < 4; ++b) tma_store_2d(&mapO, 64 * b, y, stage + b * kAtomA);
         if (P.out_t)
           for (int b = 0; b < 2; ++b)
-            tma_store_2d(&maps.ot, y + 64 * b, 0, stage + 4 * kAtomA + b * kAtomB);
+            tma_store_2d(&mapOT, y + 64 * b, 0, stage + 4 * kAtomA + b * kAtomB);
       }
       bulk_commit();
     }
@@ -1111,6 +1097,187 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
                  "r"(kTmemCols)
+                 : "memory");
+}
+
+
+// ---------------------------------------------------------------------------
+// Weight gradients of the hidden layers: for up to kGemmBatch problems q,
+// C_q[256][256] += A_q[256][K] B_q[256][K]^T (A = dz_l^T, B = h_{l-1}^T, K the
+// batch) and rowsum_q[m] += sum_k A_q[m][k] (the bias gradient).  A work item
+// is one problem's K range; the CTA computes the whole 256 x 256 output of it
+// in 512 TMEM columns (two M = 128 halves against the same B chunk).  The K
+// range streams through three shared-memory stages of 64 columns (A and B
+// 256 x 64 bf16 each, 128-byte swizzle, 64 KB a stage): one thread starts the
+// TMA copies two chunks ahead, issues a chunk's 8 MMAs as soon as it has
+// landed and commits them to the stage's "freed" barrier, which the refill of
+// that stage waits for; meanwhile every thread adds its A row of the chunk to
+// its row sum.  The epilogue stages each half as FP32 boxes and adds it to C
+// with TMA reduce-add.
+// ---------------------------------------------------------------------------
+constexpr int kGemmBatch = 3;  // problems of one launch
+constexpr int kWgStages = 3;
+constexpr uint32_t kWgA = 256 * 128;  // 256 rows x 64 bf16 columns: 32 KB
+constexpr uint32_t kWgStage = 2 * kWgA;
+constexpr size_t kWgSmem = 1024 + kWgStages * kWgStage + 2 * kWgStages * 8 + 16;
+constexpr uint32_t kWgTmemCols = 512;
+
+struct WgradMaps {
+  CUtensorMap a[kGemmBatch], b[kGemmBatch], o[kGemmBatch];
+  float* rowsum[kGemmBatch];
+  int n_problems;
+  int64_t K;       // columns of A and B (a multiple of 64)
+  int64_t kchunk;  // K range of an item (a multiple of 64)
+  int64_t splits;  // items per problem
+  unsigned* err;
+};
+
+__global__ void __launch_bounds__(kThreads, 1) k_wgrad_tc(const __grid_constant__ WgradMaps W) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  unsigned char* base = tc_smem + ((1024u - (smem_u32(tc_smem) & 1023u)) & 1023u);
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + kWgStages * kWgStage);  // bytes landed
+  uint64_t* freed = full + kWgStages;                                          // MMAs done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(freed + kWgStages);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int r = tid & (kRows - 1), g = tid >> 7;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kWgTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < kWgStages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(full + s)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(freed + s)) : "memory");
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t tmem_warp = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+
+  const int64_t items = W.splits * W.n_problems;
+  uint32_t fph = 0, eph = 0;  // phase parity of each stage's full / freed barrier
+  bool failed = false;
+  for (int64_t item = blockIdx.x; item < items && !failed; item += gridDim.x) {
+    const int q = (int)(item / W.splits);
+    const int64_t kb = (item % W.splits) * W.kchunk;
+    const int64_t ke = kb + W.kchunk < W.K ? kb + W.kchunk : W.K;
+    if (kb >= ke) continue;  // the same for every thread
+    const int nch = (int)((ke - kb) / 64);
+    // thread 0: the TMA copies of chunk c into its stage
+    auto issue = [&](int c) {
+      const int s = c % kWgStages;
+      unsigned char* st = base + s * kWgStage;
+      bar_expect_tx(full + s, kWgStage);
+      tma_load_2d(st, &W.a[q], (int)(kb + 64 * c), 0, full + s);
+      tma_load_2d(st + kWgA, &W.b[q], (int)(kb + 64 * c), 0, full + s);
+    };
+    // thread 0: wait (bounded) for the MMAs that read stage s
+    auto wait_freed = [&](int s) -> bool {
+      bool ok = bar_wait(freed + s, (eph >> s) & 1u);
+      if (!ok) ok = bar_wait(freed + s, (eph >> s) & 1u);
+      eph ^= 1u << s;
+      return ok;
+    };
+    bool t0_ok = true;
+    if (tid == 0) {
+      issue(0);
+      if (nch > 1) issue(1);
+    }
+    float racc = 0.f;  // row tid of A summed over the item's K range
+    for (int c = 0; c < nch; ++c) {
+      const int s = c % kWgStages;
+      bool ok = bar_wait(full + s, (fph >> s) & 1u);  // the chunk's bytes are in shared memory
+      if (!ok) ok = bar_wait(full + s, (fph >> s) & 1u);
+      fph ^= 1u << s;
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const unsigned char* st = base + s * kWgStage;
+      if (tid == 0) {
+        const uint32_t a0 = smem_u32(st), b0 = smem_u32(st + kWgA);
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            mma_bf16(tmem + 256u * h, sdesc_sw128(a0 + 16384u * h + 32u * k),
+                     sdesc_sw128(b0 + 32u * k), kIdesc, (c > 0 || k > 0) ? 1u : 0u);
+        mma_commit(freed + s);
+      }
+      {
+        // row tid of A in this chunk (thread t starts at chunk t % 8 of its
+        // row: a warp's loads then spread over the banks; the swizzle only
+        // permutes a row's 16-byte chunks, so the sum needs no unswizzling)
+        const uint4* rp = reinterpret_cast<const uint4*>(st + tid * 128);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const uint4 v = rp[(j + tid) & 7];
+          const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const __nv_bfloat162 p = *reinterpret_cast<const __nv_bfloat162*>(&w[e]);
+            racc += __low2float(p) + __high2float(p);
+          }
+        }
+      }
+      // chunk c + 2 goes into the stage chunk c - 1 used, once its MMAs are done
+      if (tid == 0 && c + 2 < nch) {
+        if (c >= 1) t0_ok = wait_freed((c + 2) % kWgStages) && t0_ok;
+        issue(c + 2);
+      }
+      __syncthreads();  // the row-sum reads of stage s are done before its refill
+    }
+    // the MMAs still unwaited: those of the last three chunks (all, if fewer)
+    if (tid == 0 && !failed)
+      for (int c = nch - 3 > 0 ? nch - 3 : 0; c < nch; ++c) t0_ok = wait_freed(c % kWgStages) && t0_ok;
+    if (__syncthreads_or(failed || !t0_ok)) {
+      failed = true;
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (W.rowsum[q]) atomicAdd(W.rowsum[q] + tid, racc);
+    // ---- epilogue: each half as eight FP32 boxes of 32 columns x 128 rows
+    // (128-byte swizzle) in the freed stages, added to C by TMA ----
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+#pragma unroll 1
+      for (int cc = 4 * g; cc < 4 * g + 4; ++cc) {
+        uint32_t v[32];
+        tmem_ld32(tmem_warp + 256u * h + (uint32_t)(cc * 32), v);
+        unsigned char* rp = base + cc * kAtomA + r * 128;
+#pragma unroll
+        for (int qq = 0; qq < 8; ++qq)
+          *reinterpret_cast<uint4*>(rp + 16 * (qq ^ (r & 7))) =
+              make_uint4(v[4 * qq], v[4 * qq + 1], v[4 * qq + 2], v[4 * qq + 3]);
+      }
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      if (tid == 0) {
+        for (int b = 0; b < 8; ++b) tma_reduce_add_2d(&W.o[q], 32 * b, 128 * h, base + b * kAtomA);
+        bulk_commit();
+        bulk_wait_read();  // the staging may be overwritten once the TMA has read it
+      }
+      __syncthreads();
+    }
+  }
+  if (failed && tid == 0) atomicOr(W.err, 1u);
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (tid == 0) bulk_wait_all();  // every TMA reduction has completed
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(kWgTmemCols)
                  : "memory");
 }
 
@@ -1199,17 +1366,15 @@ cudaError_t gemm_tc(int epi, const GemmTcParams& p, int device, int sm_count, cu
   if (p.xin) ok = ok && epi == GEMM_TC_MASK && p.n_in >= 1 && p.n_in <= 8 && p.gw_in && p.gb_in;
   if (!ok || epi < GEMM_TC_BIAS_RELU || epi > GEMM_TC_ATOMIC) return cudaErrorInvalidValue;
   // operand maps (loads) and output maps (stores / reductions of the tile)
-  GemmTcMaps tm;
-  memset(&tm, 0, sizeof(tm));
-  tm.n_problems = 1;
-  tm.rowsum[0] = p.rowsum;
-  bool maps = tensor_map(p.A, false, p.M, p.K, p.lda, kRows, &tm.a[0]) &&
-              tensor_map(p.B, false, kH, p.K, p.ldb, kH, &tm.b[0]);
+  CUtensorMap mapA, mapB, mapO, mapOT;
+  memset(&mapOT, 0, sizeof(mapOT));
+  bool maps = tensor_map(p.A, false, p.M, p.K, p.lda, kRows, &mapA) &&
+              tensor_map(p.B, false, kH, p.K, p.ldb, kH, &mapB);
   if (epi == GEMM_TC_ATOMIC) {
-    maps = maps && tensor_map(p.out_f, true, p.M, kH, p.ldf, kRows, &tm.o[0]);
+    maps = maps && tensor_map(p.out_f, true, p.M, kH, p.ldf, kRows, &mapO);
   } else {
-    maps = maps && tensor_map(p.out, false, p.M, kH, p.ldo, kRows, &tm.o[0]);
-    if (p.out_t) maps = maps && tensor_map(p.out_t, false, kH, p.M, p.ldot, kH, &tm.ot);
+    maps = maps && tensor_map(p.out, false, p.M, kH, p.ldo, kRows, &mapO);
+    if (p.out_t) maps = maps && tensor_map(p.out_t, false, kH, p.M, p.ldot, kH, &mapOT);
   }
   if (!maps) return cudaErrorInvalidValue;
   auto k = epi == GEMM_TC_BIAS_RELU ? k_gemm_tc<GEMM_TC_BIAS_RELU>
@@ -1226,39 +1391,47 @@ cudaError_t gemm_tc(int epi, const GemmTcParams& p, int device, int sm_count, cu
   }
   const int64_t items = p.M / kRows * p.splits;
   const int64_t grid = items < sm_count ? items : sm_count;
-  k<<<(unsigned)grid, kThreads, kGemmSmem, s>>>(p, tm);
+  k<<<(unsigned)grid, kThreads, kGemmSmem, s>>>(p, mapA, mapB, mapO, mapOT);
   return cudaGetLastError();
 }
 
-cudaError_t gemm_tc_batch_atomic(const GemmTcParams* ps, int np, int device, int sm_count,
-                                 cudaStream_t s) {
+cudaError_t wgrad_tc(const GemmTcParams* ps, int np, int sm_count, cudaStream_t s) {
   if (np < 1 || np > kGemmBatch) return cudaErrorInvalidValue;
-  if (np == 1) return gemm_tc(GEMM_TC_ATOMIC, ps[0], device, sm_count, s);
-  GemmTcMaps tm;
-  memset(&tm, 0, sizeof(tm));
-  tm.n_problems = np;
-  const GemmTcParams& p0 = ps[0];
+  WgradMaps W;
+  memset(&W, 0, sizeof(W));
+  W.n_problems = np;
+  W.K = ps[0].K;
+  W.err = ps[0].err;
   for (int q = 0; q < np; ++q) {
     const GemmTcParams& p = ps[q];
-    // one shape for all: the kernel derives items and K ranges from p0
-    const bool ok = p.M == p0.M && p.K == p0.K && p.splits == p0.splits && p.err == p0.err &&
-                    ((uintptr_t)p.A % 16 == 0) && ((uintptr_t)p.B % 16 == 0) && p.lda % 8 == 0 &&
-                    p.ldb % 8 == 0 && p.lda >= p.K && p.ldb >= p.K && p.M > 0 && p.M % kRows == 0 &&
-                    p.K > 0 && p.K % 64 == 0 && p.splits >= 1 && p.err && p.out_f &&
-                    (uintptr_t)p.out_f % 16 == 0 && p.ldf % 4 == 0 && p.ldf >= kH && !p.xin;
+    const bool ok = p.M == kH && p.K == W.K && p.K > 0 && p.K % 64 == 0 && p.err == W.err &&
+                    p.err && ((uintptr_t)p.A % 16 == 0) && ((uintptr_t)p.B % 16 == 0) &&
+                    p.lda % 8 == 0 && p.ldb % 8 == 0 && p.lda >= p.K && p.ldb >= p.K && p.out_f &&
+                    (uintptr_t)p.out_f % 16 == 0 && p.ldf % 4 == 0 && p.ldf >= kH;
     if (!ok) return cudaErrorInvalidValue;
-    tm.rowsum[q] = p.rowsum;
-    if (!tensor_map(p.A, false, p.M, p.K, p.lda, kRows, &tm.a[q]) ||
-        !tensor_map(p.B, false, kH, p.K, p.ldb, kH, &tm.b[q]) ||
-        !tensor_map(p.out_f, true, p.M, kH, p.ldf, kRows, &tm.o[q]))
+    W.rowsum[q] = p.rowsum;
+    if (!tensor_map(p.A, false, kH, p.K, p.lda, kH, &W.a[q]) ||
+        !tensor_map(p.B, false, kH, p.K, p.ldb, kH, &W.b[q]) ||
+        !tensor_map(p.out_f, true, kH, kH, p.ldf, kRows, &W.o[q]))
       return cudaErrorInvalidValue;
   }
-  auto k = k_gemm_tc<GEMM_TC_ATOMIC>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
-  if (e != cudaSuccess) return e;
-  const int64_t items = p0.M / kRows * p0.splits * np;
+  // one wave: at most sm_count items, K ranges a multiple of 64
+  const int64_t per = sm_count / np > 1 ? sm_count / np : 1;
+  W.kchunk = ((W.K + per - 1) / per + 63) / 64 * 64;
+  W.splits = (W.K + W.kchunk - 1) / W.kchunk;
+  static std::atomic<uint64_t> set_mask{0};
+  int device = 0;
+  cudaGetDevice(&device);
+  const uint64_t bit = device >= 0 && device < 64 ? (1ull << device) : 0ull;
+  if (!bit || !(set_mask.load() & bit)) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
+    if (e != cudaSuccess) return e;
+    set_mask.fetch_or(bit);
+  }
+  const int64_t items = W.splits * np;
   const int64_t grid = items < sm_count ? items : sm_count;
-  k<<<(unsigned)grid, kThreads, kGemmSmem, s>>>(p0, tm);
+  k_wgrad_tc<<<(unsigned)grid, kThreads, kWgSmem, s>>>(W);
   return cudaGetLastError();
 }
 

@@ -72,10 +72,11 @@ struct GemmTcParams {
   unsigned* err;  // set to 1 when a tensor-core wait timed out
 };
 cudaError_t gemm_tc(int epi, const GemmTcParams& p, int device, int sm_count, cudaStream_t s);
-// np (<= 3) weight-gradient problems (GEMM_TC_ATOMIC) of one shape -- the same
-// M, K and splits -- in one launch (ps[q].rowsum as in gemm_tc).
-cudaError_t gemm_tc_batch_atomic(const GemmTcParams* ps, int np, int device, int sm_count,
-                                 cudaStream_t s);
+// np (<= 3) weight-gradient problems of one shape (M = 256, the same K; the
+// GEMM_TC_ATOMIC fields with row sums) in one launch of a K-pipelined kernel:
+// each work item computes a whole 256 x 256 output over its K range,
+// streaming 64-column chunks through three shared-memory stages.
+cudaError_t wgrad_tc(const GemmTcParams* ps, int np, int sm_count, cudaStream_t s);
 
 // One training step's forward pass, output layer, loss and backward signals
 // in one persistent tcgen05 kernel (hidden 256, three hidden-to-hidden
