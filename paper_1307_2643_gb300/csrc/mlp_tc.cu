@@ -333,6 +333,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const MlpTcParam
       }
     }
   }
+  // a timed-out MMA wait: one more bounded wait for those MMAs before the
+  // TMEM is given up (the phase that did not complete has parity ^ 1)
+  if (failed && tid == 0) bar_wait(bar, parity ^ 1u);
   asm volatile("cp.async.wait_all;\n" ::: "memory");  // no copy outlives the kernel
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -763,6 +766,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_train_tc(const MlpTrainTcPa
     else if (tid == 3)
       atomicAdd(P.loss, gsmall);
   }
+  // a timed-out MMA wait: one more bounded wait for those MMAs before the
+  // TMEM is given up (the phase that did not complete has parity ^ 1)
+  if (failed && tid == 0) bar_wait(bar, parity ^ 1u);
   asm volatile("cp.async.wait_all;\n" ::: "memory");  // no copy outlives the kernel
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -895,6 +901,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   };
   uint32_t parity = 0, tparity = 0;
   bool failed = false, b_loaded = false, prefetched = false;
+  bool copy_failed = false, mma_failed = false;  // which bounded wait gave up
 
   for (int64_t item = blockIdx.x; item < items && !failed; item += gridDim.x) {
     int64_t kb, ke;
@@ -913,7 +920,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       tparity ^= 1u;
       if (__syncthreads_or(!landed)) {
         if (tid == 0) atomicOr(P.err, 1u);
-        failed = true;
+        failed = copy_failed = true;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -952,7 +959,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       parity ^= 1u;
       if (__syncthreads_or(!ok)) {
         if (tid == 0) atomicOr(P.err, 1u);
-        failed = true;
+        failed = mma_failed = true;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -1093,7 +1100,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-  if (tid == 0) bulk_wait_all();  // every TMA store / reduction has completed
+  if (tid == 0) {
+    // a timed-out wait: one more bounded wait for the copy or the MMAs still
+    // in flight before the shared memory and TMEM are given up
+    if (copy_failed) bar_wait(tbar, tparity ^ 1u);
+    if (mma_failed) bar_wait(bar, parity ^ 1u);
+    bulk_wait_all();  // every TMA store / reduction has completed
+  }
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
                  "r"(kTmemCols)
@@ -1163,6 +1176,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_wgrad_tc(const __grid_constant_
 
   const int64_t items = W.splits * W.n_problems;
   uint32_t fph = 0, eph = 0;  // phase parity of each stage's full / freed barrier
+  // thread 0: stages whose copies / MMAs have not been waited for (at most one
+  // of each per stage: a stage is refilled only after both)
+  uint32_t pend_full = 0, pend_freed = 0;
   bool failed = false;
   for (int64_t item = blockIdx.x; item < items && !failed; item += gridDim.x) {
     const int q = (int)(item / W.splits);
@@ -1177,12 +1193,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_wgrad_tc(const __grid_constant_
       bar_expect_tx(full + s, kWgStage);
       tma_load_2d(st, &W.a[q], (int)(kb + 64 * c), 0, full + s);
       tma_load_2d(st + kWgA, &W.b[q], (int)(kb + 64 * c), 0, full + s);
+      pend_full |= 1u << s;
     };
     // thread 0: wait (bounded) for the MMAs that read stage s
     auto wait_freed = [&](int s) -> bool {
       bool ok = bar_wait(freed + s, (eph >> s) & 1u);
       if (!ok) ok = bar_wait(freed + s, (eph >> s) & 1u);
-      eph ^= 1u << s;
+      if (ok) {
+        eph ^= 1u << s;
+        pend_freed &= ~(1u << s);
+      }
       return ok;
     };
     bool t0_ok = true;
@@ -1195,7 +1215,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_wgrad_tc(const __grid_constant_
       const int s = c % kWgStages;
       bool ok = bar_wait(full + s, (fph >> s) & 1u);  // the chunk's bytes are in shared memory
       if (!ok) ok = bar_wait(full + s, (fph >> s) & 1u);
-      fph ^= 1u << s;
+      if (ok) {
+        fph ^= 1u << s;
+        pend_full &= ~(1u << s);
+      }
       if (__syncthreads_or(!ok)) {
         failed = true;
         break;
@@ -1211,6 +1234,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_wgrad_tc(const __grid_constant_
             mma_bf16(tmem + 256u * h, sdesc_sw128(a0 + 16384u * h + 32u * k),
                      sdesc_sw128(b0 + 32u * k), kIdesc, (c > 0 || k > 0) ? 1u : 0u);
         mma_commit(freed + s);
+        pend_freed |= 1u << s;
       }
       {
         // row tid of A in this chunk (thread t starts at chunk t % 8 of its
@@ -1230,14 +1254,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_wgrad_tc(const __grid_constant_
       }
       // chunk c + 2 goes into the stage chunk c - 1 used, once its MMAs are done
       if (tid == 0 && c + 2 < nch) {
-        if (c >= 1) t0_ok = wait_freed((c + 2) % kWgStages) && t0_ok;
-        issue(c + 2);
+        if (c >= 1 && !wait_freed((c + 2) % kWgStages)) t0_ok = false;
+        if (t0_ok) issue(c + 2);
       }
-      __syncthreads();  // the row-sum reads of stage s are done before its refill
+      // the row-sum reads of stage s are done before its refill
+      if (__syncthreads_or(!t0_ok)) {
+        failed = true;
+        break;
+      }
     }
     // the MMAs still unwaited: those of the last three chunks (all, if fewer)
     if (tid == 0 && !failed)
-      for (int c = nch - 3 > 0 ? nch - 3 : 0; c < nch; ++c) t0_ok = wait_freed(c % kWgStages) && t0_ok;
+      for (int c = nch - 3 > 0 ? nch - 3 : 0; c < nch; ++c)
+        if (!wait_freed(c % kWgStages)) t0_ok = false;
     if (__syncthreads_or(failed || !t0_ok)) {
       failed = true;
       break;
@@ -1270,7 +1299,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_wgrad_tc(const __grid_constant_
       __syncthreads();
     }
   }
-  if (failed && tid == 0) atomicOr(W.err, 1u);
+  if (failed && tid == 0) {
+    atomicOr(W.err, 1u);
+    // before the shared memory and TMEM are given up: one more bounded wait
+    // for every copy and MMA still in flight
+    for (int s = 0; s < kWgStages; ++s) {
+      if ((pend_full >> s) & 1u) bar_wait(full + s, (fph >> s) & 1u);
+      if ((pend_freed >> s) & 1u) bar_wait(freed + s, (eph >> s) & 1u);
+    }
+  }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
