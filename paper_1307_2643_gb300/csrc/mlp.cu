@@ -683,7 +683,8 @@ __global__ void k_adam(float* p, const float* g, float* m, float* v, int64_t n, 
     for (int j = 0; j < nj; ++j) {
       const int64_t e = (p + i) - jobs.W[j];
       if (e < 0 || e >= nn) continue;
-      const int o = (int)(e / hn), ii = (int)(e % hn);
+      const int ei = (int)e;  // < hn * hn: 32-bit division
+      const int o = ei / hn, ii = ei - o * hn;
       const __nv_bfloat16 bv = __float2bfloat16_rn(pi);
       jobs.wb[j][e] = bv;
       jobs.wbt[j][(int64_t)ii * hn + o] = bv;
