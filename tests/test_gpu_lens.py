@@ -122,6 +122,12 @@ def test_lens_apply_matches_oracle(setup):
         lens, _ = crp.crp_lens_build(ctx, gr, _mods(), NSIDE, NBINS, W["r_lo"], W["r_hi"],
                                      W["earth"], dirs, E, bins)
         crp.crp_candidates_inject(ctx, crp.candidate_arrays(crp.host_injection(inj)), m)
+        # the status filter: every injected candidate is active, so DETECTED
+        # selects none (pixels stay "not applied") and ACTIVE all of them
+        crp.crp_lens_apply(ctx, lens, crp.COLLECT_DETECTED)
+        rec_none = np.sort(crp.crp_collect(ctx, crp.COLLECT_ALL), order="id")
+        crp.crp_lens_apply(ctx, lens, crp.COLLECT_ACTIVE)
+        rec_active = np.sort(crp.crp_collect(ctx, crp.COLLECT_ALL), order="id")
         crp.crp_lens_apply(ctx, lens, crp.COLLECT_ALL)
         rec = np.sort(crp.crp_collect(ctx, crp.COLLECT_ALL), order="id")
         hist_earth = crp.crp_histogram_healpix(ctx, crp.COLLECT_ALL, NSIDE, 1)
@@ -131,6 +137,8 @@ def test_lens_apply_matches_oracle(setup):
     finally:
         crp.crp_context_destroy(ctx)
     want = olens.apply(ref_lens, NSIDE, W["r_lo"], W["r_hi"], NBINS, seed, inj["id"], u, Ev, Z)
+    assert np.all(rec_none["lens_pixel"] == olens.NOT_APPLIED)
+    assert np.array_equal(rec_active["lens_pixel"], want)
     assert np.array_equal(rec["lens_pixel"], want)
     observed = want < 12 * NSIDE * NSIDE
     assert 0.2 < observed.mean() < 0.98
@@ -227,6 +235,12 @@ def test_lens_apply_at_scale_matches_oracle(built):
         inj = dict(id=ids, x=np.zeros(m), y=np.zeros(m), z=np.zeros(m), ux=u[:, 0].copy(),
                    uy=u[:, 1].copy(), uz=u[:, 2].copy(), E=Ev, A=A, Z=Z)
         crp.crp_candidates_inject(ctx, crp.candidate_arrays(crp.host_injection(inj)), m)
+        # the status filter: every injected candidate is active, so DETECTED
+        # selects none (pixels stay "not applied") and ACTIVE all of them
+        crp.crp_lens_apply(ctx, lens, crp.COLLECT_DETECTED)
+        rec_none = np.sort(crp.crp_collect(ctx, crp.COLLECT_ALL), order="id")
+        crp.crp_lens_apply(ctx, lens, crp.COLLECT_ACTIVE)
+        rec_active = np.sort(crp.crp_collect(ctx, crp.COLLECT_ALL), order="id")
         crp.crp_lens_apply(ctx, lens, crp.COLLECT_ALL)
         rec = np.sort(crp.crp_collect(ctx, crp.COLLECT_ALL), order="id")
         crp.crp_lens_destroy(lens)
