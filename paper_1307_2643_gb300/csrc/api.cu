@@ -697,8 +697,9 @@ crp_status crp_grid_create(crp_context* c, const crp_grid_desc* d, crp_grid** ou
     dev_free(staging);
   }
   gr->cells = nullptr;
-  if (st == CRP_OK && d->dtype == CRP_F32 && d->cell_records == 0) {
-    // optional: a grid without records still works (node gathers)
+  if (st == CRP_OK && d->dtype == CRP_F32 && d->cell_records == 0 && N < (int64_t(1) << 32)) {
+    // optional: a grid without records still works (node gathers); records
+    // are indexed in 32 bits by some kernels, so only below 2^32 cells
     gr->cells = dev_alloc((size_t)N * 8 * sizeof(float4));
     if (gr->cells) {
       st = grid_cells(gr->nodes, d->n, gr->cells, s);
