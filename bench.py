@@ -246,10 +246,10 @@ def flops_per_trial_mixed():
 GATHER_BYTES_PER_TRIAL_F32 = 6 * 8 * 3 * 4
 # DRAM bytes (read + write) per Cash-Karp trial of the mixed propagate kernel this
 # workload runs (its module list fixed at compile time), from one ncu capture of the
-# current kernel (2e5 candidates of this workload: 154.595 GB read + 0.156 GB written
+# current kernel (2e5 candidates of this workload: 154.594 GB read + 0.157 GB written
 # over 1.5611e9 trials); traffic grows with the number of trials, so a launch's
 # traffic is this figure times its trials
-DRAM_BYTES_PER_TRIAL_MIXED = (154.595e9 + 0.156e9) / 1.5611e9
+DRAM_BYTES_PER_TRIAL_MIXED = (154.594e9 + 0.157e9) / 1.5611e9
 
 # the equal-error statement: tolerances, subsample sizes and the chaos-floor kick
 TIGHT_TOL, TIGHT_HMIN = 1e-8, 1e-4          # where the method resolves 1e-5 per candidate
