@@ -1349,6 +1349,10 @@ crp_status crp_propagate(crp_context* c, const crp_grid* g, const crp_modules* m
     variant = (m->blocks_per_sm == 0 || m->blocks_per_sm <= 5) ? 5 : 3;
   else if (m->blocks_per_sm >= 3)
     variant = 3;
+  // the analytic galactic fields' binary32 arithmetic is contracted
+  // differently under the smaller register budgets, which would make the
+  // records depend on the launch; those lists always run in the first
+  if (m->flags & (CRP_GALACTIC | CRP_GMF)) variant = 2;
   int bps = m->blocks_per_sm;
   if (!bps) {
     cudaError_t e = m->precision == CRP_FP64

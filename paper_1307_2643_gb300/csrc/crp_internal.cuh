@@ -182,6 +182,7 @@ cudaError_t occupancy_propagate_mixed_nuc(int dtype, uint32_t flags, int block, 
 // without photodisintegration.
 constexpr uint32_t kModsEgal = CRP_PAIR | CRP_ADIABATIC | CRP_PION | CRP_EMIN | CRP_OBSERVER;
 constexpr uint32_t kModsEgalPd = kModsEgal | CRP_PHOTODIS;
+constexpr uint32_t kModsGalBorder = CRP_GALACTIC | CRP_BORDER;  // galactic back-tracking
 int fixed_modules_index(uint32_t flags);  // -1: no fixed instantiation
 cudaError_t launch_propagate_mixed_fixed(int index, const KParams& kp, const DevState& st,
                                          DevCounters* dc, int grid, int block, cudaStream_t s);
