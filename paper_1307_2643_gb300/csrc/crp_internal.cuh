@@ -183,13 +183,15 @@ cudaError_t occupancy_propagate_mixed_nuc(int dtype, uint32_t flags, int block, 
 constexpr uint32_t kModsEgal = CRP_PAIR | CRP_ADIABATIC | CRP_PION | CRP_EMIN | CRP_OBSERVER;
 constexpr uint32_t kModsEgalPd = kModsEgal | CRP_PHOTODIS;
 constexpr uint32_t kModsGalBorder = CRP_GALACTIC | CRP_BORDER;  // galactic back-tracking
+constexpr uint32_t kModsGmfBorder = CRP_GMF | CRP_BORDER;  // multi-arm back-tracking
 int fixed_modules_index(uint32_t flags);  // -1: no fixed instantiation
 cudaError_t launch_propagate_mixed_fixed(int index, const KParams& kp, const DevState& st,
                                          DevCounters* dc, int grid, int block, cudaStream_t s);
 cudaError_t occupancy_propagate_mixed_fixed(int index, int dtype, int block, int* bps);
 cudaError_t launch_propagate_mixed_gmf(const KParams& kp, const DevState& st, DevCounters* dc,
                                        int grid, int block, int variant, cudaStream_t s);
-cudaError_t occupancy_propagate_mixed_gmf(int dtype, int variant, int block, int* bps);
+cudaError_t occupancy_propagate_mixed_gmf(int dtype, uint32_t flags, int variant, int block,
+                                          int* bps);
 cudaError_t sample_field_mixed_gmf(const KParams& kp, const double* xyz, int64_t n, double* B,
                                    cudaStream_t s);
 cudaError_t occupancy_propagate_mixed(int dtype, uint32_t flags, int variant, int block,

@@ -5,12 +5,24 @@
 
 namespace crp {
 
+namespace {
+// back-tracking through the multi-arm field to the galaxy border, with the
+// module list fixed at compile time (records byte-identical to the generic
+// kernel's)
+using PolicyGmfBorder = PolicyMixedT<true, true, kModsGmfBorder>;
+}  // namespace
+
 cudaError_t launch_propagate_mixed_gmf(const KParams& kp, const DevState& st, DevCounters* dc,
                                        int grid, int block, int variant, cudaStream_t s) {
+  if (variant == 2 && kp.flags == kModsGmfBorder)
+    return launch_policy<PolicyGmfBorder, 256, 2>(kp, st, dc, grid, block, s);
   return launch_variant<PolicyMixedGmf>(kp, st, dc, grid, block, variant, s);
 }
 
-cudaError_t occupancy_propagate_mixed_gmf(int dtype, int variant, int block, int* bps) {
+cudaError_t occupancy_propagate_mixed_gmf(int dtype, uint32_t flags, int variant, int block,
+                                          int* bps) {
+  if (variant == 2 && flags == kModsGmfBorder)
+    return occupancy_policy<PolicyGmfBorder, 256, 2>(dtype, block, bps);
   return occupancy_variant<PolicyMixedGmf>(dtype, variant, block, bps);
 }
 

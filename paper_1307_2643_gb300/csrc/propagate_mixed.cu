@@ -27,7 +27,7 @@ cudaError_t occupancy_propagate_mixed(int dtype, uint32_t flags, int variant, in
     const int fx = fixed_modules_index(flags);
     if (fx >= 0) return occupancy_propagate_mixed_fixed(fx, dtype, block, bps);
   }
-  if (flags & CRP_GMF) return occupancy_propagate_mixed_gmf(dtype, variant, block, bps);
+  if (flags & CRP_GMF) return occupancy_propagate_mixed_gmf(dtype, flags, variant, block, bps);
   return (flags & CRP_GALACTIC) ? occupancy_variant<PolicyMixedGal>(dtype, variant, block, bps)
                                 : occupancy_variant<PolicyMixed>(dtype, variant, block, bps);
 }

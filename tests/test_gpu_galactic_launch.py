@@ -1,9 +1,10 @@
-"""Back-tracking through the disk + halo + random galactic field on the
-mixed path (Sect. 4 lenses are built this way): the records do not depend on
-the launch (block size, resident blocks, queue order), and the kernel with
-the module list fixed at compile time (galactic field + border) gives the
-same bytes as the generic kernel, which a run with one more module that never
-fires (E_min far below every energy) takes."""
+"""Back-tracking through the galactic fields on the mixed path (Sect. 4 lenses
+are built this way), for the disk + halo + random field and the analytic
+multi-arm field: the records do not depend on the launch (block size,
+resident blocks, queue order), and the kernel with the module list fixed at
+compile time (the field + border) gives the same bytes as the generic kernel,
+which a run with one more module that never fires (E_min far below every
+energy) takes."""
 import numpy as np
 import pytest
 
@@ -20,20 +21,31 @@ def lib():
     return crp
 
 
-def _run(n_side, inj, n, extra_flags=0, **launch):
+def _setup(galaxy):
     w = workloads.GALACTIC_LENS
-    dx, lmin, org = workloads.galactic_grid_geometry(n_side, w["box"])
-    desc = crp.grid_desc((n_side,) * 3, dx, origin=org, dtype=crp.F32,
-                         source=crp.GRID_TURBULENT, lmin=lmin, lmax=w["lmax"], brms=w["brms"],
-                         seed=w["seed"])
+    if galaxy == "disk_halo_random":
+        dx, lmin, org = workloads.galactic_grid_geometry(64, w["box"])
+        desc = crp.grid_desc((64,) * 3, dx, origin=org, dtype=crp.F32,
+                             source=crp.GRID_TURBULENT, lmin=lmin, lmax=w["lmax"],
+                             brms=w["brms"], seed=w["seed"])
+        return w, desc, dict(flags=crp.GALACTIC | crp.BORDER, galactic=w["disk"])
+    w = workloads.GALACTIC_MULTIARM
+    zn = (4, 4, 4)
+    desc = crp.grid_desc(zn, 20.0, origin=(-40.0, -40.0, -40.0), dtype=crp.F32,
+                         data=np.zeros(zn + (3,)))
+    return w, desc, dict(flags=crp.GMF | crp.BORDER, gmf=workloads.multiarm_gmf_params())
+
+
+def _run(galaxy, inj, n, extra_flags=0, **launch):
+    w, desc, analytic = _setup(galaxy)
+    analytic = dict(analytic)
+    analytic["flags"] |= extra_flags
     ctx = crp.crp_context_create(0, w["seed"], n + 16)
     try:
         grid = crp.crp_grid_create(ctx, desc)
         mods = crp.modules(precision=crp.MIXED, tol=w["tol"], h_min=w["h_min"], h_max=w["h_max"],
                            field_unit_T=crp.MICROGAUSS_T, length_unit_m=crp.KPC_M,
-                           border_radius=w["border_r"], e_min=1.0,
-                           flags=crp.GALACTIC | crp.BORDER | extra_flags, galactic=w["disk"],
-                           **launch)
+                           border_radius=w["border_r"], e_min=1.0, **analytic, **launch)
         crp.crp_candidates_inject(ctx, crp.candidate_arrays(inj), n)
         crp.crp_propagate(ctx, grid, mods)
         rec = crp.crp_collect(ctx, crp.COLLECT_ALL)
@@ -43,7 +55,8 @@ def _run(n_side, inj, n, extra_flags=0, **launch):
     return np.sort(rec, order="id")
 
 
-def test_galactic_backtracking_records_do_not_depend_on_the_launch(lib):
+@pytest.mark.parametrize("galaxy", ["disk_halo_random", "multiarm"])
+def test_galactic_backtracking_records_do_not_depend_on_the_launch(lib, galaxy):
     w = workloads.GALACTIC_LENS
     n = 3000
     dirs, R = workloads.backtrack_directions(n, w["r_lo"], w["r_hi"], 91)
@@ -51,10 +64,10 @@ def test_galactic_backtracking_records_do_not_depend_on_the_launch(lib):
     inj = crp.host_injection(dict(x=np.full(n, e[0]), y=np.full(n, e[1]), z=np.full(n, e[2]),
                                   ux=dirs[:, 0], uy=dirs[:, 1], uz=dirs[:, 2], E=R,
                                   A=np.ones(n), Z=np.ones(n), q=-np.ones(n)))
-    fixed = _run(64, inj, n, block_size=256, blocks_per_sm=2, queue_order=0)
+    fixed = _run(galaxy, inj, n, block_size=256, blocks_per_sm=2, queue_order=0)
     assert np.all(fixed["status"] == crp.AT_BORDER)
-    others = [_run(64, inj, n, block_size=128, blocks_per_sm=5, queue_order=1),
-              _run(64, inj, n, block_size=32, blocks_per_sm=3, queue_order=-1),
-              _run(64, inj, n, extra_flags=crp.EMIN, block_size=256, blocks_per_sm=2)]
+    others = [_run(galaxy, inj, n, block_size=128, blocks_per_sm=5, queue_order=1),
+              _run(galaxy, inj, n, block_size=32, blocks_per_sm=3, queue_order=-1),
+              _run(galaxy, inj, n, extra_flags=crp.EMIN, block_size=256, blocks_per_sm=2)]
     for o in others:
         assert o.tobytes() == fixed.tobytes()
