@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_train_tc(const MlpTrainTcPa
   float* sbo = sWo + 3 * kH;    // [4]
   float* sy = sbo + 4;          // [2 halves][3][kRows] output-layer partial sums
   float* sdy = sy + 6 * kRows;  // [3][kRows]
-  float* sl = sdy + 3 * kRows;  // [kRows] loss terms
+  float* sl = sdy + 3 * kRows;  // [4 warps][4]: their sums of dy and of the loss terms
   float* sx = sl + kRows;       // [kRows][kMaxIn] the tile's inputs
   const int tid = threadIdx.x, warp = tid >> 5;
   const int r = tid & (kRows - 1);  // row of the tile this thread owns
@@ -649,7 +649,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_train_tc(const MlpTrainTcPa
       sdy[r] = dy0;
       sdy[kRows + r] = dy1;
       sdy[2 * kRows + r] = dy2;
-      sl[r] = 1.f - d;
+      // the output biases' gradients and the loss: sums over this warp's rows
+      float s0 = dy0, s1 = dy1, s2 = dy2, s3 = 1.f - d;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+      }
+      if ((tid & 31) == 0) {
+        sl[4 * warp] = s0;
+        sl[4 * warp + 1] = s1;
+        sl[4 * warp + 2] = s2;
+        sl[4 * warp + 3] = s3;
+      }
     }
     __syncthreads();
     {
@@ -659,25 +673,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_train_tc(const MlpTrainTcPa
       // banks) instead of one
       const unsigned char* cb = As + (tid >> 3) * kLbo + (tid & 7) * 2;
       const int skew = tid >> 3;
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+      // two partial sums per output (even and odd rows) halve the FMA chains
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, b0 = 0.f, b1 = 0.f, b2 = 0.f;
 #pragma unroll 4
-      for (int rr = 0; rr < kRows; ++rr) {
-        const int R = (rr + skew) & (kRows - 1);
+      for (int rr = 0; rr < kRows; rr += 2) {
+        const int R = (rr + skew) & (kRows - 1), R2 = (R + 1) & (kRows - 1);
         const float hv = __bfloat162float(
             *reinterpret_cast<const __nv_bfloat16*>(cb + (R >> 3) * kSbo + (R & 7) * 16));
+        const float hw = __bfloat162float(
+            *reinterpret_cast<const __nv_bfloat16*>(cb + (R2 >> 3) * kSbo + (R2 & 7) * 16));
         a0 = fmaf(sdy[R], hv, a0);
         a1 = fmaf(sdy[kRows + R], hv, a1);
         a2 = fmaf(sdy[2 * kRows + R], hv, a2);
+        b0 = fmaf(sdy[R2], hw, b0);
+        b1 = fmaf(sdy[kRows + R2], hw, b1);
+        b2 = fmaf(sdy[2 * kRows + R2], hw, b2);
       }
-      go0 += a0;
-      go1 += a1;
-      go2 += a2;
-      if (tid < 4) {
-        const float* src = tid < 3 ? sdy + tid * kRows : sl;
-        float sacc = 0.f;
-        for (int rr = 0; rr < kRows; ++rr) sacc += src[rr];
-        gsmall += sacc;
-      }
+      go0 += a0 + b0;
+      go1 += a1 + b1;
+      go2 += a2 + b2;
+      if (tid < 4) gsmall += (sl[tid] + sl[4 + tid]) + (sl[8 + tid] + sl[12 + tid]);
     }
     __syncthreads();  // every column has read h_3 before it is overwritten
     // dz_3 = bf16((dy . W_out[:, c]) where h_3 > 0), in place in tile A
@@ -734,21 +749,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_train_tc(const MlpTrainTcPa
       // column tid: the input layer's gradients from dz_0 and the tile's inputs
       const unsigned char* cb = As + (tid >> 3) * kLbo + (tid & 7) * 2;
       const int skew = tid >> 3;
-      float aw[kMaxIn], ab = 0.f;
+      // two partial sums per output (even and odd rows) halve the FMA chains
+      float aw[kMaxIn], bw[kMaxIn], ab = 0.f, bb = 0.f;
 #pragma unroll
-      for (int i = 0; i < kMaxIn; ++i) aw[i] = 0.f;
-#pragma unroll 4
-      for (int rr = 0; rr < kRows; ++rr) {
-        const int R = (rr + skew) & (kRows - 1);
+      for (int i = 0; i < kMaxIn; ++i) aw[i] = bw[i] = 0.f;
+#pragma unroll 2
+      for (int rr = 0; rr < kRows; rr += 2) {
+        const int R = (rr + skew) & (kRows - 1), R2 = (R + 1) & (kRows - 1);
         const float z = __bfloat162float(
             *reinterpret_cast<const __nv_bfloat16*>(cb + (R >> 3) * kSbo + (R & 7) * 16));
+        const float z2 = __bfloat162float(
+            *reinterpret_cast<const __nv_bfloat16*>(cb + (R2 >> 3) * kSbo + (R2 & 7) * 16));
         ab += z;
+        bb += z2;
 #pragma unroll
-        for (int i = 0; i < NI; ++i) aw[i] = fmaf(z, sx[R * kMaxIn + i], aw[i]);
+        for (int i = 0; i < NI; ++i) {
+          aw[i] = fmaf(z, sx[R * kMaxIn + i], aw[i]);
+          bw[i] = fmaf(z2, sx[R2 * kMaxIn + i], bw[i]);
+        }
       }
 #pragma unroll
-      for (int i = 0; i < NI; ++i) gi[i] += aw[i];
-      gib += ab;
+      for (int i = 0; i < NI; ++i) gi[i] += aw[i] + bw[i];
+      gib += ab + bb;
     }
     __syncthreads();  // tile A and the staged inputs are rewritten by the next tile
   }
