@@ -476,7 +476,8 @@ int64_t crp_mlp_num_params(const crp_mlp* mlp);
 crp_status crp_mlp_set_params(crp_mlp* mlp, const float* params);
 /* either pointer may be NULL; grad is the last train step's gradient */
 crp_status crp_mlp_get_params(const crp_mlp* mlp, float* params, float* grad);
-/* device pointers; n a multiple of 128; y_hat [n][3].  With hidden = 256 and
+/* device pointers (either may be NULL when n = 0, which does nothing); n a
+ * multiple of 128; y_hat [n][3].  With hidden = 256 and
  * n_in <= 8 the default path is one fused kernel on the fifth-generation
  * tensor cores (tcgen05 MMAs into TMEM, activations kept on chip; it
  * synchronises the stream to read its completion flag and returns CRP_E_CUDA

@@ -1427,7 +1427,7 @@ crp_status crp_mlp_get_params(const crp_mlp* M, float* host, float* host_grad) {
 }
 
 crp_status crp_mlp_forward(crp_mlp* M, const float* x, float* y_hat, int64_t n, void* stream) {
-  if (!M || !x || !y_hat || n < 0) {
+  if (!M || n < 0 || (n > 0 && (!x || !y_hat))) {
     set_error("crp_mlp_forward: bad argument");
     return CRP_E_INVALID;
   }

@@ -371,6 +371,17 @@ def test_empty_and_invalid_inputs(field64):
         assert e.value.status == crp.E_QUEUE_FULL
         with pytest.raises(crp.CrpError):
             crp.crp_propagate(ctx, g, crp.modules(h_min=0.0))
+        # the other calls on an empty pool: histograms of nothing, the
+        # surrogate on no samples
+        assert not np.any(crp.crp_histogram_energy(ctx, crp.COLLECT_ALL, 1e18, 1e21, 10))
+        assert not np.any(crp.crp_histogram_healpix(ctx, crp.COLLECT_ALL, 4, 0))
+        import torch
+        mlp = crp.crp_mlp_create(ctx, 4, 256, 4, 7)
+        try:
+            crp.crp_mlp_forward(mlp, torch.zeros((0, 4), device="cuda"),
+                                torch.zeros((0, 3), device="cuda"), 0)
+        finally:
+            crp.crp_mlp_destroy(mlp)
         crp.crp_grid_destroy(g)
     finally:
         crp.crp_context_destroy(ctx)
