@@ -268,6 +268,35 @@ def test_fused_tensor_core_forward_matches_layered(torch_dev, n):
     assert_outputs_close(layered, ref)
 
 
+def test_layered_forward_after_tensor_core_training(torch_dev):
+    """After training steps on the one-kernel path (eager, then graph
+    replays), whose Adam writes the bf16 weight copies and tensor-core
+    images, both forward paths see the same updated weights."""
+    torch = torch_dev
+    p = _params(23)
+    x, t = _batch(4096, 24)
+    ctx = crp.crp_context_create(0, 1, 16)
+    try:
+        mlp = crp.crp_mlp_create(ctx, 4, 256, 4, 7)
+        crp.crp_mlp_set_params(mlp, p)
+        xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+        for _ in range(5):
+            crp.crp_mlp_train_step(mlp, xd, td, 4096, 1e-3)
+        out = {}
+        for path in (crp.MLP_PATH_TENSOR_CORE_FUSED, crp.MLP_PATH_LAYERED):
+            crp.crp_mlp_set_forward_path(mlp, path)
+            yd = torch.zeros((4096, 3), dtype=torch.float32, device="cuda")
+            crp.crp_mlp_forward(mlp, xd, yd, 4096)
+            torch.cuda.synchronize()
+            out[path] = yd.cpu().numpy().astype(np.float64)
+        p1 = crp.crp_mlp_get_params(mlp)[0]
+        crp.crp_mlp_destroy(mlp)
+    finally:
+        crp.crp_context_destroy(ctx)
+    assert np.max(np.abs(p1 - p)) > 1e-4  # the steps changed the weights
+    assert_outputs_close(out[crp.MLP_PATH_TENSOR_CORE_FUSED], out[crp.MLP_PATH_LAYERED])
+
+
 @pytest.mark.parametrize("n", [2048, 128 * 37, 16384])
 def test_tensor_core_training_gradients(torch_dev, n):
     """The training step on the tensor cores (the one-kernel forward, output
