@@ -1126,8 +1126,9 @@ crp_status backward(crp_mlp* M, const float* x, const float* t, int64_t n, cudaS
 // Gradients of one training step on the tensor cores with the per-sample work
 // in one kernel (forward, output layer and loss, backward signals, the input
 // and output layers' gradients), then the hidden layers' weight gradients
-// dW_l = dz_l^T h_{l-1} and bias sums as split-K GEMMs over the transposed
-// signals that kernel wrote.
+// dW_l = dz_l^T h_{l-1} and bias sums as split-K GEMMs over the activations
+// and signals that kernel wrote (row-major, in the transposed-activation
+// workspace of the layered path, which has the same size).
 crp_status train_fused(crp_mlp* M, const float* x, const float* t, int64_t n, cudaStream_t s) {
   const int H = M->hidden, L = M->n_hidden;
   cudaError_t e = cudaMemsetAsync(M->grad, 0, sizeof(float) * M->n_params, s);
@@ -1148,10 +1149,9 @@ crp_status train_fused(crp_mlp* M, const float* x, const float* t, int64_t n, cu
   }
   P.Wout = M->params + M->w_off[L];
   P.bout = M->params + M->b_off[L];
-  for (int l = 0; l + 1 < L; ++l) P.hT[l] = M->hT[l];
+  for (int l = 0; l + 1 < L; ++l) P.h[l] = M->hT[l];
   __nv_bfloat16* sig[kMlpTrainGemm] = {M->dzT, M->dzT2, M->dzT3};
-  for (int l = L - 1, k = 0; l >= 1; --l, ++k) P.dzT[l] = sig[k];
-  P.ldt = n;
+  for (int l = L - 1, k = 0; l >= 1; --l, ++k) P.dz[l] = sig[k];
   P.loss = M->loss;
   P.gW1 = M->grad + M->w_off[0];
   P.gb1 = M->grad + M->b_off[0];
@@ -1164,14 +1164,14 @@ crp_status train_fused(crp_mlp* M, const float* x, const float* t, int64_t n, cu
   GemmTcParams gs[kMlpTrainGemm];
   int ng = 0;
   for (int l = L - 1; l >= 1; --l) {
-    // dW_l += dz_l^T h_{l-1}: A = dz_l^T [H][n], B = h_{l-1}^T [H][n], K = n split
+    // dW_l += dz_l^T h_{l-1}: A = dz_l [n][H], B = h_{l-1} [n][H], K = n split
     GemmTcParams& g = gs[ng++];
     memset(&g, 0, sizeof(g));
     g.err = M->tc_err;
-    g.A = P.dzT[l];
-    g.lda = n;
-    g.B = M->hT[l - 1];
-    g.ldb = n;
+    g.A = P.dz[l];
+    g.lda = H;
+    g.B = P.h[l - 1];
+    g.ldb = H;
     g.M = H;
     g.K = n;
     const int64_t sp = n / 256 < 1 ? 1 : n / 256;
@@ -1179,7 +1179,7 @@ crp_status train_fused(crp_mlp* M, const float* x, const float* t, int64_t n, cu
     g.splits = (int)(sp < sp_max ? sp : sp_max);
     g.out_f = M->grad + M->w_off[l];
     g.ldf = H;
-    g.rowsum = M->grad + M->b_off[l];  // db_l: the rows of dz_l^T summed over the batch
+    g.rowsum = M->grad + M->b_off[l];  // db_l: the columns of dz_l summed over the batch
   }
   e = wgrad_tc(gs, ng, M->sm_count, s);
   if (e != cudaSuccess) return fail_cuda(e, "mlp: tensor-core weight-gradient GEMMs");

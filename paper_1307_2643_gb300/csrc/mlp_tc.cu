@@ -346,13 +346,64 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const MlpTcParam
                  : "memory");
 }
 
+// Descriptor of a 128-byte-swizzled K-major operand: start address, leading
+// byte offset 16 (unused within a swizzle atom), 1024 bytes between groups
+// of 8 rows, version 1, swizzle mode 2 (128 B) in bits 61-63.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         (1ull << 46) | (2ull << 61);
+}
+
+__device__ __forceinline__ void bar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// One 2D TMA box (64 columns x the map's box rows) at column x, row y.
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Store / add one 2D box from shared memory to global through the TMA (bulk
+// async group of the issuing thread).
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];\n" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(x), "r"(y), "r"(smem_u32(src))
+      : "memory");
+}
+__device__ __forceinline__ void tma_reduce_add_2d(const CUtensorMap* map, int x, int y,
+                                                  const void* src) {
+  asm volatile(
+      "cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2}], "
+      "[%3];\n" ::"l"(reinterpret_cast<uint64_t>(map)),
+      "r"(x), "r"(y), "r"(smem_u32(src))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+}
+
 // ---------------------------------------------------------------------------
 // A whole training step's per-sample work in one kernel (hidden 256, three
 // hidden-to-hidden layers), with the forward kernel's layout and thread roles.
 // Per tile of 128 samples:
 //   * input layer -> h_0 (tile A); GEMMs with W_1 .. W_3 -> h_1 .. h_3 (bias,
-//     ReLU); h_0 .. h_2 also written transposed for the weight gradients, and
-//     their ReLU masks kept as bits in registers (thread (row r, half g):
+//     ReLU); h_0 .. h_2 also written out (row-major) for the weight
+//     gradients, and their ReLU masks kept as bits in registers (thread (row r, half g):
 //     bit k of word q is column 128 g + 32 q + k);
 //   * output layer on the CUDA cores: y = W_out h_3 + b_out from the two
 //     warpgroups' partial sums, y_hat = y / |y|, the loss term 1 - y_hat . t
@@ -361,7 +412,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const MlpTcParam
 //     dz_3 = bf16((dy . W_out[:, c]) where h_3 > 0), in place in tile A;
 //   * GEMMs with W_3^T, W_2^T, W_1^T (images of the transposed weights) ->
 //     dz_2, dz_1, dz_0 = bf16(C where h_{l-1} > 0) in tile A (dz_3 .. dz_1 also
-//     written transposed for the weight gradients);
+//     written out, row-major, for the weight gradients);
 //   * per column c the input layer's gradients sum_r dz_0[r][c] x[r][i] and
 //     sum_r dz_0[r][c].
 // The six weight images of a tile are copied into tile B in that order, each
@@ -376,15 +427,13 @@ constexpr size_t kTrainFloats = kH * kMaxIn + kH + kMlpTrainGemm * kH + 3 * kH +
 constexpr size_t kTrainSmem = 1024 + kABytes + kBBytes + 64 + kTrainFloats * 4;
 static_assert(kTrainSmem <= 232448, "shared memory of the training kernel");
 
-// Transposed store of row `row`'s bf16 values (packed pairs w) of columns
-// c0 .. c0 + n - 1: one 2-byte store per column (a warp's 32 consecutive rows
-// make each column's stores one contiguous 64-byte run).
-__device__ __forceinline__ void store_transposed(const uint32_t* w, int n, int64_t row, int c0,
-                                                 __nv_bfloat16* T, int64_t ldt) {
-  unsigned short* t = reinterpret_cast<unsigned short*>(T);
-#pragma unroll
-  for (int j = 0; j < n; ++j)
-    t[(int64_t)(c0 + j) * ldt + row] = (unsigned short)(w[j / 2] >> (16 * (j & 1)));
+// Byte offset of the 16-byte chunk q (columns 8 q .. 8 q + 7) of row r in the
+// training kernel's tile A: 128 rows x 256 bf16 columns, 128-byte-swizzled
+// K-major (four 64-column blocks of 16 KB; a row's 128 bytes of a block at
+// 128 r, its chunks XOR-ed with r % 8), the layout of a TMA box of 64 columns
+// x 128 rows with the 128-byte swizzle.
+__device__ __forceinline__ uint32_t sw_chunk(int r, int q) {
+  return (uint32_t)((q >> 3) * 16384 + r * 128 + (((q & 7) ^ (r & 7)) << 4));
 }
 
 // Bits of the positive values among 2 nw packed bf16 (bit 2 e: low half of
@@ -411,8 +460,16 @@ __device__ __forceinline__ void set_word(uint32_t (&m)[4], int q, uint32_t v) {
   m[3] = q == 3 ? v : m[3];
 }
 
+// Tensor maps of the row-major [n][256] outputs h_0 .. h_2 and dz_1 .. dz_3
+// (boxes of 64 columns x 128 rows, 128-byte swizzle), in the order of the
+// GEMMs that read them: store s holds the input of GEMM s.
+struct TrainStoreMaps {
+  CUtensorMap out[2 * kMlpTrainGemm];
+};
+
 template <int NIN>
-__global__ void __launch_bounds__(kThreads, 1) k_mlp_train_tc(const MlpTrainTcParams P) {
+__global__ void __launch_bounds__(kThreads, 1)
+    k_mlp_train_tc(const MlpTrainTcParams P, const __grid_constant__ TrainStoreMaps T) {
   constexpr int NG = kMlpTrainGemm;
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   unsigned char* base = tc_smem + ((1024u - (smem_u32(tc_smem) & 1023u)) & 1023u);
@@ -468,26 +525,30 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_train_tc(const MlpTrainTcPa
     for (uint32_t c = tid; c < kBBytes / 16; c += kThreads) cp_async16(Bs + 16 * c, src + 16 * c);
   };
   if (blockIdx.x < P.n_tiles) fetch(0);
-  // step s of the schedule on tiles A and B: wait for its weights, 16 MMAs,
-  // wait for their completion (bounded), start copying the next weights;
-  // false on a timed-out wait
-  auto gemm_step = [&](int s, bool more_tiles) -> bool {
+  // step s of the schedule on tiles A and B: wait for its weights, write
+  // tile A (the GEMM's input) out by TMA, 16 MMAs, wait for their completion
+  // (bounded) and for the TMA's reads of tile A, start copying the next
+  // weights; false on a timed-out wait
+  auto gemm_step = [&](int s, bool more_tiles, int64_t tile) -> bool {
     asm volatile("cp.async.wait_all;\n" ::: "memory");
-    // generic-proxy writes of A and B -> visible to the tensor cores
+    // generic-proxy writes of A and B -> visible to the tensor cores and TMA
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (tid == 0) {
       const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+      for (int b = 0; b < 4; ++b) tma_store_2d(&T.out[s], 64 * b, (int)(tile * kRows), As + b * 16384);
+      bulk_commit();
 #pragma unroll 1
       for (int k = 0; k < kH / 16; ++k)
-        mma_bf16(tmem, sdesc(a0 + 2u * k * kLbo, kLbo, kSbo), sdesc(b0 + 2u * k * kLbo, kLbo, kSbo),
-                 kIdesc, k > 0 ? 1u : 0u);
+        mma_bf16(tmem, sdesc_sw128(a0 + (uint32_t)(k >> 2) * 16384u + 32u * (uint32_t)(k & 3)),
+                 sdesc(b0 + 2u * k * kLbo, kLbo, kSbo), kIdesc, k > 0 ? 1u : 0u);
       mma_commit(bar);
     }
     bool ok = bar_wait(bar, parity);
     if (!ok) ok = bar_wait(bar, parity);  // a second bounded wait before giving up
+    if (tid == 0) bulk_wait_read();  // tile A may be rewritten once the TMA has read it
     parity ^= 1u;
     if (__syncthreads_or(!ok)) {
       if (tid == 0) atomicOr(P.err, 1u);
@@ -562,9 +623,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_train_tc(const MlpTrainTcPa
           w[e / 2] = pack_bf16(v[0], v[1]);
           w[e / 2 + 1] = pack_bf16(v[2], v[3]);
         }
-        *reinterpret_cast<uint4*>(As + (r >> 3) * kSbo + kc * kLbo + (r & 7) * 16) =
-            make_uint4(w[0], w[1], w[2], w[3]);
-        store_transposed(w, 8, row, kc * 8, P.hT[0], P.ldt);
+        *reinterpret_cast<uint4*>(As + sw_chunk(r, kc)) = make_uint4(w[0], w[1], w[2], w[3]);
         mq |= positive_bits(w, 4) << (8 * kk);
       }
       set_word(mk[0], q, mq);
@@ -573,7 +632,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_train_tc(const MlpTrainTcPa
     float y0 = 0.f, y1 = 0.f, y2 = 0.f;
 #pragma unroll
     for (int j = 0; j < NG; ++j) {
-      if (!gemm_step(j, more)) {
+      if (!gemm_step(j, more, tile)) {
         failed = true;
         break;
       }
@@ -618,12 +677,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_train_tc(const MlpTrainTcPa
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          *reinterpret_cast<uint4*>(As + (r >> 3) * kSbo + (cc * 4 + u) * kLbo + (r & 7) * 16) =
+          *reinterpret_cast<uint4*>(As + sw_chunk(r, cc * 4 + u)) =
               make_uint4(w[4 * u], w[4 * u + 1], w[4 * u + 2], w[4 * u + 3]);
-        if (!last) {
-          store_transposed(w, 32, row, cc * 32, P.hT[j + 1], P.ldt);
-          set_word(mk[j + 1], q, positive_bits(w, 16));
-        }
+        if (!last) set_word(mk[j + 1], q, positive_bits(w, 16));
       }
       after_epilogue();
     }
@@ -667,21 +723,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_train_tc(const MlpTrainTcPa
     }
     __syncthreads();
     {
-      // column tid: the output layer's weight gradients over the tile's rows.
-      // Column passes start at row tid / 8: a warp's four 8-column chunks
-      // then sit in four different rows of their core matrices (different
-      // banks) instead of one
-      const unsigned char* cb = As + (tid >> 3) * kLbo + (tid & 7) * 2;
-      const int skew = tid >> 3;
+      // column tid: the output layer's weight gradients over the tile's rows
+      // (a warp reads 64 bytes of one row: four chunks in distinct banks)
+      const unsigned char* cb = As + (tid >> 6) * 16384 + (tid & 7) * 2;
+      const int qc = (tid >> 3) & 7;
       // two partial sums per output (even and odd rows) halve the FMA chains
       float a0 = 0.f, a1 = 0.f, a2 = 0.f, b0 = 0.f, b1 = 0.f, b2 = 0.f;
 #pragma unroll 4
       for (int rr = 0; rr < kRows; rr += 2) {
-        const int R = (rr + skew) & (kRows - 1), R2 = (R + 1) & (kRows - 1);
-        const float hv = __bfloat162float(
-            *reinterpret_cast<const __nv_bfloat16*>(cb + (R >> 3) * kSbo + (R & 7) * 16));
-        const float hw = __bfloat162float(
-            *reinterpret_cast<const __nv_bfloat16*>(cb + (R2 >> 3) * kSbo + (R2 & 7) * 16));
+        const int R = rr, R2 = rr + 1;
+        const float hv = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(
+            cb + R * 128 + ((qc ^ (R & 7)) << 4)));
+        const float hw = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(
+            cb + R2 * 128 + ((qc ^ (R2 & 7)) << 4)));
         a0 = fmaf(sdy[R], hv, a0);
         a1 = fmaf(sdy[kRows + R], hv, a1);
         a2 = fmaf(sdy[2 * kRows + R], hv, a2);
@@ -702,7 +756,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_train_tc(const MlpTrainTcPa
       uint32_t w[16];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        uint4* ap = reinterpret_cast<uint4*>(As + (r >> 3) * kSbo + (cc * 4 + u) * kLbo + (r & 7) * 16);
+        uint4* ap = reinterpret_cast<uint4*>(As + sw_chunk(r, cc * 4 + u));
         const uint4 hq = *ap;
         const uint32_t hw[4] = {hq.x, hq.y, hq.z, hq.w};
 #pragma unroll
@@ -716,12 +770,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_train_tc(const MlpTrainTcPa
         }
         *ap = make_uint4(w[4 * u], w[4 * u + 1], w[4 * u + 2], w[4 * u + 3]);
       }
-      store_transposed(w, 32, row, cc * 32, P.dzT[NG], P.ldt);
     }
     // ---- backward: dz_{l-1} = (dz_l W_l) where h_{l-1} > 0, l = NG .. 1 ----
 #pragma unroll
     for (int j = NG - 1; j >= 0; --j) {
-      if (!gemm_step(2 * NG - 1 - j, more)) {
+      if (!gemm_step(2 * NG - 1 - j, more, tile)) {
         failed = true;
         break;
       }
@@ -738,28 +791,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_train_tc(const MlpTrainTcPa
                                 (mw >> (jj + 1)) & 1u ? __uint_as_float(v[jj + 1]) : 0.f);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          *reinterpret_cast<uint4*>(As + (r >> 3) * kSbo + (cc * 4 + u) * kLbo + (r & 7) * 16) =
+          *reinterpret_cast<uint4*>(As + sw_chunk(r, cc * 4 + u)) =
               make_uint4(w[4 * u], w[4 * u + 1], w[4 * u + 2], w[4 * u + 3]);
-        if (j >= 1) store_transposed(w, 32, row, cc * 32, P.dzT[j], P.ldt);
       }
       after_epilogue();
     }
     if (failed) break;
     {
       // column tid: the input layer's gradients from dz_0 and the tile's inputs
-      const unsigned char* cb = As + (tid >> 3) * kLbo + (tid & 7) * 2;
-      const int skew = tid >> 3;
+      const unsigned char* cb = As + (tid >> 6) * 16384 + (tid & 7) * 2;
+      const int qc = (tid >> 3) & 7;
       // two partial sums per output (even and odd rows) halve the FMA chains
       float aw[kMaxIn], bw[kMaxIn], ab = 0.f, bb = 0.f;
 #pragma unroll
       for (int i = 0; i < kMaxIn; ++i) aw[i] = bw[i] = 0.f;
 #pragma unroll 2
       for (int rr = 0; rr < kRows; rr += 2) {
-        const int R = (rr + skew) & (kRows - 1), R2 = (R + 1) & (kRows - 1);
-        const float z = __bfloat162float(
-            *reinterpret_cast<const __nv_bfloat16*>(cb + (R >> 3) * kSbo + (R & 7) * 16));
-        const float z2 = __bfloat162float(
-            *reinterpret_cast<const __nv_bfloat16*>(cb + (R2 >> 3) * kSbo + (R2 & 7) * 16));
+        const int R = rr, R2 = rr + 1;
+        const float z = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(
+            cb + R * 128 + ((qc ^ (R & 7)) << 4)));
+        const float z2 = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(
+            cb + R2 * 128 + ((qc ^ (R2 & 7)) << 4)));
         ab += z;
         bb += z2;
 #pragma unroll
@@ -791,6 +843,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_train_tc(const MlpTrainTcPa
   // a timed-out MMA wait: one more bounded wait for those MMAs before the
   // TMEM is given up (the phase that did not complete has parity ^ 1)
   if (failed && tid == 0) bar_wait(bar, parity ^ 1u);
+  if (tid == 0) bulk_wait_all();  // every TMA store has completed
   asm volatile("cp.async.wait_all;\n" ::: "memory");  // no copy outlives the kernel
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -817,57 +870,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_train_tc(const MlpTrainTcPa
 constexpr uint32_t kAtomA = kRows * 128;  // 64 columns of 128 rows: 16 KB
 constexpr uint32_t kAtomB = kH * 128;     // 64 columns of 256 rows: 32 KB
 constexpr size_t kGemmSmem = 1024 + 4 * kAtomA + 4 * kAtomB + 64;
-
-// Descriptor of a 128-byte-swizzled K-major operand: start address, leading
-// byte offset 16 (unused within a swizzle atom), 1024 bytes between groups
-// of 8 rows, version 1, swizzle mode 2 (128 B) in bits 61-63.
-__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
-  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         (1ull << 46) | (2ull << 61);
-}
-
-__device__ __forceinline__ void bar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-// One 2D TMA box (64 columns x the map's box rows) at column x, row y.
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
-                                            uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// Store / add one 2D box from shared memory to global through the TMA (bulk
-// async group of the issuing thread).
-__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];\n" ::"l"(
-          reinterpret_cast<uint64_t>(map)),
-      "r"(x), "r"(y), "r"(smem_u32(src))
-      : "memory");
-}
-__device__ __forceinline__ void tma_reduce_add_2d(const CUtensorMap* map, int x, int y,
-                                                  const void* src) {
-  asm volatile(
-      "cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2}], "
-      "[%3];\n" ::"l"(reinterpret_cast<uint64_t>(map)),
-      "r"(x), "r"(y), "r"(smem_u32(src))
-      : "memory");
-}
-__device__ __forceinline__ void bulk_commit() {
-  asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
-}
-__device__ __forceinline__ void bulk_wait_read() {
-  asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
-}
-__device__ __forceinline__ void bulk_wait_all() {
-  asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
-}
 
 template <int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -1138,24 +1140,40 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // ---------------------------------------------------------------------------
 // Weight gradients of the hidden layers: for up to kGemmBatch problems q,
-// C_q[256][256] += A_q[256][K] B_q[256][K]^T (A = dz_l^T, B = h_{l-1}^T, K the
-// batch) and rowsum_q[m] += sum_k A_q[m][k] (the bias gradient).  A work item
-// is one problem's K range; the CTA computes the whole 256 x 256 output of it
-// in 512 TMEM columns (two M = 128 halves against the same B chunk).  The K
-// range streams through three shared-memory stages of 64 columns (A and B
-// 256 x 64 bf16 each, 128-byte swizzle, 64 KB a stage): one thread starts the
-// TMA copies two chunks ahead, issues a chunk's 8 MMAs as soon as it has
+// C_q[256][256] += A_q^T B_q with A_q = dz_l and B_q = h_{l-1} stored
+// row-major [K][256] (K the batch), and rowsum_q[m] += sum_k A_q[k][m] (the
+// bias gradient).  A work item is one problem's K range; the CTA computes the
+// whole 256 x 256 output of it in 512 TMEM columns (two M = 128 halves against
+// the same B chunk).  The K range streams through three shared-memory stages
+// of 64 rows (A and B 64 x 256 bf16 each, 64 KB a stage) as TMA boxes of 64
+// rows x 64 columns with the 128-byte swizzle, which the MMAs read as
+// MN-major operands (the 256 columns contiguous, K the row): one thread starts
+// the copies two chunks ahead, issues a chunk's 8 MMAs as soon as it has
 // landed and commits them to the stage's "freed" barrier, which the refill of
-// that stage waits for; meanwhile every thread adds its A row of the chunk to
-// its row sum.  The epilogue stages each half as FP32 boxes and adds it to C
-// with TMA reduce-add.
+// that stage waits for; meanwhile every thread adds eight columns of eight of
+// the chunk's A rows to its column sums.  The epilogue stages each half as
+// FP32 boxes and adds it to C with TMA reduce-add.
 // ---------------------------------------------------------------------------
 constexpr int kGemmBatch = 3;  // problems of one launch
 constexpr int kWgStages = 3;
-constexpr uint32_t kWgA = 256 * 128;  // 256 rows x 64 bf16 columns: 32 KB
+constexpr uint32_t kWgBox = 64 * 128;  // 64 rows x 64 bf16 columns: 8 KB
+constexpr uint32_t kWgA = 4 * kWgBox;  // 64 rows x 256 columns: 32 KB
 constexpr uint32_t kWgStage = 2 * kWgA;
-constexpr size_t kWgSmem = 1024 + kWgStages * kWgStage + 2 * kWgStages * 8 + 16;
+constexpr size_t kWgSmem =
+    1024 + kWgStages * kWgStage + 8 * kH * sizeof(float) + 2 * kWgStages * 8 + 16;
 constexpr uint32_t kWgTmemCols = 512;
+// kind::f16 instruction descriptor as kIdesc with both operands MN-major
+// (bits 15 and 16: A and B transposed)
+constexpr uint32_t kIdescMN = kIdesc | (1u << 15) | (1u << 16);
+
+// Descriptor of a 128-byte-swizzled MN-major operand made of the boxes above:
+// 64 MN-contiguous elements per 128-byte row, one row per K; leading byte
+// offset 8192 (the next box, 64 elements further along MN), stride byte
+// offset 1024 (the next group of 8 K rows), version 1, swizzle mode 2.
+__device__ __forceinline__ uint64_t sdesc_mn_sw128(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(kWgBox >> 4) << 16) |
+         ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
+}
 
 struct WgradMaps {
   CUtensorMap a[kGemmBatch], b[kGemmBatch], o[kGemmBatch];
@@ -1170,8 +1188,9 @@ struct WgradMaps {
 __global__ void __launch_bounds__(kThreads, 1) k_wgrad_tc(const __grid_constant__ WgradMaps W) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   unsigned char* base = tc_smem + ((1024u - (smem_u32(tc_smem) & 1023u)) & 1023u);
-  uint64_t* full = reinterpret_cast<uint64_t*>(base + kWgStages * kWgStage);  // bytes landed
-  uint64_t* freed = full + kWgStages;                                          // MMAs done
+  float* colsum = reinterpret_cast<float*>(base + kWgStages * kWgStage);  // [8][256]
+  uint64_t* full = reinterpret_cast<uint64_t*>(colsum + 8 * kH);         // bytes landed
+  uint64_t* freed = full + kWgStages;                                    // MMAs done
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(freed + kWgStages);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int r = tid & (kRows - 1), g = tid >> 7;
@@ -1213,8 +1232,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_wgrad_tc(const __grid_constant_
       const int s = c % kWgStages;
       unsigned char* st = base + s * kWgStage;
       bar_expect_tx(full + s, kWgStage);
-      tma_load_2d(st, &W.a[q], (int)(kb + 64 * c), 0, full + s);
-      tma_load_2d(st + kWgA, &W.b[q], (int)(kb + 64 * c), 0, full + s);
+      const int y = (int)(kb + 64 * c);
+      for (int j = 0; j < 4; ++j) tma_load_2d(st + j * kWgBox, &W.a[q], 64 * j, y, full + s);
+      for (int j = 0; j < 4; ++j) tma_load_2d(st + kWgA + j * kWgBox, &W.b[q], 64 * j, y, full + s);
       pend_full |= 1u << s;
     };
     // thread 0: wait (bounded) for the MMAs that read stage s
@@ -1232,7 +1252,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_wgrad_tc(const __grid_constant_
       issue(0);
       if (nch > 1) issue(1);
     }
-    float racc = 0.f;  // row tid of A summed over the item's K range
+    // columns 8 (tid % 32) .. + 7 of A summed over the item's rows k with
+    // k % 8 = tid / 32
+    float racc[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) racc[e] = 0.f;
     for (int c = 0; c < nch; ++c) {
       const int s = c % kWgStages;
       bool ok = bar_wait(full + s, (fph >> s) & 1u);  // the chunk's bytes are in shared memory
@@ -1253,24 +1277,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_wgrad_tc(const __grid_constant_
         for (int h = 0; h < 2; ++h)
 #pragma unroll
           for (int k = 0; k < 4; ++k)
-            mma_bf16(tmem + 256u * h, sdesc_sw128(a0 + 16384u * h + 32u * k),
-                     sdesc_sw128(b0 + 32u * k), kIdesc, (c > 0 || k > 0) ? 1u : 0u);
+            mma_bf16(tmem + 256u * h, sdesc_mn_sw128(a0 + 2u * kWgBox * h + 2048u * k),
+                     sdesc_mn_sw128(b0 + 2048u * k), kIdescMN, (c > 0 || k > 0) ? 1u : 0u);
         mma_commit(freed + s);
         pend_freed |= 1u << s;
       }
       {
-        // row tid of A in this chunk (thread t starts at chunk t % 8 of its
-        // row: a warp's loads then spread over the banks; the swizzle only
-        // permutes a row's 16-byte chunks, so the sum needs no unswizzling)
-        const uint4* rp = reinterpret_cast<const uint4*>(st + tid * 128);
+        // the 16-byte chunk of columns 8 og .. 8 og + 7 in rows k = rk + 8 j:
+        // box og / 8, chunk og % 8 XOR-ed with k % 8 = rk by the swizzle (a
+        // warp's loads cover one row's 512 bytes: conflict-free)
+        const int og = tid & 31, rk = tid >> 5;
+        const unsigned char* cp = st + (og >> 3) * kWgBox + rk * 128 + (((og & 7) ^ rk) << 4);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          const uint4 v = rp[(j + tid) & 7];
+          const uint4 v = *reinterpret_cast<const uint4*>(cp + j * 1024);
           const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             const __nv_bfloat162 p = *reinterpret_cast<const __nv_bfloat162*>(&w[e]);
-            racc += __low2float(p) + __high2float(p);
+            racc[2 * e] += __low2float(p);
+            racc[2 * e + 1] += __high2float(p);
           }
         }
       }
@@ -1289,12 +1315,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_wgrad_tc(const __grid_constant_
     if (tid == 0 && !failed)
       for (int c = nch - 3 > 0 ? nch - 3 : 0; c < nch; ++c)
         if (!wait_freed(c % kWgStages)) t0_ok = false;
+    {
+      float4* cs = reinterpret_cast<float4*>(colsum + (tid >> 5) * kH + 8 * (tid & 31));
+      cs[0] = make_float4(racc[0], racc[1], racc[2], racc[3]);
+      cs[1] = make_float4(racc[4], racc[5], racc[6], racc[7]);
+    }
     if (__syncthreads_or(failed || !t0_ok)) {
       failed = true;
       break;
     }
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    if (W.rowsum[q]) atomicAdd(W.rowsum[q] + tid, racc);
+    if (W.rowsum[q]) {
+      // column tid: the eight row classes' sums in a fixed order
+      float cs = 0.f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) cs += colsum[k * kH + tid];
+      atomicAdd(W.rowsum[q] + tid, cs);
+    }
     // ---- epilogue: each half as eight FP32 boxes of 32 columns x 128 rows
     // (128-byte swizzle) in the freed stages, added to C by TMA ----
 #pragma unroll 1
@@ -1463,14 +1500,15 @@ cudaError_t wgrad_tc(const GemmTcParams* ps, int np, int sm_count, cudaStream_t 
   W.err = ps[0].err;
   for (int q = 0; q < np; ++q) {
     const GemmTcParams& p = ps[q];
+    // A and B row-major [K][256]: 16-byte aligned bases and row pitches
     const bool ok = p.M == kH && p.K == W.K && p.K > 0 && p.K % 64 == 0 && p.err == W.err &&
                     p.err && ((uintptr_t)p.A % 16 == 0) && ((uintptr_t)p.B % 16 == 0) &&
-                    p.lda % 8 == 0 && p.ldb % 8 == 0 && p.lda >= p.K && p.ldb >= p.K && p.out_f &&
+                    p.lda % 8 == 0 && p.ldb % 8 == 0 && p.lda >= kH && p.ldb >= kH && p.out_f &&
                     (uintptr_t)p.out_f % 16 == 0 && p.ldf % 4 == 0 && p.ldf >= kH;
     if (!ok) return cudaErrorInvalidValue;
     W.rowsum[q] = p.rowsum;
-    if (!tensor_map(p.A, false, kH, p.K, p.lda, kH, &W.a[q]) ||
-        !tensor_map(p.B, false, kH, p.K, p.ldb, kH, &W.b[q]) ||
+    if (!tensor_map(p.A, false, p.K, kH, p.lda, 64, &W.a[q]) ||
+        !tensor_map(p.B, false, p.K, kH, p.ldb, 64, &W.b[q]) ||
         !tensor_map(p.out_f, true, kH, kH, p.ldf, kRows, &W.o[q]))
       return cudaErrorInvalidValue;
   }
@@ -1527,7 +1565,16 @@ cudaError_t mlp_train_tc(const MlpTrainTcParams& p, int sm_count, cudaStream_t s
   if (e != cudaSuccess) return e;
   int64_t grid = p.n_tiles < sm_count ? p.n_tiles : sm_count;
   if (grid < 1) return cudaSuccess;
-  k<<<(unsigned)grid, kThreads, kTrainSmem, s>>>(p);
+  // the inputs of GEMMs 0 .. 5: h_0, h_1, h_2, dz_3, dz_2, dz_1 (row-major
+  // [n][256], 16-byte aligned: TMA stores of 64-column boxes)
+  const __nv_bfloat16* outs[2 * kMlpTrainGemm] = {p.h[0], p.h[1], p.h[2], p.dz[3], p.dz[2], p.dz[1]};
+  TrainStoreMaps T;
+  memset(&T, 0, sizeof(T));
+  for (int i = 0; i < 2 * kMlpTrainGemm; ++i)
+    if (!outs[i] || (uintptr_t)outs[i] % 16 != 0 ||
+        !tensor_map(outs[i], false, p.n, kH, kH, kRows, &T.out[i]))
+      return cudaErrorInvalidValue;
+  k<<<(unsigned)grid, kThreads, kTrainSmem, s>>>(p, T);
   return cudaGetLastError();
 }
 

@@ -72,17 +72,19 @@ struct GemmTcParams {
   unsigned* err;  // set to 1 when a tensor-core wait timed out
 };
 cudaError_t gemm_tc(int epi, const GemmTcParams& p, int device, int sm_count, cudaStream_t s);
-// np (<= 3) weight-gradient problems of one shape (M = 256, the same K; the
-// GEMM_TC_ATOMIC fields with row sums) in one launch of a K-pipelined kernel:
-// each work item computes a whole 256 x 256 output over its K range,
-// streaming 64-column chunks through three shared-memory stages.
+// np (<= 3) weight-gradient problems of one shape in one launch of a
+// K-pipelined kernel: out_f[256][256] += A^T B with A and B stored row-major
+// [K][256] (leading dimensions lda, ldb >= 256; M = 256, the same K, a
+// multiple of 64), and rowsum[m] += sum_k A[k][m].  Each work item computes a
+// whole 256 x 256 output over its K range, streaming 64-row chunks through
+// three shared-memory stages.
 cudaError_t wgrad_tc(const GemmTcParams* ps, int np, int sm_count, cudaStream_t s);
 
 // One training step's forward pass, output layer, loss and backward signals
 // in one persistent tcgen05 kernel (hidden 256, three hidden-to-hidden
 // layers): per tile of 128 samples the activations and backward signals stay
 // in shared memory, the ReLU masks in registers; written out are the
-// transposed activations h_0 .. h_2 and backward signals dz_1 .. dz_3 the
+// activations h_0 .. h_2 and backward signals dz_1 .. dz_3 (row-major) the
 // weight-gradient GEMMs read, and the output and input layers' gradients.
 constexpr int kMlpTrainGemm = 3;
 struct MlpTrainTcParams {
@@ -100,9 +102,8 @@ struct MlpTrainTcParams {
   const float* bh[kMlpTrainGemm];
   const float* Wout;  // [3][256]
   const float* bout;
-  __nv_bfloat16* hT[kMlpTrainGemm];       // h_0 .. h_2 transposed, [256][ldt]
-  __nv_bfloat16* dzT[kMlpTrainGemm + 1];  // dz_1 .. dz_3 transposed (index = layer; 0 unused)
-  int64_t ldt;
+  __nv_bfloat16* h[kMlpTrainGemm];        // h_0 .. h_2, row-major [n][256]
+  __nv_bfloat16* dz[kMlpTrainGemm + 1];   // dz_1 .. dz_3, row-major [n][256] (index = layer)
   float* loss;   // += sum over the batch of 1 - y_hat . t
   float* gW1;    // [256][n_in] +=
   float* gb1;    // [256] +=
