@@ -117,6 +117,13 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 
+// bf16 pair of max(lo, 0), max(hi, 0), rounded to nearest even (low half lo).
+__device__ __forceinline__ uint32_t pack_bf16_relu(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;\n" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+
 // Store row `row`'s bf16 values of columns c0 .. c0 + 8 q - 1 (packed pairs w)
 // into h (row-major, ld 256: q 16-byte stores) and, when hT is given, into the
 // transpose (ld ldt: one 2-byte store per column; a warp's 32 consecutive rows
@@ -225,10 +232,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const MlpTcParam
             if (NI > 6) acc = fmaf(w1.z, xin[6], acc);
             if (NI > 7) acc = fmaf(w1.w, xin[7], acc);
           }
-          v[q] = fmaxf(acc, 0.f);
+          v[q] = acc;
         }
-        w[e / 2] = pack_bf16(v[0], v[1]);
-        w[e / 2 + 1] = pack_bf16(v[2], v[3]);
+        w[e / 2] = pack_bf16_relu(v[0], v[1]);
+        w[e / 2 + 1] = pack_bf16_relu(v[2], v[3]);
       }
       if (TRAIN) store_activation<1>(w, row, kc * 8, P.h[0], P.hT[0], P.ldt);
       *reinterpret_cast<uint4*>(As + (r >> 3) * kSbo + kc * kLbo + (r & 7) * 16) =
@@ -276,12 +283,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const MlpTcParam
         for (int j = 0; j < 32; j += 4) {
           const int col = cc * 32 + j;
           const float4 b4 = *reinterpret_cast<const float4*>(bias + col);
-          const float h0 = fmaxf(__uint_as_float(v[j]) + b4.x, 0.f);
-          const float h1 = fmaxf(__uint_as_float(v[j + 1]) + b4.y, 0.f);
-          const float h2 = fmaxf(__uint_as_float(v[j + 2]) + b4.z, 0.f);
-          const float h3 = fmaxf(__uint_as_float(v[j + 3]) + b4.w, 0.f);
-          w[j / 2] = pack_bf16(h0, h1);
-          w[j / 2 + 1] = pack_bf16(h2, h3);
+          w[j / 2] = pack_bf16_relu(__uint_as_float(v[j]) + b4.x, __uint_as_float(v[j + 1]) + b4.y);
+          w[j / 2 + 1] =
+              pack_bf16_relu(__uint_as_float(v[j + 2]) + b4.z, __uint_as_float(v[j + 3]) + b4.w);
           if (last && !TRAIN) {
             const __nv_bfloat162 p01 = *reinterpret_cast<const __nv_bfloat162*>(&w[j / 2]);
             const __nv_bfloat162 p23 = *reinterpret_cast<const __nv_bfloat162*>(&w[j / 2 + 1]);
@@ -360,6 +364,17 @@ __device__ __forceinline__ void bar_expect_tx(uint64_t* bar, uint32_t bytes) {
                : "memory");
 }
 
+// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+// from global to shared memory, completing on the mbarrier.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes,
+                                              uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // One 2D TMA box (64 columns x the map's box rows) at column x, row y.
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
                                             uint64_t* bar) {
@@ -403,8 +418,9 @@ __device__ __forceinline__ void bulk_wait_all() {
 // Per tile of 128 samples:
 //   * input layer -> h_0 (tile A); GEMMs with W_1 .. W_3 -> h_1 .. h_3 (bias,
 //     ReLU); h_0 .. h_2 also written out (row-major) for the weight
-//     gradients, and their ReLU masks kept as bits in registers (thread (row r, half g):
-//     bit k of word q is column 128 g + 32 q + k);
+//     gradients, and their ReLU masks kept as bits in registers (thread
+//     (row r, half g): word q covers columns 128 g + 32 q + [0, 32), bit e
+//     the column 2 e, bit 16 + e the column 2 e + 1);
 //   * output layer on the CUDA cores: y = W_out h_3 + b_out from the two
 //     warpgroups' partial sums, y_hat = y / |y|, the loss term 1 - y_hat . t
 //     and dy = -(t - (y_hat . t) y_hat) / |y| / n; per column c the output
@@ -415,8 +431,10 @@ __device__ __forceinline__ void bulk_wait_all() {
 //     written out, row-major, for the weight gradients);
 //   * per column c the input layer's gradients sum_r dz_0[r][c] x[r][i] and
 //     sum_r dz_0[r][c].
-// The six weight images of a tile are copied into tile B in that order, each
-// as soon as the previous GEMM's MMAs have completed.  Gradient partial sums
+// The six weight images of a tile are copied into tile B in that order (one
+// bulk copy each, completing on an mbarrier), each as soon as the previous
+// GEMM's MMAs have completed; each GEMM's input in tile A is written out by
+// TMA while its MMAs run.  Gradient partial sums
 // stay in registers over the CTA's tiles and are added to global memory once.
 // The values are rounded to bf16 where the layered training step rounds them
 // (activations, backward signals), so the two give the same step up to the
@@ -436,18 +454,19 @@ __device__ __forceinline__ uint32_t sw_chunk(int r, int q) {
   return (uint32_t)((q >> 3) * 16384 + r * 128 + (((q & 7) ^ (r & 7)) << 4));
 }
 
-// Bits of the positive values among 2 nw packed bf16 (bit 2 e: low half of
-// w[e], bit 2 e + 1: high half); a bf16 is positive when its 16 bits, as a
-// signed integer, are.
-__device__ __forceinline__ uint32_t positive_bits(const uint32_t* w, int nw) {
-  uint32_t m = 0;
-#pragma unroll
-  for (int e = 0; e < nw; ++e) {
-    m |= (uint32_t)((short)(w[e] & 0xffffu) > 0) << (2 * e);
-    m |= (uint32_t)((short)(w[e] >> 16) > 0) << (2 * e + 1);
-  }
-  return m;
+// ReLU masks.  A packed pair of non-negative bf16 (ReLU outputs: sign bits
+// clear) has a positive low (high) half iff adding 0x7fff to that half sets
+// its bit 15, with no carry into the other half.  Pair e of a 32-column chunk
+// (columns 2 e, 2 e + 1) is kept as bits e and 16 + e of the chunk's mask;
+// pair_flags(w, e) returns them in place.
+__device__ __forceinline__ uint32_t pair_flags(uint32_t w, int e) {
+  return ((w + 0x7fff7fffu) & 0x80008000u) >> (15 - e);
 }
+// The pair's halves kept where its mask bits are set, zeroed elsewhere.
+__device__ __forceinline__ uint32_t keep_pair(uint32_t p, uint32_t m, int e) {
+  return p & (((m >> e) & 0x10001u) * 0xffffu);
+}
+
 
 // Word q of a 4-word register array without dynamic indexing.
 __device__ __forceinline__ uint32_t word_of(const uint32_t (&m)[4], int q) {
@@ -475,8 +494,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   unsigned char* base = tc_smem + ((1024u - (smem_u32(tc_smem) & 1023u)) & 1023u);
   unsigned char* As = base;
   unsigned char* Bs = base + kABytes;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(Bs + kBBytes);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(Bs + kBBytes);  // MMAs done
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
+  uint64_t* wbar = bar + 2;  // weight image landed in tile B
   float* sW1 = reinterpret_cast<float*>(Bs + kBBytes + 64);  // [kH][kMaxIn]
   float* sb1 = sW1 + kH * kMaxIn;
   float* sbh = sb1 + kH;        // [NG][kH]
@@ -499,6 +519,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(wbar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   for (int e = tid; e < kH * kMaxIn; e += kThreads) {
@@ -515,14 +536,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   const uint32_t tmem_warp = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-  uint32_t parity = 0;
-  bool failed = false;
+  uint32_t parity = 0, wparity = 0;
+  bool failed = false, wpend = false;
   const float inv_n = 1.f / (float)P.n;
-  // the tile's weight schedule: W_1 .. W_NG, then W_NG^T .. W_1^T
+  // the tile's weight schedule: W_1 .. W_NG, then W_NG^T .. W_1^T (every
+  // thread tracks the copy; thread 0 starts it)
   auto fetch = [&](int s) {
-    const unsigned char* src = reinterpret_cast<const unsigned char*>(
-        s < NG ? P.Wimg[s] : P.WimgT[2 * NG - 1 - s]);
-    for (uint32_t c = tid; c < kBBytes / 16; c += kThreads) cp_async16(Bs + 16 * c, src + 16 * c);
+    if (tid == 0) {
+      bar_expect_tx(wbar, kBBytes);
+      bulk_copy_g2s(Bs, s < NG ? P.Wimg[s] : P.WimgT[2 * NG - 1 - s], kBBytes, wbar);
+    }
+    wpend = true;
   };
   if (blockIdx.x < P.n_tiles) fetch(0);
   // step s of the schedule on tiles A and B: wait for its weights, write
@@ -530,13 +554,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   // (bounded) and for the TMA's reads of tile A, start copying the next
   // weights; false on a timed-out wait
   auto gemm_step = [&](int s, bool more_tiles, int64_t tile) -> bool {
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
-    // generic-proxy writes of A and B -> visible to the tensor cores and TMA
+    // generic-proxy writes of A -> visible to the tensor cores and the TMA
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    if (tid == 0) {
+    bool wok = bar_wait(wbar, wparity);  // this GEMM's weights are in tile B
+    if (!wok) wok = bar_wait(wbar, wparity);
+    if (wok) {
+      wparity ^= 1u;
+      wpend = false;
+    }
+    if (tid == 0 && wok) {
       const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
       for (int b = 0; b < 4; ++b) tma_store_2d(&T.out[s], 64 * b, (int)(tile * kRows), As + b * 16384);
       bulk_commit();
@@ -546,8 +575,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                  sdesc(b0 + 2u * k * kLbo, kLbo, kSbo), kIdesc, k > 0 ? 1u : 0u);
       mma_commit(bar);
     }
-    bool ok = bar_wait(bar, parity);
-    if (!ok) ok = bar_wait(bar, parity);  // a second bounded wait before giving up
+    bool ok = wok && bar_wait(bar, parity);
+    if (wok && !ok) ok = bar_wait(bar, parity);  // a second bounded wait before giving up
     if (tid == 0) bulk_wait_read();  // tile A may be rewritten once the TMA has read it
     parity ^= 1u;
     if (__syncthreads_or(!ok)) {
@@ -618,13 +647,14 @@ __global__ void __launch_bounds__(kThreads, 1)
               if (NI > 6) acc = fmaf(w1.z, xin[6], acc);
               if (NI > 7) acc = fmaf(w1.w, xin[7], acc);
             }
-            v[u] = fmaxf(acc, 0.f);
+            v[u] = acc;
           }
-          w[e / 2] = pack_bf16(v[0], v[1]);
-          w[e / 2 + 1] = pack_bf16(v[2], v[3]);
+          w[e / 2] = pack_bf16_relu(v[0], v[1]);
+          w[e / 2 + 1] = pack_bf16_relu(v[2], v[3]);
         }
         *reinterpret_cast<uint4*>(As + sw_chunk(r, kc)) = make_uint4(w[0], w[1], w[2], w[3]);
-        mq |= positive_bits(w, 4) << (8 * kk);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) mq |= pair_flags(w[i], 4 * kk + i);
       }
       set_word(mk[0], q, mq);
     }
@@ -648,10 +678,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int jj = 0; jj < 32; jj += 4) {
           const int col = cc * 32 + jj;
           const float4 b4 = *reinterpret_cast<const float4*>(bias + col);
-          w[jj / 2] = pack_bf16(fmaxf(__uint_as_float(v[jj]) + b4.x, 0.f),
-                                fmaxf(__uint_as_float(v[jj + 1]) + b4.y, 0.f));
-          w[jj / 2 + 1] = pack_bf16(fmaxf(__uint_as_float(v[jj + 2]) + b4.z, 0.f),
-                                    fmaxf(__uint_as_float(v[jj + 3]) + b4.w, 0.f));
+          w[jj / 2] = pack_bf16_relu(__uint_as_float(v[jj]) + b4.x, __uint_as_float(v[jj + 1]) + b4.y);
+          w[jj / 2 + 1] =
+              pack_bf16_relu(__uint_as_float(v[jj + 2]) + b4.z, __uint_as_float(v[jj + 3]) + b4.w);
           if (last) {
             // the output layer reads the bf16-rounded activations
             const __nv_bfloat162 p01 = *reinterpret_cast<const __nv_bfloat162*>(&w[jj / 2]);
@@ -679,7 +708,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int u = 0; u < 4; ++u)
           *reinterpret_cast<uint4*>(As + sw_chunk(r, cc * 4 + u)) =
               make_uint4(w[4 * u], w[4 * u + 1], w[4 * u + 2], w[4 * u + 3]);
-        if (!last) set_word(mk[j + 1], q, positive_bits(w, 16));
+        if (!last) {
+          uint32_t mq = 0;
+#pragma unroll
+          for (int e = 0; e < 16; ++e) mq |= pair_flags(w[e], e);
+          set_word(mk[j + 1], q, mq);
+        }
       }
       after_epilogue();
     }
@@ -786,9 +820,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t mw = word_of(mk[j], q);
         uint32_t w[16];
 #pragma unroll
-        for (int jj = 0; jj < 32; jj += 2)
-          w[jj / 2] = pack_bf16((mw >> jj) & 1u ? __uint_as_float(v[jj]) : 0.f,
-                                (mw >> (jj + 1)) & 1u ? __uint_as_float(v[jj + 1]) : 0.f);
+        for (int e = 0; e < 16; ++e)
+          w[e] = keep_pair(pack_bf16(__uint_as_float(v[2 * e]), __uint_as_float(v[2 * e + 1])), mw, e);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
           *reinterpret_cast<uint4*>(As + sw_chunk(r, cc * 4 + u)) =
@@ -842,9 +875,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   // a timed-out MMA wait: one more bounded wait for those MMAs before the
   // TMEM is given up (the phase that did not complete has parity ^ 1)
-  if (failed && tid == 0) bar_wait(bar, parity ^ 1u);
+  if (failed && tid == 0) {
+    bar_wait(bar, parity ^ 1u);
+    if (wpend) bar_wait(wbar, wparity);  // a weight copy still in flight
+  }
   if (tid == 0) bulk_wait_all();  // every TMA store has completed
-  asm volatile("cp.async.wait_all;\n" ::: "memory");  // no copy outlives the kernel
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -1565,6 +1600,11 @@ cudaError_t mlp_train_tc(const MlpTrainTcParams& p, int sm_count, cudaStream_t s
   if (e != cudaSuccess) return e;
   int64_t grid = p.n_tiles < sm_count ? p.n_tiles : sm_count;
   if (grid < 1) return cudaSuccess;
+  // weight images: one bulk copy each (16-byte aligned)
+  for (int l = 0; l < kMlpTrainGemm; ++l)
+    if (!p.Wimg[l] || !p.WimgT[l] || (uintptr_t)p.Wimg[l] % 16 != 0 ||
+        (uintptr_t)p.WimgT[l] % 16 != 0)
+      return cudaErrorInvalidValue;
   // the inputs of GEMMs 0 .. 5: h_0, h_1, h_2, dz_3, dz_2, dz_1 (row-major
   // [n][256], 16-byte aligned: TMA stores of 64-column boxes)
   const __nv_bfloat16* outs[2 * kMlpTrainGemm] = {p.h[0], p.h[1], p.h[2], p.dz[3], p.dz[2], p.dz[1]};
