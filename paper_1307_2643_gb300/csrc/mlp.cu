@@ -61,13 +61,18 @@ struct crp_mlp {
   std::vector<__nv_bfloat16*> hT;
   __nv_bfloat16 *dzT, *dzT2, *dzT3;
   // the tensor-core training step as a CUDA graph, replayed with the Adam
-  // node's arguments updated; each step's x and t are first copied into the
-  // fixed staging buffers xs, ts the graph reads
+  // node's arguments updated.  With the one-kernel step the kernel's node
+  // gets each step's x and t as arguments (tg_train); otherwise they are
+  // first copied into the fixed staging buffers xs, ts the graph reads
   bool use_graph;
   cudaGraph_t tg_graph;  // the captured graph: its node handles address the exec's nodes
   cudaGraphExec_t tg_exec;
   cudaGraphNode_t tg_adam;
   cudaKernelNodeParams tg_adam_params;
+  cudaGraphNode_t tg_train;  // the one-kernel step's node, or null
+  cudaKernelNodeParams tg_train_params;
+  MlpTrainTcParams tg_train_args;
+  TrainStoreMaps tg_train_maps;
   int64_t tg_n;
   cudaStream_t tg_stream;  // private stream the graph is captured on
   float *xs, *ts;
@@ -664,35 +669,73 @@ struct Bf16Jobs {
   __nv_bfloat16* imgT[16];
 };
 
+// Adam step of one parameter (FP32, bias-corrected moments).
+__device__ __forceinline__ float adam_one(float* p, const float* g, float* m, float* v, int64_t i,
+                                          float lr, float b1, float b2, float eps, float c1,
+                                          float c2) {
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  p[i] = pi;
+  return pi;
+}
+
+constexpr int kAdamTile = 32;       // hidden weights: 32 x 32 tiles, one per block
+constexpr int kAdamRest = 64;       // blocks for the other parameters
+int adam_blocks(int nj, int hn) { return nj * (hn / kAdamTile) * (hn / kAdamTile) + kAdamRest; }
+
 // Adam step of every parameter; a parameter of a hidden weight matrix
-// (nj jobs, hn x hn each) also goes to that layer's bf16 copies and images,
-// so no separate conversion pass follows the step.
-__global__ void k_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1,
-                       float b2, float eps, float c1, float c2, const Bf16Jobs jobs, int nj,
-                       int hn) {
-  const int64_t nn = (int64_t)hn * hn;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-    p[i] = pi;
-    for (int j = 0; j < nj; ++j) {
-      const int64_t e = (p + i) - jobs.W[j];
-      if (e < 0 || e >= nn) continue;
-      const int ei = (int)e;  // < hn * hn: 32-bit division
-      const int o = ei / hn, ii = ei - o * hn;
+// (nj jobs, hn x hn each, hn a multiple of 32) also goes to that layer's bf16
+// copies and images, so no separate conversion pass follows the step.  The
+// first nj (hn / 32)^2 blocks (256 threads) each take a 32 x 32 tile of one
+// matrix: coalesced updates and row-major copies, then the transposed copies
+// from the tile staged in shared memory; the last kAdamRest blocks take
+// every other parameter.
+__global__ void __launch_bounds__(256)
+    k_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2,
+           float eps, float c1, float c2, const Bf16Jobs jobs, int nj, int hn) {
+  const int tpr = hn / kAdamTile;  // tiles per row of a matrix
+  const int tiles = nj * tpr * tpr;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  if ((int)blockIdx.x < tiles) {
+    __shared__ __nv_bfloat16 tile[kAdamTile][kAdamTile + 2];
+    const int j = blockIdx.x / (tpr * tpr), tb = blockIdx.x % (tpr * tpr);
+    const int o0 = (tb / tpr) * kAdamTile, i0 = (tb % tpr) * kAdamTile;
+    const int64_t base = jobs.W[j] - p;
+    __nv_bfloat16 *wb = jobs.wb[j], *wbt = jobs.wbt[j], *img = jobs.img[j], *imgT = jobs.imgT[j];
+#pragma unroll
+    for (int k = 0; k < kAdamTile / 8; ++k) {
+      const int o = o0 + ty + 8 * k, ii = i0 + tx;
+      const int64_t e = (int64_t)o * hn + ii;
+      const float pi = adam_one(p, g, m, v, base + e, lr, b1, b2, eps, c1, c2);
       const __nv_bfloat16 bv = __float2bfloat16_rn(pi);
-      jobs.wb[j][e] = bv;
-      jobs.wbt[j][(int64_t)ii * hn + o] = bv;
-      if (jobs.img[j])
-        jobs.img[j][(int64_t)(o >> 3) * (8 * hn) + (ii >> 3) * 64 + (o & 7) * 8 + (ii & 7)] = bv;
-      if (jobs.imgT[j])
-        jobs.imgT[j][(int64_t)(ii >> 3) * (8 * hn) + (o >> 3) * 64 + (ii & 7) * 8 + (o & 7)] = bv;
+      wb[e] = bv;
+      if (img) img[(int64_t)(o >> 3) * (8 * hn) + (ii >> 3) * 64 + (o & 7) * 8 + (ii & 7)] = bv;
+      tile[ty + 8 * k][tx] = bv;
     }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kAdamTile / 8; ++k) {
+      // element (o, ii) = (o0 + tx, i0 + ty + 8 k): consecutive lanes, consecutive o
+      const int o = o0 + tx, ii = i0 + ty + 8 * k;
+      const __nv_bfloat16 bv = tile[tx][ty + 8 * k];
+      wbt[(int64_t)ii * hn + o] = bv;
+      if (imgT) imgT[(int64_t)(ii >> 3) * (8 * hn) + (o >> 3) * 64 + (ii & 7) * 8 + (o & 7)] = bv;
+    }
+    return;
+  }
+  const int64_t nn = (int64_t)hn * hn;
+  const int64_t stride = (int64_t)(gridDim.x - tiles) * blockDim.x;
+  for (int64_t i = (int64_t)(blockIdx.x - tiles) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    bool in_job = false;
+    for (int jj = 0; jj < nj; ++jj) {
+      const int64_t e = (p + i) - jobs.W[jj];
+      in_job = in_job || (e >= 0 && e < nn);
+    }
+    if (!in_job) adam_one(p, g, m, v, i, lr, b1, b2, eps, c1, c2);
   }
 }
 
@@ -770,6 +813,7 @@ void drop_graph(crp_mlp* M) {
   M->tg_exec = nullptr;
   M->tg_graph = nullptr;
   M->tg_adam = nullptr;
+  M->tg_train = nullptr;
   M->tg_n = 0;
 }
 
@@ -1215,16 +1259,18 @@ void capture_train_graph(crp_mlp* M, int64_t n) {
   if (st == CRP_OK) {
     Bf16Jobs jobs;
     const int nj = bf16_jobs(M, &jobs);
-    k_adam<<<nblk(M->n_params, 256), 256, 0, cs>>>(M->params, M->grad, M->m, M->v, M->n_params,
-                                                   0.f, 0.9f, 0.999f, 1e-8f, 1.f, 1.f, jobs, nj,
-                                                   M->hidden);
+    k_adam<<<adam_blocks(nj, M->hidden), 256, 0, cs>>>(M->params, M->grad, M->m, M->v,
+                                                       M->n_params, 0.f, 0.9f, 0.999f, 1e-8f, 1.f,
+                                                       1.f, jobs, nj, M->hidden);
     if (cudaGetLastError() != cudaSuccess) st = CRP_E_CUDA;
   }
   cudaGraph_t g = nullptr;
   const cudaError_t ec = cudaStreamEndCapture(cs, &g);
-  cudaGraphNode_t adam = nullptr;
-  cudaKernelNodeParams ap;
+  cudaGraphNode_t adam = nullptr, train = nullptr;
+  cudaKernelNodeParams ap, tp;
   memset(&ap, 0, sizeof(ap));
+  memset(&tp, 0, sizeof(tp));
+  const void* train_fn = train_fused_ok(M) ? mlp_train_tc_kernel(M->n_in) : nullptr;
   if (st == CRP_OK && ec == cudaSuccess && g) {
     size_t count = 0;
     cudaGraphGetNodes(g, nullptr, &count);
@@ -1234,10 +1280,16 @@ void capture_train_graph(crp_mlp* M, int64_t n) {
         cudaGraphNodeType ty;
         if (cudaGraphNodeGetType(nd, &ty) != cudaSuccess || ty != cudaGraphNodeTypeKernel) continue;
         cudaKernelNodeParams p;
-        if (cudaGraphKernelNodeGetParams(nd, &p) == cudaSuccess &&
-            p.func == reinterpret_cast<void*>(k_adam)) {
+        if (cudaGraphKernelNodeGetParams(nd, &p) != cudaSuccess) continue;
+        if (p.func == reinterpret_cast<void*>(k_adam)) {
           adam = nd;
           ap = p;
+        } else if (train_fn && p.func == train_fn && p.kernelParams) {
+          // the launch's arguments, kept to be re-sent with each step's x, t
+          train = nd;
+          tp = p;
+          memcpy(&M->tg_train_args, p.kernelParams[0], sizeof(MlpTrainTcParams));
+          memcpy(&M->tg_train_maps, p.kernelParams[1], sizeof(TrainStoreMaps));
         }
       }
     }
@@ -1248,6 +1300,8 @@ void capture_train_graph(crp_mlp* M, int64_t n) {
       M->tg_exec = ex;
       M->tg_adam = adam;
       M->tg_adam_params = ap;
+      M->tg_train = train;
+      M->tg_train_params = tp;
       M->tg_n = n;
     }
   }
@@ -1288,6 +1342,10 @@ crp_status crp_mlp_create(crp_context* ctx, int32_t n_in, int32_t hidden, int32_
   M->tg_exec = nullptr;
   M->tg_adam = nullptr;
   memset(&M->tg_adam_params, 0, sizeof(M->tg_adam_params));
+  M->tg_train = nullptr;
+  memset(&M->tg_train_params, 0, sizeof(M->tg_train_params));
+  memset(&M->tg_train_args, 0, sizeof(M->tg_train_args));
+  memset(&M->tg_train_maps, 0, sizeof(M->tg_train_maps));
   M->tg_n = 0;
   M->tg_stream = nullptr;
   M->xs = M->ts = nullptr;
@@ -1524,10 +1582,23 @@ crp_status crp_mlp_train_step(crp_mlp* M, const float* x, const float* t, int64_
   if (st != CRP_OK) return st;
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   if (graph && M->tg_exec && M->tg_n == n) {
-    cudaError_t e = cudaMemcpyAsync(M->xs, x, sizeof(float) * (size_t)n * M->n_in,
-                                    cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(M->ts, t, sizeof(float) * (size_t)n * 3, cudaMemcpyDeviceToDevice, s);
+    cudaError_t e = cudaSuccess;
+    MlpTrainTcParams tpar = M->tg_train_args;
+    if (M->tg_train) {
+      // the one-kernel step reads this step's x and t where they are
+      tpar.x = x;
+      tpar.t = t;
+      void* targs[] = {&tpar, &M->tg_train_maps};
+      cudaKernelNodeParams kp = M->tg_train_params;
+      kp.kernelParams = targs;
+      kp.extra = nullptr;
+      e = cudaGraphExecKernelNodeSetParams(M->tg_exec, M->tg_train, &kp);
+    } else {
+      e = cudaMemcpyAsync(M->xs, x, sizeof(float) * (size_t)n * M->n_in, cudaMemcpyDeviceToDevice,
+                          s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(M->ts, t, sizeof(float) * (size_t)n * 3, cudaMemcpyDeviceToDevice, s);
+    }
     M->step += 1;
     float c1 = 1.f - powf(b1, (float)M->step), c2 = 1.f - powf(b2, (float)M->step);
     float lr_ = lr;
@@ -1549,8 +1620,9 @@ crp_status crp_mlp_train_step(crp_mlp* M, const float* x, const float* t, int64_
       const float c1 = 1.f - powf(b1, (float)M->step), c2 = 1.f - powf(b2, (float)M->step);
       Bf16Jobs jobs;
       const int nj = bf16_jobs(M, &jobs);
-      k_adam<<<nblk(M->n_params, 256), 256, 0, s>>>(M->params, M->grad, M->m, M->v, M->n_params,
-                                                    lr, b1, b2, eps, c1, c2, jobs, nj, M->hidden);
+      k_adam<<<adam_blocks(nj, M->hidden), 256, 0, s>>>(M->params, M->grad, M->m, M->v,
+                                                         M->n_params, lr, b1, b2, eps, c1, c2, jobs,
+                                                         nj, M->hidden);
       const cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) st = fail_cuda(e, "crp_mlp_train_step: Adam");
     }

@@ -444,6 +444,7 @@ constexpr size_t kTrainFloats = kH * kMaxIn + kH + kMlpTrainGemm * kH + 3 * kH +
                                 3 * kRows + kRows + kRows * kMaxIn;
 constexpr size_t kTrainSmem = 1024 + kABytes + kBBytes + 64 + kTrainFloats * 4;
 static_assert(kTrainSmem <= 232448, "shared memory of the training kernel");
+static_assert(kH == kThreads && (kH * kMaxIn) % kThreads == 0, "parameter staging of the training kernel");
 
 // Byte offset of the 16-byte chunk q (columns 8 q .. 8 q + 7) of row r in the
 // training kernel's tile A: 128 rows x 256 bf16 columns, 128-byte-swizzled
@@ -454,13 +455,13 @@ __device__ __forceinline__ uint32_t sw_chunk(int r, int q) {
   return (uint32_t)((q >> 3) * 16384 + r * 128 + (((q & 7) ^ (r & 7)) << 4));
 }
 
-// ReLU masks.  A packed pair of non-negative bf16 (ReLU outputs: sign bits
-// clear) has a positive low (high) half iff adding 0x7fff to that half sets
-// its bit 15, with no carry into the other half.  Pair e of a 32-column chunk
-// (columns 2 e, 2 e + 1) is kept as bits e and 16 + e of the chunk's mask;
-// pair_flags(w, e) returns them in place.
+// ReLU masks.  A half of a packed pair of ReLU outputs (bf16, +0, -0 or
+// positive) is positive iff adding 0x7fff to it sets its bit 15 while its
+// own bit 15 is clear; no such half carries into the other.  Pair e of a
+// 32-column chunk (columns 2 e, 2 e + 1) is kept as bits e and 16 + e of the
+// chunk's mask; pair_flags(w, e) returns them in place.
 __device__ __forceinline__ uint32_t pair_flags(uint32_t w, int e) {
-  return ((w + 0x7fff7fffu) & 0x80008000u) >> (15 - e);
+  return ((w + 0x7fff7fffu) & ~w & 0x80008000u) >> (15 - e);
 }
 // The pair's halves kept where its mask bits are set, zeroed elsewhere.
 __device__ __forceinline__ uint32_t keep_pair(uint32_t p, uint32_t m, int e) {
@@ -478,13 +479,6 @@ __device__ __forceinline__ void set_word(uint32_t (&m)[4], int q, uint32_t v) {
   m[2] = q == 2 ? v : m[2];
   m[3] = q == 3 ? v : m[3];
 }
-
-// Tensor maps of the row-major [n][256] outputs h_0 .. h_2 and dz_1 .. dz_3
-// (boxes of 64 columns x 128 rows, 128-byte swizzle), in the order of the
-// GEMMs that read them: store s holds the input of GEMM s.
-struct TrainStoreMaps {
-  CUtensorMap out[2 * kMlpTrainGemm];
-};
 
 template <int NIN>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -509,6 +503,19 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int tid = threadIdx.x, warp = tid >> 5;
   const int r = tid & (kRows - 1);  // row of the tile this thread owns
   const int g = tid >> 7;           // warpgroup: columns [128 g, 128 g + 128)
+  constexpr int NI = NIN > 0 ? NIN : kMaxIn;  // inputs summed (zero-padded when NIN = 0)
+  // row r's inputs of a tile, loaded one tile ahead (the first before the
+  // parameters are staged)
+  float xnext[kMaxIn];
+  auto load_x = [&](int64_t tile) {
+    const int64_t row = tile * kRows + r;
+#pragma unroll
+    for (int i = 0; i < kMaxIn; ++i)
+      xnext[i] = tile < P.n_tiles && (NIN > 0 ? i < NIN : i < P.n_in)
+                     ? P.x[row * (NIN > 0 ? NIN : P.n_in) + i]
+                     : 0.f;
+  };
+  load_x(blockIdx.x);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
@@ -521,23 +528,44 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(wbar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    // the first GEMM's weights, copied while the small parameters are staged
+    if (blockIdx.x < P.n_tiles) {
+      bar_expect_tx(wbar, kBBytes);
+      bulk_copy_g2s(Bs, P.Wimg[0], kBBytes, wbar);
+    }
   }
-  for (int e = tid; e < kH * kMaxIn; e += kThreads) {
-    const int o = e / kMaxIn, i = e % kMaxIn;
-    sW1[e] = i < P.n_in ? P.W1[o * P.n_in + i] : 0.f;
+  {
+    // the small parameters: every load in flight before the first store
+    // (kH = kThreads: one value of each kH-vector per thread)
+    constexpr int kW1 = kH * kMaxIn / kThreads;
+    float w1v[kW1], bhv[NG], wov[3];
+#pragma unroll
+    for (int k = 0; k < kW1; ++k) {
+      const int e = tid + k * kThreads, o = e / kMaxIn, i = e % kMaxIn;
+      w1v[k] = i < P.n_in ? P.W1[o * P.n_in + i] : 0.f;
+    }
+    const float b1v = P.b1[tid];
+#pragma unroll
+    for (int l = 0; l < NG; ++l) bhv[l] = P.bh[l][tid];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) wov[k] = P.Wout[tid + k * kThreads];
+    const float bov = tid < 3 ? P.bout[tid] : 0.f;
+#pragma unroll
+    for (int k = 0; k < kW1; ++k) sW1[tid + k * kThreads] = w1v[k];
+    sb1[tid] = b1v;
+#pragma unroll
+    for (int l = 0; l < NG; ++l) sbh[l * kH + tid] = bhv[l];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) sWo[tid + k * kThreads] = wov[k];
+    if (tid < 3) sbo[tid] = bov;
   }
-  for (int e = tid; e < kH; e += kThreads) sb1[e] = P.b1[e];
-  for (int l = 0; l < NG; ++l)
-    for (int e = tid; e < kH; e += kThreads) sbh[l * kH + e] = P.bh[l][e];
-  for (int e = tid; e < 3 * kH; e += kThreads) sWo[e] = P.Wout[e];
-  if (tid < 3) sbo[tid] = P.bout[tid];
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   const uint32_t tmem_warp = tmem + ((uint32_t)((warp & 3) * 32) << 16);
   uint32_t parity = 0, wparity = 0;
-  bool failed = false, wpend = false;
+  bool failed = false, wpend = blockIdx.x < P.n_tiles;  // the first copy, started above
   const float inv_n = 1.f / (float)P.n;
   // the tile's weight schedule: W_1 .. W_NG, then W_NG^T .. W_1^T (every
   // thread tracks the copy; thread 0 starts it)
@@ -548,7 +576,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     wpend = true;
   };
-  if (blockIdx.x < P.n_tiles) fetch(0);
   // step s of the schedule on tiles A and B: wait for its weights, write
   // tile A (the GEMM's input) out by TMA, 16 MMAs, wait for their completion
   // (bounded) and for the TMA's reads of tile A, start copying the next
@@ -607,13 +634,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   for (int64_t tile = blockIdx.x; tile < P.n_tiles && !failed; tile += gridDim.x) {
     const int64_t row = tile * kRows + r;
     const bool more = tile + gridDim.x < P.n_tiles;
+    // the targets, first needed after the forward pass
+    const float t0 = P.t[row * 3], t1 = P.t[row * 3 + 1], t2 = P.t[row * 3 + 2];
     uint32_t mk[NG][4];  // ReLU masks of h_0 .. h_{NG-1}
     // ---- input layer (FP32): this warpgroup's 128 outputs of row r ----
-    constexpr int NI = NIN > 0 ? NIN : kMaxIn;
     float xin[kMaxIn];
 #pragma unroll
-    for (int i = 0; i < kMaxIn; ++i)
-      xin[i] = (NIN > 0 ? i < NIN : i < P.n_in) ? P.x[row * (NIN > 0 ? NIN : P.n_in) + i] : 0.f;
+    for (int i = 0; i < kMaxIn; ++i) xin[i] = xnext[i];
+    load_x(tile + gridDim.x);
     if (g == 0) {
 #pragma unroll
       for (int i = 0; i < kMaxIn; ++i) sx[r * kMaxIn + i] = xin[i];
@@ -621,7 +649,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll 1
     for (int q = 0; q < 4; ++q) {
       uint32_t mq = 0;
-#pragma unroll 2
+#pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
         const int kc = 16 * g + 4 * q + kk;
         uint32_t w[4];
@@ -730,7 +758,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     const float nrm = sqrtf(Y0 * Y0 + Y1 * Y1 + Y2 * Y2);
     const float inv = nrm > 0.f ? 1.f / nrm : 0.f;
     const float yh0 = Y0 * inv, yh1 = Y1 * inv, yh2 = Y2 * inv;
-    const float t0 = P.t[row * 3], t1 = P.t[row * 3 + 1], t2 = P.t[row * 3 + 2];
     const float d = yh0 * t0 + yh1 * t1 + yh2 * t2;
     const float dy0 = -(t0 - d * yh0) * inv * inv_n;
     const float dy1 = -(t1 - d * yh1) * inv * inv_n;
@@ -761,21 +788,25 @@ __global__ void __launch_bounds__(kThreads, 1)
       // (a warp reads 64 bytes of one row: four chunks in distinct banks)
       const unsigned char* cb = As + (tid >> 6) * 16384 + (tid & 7) * 2;
       const int qc = (tid >> 3) & 7;
-      // two partial sums per output (even and odd rows) halve the FMA chains
+      // two partial sums per output (even and odd rows) halve the FMA chains;
+      // dy of four rows per 16-byte load
       float a0 = 0.f, a1 = 0.f, a2 = 0.f, b0 = 0.f, b1 = 0.f, b2 = 0.f;
-#pragma unroll 4
-      for (int rr = 0; rr < kRows; rr += 2) {
-        const int R = rr, R2 = rr + 1;
-        const float hv = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(
-            cb + R * 128 + ((qc ^ (R & 7)) << 4)));
-        const float hw = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(
-            cb + R2 * 128 + ((qc ^ (R2 & 7)) << 4)));
-        a0 = fmaf(sdy[R], hv, a0);
-        a1 = fmaf(sdy[kRows + R], hv, a1);
-        a2 = fmaf(sdy[2 * kRows + R], hv, a2);
-        b0 = fmaf(sdy[R2], hw, b0);
-        b1 = fmaf(sdy[kRows + R2], hw, b1);
-        b2 = fmaf(sdy[2 * kRows + R2], hw, b2);
+#pragma unroll 2
+      for (int rr = 0; rr < kRows; rr += 4) {
+        float hv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          hv[i] = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(
+              cb + (rr + i) * 128 + ((qc ^ ((rr + i) & 7)) << 4)));
+        const float4 d0 = *reinterpret_cast<const float4*>(sdy + rr);
+        const float4 d1 = *reinterpret_cast<const float4*>(sdy + kRows + rr);
+        const float4 d2 = *reinterpret_cast<const float4*>(sdy + 2 * kRows + rr);
+        a0 = fmaf(d0.z, hv[2], fmaf(d0.x, hv[0], a0));
+        a1 = fmaf(d1.z, hv[2], fmaf(d1.x, hv[0], a1));
+        a2 = fmaf(d2.z, hv[2], fmaf(d2.x, hv[0], a2));
+        b0 = fmaf(d0.w, hv[3], fmaf(d0.y, hv[1], b0));
+        b1 = fmaf(d1.w, hv[3], fmaf(d1.y, hv[1], b1));
+        b2 = fmaf(d2.w, hv[3], fmaf(d2.y, hv[1], b2));
       }
       go0 += a0 + b0;
       go1 += a1 + b1;
@@ -794,13 +825,18 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint4 hq = *ap;
         const uint32_t hw[4] = {hq.x, hq.y, hq.z, hq.w};
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
+        for (int e = 0; e < 4; e += 2) {
+          // W_out of four columns per 16-byte load
           const int c0 = (cc * 4 + u) * 8 + 2 * e;
-          const float z0 = fmaf(dy2, sWo[2 * kH + c0], fmaf(dy1, sWo[kH + c0], dy0 * sWo[c0]));
-          const float z1 =
-              fmaf(dy2, sWo[2 * kH + c0 + 1], fmaf(dy1, sWo[kH + c0 + 1], dy0 * sWo[c0 + 1]));
-          w[4 * u + e] = pack_bf16((short)(hw[e] & 0xffffu) > 0 ? z0 : 0.f,
-                                   (short)(hw[e] >> 16) > 0 ? z1 : 0.f);
+          const float4 wa = *reinterpret_cast<const float4*>(sWo + c0);
+          const float4 wb = *reinterpret_cast<const float4*>(sWo + kH + c0);
+          const float4 wc = *reinterpret_cast<const float4*>(sWo + 2 * kH + c0);
+          const float z0 = fmaf(dy2, wc.x, fmaf(dy1, wb.x, dy0 * wa.x));
+          const float z1 = fmaf(dy2, wc.y, fmaf(dy1, wb.y, dy0 * wa.y));
+          const float z2 = fmaf(dy2, wc.z, fmaf(dy1, wb.z, dy0 * wa.z));
+          const float z3 = fmaf(dy2, wc.w, fmaf(dy1, wb.w, dy0 * wa.w));
+          w[4 * u + e] = keep_pair(pack_bf16(z0, z1), pair_flags(hw[e], 0), 0);
+          w[4 * u + e + 1] = keep_pair(pack_bf16(z2, z3), pair_flags(hw[e + 1], 0), 0);
         }
         *ap = make_uint4(w[4 * u], w[4 * u + 1], w[4 * u + 2], w[4 * u + 3]);
       }
@@ -847,10 +883,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             cb + R2 * 128 + ((qc ^ (R2 & 7)) << 4)));
         ab += z;
         bb += z2;
+        // the rows' inputs by 16-byte loads
+        float xr[kMaxIn], xr2[kMaxIn];
+#pragma unroll
+        for (int i = 0; i < NI; i += 4) {
+          const float4 p = *reinterpret_cast<const float4*>(sx + R * kMaxIn + i);
+          const float4 p2 = *reinterpret_cast<const float4*>(sx + R2 * kMaxIn + i);
+          xr[i] = p.x, xr[i + 1] = p.y, xr[i + 2] = p.z, xr[i + 3] = p.w;
+          xr2[i] = p2.x, xr2[i + 1] = p2.y, xr2[i + 2] = p2.z, xr2[i + 3] = p2.w;
+        }
 #pragma unroll
         for (int i = 0; i < NI; ++i) {
-          aw[i] = fmaf(z, sx[R * kMaxIn + i], aw[i]);
-          bw[i] = fmaf(z2, sx[R2 * kMaxIn + i], bw[i]);
+          aw[i] = fmaf(z, xr[i], aw[i]);
+          bw[i] = fmaf(z2, xr2[i], bw[i]);
         }
       }
 #pragma unroll
@@ -1591,6 +1636,11 @@ cudaError_t mlp_forward_tc(const MlpTcParams& p, int sm_count, cudaStream_t s) {
 
 cudaError_t mlp_forward_tc_train(const MlpTcParams& p, int sm_count, cudaStream_t s) {
   return launch_forward_tc<true>(p, sm_count, s);
+}
+
+const void* mlp_train_tc_kernel(int n_in) {
+  return n_in == 4 ? reinterpret_cast<const void*>(k_mlp_train_tc<4>)
+                   : reinterpret_cast<const void*>(k_mlp_train_tc<0>);
 }
 
 cudaError_t mlp_train_tc(const MlpTrainTcParams& p, int sm_count, cudaStream_t s) {

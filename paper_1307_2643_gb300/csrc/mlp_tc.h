@@ -2,6 +2,7 @@
 // forward pass and the GEMMs of the training step.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -112,6 +113,15 @@ struct MlpTrainTcParams {
   unsigned* err;  // set to 1 when a tensor-core wait timed out
 };
 cudaError_t mlp_train_tc(const MlpTrainTcParams& p, int sm_count, cudaStream_t s);
+// The kernel's second argument: tensor maps of the row-major [n][256] outputs
+// h_0 .. h_2 and dz_1 .. dz_3 (boxes of 64 columns x 128 rows, 128-byte
+// swizzle) in the order of the GEMMs that read them (store s holds the input
+// of GEMM s).  A captured launch has the arguments (MlpTrainTcParams,
+// TrainStoreMaps); the kernel's address identifies its graph node.
+struct TrainStoreMaps {
+  CUtensorMap out[2 * kMlpTrainGemm];
+};
+const void* mlp_train_tc_kernel(int n_in);
 
 // Element count of one hidden layer's weight image (256 x 256).
 size_t mlp_tc_weight_image_elems();
