@@ -669,48 +669,59 @@ struct Bf16Jobs {
   __nv_bfloat16* imgT[16];
 };
 
-// Adam step of one parameter (FP32, bias-corrected moments).
-__device__ __forceinline__ float adam_one(float* p, const float* g, float* m, float* v, int64_t i,
-                                          float lr, float b1, float b2, float eps, float c1,
-                                          float c2) {
-  const float gi = g[i];
-  const float mi = b1 * m[i] + (1.f - b1) * gi;
-  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-  m[i] = mi;
-  v[i] = vi;
-  const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-  p[i] = pi;
-  return pi;
+// Adam step of one parameter (FP32, bias-corrected moments) from its
+// gradient gi and moments mi, vi; returns the new parameter.
+__device__ __forceinline__ float adam_one(float pi, float gi, float& mi, float& vi, float lr,
+                                          float b1, float b2, float eps, float c1, float c2) {
+  mi = b1 * mi + (1.f - b1) * gi;
+  vi = b2 * vi + (1.f - b2) * gi * gi;
+  return pi - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
-constexpr int kAdamTile = 32;       // hidden weights: 32 x 32 tiles, one per block
-constexpr int kAdamRest = 64;       // blocks for the other parameters
+constexpr int kAdamTile = 32;  // hidden weights: 32 x 32 tiles, one per block
+constexpr int kAdamRest = 64;  // blocks for the other parameters
 int adam_blocks(int nj, int hn) { return nj * (hn / kAdamTile) * (hn / kAdamTile) + kAdamRest; }
 
 // Adam step of every parameter; a parameter of a hidden weight matrix
-// (nj jobs, hn x hn each, hn a multiple of 32) also goes to that layer's bf16
-// copies and images, so no separate conversion pass follows the step.  The
-// first nj (hn / 32)^2 blocks (256 threads) each take a 32 x 32 tile of one
-// matrix: coalesced updates and row-major copies, then the transposed copies
-// from the tile staged in shared memory; the last kAdamRest blocks take
-// every other parameter.
+// (nj jobs, hn x hn each, hn a multiple of 32, in ascending address order)
+// also goes to that layer's bf16 copies and images, so no separate
+// conversion pass follows the step.  The first nj (hn / 32)^2 blocks (256
+// threads) each take a 32 x 32 tile of one matrix: all loads first, then
+// coalesced updates and row-major copies, then the transposed copies from
+// the tile staged in shared memory; the last kAdamRest blocks take the other
+// parameters (the ranges between the matrices).
 __global__ void __launch_bounds__(256)
-    k_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2,
-           float eps, float c1, float c2, const Bf16Jobs jobs, int nj, int hn) {
+    k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+           float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float c1,
+           float c2, const Bf16Jobs jobs, int nj, int hn) {
   const int tpr = hn / kAdamTile;  // tiles per row of a matrix
   const int tiles = nj * tpr * tpr;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t nn = (int64_t)hn * hn;
   if ((int)blockIdx.x < tiles) {
+    constexpr int R = kAdamTile / 8;  // rows of the tile per thread
     __shared__ __nv_bfloat16 tile[kAdamTile][kAdamTile + 2];
     const int j = blockIdx.x / (tpr * tpr), tb = blockIdx.x % (tpr * tpr);
     const int o0 = (tb / tpr) * kAdamTile, i0 = (tb % tpr) * kAdamTile;
     const int64_t base = jobs.W[j] - p;
     __nv_bfloat16 *wb = jobs.wb[j], *wbt = jobs.wbt[j], *img = jobs.img[j], *imgT = jobs.imgT[j];
+    float pv[R], gv[R], mv[R], vv[R];
 #pragma unroll
-    for (int k = 0; k < kAdamTile / 8; ++k) {
+    for (int k = 0; k < R; ++k) {
+      const int64_t i = base + (int64_t)(o0 + ty + 8 * k) * hn + i0 + tx;
+      pv[k] = p[i];
+      gv[k] = g[i];
+      mv[k] = m[i];
+      vv[k] = v[i];
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
       const int o = o0 + ty + 8 * k, ii = i0 + tx;
       const int64_t e = (int64_t)o * hn + ii;
-      const float pi = adam_one(p, g, m, v, base + e, lr, b1, b2, eps, c1, c2);
+      const float pi = adam_one(pv[k], gv[k], mv[k], vv[k], lr, b1, b2, eps, c1, c2);
+      p[base + e] = pi;
+      m[base + e] = mv[k];
+      v[base + e] = vv[k];
       const __nv_bfloat16 bv = __float2bfloat16_rn(pi);
       wb[e] = bv;
       if (img) img[(int64_t)(o >> 3) * (8 * hn) + (ii >> 3) * 64 + (o & 7) * 8 + (ii & 7)] = bv;
@@ -718,7 +729,7 @@ __global__ void __launch_bounds__(256)
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < kAdamTile / 8; ++k) {
+    for (int k = 0; k < R; ++k) {
       // element (o, ii) = (o0 + tx, i0 + ty + 8 k): consecutive lanes, consecutive o
       const int o = o0 + tx, ii = i0 + ty + 8 * k;
       const __nv_bfloat16 bv = tile[tx][ty + 8 * k];
@@ -727,15 +738,19 @@ __global__ void __launch_bounds__(256)
     }
     return;
   }
-  const int64_t nn = (int64_t)hn * hn;
+  // parameter c of the ones outside the matrices -> its index (the matrices
+  // are skipped in ascending order)
+  const int64_t nrest = n - (int64_t)nj * nn;
   const int64_t stride = (int64_t)(gridDim.x - tiles) * blockDim.x;
-  for (int64_t i = (int64_t)(blockIdx.x - tiles) * blockDim.x + threadIdx.x; i < n; i += stride) {
-    bool in_job = false;
-    for (int jj = 0; jj < nj; ++jj) {
-      const int64_t e = (p + i) - jobs.W[jj];
-      in_job = in_job || (e >= 0 && e < nn);
-    }
-    if (!in_job) adam_one(p, g, m, v, i, lr, b1, b2, eps, c1, c2);
+  for (int64_t c = (int64_t)(blockIdx.x - tiles) * blockDim.x + threadIdx.x; c < nrest;
+       c += stride) {
+    int64_t i = c;
+    for (int jj = 0; jj < nj; ++jj)
+      if (i >= jobs.W[jj] - p) i += nn;
+    float mi = m[i], vi = v[i];
+    p[i] = adam_one(p[i], g[i], mi, vi, lr, b1, b2, eps, c1, c2);
+    m[i] = mi;
+    v[i] = vi;
   }
 }
 
