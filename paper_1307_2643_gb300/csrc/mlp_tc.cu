@@ -1227,20 +1227,25 @@ __global__ void __launch_bounds__(kThreads, 1)
 // the same B chunk).  The K range streams through three shared-memory stages
 // of 64 rows (A and B 64 x 256 bf16 each, 64 KB a stage) as TMA boxes of 64
 // rows x 64 columns with the 128-byte swizzle, which the MMAs read as
-// MN-major operands (the 256 columns contiguous, K the row): one thread starts
-// the copies two chunks ahead, issues a chunk's 8 MMAs as soon as it has
-// landed and commits them to the stage's "freed" barrier, which the refill of
-// that stage waits for; meanwhile every thread adds eight columns of eight of
-// the chunk's A rows to its column sums.  The epilogue stages each half as
-// FP32 boxes and adds it to C with TMA reduce-add.
+// MN-major operands (the 256 columns contiguous, K the row).  The roles run
+// independently, synchronised per stage by mbarriers only: one thread of
+// warp 0 starts a stage's copies once its previous chunk's MMAs are done and
+// its columns summed; one thread of warp 1 issues a chunk's 8 MMAs once it has
+// landed and commits them to the stage's "MMAs done" barrier; warps 4..7 add
+// the chunk's A columns to their column sums and arrive on its "summed"
+// barrier.  After the item's last MMAs every warp takes part in the
+// epilogue, which stages the FP32 output in the freed stages and adds it to C
+// with TMA reduce-add, each CTA starting at a different box (the CTAs of a
+// problem reduce into the same lines).
 // ---------------------------------------------------------------------------
 constexpr int kGemmBatch = 3;  // problems of one launch
 constexpr int kWgStages = 3;
+constexpr int kWgSumWarps = 4;  // column-sum warps: the last four
 constexpr uint32_t kWgBox = 64 * 128;  // 64 rows x 64 bf16 columns: 8 KB
 constexpr uint32_t kWgA = 4 * kWgBox;  // 64 rows x 256 columns: 32 KB
 constexpr uint32_t kWgStage = 2 * kWgA;
-constexpr size_t kWgSmem =
-    1024 + kWgStages * kWgStage + 8 * kH * sizeof(float) + 2 * kWgStages * 8 + 16;
+constexpr size_t kWgSmem = 1024 + kWgStages * kWgStage + kWgSumWarps * kH * sizeof(float) +
+                           (3 * kWgStages + 1) * 8 + 16;
 constexpr uint32_t kWgTmemCols = 512;
 // kind::f16 instruction descriptor as kIdesc with both operands MN-major
 // (bits 15 and 16: A and B transposed)
@@ -1253,6 +1258,15 @@ constexpr uint32_t kIdescMN = kIdesc | (1u << 15) | (1u << 16);
 __device__ __forceinline__ uint64_t sdesc_mn_sw128(uint32_t addr) {
   return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(kWgBox >> 4) << 16) |
          ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+__device__ __forceinline__ void bar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Two bounded waits for the phase with the given parity.
+__device__ __forceinline__ bool bar_wait2(uint64_t* bar, uint32_t parity) {
+  return bar_wait(bar, parity) || bar_wait(bar, parity);
 }
 
 struct WgradMaps {
@@ -1268,12 +1282,15 @@ struct WgradMaps {
 __global__ void __launch_bounds__(kThreads, 1) k_wgrad_tc(const __grid_constant__ WgradMaps W) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   unsigned char* base = tc_smem + ((1024u - (smem_u32(tc_smem) & 1023u)) & 1023u);
-  float* colsum = reinterpret_cast<float*>(base + kWgStages * kWgStage);  // [8][256]
-  uint64_t* full = reinterpret_cast<uint64_t*>(colsum + 8 * kH);         // bytes landed
-  uint64_t* freed = full + kWgStages;                                    // MMAs done
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(freed + kWgStages);
-  const int tid = threadIdx.x, warp = tid >> 5;
+  float* colsum = reinterpret_cast<float*>(base + kWgStages * kWgStage);  // [kWgSumWarps][256]
+  uint64_t* full = reinterpret_cast<uint64_t*>(colsum + kWgSumWarps * kH);  // bytes landed
+  uint64_t* mdone = full + kWgStages;    // the stage's MMAs completed
+  uint64_t* cdone = mdone + kWgStages;   // the stage's columns summed
+  uint64_t* acc = cdone + kWgStages;     // every MMA of the item completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int r = tid & (kRows - 1), g = tid >> 7;
+  constexpr int kSumWarp0 = kThreads / 32 - kWgSumWarps;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
@@ -1285,8 +1302,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_wgrad_tc(const __grid_constant_
   if (tid == 0) {
     for (int s = 0; s < kWgStages; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(full + s)) : "memory");
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(freed + s)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mdone + s)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(cdone + s)),
+                   "r"(kWgSumWarps)
+                   : "memory");
     }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(acc)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -1296,81 +1317,85 @@ __global__ void __launch_bounds__(kThreads, 1) k_wgrad_tc(const __grid_constant_
   const uint32_t tmem_warp = tmem + ((uint32_t)((warp & 3) * 32) << 16);
 
   const int64_t items = W.splits * W.n_problems;
-  uint32_t fph = 0, eph = 0;  // phase parity of each stage's full / freed barrier
-  // thread 0: stages whose copies / MMAs have not been waited for (at most one
-  // of each per stage: a stage is refilled only after both)
-  uint32_t pend_full = 0, pend_freed = 0;
-  bool failed = false;
+  // chunks started in the CTA's earlier items (stage of chunk gc: gc % 3, its
+  // use of that stage: gc / 3) and items finished (phase of acc)
+  uint32_t gbase = 0, nitem = 0;
+  // for the drain after a timed-out wait: chunks copied (producer thread),
+  // chunks committed and whether an acc commit is unwaited (MMA thread)
+  uint32_t n_issued = 0, n_committed = 0;
+  bool acc_pending = false, failed = false;
   for (int64_t item = blockIdx.x; item < items && !failed; item += gridDim.x) {
     const int q = (int)(item / W.splits);
     const int64_t kb = (item % W.splits) * W.kchunk;
     const int64_t ke = kb + W.kchunk < W.K ? kb + W.kchunk : W.K;
     if (kb >= ke) continue;  // the same for every thread
     const int nch = (int)((ke - kb) / 64);
-    // thread 0: the TMA copies of chunk c into its stage
-    auto issue = [&](int c) {
-      const int s = c % kWgStages;
-      unsigned char* st = base + s * kWgStage;
-      bar_expect_tx(full + s, kWgStage);
-      const int y = (int)(kb + 64 * c);
-      for (int j = 0; j < 4; ++j) tma_load_2d(st + j * kWgBox, &W.a[q], 64 * j, y, full + s);
-      for (int j = 0; j < 4; ++j) tma_load_2d(st + kWgA + j * kWgBox, &W.b[q], 64 * j, y, full + s);
-      pend_full |= 1u << s;
-    };
-    // thread 0: wait (bounded) for the MMAs that read stage s
-    auto wait_freed = [&](int s) -> bool {
-      bool ok = bar_wait(freed + s, (eph >> s) & 1u);
-      if (!ok) ok = bar_wait(freed + s, (eph >> s) & 1u);
-      if (ok) {
-        eph ^= 1u << s;
-        pend_freed &= ~(1u << s);
-      }
-      return ok;
-    };
-    bool t0_ok = true;
-    if (tid == 0) {
-      issue(0);
-      if (nch > 1) issue(1);
-    }
-    // columns 8 (tid % 32) .. + 7 of A summed over the item's rows k with
-    // k % 8 = tid / 32
+    bool ok = true;
+    // columns 8 lane .. + 7 of A summed over the item's rows k with
+    // k % 4 = (column-sum warp index)
     float racc[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) racc[e] = 0.f;
-    for (int c = 0; c < nch; ++c) {
-      const int s = c % kWgStages;
-      bool ok = bar_wait(full + s, (fph >> s) & 1u);  // the chunk's bytes are in shared memory
-      if (!ok) ok = bar_wait(full + s, (fph >> s) & 1u);
-      if (ok) {
-        fph ^= 1u << s;
-        pend_full &= ~(1u << s);
+    if (warp == 0) {
+      if (lane == 0) {
+        // producer: a stage is refilled once its previous chunk's MMAs are
+        // done and its columns summed
+        for (int c = 0; c < nch; ++c) {
+          const uint32_t gc = gbase + (uint32_t)c, s = gc % kWgStages, u = gc / kWgStages;
+          if (u > 0 && !(bar_wait2(mdone + s, (u - 1) & 1u) && bar_wait2(cdone + s, (u - 1) & 1u))) {
+            ok = false;
+            break;
+          }
+          unsigned char* st = base + s * kWgStage;
+          bar_expect_tx(full + s, kWgStage);
+          const int y = (int)(kb + 64 * c);
+          for (int j = 0; j < 4; ++j) tma_load_2d(st + j * kWgBox, &W.a[q], 64 * j, y, full + s);
+          for (int j = 0; j < 4; ++j)
+            tma_load_2d(st + kWgA + j * kWgBox, &W.b[q], 64 * j, y, full + s);
+          n_issued = gc + 1;
+        }
       }
-      if (__syncthreads_or(!ok)) {
-        failed = true;
-        break;
+    } else if (warp == 1) {
+      if (lane == 0) {
+        // MMA issuer: a chunk's 8 MMAs as soon as it has landed
+        for (int c = 0; c < nch; ++c) {
+          const uint32_t gc = gbase + (uint32_t)c, s = gc % kWgStages, u = gc / kWgStages;
+          if (!bar_wait2(full + s, u & 1u)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+          const uint32_t a0 = smem_u32(base + s * kWgStage), b0 = a0 + kWgA;
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              mma_bf16(tmem + 256u * h, sdesc_mn_sw128(a0 + 2u * kWgBox * h + 2048u * k),
+                       sdesc_mn_sw128(b0 + 2048u * k), kIdescMN, (c > 0 || k > 0) ? 1u : 0u);
+          mma_commit(mdone + s);
+          n_committed = gc + 1;
+        }
+        if (ok) {
+          mma_commit(acc);  // arrives once every MMA issued so far has completed
+          acc_pending = true;
+        }
       }
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const unsigned char* st = base + s * kWgStage;
-      if (tid == 0) {
-        const uint32_t a0 = smem_u32(st), b0 = smem_u32(st + kWgA);
+    } else if (warp >= kSumWarp0) {
+      // column sums: lane l adds columns 8 l .. 8 l + 7 (box l / 8, 16-byte
+      // chunk l % 8 XOR-ed with the row's k % 8 by the swizzle) of the rows
+      // k = sw + 4 j; a warp's load covers one row's 512 bytes
+      const int sw = warp - kSumWarp0;
+      for (int c = 0; c < nch; ++c) {
+        const uint32_t gc = gbase + (uint32_t)c, s = gc % kWgStages, u = gc / kWgStages;
+        if (!__all_sync(0xffffffffu, bar_wait2(full + s, u & 1u))) {
+          ok = false;
+          break;
+        }
+        const unsigned char* cp = base + s * kWgStage + (lane >> 3) * kWgBox;
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
-#pragma unroll
-          for (int k = 0; k < 4; ++k)
-            mma_bf16(tmem + 256u * h, sdesc_mn_sw128(a0 + 2u * kWgBox * h + 2048u * k),
-                     sdesc_mn_sw128(b0 + 2048u * k), kIdescMN, (c > 0 || k > 0) ? 1u : 0u);
-        mma_commit(freed + s);
-        pend_freed |= 1u << s;
-      }
-      {
-        // the 16-byte chunk of columns 8 og .. 8 og + 7 in rows k = rk + 8 j:
-        // box og / 8, chunk og % 8 XOR-ed with k % 8 = rk by the swizzle (a
-        // warp's loads cover one row's 512 bytes: conflict-free)
-        const int og = tid & 31, rk = tid >> 5;
-        const unsigned char* cp = st + (og >> 3) * kWgBox + rk * 128 + (((og & 7) ^ rk) << 4);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const uint4 v = *reinterpret_cast<const uint4*>(cp + j * 1024);
+        for (int j = 0; j < 64 / kWgSumWarps; ++j) {
+          const int k = sw + kWgSumWarps * j;
+          const uint4 v = *reinterpret_cast<const uint4*>(cp + k * 128 + (((lane & 7) ^ (k & 7)) << 4));
           const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
@@ -1379,43 +1404,42 @@ __global__ void __launch_bounds__(kThreads, 1) k_wgrad_tc(const __grid_constant_
             racc[2 * e + 1] += __high2float(p);
           }
         }
-      }
-      // chunk c + 2 goes into the stage chunk c - 1 used, once its MMAs are done
-      if (tid == 0 && c + 2 < nch) {
-        if (c >= 1 && !wait_freed((c + 2) % kWgStages)) t0_ok = false;
-        if (t0_ok) issue(c + 2);
-      }
-      // the row-sum reads of stage s are done before its refill
-      if (__syncthreads_or(!t0_ok)) {
-        failed = true;
-        break;
+        __syncwarp();
+        if (lane == 0) bar_arrive(cdone + s);
       }
     }
-    // the MMAs still unwaited: those of the last three chunks (all, if fewer)
-    if (tid == 0 && !failed)
-      for (int c = nch - 3 > 0 ? nch - 3 : 0; c < nch; ++c)
-        if (!wait_freed(c % kWgStages)) t0_ok = false;
-    {
-      float4* cs = reinterpret_cast<float4*>(colsum + (tid >> 5) * kH + 8 * (tid & 31));
-      cs[0] = make_float4(racc[0], racc[1], racc[2], racc[3]);
-      cs[1] = make_float4(racc[4], racc[5], racc[6], racc[7]);
-    }
-    if (__syncthreads_or(failed || !t0_ok)) {
+    if (__syncthreads_or(!ok)) {
       failed = true;
       break;
     }
+    // every MMA of the item has completed: the accumulators are final
+    const bool aok = bar_wait2(acc, nitem & 1u);
+    if (warp == 1 && lane == 0 && aok) acc_pending = false;
+    if (warp >= kSumWarp0) {
+      float4* cs = reinterpret_cast<float4*>(colsum + (warp - kSumWarp0) * kH + 8 * lane);
+      cs[0] = make_float4(racc[0], racc[1], racc[2], racc[3]);
+      cs[1] = make_float4(racc[4], racc[5], racc[6], racc[7]);
+    }
+    if (__syncthreads_or(!aok)) {
+      failed = true;
+      break;
+    }
+    ++nitem;
+    gbase += (uint32_t)nch;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (W.rowsum[q]) {
-      // column tid: the eight row classes' sums in a fixed order
+      // column tid: the row classes' sums in a fixed order
       float cs = 0.f;
 #pragma unroll
-      for (int k = 0; k < 8; ++k) cs += colsum[k * kH + tid];
+      for (int k = 0; k < kWgSumWarps; ++k) cs += colsum[k * kH + tid];
       atomicAdd(W.rowsum[q] + tid, cs);
     }
     // ---- epilogue: each half as eight FP32 boxes of 32 columns x 128 rows
-    // (128-byte swizzle) in the freed stages, added to C by TMA ----
+    // (128-byte swizzle) in the freed stages, added to C by TMA; the CTA's
+    // first half and first box rotate with its index ----
 #pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
+    for (int hh = 0; hh < 2; ++hh) {
+      const int h = hh ^ (int)((blockIdx.x >> 3) & 1u);
 #pragma unroll 1
       for (int cc = 4 * g; cc < 4 * g + 4; ++cc) {
         uint32_t v[32];
@@ -1431,20 +1455,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_wgrad_tc(const __grid_constant_
       __syncthreads();
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       if (tid == 0) {
-        for (int b = 0; b < 8; ++b) tma_reduce_add_2d(&W.o[q], 32 * b, 128 * h, base + b * kAtomA);
+        for (int b0 = 0; b0 < 8; ++b0) {
+          const int b = (b0 + (int)blockIdx.x) & 7;
+          tma_reduce_add_2d(&W.o[q], 32 * b, 128 * h, base + b * kAtomA);
+        }
         bulk_commit();
         bulk_wait_read();  // the staging may be overwritten once the TMA has read it
       }
       __syncthreads();
     }
   }
-  if (failed && tid == 0) {
-    atomicOr(W.err, 1u);
+  if (failed) {
+    if (tid == 0) atomicOr(W.err, 1u);
     // before the shared memory and TMEM are given up: one more bounded wait
-    // for every copy and MMA still in flight
-    for (int s = 0; s < kWgStages; ++s) {
-      if ((pend_full >> s) & 1u) bar_wait(full + s, (fph >> s) & 1u);
-      if ((pend_freed >> s) & 1u) bar_wait(freed + s, (eph >> s) & 1u);
+    // for the copies (producer) and MMAs (issuer) possibly still in flight
+    if (warp == 0 && lane == 0)
+      for (uint32_t gc = n_issued > kWgStages ? n_issued - kWgStages : 0; gc < n_issued; ++gc)
+        bar_wait(full + gc % kWgStages, (gc / kWgStages) & 1u);
+    if (warp == 1 && lane == 0) {
+      for (uint32_t gc = n_committed > kWgStages ? n_committed - kWgStages : 0; gc < n_committed;
+           ++gc)
+        bar_wait(mdone + gc % kWgStages, (gc / kWgStages) & 1u);
+      if (acc_pending) bar_wait(acc, nitem & 1u);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
