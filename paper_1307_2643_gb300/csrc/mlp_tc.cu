@@ -108,8 +108,21 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem)), "l"(gmem));
+__device__ __forceinline__ void bar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+// from global to shared memory, completing on the mbarrier.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes,
+                                              uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
@@ -152,8 +165,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const MlpTcParam
   unsigned char* base = tc_smem + ((1024u - (smem_u32(tc_smem) & 1023u)) & 1023u);
   unsigned char* As = base;
   unsigned char* Bs = base + kABytes;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(Bs + kBBytes);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(Bs + kBBytes);  // MMAs done
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
+  uint64_t* wbar = bar + 2;  // weight image landed in tile B
   float* sW1 = reinterpret_cast<float*>(Bs + kBBytes + 64);  // [kH][kMaxIn]
   float* sb1 = sW1 + kH * kMaxIn;
   float* sbh = sb1 + kH;                       // [kMlpTcMaxGemm][kH]
@@ -173,6 +187,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const MlpTcParam
   }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(wbar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   for (int e = tid; e < kH * kMaxIn; e += kThreads) {
@@ -189,13 +204,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const MlpTcParam
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   const uint32_t tmem_warp = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-  uint32_t parity = 0;
-  bool failed = false;
+  uint32_t parity = 0, wparity = 0;
+  bool failed = false, wpend = false;
   // weights of the first layer for the first tile; later copies are issued as
-  // soon as the previous MMAs have released tile B, so they overlap the epilogue
+  // soon as the previous MMAs have released tile B, so they overlap the
+  // epilogue (one bulk copy, started by thread 0, tracked by every thread)
   auto fetch_weights = [&](int l) {
-    const unsigned char* src = reinterpret_cast<const unsigned char*>(P.Wimg[l]);
-    for (uint32_t c = tid; c < kBBytes / 16; c += kThreads) cp_async16(Bs + 16 * c, src + 16 * c);
+    if (tid == 0) {
+      bar_expect_tx(wbar, kBBytes);
+      bulk_copy_g2s(Bs, P.Wimg[l], kBBytes, wbar);
+    }
+    wpend = true;
   };
   if (blockIdx.x < P.n_tiles) fetch_weights(0);
 
@@ -243,13 +262,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const MlpTcParam
     }
     // ---- hidden layers on the tensor cores ----
     for (int l = 0; l < P.n_gemm; ++l) {
-      asm volatile("cp.async.wait_all;\n" ::: "memory");  // this layer's weights are in B
-      // generic-proxy writes of A and B -> visible to the tensor cores
+      // generic-proxy writes of A -> visible to the tensor cores
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       __syncthreads();
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      if (tid == 0) {
+      bool wok = bar_wait(wbar, wparity);  // this layer's weights are in B
+      if (!wok) wok = bar_wait(wbar, wparity);
+      if (wok) {
+        wparity ^= 1u;
+        wpend = false;
+      }
+      if (tid == 0 && wok) {
         const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
 #pragma unroll 1
         for (int k = 0; k < kH / 16; ++k)
@@ -257,8 +281,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const MlpTcParam
                    kIdesc, k > 0 ? 1u : 0u);
         mma_commit(bar);
       }
-      bool ok = bar_wait(bar, parity);
-      if (!ok) ok = bar_wait(bar, parity);  // a second bounded wait before giving up
+      bool ok = wok && bar_wait(bar, parity);
+      if (wok && !ok) ok = bar_wait(bar, parity);  // a second bounded wait before giving up
       parity ^= 1u;
       if (__syncthreads_or(!ok)) {
         if (tid == 0) atomicOr(P.err, 1u);
@@ -339,8 +363,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const MlpTcParam
   }
   // a timed-out MMA wait: one more bounded wait for those MMAs before the
   // TMEM is given up (the phase that did not complete has parity ^ 1)
-  if (failed && tid == 0) bar_wait(bar, parity ^ 1u);
-  asm volatile("cp.async.wait_all;\n" ::: "memory");  // no copy outlives the kernel
+  if (failed && tid == 0) {
+    bar_wait(bar, parity ^ 1u);
+    if (wpend) bar_wait(wbar, wparity);  // a weight copy still in flight
+  }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -358,22 +384,7 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
          (1ull << 46) | (2ull << 61);
 }
 
-__device__ __forceinline__ void bar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
 
-// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
-// from global to shared memory, completing on the mbarrier.
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes,
-                                              uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
 
 // One 2D TMA box (64 columns x the map's box rows) at column x, row y.
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
@@ -1653,6 +1664,10 @@ bool mlp_tc_supported(int n_in, int hidden, int n_hidden, int n_out) {
 
 template <bool TRAIN>
 cudaError_t launch_forward_tc(const MlpTcParams& p, int sm_count, cudaStream_t s) {
+  // weight images: one bulk copy each (16-byte aligned)
+  if (p.n_gemm < 1 || p.n_gemm > kMlpTcMaxGemm) return cudaErrorInvalidValue;
+  for (int l = 0; l < p.n_gemm; ++l)
+    if (!p.Wimg[l] || (uintptr_t)p.Wimg[l] % 16 != 0) return cudaErrorInvalidValue;
   auto k = p.n_in == 4 ? k_mlp_forward_tc<4, TRAIN> : k_mlp_forward_tc<0, TRAIN>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
   if (e != cudaSuccess) return e;
