@@ -661,6 +661,14 @@ __global__ void k_transpose(const __nv_bfloat16* __restrict__ in, int64_t rows, 
 // element (o, i) at (o / 8) * (8 n) + (i / 8) * 64 + (o % 8) * 8 + i % 8, and
 // W^T in the same image (imgT): element (o, i) of W at
 // (i / 8) * (8 n) + (o / 8) * 64 + (i % 8) * 8 + o % 8.
+// Index of element (n, k) of an hn x hn bf16 matrix in its tensor-core
+// image (the B operand of the tcgen05 kernels): 128-byte-swizzled K-major,
+// 64-column blocks of hn rows x 128 bytes, a row's 16-byte chunks XOR-ed with
+// the row index mod 8.
+__device__ __forceinline__ int64_t img_index(int n, int k, int hn) {
+  return (int64_t)(k >> 6) * hn * 64 + n * 64 + ((((k >> 3) & 7) ^ (n & 7)) << 3) + (k & 7);
+}
+
 struct Bf16Jobs {
   const float* W[16];
   __nv_bfloat16* wb[16];
@@ -724,7 +732,7 @@ __global__ void __launch_bounds__(256)
       v[base + e] = vv[k];
       const __nv_bfloat16 bv = __float2bfloat16_rn(pi);
       wb[e] = bv;
-      if (img) img[(int64_t)(o >> 3) * (8 * hn) + (ii >> 3) * 64 + (o & 7) * 8 + (ii & 7)] = bv;
+      if (img) img[img_index(o, ii, hn)] = bv;
       tile[ty + 8 * k][tx] = bv;
     }
     __syncthreads();
@@ -734,7 +742,7 @@ __global__ void __launch_bounds__(256)
       const int o = o0 + tx, ii = i0 + ty + 8 * k;
       const __nv_bfloat16 bv = tile[tx][ty + 8 * k];
       wbt[(int64_t)ii * hn + o] = bv;
-      if (imgT) imgT[(int64_t)(ii >> 3) * (8 * hn) + (o >> 3) * 64 + (ii & 7) * 8 + (o & 7)] = bv;
+      if (imgT) imgT[img_index(ii, o, hn)] = bv;
     }
     return;
   }
@@ -767,8 +775,8 @@ __global__ void k_to_bf16_pair(const Bf16Jobs jobs, int n) {
     const __nv_bfloat16 v = __float2bfloat16_rn(W[e]);
     wb[e] = v;
     wbt[(int64_t)i * n + o] = v;
-    if (img) img[(int64_t)(o >> 3) * (8 * n) + (i >> 3) * 64 + (o & 7) * 8 + (i & 7)] = v;
-    if (imgT) imgT[(int64_t)(i >> 3) * (8 * n) + (o >> 3) * 64 + (i & 7) * 8 + (o & 7)] = v;
+    if (img) img[img_index(o, i, n)] = v;
+    if (imgT) imgT[img_index(i, o, n)] = v;
   }
 }
 

@@ -6,16 +6,18 @@
 // columns of half t / 128.  The activations of a tile never leave the SM:
 //   * input layer (K = n_in, FP32 on the CUDA cores) -> bf16 tile A in shared
 //     memory (128 x 256, K-major core-matrix layout, 64 KB);
-//   * each hidden 256 -> 256 layer: its bf16 weights (already stored in the
-//     same core-matrix layout in global memory, 128 KB) are copied into
-//     shared tile B; one thread issues 16 tcgen05.mma (M 128, N 256, K 16,
+//   * each hidden 256 -> 256 layer: its bf16 weights (stored in global memory
+//     as a 128 KB image in the 128-byte-swizzled K-major layout: four
+//     64-column blocks of 256 rows x 128 bytes, a row's 16-byte chunks XOR-ed
+//     with the row index mod 8) are copied into shared tile B by one bulk
+//     copy; one thread issues 16 tcgen05.mma (M 128, N 256, K 16,
 //     bf16 x bf16 -> FP32) into 256 TMEM columns and commits them to an
 //     mbarrier; every warp then reads its 32 TMEM lanes (rows) with
 //     tcgen05.ld, adds the bias, applies ReLU and writes the bf16 result back
 //     into tile A as the next layer's operand;
 //   * the last hidden layer's epilogue feeds the thin output layer (N = 3,
 //     FP32) and the normalisation directly.
-// Shared-memory operand layout (no swizzle, K-major): 8 x 8 bf16 core
+// Tile A's layout here (no swizzle, K-major): 8 x 8 bf16 core
 // matrices of 128 contiguous bytes (row r of the core matrix at 16 r); the
 // core matrix of rows 8g.. and columns 8j.. sits at g * SBO + j * LBO with
 // LBO = 128 B (next 8 columns, the K direction) and SBO = 4096 B (next 8
@@ -43,6 +45,7 @@ constexpr int kThreads = 256;  // two warpgroups; warp w reads TMEM lanes 32 (w 
 constexpr int kMaxIn = 8;
 constexpr uint32_t kABytes = kRows * kH * 2;
 constexpr uint32_t kBBytes = kH * kH * 2;
+constexpr uint32_t kBBlock = kH * 128;     // tile B: 64-column blocks of 256 rows x 128 B
 constexpr uint32_t kLbo = 128;             // next 8-column (K) group
 constexpr uint32_t kSbo = (kH / 8) * 128;  // next 8-row group: 4096
 constexpr uint32_t kTmemCols = 256;
@@ -68,6 +71,14 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
   return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Descriptor of a 128-byte-swizzled K-major operand: start address, leading
+// byte offset 16 (unused within a swizzle atom), 1024 bytes between groups
+// of 8 rows, version 1, swizzle mode 2 (128 B) in bits 61-63.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         (1ull << 46) | (2ull << 61);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
@@ -277,8 +288,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const MlpTcParam
         const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
 #pragma unroll 1
         for (int k = 0; k < kH / 16; ++k)
-          mma_bf16(tmem, sdesc(a0 + 2u * k * kLbo, kLbo, kSbo), sdesc(b0 + 2u * k * kLbo, kLbo, kSbo),
-                   kIdesc, k > 0 ? 1u : 0u);
+          mma_bf16(tmem, sdesc(a0 + 2u * k * kLbo, kLbo, kSbo),
+                   sdesc_sw128(b0 + (uint32_t)(k >> 2) * kBBlock + 32u * (uint32_t)(k & 3)), kIdesc,
+                   k > 0 ? 1u : 0u);
         mma_commit(bar);
       }
       bool ok = wok && bar_wait(bar, parity);
@@ -376,13 +388,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const MlpTcParam
                  : "memory");
 }
 
-// Descriptor of a 128-byte-swizzled K-major operand: start address, leading
-// byte offset 16 (unused within a swizzle atom), 1024 bytes between groups
-// of 8 rows, version 1, swizzle mode 2 (128 B) in bits 61-63.
-__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
-  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         (1ull << 46) | (2ull << 61);
-}
 
 
 
@@ -610,7 +615,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll 1
       for (int k = 0; k < kH / 16; ++k)
         mma_bf16(tmem, sdesc_sw128(a0 + (uint32_t)(k >> 2) * 16384u + 32u * (uint32_t)(k & 3)),
-                 sdesc(b0 + 2u * k * kLbo, kLbo, kSbo), kIdesc, k > 0 ? 1u : 0u);
+                 sdesc_sw128(b0 + (uint32_t)(k >> 2) * kBBlock + 32u * (uint32_t)(k & 3)), kIdesc,
+                 k > 0 ? 1u : 0u);
       mma_commit(bar);
     }
     bool ok = wok && bar_wait(bar, parity);

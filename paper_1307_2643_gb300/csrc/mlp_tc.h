@@ -18,8 +18,9 @@ struct MlpTcParams {
   int64_t n_tiles;  // n / 128
   const float* W1;  // [256][n_in]
   const float* b1;
-  // hidden layer weights as bf16 core-matrix images: element (o, i) of W at
-  // (o / 8) * 2048 + (i / 8) * 64 + (o % 8) * 8 + i % 8
+  // hidden layer weights as bf16 tensor-core images (128-byte-swizzled
+  // K-major): element (o, i) of W at (i / 64) * 16384 + o * 64 +
+  // (((i / 8) % 8) ^ (o % 8)) * 8 + i % 8
   const __nv_bfloat16* Wimg[kMlpTcMaxGemm];
   const float* bh[kMlpTcMaxGemm];
   const float* Wout;  // [3][256]
@@ -96,8 +97,8 @@ struct MlpTrainTcParams {
   const float* W1;     // [256][n_in]
   const float* b1;
   // forward images of the hidden weights W_{k+1} (as MlpTcParams::Wimg) and
-  // images of their transposes: element (o, i) of W at
-  // (i / 8) * 2048 + (o / 8) * 64 + (i % 8) * 8 + o % 8
+  // the same images of their transposes: element (o, i) of W at
+  // (o / 64) * 16384 + i * 64 + (((o / 8) % 8) ^ (i % 8)) * 8 + o % 8
   const __nv_bfloat16* Wimg[kMlpTrainGemm];
   const __nv_bfloat16* WimgT[kMlpTrainGemm];
   const float* bh[kMlpTrainGemm];
