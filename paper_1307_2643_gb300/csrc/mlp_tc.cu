@@ -456,9 +456,14 @@ __device__ __forceinline__ void bulk_wait_all() {
 // (activations, backward signals), so the two give the same step up to the
 // order of FP32 summation.
 // ---------------------------------------------------------------------------
+// The column tile S of the training kernel: 32 rows (n) x 128 columns (the
+// tile's rows r) of bf16, 128-byte-swizzled K-major (two 64-column blocks of
+// 32 rows x 128 bytes): rows 0..2 / 3..5 the high / low bf16 parts of dy,
+// row 8 ones, rows 16..23 / 24..31 the high / low parts of the inputs x.
+constexpr uint32_t kSBytes = 32 * kRows * 2;
 constexpr size_t kTrainFloats = kH * kMaxIn + kH + kMlpTrainGemm * kH + 3 * kH + 4 + 6 * kRows +
-                                3 * kRows + kRows + kRows * kMaxIn;
-constexpr size_t kTrainSmem = 1024 + kABytes + kBBytes + 64 + kTrainFloats * 4;
+                                kRows;
+constexpr size_t kTrainSmem = 1024 + kABytes + kBBytes + kSBytes + 64 + kTrainFloats * 4;
 static_assert(kTrainSmem <= 232448, "shared memory of the training kernel");
 static_assert(kH == kThreads && (kH * kMaxIn) % kThreads == 0, "parameter staging of the training kernel");
 
@@ -469,6 +474,43 @@ static_assert(kH == kThreads && (kH * kMaxIn) % kThreads == 0, "parameter stagin
 // x 128 rows with the 128-byte swizzle.
 __device__ __forceinline__ uint32_t sw_chunk(int r, int q) {
   return (uint32_t)((q >> 3) * 16384 + r * 128 + (((q & 7) ^ (r & 7)) << 4));
+}
+
+// Byte offset of element (n, r) in the column tile S.
+__device__ __forceinline__ uint32_t s_elem(int n, int r) {
+  return (uint32_t)((r >> 6) * 4096 + n * 128 + ((((r & 63) >> 3) ^ (n & 7)) << 4) + (r & 7) * 2);
+}
+
+// bf16 high and low parts of x: x ~ hi + lo to 2^-16 relative, and the
+// product of either with a bf16 is exact in FP32.
+__device__ __forceinline__ void split_bf16(float x, unsigned short& hi, unsigned short& lo) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(x);
+  const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+  hi = *reinterpret_cast<const unsigned short*>(&h);
+  lo = *reinterpret_cast<const unsigned short*>(&l);
+}
+
+// Descriptor of a 128-byte-swizzled MN-major operand: 64 MN-contiguous
+// elements per 128-byte row, one row per K; leading byte offset `lbo` between
+// 64-element MN groups, 1024 bytes between groups of 8 K rows.
+__device__ __forceinline__ uint64_t sdesc_mn(uint32_t addr, uint32_t lbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+// kind::f16 instruction descriptors of the column reductions: M 128, N 16 or
+// 32, A MN-major (tile A read by columns), B K-major (tile S).
+constexpr uint32_t kIdescCol16 =
+    (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (2u << 17) | ((uint32_t)(kRows >> 4) << 24);
+constexpr uint32_t kIdescCol32 =
+    (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (4u << 17) | ((uint32_t)(kRows >> 4) << 24);
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                 "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
 
 // ReLU masks.  A half of a packed pair of ReLU outputs (bf16, +0, -0 or
@@ -504,18 +546,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   unsigned char* base = tc_smem + ((1024u - (smem_u32(tc_smem) & 1023u)) & 1023u);
   unsigned char* As = base;
   unsigned char* Bs = base + kABytes;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(Bs + kBBytes);  // MMAs done
+  unsigned char* Ss = Bs + kBBytes;  // column tile S
+  uint64_t* bar = reinterpret_cast<uint64_t*>(Ss + kSBytes);  // MMAs done
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
   uint64_t* wbar = bar + 2;  // weight image landed in tile B
-  float* sW1 = reinterpret_cast<float*>(Bs + kBBytes + 64);  // [kH][kMaxIn]
+  float* sW1 = reinterpret_cast<float*>(Ss + kSBytes + 64);  // [kH][kMaxIn]
   float* sb1 = sW1 + kH * kMaxIn;
   float* sbh = sb1 + kH;        // [NG][kH]
   float* sWo = sbh + NG * kH;   // [3][kH]
   float* sbo = sWo + 3 * kH;    // [4]
   float* sy = sbo + 4;          // [2 halves][3][kRows] output-layer partial sums
-  float* sdy = sy + 6 * kRows;  // [3][kRows]
-  float* sl = sdy + 3 * kRows;  // [4 warps][4]: their sums of dy and of the loss terms
-  float* sx = sl + kRows;       // [kRows][kMaxIn] the tile's inputs
+  float* sl = sy + 6 * kRows;   // [4 warps][4]: their sums of dy and of the loss terms
   const int tid = threadIdx.x, warp = tid >> 5;
   const int r = tid & (kRows - 1);  // row of the tile this thread owns
   const int g = tid >> 7;           // warpgroup: columns [128 g, 128 g + 128)
@@ -574,6 +615,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
     for (int k = 0; k < 3; ++k) sWo[tid + k * kThreads] = wov[k];
     if (tid < 3) sbo[tid] = bov;
+    // the ones row of S (the bias gradient's column sums)
+    if (tid < kRows) *reinterpret_cast<unsigned short*>(Ss + s_elem(8, tid)) = 0x3F80u;
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -641,6 +684,36 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   };
+  // the column reduction D[c][n] = sum_r A[r][c] S[n][r] for both column
+  // halves (c in [128 h, 128 h + 128) -> TMEM lanes, columns n_cols h + n):
+  // 2 x 8 MMAs of K 16; false on a timed-out wait
+  auto col_mma = [&](uint32_t idesc, uint32_t n_cols) -> bool {
+    // generic-proxy writes of A and S -> visible to the tensor cores
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (tid == 0) {
+      const uint32_t a0 = smem_u32(As), s0 = smem_u32(Ss);
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h)
+#pragma unroll 1
+        for (int k = 0; k < kRows / 16; ++k)
+          mma_bf16(tmem + n_cols * (uint32_t)h, sdesc_mn(a0 + 32768u * h + 2048u * k, 16384u),
+                   sdesc_sw128(s0 + (uint32_t)(k >> 2) * 4096u + 32u * (uint32_t)(k & 3)), idesc,
+                   k > 0 ? 1u : 0u);
+      mma_commit(bar);
+    }
+    bool ok = bar_wait(bar, parity);
+    if (!ok) ok = bar_wait(bar, parity);
+    parity ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicOr(P.err, 1u);
+      return false;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    return true;
+  };
   // gradient partial sums over this CTA's tiles: output and input layer of
   // column tid; tid 0..2: db_out, tid 3: the loss
   float go0 = 0.f, go1 = 0.f, go2 = 0.f, gib = 0.f, gsmall = 0.f;
@@ -660,8 +733,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int i = 0; i < kMaxIn; ++i) xin[i] = xnext[i];
     load_x(tile + gridDim.x);
     if (g == 0) {
+      // the inputs' high and low parts: rows 16 + i, 24 + i of S
 #pragma unroll
-      for (int i = 0; i < kMaxIn; ++i) sx[r * kMaxIn + i] = xin[i];
+      for (int i = 0; i < NI; ++i) {
+        unsigned short hi, lo;
+        split_bf16(xin[i], hi, lo);
+        *reinterpret_cast<unsigned short*>(Ss + s_elem(16 + i, r)) = hi;
+        *reinterpret_cast<unsigned short*>(Ss + s_elem(24 + i, r)) = lo;
+      }
     }
 #pragma unroll 1
     for (int q = 0; q < 4; ++q) {
@@ -780,9 +859,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     const float dy1 = -(t1 - d * yh1) * inv * inv_n;
     const float dy2 = -(t2 - d * yh2) * inv * inv_n;
     if (g == 0) {
-      sdy[r] = dy0;
-      sdy[kRows + r] = dy1;
-      sdy[2 * kRows + r] = dy2;
+      // dy's high and low parts: rows 0..2, 3..5 of S
+      const float dyk[3] = {dy0, dy1, dy2};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        unsigned short hi, lo;
+        split_bf16(dyk[k], hi, lo);
+        *reinterpret_cast<unsigned short*>(Ss + s_elem(k, r)) = hi;
+        *reinterpret_cast<unsigned short*>(Ss + s_elem(3 + k, r)) = lo;
+      }
       // the output biases' gradients and the loss: sums over this warp's rows
       float s0 = dy0, s1 = dy1, s2 = dy2, s3 = 1.f - d;
 #pragma unroll
@@ -799,37 +884,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         sl[4 * warp + 3] = s3;
       }
     }
-    __syncthreads();
+    // column tid of the output layer's weight gradients, sum_r h_3[r][c] dy[r]:
+    // on the tensor cores with tile A (h_3) as the MN-major operand, the
+    // parts of dy (tile S) as B; D[c][n] in TMEM columns 16 h + n
+    if (!col_mma(kIdescCol16, 16)) {
+      failed = true;
+      break;
+    }
     {
-      // column tid: the output layer's weight gradients over the tile's rows
-      // (a warp reads 64 bytes of one row: four chunks in distinct banks)
-      const unsigned char* cb = As + (tid >> 6) * 16384 + (tid & 7) * 2;
-      const int qc = (tid >> 3) & 7;
-      // two partial sums per output (even and odd rows) halve the FMA chains;
-      // dy of four rows per 16-byte load
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f, b0 = 0.f, b1 = 0.f, b2 = 0.f;
-#pragma unroll 2
-      for (int rr = 0; rr < kRows; rr += 4) {
-        float hv[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-          hv[i] = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(
-              cb + (rr + i) * 128 + ((qc ^ ((rr + i) & 7)) << 4)));
-        const float4 d0 = *reinterpret_cast<const float4*>(sdy + rr);
-        const float4 d1 = *reinterpret_cast<const float4*>(sdy + kRows + rr);
-        const float4 d2 = *reinterpret_cast<const float4*>(sdy + 2 * kRows + rr);
-        a0 = fmaf(d0.z, hv[2], fmaf(d0.x, hv[0], a0));
-        a1 = fmaf(d1.z, hv[2], fmaf(d1.x, hv[0], a1));
-        a2 = fmaf(d2.z, hv[2], fmaf(d2.x, hv[0], a2));
-        b0 = fmaf(d0.w, hv[3], fmaf(d0.y, hv[1], b0));
-        b1 = fmaf(d1.w, hv[3], fmaf(d1.y, hv[1], b1));
-        b2 = fmaf(d2.w, hv[3], fmaf(d2.y, hv[1], b2));
-      }
-      go0 += a0 + b0;
-      go1 += a1 + b1;
-      go2 += a2 + b2;
+      uint32_t dv[8];
+      tmem_ld8(tmem_warp + 16u * (uint32_t)g, dv);
+      go0 += __uint_as_float(dv[0]) + __uint_as_float(dv[3]);
+      go1 += __uint_as_float(dv[1]) + __uint_as_float(dv[4]);
+      go2 += __uint_as_float(dv[2]) + __uint_as_float(dv[5]);
       if (tid < 4) gsmall += (sl[tid] + sl[4 + tid]) + (sl[8 + tid] + sl[12 + tid]);
     }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();  // every column has read h_3 before it is overwritten
     // dz_3 = bf16((dy . W_out[:, c]) where h_3 > 0), in place in tile A
 #pragma unroll 1
@@ -883,42 +953,20 @@ __global__ void __launch_bounds__(kThreads, 1)
       after_epilogue();
     }
     if (failed) break;
-    {
-      // column tid: the input layer's gradients from dz_0 and the tile's inputs
-      const unsigned char* cb = As + (tid >> 6) * 16384 + (tid & 7) * 2;
-      const int qc = (tid >> 3) & 7;
-      // two partial sums per output (even and odd rows) halve the FMA chains
-      float aw[kMaxIn], bw[kMaxIn], ab = 0.f, bb = 0.f;
-#pragma unroll
-      for (int i = 0; i < kMaxIn; ++i) aw[i] = bw[i] = 0.f;
-#pragma unroll 2
-      for (int rr = 0; rr < kRows; rr += 2) {
-        const int R = rr, R2 = rr + 1;
-        const float z = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(
-            cb + R * 128 + ((qc ^ (R & 7)) << 4)));
-        const float z2 = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(
-            cb + R2 * 128 + ((qc ^ (R2 & 7)) << 4)));
-        ab += z;
-        bb += z2;
-        // the rows' inputs by 16-byte loads
-        float xr[kMaxIn], xr2[kMaxIn];
-#pragma unroll
-        for (int i = 0; i < NI; i += 4) {
-          const float4 p = *reinterpret_cast<const float4*>(sx + R * kMaxIn + i);
-          const float4 p2 = *reinterpret_cast<const float4*>(sx + R2 * kMaxIn + i);
-          xr[i] = p.x, xr[i + 1] = p.y, xr[i + 2] = p.z, xr[i + 3] = p.w;
-          xr2[i] = p2.x, xr2[i + 1] = p2.y, xr2[i + 2] = p2.z, xr2[i + 3] = p2.w;
-        }
-#pragma unroll
-        for (int i = 0; i < NI; ++i) {
-          aw[i] = fmaf(z, xr[i], aw[i]);
-          bw[i] = fmaf(z2, xr2[i], bw[i]);
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < NI; ++i) gi[i] += aw[i] + bw[i];
-      gib += ab + bb;
+    // column tid of the input layer's gradients, sum_r dz_0[r][c] x[r][i] and
+    // sum_r dz_0[r][c]: tile A (dz_0) against S's inputs and ones row
+    if (!col_mma(kIdescCol32, 32)) {
+      failed = true;
+      break;
     }
+    {
+      uint32_t dv[32];
+      tmem_ld32(tmem_warp + 32u * (uint32_t)g, dv);
+      gib += __uint_as_float(dv[8]);
+#pragma unroll
+      for (int i = 0; i < NI; ++i) gi[i] += __uint_as_float(dv[16 + i]) + __uint_as_float(dv[24 + i]);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();  // tile A and the staged inputs are rewritten by the next tile
   }
   if (!failed) {
