@@ -459,11 +459,17 @@ __device__ __forceinline__ void bulk_wait_all() {
 // The column tile S of the training kernel: 32 rows (n) x 128 columns (the
 // tile's rows r) of bf16, 128-byte-swizzled K-major (two 64-column blocks of
 // 32 rows x 128 bytes): rows 0..2 / 3..5 the high / low bf16 parts of dy,
-// row 8 ones, rows 16..23 / 24..31 the high / low parts of the inputs x.
+// rows 9..11 the high parts again, row 8 ones, rows 6, 7, 12..15 zero, rows
+// 16..23 / 24..31 the high / low parts of the inputs x.
 constexpr uint32_t kSBytes = 32 * kRows * 2;
-constexpr size_t kTrainFloats = kH * kMaxIn + kH + kMlpTrainGemm * kH + 3 * kH + 4 + 6 * kRows +
-                                kRows;
-constexpr size_t kTrainSmem = 1024 + kABytes + kBBytes + kSBytes + 64 + kTrainFloats * 4;
+// Region U (8 KB): the output layer's partial sums (FP32 [2][3][kRows]), then,
+// once they are read, the W_out tile: [256 c][16 k] bf16, K-major without
+// swizzle (8 x 8 core matrices: LBO 128 B next 8 k, SBO 256 B next 8 c),
+// k = 0..2 and 3..5 the high parts of W_out[k % 3][c], 9..11 the low parts.
+constexpr uint32_t kUBytes = kH * 16 * 2;
+static_assert(kUBytes >= 6 * kRows * 4, "region U holds the output-layer partial sums");
+constexpr size_t kTrainFloats = kH * kMaxIn + kH + kMlpTrainGemm * kH + 3 * kH + 4 + kRows;
+constexpr size_t kTrainSmem = 1024 + kABytes + kBBytes + kSBytes + kUBytes + 64 + kTrainFloats * 4;
 static_assert(kTrainSmem <= 232448, "shared memory of the training kernel");
 static_assert(kH == kThreads && (kH * kMaxIn) % kThreads == 0, "parameter staging of the training kernel");
 
@@ -504,6 +510,8 @@ constexpr uint32_t kIdescCol16 =
     (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (2u << 17) | ((uint32_t)(kRows >> 4) << 24);
 constexpr uint32_t kIdescCol32 =
     (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (4u << 17) | ((uint32_t)(kRows >> 4) << 24);
+// dz_3 = dy W_out: M 128 (rows), N 256, K 16, A MN-major (tile S), B K-major
+constexpr uint32_t kIdescDz = kIdesc | (1u << 15);
 
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
@@ -546,17 +554,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   unsigned char* base = tc_smem + ((1024u - (smem_u32(tc_smem) & 1023u)) & 1023u);
   unsigned char* As = base;
   unsigned char* Bs = base + kABytes;
-  unsigned char* Ss = Bs + kBBytes;  // column tile S
-  uint64_t* bar = reinterpret_cast<uint64_t*>(Ss + kSBytes);  // MMAs done
+  unsigned char* Ss = Bs + kBBytes;   // column tile S
+  unsigned char* Us = Ss + kSBytes;   // region U
+  uint64_t* bar = reinterpret_cast<uint64_t*>(Us + kUBytes);  // MMAs done
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
   uint64_t* wbar = bar + 2;  // weight image landed in tile B
-  float* sW1 = reinterpret_cast<float*>(Ss + kSBytes + 64);  // [kH][kMaxIn]
+  float* sW1 = reinterpret_cast<float*>(Us + kUBytes + 64);  // [kH][kMaxIn]
   float* sb1 = sW1 + kH * kMaxIn;
   float* sbh = sb1 + kH;        // [NG][kH]
   float* sWo = sbh + NG * kH;   // [3][kH]
   float* sbo = sWo + 3 * kH;    // [4]
-  float* sy = sbo + 4;          // [2 halves][3][kRows] output-layer partial sums
-  float* sl = sy + 6 * kRows;   // [4 warps][4]: their sums of dy and of the loss terms
+  float* sl = sbo + 4;  // [4 warps][4]: their sums of dy and of the loss terms
+  float* sy = reinterpret_cast<float*>(Us);  // [2 halves][3][kRows] output-layer partial sums
   const int tid = threadIdx.x, warp = tid >> 5;
   const int r = tid & (kRows - 1);  // row of the tile this thread owns
   const int g = tid >> 7;           // warpgroup: columns [128 g, 128 g + 128)
@@ -615,8 +624,14 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
     for (int k = 0; k < 3; ++k) sWo[tid + k * kThreads] = wov[k];
     if (tid < 3) sbo[tid] = bov;
-    // the ones row of S (the bias gradient's column sums)
-    if (tid < kRows) *reinterpret_cast<unsigned short*>(Ss + s_elem(8, tid)) = 0x3F80u;
+    // S's ones row (the bias gradient's column sums) and its zero rows (the
+    // dz_3 product reads rows 0..15 against zero W_out columns there)
+    if (tid < kRows) {
+      *reinterpret_cast<unsigned short*>(Ss + s_elem(8, tid)) = 0x3F80u;
+      const int zr[6] = {6, 7, 12, 13, 14, 15};
+#pragma unroll
+      for (int z = 0; z < 6; ++z) *reinterpret_cast<unsigned short*>(Ss + s_elem(zr[z], tid)) = 0;
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -684,24 +699,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   };
-  // the column reduction D[c][n] = sum_r A[r][c] S[n][r] for both column
-  // halves (c in [128 h, 128 h + 128) -> TMEM lanes, columns n_cols h + n):
-  // 2 x 8 MMAs of K 16; false on a timed-out wait
-  auto col_mma = [&](uint32_t idesc, uint32_t n_cols) -> bool {
-    // generic-proxy writes of A and S -> visible to the tensor cores
+  // a tensor-core step on shared-memory operands already written: issue
+  // (thread 0), commit, bounded wait; false on a timed-out wait
+  auto tc_step = [&](auto issue) -> bool {
+    // generic-proxy writes of the operands -> visible to the tensor cores
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (tid == 0) {
-      const uint32_t a0 = smem_u32(As), s0 = smem_u32(Ss);
-#pragma unroll 1
-      for (int h = 0; h < 2; ++h)
-#pragma unroll 1
-        for (int k = 0; k < kRows / 16; ++k)
-          mma_bf16(tmem + n_cols * (uint32_t)h, sdesc_mn(a0 + 32768u * h + 2048u * k, 16384u),
-                   sdesc_sw128(s0 + (uint32_t)(k >> 2) * 4096u + 32u * (uint32_t)(k & 3)), idesc,
-                   k > 0 ? 1u : 0u);
+      issue();
       mma_commit(bar);
     }
     bool ok = bar_wait(bar, parity);
@@ -713,6 +720,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     return true;
+  };
+  // the column reduction D[c][n] = sum_r A[r][c] S[n][r] for both column
+  // halves (c in [128 h, 128 h + 128) -> TMEM lanes, columns n_cols h + n):
+  // 2 x 8 MMAs of K 16
+  auto col_mma = [&](uint32_t idesc, uint32_t n_cols) -> bool {
+    return tc_step([&] {
+      const uint32_t a0 = smem_u32(As), s0 = smem_u32(Ss);
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h)
+#pragma unroll 1
+        for (int k = 0; k < kRows / 16; ++k)
+          mma_bf16(tmem + n_cols * (uint32_t)h, sdesc_mn(a0 + 32768u * h + 2048u * k, 16384u),
+                   sdesc_sw128(s0 + (uint32_t)(k >> 2) * 4096u + 32u * (uint32_t)(k & 3)), idesc,
+                   k > 0 ? 1u : 0u);
+    });
   };
   // gradient partial sums over this CTA's tiles: output and input layer of
   // column tid; tid 0..2: db_out, tid 3: the loss
@@ -867,6 +889,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         split_bf16(dyk[k], hi, lo);
         *reinterpret_cast<unsigned short*>(Ss + s_elem(k, r)) = hi;
         *reinterpret_cast<unsigned short*>(Ss + s_elem(3 + k, r)) = lo;
+        *reinterpret_cast<unsigned short*>(Ss + s_elem(9 + k, r)) = hi;
       }
       // the output biases' gradients and the loss: sums over this warp's rows
       float s0 = dy0, s1 = dy1, s2 = dy2, s3 = 1.f - d;
@@ -899,33 +922,51 @@ __global__ void __launch_bounds__(kThreads, 1)
       go2 += __uint_as_float(dv[2]) + __uint_as_float(dv[5]);
       if (tid < 4) gsmall += (sl[tid] + sl[4 + tid]) + (sl[8 + tid] + sl[12 + tid]);
     }
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();  // every column has read h_3 before it is overwritten
-    // dz_3 = bf16((dy . W_out[:, c]) where h_3 > 0), in place in tile A
+    {
+      // the partial sums are read: region U becomes the W_out tile (column
+      // tid: its 16 k values as two 16-byte chunks)
+      uint32_t wv[8];
+      unsigned short hi[3], lo[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) split_bf16(sWo[k * kH + tid], hi[k], lo[k]);
+      wv[0] = hi[0] | ((uint32_t)hi[1] << 16);
+      wv[1] = hi[2] | ((uint32_t)hi[0] << 16);
+      wv[2] = hi[1] | ((uint32_t)hi[2] << 16);
+      wv[3] = 0u;
+      wv[4] = (uint32_t)lo[0] << 16;
+      wv[5] = lo[1] | ((uint32_t)lo[2] << 16);
+      wv[6] = 0u;
+      wv[7] = 0u;
+      unsigned char* wp = Us + (tid >> 3) * 256 + (tid & 7) * 16;
+      *reinterpret_cast<uint4*>(wp) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+      *reinterpret_cast<uint4*>(wp + 128) = make_uint4(wv[4], wv[5], wv[6], wv[7]);
+    }
+    // dz_3 = bf16((dy . W_out[:, c]) where h_3 > 0): one MMA of K 16 from S's
+    // dy parts (MN-major A) and the W_out tile, then in place in tile A
+    if (!tc_step([&] {
+          mma_bf16(tmem, sdesc_mn(smem_u32(Ss), 4096u), sdesc(smem_u32(Us), 128u, 256u), kIdescDz,
+                   0u);
+        })) {
+      failed = true;
+      break;
+    }
 #pragma unroll 1
     for (int q = 0; q < 4; ++q) {
       const int cc = 4 * g + q;
-      uint32_t w[16];
+      uint32_t v[32];
+      tmem_ld32(tmem_warp + (uint32_t)(cc * 32), v);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         uint4* ap = reinterpret_cast<uint4*>(As + sw_chunk(r, cc * 4 + u));
         const uint4 hq = *ap;
         const uint32_t hw[4] = {hq.x, hq.y, hq.z, hq.w};
+        uint32_t w[4];
 #pragma unroll
-        for (int e = 0; e < 4; e += 2) {
-          // W_out of four columns per 16-byte load
-          const int c0 = (cc * 4 + u) * 8 + 2 * e;
-          const float4 wa = *reinterpret_cast<const float4*>(sWo + c0);
-          const float4 wb = *reinterpret_cast<const float4*>(sWo + kH + c0);
-          const float4 wc = *reinterpret_cast<const float4*>(sWo + 2 * kH + c0);
-          const float z0 = fmaf(dy2, wc.x, fmaf(dy1, wb.x, dy0 * wa.x));
-          const float z1 = fmaf(dy2, wc.y, fmaf(dy1, wb.y, dy0 * wa.y));
-          const float z2 = fmaf(dy2, wc.z, fmaf(dy1, wb.z, dy0 * wa.z));
-          const float z3 = fmaf(dy2, wc.w, fmaf(dy1, wb.w, dy0 * wa.w));
-          w[4 * u + e] = keep_pair(pack_bf16(z0, z1), pair_flags(hw[e], 0), 0);
-          w[4 * u + e + 1] = keep_pair(pack_bf16(z2, z3), pair_flags(hw[e + 1], 0), 0);
-        }
-        *ap = make_uint4(w[4 * u], w[4 * u + 1], w[4 * u + 2], w[4 * u + 3]);
+        for (int e = 0; e < 4; ++e)
+          w[e] = keep_pair(pack_bf16(__uint_as_float(v[8 * u + 2 * e]),
+                                     __uint_as_float(v[8 * u + 2 * e + 1])),
+                           pair_flags(hw[e], 0), 0);
+        *ap = make_uint4(w[0], w[1], w[2], w[3]);
       }
     }
     // ---- backward: dz_{l-1} = (dz_l W_l) where h_{l-1} > 0, l = NG .. 1 ----
