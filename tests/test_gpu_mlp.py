@@ -297,13 +297,15 @@ def test_layered_forward_after_tensor_core_training(torch_dev):
     assert_outputs_close(out[crp.MLP_PATH_TENSOR_CORE_FUSED], out[crp.MLP_PATH_LAYERED])
 
 
-@pytest.mark.parametrize("n", [2048, 128 * 37, 16384])
+@pytest.mark.parametrize("n", [2048, 128 * 37, 16384, 128 * 160])
 def test_tensor_core_training_gradients(torch_dev, n):
     """The training step on the tensor cores (the one-kernel forward, output
     layer and backward signals, then the weight-gradient GEMMs: TMA operand
     boxes, split over K with vector reductions) against the layered mma.sync
     step and the binary64 oracle.  n = 128 * 37 gives K ranges of 320: two
-    chunks per split, the second 64 wide."""
+    chunks per split, the second 64 wide; n = 128 * 160 gives more tiles than
+    a GB300 has SMs (152), so some CTAs of the one-kernel step take a second
+    tile (the next tile's weight copy, inputs and shared tiles reused)."""
     torch = torch_dev
     p = _params(31)
     x, t = _batch(int(1.25 * n), 32)
