@@ -440,13 +440,16 @@ __device__ __forceinline__ void bulk_wait_all() {
 //   * output layer on the CUDA cores: y = W_out h_3 + b_out from the two
 //     warpgroups' partial sums, y_hat = y / |y|, the loss term 1 - y_hat . t
 //     and dy = -(t - (y_hat . t) y_hat) / |y| / n; per column c the output
-//     layer's gradients sum_r dy[r] h_3[r][c]; then
-//     dz_3 = bf16((dy . W_out[:, c]) where h_3 > 0), in place in tile A;
+//     layer's gradients sum_r dy[r] h_3[r][c] (tensor cores: tile A read as
+//     the MN-major operand against dy's high and low bf16 parts in tile S);
+//     then dz_3 = bf16((dy . W_out[:, c]) where h_3 > 0), one MMA of K 16 (the
+//     parts of dy against those of W_out), in place in tile A;
 //   * GEMMs with W_3^T, W_2^T, W_1^T (images of the transposed weights) ->
 //     dz_2, dz_1, dz_0 = bf16(C where h_{l-1} > 0) in tile A (dz_3 .. dz_1 also
 //     written out, row-major, for the weight gradients);
 //   * per column c the input layer's gradients sum_r dz_0[r][c] x[r][i] and
-//     sum_r dz_0[r][c].
+//     sum_r dz_0[r][c] (tensor cores: tile A against x's parts and a ones
+//     row in tile S).
 // The six weight images of a tile are copied into tile B in that order (one
 // bulk copy each, completing on an mbarrier), each as soon as the previous
 // GEMM's MMAs have completed; each GEMM's input in tile A is written out by
@@ -454,7 +457,8 @@ __device__ __forceinline__ void bulk_wait_all() {
 // stay in registers over the CTA's tiles and are added to global memory once.
 // The values are rounded to bf16 where the layered training step rounds them
 // (activations, backward signals), so the two give the same step up to the
-// order of FP32 summation.
+// order of FP32 summation and the 2^-16 relative error of the high and low
+// parts (products of bf16 values are exact in FP32).
 // ---------------------------------------------------------------------------
 // The column tile S of the training kernel: 32 rows (n) x 128 columns (the
 // tile's rows r) of bf16, 128-byte-swizzled K-major (two 64-column blocks of
